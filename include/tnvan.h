@@ -1,0 +1,199 @@
+/*
+ * tnvan.h -- C-ABI of the GB300 (sm_103a) TNVAN hot path.
+ *
+ * TNVAN (tensor-network-based variational autoregressive networks, arXiv
+ * 2504.12037) splits the spins into a width set W and a remainder R (Sec. 2).
+ * For every configuration s of W drawn from an autoregressive network q_theta
+ * (Eq. 6-8) it contracts R exactly, giving the effective energy Etilde(s)
+ * (Eq. 3-4), and reduces the batch to the variational free energy F_q (Eq. 9)
+ * and its score-function gradient (Eq. 10).  This library runs those steps on
+ * one GPU.
+ *
+ * Conventions shared by every call
+ *   - Return value: TNVAN_OK (0) or a negative TNVAN_E_* code.  No exception,
+ *     abort or exit crosses this boundary; the message of the last failure on a
+ *     context is returned by tnvan_last_error().
+ *   - "host" pointers are read during the call and copied; the caller keeps
+ *     ownership.  "device" pointers are borrowed: they must stay valid until the
+ *     work queued on `stream` has finished.  `stream` is a cudaStream_t (NULL =
+ *     the legacy default stream).
+ *   - Calls that launch work are asynchronous on `stream` unless stated.
+ *   - Instances: a context holds instances 0..n-1 (graph + width set +
+ *     network), registered in order.  Batched calls process all of them in one
+ *     launch per stage.  For instance k with D_k width-set spins, per-sample
+ *     outputs sit at:   spins  byte offset  batch * sum_{j<k} D_j, layout [batch][D_k]
+ *                       logq / logZR / dbeta  element offset  k * batch.
+ *   - Per-sample quantity: log Z_R(s) := -beta * Etilde(s)
+ *       = -beta E_1(s) + ln sum_{r in R} exp(-beta E_2(s, r))     (Eq. 4)
+ *     i.e. it includes the W-W energy E_1.  Energies follow Eq. 1:
+ *     E(s) = - sum_<ij> J_ij s_i s_j.
+ *   - Spins are int8 values +1 / -1.
+ *   - Not thread-safe: one host thread drives a context at a time.
+ */
+#ifndef TNVAN_H
+#define TNVAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define TNVAN_OK 0
+#define TNVAN_E_ARG (-1)          /* invalid argument or inconsistent sizes        */
+#define TNVAN_E_NOMEM (-2)        /* device or host allocation failed              */
+#define TNVAN_E_CUDA (-3)         /* a CUDA runtime call or kernel launch failed   */
+#define TNVAN_E_TIMEOUT (-4)      /* a bounded device wait gave up                 */
+#define TNVAN_E_OVERFLOW (-5)     /* a non-finite value reached a reduction        */
+#define TNVAN_E_STATE (-6)        /* call out of order (e.g. no graph yet)         */
+#define TNVAN_E_UNSUPPORTED (-7)  /* shape outside what the kernels implement      */
+
+/* Graph topologies (how the remainder R is contracted). */
+#define TNVAN_LATTICE2D 0  /* Lx x Ly open lattice, spin = y*Lx + x; W = whole columns -> strips */
+#define TNVAN_DENSE 1      /* fully connected; |R| <= 16 summed as a dense block              */
+#define TNVAN_GENERAL 2    /* any graph; R components contracted by variable elimination       */
+
+/* Arithmetic modes for the contractions and network GEMMs. */
+#define TNVAN_FP32 0 /* FP32 everywhere (FP64 only for final log-norms and reductions)   */
+#define TNVAN_TF32 1 /* TF32 tensor-core GEMMs, FP32 accumulate                         */
+#define TNVAN_BF16 2 /* BF16 tensor-core GEMMs / dense block, FP32 accumulate           */
+
+typedef struct tnvan_ctx tnvan_ctx;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tnvan_version(void);
+
+/* Create a context bound to CUDA device `device`.  *out receives the handle.
+ * Errors: TNVAN_E_ARG (out NULL), TNVAN_E_CUDA (bad device). */
+int tnvan_create(tnvan_ctx** out, int device);
+
+/* Release every device buffer the context owns.  Borrowed pointers are not
+ * touched.  Synchronises the device first.  NULL is accepted (no-op). */
+int tnvan_destroy(tnvan_ctx* ctx);
+
+/* Message of the last failed call on `ctx` ("" if none); for ctx == NULL the
+ * last failure of tnvan_create on this thread.  Valid until the next call. */
+const char* tnvan_last_error(const tnvan_ctx* ctx);
+
+/* Define instance `instance` (must be 0..n, n = current count; n appends).
+ * Sec. 2, Eq. 1-2: the Ising graph TN({B},{s}).
+ *   n_spins, n_edges   sizes; edges are undirected, (ei[k], ej[k]) with
+ *                      0 <= ei, ej < n_spins, ei != ej, no repeated pair.
+ *   ei, ej, J          host arrays [n_edges] (copied).
+ *   topology           TNVAN_LATTICE2D | TNVAN_DENSE | TNVAN_GENERAL.
+ *   Lx, Ly, periodic   lattice shape (LATTICE2D only; periodic must be 0).
+ * Redefining an instance drops its width set and network.
+ * Errors: TNVAN_E_ARG, TNVAN_E_UNSUPPORTED (periodic lattice). */
+int tnvan_init_graph(tnvan_ctx* ctx, int instance, int n_spins, int n_edges, const int32_t* ei,
+                     const int32_t* ej, const double* J, int topology, int Lx, int Ly,
+                     int periodic);
+
+/* Set the width set W of `instance` (Sec. 2; Algorithm 1 step 1 takes it as
+ * given).  w: host array [n_w] of distinct spin indices in autoregressive
+ * order (Eq. 6's "predetermined order").  The host planner then builds the
+ * contraction plan of R: lattice strips (W must then be whole columns),
+ * a dense block (|R| <= 16), or per-component elimination programs
+ * (elimination width <= 8).  Plans are independent of beta.
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no graph), TNVAN_E_UNSUPPORTED. */
+int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w);
+
+/* Attach the MADE network of `instance` (Eq. 7, Fig. 1(d)): D = n_w inputs and
+ * outputs, n_hidden (0..2) ReLU hidden layers of widths[0..n_hidden-1]
+ * (each <= 512).  d_params: borrowed device pointer to float32 parameters,
+ * layer by layer W_l [out][in] row-major then b_l [out]; entries outside the
+ * MADE masks are ignored (hidden unit k has degree (k mod max(D-1,1)) + 1,
+ * input/output i has degree i+1).  Count with tnvan_n_params().
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no width set), TNVAN_E_NOMEM. */
+int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* widths,
+                   float* d_params);
+
+/* Number of float32 parameters of instance's network (after set_made), and
+ * the offset of that instance in the packed all-instances gradient layout
+ * used by tnvan_backward / tnvan_adam (sum of n_params of lower instances). */
+int tnvan_n_params(const tnvan_ctx* ctx, int instance, int64_t* n_params, int64_t* offset);
+
+/* Plan summary of `instance`: info[0] n_spins, [1] n_edges, [2] n_w (D),
+ * [3] contraction kind (0 strips, 1 dense, 2 general), [4] number of R
+ * components, [5] largest component (spins), [6] largest elimination width,
+ * [7] number of W-W edges.  info: host array [8]. */
+int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info);
+
+/* Pre-allocate the context's internal workspaces for batches up to
+ * max_batch so that later calls allocate nothing (needed before capturing
+ * calls into a CUDA graph).  Synchronous. */
+int tnvan_reserve(tnvan_ctx* ctx, int max_batch);
+
+/* Algorithm 1 steps (a)-(b) for every instance, in one pass on `stream`:
+ * ancestral sampling from q_theta (Eq. 8: s_i = +1 iff u < sigmoid(x_i), u a
+ * 24-bit uniform from Philox4x32-10 with counter (b, i>>2, step mod 2^32,
+ * instance) and key (seed mod 2^32, seed >> 32), word i & 3, u = (word >> 8)
+ * * 2^-24), log q (Eq. 6, 8) and the exact conditional contraction log Z_R(s)
+ * (Eq. 3-4).
+ *   betas     host [n_instances] inverse temperatures.
+ *   batch     samples per instance (>= 0).
+ *   precision TNVAN_FP32 | TNVAN_TF32 | TNVAN_BF16 (dense blocks and GEMMs).
+ *   d_spins   device int8 out, layout above.   d_logq  device float out.
+ *   d_logZR   device double out.
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE (an instance lacks network or width set),
+ * TNVAN_E_CUDA. */
+int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed,
+                              uint64_t step, int precision, int8_t* d_spins, float* d_logq,
+                              double* d_logZR, void* stream);
+
+/* Eq. 6 and 8 alone: log q_theta(s) for caller-given width-set
+ * configurations d_spins (device int8 +-1, layout above), by the same
+ * masked forward the sampler runs (teacher forcing).  d_logq: device float
+ * [n_inst * batch] out.  Asynchronous.
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no network), TNVAN_E_CUDA. */
+int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, float* d_logq, void* stream);
+
+/* Eq. 3-4 alone: log Z_R(s) for caller-given width-set configurations
+ * d_spins (device int8, layout above) of every instance.  Optional
+ * d_dlogZR_dbeta (device double [n_inst*batch], may be NULL) receives
+ * d log Z_R / d beta = -E_1(s) - <E_2(s, r)>_{r|s}.  Asynchronous. */
+int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                   int precision, double* d_logZR, double* d_dlogZR_dbeta, void* stream);
+
+/* Eq. 9 and the importance-sampled log Z over each instance's batch, with
+ * l_b = log Z_R(s_b) - log q(s_b):
+ *   h_out[4k+0] F_q      = -(1/beta) mean_b l_b
+ *   h_out[4k+1] F_IS     = -(1/beta) (logsumexp_b l_b - ln batch)
+ *   h_out[4k+2] stderr   = std_b(l_b) / (beta sqrt(batch))   (ddof 1)
+ *   h_out[4k+3] logZ_IS  =  logsumexp_b l_b - ln batch
+ * reduced in FP64 on the device.  h_out: host double [4 * n_instances].
+ * Synchronises `stream`.  Errors: TNVAN_E_ARG (batch < 1),
+ * TNVAN_E_OVERFLOW (a non-finite l_b), TNVAN_E_CUDA. */
+int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR,
+                      const float* d_logq, double* h_out, void* stream);
+
+/* Eq. 10: REINFORCE gradient of F_q for every instance,
+ *   grad = sum_b w_b grad_theta log q(s_b),  w_b = -(l_b - mean_b l) / (beta batch),
+ * (the batch mean is the baseline; it leaves the expectation unchanged), by a
+ * teacher-forced forward and hand-written backward of the network.
+ *   d_grad_params   device float [total params] out, packed layout of
+ *                   tnvan_n_params (overwritten; masked entries are 0).
+ * Contraction adjoint (optional, NULL to skip):
+ *   d_dlogZR_dbeta  device double [n_inst*batch]: d log Z_R(s_b)/d beta.
+ *   d_dlogZR_dJ     device double [sum_k n_edges_k] (instance k at offset
+ *                   sum_{j<k} n_edges_j): (1/batch) sum_b d log Z_R(s_b)/d J_e
+ *                   = beta * mean_b <s_i s_j>_{r|s_b}.
+ * Asynchronous.  Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_CUDA. */
+int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                   const double* d_logZR, const float* d_logq, int precision,
+                   float* d_grad_params, double* d_dlogZR_dbeta, double* d_dlogZR_dJ,
+                   void* stream);
+
+/* Algorithm 1 step (d) with Adam (Kingma & Ba 2015) over n float32 entries:
+ * m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).  t >= 1.
+ * All pointers are device float [n].  Asynchronous. */
+int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, float* d_m,
+               float* d_v, double lr, double beta1, double beta2, double eps, int64_t t,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNVAN_H */

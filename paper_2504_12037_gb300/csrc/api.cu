@@ -1,0 +1,877 @@
+// C-ABI of the TNVAN GB300 library: context, host planner, launch sequencing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <numeric>
+#include <utility>
+
+#include "internal.h"
+
+using namespace tnvan;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(tnvan_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_err = buf;
+  return code;
+}
+
+int cuda_fail(tnvan_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, TNVAN_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                              \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+int upload(tnvan_ctx* ctx, Instance& in, const std::vector<T>& v, T** out) {
+  *out = nullptr;
+  if (v.empty()) return TNVAN_OK;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(%zu): %s", v.size() * sizeof(T), cudaGetErrorString(e));
+  in.dev_allocs.push_back(p);
+  e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy (plan upload)");
+  *out = static_cast<T*>(p);
+  return TNVAN_OK;
+}
+
+void free_instance(Instance& in) {
+  for (void* p : in.dev_allocs) cudaFree(p);
+  in.dev_allocs.clear();
+}
+
+// Drop the device plan + network of an instance (keeps the graph).
+void reset_plan(Instance& in) {
+  free_instance(in);
+  in.has_ws = false;
+  in.has_made = false;
+  in.dev = InstDev{};
+}
+
+int check_inst(tnvan_ctx* ctx, int instance, bool allow_append) {
+  if (!ctx) return TNVAN_E_ARG;
+  const int n = (int)ctx->inst.size();
+  if (instance < 0 || instance > n || (!allow_append && instance == n) || instance >= TNVAN_MAX_INST)
+    return fail(ctx, TNVAN_E_ARG, "instance %d out of range (have %d, max %d)", instance, n, TNVAN_MAX_INST);
+  return TNVAN_OK;
+}
+
+int host_strip_tab_floats(int w, int L) {
+  int n = L * w * 4 + 2 * L * 4 * (1 << w) + 2 * L;
+  return (n + 3) & ~3;
+}
+
+// ---------------------------------------------------------------------------
+// Planner: lattice strips.
+// ---------------------------------------------------------------------------
+int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>, int>& edge_of,
+                const std::vector<int>& pos) {
+  const int Lx = in.Lx, Ly = in.Ly;
+  std::vector<int> colW(Lx, 0);
+  for (int w : in.W) colW[w % Lx]++;
+  for (int x = 0; x < Lx; ++x)
+    if (colW[x] != 0 && colW[x] != Ly) return TNVAN_E_UNSUPPORTED;  // not whole columns
+  auto eid = [&](int a, int b) {
+    auto it = edge_of.find({std::min(a, b), std::max(a, b)});
+    return it == edge_of.end() ? -1 : it->second;
+  };
+  std::vector<char> used(in.m, 0);
+  HostStripPlan plan;
+  int tab = 0;
+  for (int x = 0; x < Lx;) {
+    if (colW[x]) {
+      ++x;
+      continue;
+    }
+    int x0 = x;
+    while (x < Lx && !colW[x]) ++x;
+    const int w = x - x0;
+    if (w > TNVAN_MAX_STRIP_W)
+      return fail(ctx, TNVAN_E_UNSUPPORTED, "strip of %d columns (max %d)", w, TNVAN_MAX_STRIP_W);
+    StripDev sd{};
+    sd.w = w;
+    sd.L = Ly;
+    sd.row0 = (int)plan.rows.size();
+    sd.tab_off = tab;
+    double chat = 0;
+    for (int y = 0; y < Ly; ++y) {
+      StripRow R{};
+      for (int c = 0; c < TNVAN_MAX_STRIP_W - 1; ++c) R.eh[c] = -1;
+      for (int c = 0; c < TNVAN_MAX_STRIP_W; ++c) R.ev[c] = -1;
+      R.eL = R.eR = -1;
+      R.posL = R.posR = -1;
+      for (int c = 0; c + 1 < w; ++c) {
+        int e = eid(y * Lx + x0 + c, y * Lx + x0 + c + 1);
+        if (e >= 0) {
+          R.Jh[c] = (float)in.J[e];
+          R.eh[c] = e;
+          used[e] = 1;
+          chat += fabs((double)R.Jh[c]);
+        }
+      }
+      if (x0 > 0) {
+        int e = eid(y * Lx + x0 - 1, y * Lx + x0);
+        if (e >= 0) {
+          R.JL = (float)in.J[e];
+          R.posL = pos[y * Lx + x0 - 1];
+          R.eL = e;
+          used[e] = 1;
+          chat += fabs((double)R.JL);
+        }
+      }
+      if (x0 + w < Lx) {
+        int e = eid(y * Lx + x0 + w - 1, y * Lx + x0 + w);
+        if (e >= 0) {
+          R.JR = (float)in.J[e];
+          R.posR = pos[y * Lx + x0 + w];
+          R.eR = e;
+          used[e] = 1;
+          chat += fabs((double)R.JR);
+        }
+      }
+      if (y + 1 < Ly) {
+        for (int c = 0; c < w; ++c) {
+          int e = eid(y * Lx + x0 + c, (y + 1) * Lx + x0 + c);
+          if (e >= 0) {
+            R.Jv[c] = (float)in.J[e];
+            R.ev[c] = e;
+            used[e] = 1;
+            chat += fabs((double)R.Jv[c]);
+          }
+        }
+      }
+      plan.rows.push_back(R);
+    }
+    sd.c_hat = chat;
+    plan.strips.push_back(sd);
+    tab += host_strip_tab_floats(w, Ly);
+  }
+  for (int e = 0; e < in.m; ++e) {
+    const bool wa = pos[in.ei[e]] >= 0, wb = pos[in.ej[e]] >= 0;
+    if (wa && wb) used[e] = 1;
+    if (!used[e]) return TNVAN_E_UNSUPPORTED;  // a bond the strip form cannot carry
+  }
+  in.strip = std::move(plan);
+  in.dev.strip_tab_floats = tab;
+  in.kind = 0;
+  return TNVAN_OK;
+}
+
+// Connected components of the graph induced on R.
+std::vector<std::vector<int>> r_components(const Instance& in, const std::vector<int>& pos) {
+  std::vector<std::vector<int>> adj(in.n);
+  for (int e = 0; e < in.m; ++e) {
+    adj[in.ei[e]].push_back(in.ej[e]);
+    adj[in.ej[e]].push_back(in.ei[e]);
+  }
+  std::vector<char> seen(in.n, 0);
+  std::vector<std::vector<int>> comps;
+  for (int v = 0; v < in.n; ++v) {
+    if (pos[v] >= 0 || seen[v]) continue;
+    std::vector<int> c{v};
+    seen[v] = 1;
+    for (size_t h = 0; h < c.size(); ++h)
+      for (int u : adj[c[h]])
+        if (pos[u] < 0 && !seen[u]) {
+          seen[u] = 1;
+          c.push_back(u);
+        }
+    std::sort(c.begin(), c.end());
+    comps.push_back(std::move(c));
+  }
+  return comps;
+}
+
+int plan_dense(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos);
+int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos);
+
+int upload_plan(tnvan_ctx* ctx, Instance& in) {
+  int rc;
+  EdgeWW* dww = nullptr;
+  if ((rc = upload(ctx, in, in.ww, &dww))) return rc;
+  in.dev.ww = dww;
+  in.dev.n_ww = (int)in.ww.size();
+  if (in.kind == 0) {
+    StripDev* ds = nullptr;
+    StripRow* dr = nullptr;
+    if ((rc = upload(ctx, in, in.strip.strips, &ds))) return rc;
+    if ((rc = upload(ctx, in, in.strip.rows, &dr))) return rc;
+    in.dev.strips = ds;
+    in.dev.rows = dr;
+    in.dev.n_strips = (int)in.strip.strips.size();
+  } else if (in.kind == 1) {
+    float *jrw = nullptr, *jrr = nullptr;
+    int *err = nullptr, *erw = nullptr;
+    if ((rc = upload(ctx, in, in.JRW, &jrw))) return rc;
+    if ((rc = upload(ctx, in, in.JRR, &jrr))) return rc;
+    if ((rc = upload(ctx, in, in.eRR, &err))) return rc;
+    if ((rc = upload(ctx, in, in.eRW, &erw))) return rc;
+    DenseDev& dd = in.dev.dense;
+    dd.nR = in.dense_nR;
+    dd.nA = std::min(8, in.dense_nR);
+    dd.nB = in.dense_nR - dd.nA;
+    dd.JRW = jrw;
+    dd.JRR = jrr;
+    dd.eRR = err;
+    dd.eRW = erw;
+    dd.c_hat = in.dense_chat;
+    std::vector<float> zc(256 * 256, 0.f);
+    float* c32 = nullptr;
+    if ((rc = upload(ctx, in, zc, &c32))) return rc;
+    std::vector<uint16_t> zc16(256 * 256, 0);
+    uint16_t* c16 = nullptr;
+    if ((rc = upload(ctx, in, zc16, &c16))) return rc;
+    std::vector<double> zc0(2, 0.0);
+    double* c0 = nullptr;
+    if ((rc = upload(ctx, in, zc0, &c0))) return rc;
+    dd.C32 = c32;
+    dd.C16 = c16;
+    dd.c0 = c0;
+  } else {
+    int *prog = nullptr, *fld = nullptr;
+    float *pj = nullptr, *fj = nullptr;
+    if ((rc = upload(ctx, in, in.gprog, &prog))) return rc;
+    if ((rc = upload(ctx, in, in.gfld, &fld))) return rc;
+    if ((rc = upload(ctx, in, in.gpairJ, &pj))) return rc;
+    if ((rc = upload(ctx, in, in.gfldJ, &fj))) return rc;
+    GenDev& g = in.dev.gen;
+    g.n_comp = in.g_ncomp;
+    g.max_entries = in.g_max_entries;
+    g.prog = prog;
+    g.prog_len = (int)in.gprog.size();
+    g.pairJ = pj;
+    g.n_pairs = in.g_npairs;
+    g.fld = fld;
+    g.fldJ = fj;
+    g.c_hat = in.g_chat;
+  }
+  return TNVAN_OK;
+}
+
+// Make sure the device descriptor array matches the host instances.
+int sync_descriptors(tnvan_ctx* ctx) {
+  if (!ctx->dirty) return TNVAN_OK;
+  const int n = (int)ctx->inst.size();
+  long long su = 0, eo = 0, po = 0;
+  std::vector<InstDev> h(n);
+  for (int k = 0; k < n; ++k) {
+    Instance& in = ctx->inst[k];
+    in.dev.kind = in.kind;
+    in.dev.n_spins = in.n;
+    in.dev.n_edges = in.m;
+    in.dev.D = (int)in.W.size();
+    in.dev.spin_units = su;
+    in.dev.edge_off = eo;
+    in.dev.made.param_off = po;
+    su += (long long)in.W.size();
+    eo += in.m;
+    po += in.n_params;
+    h[k] = in.dev;
+  }
+  if (n > ctx->d_inst_cap) {
+    if (ctx->d_inst) cudaFree(ctx->d_inst);
+    ctx->d_inst = nullptr;
+    CK(cudaMalloc(&ctx->d_inst, sizeof(InstDev) * TNVAN_MAX_INST), "cudaMalloc(descriptors)");
+    ctx->d_inst_cap = TNVAN_MAX_INST;
+  }
+  if (n) CK(cudaMemcpy(ctx->d_inst, h.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice), "cudaMemcpy(descriptors)");
+  ctx->dirty = false;
+  return TNVAN_OK;
+}
+
+int check_ready(tnvan_ctx* ctx, bool need_made) {
+  if (ctx->inst.empty()) return fail(ctx, TNVAN_E_STATE, "no instances");
+  for (size_t k = 0; k < ctx->inst.size(); ++k) {
+    const Instance& in = ctx->inst[k];
+    if (!in.has_graph || !in.has_ws) return fail(ctx, TNVAN_E_STATE, "instance %zu has no graph/width set", k);
+    if (need_made && !in.has_made) return fail(ctx, TNVAN_E_STATE, "instance %zu has no network", k);
+  }
+  return sync_descriptors(ctx);
+}
+
+int fill_launch(tnvan_ctx* ctx, const double* betas, int batch, int tile, LaunchInfo& li) {
+  memset(&li, 0, sizeof li);
+  li.n_inst = (int)ctx->inst.size();
+  li.batch = batch;
+  li.tile = tile;
+  if (!betas) return fail(ctx, TNVAN_E_ARG, "betas is NULL");
+  int acc = 0;
+  for (int k = 0; k < li.n_inst; ++k) {
+    if (!(betas[k] > 0.0) || !isfinite(betas[k])) return fail(ctx, TNVAN_E_ARG, "beta[%d] = %g must be finite and > 0", k, betas[k]);
+    li.beta[k] = betas[k];
+    li.tile_begin[k] = acc;
+    acc += (batch + tile - 1) / tile;
+  }
+  li.tile_begin[li.n_inst] = acc;
+  return TNVAN_OK;
+}
+
+int pick_sample_tile(const tnvan_ctx* ctx) {
+  int worst = 0;
+  for (const Instance& in : ctx->inst)
+    worst = std::max(worst, (int)(in.W.size() + in.H[0] + in.H[1]) * 4);
+  if (worst * 128 <= 113 * 1024) return 128;
+  if (worst * 64 <= 220 * 1024) return 64;
+  return 32;
+}
+
+int max_sample_smem(const tnvan_ctx* ctx, int tile) {
+  int m = 0;
+  for (const Instance& in : ctx->inst) m = std::max(m, sample_smem_bytes(in, tile));
+  return m;
+}
+
+int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                 int precision, double* d_logZR, double* d_dbeta, cudaStream_t s);
+
+}  // namespace
+
+// ===========================================================================
+// Public API
+// ===========================================================================
+extern "C" {
+
+int tnvan_version(void) { return 100; }
+
+int tnvan_create(tnvan_ctx** out, int device) {
+  if (!out) return fail(nullptr, TNVAN_E_ARG, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return fail(nullptr, TNVAN_E_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  if (device < 0 || device >= n) return fail(nullptr, TNVAN_E_ARG, "device %d out of range (%d devices)", device, n);
+  tnvan_ctx* ctx = new (std::nothrow) tnvan_ctx();
+  if (!ctx) return fail(nullptr, TNVAN_E_NOMEM, "host allocation failed");
+  ctx->device = device;
+  DeviceGuard g(device);
+  const size_t stats_doubles = 8 * TNVAN_MAX_INST + (size_t)TNVAN_MAX_INST * 64 * 6;
+  e = cudaMalloc(&ctx->d_stats, stats_doubles * sizeof(double));
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(nullptr, TNVAN_E_NOMEM, "cudaMalloc(stats): %s", cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return TNVAN_OK;
+}
+
+int tnvan_destroy(tnvan_ctx* ctx) {
+  if (!ctx) return TNVAN_OK;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  for (Instance& in : ctx->inst) free_instance(in);
+  if (ctx->d_inst) cudaFree(ctx->d_inst);
+  if (ctx->d_stats) cudaFree(ctx->d_stats);
+  if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
+  delete ctx;
+  return TNVAN_OK;
+}
+
+const char* tnvan_last_error(const tnvan_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+int tnvan_init_graph(tnvan_ctx* ctx, int instance, int n_spins, int n_edges, const int32_t* ei,
+                     const int32_t* ej, const double* J, int topology, int Lx, int Ly,
+                     int periodic) {
+  int rc = check_inst(ctx, instance, true);
+  if (rc) return rc;
+  if (n_spins < 1 || n_edges < 0 || (n_edges > 0 && (!ei || !ej || !J)))
+    return fail(ctx, TNVAN_E_ARG, "bad graph sizes or NULL arrays");
+  if (topology < 0 || topology > 2) return fail(ctx, TNVAN_E_ARG, "unknown topology %d", topology);
+  if (topology == TNVAN_LATTICE2D) {
+    if (periodic) return fail(ctx, TNVAN_E_UNSUPPORTED, "periodic lattices are not supported");
+    if (Lx < 1 || Ly < 1 || (long long)Lx * Ly != n_spins)
+      return fail(ctx, TNVAN_E_ARG, "lattice %d x %d does not match %d spins", Lx, Ly, n_spins);
+  }
+  std::map<std::pair<int, int>, int> seen;
+  for (int e = 0; e < n_edges; ++e) {
+    if (ei[e] < 0 || ej[e] < 0 || ei[e] >= n_spins || ej[e] >= n_spins || ei[e] == ej[e])
+      return fail(ctx, TNVAN_E_ARG, "edge %d (%d,%d) invalid", e, ei[e], ej[e]);
+    if (!isfinite(J[e])) return fail(ctx, TNVAN_E_ARG, "J[%d] is not finite", e);
+    auto key = std::make_pair(std::min(ei[e], ej[e]), std::max(ei[e], ej[e]));
+    if (!seen.emplace(key, e).second) return fail(ctx, TNVAN_E_ARG, "edge %d repeats a pair", e);
+  }
+  DeviceGuard g(ctx->device);
+  if (instance == (int)ctx->inst.size()) ctx->inst.emplace_back();
+  Instance& in = ctx->inst[instance];
+  reset_plan(in);
+  in.has_graph = true;
+  in.n = n_spins;
+  in.m = n_edges;
+  in.topology = topology;
+  in.Lx = Lx;
+  in.Ly = Ly;
+  in.ei.assign(ei, ei + n_edges);
+  in.ej.assign(ej, ej + n_edges);
+  in.J.assign(J, J + n_edges);
+  in.W.clear();
+  in.n_params = 0;
+  ctx->dirty = true;
+  return TNVAN_OK;
+}
+
+int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w) {
+  int rc = check_inst(ctx, instance, false);
+  if (rc) return rc;
+  Instance& in = ctx->inst[instance];
+  if (!in.has_graph) return fail(ctx, TNVAN_E_STATE, "instance %d has no graph", instance);
+  if (n_w < 1 || n_w > TNVAN_MAX_D || !w) return fail(ctx, TNVAN_E_ARG, "n_w = %d out of range [1, %d]", n_w, TNVAN_MAX_D);
+  std::vector<int> pos(in.n, -1);
+  for (int i = 0; i < n_w; ++i) {
+    if (w[i] < 0 || w[i] >= in.n) return fail(ctx, TNVAN_E_ARG, "w[%d] = %d out of range", i, w[i]);
+    if (pos[w[i]] >= 0) return fail(ctx, TNVAN_E_ARG, "w[%d] = %d repeated", i, w[i]);
+    pos[w[i]] = i;
+  }
+  DeviceGuard g(ctx->device);
+  reset_plan(in);
+  in.W.assign(w, w + n_w);
+  in.ww.clear();
+  std::map<std::pair<int, int>, int> edge_of;
+  for (int e = 0; e < in.m; ++e) {
+    edge_of[{std::min(in.ei[e], in.ej[e]), std::max(in.ei[e], in.ej[e])}] = e;
+    const int a = pos[in.ei[e]], b = pos[in.ej[e]];
+    if (a >= 0 && b >= 0) in.ww.push_back(EdgeWW{a, b, (float)in.J[e], e});
+  }
+  auto comps = r_components(in, pos);
+  in.n_comp = (int)comps.size();
+  in.max_comp = 0;
+  for (auto& c : comps) in.max_comp = std::max(in.max_comp, (int)c.size());
+  in.max_width = 0;
+  rc = TNVAN_E_UNSUPPORTED;
+  if (in.topology == TNVAN_LATTICE2D) {
+    rc = plan_strips(ctx, in, edge_of, pos);
+    if (rc == TNVAN_OK) {
+      int mw = 0;
+      for (auto& sd : in.strip.strips) mw = std::max(mw, sd.w);
+      in.max_width = mw;
+    } else if (rc != TNVAN_E_UNSUPPORTED) {
+      return rc;
+    }
+  } else if (in.topology == TNVAN_DENSE) {
+    rc = plan_dense(ctx, in, pos);
+    if (rc != TNVAN_OK && rc != TNVAN_E_UNSUPPORTED) return rc;
+  }
+  if (rc == TNVAN_E_UNSUPPORTED) {
+    ctx->err.clear();
+    rc = plan_general(ctx, in, pos);
+    if (rc) return rc;
+  }
+  if ((rc = upload_plan(ctx, in))) return rc;
+  in.has_ws = true;
+  in.has_made = false;
+  ctx->dirty = true;
+  return TNVAN_OK;
+}
+
+int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* widths,
+                   float* d_params) {
+  int rc = check_inst(ctx, instance, false);
+  if (rc) return rc;
+  Instance& in = ctx->inst[instance];
+  if (!in.has_ws) return fail(ctx, TNVAN_E_STATE, "instance %d has no width set", instance);
+  if (n_hidden < 0 || n_hidden > 2 || (n_hidden > 0 && !widths))
+    return fail(ctx, TNVAN_E_ARG, "n_hidden = %d (0..2)", n_hidden);
+  if (!d_params) return fail(ctx, TNVAN_E_ARG, "d_params is NULL");
+  const int D = (int)in.W.size();
+  int H[2] = {0, 0};
+  for (int l = 0; l < n_hidden; ++l) {
+    if (widths[l] < 1 || widths[l] > TNVAN_MAX_HIDDEN)
+      return fail(ctx, TNVAN_E_ARG, "hidden width %d out of range [1, %d]", widths[l], TNVAN_MAX_HIDDEN);
+    H[l] = widths[l];
+  }
+  DeviceGuard g(ctx->device);
+  const int cyc = std::max(D - 1, 1);
+  // integer buffer: degIO [D] | deg1s [H1] | deg2s [H2] | perm1 [H1] | perm2 [H2] | c1 [D+1] | c2 [D+1]
+  std::vector<int> buf;
+  std::vector<int> degIO(D), deg1(H[0]), deg2(H[1]), perm1(H[0]), perm2(H[1]);
+  for (int i = 0; i < D; ++i) degIO[i] = i + 1;
+  auto sorted = [&](int Hn, std::vector<int>& perm, std::vector<int>& deg) {
+    std::vector<int> raw(Hn);
+    for (int k = 0; k < Hn; ++k) raw[k] = k % cyc + 1;
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return raw[a] < raw[b]; });
+    for (int k = 0; k < Hn; ++k) deg[k] = raw[perm[k]];
+  };
+  sorted(H[0], perm1, deg1);
+  sorted(H[1], perm2, deg2);
+  std::vector<int> c1(D + 1, 0), c2(D + 1, 0);
+  for (int d = 0; d <= D; ++d) {
+    c1[d] = (int)std::count_if(deg1.begin(), deg1.end(), [d](int x) { return x <= d; });
+    c2[d] = (int)std::count_if(deg2.begin(), deg2.end(), [d](int x) { return x <= d; });
+  }
+  const int o_deg = 0, o_d1 = D, o_d2 = o_d1 + H[0], o_p1 = o_d2 + H[1], o_p2 = o_p1 + H[0],
+            o_c1 = o_p2 + H[1], o_c2 = o_c1 + D + 1;
+  buf.insert(buf.end(), degIO.begin(), degIO.end());
+  buf.insert(buf.end(), deg1.begin(), deg1.end());
+  buf.insert(buf.end(), deg2.begin(), deg2.end());
+  buf.insert(buf.end(), perm1.begin(), perm1.end());
+  buf.insert(buf.end(), perm2.begin(), perm2.end());
+  buf.insert(buf.end(), c1.begin(), c1.end());
+  buf.insert(buf.end(), c2.begin(), c2.end());
+  (void)o_c2;
+  int* dbuf = nullptr;
+  if ((rc = upload(ctx, in, buf, &dbuf))) return rc;
+  MadeDev md{};
+  md.D = D;
+  md.nh = n_hidden;
+  md.H1 = H[0];
+  md.H2 = H[1];
+  md.Hl = n_hidden == 0 ? D : H[n_hidden - 1];
+  md.n_layers = n_hidden + 1;
+  const int sizes[4] = {D, H[0], H[1], D};
+  int szl[4];
+  int nl = 0;
+  szl[nl++] = D;
+  for (int l = 0; l < n_hidden; ++l) szl[nl++] = H[l];
+  szl[nl++] = D;
+  (void)sizes;
+  const int* degp[4];
+  const int* permp[4];
+  degp[0] = dbuf + o_deg;
+  permp[0] = nullptr;
+  if (n_hidden >= 1) {
+    degp[1] = dbuf + o_d1;
+    permp[1] = dbuf + o_p1;
+  }
+  if (n_hidden >= 2) {
+    degp[2] = dbuf + o_d2;
+    permp[2] = dbuf + o_p2;
+  }
+  degp[n_hidden + 1] = dbuf + o_deg;
+  permp[n_hidden + 1] = nullptr;
+  long long off = 0;
+  for (int l = 0; l <= n_hidden; ++l) {
+    LayerDev& L = md.layer[l];
+    L.nin = szl[l];
+    L.nout = szl[l + 1];
+    L.src_off = off;
+    L.dst_off = off;
+    L.perm_in = permp[l];
+    L.perm_out = permp[l + 1];
+    L.deg_in = degp[l];
+    L.deg_out = degp[l + 1];
+    L.strict = (l == n_hidden) ? 1 : 0;
+    off += (long long)L.nout * L.nin + L.nout;
+  }
+  md.n_params = off;
+  md.c1 = dbuf + o_c1;
+  md.c2 = dbuf + o_c2;
+  md.raw = d_params;
+  void* packed = nullptr;
+  cudaError_t e = cudaMalloc(&packed, off * sizeof(float));
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(packed params): %s", cudaGetErrorString(e));
+  in.dev_allocs.push_back(packed);
+  md.packed = static_cast<float*>(packed);
+  in.dev.made = md;
+  in.nh = n_hidden;
+  in.H[0] = H[0];
+  in.H[1] = H[1];
+  in.d_params = d_params;
+  in.n_params = off;
+  in.has_made = true;
+  ctx->dirty = true;
+  return TNVAN_OK;
+}
+
+int tnvan_n_params(const tnvan_ctx* ctx, int instance, int64_t* n_params, int64_t* offset) {
+  if (!ctx || instance < 0 || instance >= (int)ctx->inst.size()) return TNVAN_E_ARG;
+  long long off = 0;
+  for (int k = 0; k < instance; ++k) off += ctx->inst[k].n_params;
+  if (n_params) *n_params = ctx->inst[instance].n_params;
+  if (offset) *offset = off;
+  return TNVAN_OK;
+}
+
+int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info) {
+  if (!ctx || !info || instance < 0 || instance >= (int)ctx->inst.size()) return TNVAN_E_ARG;
+  const Instance& in = ctx->inst[instance];
+  info[0] = in.n;
+  info[1] = in.m;
+  info[2] = (int)in.W.size();
+  info[3] = in.kind;
+  info[4] = in.n_comp;
+  info[5] = in.max_comp;
+  info[6] = in.max_width;
+  info[7] = (int)in.ww.size();
+  return TNVAN_OK;
+}
+
+static int ensure_grad_ws(tnvan_ctx* ctx, size_t floats) {
+  if (floats <= ctx->grad_packed_floats) return TNVAN_OK;
+  if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
+  ctx->d_grad_packed = nullptr;
+  ctx->grad_packed_floats = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_grad_packed, floats * sizeof(float));
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(gradient partials, %zu floats): %s", floats, cudaGetErrorString(e));
+  ctx->grad_packed_floats = floats;
+  return TNVAN_OK;
+}
+
+// Backward chunking: about two CTAs per SM over all instances.
+static int backward_chunk(const tnvan_ctx* ctx, int batch) {
+  const int n = (int)ctx->inst.size();
+  int per = std::max(1, 304 / std::max(n, 1));
+  int chunk = (batch + per - 1) / per;
+  chunk = ((chunk + 31) / 32) * 32;
+  return std::max(chunk, 32);
+}
+
+static size_t grad_ws_floats(const tnvan_ctx* ctx, int batch) {
+  const int chunk = backward_chunk(ctx, batch);
+  const int parts = (batch + chunk - 1) / chunk;
+  long long maxp = 0;
+  for (const Instance& in : ctx->inst) maxp = std::max(maxp, in.n_params);
+  return (size_t)parts * ctx->inst.size() * (size_t)maxp;
+}
+
+int tnvan_reserve(tnvan_ctx* ctx, int max_batch) {
+  if (!ctx || max_batch < 0) return TNVAN_E_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, std::max(max_batch, 1)));
+  if (rc) return rc;
+  ctx->reserved_batch = std::max(ctx->reserved_batch, max_batch);
+  CK(cudaDeviceSynchronize(), "reserve");
+  return TNVAN_OK;
+}
+
+int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed,
+                              uint64_t step, int precision, int8_t* d_spins, float* d_logq,
+                              double* d_logZR, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 0) return fail(ctx, TNVAN_E_ARG, "batch < 0");
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
+  if (batch > 0 && (!d_spins || !d_logq || !d_logZR)) return fail(ctx, TNVAN_E_ARG, "NULL output");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (batch == 0) return TNVAN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  long long max_elems = 0;
+  for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
+  CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, s), "pack kernel");
+  const int tile = pick_sample_tile(ctx);
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, tile, li))) return rc;
+  li.seed = seed;
+  li.step = step;
+  CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), d_spins, d_logq, nullptr, s), "sample kernel");
+  return contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
+}
+
+int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, float* d_logq, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 0) return fail(ctx, TNVAN_E_ARG, "batch < 0");
+  if (batch > 0 && (!d_spins || !d_logq)) return fail(ctx, TNVAN_E_ARG, "NULL spins or output");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (batch == 0) return TNVAN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  long long max_elems = 0;
+  for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
+  CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, s), "pack kernel");
+  const int tile = pick_sample_tile(ctx);
+  LaunchInfo li;
+  std::vector<double> ones(ctx->inst.size(), 1.0);
+  if ((rc = fill_launch(ctx, ones.data(), batch, tile, li))) return rc;
+  CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), nullptr, d_logq, d_spins, s), "log-prob kernel");
+  return TNVAN_OK;
+}
+
+int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                   int precision, double* d_logZR, double* d_dbeta, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 0) return fail(ctx, TNVAN_E_ARG, "batch < 0");
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
+  if (batch > 0 && (!d_spins || !d_logZR)) return fail(ctx, TNVAN_E_ARG, "NULL spins or output");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (batch == 0) return TNVAN_OK;
+  return contract_all(ctx, betas, batch, d_spins, precision, d_logZR, d_dbeta,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR,
+                      const float* d_logq, double* h_out, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (!d_logZR || !d_logq || !h_out) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+  const int n = li.n_inst;
+  std::vector<double> st(8 * n);
+  CK(cudaMemcpyAsync(st.data(), ctx->d_stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "stats copy");
+  CK(cudaStreamSynchronize(s), "stream sync");
+  for (int k = 0; k < n; ++k) {
+    if (st[8 * k + 5] > 0)
+      return fail(ctx, TNVAN_E_OVERFLOW, "instance %d: %.0f non-finite l_b values", k, st[8 * k + 5]);
+    for (int j = 0; j < 4; ++j) h_out[4 * k + j] = st[8 * k + j];
+  }
+  return TNVAN_OK;
+}
+
+int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                   const double* d_logZR, const float* d_logq, int precision,
+                   float* d_grad_params, double* d_dbeta, double* d_dJ, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
+  if (!d_spins || !d_logZR || !d_logq || !d_grad_params) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  long long max_elems = 0;
+  for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  CK(launch_pack(ctx->d_inst, li.n_inst, max_elems, s), "pack kernel");
+  CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+  const int chunk = backward_chunk(ctx, batch);
+  LaunchInfo lb;
+  if ((rc = fill_launch(ctx, betas, batch, chunk, lb))) return rc;
+  if ((rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, batch)))) return rc;
+  int smem = 0;
+  for (const Instance& in : ctx->inst)
+    smem = std::max(smem, (int)((2 * in.W.size() + 2 * in.H[0] + 2 * in.H[1]) * 33 * sizeof(float)));
+  CK(launch_backward(ctx->d_inst, lb, smem, precision, d_spins, d_logZR, d_logq, ctx->d_stats,
+                     ctx->d_grad_packed, (int)max_elems, s),
+     "backward kernel");
+  CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+     "gradient reduce kernel");
+  if (d_dbeta) {
+    // forward-mode d/dbeta: a second contraction pass that writes only the derivative
+    if ((rc = contract_all(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, s))) return rc;
+  }
+  if (d_dJ) {
+    long long ne = 0;
+    for (const Instance& in : ctx->inst) ne += in.m;
+    CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
+    LaunchInfo lt;
+    if ((rc = fill_launch(ctx, betas, batch, 128, lt))) return rc;
+    CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
+    bool any_strip = false, other = false;
+    for (const Instance& in : ctx->inst) {
+      if (in.kind == 0) any_strip = true;
+      else other = true;
+    }
+    if (any_strip) {
+      for (const Instance& in : ctx->inst)
+        if (in.kind == 0)
+          for (const StripDev& sd : in.strip.strips)
+            if (sd.L > 64) return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ supports strips of at most 64 rows (got %d)", sd.L);
+      int sm = 0;
+      for (const Instance& in : ctx->inst)
+        if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
+      CK(launch_strips_dJ(ctx->d_inst, lt, sm, d_spins, d_dJ, s), "strip adjoint kernel");
+    }
+    if (other) {
+      CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
+      int sm = 0;
+      for (const Instance& in : ctx->inst)
+        if (in.kind == 2) sm = std::max(sm, in.g_max_entries * 4 * 32 + 4096);
+      CK(launch_general(ctx->d_inst, lt, sm, d_spins, nullptr, nullptr, d_dJ, s), "general adjoint kernel");
+    }
+  }
+  return TNVAN_OK;
+}
+
+int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, float* d_m,
+               float* d_v, double lr, double beta1, double beta2, double eps, int64_t t,
+               void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (n < 0 || t < 1 || (n > 0 && (!d_params || !d_grad || !d_m || !d_v)))
+    return fail(ctx, TNVAN_E_ARG, "bad Adam arguments");
+  if (!(beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps >= 0))
+    return fail(ctx, TNVAN_E_ARG, "bad Adam hyper-parameters");
+  DeviceGuard g(ctx->device);
+  const double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+  CK(launch_adam(n, d_params, d_grad, d_m, d_v, (float)lr, (float)beta1, (float)beta2, (float)eps,
+                 (float)bc1, (float)bc2, static_cast<cudaStream_t>(stream)),
+     "adam kernel");
+  return TNVAN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                 int precision, double* d_logZR, double* d_dbeta, cudaStream_t s) {
+  int rc;
+  bool k0 = false, k1 = false, k2 = false;
+  for (const Instance& in : ctx->inst) {
+    k0 |= in.kind == 0;
+    k1 |= in.kind == 1;
+    k2 |= in.kind == 2;
+  }
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
+  if (k0) {
+    int sm = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
+    if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "strip tables need %d B of shared memory", sm);
+    CK(launch_strips(ctx->d_inst, li, sm, d_spins, d_logZR, d_dbeta, s), "strip kernel");
+  }
+  if (k1) CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s), "dense kernel");
+  if (k2) {
+    int sm = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 2) sm = std::max(sm, in.g_max_entries * 4 * 32 + 4096);
+    CK(launch_general(ctx->d_inst, li, sm, d_spins, d_logZR, d_dbeta, nullptr, s), "general kernel");
+  }
+  return TNVAN_OK;
+}
+
+int plan_dense(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
+  (void)ctx;
+  (void)in;
+  (void)pos;
+  return TNVAN_E_UNSUPPORTED;
+}
+
+int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
+  (void)pos;
+  return fail(ctx, TNVAN_E_UNSUPPORTED, "general component contraction not available for this graph (%d spins)", in.n);
+}
+
+}  // namespace

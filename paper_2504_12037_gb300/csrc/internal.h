@@ -1,0 +1,220 @@
+// Internal declarations of the TNVAN GB300 library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tnvan.h"
+
+#define TNVAN_MAX_INST 128
+#define TNVAN_MAX_HIDDEN 512
+#define TNVAN_MAX_D 1024
+#define TNVAN_MAX_STRIP_W 4
+#define TNVAN_MAX_ELIM_W 8
+
+namespace tnvan {
+
+// ---------------------------------------------------------------------------
+// Device-side descriptors (plain structs, pointers into context-owned memory).
+// ---------------------------------------------------------------------------
+
+// One layer of the packed network: units of hidden layers are stored sorted by
+// MADE degree, so "all units of degree <= d" is a prefix.
+struct LayerDev {
+  int nin, nout;
+  long long src_off;  // offset of W_l in the caller's natural parameter layout
+  long long dst_off;  // offset of the packed [nout][nin] block in the packed buffer
+  const int* perm_in;   // packed input index -> natural (nullptr = identity)
+  const int* perm_out;  // packed output index -> natural (nullptr = identity)
+  const int* deg_in;    // degree of each packed input
+  const int* deg_out;   // degree of each packed output
+  int strict;           // output layer: connect iff deg_out > deg_in, else >=
+};
+
+struct MadeDev {
+  int D, nh, H1, H2, Hl;  // Hl = width feeding the output layer (D if nh == 0)
+  int n_layers;
+  LayerDev layer[3];
+  const float* raw;       // borrowed natural-layout parameters
+  float* packed;          // packed, masked, degree-sorted copy (W then b per layer)
+  const int* c1;          // [D+1] number of layer-1 units with degree <= d
+  const int* c2;          // [D+1] number of layer-2 units with degree <= d
+  long long n_params;     // size of the natural layout
+  long long param_off;    // offset in the all-instances packed gradient layout
+};
+
+// Lattice strip: w whole columns x0..x0+w-1, L rows.  Row y has horizontal
+// bonds Jh[c] (c, c+1), left/right W neighbours at AR positions posL/posR
+// (-1 = none), and vertical bonds Jv[c] to row y+1.
+struct StripRow {
+  float Jh[TNVAN_MAX_STRIP_W - 1];
+  float JL, JR;
+  int posL, posR;
+  float Jv[TNVAN_MAX_STRIP_W];
+  int eh[TNVAN_MAX_STRIP_W - 1];  // edge ids (-1 none), for d/dJ
+  int eL, eR;
+  int ev[TNVAN_MAX_STRIP_W];
+};
+
+struct StripDev {
+  int w, L;
+  int row0;       // index of the first row in the instance's row array
+  int tab_off;    // float offset of this strip's tables in shared memory
+  double c_hat;   // sum_y (sum|Jh| + |JL| + |JR|) + sum |Jv|: constant log-offset / beta
+};
+
+struct EdgeWW {
+  int a, b;  // AR positions
+  float J;
+  int e;     // edge id
+};
+
+// Dense block: R = 16 spins (padded), split in halves A (first 8) and B.
+struct DenseDev {
+  int nR;              // real leftover spins (<= 16)
+  int nA, nB;          // real spins in each half (<= 8)
+  const float* JRW;    // [16][D] couplings R -> W positions (zero rows for padding)
+  const float* JRR;    // [16][16] symmetric, zero diagonal, zero padding
+  float* C32;          // [256][256] exp(beta(E_AA+E_BB+a^T J_AB b) - c0), per call
+  uint16_t* C16;       // same in bf16
+  double* c0;          // [1] log offset, written with C
+  double c_hat;        // sum_{i<j in R} |J_ij| (c0 = beta * c_hat)
+  const int* eRR;      // [16][16] edge ids (-1 none)
+  const int* eRW;      // [16][D] edge ids (-1 none)
+};
+
+// General components: elimination programs (see k_general.cu).
+struct GenDev {
+  int n_comp;
+  int max_entries;       // per-sample table arena size (floats)
+  const int* prog;       // packed int program
+  int prog_len;
+  const float* pairJ;    // couplings of R-R bonds referenced by the program
+  int n_pairs;
+  const int* fld;        // per R spin: W-neighbour list (pos, edge id) packed
+  const float* fldJ;
+  double c_hat;          // constant log-offset / beta
+};
+
+struct InstDev {
+  int kind;  // 0 strips, 1 dense, 2 general
+  int n_spins, n_edges, D;
+  long long spin_units;  // sum_{j<k} D_j : spins offset = batch * spin_units
+  long long edge_off;    // sum_{j<k} n_edges_j
+  MadeDev made;
+  int n_ww;
+  const EdgeWW* ww;
+  // strips
+  int n_strips;
+  const StripDev* strips;
+  const StripRow* rows;
+  int strip_tab_floats;  // shared-memory floats for all strip tables
+  // dense
+  DenseDev dense;
+  // general
+  GenDev gen;
+};
+
+// Per-launch parameters passed by value.
+struct LaunchInfo {
+  int n_inst;
+  int batch;
+  int tile;  // samples per CTA
+  unsigned long long seed, step;
+  double beta[TNVAN_MAX_INST];
+  int tile_begin[TNVAN_MAX_INST + 1];
+};
+
+// ---------------------------------------------------------------------------
+// Host-side instance state.
+// ---------------------------------------------------------------------------
+struct HostStripPlan {
+  std::vector<StripDev> strips;
+  std::vector<StripRow> rows;
+};
+
+struct Instance {
+  bool has_graph = false, has_ws = false, has_made = false;
+  int n = 0, m = 0, topology = 0, Lx = 0, Ly = 0;
+  std::vector<int> ei, ej;
+  std::vector<double> J;
+  std::vector<int> W;   // AR order
+  int kind = -1;
+  // plan summary
+  int n_comp = 0, max_comp = 0, max_width = 0;
+  std::vector<EdgeWW> ww;
+  HostStripPlan strip;
+  // dense
+  int dense_nR = 0;
+  std::vector<float> JRW, JRR;
+  std::vector<int> eRR, eRW;
+  double dense_chat = 0;
+  // general
+  std::vector<int> gprog, gfld;
+  std::vector<float> gpairJ, gfldJ;
+  int g_ncomp = 0, g_max_entries = 0, g_npairs = 0;
+  double g_chat = 0;
+  // network
+  int nh = 0, H[2] = {0, 0};
+  float* d_params = nullptr;
+  long long n_params = 0;
+  // device allocations owned by this instance
+  std::vector<void*> dev_allocs;
+  InstDev dev{};
+};
+
+}  // namespace tnvan
+
+struct tnvan_ctx {
+  int device = 0;
+  std::string err;
+  std::vector<tnvan::Instance> inst;
+  tnvan::InstDev* d_inst = nullptr;  // device copy of the descriptors
+  int d_inst_cap = 0;
+  bool dirty = true;                 // descriptors changed since last upload
+  // workspaces (grown on demand, or by tnvan_reserve)
+  double* d_stats = nullptr;         // [n_inst][8]
+  size_t ws_bytes = 0;
+  void* d_ws = nullptr;              // general workspace
+  int reserved_batch = 0;
+  float* d_grad_packed = nullptr;    // packed-layout gradient partials
+  size_t grad_packed_floats = 0;
+};
+
+namespace tnvan {
+
+// Kernel launchers (defined in the .cu files).  All return a cudaError_t.
+cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, cudaStream_t s);
+cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                          int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);
+cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                          const int8_t* spins, double* logZR, double* dbeta, cudaStream_t s);
+cudaError_t launch_strips_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                             const int8_t* spins, double* dJ, cudaStream_t s);
+cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
+                         const int8_t* spins, double* logZR, double* dbeta, double* dJ,
+                         cudaStream_t s);
+cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                           const int8_t* spins, double* logZR, double* dbeta, double* dJ,
+                           cudaStream_t s);
+cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
+                      double* dJ, cudaStream_t s);
+cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
+                          const float* logq, double* stats, cudaStream_t s);
+cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                            int precision, const int8_t* spins, const double* logZR,
+                            const float* logq, const double* stats, float* partials,
+                            int part_stride, cudaStream_t s);
+cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
+                               const float* partials, int part_stride, float* grad,
+                               cudaStream_t s);
+cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+
+int sample_smem_bytes(const Instance& in, int tile);
+int strip_smem_bytes(const Instance& in, int tile);
+
+}  // namespace tnvan

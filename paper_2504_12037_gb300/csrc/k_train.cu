@@ -1,0 +1,412 @@
+// Reduction to F_q / log Z_IS (Eq. 9), REINFORCE backward of the network
+// (Eq. 10) and the Adam update (Algorithm 1 step (d)).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace tnvan {
+
+// ---------------------------------------------------------------------------
+// K7: per-instance reduction of l_b = log Z_R(s_b) - log q(s_b) in FP64.
+// Pass 1 (grid n_part x n_inst): each CTA reduces a contiguous chunk to the
+// mergeable tuple (n, sum(l-K), sum((l-K)^2), max l, sum exp(l - max), #bad),
+// K = l_0 of the instance (a shift that keeps the second moment accurate).
+// Pass 2 (grid n_inst): merges the n_part tuples in order and writes
+//   stats[8k + 0..6] = F_q, F_IS, stderr, logZ_IS, mean l, #non-finite, var l.
+// ---------------------------------------------------------------------------
+struct Tuple {
+  double n, s1, s2, m, se, bad;
+};
+
+__device__ __forceinline__ Tuple merge(Tuple a, Tuple b) {
+  Tuple r;
+  r.n = a.n + b.n;
+  r.s1 = a.s1 + b.s1;
+  r.s2 = a.s2 + b.s2;
+  r.bad = a.bad + b.bad;
+  if (a.se == 0.0) {
+    r.m = b.m;
+    r.se = b.se;
+  } else if (b.se == 0.0) {
+    r.m = a.m;
+    r.se = a.se;
+  } else {
+    r.m = fmax(a.m, b.m);
+    r.se = a.se * (double)expf((float)(a.m - r.m)) + b.se * (double)expf((float)(b.m - r.m));
+  }
+  return r;
+}
+
+__device__ __forceinline__ Tuple shfl_tuple(Tuple t, int o) {
+  Tuple r;
+  r.n = __shfl_xor_sync(0xffffffffu, t.n, o);
+  r.s1 = __shfl_xor_sync(0xffffffffu, t.s1, o);
+  r.s2 = __shfl_xor_sync(0xffffffffu, t.s2, o);
+  r.m = __shfl_xor_sync(0xffffffffu, t.m, o);
+  r.se = __shfl_xor_sync(0xffffffffu, t.se, o);
+  r.bad = __shfl_xor_sync(0xffffffffu, t.bad, o);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) reduce_part_kernel(const LaunchInfo li, int n_part,
+                                                          const double* __restrict__ logZR,
+                                                          const float* __restrict__ logq,
+                                                          double* __restrict__ part) {
+  const int k = blockIdx.y, p = blockIdx.x, B = li.batch;
+  const long long base = (long long)k * B;
+  const double K = logZR[base] - (double)logq[base];
+  const int chunk = (B + n_part - 1) / n_part;
+  const int lo = p * chunk, hi = min(B, lo + chunk);
+  Tuple acc = {0, 0, 0, 0, 0, 0};
+  for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+    const double l = logZR[base + b] - (double)logq[base + b];
+    if (!isfinite(l)) {
+      acc.bad += 1.0;
+      continue;
+    }
+    const double d = l - K;
+    acc.n += 1.0;
+    acc.s1 += d;
+    acc.s2 += d * d;
+    if (acc.se == 0.0) {
+      acc.m = l;
+      acc.se = 1.0;
+    } else if (l > acc.m) {
+      acc.se = acc.se * (double)expf((float)(acc.m - l)) + 1.0;
+      acc.m = l;
+    } else {
+      acc.se += (double)expf((float)(l - acc.m));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc = merge(acc, shfl_tuple(acc, o));
+  __shared__ Tuple red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Tuple r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = merge(r, red[w]);
+    double* o = part + ((long long)k * n_part + p) * 6;
+    o[0] = r.n;
+    o[1] = r.s1;
+    o[2] = r.s2;
+    o[3] = r.m;
+    o[4] = r.se;
+    o[5] = r.bad;
+  }
+}
+
+__global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
+                                    const float* __restrict__ logq,
+                                    const double* __restrict__ part, double* __restrict__ stats) {
+  const int k = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  Tuple r = {0, 0, 0, 0, 0, 0};
+  for (int p = 0; p < n_part; ++p) {
+    const double* o = part + ((long long)k * n_part + p) * 6;
+    Tuple t = {o[0], o[1], o[2], o[3], o[4], o[5]};
+    r = merge(r, t);
+  }
+  const long long base = (long long)k * li.batch;
+  const double K = logZR[base] - (double)logq[base];
+  const double beta = li.beta[k];
+  const double n = r.n;
+  const double mean_d = r.s1 / n;
+  const double var = n > 1.0 ? fmax(r.s2 - r.s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
+  const double mean = K + mean_d;
+  const double lz = r.m + log(r.se) - log(n);
+  double* s = stats + 8 * k;
+  s[0] = -mean / beta;
+  s[1] = -lz / beta;
+  s[2] = sqrt(var) / (beta * sqrt(n));
+  s[3] = lz;
+  s[4] = mean;
+  s[5] = r.bad;
+  s[6] = var;
+  s[7] = n;
+}
+
+cudaError_t launch_reduce(const InstDev*, const LaunchInfo& li, const double* logZR,
+                          const float* logq, double* stats, cudaStream_t s) {
+  // n_part chosen so every instance gets >= 1 CTA of >= 1024 samples.
+  int n_part = (li.batch + 1023) / 1024;
+  if (n_part > 64) n_part = 64;
+  if (n_part < 1) n_part = 1;
+  // partial tuples live right after the stats block
+  double* part = stats + 8 * TNVAN_MAX_INST;
+  reduce_part_kernel<<<dim3(n_part, li.n_inst), 256, 0, s>>>(li, n_part, logZR, logq, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_final_kernel<<<li.n_inst, 32, 0, s>>>(li, n_part, logZR, logq, part, stats);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K2 + K3: teacher-forced forward and hand-written backward of
+//   sum_b w_b log q(s_b),   w_b = -(l_b - mean l) / (beta B)       (Eq. 10)
+// for a chunk of samples per CTA, 32 samples at a time (FP32 SIMT).
+//   d log q / d x_i = s_i sigmoid(-s_i x_i)
+// Shared memory, layout [unit][TP] with TP = 33:
+//   S [D], A1 [H1], A2 [H2], X/dX [D], dA2 [H2], dA1 [H1].
+// Weight-gradient partial sums of the chunk are accumulated in this CTA's
+// slice of `partials` (packed, degree-sorted layout, n_params floats).
+// ---------------------------------------------------------------------------
+#define BW_TS 32
+#define BW_TP 33
+
+// G[M][N] (+)= sum_t A[m][t] Bm[n][t];  gb[M] (+)= sum_t A[m][t].
+__device__ void outer_acc(float* __restrict__ G, float* __restrict__ gb, const float* A,
+                          const float* Bm, int M, int N, int TS, bool first, int tid, int nth) {
+  const int mb = (M + 3) >> 2, nb = (N + 3) >> 2;
+  for (int blk = tid; blk < mb * nb; blk += nth) {
+    const int i0 = (blk / nb) << 2, j0 = (blk % nb) << 2;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+    for (int t = 0; t < TS; ++t) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = (i0 + r < M) ? A[(i0 + r) * BW_TP + t] : 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bb[c] = (j0 + c < N) ? Bm[(j0 + c) * BW_TP + t] : 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], bb[c], acc[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (i0 + r < M && j0 + c < N) {
+          float* g = G + (long long)(i0 + r) * N + j0 + c;
+          *g = first ? acc[r][c] : *g + acc[r][c];
+        }
+  }
+  for (int m = tid; m < M; m += nth) {
+    float s = 0.f;
+    for (int t = 0; t < TS; ++t) s += A[m * BW_TP + t];
+    gb[m] = first ? s : gb[m] + s;
+  }
+}
+
+__device__ __forceinline__ float dot_row(const float* __restrict__ w, const float* col, int n) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int j = 0;
+  for (; j + 4 <= n; j += 4) {
+    a0 = fmaf(__ldg(w + j), col[j * BW_TP], a0);
+    a1 = fmaf(__ldg(w + j + 1), col[(j + 1) * BW_TP], a1);
+    a2 = fmaf(__ldg(w + j + 2), col[(j + 2) * BW_TP], a2);
+    a3 = fmaf(__ldg(w + j + 3), col[(j + 3) * BW_TP], a3);
+  }
+  for (; j < n; ++j) a0 = fmaf(__ldg(w + j), col[j * BW_TP], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// sum_{i = i0}^{n-1} col[i] * w[i * stride]
+__device__ __forceinline__ float dot_strided(const float* __restrict__ w, long long stride,
+                                             const float* col, int i0, int n) {
+  float a0 = 0.f, a1 = 0.f;
+  int i = i0;
+  for (; i + 2 <= n; i += 2) {
+    a0 = fmaf(__ldg(w + i * stride), col[i * BW_TP], a0);
+    a1 = fmaf(__ldg(w + (i + 1) * stride), col[(i + 1) * BW_TP], a1);
+  }
+  if (i < n) a0 = fmaf(__ldg(w + i * stride), col[i * BW_TP], a0);
+  return a0 + a1;
+}
+
+__global__ void __launch_bounds__(256) backward_kernel(const InstDev* __restrict__ inst,
+                                                       const LaunchInfo li,
+                                                       const int8_t* __restrict__ spins,
+                                                       const double* __restrict__ logZR,
+                                                       const float* __restrict__ logq,
+                                                       const double* __restrict__ stats,
+                                                       float* __restrict__ partials,
+                                                       long long part_stride) {
+  extern __shared__ float sm[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  const MadeDev& md = I.made;
+  const int D = md.D, nh = md.nh, H1 = md.H1, H2 = md.H2, Hl = md.Hl;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int t = tid & 31, q = tid >> 5, nq = nth >> 5;
+  const int chunk = li.tile;
+  const int c_idx = blockIdx.x - li.tile_begin[k];
+  const int b_lo = c_idx * chunk, b_hi = min(li.batch, b_lo + chunk);
+  float* S = sm;
+  float* A1 = S + D * BW_TP;
+  float* A2 = A1 + H1 * BW_TP;
+  float* X = A2 + H2 * BW_TP;
+  float* dA2 = X + D * BW_TP;
+  float* dA1 = dA2 + H2 * BW_TP;
+  const float* W1 = md.packed + md.layer[0].dst_off;
+  const float* b1 = W1 + (long long)H1 * D;
+  const float* W2 = nh >= 2 ? md.packed + md.layer[1].dst_off : nullptr;
+  const float* b2 = nh >= 2 ? W2 + (long long)H2 * H1 : nullptr;
+  const float* Wo = md.packed + md.layer[nh].dst_off;
+  const float* bo = Wo + (long long)D * Hl;
+  const float* src = nh == 0 ? S : (nh == 1 ? A1 : A2);
+  const int* deg1 = nh >= 1 ? md.layer[0].deg_out : nullptr;
+  const int* deg2 = nh >= 2 ? md.layer[1].deg_out : nullptr;
+  const int* cL = nh == 1 ? md.c1 : md.c2;
+  const double mean = stats[8 * k + 4];
+  const double beta = li.beta[k];
+  const double wscale = -1.0 / (beta * (double)li.batch);
+  float* Gk = partials + (long long)blockIdx.x * part_stride;
+  const int8_t* sp = spins + I.spin_units * li.batch;
+  bool first = true;
+  for (int b0 = b_lo; b0 < b_hi; b0 += BW_TS) {
+    const int nv = min(BW_TS, b_hi - b0);
+    __syncthreads();
+    for (int e = tid; e < BW_TS * D; e += nth) {
+      const int tt = e / D, i = e % D;
+      S[i * BW_TP + tt] = tt < nv ? (float)sp[(long long)(b0 + tt) * D + i] : 0.f;
+    }
+    __syncthreads();
+    if (nh >= 1) {
+      for (int o = q; o < H1; o += nq)
+        A1[o * BW_TP + t] = fmaxf(__ldg(b1 + o) + dot_row(W1 + (long long)o * D, S + t, deg1[o]), 0.f);
+      __syncthreads();
+    }
+    if (nh >= 2) {
+      for (int o = q; o < H2; o += nq)
+        A2[o * BW_TP + t] =
+            fmaxf(__ldg(b2 + o) + dot_row(W2 + (long long)o * H1, A1 + t, md.c1[deg2[o]]), 0.f);
+      __syncthreads();
+    }
+    // output logits -> dX = w_b s_i sigmoid(-s_i x_i)
+    const bool valid = t < nv;
+    const float wb =
+        valid ? (float)(wscale * (logZR[(long long)k * li.batch + b0 + t] -
+                                  (double)logq[(long long)k * li.batch + b0 + t] - mean))
+              : 0.f;
+    for (int i = q; i < D; i += nq) {
+      const int nin = nh == 0 ? i : cL[i];
+      const float x = __ldg(bo + i) + dot_row(Wo + (long long)i * Hl, src + t, nin);
+      const float s = S[i * BW_TP + t];
+      X[i * BW_TP + t] = wb * s / (1.f + expf(s * x));
+    }
+    __syncthreads();
+    if (nh == 2) {
+      // dA2[o] = 1[h2 > 0] sum_{i >= deg2(o)} dX[i] Wo[i][o]
+      for (int o = q; o < H2; o += nq) {
+        const float h = A2[o * BW_TP + t];
+        dA2[o * BW_TP + t] = h > 0.f ? dot_strided(Wo + o, Hl, X + t, deg2[o], D) : 0.f;
+      }
+      __syncthreads();
+      // dA1[j] = 1[h1 > 0] sum_{o: deg2(o) >= deg1(j)} dA2[o] W2[o][j]
+      for (int j = q; j < H1; j += nq) {
+        const float h = A1[j * BW_TP + t];
+        const int o0 = md.c2[deg1[j] - 1];
+        dA1[j * BW_TP + t] = h > 0.f ? dot_strided(W2 + j, H1, dA2 + t, o0, H2) : 0.f;
+      }
+      __syncthreads();
+    } else if (nh == 1) {
+      for (int j = q; j < H1; j += nq) {
+        const float h = A1[j * BW_TP + t];
+        dA1[j * BW_TP + t] = h > 0.f ? dot_strided(Wo + j, Hl, X + t, deg1[j], D) : 0.f;
+      }
+      __syncthreads();
+    }
+    // weight gradients of this sub-tile
+    float* Go = Gk + md.layer[nh].dst_off;
+    outer_acc(Go, Go + (long long)D * Hl, X, src, D, Hl, BW_TS, first, tid, nth);
+    if (nh == 2) {
+      float* G2 = Gk + md.layer[1].dst_off;
+      outer_acc(G2, G2 + (long long)H2 * H1, dA2, A1, H2, H1, BW_TS, first, tid, nth);
+    }
+    if (nh >= 1) {
+      float* G1 = Gk + md.layer[0].dst_off;
+      outer_acc(G1, G1 + (long long)H1 * D, dA1, S, H1, D, BW_TS, first, tid, nth);
+    }
+    first = false;
+  }
+  if (first) {  // empty chunk: zero the slice
+    for (long long e = tid; e < md.n_params; e += nth) Gk[e] = 0.f;
+  }
+}
+
+cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int,
+                            const int8_t* spins, const double* logZR, const float* logq,
+                            const double* stats, float* partials, int part_stride,
+                            cudaStream_t s) {
+  const int nblk = li.tile_begin[li.n_inst];
+  if (nblk == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes);
+  if (e != cudaSuccess) return e;
+  backward_kernel<<<nblk, 256, smem_bytes, s>>>(d_inst, li, spins, logZR, logq, stats, partials,
+                                                part_stride);
+  return cudaGetLastError();
+}
+
+// Sum the chunk partials of every instance (fixed order: deterministic) and
+// scatter from the packed, degree-sorted layout to the caller's natural
+// layout; entries outside the MADE masks get 0.
+__global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                   const float* __restrict__ partials, long long part_stride,
+                                   float* __restrict__ grad) {
+  const int k = blockIdx.y;
+  const MadeDev& md = inst[k].made;
+  const int p0 = li.tile_begin[k], p1 = li.tile_begin[k + 1];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < md.n_params;
+       e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int p = p0; p < p1; ++p) s += partials[(long long)p * part_stride + e];
+    long long r = e;
+    for (int l = 0; l < md.n_layers; ++l) {
+      const LayerDev& L = md.layer[l];
+      const long long nw = (long long)L.nout * L.nin;
+      if (r < nw) {
+        const int o = (int)(r / L.nin), i = (int)(r % L.nin);
+        const int no = L.perm_out ? L.perm_out[o] : o;
+        const int ni = L.perm_in ? L.perm_in[i] : i;
+        const bool conn = L.strict ? (L.deg_out[o] > L.deg_in[i]) : (L.deg_out[o] >= L.deg_in[i]);
+        grad[md.param_off + L.src_off + (long long)no * L.nin + ni] = conn ? s : 0.f;
+        break;
+      }
+      r -= nw;
+      if (r < L.nout) {
+        const int no = L.perm_out ? L.perm_out[r] : (int)r;
+        grad[md.param_off + L.src_off + nw + no] = s;
+        break;
+      }
+      r -= L.nout;
+    }
+  }
+}
+
+cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* partials,
+                               int part_stride, float* grad, cudaStream_t s) {
+  if (li.n_inst == 0) return cudaSuccess;
+  grad_reduce_kernel<<<dim3(64, li.n_inst), 256, 0, s>>>(d_inst, li, partials, part_stride, grad);
+  return cudaGetLastError();
+}
+
+// Adam (Kingma & Ba 2015), bias corrections bc1 = 1 - b1^t, bc2 = 1 - b2^t.
+__global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, float lr, float b1,
+                            float b2, float eps, float bc1, float bc2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
+                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  long long nb = (n + 255) / 256;
+  if (nb > 1216) nb = 1216;
+  adam_kernel<<<(int)nb, 256, 0, s>>>(n, p, g, m, v, lr, b1, b2, eps, bc1, bc2);
+  return cudaGetLastError();
+}
+
+}  // namespace tnvan

@@ -1,0 +1,182 @@
+"""Thin ctypes binding of libtnvan.so (the C-ABI in include/tnvan.h).
+
+The functions here only marshal arguments: every step of the hot path runs in
+the library's CUDA kernels.  Tensors are torch CUDA tensors (device memory and
+streams only); host arrays are NumPy.  There is no CPU fallback: if the library
+is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtnvan.so")
+
+OK = 0
+E_ARG, E_NOMEM, E_CUDA, E_TIMEOUT, E_OVERFLOW, E_STATE, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+LATTICE2D, DENSE, GENERAL = 0, 1, 2
+FP32, TF32, BF16 = 0, 1, 2
+
+_c_int, _c_i64, _c_u64, _c_dbl, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dblp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (restype, argtypes); mirrors include/tnvan.h
+SIGNATURES = {
+    "tnvan_version": (_c_int, []),
+    "tnvan_create": (_c_int, [ctypes.POINTER(_vp), _c_int]),
+    "tnvan_destroy": (_c_int, [_vp]),
+    "tnvan_last_error": (ctypes.c_char_p, [_vp]),
+    "tnvan_init_graph": (_c_int, [_vp, _c_int, _c_int, _c_int, _i32p, _i32p, _dblp, _c_int, _c_int, _c_int, _c_int]),
+    "tnvan_set_width_set": (_c_int, [_vp, _c_int, _c_int, _i32p]),
+    "tnvan_set_made": (_c_int, [_vp, _c_int, _c_int, _i32p, _vp]),
+    "tnvan_n_params": (_c_int, [_vp, _c_int, _i64p, _i64p]),
+    "tnvan_instance_info": (_c_int, [_vp, _c_int, _i32p]),
+    "tnvan_reserve": (_c_int, [_vp, _c_int]),
+    "tnvan_sample_and_contract": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp]),
+    "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _vp, _vp]),
+    "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+    "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
+    "tnvan_backward": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
+    "tnvan_adam": (_c_int, [_vp, _c_i64, _vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
+}
+
+_LIB = None
+
+
+class TnvanError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tnvan error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libtnvan.so (built in-tree by build.py); raise if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    ctype = {np.int32: ctypes.c_int32, np.float64: ctypes.c_double, np.int64: ctypes.c_int64}[dtype]
+    return a, a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Context:
+    """Owns one tnvan_ctx.  Method names follow the C-ABI."""
+
+    def __init__(self, device: int = 0):
+        self._h = _vp()
+        rc = lib().tnvan_create(ctypes.byref(self._h), device)
+        if rc != OK:
+            raise TnvanError(rc, lib().tnvan_last_error(None).decode())
+        self.device = device
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise TnvanError(rc, lib().tnvan_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            lib().tnvan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- set-up -----------------------------------------------------------
+    def init_graph(self, instance: int, n_spins: int, ei, ej, J, topology: int, Lx: int = 0, Ly: int = 0,
+                   periodic: bool = False):
+        ei, pi = _arr(ei, np.int32)
+        ej, pj = _arr(ej, np.int32)
+        J, pJ = _arr(J, np.float64)
+        self._check(lib().tnvan_init_graph(self._h, instance, n_spins, ei.shape[0], pi, pj, pJ, topology,
+                                           Lx, Ly, int(periodic)))
+
+    def set_width_set(self, instance: int, w):
+        w, pw = _arr(w, np.int32)
+        self._check(lib().tnvan_set_width_set(self._h, instance, w.shape[0], pw))
+
+    def set_made(self, instance: int, hidden: Sequence[int], d_params):
+        h, ph = _arr(list(hidden) if len(hidden) else [0], np.int32)
+        self._check(lib().tnvan_set_made(self._h, instance, len(hidden), ph, _ptr(d_params)))
+
+    def n_params(self, instance: int):
+        n, off = ctypes.c_int64(), ctypes.c_int64()
+        self._check(lib().tnvan_n_params(self._h, instance, ctypes.byref(n), ctypes.byref(off)))
+        return n.value, off.value
+
+    def instance_info(self, instance: int):
+        info = (ctypes.c_int32 * 8)()
+        self._check(lib().tnvan_instance_info(self._h, instance, info))
+        keys = ["n_spins", "n_edges", "D", "kind", "n_components", "max_component", "max_width", "n_ww"]
+        return dict(zip(keys, list(info)))
+
+    def reserve(self, max_batch: int):
+        self._check(lib().tnvan_reserve(self._h, max_batch))
+
+    # --- hot path ---------------------------------------------------------
+    def sample_and_contract(self, betas, batch: int, seed: int, step: int, precision: int, spins, logq,
+                            logZR, stream=None):
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_sample_and_contract(self._h, pb, batch, seed, step, precision, _ptr(spins),
+                                                    _ptr(logq), _ptr(logZR), _stream(stream)))
+
+    def log_prob(self, batch: int, spins, logq, stream=None):
+        self._check(lib().tnvan_log_prob(self._h, batch, _ptr(spins), _ptr(logq), _stream(stream)))
+
+    def contract(self, betas, batch: int, spins, precision: int, logZR, dlogZR_dbeta=None, stream=None):
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_contract(self._h, pb, batch, _ptr(spins), precision, _ptr(logZR),
+                                         _ptr(dlogZR_dbeta), _stream(stream)))
+
+    def free_energy(self, betas, batch: int, logZR, logq, stream=None) -> np.ndarray:
+        b, pb = _arr(betas, np.float64)
+        out = np.zeros(4 * len(b))
+        _, po = _arr(out, np.float64)
+        self._check(lib().tnvan_free_energy(self._h, pb, batch, _ptr(logZR), _ptr(logq),
+                                            out.ctypes.data_as(_dblp), _stream(stream)))
+        return out.reshape(len(b), 4)
+
+    def backward(self, betas, batch: int, spins, logZR, logq, precision: int, grad, dlogZR_dbeta=None,
+                 dlogZR_dJ=None, stream=None):
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_backward(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq), precision,
+                                         _ptr(grad), _ptr(dlogZR_dbeta), _ptr(dlogZR_dJ), _stream(stream)))
+
+    def adam(self, params, grad, m, v, lr: float, beta1: float, beta2: float, eps: float, t: int, stream=None):
+        self._check(lib().tnvan_adam(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
+                                     lr, beta1, beta2, eps, t, _stream(stream)))

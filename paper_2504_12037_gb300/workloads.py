@@ -285,3 +285,26 @@ def workload(config: int, n_instances: Optional[int] = None) -> Workload:
         return Workload("ea_gauss_multi_instance_train", graphs, Ws, [128, 128], 1024,
                         [0.8] * n)
     raise ValueError(f"unknown workload {config}")
+
+
+# ---------------------------------------------------------------------------
+# Network parameters (seeded initial values; layout of the C-ABI: per layer
+# W [out][in] row-major, then b [out]).
+# ---------------------------------------------------------------------------
+
+def made_param_count(D: int, hidden: Sequence[int]) -> int:
+    sz = [D] + list(hidden) + [D]
+    return sum(sz[l + 1] * sz[l] + sz[l + 1] for l in range(len(sz) - 1))
+
+
+def made_params(D: int, hidden: Sequence[int], seed: int, scale: float = 1.0) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases (PyTorch's
+    default Linear initialisation), times `scale`, as float32."""
+    rng = np.random.default_rng(seed)
+    sz = [D] + list(hidden) + [D]
+    parts = []
+    for l in range(len(sz) - 1):
+        bound = scale / np.sqrt(sz[l])
+        parts.append(rng.uniform(-bound, bound, size=sz[l + 1] * sz[l]))
+        parts.append(rng.uniform(-bound, bound, size=sz[l + 1]))
+    return np.concatenate(parts).astype(np.float32)
