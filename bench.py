@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""TNVAN hot-path benchmark on GB300.
+
+One step = one iteration of Algorithm 1 over every instance of the 16x16
+Edwards-Anderson workload (Gaussian J, open boundary, W = every 4th column,
+leftover 16x3 strips, MADE 64-128-128-64, beta in {0.2, 0.4, 0.6, 0.8, 1.0},
+16384 samples per beta):
+  sample + log q (Eq. 6-8) -> strip contraction log Z_R (Eq. 3-4)
+  -> F_q / log Z_IS reduction (Eq. 9) -> REINFORCE backward (Eq. 10)
+  -> contraction adjoint d log Z_R / d beta and d / d J -> Adam update.
+Metric: samples per second (all instances, all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the same instances on its own GPU with its own
+random stream (weak scaling, no data-path collective); rank 0 prints one JSON
+line.  `--impl reference` times the FP64 CPU oracle on the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = 2
+METRIC = "samples/sec (sample+contract+reduce) and |F_q-F_exact|/N; mixed vs FP32 on one GB300"
+UNIT = "samples/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        sm, smax, reasons = [], [], set()
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per sample (used for the roofline figures)
+# ---------------------------------------------------------------------------
+def made_macs(D, hidden):
+    """Masked multiply-adds of one MADE forward pass (each unit once)."""
+    import numpy as np
+    cyc = max(D - 1, 1)
+    d1 = np.sort(np.arange(hidden[0]) % cyc + 1)
+    d2 = np.sort(np.arange(hidden[1]) % cyc + 1)
+    c1 = lambda d: int((d1 <= d).sum())
+    c2 = lambda d: int((d2 <= d).sum())
+    l1 = int(d1.sum())                       # unit of degree d reads inputs 1..d
+    l2 = sum(c1(int(d)) for d in d2)         # layer-2 unit reads layer-1 units of degree <= d
+    lo = sum(c2(i) for i in range(D))        # output i reads layer-2 units of degree <= i
+    return l1 + l2 + lo, (l1, l2, lo)
+
+
+def strip_flops(w, L):
+    """FP32 operations of one strip chain (per sample): each of L-1 vertical
+    steps applies w Kronecker 2x2 factors (2^w outputs x 3 ops) and a diagonal
+    (2^w mults); renormalisation adds 2^w mults + 2^w max per row."""
+    nx = 1 << w
+    return (L - 1) * (w * nx * 3 + nx) + L * 2 * nx
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2504_12037_gb300 import tnvan as tv
+    from paper_2504_12037_gb300 import workloads as wl
+    from paper_2504_12037_gb300.model import TNVAN
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = {"fp32": tv.FP32, "tf32": tv.TF32, "bf16": tv.BF16}[a.precision]
+    w = wl.workload(CONFIG)
+    B = w.batch
+    model = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
+    n_inst = model.n
+    model.ctx.reserve(B)
+    spins, logq, logZR = model.buffers(B)
+    dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
+    dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    seed = 12037 + 7919 * rank
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step(i):
+        model.train_step(B, seed, i, prec, 0.01, (spins, logq, logZR), dbeta, dJ, stream)
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    model.ctx.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for i in range(a.steps):
+        flush.zero_()  # evict L2 between timed steps (not inside the timed interval)
+        starts[i].record(stream)
+        step(a.warmup + i)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    model.ctx.profile(False)
+    clk = clocks.stop()
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(per_step) / len(per_step)
+    prof = model.ctx.profile_read()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    samples_step = n_inst * B * world
+    value = samples_step / (ms_max / 1e3)
+
+    # ----- end to end through the public API with host buffers -----
+    h_spins = torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True)
+    h_logq = torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True)
+    h_logZR = torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    fe_last = None
+    t0 = time.perf_counter()
+    for i in range(a.e2e_steps):
+        step(10 ** 6 + i)
+        fe_last = model.free_energy(B, logZR, logq, stream)  # D2H of the per-instance results (syncs)
+        h_spins.copy_(spins, non_blocking=True)
+        h_logq.copy_(logq, non_blocking=True)
+        h_logZR.copy_(logZR, non_blocking=True)
+        stream.synchronize()
+    t_e2e = (time.perf_counter() - t0) / a.e2e_steps
+    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": samples_step / float(te.item()), "unit": UNIT,
+           "h2d_bytes_per_step": 8 * n_inst,
+           "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 32 * n_inst)}
+
+    # ----- roofline of the dominant kernel -----
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    D, H = model.D[0], w.hidden
+    macs, parts = made_macs(D, H)
+    strips = 4
+    per_sample = {
+        "sample": 2.0 * macs,
+        "backward": 2.0 * macs * 3,  # forward + input-gradient + weight-gradient passes
+        "strips": strips * strip_flops(3, 16),
+        "strips+dbeta": strips * 2 * strip_flops(3, 16),
+        "strips_dbeta": strips * 2 * strip_flops(3, 16),
+        "strips_dJ": strips * 5 * strip_flops(3, 16),
+    }
+    flop_launch = per_sample.get(dom_name, float("nan")) * n_inst * B
+    achieved = flop_launch / (dom_ms / dom_n / 1e3) / 1e12 if dom_n else float("nan")
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+                "flop_per_launch": flop_launch, "ms_per_launch": dom_ms / dom_n}
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()}
+    launches_per_step = sum(v[1] for v in prof.values()) / a.steps
+
+    # ----- accuracy context: exact F of the lattice and F_q/N -----
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[a.precision],
+        "data": "synthetic (seeded EA couplings; random-init MADE)",
+        "config": {"workload": w.name, "lattice": "16x16 open", "couplings": "N(0,1)",
+                   "betas": w.betas, "batch_per_beta": B, "instances": n_inst,
+                   "width_set": "every 4th column (64 spins)", "made": [64] + w.hidden + [64],
+                   "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * a.steps)),
+        "roofline": roofline, "kernels": kernels,
+        "fe_last": {"F_q_per_spin": [float(x) / 256 for x in fe_last[:, 0]],
+                    "F_IS_per_spin": [float(x) / 256 for x in fe_last[:, 1]]},
+    }
+    if rank == 0 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle as the CPU baseline / reference arm
+# ---------------------------------------------------------------------------
+def oracle_step(w, params, offsets, n_b, seed, step):
+    """One oracle iteration of Algorithm 1 on n_b samples per instance."""
+    import numpy as np
+    import torch
+
+    from oracle import estimators as est
+    from oracle import made, philox, transfer
+
+    done = 0
+    for k, (g, W, beta) in enumerate(zip(w.graphs, w.widths_sets, w.betas)):
+        D = len(W)
+        th = torch.as_tensor(params[offsets[k]:offsets[k + 1]].astype(np.float64))
+        u = philox.uniforms(seed, step, k, n_b, D)
+        s, _ = made.sample(th, D, w.hidden, u)
+        lq = made.log_q(th, D, w.hidden, s)
+        bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+        Jt = torch.tensor(g.J, dtype=torch.float64, requires_grad=True)
+        lz = transfer.log_zr_lattice(g.n, g.ei, g.ej, Jt, bt, W, s, g.Lx)
+        est.free_energies(lz.detach(), lq.detach(), beta)
+        wts = est.reinforce_weights(lz.detach(), lq.detach(), beta)
+        grad = est.surrogate_grad(th.numpy(), D, w.hidden, s, wts)
+        torch.autograd.grad(lz.sum(), [bt, Jt])  # adjoint: d/dbeta and d/dJ
+        est.adam_step(th.numpy(), grad.numpy(), np.zeros(th.numel()), np.zeros(th.numel()), 1)
+        done += n_b
+    return done
+
+
+def cpu_baseline(w, params, offsets, budget_s=15.0, n_b=2048):
+    """The oracle, as it stands, on a bounded sample of the workload: repeated
+    oracle steps of n_b samples per beta until about budget_s has elapsed."""
+    import torch
+
+    torch.set_num_threads(os.cpu_count() or 1)
+    done, steps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        done += oracle_step(w, params, offsets, n_b, 1, steps)
+        steps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or steps >= 50:
+            break
+    return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{steps} oracle steps x {n_b} samples per beta x {len(w.graphs)} betas "
+                      f"(FP64 sampling replay, strip transfer matrices, estimators, autograd gradient "
+                      f"and adjoint, Adam) in {dt:.1f} s"}
+
+
+def run_reference(a):
+    import numpy as np
+
+    from paper_2504_12037_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    w = wl.workload(CONFIG)
+    params = np.concatenate([wl.made_params(len(W), w.hidden, 1 + k) for k, W in enumerate(w.widths_sets)])
+    sizes = [wl.made_param_count(len(W), w.hidden) for W in w.widths_sets]
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    import torch
+
+    torch.set_num_threads(os.cpu_count() or 1)
+    n_b = 16
+    for i in range(a.warmup):
+        oracle_step(w, params, offsets, n_b, 1, i)
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(a.steps):
+        done += oracle_step(w, params, offsets, n_b, 1, a.warmup + i)
+    dt = time.perf_counter() - t0
+    value = done / dt
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": w.name, "batch_per_beta": n_b, "instances": len(w.graphs)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                            "sample": f"{n_b} samples per beta x {len(w.graphs)} betas per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -192,6 +192,17 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
                float* d_v, double lr, double beta1, double beta2, double eps, int64_t t,
                void* stream);
 
+/* Per-kernel timing, a tracing aid (not in the paper).  enable = 1 clears the
+ * records and starts bracketing every kernel launch of this context with a
+ * pair of CUDA events on the launch stream; enable = 0 stops recording.
+ * Synchronous only in tnvan_profile_read, which waits for the recorded
+ * events and reports, for kernel `index` (0-based, in first-launch order):
+ * its name (NUL-terminated, truncated to name_len), summed elapsed ms and
+ * number of launches.  Returns TNVAN_E_ARG when index is past the last kernel. */
+int tnvan_profile(tnvan_ctx* ctx, int enable);
+int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, double* total_ms,
+                       int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,43 @@ struct DeviceGuard {
   }
 };
 
+// Brackets one kernel launch with CUDA events when profiling is on.
+struct Prof {
+  tnvan_ctx* ctx;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  size_t idx = 0;
+  static cudaEvent_t take(tnvan_ctx* c) {
+    if (!c->event_pool.empty()) {
+      cudaEvent_t e = c->event_pool.back();
+      c->event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  Prof(tnvan_ctx* c, const char* name, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx->prof_on) return;
+    for (idx = 0; idx < ctx->prof.size(); ++idx)
+      if (ctx->prof[idx].name == name) break;
+    if (idx == ctx->prof.size()) {
+      ctx->prof.emplace_back();
+      ctx->prof.back().name = name;
+    }
+    a = take(ctx);
+    b = take(ctx);
+    if (a) cudaEventRecord(a, s);
+  }
+  ~Prof() {
+    if (!a || !b) return;
+    cudaEventRecord(b, s);
+    ctx->prof[idx].pending.emplace_back(a, b);
+  }
+};
+
+#define PROF(name, stream) Prof _prof_guard(ctx, name, stream)
+
 template <typename T>
 int upload(tnvan_ctx* ctx, Instance& in, const std::vector<T>& v, T** out) {
   *out = nullptr;
@@ -389,6 +426,12 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
   for (Instance& in : ctx->inst) free_instance(in);
+  for (auto& r : ctx->prof)
+    for (auto& pr : r.pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->d_inst) cudaFree(ctx->d_inst);
   if (ctx->d_stats) cudaFree(ctx->d_stats);
   if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
@@ -680,13 +723,19 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   long long max_elems = 0;
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
-  CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, s), "pack kernel");
+  {
+    PROF("pack", s);
+    CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, s), "pack kernel");
+  }
   const int tile = pick_sample_tile(ctx);
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, tile, li))) return rc;
   li.seed = seed;
   li.step = step;
-  CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), d_spins, d_logq, nullptr, s), "sample kernel");
+  {
+    PROF("sample", s);
+    CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), d_spins, d_logq, nullptr, s), "sample kernel");
+  }
   return contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
 }
 
@@ -735,7 +784,10 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+  {
+    PROF("reduce", s);
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+  }
   const int n = li.n_inst;
   std::vector<double> st(8 * n);
   CK(cudaMemcpyAsync(st.data(), ctx->d_stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "stats copy");
@@ -763,8 +815,14 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
-  CK(launch_pack(ctx->d_inst, li.n_inst, max_elems, s), "pack kernel");
-  CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+  {
+    PROF("pack", s);
+    CK(launch_pack(ctx->d_inst, li.n_inst, max_elems, s), "pack kernel");
+  }
+  {
+    PROF("reduce", s);
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+  }
   const int chunk = backward_chunk(ctx, batch);
   LaunchInfo lb;
   if ((rc = fill_launch(ctx, betas, batch, chunk, lb))) return rc;
@@ -772,11 +830,17 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   int smem = 0;
   for (const Instance& in : ctx->inst)
     smem = std::max(smem, (int)((2 * in.W.size() + 2 * in.H[0] + 2 * in.H[1]) * 33 * sizeof(float)));
-  CK(launch_backward(ctx->d_inst, lb, smem, precision, d_spins, d_logZR, d_logq, ctx->d_stats,
-                     ctx->d_grad_packed, (int)max_elems, s),
-     "backward kernel");
-  CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
-     "gradient reduce kernel");
+  {
+    PROF("backward", s);
+    CK(launch_backward(ctx->d_inst, lb, smem, precision, d_spins, d_logZR, d_logq, ctx->d_stats,
+                       ctx->d_grad_packed, (int)max_elems, s),
+       "backward kernel");
+  }
+  {
+    PROF("grad_reduce", s);
+    CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+       "gradient reduce kernel");
+  }
   if (d_dbeta) {
     // forward-mode d/dbeta: a second contraction pass that writes only the derivative
     if ((rc = contract_all(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, s))) return rc;
@@ -787,7 +851,10 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
     LaunchInfo lt;
     if ((rc = fill_launch(ctx, betas, batch, 128, lt))) return rc;
-    CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
+    {
+      PROF("ww_dJ", s);
+      CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
+    }
     bool any_strip = false, other = false;
     for (const Instance& in : ctx->inst) {
       if (in.kind == 0) any_strip = true;
@@ -801,6 +868,7 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
       int sm = 0;
       for (const Instance& in : ctx->inst)
         if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
+      PROF("strips_dJ", s);
       CK(launch_strips_dJ(ctx->d_inst, lt, sm, d_spins, d_dJ, s), "strip adjoint kernel");
     }
     if (other) {
@@ -824,9 +892,50 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
     return fail(ctx, TNVAN_E_ARG, "bad Adam hyper-parameters");
   DeviceGuard g(ctx->device);
   const double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+  PROF("adam", static_cast<cudaStream_t>(stream));
   CK(launch_adam(n, d_params, d_grad, d_m, d_v, (float)lr, (float)beta1, (float)beta2, (float)eps,
                  (float)bc1, (float)bc2, static_cast<cudaStream_t>(stream)),
      "adam kernel");
+  return TNVAN_OK;
+}
+
+int tnvan_profile(tnvan_ctx* ctx, int enable) {
+  if (!ctx) return TNVAN_E_ARG;
+  DeviceGuard g(ctx->device);
+  if (enable) {
+    cudaDeviceSynchronize();
+    for (auto& r : ctx->prof)
+      for (auto& pr : r.pending) {
+        ctx->event_pool.push_back(pr.first);
+        ctx->event_pool.push_back(pr.second);
+      }
+    ctx->prof.clear();
+  }
+  ctx->prof_on = enable != 0;
+  return TNVAN_OK;
+}
+
+int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, double* total_ms,
+                       int64_t* launches) {
+  if (!ctx || index < 0 || index >= (int)ctx->prof.size()) return TNVAN_E_ARG;
+  DeviceGuard g(ctx->device);
+  tnvan_prof_rec& r = ctx->prof[index];
+  for (auto& pr : r.pending) {
+    CK(cudaEventSynchronize(pr.second), "profile event sync");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pr.first, pr.second), "profile elapsed time");
+    r.total_ms += ms;
+    r.launches += 1;
+    ctx->event_pool.push_back(pr.first);
+    ctx->event_pool.push_back(pr.second);
+  }
+  r.pending.clear();
+  if (name && name_len > 0) {
+    strncpy(name, r.name.c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (total_ms) *total_ms = r.total_ms;
+  if (launches) *launches = r.launches;
   return TNVAN_OK;
 }
 
@@ -850,6 +959,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     for (const Instance& in : ctx->inst)
       if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "strip tables need %d B of shared memory", sm);
+    PROF(d_dbeta ? (d_logZR ? "strips+dbeta" : "strips_dbeta") : "strips", s);
     CK(launch_strips(ctx->d_inst, li, sm, d_spins, d_logZR, d_dbeta, s), "strip kernel");
   }
   if (k1) CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s), "dense kernel");

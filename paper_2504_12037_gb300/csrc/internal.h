@@ -168,8 +168,18 @@ struct Instance {
 
 }  // namespace tnvan
 
+struct tnvan_prof_rec {
+  std::string name;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double total_ms = 0;
+  long long launches = 0;
+};
+
 struct tnvan_ctx {
   int device = 0;
+  bool prof_on = false;
+  std::vector<tnvan_prof_rec> prof;
+  std::vector<cudaEvent_t> event_pool;
   std::string err;
   std::vector<tnvan::Instance> inst;
   tnvan::InstDev* d_inst = nullptr;  // device copy of the descriptors

@@ -43,6 +43,8 @@ SIGNATURES = {
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
     "tnvan_backward": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
     "tnvan_adam": (_c_int, [_vp, _c_i64, _vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
+    "tnvan_profile": (_c_int, [_vp, _c_int]),
+    "tnvan_profile_read": (_c_int, [_vp, _c_int, ctypes.c_char_p, _c_int, _dblp, _i64p]),
 }
 
 _LIB = None
@@ -176,6 +178,24 @@ class Context:
         b, pb = _arr(betas, np.float64)
         self._check(lib().tnvan_backward(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq), precision,
                                          _ptr(grad), _ptr(dlogZR_dbeta), _ptr(dlogZR_dJ), _stream(stream)))
+
+    def profile(self, enable: bool):
+        self._check(lib().tnvan_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} of the recorded launches."""
+        out = {}
+        k = 0
+        buf = ctypes.create_string_buffer(64)
+        while True:
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            rc = lib().tnvan_profile_read(self._h, k, buf, 64, ctypes.byref(ms), ctypes.byref(n))
+            if rc == E_ARG:
+                break
+            self._check(rc)
+            out[buf.value.decode()] = (ms.value, n.value)
+            k += 1
+        return out
 
     def adam(self, params, grad, m, v, lr: float, beta1: float, beta2: float, eps: float, t: int, stream=None):
         self._check(lib().tnvan_adam(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
