@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <map>
 #include <numeric>
+#include <set>
 #include <utility>
 
 #include "internal.h"
@@ -285,6 +286,9 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     std::vector<float> zc(256 * 256, 0.f);
     float* c32 = nullptr;
     if ((rc = upload(ctx, in, zc, &c32))) return rc;
+    float* dc32 = nullptr;
+    if ((rc = upload(ctx, in, zc, &dc32))) return rc;
+    dd.dC32 = dc32;
     std::vector<uint16_t> zc16(256 * 256, 0);
     uint16_t* c16 = nullptr;
     if ((rc = upload(ctx, in, zc16, &c16))) return rc;
@@ -811,6 +815,14 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d_dJ)
+    for (const Instance& in : ctx->inst) {
+      if (in.kind == 2)
+        return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ is not implemented for general components (instance with %d spins)", in.n);
+      if (in.kind == 0)
+        for (const StripDev& sd : in.strip.strips)
+          if (sd.L > 64) return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ supports strips of at most 64 rows (got %d)", sd.L);
+    }
   long long max_elems = 0;
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
   LaunchInfo li;
@@ -861,10 +873,6 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
       else other = true;
     }
     if (any_strip) {
-      for (const Instance& in : ctx->inst)
-        if (in.kind == 0)
-          for (const StripDev& sd : in.strip.strips)
-            if (sd.L > 64) return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ supports strips of at most 64 rows (got %d)", sd.L);
       int sm = 0;
       for (const Instance& in : ctx->inst)
         if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
@@ -872,11 +880,10 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
       CK(launch_strips_dJ(ctx->d_inst, lt, sm, d_spins, d_dJ, s), "strip adjoint kernel");
     }
     if (other) {
-      CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
-      int sm = 0;
-      for (const Instance& in : ctx->inst)
-        if (in.kind == 2) sm = std::max(sm, in.g_max_entries * 4 * 32 + 4096);
-      CK(launch_general(ctx->d_inst, lt, sm, d_spins, nullptr, nullptr, d_dJ, s), "general adjoint kernel");
+      {
+        PROF("dense_dJ", s);
+        CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
+      }
     }
   }
   return TNVAN_OK;
@@ -962,26 +969,210 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     PROF(d_dbeta ? (d_logZR ? "strips+dbeta" : "strips_dbeta") : "strips", s);
     CK(launch_strips(ctx->d_inst, li, sm, d_spins, d_logZR, d_dbeta, s), "strip kernel");
   }
-  if (k1) CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s), "dense kernel");
+  if (k1) {
+    PROF(d_dbeta ? "dense_dbeta" : "dense", s);
+    CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s), "dense kernel");
+  }
   if (k2) {
-    int sm = 0;
+    int arena = 0, pairs = 0, Dm = 0;
     for (const Instance& in : ctx->inst)
-      if (in.kind == 2) sm = std::max(sm, in.g_max_entries * 4 * 32 + 4096);
-    CK(launch_general(ctx->d_inst, li, sm, d_spins, d_logZR, d_dbeta, nullptr, s), "general kernel");
+      if (in.kind == 2) {
+        arena = std::max(arena, in.g_max_entries);
+        pairs = std::max(pairs, in.g_npairs);
+        Dm = std::max(Dm, (int)in.W.size());
+      }
+    int T = 64;
+    while (T > 1 && general_smem_bytes(arena, pairs, Dm, T, d_dbeta != nullptr) > 200 * 1024) T /= 2;
+    const int sm = general_smem_bytes(arena, pairs, Dm, T, d_dbeta != nullptr);
+    if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
+    LaunchInfo lg;
+    if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
+    lg.seed = (unsigned long long)arena | ((unsigned long long)pairs << 32);
+    PROF(d_dbeta ? "general_dbeta" : "general", s);
+    CK(launch_general(ctx->d_inst, lg, sm, d_spins, d_logZR, d_dbeta, nullptr, s), "general kernel");
   }
   return TNVAN_OK;
 }
 
+// Dense leftover block: R (|R| <= 16, in index order) split in halves A = R[0..7]
+// and B = R[8..15]; missing spins are free phantoms (no couplings).
 int plan_dense(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
+  std::vector<int> R;
+  for (int v = 0; v < in.n; ++v)
+    if (pos[v] < 0) R.push_back(v);
+  if (R.size() > 16) return TNVAN_E_UNSUPPORTED;
+  const int D = (int)in.W.size();
+  std::vector<int> rpos(in.n, -1);
+  for (size_t i = 0; i < R.size(); ++i) rpos[R[i]] = (int)i;
+  in.dense_nR = (int)R.size();
+  in.JRW.assign(16 * D, 0.f);
+  in.JRR.assign(16 * 16, 0.f);
+  in.eRR.assign(16 * 16, -1);
+  in.eRW.assign(16 * D, -1);
+  double chat = 0;
+  for (int e = 0; e < in.m; ++e) {
+    const int a = in.ei[e], b = in.ej[e];
+    const int ra = rpos[a], rb = rpos[b];
+    if (ra >= 0 && rb >= 0) {
+      in.JRR[ra * 16 + rb] = in.JRR[rb * 16 + ra] = (float)in.J[e];
+      in.eRR[ra * 16 + rb] = in.eRR[rb * 16 + ra] = e;
+      chat += fabs((double)(float)in.J[e]);
+    } else if (ra >= 0 || rb >= 0) {
+      const int r = ra >= 0 ? ra : rb, w = ra >= 0 ? pos[b] : pos[a];
+      in.JRW[r * D + w] = (float)in.J[e];
+      in.eRW[r * D + w] = e;
+    }
+  }
   (void)ctx;
-  (void)in;
-  (void)pos;
-  return TNVAN_E_UNSUPPORTED;
+  in.dense_chat = chat;
+  in.kind = 1;
+  return TNVAN_OK;
 }
 
+// General leftover components: each connected component of R is compiled into
+// a variable-elimination program (order: min-fill on the component graph, ties
+// to the lowest local index).  Program layout (ints), per component:
+//   n_steps, arena_floats, final_offset, then per step:
+//   v, fld_begin, fld_count, m, out_off, n_in, n_pair,
+//   n_in x { in_off, k, pos_0 .. pos_{k-1} }  (pos in the extended scope out+{v})
+//   n_pair x { pair_id, pos_u }                (pos of the neighbour in the out scope)
+// fld: per W-neighbour bond of an R spin, (AR position, edge id); fldJ its coupling.
 int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
-  (void)pos;
-  return fail(ctx, TNVAN_E_UNSUPPORTED, "general component contraction not available for this graph (%d spins)", in.n);
+  auto comps = r_components(in, pos);
+  std::vector<std::vector<std::pair<int, int>>> adj(in.n);  // (neighbour, edge)
+  for (int e = 0; e < in.m; ++e) {
+    adj[in.ei[e]].push_back({in.ej[e], e});
+    adj[in.ej[e]].push_back({in.ei[e], e});
+  }
+  std::vector<int> prog{(int)comps.size()};
+  std::vector<int> fld;
+  std::vector<float> fldJ, pairJ;
+  double chat = 0;
+  int arena_max = 0, width_max = 0;
+  for (const auto& comp : comps) {
+    const int n = (int)comp.size();
+    std::map<int, int> loc;
+    for (int i = 0; i < n; ++i) loc[comp[i]] = i;
+    // local graph, pair ids, field lists
+    std::vector<std::set<int>> g(n);
+    std::map<std::pair<int, int>, int> pair_of;  // (lo, hi) local -> pair id
+    std::vector<int> fb(n), fc(n);
+    for (int i = 0; i < n; ++i) {
+      fb[i] = (int)fld.size() / 2;
+      for (auto [u, e] : adj[comp[i]]) {
+        auto it = loc.find(u);
+        if (it != loc.end()) {
+          const int j = it->second;
+          g[i].insert(j);
+          if (i < j) {
+            pair_of[{i, j}] = (int)pairJ.size();
+            pairJ.push_back((float)in.J[e]);
+            chat += fabs((double)(float)in.J[e]);
+          }
+        } else if (pos[u] >= 0) {
+          fld.push_back(pos[u]);
+          fld.push_back(e);
+          fldJ.push_back((float)in.J[e]);
+        }
+      }
+      fc[i] = (int)fld.size() / 2 - fb[i];
+    }
+    // min-fill elimination order
+    std::vector<std::set<int>> h = g;
+    std::vector<char> gone(n, 0);
+    std::vector<int> order;
+    for (int step = 0; step < n; ++step) {
+      int best = -1;
+      long best_fill = -1;
+      for (int v = 0; v < n; ++v) {
+        if (gone[v]) continue;
+        long fill = 0;
+        for (auto a = h[v].begin(); a != h[v].end(); ++a)
+          for (auto b = std::next(a); b != h[v].end(); ++b)
+            if (!h[*a].count(*b)) ++fill;
+        if (best < 0 || fill < best_fill) {
+          best = v;
+          best_fill = fill;
+        }
+      }
+      order.push_back(best);
+      gone[best] = 1;
+      for (int a : h[best])
+        for (int b : h[best])
+          if (a != b) h[a].insert(b);
+      for (int a : h[best]) h[a].erase(best);
+      h[best].clear();
+    }
+    // simulate elimination to emit the program
+    struct Fac { std::vector<int> scope; int off; };
+    std::vector<Fac> active;
+    std::set<std::pair<int, int>> edges_left;
+    for (auto& kv : pair_of) edges_left.insert(kv.first);
+    const size_t hdr = prog.size();
+    prog.push_back(n);
+    prog.push_back(0);  // arena size, patched below
+    prog.push_back(0);  // final offset, patched below
+    int arena = 0, last_off = 0;
+    for (int v : order) {
+      std::vector<Fac> use, keep;
+      for (auto& f : active) (std::count(f.scope.begin(), f.scope.end(), v) ? use : keep).push_back(f);
+      active.swap(keep);
+      std::vector<std::pair<int, int>> pairs;  // (pair id, u)
+      for (int u : g[v]) {
+        auto key = std::make_pair(std::min(u, v), std::max(u, v));
+        if (edges_left.count(key)) {
+          pairs.push_back({pair_of[key], u});
+          edges_left.erase(key);
+        }
+      }
+      std::set<int> sc;
+      for (auto& f : use) sc.insert(f.scope.begin(), f.scope.end());
+      for (auto& p : pairs) sc.insert(p.second);
+      sc.erase(v);
+      std::vector<int> out(sc.begin(), sc.end());
+      const int m = (int)out.size();
+      if (m > TNVAN_MAX_ELIM_W)
+        return fail(ctx, TNVAN_E_UNSUPPORTED, "component of %d spins needs elimination width %d (max %d)", n, m, TNVAN_MAX_ELIM_W);
+      width_max = std::max(width_max, m);
+      auto ext_pos = [&](int var) -> int {
+        if (var == v) return m;
+        return (int)(std::lower_bound(out.begin(), out.end(), var) - out.begin());
+      };
+      prog.push_back(v);
+      prog.push_back(fb[v]);
+      prog.push_back(fc[v]);
+      prog.push_back(m);
+      prog.push_back(arena);
+      prog.push_back((int)use.size());
+      prog.push_back((int)pairs.size());
+      for (auto& f : use) {
+        prog.push_back(f.off);
+        prog.push_back((int)f.scope.size());
+        for (int var : f.scope) prog.push_back(ext_pos(var));
+      }
+      for (auto& p : pairs) {
+        prog.push_back(p.first);
+        prog.push_back(ext_pos(p.second));
+      }
+      active.push_back(Fac{out, arena});
+      last_off = arena;
+      arena += 1 << m;
+    }
+    prog[hdr + 1] = arena;
+    prog[hdr + 2] = last_off;
+    arena_max = std::max(arena_max, (arena + 3) & ~3);  // keeps the float4 pair table aligned
+  }
+  in.gprog.swap(prog);
+  in.gfld.swap(fld);
+  in.gfldJ.swap(fldJ);
+  in.gpairJ.swap(pairJ);
+  in.g_npairs = (int)in.gpairJ.size();
+  in.g_ncomp = (int)comps.size();
+  in.g_max_entries = arena_max;
+  in.g_chat = chat;
+  in.max_width = width_max;
+  in.kind = 2;
+  return TNVAN_OK;
 }
 
 }  // namespace

@@ -79,6 +79,7 @@ struct DenseDev {
   const float* JRW;    // [16][D] couplings R -> W positions (zero rows for padding)
   const float* JRR;    // [16][16] symmetric, zero diagonal, zero padding
   float* C32;          // [256][256] exp(beta(E_AA+E_BB+a^T J_AB b) - c0), per call
+  float* dC32;         // [256][256] d C / d beta
   uint16_t* C16;       // same in bf16
   double* c0;          // [1] log offset, written with C
   double c_hat;        // sum_{i<j in R} |J_ij| (c0 = beta * c_hat)
@@ -225,6 +226,7 @@ cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* 
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 
 int sample_smem_bytes(const Instance& in, int tile);
+int general_smem_bytes(int arena, int pairs, int D, int T, bool db);
 int strip_smem_bytes(const Instance& in, int tile);
 
 }  // namespace tnvan
