@@ -10,6 +10,7 @@
 #include <set>
 #include <utility>
 
+#include "gemm.h"
 #include "internal.h"
 
 using namespace tnvan;
@@ -362,6 +363,7 @@ int check_ready(tnvan_ctx* ctx, bool need_made) {
 
 int fill_launch(tnvan_ctx* ctx, const double* betas, int batch, int tile, LaunchInfo& li) {
   memset(&li, 0, sizeof li);
+  li.status = ctx->d_status;
   li.n_inst = (int)ctx->inst.size();
   li.batch = batch;
   li.tile = tile;
@@ -377,25 +379,223 @@ int fill_launch(tnvan_ctx* ctx, const double* betas, int batch, int tile, Launch
   return TNVAN_OK;
 }
 
-int pick_sample_tile(const tnvan_ctx* ctx) {
-  int worst = 0;
-  for (const Instance& in : ctx->inst)
-    worst = std::max(worst, (int)(in.W.size() + in.H[0] + in.H[1]) * 4);
-  if (worst * 128 <= 113 * 1024) return 128;
-  if (worst * 64 <= 220 * 1024) return 64;
-  return 32;
-}
-
 int max_sample_smem(const tnvan_ctx* ctx, int tile) {
   int m = 0;
   for (const Instance& in : ctx->inst) m = std::max(m, sample_smem_bytes(in, tile));
   return m;
 }
 
+int pick_sample_tile(const tnvan_ctx* ctx) {
+  // largest tile that keeps two CTAs per SM, else the largest that fits
+  for (int T : {64, 32})
+    if (max_sample_smem(ctx, T) <= 113 * 1024) return T;
+  for (int T : {32, 16, 8})
+    if (max_sample_smem(ctx, T) <= 227 * 1024) return T;
+  return 8;
+}
+
+
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s);
 
 }  // namespace
+
+int ensure_ws(tnvan_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return TNVAN_OK;
+  if (ctx->d_ws) cudaFree(ctx->d_ws);
+  ctx->d_ws = nullptr;
+  ctx->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_ws, bytes);
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(workspace, %zu B): %s", bytes, cudaGetErrorString(e));
+  ctx->ws_bytes = bytes;
+  return TNVAN_OK;
+}
+
+// Floats of the tensor-core backward workspace for `batch` samples.
+size_t tc_ws_floats(const tnvan_ctx* ctx, int batch) {
+  size_t tot = 0;
+  for (const Instance& in : ctx->inst)
+    tot += (size_t)batch * (2 * in.H[0] + 2 * in.H[1] + in.W.size() + 1) + 64;
+  return tot;
+}
+
+#define TC_SPLITS 16
+
+// Backward of sum_b w_b log q(s_b) on the tensor cores (TF32 or BF16 operands,
+// FP32 accumulation): forward chain, delta propagation, and split-K weight
+// gradients (bias gradients ride along as an extra column of ones).
+int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                const double* d_logZR, const float* d_logq, bool bf16, int part_stride,
+                cudaStream_t s) {
+  int rc;
+  const int n = (int)ctx->inst.size();
+  if ((rc = ensure_ws(ctx, tc_ws_floats(ctx, batch) * sizeof(float)))) return rc;
+  float* ws = static_cast<float*>(ctx->d_ws);
+  struct Bufs { float *A1, *A2, *dX, *dA2, *dA1, *w; };
+  std::vector<Bufs> bf(n);
+  size_t off = 0;
+  auto take = [&](size_t cnt) {
+    float* p = ws + off;
+    off += (cnt + 15) & ~size_t(15);
+    return p;
+  };
+  for (int k = 0; k < n; ++k) {
+    const Instance& in = ctx->inst[k];
+    const size_t B = batch, D = in.W.size();
+    bf[k].A1 = take(B * in.H[0]);
+    bf[k].A2 = take(B * in.H[1]);
+    bf[k].dX = take(B * D);
+    bf[k].dA2 = take(B * in.H[1]);
+    bf[k].dA1 = take(B * in.H[0]);
+    bf[k].w = take(B);
+  }
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  // per-instance REINFORCE weights laid out [k][batch] in one contiguous buffer
+  float* wall = take((size_t)n * batch);
+  {
+    PROF("reinforce_w", s);
+    CK(launch_reinforce_w(li, d_logZR, d_logq, ctx->d_stats, wall, s), "weights kernel");
+  }
+  auto op = [](const void* p, long long sr, long long sk, int type) { return GemmOperand{p, sr, sk, type}; };
+  std::vector<GemmProblem> probs;
+  int max_m = 0, splits = 1;
+  auto flush = [&](const char* name) -> int {
+    for (size_t i = 0; i < probs.size(); i += GEMM_MAX_PROB) {
+      GemmLaunch L;
+      memset(&L, 0, sizeof L);
+      L.status = ctx->d_status;
+      const int cnt = (int)std::min<size_t>(GEMM_MAX_PROB, probs.size() - i);
+      for (int j = 0; j < cnt; ++j) L.prob[j] = probs[i + j];
+      PROF(name, s);
+      CK(launch_gemm(L, cnt, max_m, splits, bf16, s), name);
+    }
+    probs.clear();
+    max_m = 0;
+    return TNVAN_OK;
+  };
+  auto base = [&](int M, int N, int K, GemmOperand A, GemmOperand Bo, int epi, float* C, long long ldc) {
+    GemmProblem P;
+    memset(&P, 0, sizeof P);
+    P.M = M;
+    P.N = N;
+    P.K = K;
+    P.A = A;
+    P.B = Bo;
+    P.ones_col = -1;
+    P.epi = epi;
+    P.C = C;
+    P.ldc = ldc;
+    return P;
+  };
+  const int B = batch;
+  // stage 1: A1 = relu(S W1^T + b1)
+  for (int k = 0; k < n; ++k) {
+    const Instance& in = ctx->inst[k];
+    const MadeDev& md = in.dev.made;
+    if (md.nh < 1) continue;
+    const int D = md.D;
+    const int8_t* S = d_spins + in.dev.spin_units * batch;
+    const float* W1 = md.packed + md.layer[0].dst_off;
+    GemmProblem P = base(B, md.H1, D, op(S, D, 1, GT_I8), op(W1, D, 1, GT_F32), EPI_BIAS_RELU, bf[k].A1, md.H1);
+    P.bias = W1 + (long long)md.H1 * D;
+    probs.push_back(P);
+    max_m = std::max(max_m, B);
+  }
+  if ((rc = flush("gemm_fwd1"))) return rc;
+  // stage 2: A2 = relu(A1 W2^T + b2)
+  for (int k = 0; k < n; ++k) {
+    const MadeDev& md = ctx->inst[k].dev.made;
+    if (md.nh < 2) continue;
+    const float* W2 = md.packed + md.layer[1].dst_off;
+    GemmProblem P = base(B, md.H2, md.H1, op(bf[k].A1, md.H1, 1, GT_F32), op(W2, md.H1, 1, GT_F32),
+                         EPI_BIAS_RELU, bf[k].A2, md.H2);
+    P.bias = W2 + (long long)md.H2 * md.H1;
+    probs.push_back(P);
+    max_m = std::max(max_m, B);
+  }
+  if ((rc = flush("gemm_fwd2"))) return rc;
+  // stage 3: dX = w_b s sigmoid(-s x), x = src Wo^T + bo
+  for (int k = 0; k < n; ++k) {
+    const Instance& in = ctx->inst[k];
+    const MadeDev& md = in.dev.made;
+    const int D = md.D, Hl = md.Hl;
+    const int8_t* S = d_spins + in.dev.spin_units * batch;
+    const float* Wo = md.packed + md.layer[md.nh].dst_off;
+    GemmOperand A = md.nh == 0 ? op(S, D, 1, GT_I8) : op(md.nh == 1 ? bf[k].A1 : bf[k].A2, Hl, 1, GT_F32);
+    GemmProblem P = base(B, D, Hl, A, op(Wo, Hl, 1, GT_F32), EPI_DX, bf[k].dX, D);
+    P.bias = Wo + (long long)D * Hl;
+    P.spins = S;
+    P.ld_spins = D;
+    P.row_w = wall + (size_t)k * batch;
+    probs.push_back(P);
+    max_m = std::max(max_m, B);
+  }
+  if ((rc = flush("gemm_out_dx"))) return rc;
+  // stage 4: delta of the last hidden layer = (dX Wo) * 1[h > 0]
+  for (int k = 0; k < n; ++k) {
+    const MadeDev& md = ctx->inst[k].dev.made;
+    if (md.nh < 1) continue;
+    const int D = md.D, Hl = md.Hl;
+    const float* Wo = md.packed + md.layer[md.nh].dst_off;
+    float* out = md.nh == 2 ? bf[k].dA2 : bf[k].dA1;
+    const float* mask = md.nh == 2 ? bf[k].A2 : bf[k].A1;
+    GemmProblem P = base(B, Hl, D, op(bf[k].dX, D, 1, GT_F32), op(Wo, 1, Hl, GT_F32), EPI_MASK, out, Hl);
+    P.mask = mask;
+    P.ld_mask = Hl;
+    probs.push_back(P);
+    max_m = std::max(max_m, B);
+  }
+  if ((rc = flush("gemm_bwd_last"))) return rc;
+  // stage 5: dA1 = (dA2 W2) * 1[h1 > 0]
+  for (int k = 0; k < n; ++k) {
+    const MadeDev& md = ctx->inst[k].dev.made;
+    if (md.nh < 2) continue;
+    const float* W2 = md.packed + md.layer[1].dst_off;
+    GemmProblem P = base(B, md.H1, md.H2, op(bf[k].dA2, md.H2, 1, GT_F32), op(W2, 1, md.H1, GT_F32),
+                         EPI_MASK, bf[k].dA1, md.H1);
+    P.mask = bf[k].A1;
+    P.ld_mask = md.H1;
+    probs.push_back(P);
+    max_m = std::max(max_m, B);
+  }
+  if ((rc = flush("gemm_bwd_h1"))) return rc;
+  // stage 6: weight gradients, split over the batch into TC_SPLITS partial slices
+  splits = std::max(1, std::min(TC_SPLITS, (batch + 127) / 128));
+  float* part = ctx->d_grad_packed;
+  for (int k = 0; k < n; ++k) {
+    const Instance& in = ctx->inst[k];
+    const MadeDev& md = in.dev.made;
+    const int D = md.D;
+    const int8_t* S = d_spins + in.dev.spin_units * batch;
+    float* pk = part + (long long)k * splits * part_stride;
+    for (int l = 0; l <= md.nh; ++l) {
+      const LayerDev& L = md.layer[l];
+      const float* delta = l == md.nh ? bf[k].dX : (l == 1 ? bf[k].dA2 : bf[k].dA1);
+      GemmOperand act;
+      if (l == 0) act = op(S, 1, D, GT_I8);
+      else act = op(l == 1 ? bf[k].A1 : bf[k].A2, 1, L.nin, GT_F32);
+      for (int n0 = 0; n0 < L.nin; n0 += 128) {
+        const bool last = n0 + 128 >= L.nin;
+        const int nn = (L.nin + 1 <= 256) ? L.nin : std::min(128, L.nin - n0);
+        GemmOperand actn = act;
+        actn.ptr = static_cast<const char*>(act.ptr) + (size_t)n0 * (act.type == GT_F32 ? 4 : 1);
+        GemmProblem P = base(L.nout, nn, B, op(delta, 1, L.nout, GT_F32), actn, EPI_STORE,
+                             pk + L.dst_off + n0, L.nin);
+        P.split_stride = part_stride;
+        if (last || L.nin + 1 <= 256) {
+          P.ones_col = nn;
+          P.bias_out = pk + L.dst_off + (long long)L.nout * L.nin;
+        }
+        probs.push_back(P);
+        max_m = std::max(max_m, L.nout);
+        if (L.nin + 1 <= 256) break;
+      }
+    }
+  }
+  if ((rc = flush("gemm_wgrad"))) return rc;
+  return TNVAN_OK;
+}
 
 // ===========================================================================
 // Public API
@@ -415,6 +615,12 @@ int tnvan_create(tnvan_ctx** out, int device) {
   if (!ctx) return fail(nullptr, TNVAN_E_NOMEM, "host allocation failed");
   ctx->device = device;
   DeviceGuard g(device);
+  e = cudaMalloc(&ctx->d_status, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(nullptr, TNVAN_E_NOMEM, "cudaMalloc(status): %s", cudaGetErrorString(e));
+  }
   const size_t stats_doubles = 8 * TNVAN_MAX_INST + (size_t)TNVAN_MAX_INST * 64 * 6;
   e = cudaMalloc(&ctx->d_stats, stats_doubles * sizeof(double));
   if (e != cudaSuccess) {
@@ -438,7 +644,9 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->d_inst) cudaFree(ctx->d_inst);
   if (ctx->d_stats) cudaFree(ctx->d_stats);
+  if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
+  if (ctx->d_ws) cudaFree(ctx->d_ws);
   delete ctx;
   return TNVAN_OK;
 }
@@ -634,6 +842,90 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   md.c1 = dbuf + o_c1;
   md.c2 = dbuf + o_c2;
   md.raw = d_params;
+  // Step groups of the blocked sampler: at most 8 steps and 32 units of each
+  // hidden layer completing inside a group.  Per group, one contiguous weight
+  // block (gathered from `packed` on every call) holds, in order:
+  //   L1 / L2 / output pre-activation tiles: chunks of 16 units, [n_in][16];
+  //   in-group triangles TW1 [n1][gi], TW2 [n2][n1], TWo [gi][nL]
+  //   (n1, n2 = the group's layer units, gi = its steps, nL = the width feeding
+  //   the output inside the group), each padded to a multiple of 4 floats.
+  {
+    const int GMAX = 8, UGMAX = 32;
+    auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
+    auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
+    std::vector<int> grp, src;
+    int ug1 = 0, ug2 = 0, ugo = 0, wmax = 0;
+    const int Hl = md.Hl;
+    auto pad4 = [&]() {
+      while (src.size() % 4) src.push_back(-1);
+    };
+    auto add_blocks = [&](int n_in, int lo, int hi, long long wofs, int stride) {
+      const int off = (int)src.size();
+      for (int c = lo; c < hi; c += 16)
+        for (int j = 0; j < n_in; ++j)
+          for (int q = 0; q < 16; ++q) {
+            const int u = c + q;
+            src.push_back(u < hi ? (int)(wofs + (long long)u * stride + j) : -1);
+          }
+      return off;
+    };
+    auto add_tile = [&](int rlo, int rhi, int clo, int chi, long long wofs, int stride) {
+      const int off = (int)src.size();
+      for (int r = rlo; r < rhi; ++r)
+        for (int c = clo; c < chi; ++c) src.push_back((int)(wofs + (long long)r * stride + c));
+      pad4();
+      return off;
+    };
+    for (int i0 = 0; i0 < D;) {
+      int i1 = i0 + 1;
+      while (i1 < D && i1 - i0 < GMAX && cnt(c1, i0, i1 + 1) <= UGMAX && cnt(c2, i0, i1 + 1) <= UGMAX) ++i1;
+      const int u1lo = before(c1, i0), u1hi = before(c1, i1);
+      const int u2lo = before(c2, i0), u2hi = before(c2, i1);
+      ug1 = std::max(ug1, u1hi - u1lo);
+      ug2 = std::max(ug2, u2hi - u2lo);
+      ugo = std::max(ugo, i1 - i0);
+      const int gstart = (int)src.size();
+      int off1 = 0, off2 = 0, offo = 0, t1 = 0, t2 = 0, to = 0;
+      if (n_hidden >= 1) off1 = add_blocks(i0, u1lo, u1hi, md.layer[0].dst_off, D);
+      if (n_hidden >= 2) off2 = add_blocks(u1lo, u2lo, u2hi, md.layer[1].dst_off, H[0]);
+      const int n_in_o = n_hidden == 0 ? i0 : (n_hidden == 1 ? u1lo : u2lo);
+      offo = add_blocks(n_in_o, i0, i1, md.layer[n_hidden].dst_off, Hl);
+      if (n_hidden >= 1) t1 = add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
+      if (n_hidden >= 2) t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
+      {
+        const int clo = n_hidden == 0 ? i0 : (n_hidden == 1 ? u1lo : u2lo);
+        const int chi = n_hidden == 0 ? i1 : (n_hidden == 1 ? u1hi : u2hi);
+        to = add_tile(i0, i1, clo, chi, md.layer[n_hidden].dst_off, Hl);
+      }
+      pad4();
+      const int gsize = (int)src.size() - gstart;
+      wmax = std::max(wmax, gsize);
+      grp.insert(grp.end(), {i0, i1, u1lo, u1hi, u2lo, u2hi, n_hidden >= 1 ? off1 - gstart : 0,
+                             n_hidden >= 2 ? off2 - gstart : 0, offo - gstart, gstart, gsize, 0,
+                             n_hidden >= 1 ? t1 - gstart : 0, n_hidden >= 2 ? t2 - gstart : 0,
+                             to - gstart});
+      i0 = i1;
+    }
+    int* dgrp = nullptr;
+    if ((rc = upload(ctx, in, grp, &dgrp))) return rc;
+    int* dsrc = nullptr;
+    if ((rc = upload(ctx, in, src, &dsrc))) return rc;
+    void* blk = nullptr;
+    if (!src.empty()) {
+      cudaError_t e2 = cudaMalloc(&blk, src.size() * sizeof(float));
+      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blocks): %s", cudaGetErrorString(e2));
+      in.dev_allocs.push_back(blk);
+    }
+    md.n_groups = (int)grp.size() / GROUP_INTS;
+    md.wmax = wmax;
+    md.groups = dgrp;
+    md.ug1 = ug1;
+    md.ug2 = ug2;
+    md.ugo = ugo;
+    md.blocks = static_cast<float*>(blk);
+    md.blk_src = dsrc;
+    md.n_blk = (long long)src.size();
+  }
   void* packed = nullptr;
   cudaError_t e = cudaMalloc(&packed, off * sizeof(float));
   if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(packed params): %s", cudaGetErrorString(e));
@@ -708,6 +1000,16 @@ int tnvan_reserve(tnvan_ctx* ctx, int max_batch) {
   if (rc) return rc;
   rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, std::max(max_batch, 1)));
   if (rc) return rc;
+  {
+    long long maxp = 0;
+    for (const Instance& in : ctx->inst) maxp = std::max(maxp, in.n_params);
+    const int splits = std::max(1, std::min(TC_SPLITS, (std::max(max_batch, 1) + 127) / 128));
+    rc = ensure_grad_ws(ctx, std::max(grad_ws_floats(ctx, std::max(max_batch, 1)),
+                                      (size_t)splits * ctx->inst.size() * (size_t)maxp));
+    if (rc) return rc;
+    rc = ensure_ws(ctx, tc_ws_floats(ctx, std::max(max_batch, 1)) * sizeof(float));
+    if (rc) return rc;
+  }
   ctx->reserved_batch = std::max(ctx->reserved_batch, max_batch);
   CK(cudaDeviceSynchronize(), "reserve");
   return TNVAN_OK;
@@ -725,11 +1027,14 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
   if (rc) return rc;
   if (batch == 0) return TNVAN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  long long max_elems = 0;
-  for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
+  long long max_elems = 0, max_blk = 0;
+  for (const Instance& in : ctx->inst) {
+    max_elems = std::max(max_elems, in.n_params);
+    max_blk = std::max(max_blk, in.dev.made.n_blk);
+  }
   {
     PROF("pack", s);
-    CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, s), "pack kernel");
+    CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
   }
   const int tile = pick_sample_tile(ctx);
   LaunchInfo li;
@@ -752,9 +1057,12 @@ int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, float* d_lo
   if (rc) return rc;
   if (batch == 0) return TNVAN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  long long max_elems = 0;
-  for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
-  CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, s), "pack kernel");
+  long long max_elems = 0, max_blk = 0;
+  for (const Instance& in : ctx->inst) {
+    max_elems = std::max(max_elems, in.n_params);
+    max_blk = std::max(max_blk, in.dev.made.n_blk);
+  }
+  CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
   const int tile = pick_sample_tile(ctx);
   LaunchInfo li;
   std::vector<double> ones(ctx->inst.size(), 1.0);
@@ -795,7 +1103,14 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
   const int n = li.n_inst;
   std::vector<double> st(8 * n);
   CK(cudaMemcpyAsync(st.data(), ctx->d_stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "stats copy");
+  int status[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(status, ctx->d_status, sizeof status, cudaMemcpyDeviceToHost, s), "status copy");
   CK(cudaStreamSynchronize(s), "stream sync");
+  if (status[0]) {
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof status, s), "status reset");
+    CK(cudaStreamSynchronize(s), "stream sync");
+    return fail(ctx, TNVAN_E_TIMEOUT, "a bounded device wait gave up (code %d); results of this batch are invalid", status[0]);
+  }
   for (int k = 0; k < n; ++k) {
     if (st[8 * k + 5] > 0)
       return fail(ctx, TNVAN_E_OVERFLOW, "instance %d: %.0f non-finite l_b values", k, st[8 * k + 5]);
@@ -829,29 +1144,46 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
   {
     PROF("pack", s);
-    CK(launch_pack(ctx->d_inst, li.n_inst, max_elems, s), "pack kernel");
+    CK(launch_pack(ctx->d_inst, li.n_inst, max_elems, 0, s), "pack kernel");
   }
   {
     PROF("reduce", s);
     CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
   }
+  if (precision != TNVAN_FP32) {
+    const int splits = std::max(1, std::min(TC_SPLITS, (batch + 127) / 128));
+    if ((rc = ensure_grad_ws(ctx, (size_t)splits * ctx->inst.size() * (size_t)max_elems))) return rc;
+    if ((rc = backward_tc(ctx, betas, batch, d_spins, d_logZR, d_logq, precision == TNVAN_BF16,
+                          (int)max_elems, s)))
+      return rc;
+    LaunchInfo lr;
+    if ((rc = fill_launch(ctx, betas, batch, 1, lr))) return rc;
+    for (int k = 0; k <= lr.n_inst; ++k) lr.tile_begin[k] = k * splits;
+    {
+      PROF("grad_reduce", s);
+      CK(launch_grad_reduce(ctx->d_inst, lr, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+         "gradient reduce kernel");
+    }
+  }
   const int chunk = backward_chunk(ctx, batch);
   LaunchInfo lb;
   if ((rc = fill_launch(ctx, betas, batch, chunk, lb))) return rc;
-  if ((rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, batch)))) return rc;
+  if (precision == TNVAN_FP32 && (rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, batch)))) return rc;
   int smem = 0;
   for (const Instance& in : ctx->inst)
     smem = std::max(smem, (int)((2 * in.W.size() + 2 * in.H[0] + 2 * in.H[1]) * 33 * sizeof(float)));
-  {
-    PROF("backward", s);
-    CK(launch_backward(ctx->d_inst, lb, smem, precision, d_spins, d_logZR, d_logq, ctx->d_stats,
-                       ctx->d_grad_packed, (int)max_elems, s),
-       "backward kernel");
-  }
-  {
-    PROF("grad_reduce", s);
-    CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
-       "gradient reduce kernel");
+  if (precision == TNVAN_FP32) {
+    {
+      PROF("backward", s);
+      CK(launch_backward(ctx->d_inst, lb, smem, precision, d_spins, d_logZR, d_logq, ctx->d_stats,
+                         ctx->d_grad_packed, (int)max_elems, s),
+         "backward kernel");
+    }
+    {
+      PROF("grad_reduce", s);
+      CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+         "gradient reduce kernel");
+    }
   }
   if (d_dbeta) {
     // forward-mode d/dbeta: a second contraction pass that writes only the derivative

@@ -14,6 +14,7 @@
 #define TNVAN_MAX_D 1024
 #define TNVAN_MAX_STRIP_W 4
 #define TNVAN_MAX_ELIM_W 8
+#define GROUP_INTS 15
 
 namespace tnvan {
 
@@ -42,6 +43,16 @@ struct MadeDev {
   float* packed;          // packed, masked, degree-sorted copy (W then b per layer)
   const int* c1;          // [D+1] number of layer-1 units with degree <= d
   const int* c2;          // [D+1] number of layer-2 units with degree <= d
+  // Blocked sampler: steps are grouped; for each group and layer the weights
+  // from all earlier inputs to the group's units are stored as chunks of 16
+  // units, [n_in][16] floats each (see k_made.cu).
+  int n_groups;
+  const int* groups;      // [n_groups][GROUP_INTS], see k_made.cu
+  int ug1, ug2, ugo;      // largest group unit counts per layer
+  int wmax;               // largest per-group weight block (floats)
+  float* blocks;          // blocked weights (gathered from `packed` every call)
+  const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
+  long long n_blk;
   long long n_params;     // size of the natural layout
   long long param_off;    // offset in the all-instances packed gradient layout
 };
@@ -125,6 +136,7 @@ struct LaunchInfo {
   int batch;
   int tile;  // samples per CTA
   unsigned long long seed, step;
+  int* status;  // device status word: nonzero after a bounded wait gave up
   double beta[TNVAN_MAX_INST];
   int tile_begin[TNVAN_MAX_INST + 1];
 };
@@ -188,6 +200,7 @@ struct tnvan_ctx {
   bool dirty = true;                 // descriptors changed since last upload
   // workspaces (grown on demand, or by tnvan_reserve)
   double* d_stats = nullptr;         // [n_inst][8]
+  int* d_status = nullptr;           // [4] device status words
   size_t ws_bytes = 0;
   void* d_ws = nullptr;              // general workspace
   int reserved_batch = 0;
@@ -198,7 +211,8 @@ struct tnvan_ctx {
 namespace tnvan {
 
 // Kernel launchers (defined in the .cu files).  All return a cudaError_t.
-cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, cudaStream_t s);
+cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, long long max_blk,
+                        cudaStream_t s);
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);
 cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
@@ -222,6 +236,8 @@ cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int sme
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                const float* partials, int part_stride, float* grad,
                                cudaStream_t s);
+cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
+                               const double* stats, float* w, cudaStream_t s);
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 

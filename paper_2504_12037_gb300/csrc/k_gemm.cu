@@ -1,0 +1,193 @@
+// Batched tensor-core GEMM on tcgen05 (sm_103a) with fused epilogues, used by
+// the TF32 / BF16 backward of the network (Eq. 10).
+//
+// One CTA (128 threads) computes a 128-row tile of C[M x N] = A[M x K] B[N x K]^T
+// (N <= 256) for one problem of the launch.  A and B are read from global
+// memory through arbitrary (row, k) strides -- so transposed operands cost
+// nothing extra -- converted to BF16 or TF32 and written by the threads into
+// the canonical no-swizzle K-major shared-memory layout.  Two K stages of 32
+// elements are double-buffered: the threads fill one stage while the tensor
+// core works on the other; one elected thread issues tcgen05.mma into a TMEM
+// accumulator and commits each stage to an mbarrier.  The epilogue reads the
+// accumulator row per thread (tcgen05.ld) and applies the fused operation.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "gemm.h"
+#include "tc.cuh"
+
+namespace tnvan {
+
+#define GM 128
+#define GK 32
+
+template <int TYPE>
+__device__ __forceinline__ float load_elem(const void* p, long long idx) {
+  if (TYPE == GT_F32) return static_cast<const float*>(p)[idx];
+  if (TYPE == GT_I8) return (float)static_cast<const int8_t*>(p)[idx];
+  return 0.f;
+}
+
+__device__ __forceinline__ float load_any(int type, const void* p, long long idx) {
+  return type == GT_F32 ? static_cast<const float*>(p)[idx]
+                        : (float)static_cast<const int8_t*>(p)[idx];
+}
+
+// Fill one K stage: rows [r0, r0 + nrows) of an operand, k in [k0, k0 + GK).
+// Rows >= rlim or k >= klim are zero; row == ones_row reads 1 (bias column).
+template <bool BF16>
+__device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
+                                           int r0, int rlim, int k0, int klim, int ones_row, int t) {
+  constexpr int EL = BF16 ? 2 : 4;
+  constexpr int KB = GK * EL;  // bytes of K per row in the stage
+  const bool kfast = op.sk == 1;  // coalesce along k when k is the contiguous index
+  const int total = nrows * GK;
+  for (int e = t; e < total; e += 128) {
+    int r, k;
+    if (kfast) {
+      r = e / GK;
+      k = e % GK;
+    } else {
+      r = e % nrows;
+      k = e / nrows;
+    }
+    const int gr = r0 + r, gk = k0 + k;
+    float v = 0.f;
+    if (gr == ones_row) v = gk < klim ? 1.f : 0.f;
+    else if (gr < rlim && gk < klim) v = load_any(op.type, op.ptr, (long long)gr * op.sr + (long long)gk * op.sk);
+    const uint32_t o = tc::kmajor_off(r, k, KB, EL);
+    if (BF16) *reinterpret_cast<__nv_bfloat16*>(s + o) = __float2bfloat16(v);
+    else *reinterpret_cast<float*>(s + o) = v;
+  }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  constexpr int EL = BF16 ? 2 : 4;
+  constexpr int KB = GK * EL;
+  const GemmProblem& P = L.prob[blockIdx.y];
+  const int m0 = blockIdx.x * GM;
+  if (m0 >= P.M) return;
+  const int t = threadIdx.x;
+  const int Np = (P.N + (P.ones_col >= 0 ? 1 : 0) + 15) & ~15;  // padded N (multiple of 16)
+  const int stageA = GM * KB, stageB = 256 * KB;
+  unsigned char* sA[2] = {smem, smem + stageA + stageB};
+  unsigned char* sB[2] = {smem + stageA, smem + 2 * stageA + stageB};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (stageA + stageB));
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  // split K
+  const int kchunk = (P.K + gridDim.z - 1) / gridDim.z;
+  const int kbeg = blockIdx.z * kchunk, kend = min(P.K, kbeg + kchunk);
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  if (t < 32) {
+    tc::tmem_alloc(slot, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  const uint32_t id = tc::idesc(GM, Np, BF16 ? 1u : 2u);
+  const int nk = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
+  bool ok = true;
+  for (int ks = 0; ks < nk; ++ks) {
+    const int st = ks & 1;
+    if (ks >= 2 && !mbar_wait(&bar[st], (uint32_t)(((ks >> 1) - 1) & 1))) {
+      ok = false;
+      break;
+    }
+    const int k0 = kbeg + ks * GK;
+    fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t);
+    fill_stage<BF16>(sB[st], Np, P.B, 0, P.N, k0, kend, P.ones_col, t);
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < KB / 32; ++kk) {
+        const uint64_t a = tc::smem_desc(smem_u32(sA[st]) + kk * 256, 128, KB / 16 * 128);
+        const uint64_t b = tc::smem_desc(smem_u32(sB[st]) + kk * 256, 128, KB / 16 * 128);
+        if (BF16) tc::mma_bf16(tmem, a, b, id, (ks > 0 || kk > 0) ? 1u : 0u);
+        else tc::mma_tf32(tmem, a, b, id, (ks > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&bar[st]);
+    }
+  }
+  if (ok && nk > 0) ok = mbar_wait(&bar[(nk - 1) & 1], (uint32_t)(((nk - 1) >> 1) & 1));
+  if (!ok && t == 0) atomicExch(L.status, 2);
+  tc::fence_after_sync();
+  // epilogue: thread t owns row m0 + t (TMEM lane t)
+  const int w = t >> 5;
+  const int m = m0 + t;
+  if (ok) {
+    for (int c = 0; c < Np; c += 16) {
+      float v[16];
+      if (nk > 0) tc::tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + (uint32_t)c, v);
+      else
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (m >= P.M) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = c + i;
+        float a = v[i];
+        if (n == P.ones_col) {
+          if (P.bias_out) P.bias_out[(long long)blockIdx.z * P.split_stride + m] = a;
+          continue;
+        }
+        if (n >= P.N) continue;
+        const long long o = (long long)m * P.ldc + n;
+        switch (P.epi) {
+          case EPI_STORE:
+            P.C[(long long)blockIdx.z * P.split_stride + o] = a;
+            break;
+          case EPI_BIAS_RELU:
+            P.C[o] = fmaxf(a + P.bias[n], 0.f);
+            break;
+          case EPI_DX: {
+            const float x = a + P.bias[n];
+            const float s = (float)P.spins[(long long)m * P.ld_spins + n];
+            P.C[o] = P.row_w[m] * s / (1.f + expf(s * x));
+            break;
+          }
+          case EPI_MASK:
+            P.C[o] = P.mask[(long long)m * P.ld_mask + n] > 0.f ? a : 0.f;
+            break;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (t < 32) tc::tmem_dealloc(tmem, 256);
+}
+
+int gemm_smem_bytes(bool bf16) {
+  const int EL = bf16 ? 2 : 4;
+  return 2 * (GM * GK * EL + 256 * GK * EL) + 64;
+}
+
+cudaError_t launch_gemm(const GemmLaunch& L, int n_prob, int max_m, int splits, bool bf16,
+                        cudaStream_t s) {
+  if (n_prob == 0 || max_m == 0) return cudaSuccess;
+  const int smem = gemm_smem_bytes(bf16);
+  dim3 grid((max_m + GM - 1) / GM, n_prob, splits);
+  cudaError_t e;
+  if (bf16) {
+    e = cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    gemm_tc_kernel<true><<<grid, 128, smem, s>>>(L);
+  } else {
+    e = cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    gemm_tc_kernel<false><<<grid, 128, smem, s>>>(L);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tnvan

@@ -31,89 +31,198 @@ __global__ void pack_kernel(const InstDev* __restrict__ inst) {
   }
 }
 
-cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, cudaStream_t s) {
+// Gather the blocked sampler weights from the packed layout.
+__global__ void pack_blocks_kernel(const InstDev* __restrict__ inst) {
+  const MadeDev& md = inst[blockIdx.y].made;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= md.n_blk) return;
+  const int src = md.blk_src[e];
+  md.blocks[e] = src >= 0 ? md.packed[src] : 0.f;
+}
+
+cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, long long max_blk,
+                        cudaStream_t s) {
   if (n_inst == 0 || max_elems == 0) return cudaSuccess;
-  dim3 grid((unsigned)((max_elems + 255) / 256), n_inst);
-  pack_kernel<<<grid, 256, 0, s>>>(d_inst);
+  pack_kernel<<<dim3((unsigned)((max_elems + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || max_blk == 0) return e;
+  pack_blocks_kernel<<<dim3((unsigned)((max_blk + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
   return cudaGetLastError();
 }
 
 // Dot product of a warp-uniform weight row with this thread's activation
-// column (layout [unit][T]), four partial sums for instruction-level parallelism.
+// column (layout [unit][T]) over entries [j0, j1).
 __device__ __forceinline__ float dot_col(const float* __restrict__ w, const float* col, int T,
-                                         int n) {
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  int j = 0;
-  for (; j + 4 <= n; j += 4) {
-    a0 = fmaf(__ldg(w + j), col[(j)*T], a0);
+                                         int j0, int j1) {
+  float a0 = 0.f, a1 = 0.f;
+  int j = j0;
+  for (; j + 2 <= j1; j += 2) {
+    a0 = fmaf(__ldg(w + j), col[j * T], a0);
     a1 = fmaf(__ldg(w + j + 1), col[(j + 1) * T], a1);
-    a2 = fmaf(__ldg(w + j + 2), col[(j + 2) * T], a2);
-    a3 = fmaf(__ldg(w + j + 3), col[(j + 3) * T], a3);
   }
-  for (; j < n; ++j) a0 = fmaf(__ldg(w + j), col[j * T], a0);
-  return (a0 + a1) + (a2 + a3);
+  if (j < j1) a0 = fmaf(__ldg(w + j), col[j * T], a0);
+  return a0 + a1;
 }
 
-// Ancestral sampling, one thread per sample, tile of T samples per CTA.
-// Hidden units are degree-sorted, so at step i (output i, degree i+1):
-//   layer-1 units of degree i need inputs 0..i-1 (all drawn),
-//   layer-2 units of degree i need the layer-1 prefix c1[i],
-//   output i needs the last hidden prefix c_L[i].
-// Every unit is therefore evaluated exactly once: one masked forward pass.
-// With `given` non-null the spins are read from it instead of drawn (teacher
-// forcing), which evaluates log q of caller-supplied configurations.
-// Shared memory (per CTA): S [D][T] spins as +-1 floats, A1 [H1][T], A2 [H2][T].
-__global__ void __launch_bounds__(128) sample_kernel(const InstDev* __restrict__ inst,
-                                                     const LaunchInfo li,
-                                                     int8_t* __restrict__ spins,
-                                                     float* __restrict__ logq,
-                                                     const int8_t* __restrict__ given) {
-  extern __shared__ float sm[];
+// Pre-activations of up to 16 units from n_in inputs: acc[q] = bias[q] +
+// sum_j blk[j][q] * act[j], one activation load per 16 FMAs, weights as
+// warp-uniform float4 loads.  Results go to pre[q][T] (q < nu).
+__device__ __forceinline__ void block_preact(const float* blk, const float* act, int T,
+                                             int n_in, const float* __restrict__ bias, int nu,
+                                             float* pre) {
+  float acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = q < nu ? __ldg(bias + q) : 0.f;
+  const float4* w4 = reinterpret_cast<const float4*>(blk);
+#pragma unroll 2
+  for (int j = 0; j < n_in; ++j) {
+    const float x = act[j * T];
+    const float4 a = w4[4 * j], b = w4[4 * j + 1], c = w4[4 * j + 2], d = w4[4 * j + 3];
+    acc[0] = fmaf(a.x, x, acc[0]);
+    acc[1] = fmaf(a.y, x, acc[1]);
+    acc[2] = fmaf(a.z, x, acc[2]);
+    acc[3] = fmaf(a.w, x, acc[3]);
+    acc[4] = fmaf(b.x, x, acc[4]);
+    acc[5] = fmaf(b.y, x, acc[5]);
+    acc[6] = fmaf(b.z, x, acc[6]);
+    acc[7] = fmaf(b.w, x, acc[7]);
+    acc[8] = fmaf(c.x, x, acc[8]);
+    acc[9] = fmaf(c.y, x, acc[9]);
+    acc[10] = fmaf(c.z, x, acc[10]);
+    acc[11] = fmaf(c.w, x, acc[11]);
+    acc[12] = fmaf(d.x, x, acc[12]);
+    acc[13] = fmaf(d.y, x, acc[13]);
+    acc[14] = fmaf(d.z, x, acc[14]);
+    acc[15] = fmaf(d.w, x, acc[15]);
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (q < nu) pre[q * T] = acc[q];
+}
+
+// Pre-activations of the units [lo, hi) of one layer for the current group.
+__device__ __forceinline__ void layer_preact(const float* blocks, int off, int n_in,
+                                             int lo, int hi, const float* __restrict__ bias,
+                                             const float* act, int T, float* pre) {
+  for (int c = lo; c < hi; c += 16) {
+    const int nu = min(16, hi - c);
+    block_preact(blocks + off + (long long)(c - lo) * n_in, act, T, n_in, bias + c, nu,
+                 pre + (c - lo) * T);
+  }
+}
+
+// Ancestral sampling (Eq. 8), one thread per sample, T samples per CTA.
+// Hidden units are degree-sorted, so output i (degree i+1) needs exactly the
+// inputs 0..i-1, the layer-1 units of degree <= i and the layer-2 units of
+// degree <= i, each evaluated once: one masked forward pass in total.
+// The steps are processed in groups (host table `groups`, GROUP_INTS ints:
+// i0, i1, u1lo, u1hi, u2lo, u2hi, off1, off2, offo, gstart, gsize, -, t1, t2, to):
+//   the group's weight block is bulk-copied (TMA 1-D) into shared memory;
+//   phase A: for the units completing inside the group, the contribution of
+//            every input known before the group (register tiled, 16 units);
+//   phase B: the group's steps one by one, adding the in-group contributions
+//            and drawing s_i = +1 iff u < sigmoid(x_i).
+// With `given` non-null the spins are read from it (teacher forcing).
+// Shared memory: [unit][T] S [D], A1 [H1], A2 [H2], P1 [ug1], P2 [ug2],
+// PO [ugo]; then the weight block [wmax] and one mbarrier.
+__global__ void __launch_bounds__(64) sample_kernel(const InstDev* __restrict__ inst,
+                                                    const LaunchInfo li,
+                                                    int8_t* __restrict__ spins,
+                                                    float* __restrict__ logq,
+                                                    const int8_t* __restrict__ given) {
+  extern __shared__ __align__(16) float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
   const MadeDev& md = I.made;
   const int T = li.tile, t = threadIdx.x;
   const int b = (blockIdx.x - li.tile_begin[k]) * T + t;
-  const int D = md.D, nh = md.nh, H1 = md.H1, H2 = md.H2, Hl = md.Hl;
+  const int D = md.D, nh = md.nh, H1 = md.H1, H2 = md.H2;
   float* S = sm;
   float* A1 = S + D * T;
   float* A2 = A1 + H1 * T;
-  const float* W1 = md.packed + md.layer[0].dst_off;
-  const float* b1 = W1 + (long long)H1 * D;
-  const float* W2 = nh >= 2 ? md.packed + md.layer[1].dst_off : nullptr;
-  const float* b2 = nh >= 2 ? W2 + (long long)H2 * H1 : nullptr;
-  const float* Wo = md.packed + md.layer[nh].dst_off;
-  const float* bo = Wo + (long long)D * Hl;
+  float* P1 = A2 + H2 * T;
+  float* P2 = P1 + md.ug1 * T;
+  float* PO = P2 + md.ug2 * T;
+  float* Wsm = PO + md.ugo * T;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Wsm + ((md.wmax + 3) & ~3));
   const float* src = nh == 0 ? S : (nh == 1 ? A1 : A2);
+  const float* bias1 = md.packed + md.layer[0].dst_off + (long long)H1 * D;
+  const float* bias2 = nh >= 2 ? md.packed + md.layer[1].dst_off + (long long)H2 * H1 : nullptr;
+  const float* biaso = md.packed + md.layer[nh].dst_off + (long long)D * md.Hl;
   const int* cL = nh == 1 ? md.c1 : md.c2;
   const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
+  const int8_t* gv = given ? given + I.spin_units * li.batch + (long long)b * D : nullptr;
+  const bool valid = b < li.batch;
+  if (t == 0) mbar_init(bar, 1);
+  __syncthreads();
   float lq = 0.f;
   uint4 rnd = make_uint4(0, 0, 0, 0);
-  for (int i = 0; i < D; ++i) {
-    if ((i & 3) == 0)
-      rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), (uint32_t)li.step, (uint32_t)k),
-                          key);
-    if (nh >= 1 && i >= 1) {
-      const int u0 = md.c1[i - 1], u1 = md.c1[i];
-      for (int u = u0; u < u1; ++u)
-        A1[u * T + t] = fmaxf(__ldg(b1 + u) + dot_col(W1 + (long long)u * D, S + t, T, i), 0.f);
+  for (int g = 0; g < md.n_groups; ++g) {
+    const int* G = md.groups + GROUP_INTS * g;
+    const int i0 = G[0], i1 = G[1], u1lo = G[2], u1hi = G[3], u2lo = G[4], u2hi = G[5];
+    const int gsize = G[10];
+    __syncthreads();  // every thread is done with the previous block
+    if (t == 0) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(bar, (uint32_t)gsize * 4u);
+      bulk_g2s(Wsm, md.blocks + G[9], (uint32_t)gsize * 4u, bar);
     }
-    if (nh >= 2 && i >= 1) {
-      const int u0 = md.c2[i - 1], u1 = md.c2[i], n1 = md.c1[i];
-      for (int u = u0; u < u1; ++u)
-        A2[u * T + t] = fmaxf(__ldg(b2 + u) + dot_col(W2 + (long long)u * H1, A1 + t, T, n1), 0.f);
+    if (!mbar_wait(bar, (uint32_t)(g & 1))) {
+      if (t == 0) atomicExch(li.status, 1);
+      return;
     }
-    const int nin = nh == 0 ? i : cL[i];
-    const float x = __ldg(bo + i) + dot_col(Wo + (long long)i * Hl, src + t, T, nin);
-    const float p = 1.f / (1.f + expf(-x));
-    const uint32_t word = (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
-    const float u = (float)(word >> 8) * 5.9604644775390625e-08f;  // 2^-24
-    float s = u < p ? 1.f : -1.f;
-    if (given) s = (b < li.batch) ? (float)given[I.spin_units * li.batch + (long long)b * D + i] : 1.f;
-    S[i * T + t] = s;
-    lq -= softplusf(-s * x);
+    // phase A
+    if (nh >= 1) layer_preact(Wsm, G[6], i0, u1lo, u1hi, bias1, S + t, T, P1 + t);
+    if (nh >= 2) layer_preact(Wsm, G[7], u1lo, u2lo, u2hi, bias2, A1 + t, T, P2 + t);
+    {
+      const int n_in = nh == 0 ? i0 : (nh == 1 ? u1lo : u2lo);
+      layer_preact(Wsm, G[8], n_in, i0, i1, biaso, src + t, T, PO + t);
+    }
+    // phase B
+    const int gi = i1 - i0, n1 = u1hi - u1lo;
+    const int clo = nh == 0 ? i0 : (nh == 1 ? u1lo : u2lo);
+    const int nL = nh == 0 ? gi : (nh == 1 ? n1 : u2hi - u2lo);
+    const float* TW1 = Wsm + G[12];
+    const float* TW2 = Wsm + G[13];
+    const float* TWo = Wsm + G[14];
+    for (int i = i0; i < i1; ++i) {
+      if ((i & 3) == 0)
+        rnd = philox4x32_10(
+            make_uint4((uint32_t)b, (uint32_t)(i >> 2), (uint32_t)li.step, (uint32_t)k), key);
+      if (nh >= 1 && i >= 1) {
+        for (int u = md.c1[i - 1]; u < md.c1[i]; ++u) {
+          const float* w = TW1 + (u - u1lo) * gi;
+          float a = P1[(u - u1lo) * T + t];
+          for (int j = i0; j < i; ++j) a = fmaf(w[j - i0], S[j * T + t], a);
+          A1[u * T + t] = fmaxf(a, 0.f);
+        }
+      }
+      if (nh >= 2 && i >= 1) {
+        const int n1i = md.c1[i];
+        for (int v = md.c2[i - 1]; v < md.c2[i]; ++v) {
+          const float* w = TW2 + (v - u2lo) * n1;
+          float a = P2[(v - u2lo) * T + t];
+          for (int u = u1lo; u < n1i; ++u) a = fmaf(w[u - u1lo], A1[u * T + t], a);
+          A2[v * T + t] = fmaxf(a, 0.f);
+        }
+      }
+      float x = PO[(i - i0) * T + t];
+      {
+        const float* w = TWo + (i - i0) * nL;
+        const int chi = nh == 0 ? i : cL[i];
+        for (int c = clo; c < chi; ++c) x = fmaf(w[c - clo], src[c * T + t], x);
+      }
+      const float p = 1.f / (1.f + expf(-x));
+      const uint32_t word =
+          (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
+      const float u = (float)(word >> 8) * 5.9604644775390625e-08f;  // 2^-24
+      float s = u < p ? 1.f : -1.f;
+      if (gv) s = valid ? (float)gv[i] : 1.f;
+      S[i * T + t] = s;
+      lq -= softplusf(-s * x);
+    }
   }
-  if (b < li.batch) {
+  if (valid) {
     if (spins) {
       int8_t* out = spins + I.spin_units * li.batch + (long long)b * D;
       for (int i = 0; i < D; ++i) out[i] = (int8_t)S[i * T + t];
@@ -123,7 +232,9 @@ __global__ void __launch_bounds__(128) sample_kernel(const InstDev* __restrict__
 }
 
 int sample_smem_bytes(const Instance& in, int tile) {
-  return (int)((in.W.size() + in.H[0] + in.H[1]) * tile * sizeof(float));
+  const MadeDev& md = in.dev.made;
+  return (int)((in.W.size() + in.H[0] + in.H[1] + md.ug1 + md.ug2 + md.ugo) * tile * sizeof(float) +
+               ((md.wmax + 3) & ~3) * sizeof(float) + 16);
 }
 
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,

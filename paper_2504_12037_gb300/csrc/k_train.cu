@@ -385,6 +385,27 @@ cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, cons
   return cudaGetLastError();
 }
 
+// REINFORCE weights w_b = -(l_b - mean_b l) / (beta B) per instance (Eq. 10
+// with the batch-mean baseline), FP32 copy for the tensor-core backward.
+__global__ void reinforce_w_kernel(const LaunchInfo li, const double* __restrict__ logZR,
+                                   const float* __restrict__ logq, const double* __restrict__ stats,
+                                   float* __restrict__ w) {
+  const int k = blockIdx.y;
+  const double mean = stats[8 * k + 4];
+  const double sc = -1.0 / (li.beta[k] * (double)li.batch);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < li.batch; b += gridDim.x * blockDim.x) {
+    const long long o = (long long)k * li.batch + b;
+    w[o] = (float)(sc * (logZR[o] - (double)logq[o] - mean));
+  }
+}
+
+cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
+                               const double* stats, float* w, cudaStream_t s) {
+  if (li.n_inst == 0 || li.batch == 0) return cudaSuccess;
+  reinforce_w_kernel<<<dim3(32, li.n_inst), 256, 0, s>>>(li, logZR, logq, stats, w);
+  return cudaGetLastError();
+}
+
 // Adam (Kingma & Ba 2015), bias corrections bc1 = 1 - b1^t, bc2 = 1 - b2^t.
 __global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, float lr, float b1,

@@ -1,0 +1,106 @@
+// Fifth-generation tensor core (tcgen05) building blocks for sm_103a:
+// TMEM allocation, shared-memory matrix descriptors (no swizzle, K-major),
+// instruction descriptors, single-thread MMA issue, commit to an mbarrier and
+// TMEM -> register loads.  Inline PTX, no library.
+#pragma once
+#include <stdint.h>
+
+namespace tnvan {
+namespace tc {
+
+// --- TMEM allocation (one full warp) -------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(slot_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// --- fences ----------------------------------------------------------------
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// --- descriptors ---------------------------------------------------------
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
+// core matrices of 8 rows x 16 bytes (128 contiguous bytes, row r at 16 r);
+// lbo = byte distance between core matrices adjacent along K,
+// sbo = byte distance between core matrices adjacent along M/N (8-row groups).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  // base offset 0, relative LBO, layout type 0 = no swizzle
+  return d;
+}
+
+// Instruction descriptor for kind::f16 / kind::tf32 with FP32 accumulation,
+// both operands K-major.  ab_fmt: 0 = F16, 1 = BF16, 2 = TF32.
+__device__ __forceinline__ uint32_t idesc(int M, int N, uint32_t ab_fmt) {
+  uint32_t d = 0;
+  d |= 1u << 4;                  // D format F32
+  d |= ab_fmt << 7;              // A format
+  d |= ab_fmt << 10;             // B format
+  d |= (uint32_t)(N >> 3) << 17; // N / 8
+  d |= (uint32_t)(M >> 4) << 24; // M / 16
+  return d;
+}
+
+// --- MMA issue (single thread) ----------------------------------------------
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          (uint32_t)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+
+// --- TMEM -> registers: lane = warp's 32-lane quarter + lane id, 16 columns -
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row r, k) in the no-swizzle K-major layout of a
+// tile with kbytes bytes per row (a multiple of 16), elem = element bytes.
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int r, int k, int kbytes, int elem) {
+  const int kb = k * elem;
+  return (uint32_t)((r >> 3) * (kbytes / 16) * 128 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
+
+}  // namespace tc
+}  // namespace tnvan

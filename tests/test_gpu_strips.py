@@ -25,6 +25,15 @@ def _model(w, n_inst=None, seed=3, scale=1.0):
     return TNVAN(w.graphs[:n], w.widths_sets[:n], w.hidden, w.betas[:n], seed=seed, init_scale=scale)
 
 
+def _param_mask(D, hidden):
+    """1 where a parameter is inside the MADE masks (biases always), flat layout."""
+    parts = []
+    for m in made.masks(D, hidden):
+        parts.append(m.numpy().reshape(-1))
+        parts.append(np.ones(m.shape[0]))
+    return np.concatenate(parts)
+
+
 def _oracle_logzr(g, W, s, beta):
     if g.n <= 16:
         return ising.log_zr_enum(g.n, g.ei, g.ej, g.J, beta, W, s)
@@ -241,3 +250,52 @@ def test_train_step_runs_and_adam_matches_oracle():
     pr, mr, vr = est.adam_step(p0, g, np.zeros_like(g), np.zeros_like(g), 1)
     pr, mr, vr = est.adam_step(pr, g, mr, vr, 2)
     assert np.abs(model.params.cpu().numpy() - pr).max() < 1e-6
+
+
+@pytest.mark.parametrize("cfg,batch,prec", [(1, 300, tv.TF32), (2, 200, tv.TF32), (2, 200, tv.BF16),
+                                            (3, 130, tv.TF32), (3, 130, tv.BF16)])
+def test_tensor_core_backward_matches_oracle(cfg, batch, prec):
+    """TF32 / BF16 tcgen05 backward vs the FP64 oracle gradient on the same samples.
+    Reduced-precision operands: the error bound is relative to the largest
+    gradient entry, and the direction must agree (cosine similarity)."""
+    from oracle import dense
+
+    w = wl.workload(cfg)
+    model = _model(w, scale=1.5)
+    s_all, lq_all, lz_all, ref = [], [], [], []
+    for k in range(model.n):
+        g, W, D, beta = w.graphs[k], w.widths_sets[k], model.D[k], w.betas[k]
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        th = torch.as_tensor(p32, dtype=torch.float64)
+        s_or, _, _ = oracle_samples(p32, D, w.hidden, 7, 1, k, batch)
+        lq = made.log_q(th, D, w.hidden, s_or).float().double()
+        if g.topology == wl.DENSE:
+            lz = dense.log_zr_dense(g.n, g.ei, g.ej, g.J, beta, W, s_or)
+        else:
+            lz = _oracle_logzr(g, W, s_or, beta)
+        wts = est.reinforce_weights(lz, lq, beta)
+        ref.append(est.surrogate_grad(p32.astype(np.float64), D, w.hidden, s_or, wts))
+        s_all.append(s_or.numpy().reshape(-1))
+        lq_all.append(lq.numpy())
+        lz_all.append(lz.detach().numpy())
+    d_spins = to_dev_spins(np.concatenate(s_all))
+    logq = torch.as_tensor(np.concatenate(lq_all), dtype=torch.float32).cuda()
+    logZR = torch.as_tensor(np.concatenate(lz_all)).cuda()
+    grad = torch.full_like(model.params, float("nan"))
+    model.ctx.backward(model.betas, batch, d_spins, logZR, logq, prec, grad)
+    torch.cuda.synchronize()
+    # reduced-precision operands: near-zero ReLU pre-activations can flip their
+    # mask, so the bound is on the relative Frobenius error and the direction
+    fro_max = 3e-2 if prec == tv.TF32 else 1e-1
+    cos_min = 0.999 if prec == tv.TF32 else 0.99
+    for k in range(model.n):
+        gk = grad[model.offsets[k]:model.offsets[k + 1]].cpu().double()
+        assert torch.isfinite(gk).all()
+        fro = float((gk - ref[k]).norm() / ref[k].norm())
+        cos = float(torch.nn.functional.cosine_similarity(gk, ref[k], dim=0))
+        print(f"cfg{cfg} inst{k} prec{prec}: rel Frobenius err = {fro:.2e}, cos = {cos:.6f}")
+        assert fro <= fro_max
+        assert cos >= cos_min
+        # entries outside the MADE masks are exactly zero
+        off = torch.as_tensor(_param_mask(model.D[k], w.hidden) == 0)
+        assert torch.equal(gk[off], torch.zeros_like(gk[off]))
