@@ -203,6 +203,31 @@ int tnvan_profile(tnvan_ctx* ctx, int enable);
 int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, double* total_ms,
                        int64_t* launches);
 
+/* Allocation-free free-energy reduction.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory at all
+ * (an external memory manager that owns every byte, a plugin that must not
+ * grow the device footprint, a launch path on which cudaMalloc's implicit
+ * synchronisation is not acceptable).  It needs no context and allocates
+ * nothing: it computes, for n_inst instances of `batch` samples each (layout
+ * of tnvan_free_energy), on `stream`, asynchronously,
+ *   d_out[5k+0..4] = F_q, F_IS, stderr, logZ_IS, number of non-finite l_b
+ * (non-finite l_b are left out of the sums instead of failing the call).
+ *   betas    host double [n_inst], finite and > 0 (read during the call).
+ *   d_logZR  device double [n_inst*batch]; d_logq device float [n_inst*batch].
+ *   d_out    device double [5*n_inst].
+ * Its scratch is a fixed 104 KB array in this library's device image, held by
+ * every GPU that loads the library until the process exits; hence the limit
+ * n_inst <= 128 (larger counts fail with TNVAN_E_ARG).  All calls on a device
+ * share that array: calls whose work may overlap on the GPU (different
+ * streams, or different host threads) race and give wrong results; calls on
+ * one stream are ordered and safe.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Errors:
+ * TNVAN_E_ARG, TNVAN_E_CUDA; message from tnvan_noalloc_last_error(). */
+int tnvan_free_energy_noalloc(int n_inst, int batch, const double* betas, const double* d_logZR,
+                              const float* d_logq, double* d_out, void* stream);
+const char* tnvan_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

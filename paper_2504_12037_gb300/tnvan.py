@@ -43,6 +43,8 @@ SIGNATURES = {
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
     "tnvan_backward": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
     "tnvan_adam": (_c_int, [_vp, _c_i64, _vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
+    "tnvan_free_energy_noalloc": (_c_int, [_c_int, _c_int, _dblp, _vp, _vp, _vp, _vp]),
+    "tnvan_noalloc_last_error": (ctypes.c_char_p, []),
     "tnvan_profile": (_c_int, [_vp, _c_int]),
     "tnvan_profile_read": (_c_int, [_vp, _c_int, ctypes.c_char_p, _c_int, _dblp, _i64p]),
 }
