@@ -839,6 +839,9 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     off += (long long)L.nout * L.nin + L.nout;
   }
   md.n_params = off;
+  md.fused_ok = n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
+                H[0] <= 128 && H[1] <= 128 && 128 + (D + 16) + (H[0] + 16) + (H[1] + 16) <= 512 &&
+                fused_bwd_smem_bytes(D, H[0], H[1]) <= 227 * 1024;
   md.c1 = dbuf + o_c1;
   md.c2 = dbuf + o_c2;
   md.raw = d_params;
@@ -1150,7 +1153,34 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     PROF("reduce", s);
     CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
   }
-  if (precision != TNVAN_FP32) {
+  bool all_fused = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
+  if (all_fused) {
+    // one CTA per chunk of 128-sample tiles, about one CTA per SM overall
+    const int n_inst = (int)ctx->inst.size();
+    const int tiles = (batch + 127) / 128;
+    const int ctas = std::max(1, std::min(tiles, (148 + n_inst - 1) / n_inst));
+    const int per = (tiles + ctas - 1) / ctas;
+    LaunchInfo lf;
+    if ((rc = fill_launch(ctx, betas, batch, per, lf))) return rc;
+    for (int k = 0; k <= lf.n_inst; ++k) lf.tile_begin[k] = k * ((tiles + per - 1) / per);
+    lf.tile = per;
+    if ((rc = ensure_grad_ws(ctx, (size_t)lf.tile_begin[lf.n_inst] * (size_t)max_elems))) return rc;
+    int smem = 0;
+    for (const Instance& in : ctx->inst)
+      smem = std::max(smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
+    {
+      PROF("bwd_fused", s);
+      CK(launch_bwd_fused(ctx->d_inst, lf, smem, d_spins, d_logZR, d_logq, ctx->d_stats, ctx->d_grad_packed,
+                          max_elems, ctx->d_status, s),
+         "fused backward kernel");
+    }
+    {
+      PROF("grad_reduce", s);
+      CK(launch_grad_reduce(ctx->d_inst, lf, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+         "gradient reduce kernel");
+    }
+  } else if (precision != TNVAN_FP32) {
     const int splits = std::max(1, std::min(TC_SPLITS, (batch + 127) / 128));
     if ((rc = ensure_grad_ws(ctx, (size_t)splits * ctx->inst.size() * (size_t)max_elems))) return rc;
     if ((rc = backward_tc(ctx, betas, batch, d_spins, d_logZR, d_logq, precision == TNVAN_BF16,

@@ -53,6 +53,7 @@ struct MadeDev {
   float* blocks;          // blocked weights (gathered from `packed` every call)
   const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
   long long n_blk;
+  int fused_ok;           // eligible for the fused BF16 tcgen05 backward
   long long n_params;     // size of the natural layout
   long long param_off;    // offset in the all-instances packed gradient layout
 };
@@ -238,6 +239,11 @@ cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                cudaStream_t s);
 cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
                                const double* stats, float* w, cudaStream_t s);
+cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                             const int8_t* spins, const double* logZR, const float* logq,
+                             const double* stats, float* partials, long long part_stride, int* status,
+                             cudaStream_t s);
+int fused_bwd_smem_bytes(int D, int H1, int H2);
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 

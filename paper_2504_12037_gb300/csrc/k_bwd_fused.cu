@@ -1,0 +1,331 @@
+// Fused BF16 backward of the MADE network on tcgen05 (Eq. 10), for networks
+// with two hidden layers of at most 128 units and at most 128 inputs.
+//
+// One CTA (128 threads, thread = sample = TMEM lane) walks the 128-sample
+// tiles of its chunk.  Per tile, everything stays on chip:
+//   A1 = relu(S W1^T + b1), A2 = relu(A1 W2^T + b2), X = A2 Wo^T + bo,
+//   dX = w_b s sigmoid(-s x), dA2 = (dX Wo) 1[A2 > 0], dA1 = (dA2 W2) 1[A1 > 0],
+// each product one chain of tcgen05.mma into a TMEM scratch accumulator whose
+// epilogue (tcgen05.ld, one row per thread) writes the next BF16 operand tile
+// into shared memory.  The weight gradients
+//   GWo += dX^T [A2 | 1],  GW2 += dA2^T [A1 | 1],  GW1 += dA1^T [S | 1]
+// reuse the same tiles read transposed (MN-major descriptors) and accumulate
+// in TMEM across all tiles of the chunk; the column of ones yields the bias
+// gradients.  At the end each CTA writes its partial gradient slice (packed,
+// degree-sorted layout) for the deterministic chunk reduction.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace tnvan {
+
+namespace {
+
+// Row-major-in-K tile geometry: rows of `kel` bf16 (a multiple of 16).
+struct Tile {
+  uint32_t base;  // shared address
+  int kel;        // elements per row
+  __device__ uint32_t rowbytes() const { return (uint32_t)kel * 2u; }
+  // K-major operand descriptor for MMA k-step kk (16 elements of K)
+  __device__ uint64_t kdesc(int kk) const {
+    return tc::smem_desc(base + (uint32_t)kk * 256u, 128u, rowbytes() / 16u * 128u);
+  }
+  // MN-major view (MN = the row's elements, K = the rows), k-step kk covers rows 16kk..16kk+15
+  __device__ uint64_t mndesc(int kk) const {
+    const uint32_t kstride = rowbytes() * 8u;  // 8 rows
+    return tc::smem_desc(base + (uint32_t)kk * 2u * kstride, kstride, 128u);
+  }
+};
+
+__device__ __forceinline__ void store8(unsigned char* sm_base, uint32_t rowbytes, int r, int c,
+                                       const float* v) {
+  // 8 consecutive elements (c multiple of 8) of row r, canonical K-major layout
+  const uint32_t o = (uint32_t)(r >> 3) * (rowbytes / 16u) * 128u + (uint32_t)(c >> 3) * 128u + (uint32_t)(r & 7) * 16u;
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+  uint4 u;
+  u.x = *reinterpret_cast<uint32_t*>(&p0);
+  u.y = *reinterpret_cast<uint32_t*>(&p1);
+  u.z = *reinterpret_cast<uint32_t*>(&p2);
+  u.w = *reinterpret_cast<uint32_t*>(&p3);
+  *reinterpret_cast<uint4*>(sm_base + o) = u;
+}
+
+__device__ __forceinline__ float load1(const unsigned char* sm_base, uint32_t rowbytes, int r, int c) {
+  const uint32_t o = (uint32_t)(r >> 3) * (rowbytes / 16u) * 128u + (uint32_t)(c >> 3) * 128u +
+                     (uint32_t)(r & 7) * 16u + (uint32_t)(c & 7) * 2u;
+  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sm_base + o));
+}
+
+}  // namespace
+
+struct FusedBwdArgs {
+  const int8_t* spins;
+  const double* logZR;
+  const float* logq;
+  const double* stats;
+  float* partials;
+  long long part_stride;
+  int* status;
+};
+
+// Shared memory bytes for (D, H1, H2).
+__host__ __device__ inline int fused_bwd_smem(int D, int H1, int H2) {
+  const int w = H1 * D + H2 * H1 + D * H2;                        // weights
+  const int a = 128 * ((D + 16) + (H1 + 16) + (H2 + 16) + D + H2);  // S, A1, A2/dA1, dX, dA2
+  return 2 * (w + a) + 64;
+}
+
+__global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
+                                                           const LaunchInfo li, FusedBwdArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  const MadeDev& md = I.made;
+  if (!md.fused_ok) return;
+  const int D = md.D, H1 = md.H1, H2 = md.H2;
+  const int t = threadIdx.x, w = t >> 5;
+  const int B = li.batch;
+  const int tiles_total = (B + 127) / 128;
+  const int c_idx = blockIdx.x - li.tile_begin[k];
+  const int per = li.tile;  // tiles per CTA
+  const int tile0 = c_idx * per, tile1 = min(tiles_total, tile0 + per);
+  // ---- shared memory carve ----
+  unsigned char* p = smem;
+  unsigned char* sW1 = p; p += H1 * D * 2;
+  unsigned char* sW2 = p; p += H2 * H1 * 2;
+  unsigned char* sWo = p; p += D * H2 * 2;
+  unsigned char* sS = p; p += 128 * (D + 16) * 2;
+  unsigned char* sA1 = p; p += 128 * (H1 + 16) * 2;
+  unsigned char* sA2 = p; p += 128 * (H2 + 16) * 2;  // later dA1 (128 x H1)
+  unsigned char* sdX = p; p += 128 * D * 2;           // must precede sdA2 (MN view overruns into it)
+  unsigned char* sdA2 = p; p += 128 * H2 * 2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(p);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const Tile tW1{smem_u32(sW1), D}, tW2{smem_u32(sW2), H1}, tWo{smem_u32(sWo), H2};
+  const Tile tS{smem_u32(sS), D + 16}, tA1{smem_u32(sA1), H1 + 16}, tA2{smem_u32(sA2), H2 + 16};
+  const Tile tdX{smem_u32(sdX), D}, tdA2{smem_u32(sdA2), H2}, tdA1{smem_u32(sA2), H1};
+  // ---- weights: packed FP32 (masked, degree-sorted) -> BF16 K-major tiles ----
+  const float* W1 = md.packed + md.layer[0].dst_off;
+  const float* b1 = W1 + (long long)H1 * D;
+  const float* W2 = md.packed + md.layer[1].dst_off;
+  const float* b2 = W2 + (long long)H2 * H1;
+  const float* Wo = md.packed + md.layer[2].dst_off;
+  const float* bo = Wo + (long long)D * H2;
+  auto load_w = [&](unsigned char* dst, const float* src, int rows, int cols) {
+    for (int e = t; e < rows * cols / 8; e += 128) {
+      const int r = e / (cols / 8), c = (e % (cols / 8)) * 8;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = src[(long long)r * cols + c + i];
+      store8(dst, (uint32_t)cols * 2u, r, c, v);
+    }
+  };
+  load_w(sW1, W1, H1, D);
+  load_w(sW2, W2, H2, H1);
+  load_w(sWo, Wo, D, H2);
+  if (t == 0) mbar_init(bar, 1);
+  if (w == 0) {
+    tc::tmem_alloc(slot, 512);
+    tc::tmem_relinquish();
+  }
+  fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *slot;
+  const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)(D + 16), tGo = tG2 + (uint32_t)(H1 + 16);
+  const uint32_t lane_off = (uint32_t)(w * 32) << 16;
+  const uint32_t id_fwd1 = tc::idesc(128, H1, 1u), id_fwd2 = tc::idesc(128, H2, 1u), id_fwd3 = tc::idesc(128, D, 1u);
+  const uint32_t id_d2 = tc::idesc(128, H2, 1u) | (1u << 16);         // B MN-major
+  const uint32_t id_d1 = tc::idesc(128, H1, 1u) | (1u << 16);
+  const uint32_t id_go = tc::idesc(128, H2 + 16, 1u) | (1u << 15) | (1u << 16);  // A, B MN-major
+  const uint32_t id_g2 = tc::idesc(128, H1 + 16, 1u) | (1u << 15) | (1u << 16);
+  const uint32_t id_g1 = tc::idesc(128, D + 16, 1u) | (1u << 15) | (1u << 16);
+  const double mean = args.stats[8 * k + 4];
+  const double wsc = -1.0 / (li.beta[k] * (double)B);
+  const int8_t* Sg = args.spins + I.spin_units * (long long)B;
+  uint32_t phase = 0;
+  bool ok = true;
+  auto mma_wait = [&]() -> bool {
+    if (t == 0) tc::mma_commit(bar);
+    const bool r = mbar_wait(bar, phase);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    return r;
+  };
+  auto sync_for_mma = [&]() {
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  bool first = true;
+  for (int tile = tile0; tile < tile1 && ok; ++tile) {
+    const int b = tile * 128 + t;
+    const bool valid = b < B;
+    const float vf = valid ? 1.f : 0.f;
+    // spins -> S tile (+ ones column)
+    float sp[8];
+    for (int c = 0; c < D + 16; c += 8) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f = c + i;
+        sp[i] = f < D ? (valid ? (float)Sg[(long long)b * D + f] : 0.f) : (f == D ? vf : 0.f);
+      }
+      store8(sS, tS.rowbytes(), t, c, sp);
+    }
+    const float wb = valid ? (float)(wsc * (args.logZR[(long long)k * B + b] - (double)args.logq[(long long)k * B + b] - mean)) : 0.f;
+    sync_for_mma();
+    // fwd1: scratch = S W1^T
+    if (t == 0)
+      for (int kk = 0; kk < D / 16; ++kk) tc::mma_bf16(tScr, tS.kdesc(kk), tW1.kdesc(kk), id_fwd1, kk > 0);
+    if (!(ok = mma_wait())) break;
+    for (int c = 0; c < H1 + 16; c += 16) {
+      float v[16];
+      if (c < H1) tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int u = c + i;
+        v[i] = u < H1 ? fmaxf(v[i] + __ldg(b1 + u), 0.f) * vf : (u == H1 ? vf : 0.f);
+      }
+      store8(sA1, tA1.rowbytes(), t, c, v);
+      store8(sA1, tA1.rowbytes(), t, c + 8, v + 8);
+    }
+    sync_for_mma();
+    // fwd2: scratch = A1 W2^T
+    if (t == 0)
+      for (int kk = 0; kk < H1 / 16; ++kk) tc::mma_bf16(tScr, tA1.kdesc(kk), tW2.kdesc(kk), id_fwd2, kk > 0);
+    if (!(ok = mma_wait())) break;
+    for (int c = 0; c < H2 + 16; c += 16) {
+      float v[16];
+      if (c < H2) tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int u = c + i;
+        v[i] = u < H2 ? fmaxf(v[i] + __ldg(b2 + u), 0.f) * vf : (u == H2 ? vf : 0.f);
+      }
+      store8(sA2, tA2.rowbytes(), t, c, v);
+      store8(sA2, tA2.rowbytes(), t, c + 8, v + 8);
+    }
+    sync_for_mma();
+    // fwd3: scratch = A2 Wo^T ; epilogue dX
+    if (t == 0)
+      for (int kk = 0; kk < H2 / 16; ++kk) tc::mma_bf16(tScr, tA2.kdesc(kk), tWo.kdesc(kk), id_fwd3, kk > 0);
+    if (!(ok = mma_wait())) break;
+    for (int c = 0; c < D; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int f = c + i;
+        const float x = v[i] + __ldg(bo + f);
+        const float s = load1(sS, tS.rowbytes(), t, f);
+        v[i] = wb * s / (1.f + expf(s * x));
+      }
+      store8(sdX, tdX.rowbytes(), t, c, v);
+      store8(sdX, tdX.rowbytes(), t, c + 8, v + 8);
+    }
+    sync_for_mma();
+    // scratch = dX Wo (B = Wo read MN-major);  GWo += dX^T [A2 | 1]
+    if (t == 0) {
+      for (int kk = 0; kk < D / 16; ++kk) tc::mma_bf16(tScr, tdX.kdesc(kk), tWo.mndesc(kk), id_d2, kk > 0);
+      for (int kk = 0; kk < 8; ++kk)
+        tc::mma_bf16(tGo, tdX.mndesc(kk), tA2.mndesc(kk), id_go, (!first || kk > 0) ? 1u : 0u);
+    }
+    if (!(ok = mma_wait())) break;
+    for (int c = 0; c < H2; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = load1(sA2, tA2.rowbytes(), t, c + i) > 0.f ? v[i] : 0.f;
+      store8(sdA2, tdA2.rowbytes(), t, c, v);
+      store8(sdA2, tdA2.rowbytes(), t, c + 8, v + 8);
+    }
+    sync_for_mma();
+    // scratch = dA2 W2 (B = W2 read MN-major);  GW2 += dA2^T [A1 | 1]
+    if (t == 0) {
+      for (int kk = 0; kk < H2 / 16; ++kk) tc::mma_bf16(tScr, tdA2.kdesc(kk), tW2.mndesc(kk), id_d1, kk > 0);
+      for (int kk = 0; kk < 8; ++kk)
+        tc::mma_bf16(tG2, tdA2.mndesc(kk), tA1.mndesc(kk), id_g2, (!first || kk > 0) ? 1u : 0u);
+    }
+    if (!(ok = mma_wait())) break;
+    for (int c = 0; c < H1; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = load1(sA1, tA1.rowbytes(), t, c + i) > 0.f ? v[i] : 0.f;
+      // dA1 overwrites A2 (GWo and the dA2 mask have consumed it)
+      store8(sA2, tdA1.rowbytes(), t, c, v);
+      store8(sA2, tdA1.rowbytes(), t, c + 8, v + 8);
+    }
+    sync_for_mma();
+    // GW1 += dA1^T [S | 1]
+    if (t == 0)
+      for (int kk = 0; kk < 8; ++kk)
+        tc::mma_bf16(tG1, tdA1.mndesc(kk), tS.mndesc(kk), id_g1, (!first || kk > 0) ? 1u : 0u);
+    if (!(ok = mma_wait())) break;
+    first = false;
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (!ok && t == 0) atomicExch(args.status, 3);
+  // ---- flush the gradient partials of this CTA ----
+  float* G = args.partials + (long long)blockIdx.x * args.part_stride;
+  if (ok && !first) {
+    // GW1 rows u (lane t < H1): [D weights | bias]
+    for (int c = 0; c < D + 16; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tG1 + lane_off + (uint32_t)c, v);
+      if (t < H1)
+        for (int i = 0; i < 16; ++i) {
+          const int j = c + i;
+          if (j < D) G[md.layer[0].dst_off + (long long)t * D + j] = v[i];
+          else if (j == D) G[md.layer[0].dst_off + (long long)H1 * D + t] = v[i];
+        }
+    }
+    for (int c = 0; c < H1 + 16; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tG2 + lane_off + (uint32_t)c, v);
+      if (t < H2)
+        for (int i = 0; i < 16; ++i) {
+          const int u = c + i;
+          if (u < H1) G[md.layer[1].dst_off + (long long)t * H1 + u] = v[i];
+          else if (u == H1) G[md.layer[1].dst_off + (long long)H2 * H1 + t] = v[i];
+        }
+    }
+    for (int c = 0; c < H2 + 16; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tGo + lane_off + (uint32_t)c, v);
+      if (t < D)
+        for (int i = 0; i < 16; ++i) {
+          const int u = c + i;
+          if (u < H2) G[md.layer[2].dst_off + (long long)t * H2 + u] = v[i];
+          else if (u == H2) G[md.layer[2].dst_off + (long long)D * H2 + t] = v[i];
+        }
+    }
+  } else {
+    for (long long e = t; e < md.n_params; e += 128) G[e] = 0.f;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+                             const int8_t* spins, const double* logZR, const float* logq,
+                             const double* stats, float* partials, long long part_stride, int* status,
+                             cudaStream_t s) {
+  const int nblk = li.tile_begin[li.n_inst];
+  if (nblk == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(bwd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  FusedBwdArgs a{spins, logZR, logq, stats, partials, part_stride, status};
+  bwd_fused_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, li, a);
+  return cudaGetLastError();
+}
+
+int fused_bwd_smem_bytes(int D, int H1, int H2) { return fused_bwd_smem(D, H1, H2); }
+
+}  // namespace tnvan

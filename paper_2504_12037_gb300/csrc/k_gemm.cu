@@ -33,31 +33,148 @@ __device__ __forceinline__ float load_any(int type, const void* p, long long idx
                         : (float)static_cast<const int8_t*>(p)[idx];
 }
 
+// Store 4 consecutive-k values of row r (k multiple of 4) into the K-major stage.
+template <bool BF16>
+__device__ __forceinline__ void st4k(unsigned char* s, int r, int k, float4 v) {
+  constexpr int EL = BF16 ? 2 : 4;
+  const uint32_t o = tc::kmajor_off(r, k, GK * EL, EL);
+  if (BF16) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(s + o) = u;
+  } else {
+    *reinterpret_cast<float4*>(s + o) = v;
+  }
+}
+
+template <bool BF16>
+__device__ __forceinline__ void st1(unsigned char* s, int r, int k, float v) {
+  constexpr int EL = BF16 ? 2 : 4;
+  const uint32_t o = tc::kmajor_off(r, k, GK * EL, EL);
+  if (BF16) *reinterpret_cast<__nv_bfloat16*>(s + o) = __float2bfloat16(v);
+  else *reinterpret_cast<float*>(s + o) = v;
+}
+
 // Fill one K stage: rows [r0, r0 + nrows) of an operand, k in [k0, k0 + GK).
 // Rows >= rlim or k >= klim are zero; row == ones_row reads 1 (bias column).
+// Loads are issued in batches (registers first, stores after) so that each
+// thread keeps many global loads in flight; FP32 operands whose contiguous
+// index is k (or the row) are read as float4.
 template <bool BF16>
 __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
                                            int r0, int rlim, int k0, int klim, int ones_row, int t) {
-  constexpr int EL = BF16 ? 2 : 4;
-  constexpr int KB = GK * EL;  // bytes of K per row in the stage
-  const bool kfast = op.sk == 1;  // coalesce along k when k is the contiguous index
-  const int total = nrows * GK;
-  for (int e = t; e < total; e += 128) {
-    int r, k;
-    if (kfast) {
-      r = e / GK;
-      k = e % GK;
-    } else {
-      r = e % nrows;
-      k = e / nrows;
+  const bool full_k = k0 + GK <= klim;
+  const bool f32 = op.type == GT_F32;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(op.ptr) & 15) == 0);
+  if (f32 && aligned && full_k && op.sk == 1 && (op.sr & 3) == 0) {
+    // row-major along k: units of (row, 4 k)
+    const float* p = static_cast<const float*>(op.ptr);
+    const int units = nrows * (GK / 4);
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      float4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        const int r = u >> 3, kq = (u & 7) * 4;
+        const int gr = r0 + r;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u < units) {
+          if (gr == ones_row) v[j] = make_float4(1.f, 1.f, 1.f, 1.f);
+          else if (gr < rlim)
+            v[j] = __ldg(reinterpret_cast<const float4*>(p + (long long)gr * op.sr + k0 + kq));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        if (u < units) st4k<BF16>(s, u >> 3, (u & 7) * 4, v[j]);
+      }
     }
-    const int gr = r0 + r, gk = k0 + k;
-    float v = 0.f;
-    if (gr == ones_row) v = gk < klim ? 1.f : 0.f;
-    else if (gr < rlim && gk < klim) v = load_any(op.type, op.ptr, (long long)gr * op.sr + (long long)gk * op.sk);
-    const uint32_t o = tc::kmajor_off(r, k, KB, EL);
-    if (BF16) *reinterpret_cast<__nv_bfloat16*>(s + o) = __float2bfloat16(v);
-    else *reinterpret_cast<float*>(s + o) = v;
+    return;
+  }
+  if (f32 && aligned && op.sr == 1 && (op.sk & 3) == 0 && (r0 & 3) == 0 && (nrows & 3) == 0) {
+    // contiguous along rows (transposed operand): units of (4 rows, k)
+    const float* p = static_cast<const float*>(op.ptr);
+    const int rq = nrows / 4;
+    const int units = rq * GK;
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      float4 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        const int r = (u % rq) * 4, k = u / rq;
+        const int gr = r0 + r, gk = k0 + k;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u < units && gk < klim) {
+          if (gr + 3 < rlim) v[j] = __ldg(reinterpret_cast<const float4*>(p + (long long)gk * op.sk + gr));
+          else {
+            float e[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i = 0; i < 4; ++i)
+              if (gr + i < rlim) e[i] = p[(long long)gk * op.sk + gr + i];
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+          }
+          if (ones_row >= gr && ones_row < gr + 4) {
+            float* f = reinterpret_cast<float*>(&v[j]);
+            f[ones_row - gr] = 1.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        if (u < units) {
+          const int r = (u % rq) * 4, k = u / rq;
+          st1<BF16>(s, r, k, v[j].x);
+          st1<BF16>(s, r + 1, k, v[j].y);
+          st1<BF16>(s, r + 2, k, v[j].z);
+          st1<BF16>(s, r + 3, k, v[j].w);
+        }
+      }
+    }
+    return;
+  }
+  // generic: element by element, loads batched 16 at a time
+  const bool kfast = op.sk == 1;
+  const int total = nrows * GK;
+  for (int e0 = 0; e0 < total; e0 += 128 * 16) {
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int e = e0 + t + 128 * j;
+      int r, k;
+      if (kfast) {
+        r = e / GK;
+        k = e % GK;
+      } else {
+        r = e % nrows;
+        k = e / nrows;
+      }
+      const int gr = r0 + r, gk = k0 + k;
+      float x = 0.f;
+      if (e < total) {
+        if (gr == ones_row) x = gk < klim ? 1.f : 0.f;
+        else if (gr < rlim && gk < klim)
+          x = load_any(op.type, op.ptr, (long long)gr * op.sr + (long long)gk * op.sk);
+      }
+      v[j] = x;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int e = e0 + t + 128 * j;
+      if (e < total) {
+        int r, k;
+        if (kfast) {
+          r = e / GK;
+          k = e % GK;
+        } else {
+          r = e % nrows;
+          k = e / nrows;
+        }
+        st1<BF16>(s, r, k, v[j]);
+      }
+    }
   }
 }
 
@@ -77,7 +194,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (stageA + stageB));
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
   // split K
-  const int kchunk = (P.K + gridDim.z - 1) / gridDim.z;
+  const int kchunk = (((P.K + gridDim.z - 1) / gridDim.z) + GK - 1) / GK * GK;
   const int kbeg = blockIdx.z * kchunk, kend = min(P.K, kbeg + kchunk);
   if (t == 0) {
     mbar_init(&bar[0], 1);
