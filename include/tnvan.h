@@ -132,7 +132,10 @@ int tnvan_reserve(tnvan_ctx* ctx, int max_batch);
  * (Eq. 3-4).
  *   betas     host [n_instances] inverse temperatures.
  *   batch     samples per instance (>= 0).
- *   precision TNVAN_FP32 | TNVAN_TF32 | TNVAN_BF16 (dense blocks and GEMMs).
+ *   precision TNVAN_FP32 | TNVAN_TF32 | TNVAN_BF16.  With TNVAN_BF16 the
+ *             network runs on the tensor cores in BF16 (FP32 accumulate) when
+ *             every instance has two hidden layers of <= 128 units and D <= 128
+ *             (multiples of 16); the contractions stay FP32.
  *   d_spins   device int8 out, layout above.   d_logq  device float out.
  *   d_logZR   device double out.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE (an instance lacks network or width set),
@@ -143,10 +146,11 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
 
 /* Eq. 6 and 8 alone: log q_theta(s) for caller-given width-set
  * configurations d_spins (device int8 +-1, layout above), by the same
- * masked forward the sampler runs (teacher forcing).  d_logq: device float
- * [n_inst * batch] out.  Asynchronous.
+ * masked forward the sampler of that precision runs (teacher forcing).
+ * d_logq: device float [n_inst * batch] out.  Asynchronous.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no network), TNVAN_E_CUDA. */
-int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, float* d_logq, void* stream);
+int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precision, float* d_logq,
+                   void* stream);
 
 /* Eq. 3-4 alone: log Z_R(s) for caller-given width-set configurations
  * d_spins (device int8, layout above) of every instance.  Optional

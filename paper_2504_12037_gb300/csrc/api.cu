@@ -397,6 +397,9 @@ int pick_sample_tile(const tnvan_ctx* ctx) {
 
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s);
+int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s);
+int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
+                int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s);
 
 }  // namespace
 
@@ -842,6 +845,17 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   md.fused_ok = n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
                 H[0] <= 128 && H[1] <= 128 && 128 + (D + 16) + (H[0] + 16) + (H[1] + 16) <= 512 &&
                 fused_bwd_smem_bytes(D, H[0], H[1]) <= 227 * 1024;
+  md.sample_tc_ok = 0;  // decided once the step groups are known
+  md.wtiles = nullptr;
+  if (md.fused_ok || (n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
+                      H[0] <= 128 && H[1] <= 128)) {
+    void* wt = nullptr;
+    const size_t n = (size_t)H[0] * D + (size_t)H[1] * H[0] + (size_t)D * H[1];
+    cudaError_t e2 = cudaMalloc(&wt, n * sizeof(uint16_t));
+    if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(weight tiles): %s", cudaGetErrorString(e2));
+    in.dev_allocs.push_back(wt);
+    md.wtiles = static_cast<uint16_t*>(wt);
+  }
   md.c1 = dbuf + o_c1;
   md.c2 = dbuf + o_c2;
   md.raw = d_params;
@@ -921,6 +935,8 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     }
     md.n_groups = (int)grp.size() / GROUP_INTS;
     md.wmax = wmax;
+    md.sample_tc_ok = md.wtiles != nullptr && ug1 <= 32 && ug2 <= 32 && ugo <= 16 &&
+                      sample_tc_smem_bytes(D, H[0], H[1], wmax) <= 227 * 1024;
     md.groups = dgrp;
     md.ug1 = ug1;
     md.ug2 = ug2;
@@ -1039,20 +1055,14 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
     PROF("pack", s);
     CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
   }
-  const int tile = pick_sample_tile(ctx);
-  LaunchInfo li;
-  if ((rc = fill_launch(ctx, betas, batch, tile, li))) return rc;
-  li.seed = seed;
-  li.step = step;
-  {
-    PROF("sample", s);
-    CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), d_spins, d_logq, nullptr, s), "sample kernel");
-  }
+  if ((rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s))) return rc;
   return contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
 }
 
-int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, float* d_logq, void* stream) {
+int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precision, float* d_logq,
+                   void* stream) {
   if (!ctx) return TNVAN_E_ARG;
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
   if (batch < 0) return fail(ctx, TNVAN_E_ARG, "batch < 0");
   if (batch > 0 && (!d_spins || !d_logq)) return fail(ctx, TNVAN_E_ARG, "NULL spins or output");
   DeviceGuard g(ctx->device);
@@ -1066,12 +1076,8 @@ int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, float* d_lo
     max_blk = std::max(max_blk, in.dev.made.n_blk);
   }
   CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
-  const int tile = pick_sample_tile(ctx);
-  LaunchInfo li;
   std::vector<double> ones(ctx->inst.size(), 1.0);
-  if ((rc = fill_launch(ctx, ones.data(), batch, tile, li))) return rc;
-  CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), nullptr, d_logq, d_spins, s), "log-prob kernel");
-  return TNVAN_OK;
+  return run_sampler(ctx, ones.data(), batch, 0, 0, precision, nullptr, d_logq, d_spins, s);
 }
 
 int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
@@ -1166,6 +1172,7 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     for (int k = 0; k <= lf.n_inst; ++k) lf.tile_begin[k] = k * ((tiles + per - 1) / per);
     lf.tile = per;
     if ((rc = ensure_grad_ws(ctx, (size_t)lf.tile_begin[lf.n_inst] * (size_t)max_elems))) return rc;
+    if ((rc = pack_weight_tiles(ctx, s))) return rc;
     int smem = 0;
     for (const Instance& in : ctx->inst)
       smem = std::max(smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
@@ -1311,6 +1318,45 @@ int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, doub
 }  // extern "C"
 
 namespace {
+
+int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s) {
+  long long mx = 0;
+  for (const Instance& in : ctx->inst) {
+    const MadeDev& md = in.dev.made;
+    if (md.wtiles) mx = std::max(mx, (long long)md.H1 * md.D + (long long)md.H2 * md.H1 + (long long)md.D * md.H2);
+  }
+  PROF("pack_tiles", s);
+  CK(launch_pack_tiles(ctx->d_inst, (int)ctx->inst.size(), mx, s), "weight tile kernel");
+  return TNVAN_OK;
+}
+
+int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
+                int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s) {
+  int rc;
+  bool tc_all = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
+  if (tc_all) {
+    if ((rc = pack_weight_tiles(ctx, s))) return rc;
+    LaunchInfo li;
+    if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
+    li.seed = seed;
+    li.step = step;
+    int smem = 0;
+    for (const Instance& in : ctx->inst)
+      smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], in.dev.made.wmax));
+    PROF(given ? "log_prob_tc" : "sample_tc", s);
+    CK(launch_sample_tc(ctx->d_inst, li, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
+    return TNVAN_OK;
+  }
+  const int tile = pick_sample_tile(ctx);
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, tile, li))) return rc;
+  li.seed = seed;
+  li.step = step;
+  PROF(given ? "log_prob" : "sample", s);
+  CK(launch_sample(ctx->d_inst, li, max_sample_smem(ctx, tile), d_spins, d_logq, given, s), "sample kernel");
+  return TNVAN_OK;
+}
 
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s) {

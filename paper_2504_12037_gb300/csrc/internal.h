@@ -54,6 +54,8 @@ struct MadeDev {
   const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
   long long n_blk;
   int fused_ok;           // eligible for the fused BF16 tcgen05 backward
+  int sample_tc_ok;       // eligible for the BF16 tcgen05 sampler
+  uint16_t* wtiles;       // BF16 K-major tiles W1 [H1 x D] | W2 [H2 x H1] | Wo [D x H2] (fused kernels)
   long long n_params;     // size of the natural layout
   long long param_off;    // offset in the all-instances packed gradient layout
 };
@@ -214,6 +216,7 @@ namespace tnvan {
 // Kernel launchers (defined in the .cu files).  All return a cudaError_t.
 cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, long long max_blk,
                         cudaStream_t s);
+cudaError_t launch_pack_tiles(const InstDev* d_inst, int n_inst, long long max_tile_elems, cudaStream_t s);
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);
 cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
@@ -244,6 +247,9 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
                              const double* stats, float* partials, long long part_stride, int* status,
                              cudaStream_t s);
 int fused_bwd_smem_bytes(int D, int H1, int H2);
+cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int8_t* spins,
+                             float* logq, const int8_t* given, cudaStream_t s);
+int sample_tc_smem_bytes(int D, int H1, int H2, int wmax);
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 

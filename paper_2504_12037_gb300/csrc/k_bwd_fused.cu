@@ -74,7 +74,7 @@ struct FusedBwdArgs {
 __host__ __device__ inline int fused_bwd_smem(int D, int H1, int H2) {
   const int w = H1 * D + H2 * H1 + D * H2;                        // weights
   const int a = 128 * ((D + 16) + (H1 + 16) + (H2 + 16) + D + H2);  // S, A1, A2/dA1, dX, dA2
-  return 2 * (w + a) + 64;
+  return 2 * (w + a) + 64;  // + barriers and the TMEM slot
 }
 
 __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   unsigned char* sdX = p; p += 128 * D * 2;           // must precede sdA2 (MN view overruns into it)
   unsigned char* sdA2 = p; p += 128 * H2 * 2;
   uint64_t* bar = reinterpret_cast<uint64_t*>(p);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);  // cbar is bar + 2
   const Tile tW1{smem_u32(sW1), D}, tW2{smem_u32(sW2), H1}, tWo{smem_u32(sWo), H2};
   const Tile tS{smem_u32(sS), D + 16}, tA1{smem_u32(sA1), H1 + 16}, tA2{smem_u32(sA2), H2 + 16};
   const Tile tdX{smem_u32(sdX), D}, tdA2{smem_u32(sdA2), H2}, tdA1{smem_u32(sA2), H1};
@@ -113,27 +113,26 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   const float* b2 = W2 + (long long)H2 * H1;
   const float* Wo = md.packed + md.layer[2].dst_off;
   const float* bo = Wo + (long long)D * H2;
-  auto load_w = [&](unsigned char* dst, const float* src, int rows, int cols) {
-    for (int e = t; e < rows * cols / 8; e += 128) {
-      const int r = e / (cols / 8), c = (e % (cols / 8)) * 8;
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = src[(long long)r * cols + c + i];
-      store8(dst, (uint32_t)cols * 2u, r, c, v);
-    }
-  };
-  load_w(sW1, W1, H1, D);
-  load_w(sW2, W2, H2, H1);
-  load_w(sWo, Wo, D, H2);
-  if (t == 0) mbar_init(bar, 1);
+  // BF16 weight tiles (laid out once per call in the canonical K-major form)
+  // arrive with one bulk copy; W1, W2, Wo are contiguous in both places
+  uint64_t* cbar = bar + 2;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_init(cbar, 1);
+  }
   if (w == 0) {
     tc::tmem_alloc(slot, 512);
     tc::tmem_relinquish();
   }
-  fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  if (t == 0) {
+    const uint32_t wbytes = 2u * (uint32_t)(H1 * D + H2 * H1 + D * H2);
+    mbar_expect_tx(cbar, wbytes);
+    bulk_g2s(sW1, md.wtiles, wbytes, cbar);
+  }
+  const bool weights_ok = mbar_wait(cbar, 0);
   const uint32_t tmem = *slot;
   const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)(D + 16), tGo = tG2 + (uint32_t)(H1 + 16);
   const uint32_t lane_off = (uint32_t)(w * 32) << 16;
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   const double wsc = -1.0 / (li.beta[k] * (double)B);
   const int8_t* Sg = args.spins + I.spin_units * (long long)B;
   uint32_t phase = 0;
-  bool ok = true;
+  bool ok = weights_ok;
   auto mma_wait = [&]() -> bool {
     if (t == 0) tc::mma_commit(bar);
     const bool r = mbar_wait(bar, phase);

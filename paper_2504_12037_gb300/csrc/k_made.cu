@@ -50,6 +50,48 @@ cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, 
   return cudaGetLastError();
 }
 
+// BF16 weight tiles in the tensor cores' canonical K-major layout (no
+// swizzle): W1 [H1 x D], W2 [H2 x H1], Wo [D x H2], back to back.
+__global__ void pack_tiles_kernel(const InstDev* __restrict__ inst) {
+  const MadeDev& md = inst[blockIdx.y].made;
+  if (!md.wtiles) return;
+  const int D = md.D, H1 = md.H1, H2 = md.H2;
+  const long long n1 = (long long)H1 * D, n2 = (long long)H2 * H1, no = (long long)D * H2;
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float* src;
+  int cols;
+  long long base;
+  if (e < n1) {
+    src = md.packed + md.layer[0].dst_off;
+    cols = D;
+    base = 0;
+  } else if (e < n1 + n2) {
+    e -= n1;
+    src = md.packed + md.layer[1].dst_off;
+    cols = H1;
+    base = n1;
+  } else if (e < n1 + n2 + no) {
+    e -= n1 + n2;
+    src = md.packed + md.layer[2].dst_off;
+    cols = H2;
+    base = n1 + n2;
+  } else {
+    return;
+  }
+  const int r = (int)(e / cols), c = (int)(e % cols);
+  const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
+  const float v = src[e];
+  uint32_t u = __float_as_uint(v);
+  u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+  md.wtiles[o] = (uint16_t)(u >> 16);
+}
+
+cudaError_t launch_pack_tiles(const InstDev* d_inst, int n_inst, long long max_tile_elems, cudaStream_t s) {
+  if (n_inst == 0 || max_tile_elems == 0) return cudaSuccess;
+  pack_tiles_kernel<<<dim3((unsigned)((max_tile_elems + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
+  return cudaGetLastError();
+}
+
 // Dot product of a warp-uniform weight row with this thread's activation
 // column (layout [unit][T]) over entries [j0, j1).
 __device__ __forceinline__ float dot_col(const float* __restrict__ w, const float* col, int T,

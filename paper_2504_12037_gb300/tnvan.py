@@ -38,7 +38,7 @@ SIGNATURES = {
     "tnvan_instance_info": (_c_int, [_vp, _c_int, _i32p]),
     "tnvan_reserve": (_c_int, [_vp, _c_int]),
     "tnvan_sample_and_contract": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp]),
-    "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _vp, _vp]),
+    "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp]),
     "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
     "tnvan_backward": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
@@ -159,8 +159,8 @@ class Context:
         self._check(lib().tnvan_sample_and_contract(self._h, pb, batch, seed, step, precision, _ptr(spins),
                                                     _ptr(logq), _ptr(logZR), _stream(stream)))
 
-    def log_prob(self, batch: int, spins, logq, stream=None):
-        self._check(lib().tnvan_log_prob(self._h, batch, _ptr(spins), _ptr(logq), _stream(stream)))
+    def log_prob(self, batch: int, spins, logq, precision: int = FP32, stream=None):
+        self._check(lib().tnvan_log_prob(self._h, batch, _ptr(spins), precision, _ptr(logq), _stream(stream)))
 
     def contract(self, betas, batch: int, spins, precision: int, logZR, dlogZR_dbeta=None, stream=None):
         b, pb = _arr(betas, np.float64)

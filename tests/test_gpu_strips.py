@@ -299,3 +299,68 @@ def test_tensor_core_backward_matches_oracle(cfg, batch, prec):
         # entries outside the MADE masks are exactly zero
         off = torch.as_tensor(_param_mask(model.D[k], w.hidden) == 0)
         assert torch.equal(gk[off], torch.zeros_like(gk[off]))
+
+
+TOL_RED = 1e-3  # |delta log q| / N in the reduced-precision modes
+
+
+def test_bf16_tensor_core_sampler_log_prob_matches_oracle():
+    w = wl.workload(2)
+    model = _model(w, scale=1.5)
+    batch = 96
+    s_all, refs = [], []
+    for k in range(model.n):
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_or, _, _ = oracle_samples(p32, model.D[k], w.hidden, 3, 0, k, batch)
+        s_all.append(s_or.numpy().reshape(-1))
+        refs.append(made.log_q(torch.as_tensor(p32, dtype=torch.float64), model.D[k], w.hidden, s_or))
+    d_spins = to_dev_spins(np.concatenate(s_all))
+    logq = torch.empty(model.n * batch, dtype=torch.float32, device="cuda")
+    model.ctx.profile(True)
+    model.ctx.log_prob(batch, d_spins, logq, tv.BF16)
+    torch.cuda.synchronize()
+    assert "log_prob_tc" in model.ctx.profile_read()  # the tensor-core path ran
+    model.ctx.profile(False)
+    for k in range(model.n):
+        err = float((logq[k * batch:(k + 1) * batch].cpu().double() - refs[k]).abs().max())
+        print(f"bf16 log q, instance {k}: max |delta| / N = {err / w.graphs[k].n:.2e}")
+        assert err / w.graphs[k].n <= TOL_RED
+
+
+def test_bf16_sampler_self_consistent_and_contracts_exactly():
+    w = wl.workload(2)
+    model = _model(w, n_inst=2)
+    B = 300
+    spins, logq, logZR = model.sample(B, 9, 4, precision=tv.BF16)
+    lq2 = torch.empty_like(logq)
+    model.ctx.log_prob(B, spins, lq2, tv.BF16)
+    lz2 = torch.empty_like(logZR)
+    model.ctx.contract(model.betas, B, spins, tv.FP32, lz2)
+    torch.cuda.synchronize()
+    assert torch.allclose(logq, lq2, atol=1e-5, rtol=0)  # same arithmetic, teacher-forced
+    assert torch.equal(logZR, lz2)  # contraction stays FP32
+
+
+def test_bf16_sampler_distribution_matches_oracle_marginal():
+    from paper_2504_12037_gb300.model import TNVAN
+
+    g = wl.sk(16, 77)
+    W = np.arange(16, dtype=np.int32)  # empty remainder: only the sampler matters
+    hidden = [32, 32]
+    model = TNVAN([g], [W], hidden, [1.0], seed=4, init_scale=2.0)
+    B = 200000
+    spins, logq, _ = model.sample(B, 1234, 0, precision=tv.BF16)
+    s = model.spins_of(spins, 0, B)[:, :4].cpu().numpy()
+    idx = (((1 - s) // 2) * (2 ** np.arange(4))).sum(1)
+    counts = np.bincount(idx, minlength=16).astype(float)
+    # exact marginal of the first four spins: prod_{i<4} q(s_i | s_<i)
+    th = torch.as_tensor(model.params.cpu().numpy().astype(np.float64))
+    from oracle import ising
+    X4 = ising.all_configs(4)
+    full = torch.zeros(16, 16, dtype=torch.float64)
+    full[:, :4] = X4
+    x = made.logits(th, 16, hidden, full)[:, :4]
+    q4 = torch.exp(-torch.nn.functional.softplus(-X4 * x).sum(1)).numpy()
+    chi2 = float(((counts - B * q4) ** 2 / (B * q4)).sum())
+    print("chi2 (15 dof):", chi2)
+    assert chi2 < 45
