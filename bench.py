@@ -35,6 +35,10 @@ UNIT = "samples/s"
 FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
+# the same kernels on the same workload (see profiles/); None if not captured
+NCU_TRAFFIC = {"sample_tc": 479488, "bwd_fused": 6685696}
 
 
 def args_():
@@ -43,7 +47,10 @@ def args_():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"],
+                    help="headline mode (bf16: network on the tensor cores, contractions FP32)")
+    ap.add_argument("--compare", default="fp32", help="second mode timed beside the headline ('' = none)")
+    ap.add_argument("--acc-steps", type=int, default=150, help="training steps before the accuracy estimate")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -148,57 +155,67 @@ def run_ours(a):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prec = {"fp32": tv.FP32, "tf32": tv.TF32, "bf16": tv.BF16}[a.precision]
+    PREC = {"fp32": tv.FP32, "tf32": tv.TF32, "bf16": tv.BF16}
+    prec = PREC[a.precision]
     w = wl.workload(CONFIG)
     B = w.batch
-    model = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
-    n_inst = model.n
-    model.ctx.reserve(B)
-    spins, logq, logZR = model.buffers(B)
-    dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
-    dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+    n_inst = len(w.graphs)
     stream = torch.cuda.current_stream()
     seed = 12037 + 7919 * rank
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-
-    def step(i):
-        model.train_step(B, seed, i, prec, 0.01, (spins, logq, logZR), dbeta, dJ, stream)
-
-    for i in range(a.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     props = torch.cuda.get_device_properties(local)
     gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
-    clocks = ClockSampler(gpu_id)
-    clocks.start()
-    time.sleep(0.3)
-    model.ctx.profile(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    for i in range(a.steps):
-        flush.zero_()  # evict L2 between timed steps (not inside the timed interval)
-        starts[i].record(stream)
-        step(a.warmup + i)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    model.ctx.profile(False)
-    clk = clocks.stop()
-    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(per_step) / len(per_step)
-    prof = model.ctx.profile_read()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+
+    def timed(mode: int, steps: int, warmup: int, sample_clocks: bool):
+        model = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
+        model.ctx.reserve(B)
+        bufs = model.buffers(B)
+        dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
+        dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+
+        def step(i):
+            model.train_step(B, seed, i, mode, 0.01, bufs, dbeta, dJ, stream)
+
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = ClockSampler(gpu_id) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        model.ctx.profile(True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        for i in range(steps):
+            flush.zero_()  # evict L2 between timed steps (not inside the timed interval)
+            starts[i].record(stream)
+            step(warmup + i)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        model.ctx.profile(False)
+        clk = clocks.stop() if clocks else None
+        ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)) / steps
+        prof = model.ctx.profile_read()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return model, bufs, dbeta, dJ, step, float(t.item()), prof, clk
+
+    model, (spins, logq, logZR), dbeta, dJ, step, ms_max, prof, clk = timed(prec, a.steps, a.warmup, True)
     samples_step = n_inst * B * world
     value = samples_step / (ms_max / 1e3)
+    compare = None
+    if a.compare and a.compare != a.precision:
+        _, _, _, _, _, ms_c, prof_c, _ = timed(PREC[a.compare], a.steps, a.warmup, False)
+        compare = {"precision": a.compare, "value": samples_step / (ms_c / 1e3), "ms_per_step": ms_c,
+                   "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof_c.items()}}
 
     # ----- end to end through the public API with host buffers -----
     h_spins = torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True)
@@ -216,7 +233,7 @@ def run_ours(a):
         h_logq.copy_(logq, non_blocking=True)
         h_logZR.copy_(logZR, non_blocking=True)
         stream.synchronize()
-    t_e2e = (time.perf_counter() - t0) / a.e2e_steps
+    t_e2e = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
     te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
@@ -230,9 +247,10 @@ def run_ours(a):
     D, H = model.D[0], w.hidden
     macs, parts = made_macs(D, H)
     strips = 4
+    # algorithmic FLOPs per sample of each kernel (masked network, strip chains)
     per_sample = {
-        "sample": 2.0 * macs,
-        "backward": 2.0 * macs * 3,  # forward + input-gradient + weight-gradient passes
+        "sample": 2.0 * macs, "sample_tc": 2.0 * macs,
+        "backward": 2.0 * macs * 3, "bwd_fused": 2.0 * macs * 3,  # forward, delta, weight gradient
         "strips": strips * strip_flops(3, 16),
         "strips+dbeta": strips * 2 * strip_flops(3, 16),
         "strips_dbeta": strips * 2 * strip_flops(3, 16),
@@ -240,15 +258,32 @@ def run_ours(a):
     }
     flop_launch = per_sample.get(dom_name, float("nan")) * n_inst * B
     achieved = flop_launch / (dom_ms / dom_n / 1e3) / 1e12 if dom_n else float("nan")
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+    if dom_name == "bwd_fused":
+        peak, bound, src = MEASURED_BF16_TFLOPS, "tensor", "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+    else:
+        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        bound, src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    roofline = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom_name), "peak_source": src,
                 "flop_per_launch": flop_launch, "ms_per_launch": dom_ms / dom_n}
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()}
     launches_per_step = sum(v[1] for v in prof.values()) / a.steps
 
-    # ----- accuracy context: exact F of the lattice and F_q/N -----
+    # ----- accuracy: both modes trained from the same start, then F_q / N -----
+    accuracy = None
+    if a.acc_steps > 0:
+        accuracy = {"train_steps": a.acc_steps, "batch_per_beta": B, "betas": w.betas}
+        for name in [a.precision] + ([a.compare] if compare else []):
+            m2 = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=77)
+            b2 = m2.buffers(B)
+            for i in range(a.acc_steps):
+                m2.train_step(B, 4242, i, PREC[name], 0.01, b2, None, None, stream)
+            sp2, lq2, lz2 = m2.sample(B, 999, 10 ** 7, PREC[name], b2, stream)
+            fe = m2.free_energy(B, lz2, lq2, stream)
+            accuracy[name] = {"F_q_per_spin": [float(x) / 256 for x in fe[:, 0]],
+                              "F_IS_per_spin": [float(x) / 256 for x in fe[:, 1]],
+                              "stderr_per_spin": [float(x) / 256 for x in fe[:, 2]]}
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -257,15 +292,23 @@ def run_ours(a):
         "config": {"workload": w.name, "lattice": "16x16 open", "couplings": "N(0,1)",
                    "betas": w.betas, "batch_per_beta": B, "instances": n_inst,
                    "width_set": "every 4th column (64 spins)", "made": [64] + w.hidden + [64],
+                   "precision": f"{a.precision}: network (sampler, backward) in {a.precision} on the "
+                                "tensor cores with FP32 accumulation; contractions FP32; reductions FP64"
+                                if a.precision != "fp32" else "fp32 everywhere, FP64 reductions",
                    "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * a.steps)),
-        "roofline": roofline, "kernels": kernels,
-        "fe_last": {"F_q_per_spin": [float(x) / 256 for x in fe_last[:, 0]],
-                    "F_IS_per_spin": [float(x) / 256 for x in fe_last[:, 1]]},
+        "roofline": roofline, "kernels": kernels, "compare": compare, "accuracy": accuracy,
     }
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
+        # the oracle's exact free energy of the lattice (single-site transfer matrix, 2^16 states)
+        f_exact = oracle_exact_f(w)
+        out["cpu_baseline"]["F_exact_per_spin"] = f_exact
+        if accuracy:
+            for name in [k for k in accuracy if isinstance(accuracy[k], dict)]:
+                accuracy[name]["abs_F_q_minus_F_exact_per_spin"] = [
+                    abs(fq - fe) for fq, fe in zip(accuracy[name]["F_q_per_spin"], f_exact)]
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -301,6 +344,17 @@ def oracle_step(w, params, offsets, n_b, seed, step):
         est.adam_step(th.numpy(), grad.numpy(), np.zeros(th.numel()), np.zeros(th.numel()), 1)
         done += n_b
     return done
+
+
+def oracle_exact_f(w):
+    """Exact F / N of each instance from the oracle's single-site transfer matrix."""
+    from oracle import transfer
+
+    out = []
+    for g, beta in zip(w.graphs, w.betas):
+        lz = float(transfer.log_z_helical(g.Lx, g.Ly, g.ei, g.ej, g.J, beta))
+        out.append(-lz / beta / g.n)
+    return out
 
 
 def cpu_baseline(w, params, offsets, budget_s=15.0, n_b=2048):

@@ -300,8 +300,11 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     dd.C16 = c16;
     dd.c0 = c0;
   } else {
-    int *prog = nullptr, *fld = nullptr;
+    int *prog = nullptr, *fld = nullptr, *pe = nullptr, *so = nullptr, *cs = nullptr;
     float *pj = nullptr, *fj = nullptr;
+    if ((rc = upload(ctx, in, in.gpairE, &pe))) return rc;
+    if ((rc = upload(ctx, in, in.gstep_off, &so))) return rc;
+    if ((rc = upload(ctx, in, in.gcomp_step0, &cs))) return rc;
     if ((rc = upload(ctx, in, in.gprog, &prog))) return rc;
     if ((rc = upload(ctx, in, in.gfld, &fld))) return rc;
     if ((rc = upload(ctx, in, in.gpairJ, &pj))) return rc;
@@ -312,6 +315,10 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     g.prog = prog;
     g.prog_len = (int)in.gprog.size();
     g.pairJ = pj;
+    g.pairE = pe;
+    g.step_off = so;
+    g.comp_step0 = cs;
+    g.max_steps = in.g_max_steps;
     g.n_pairs = in.g_npairs;
     g.fld = fld;
     g.fldJ = fj;
@@ -650,6 +657,7 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
   if (ctx->d_ws) cudaFree(ctx->d_ws);
+  if (ctx->d_dj_part) cudaFree(ctx->d_dj_part);
   delete ctx;
   return TNVAN_OK;
 }
@@ -984,6 +992,17 @@ int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info) {
   return TNVAN_OK;
 }
 
+static int ensure_dj_part(tnvan_ctx* ctx, size_t floats) {
+  if (floats <= ctx->dj_part_floats) return TNVAN_OK;
+  if (ctx->d_dj_part) cudaFree(ctx->d_dj_part);
+  ctx->d_dj_part = nullptr;
+  ctx->dj_part_floats = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_dj_part, floats * sizeof(float));
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(d/dJ partials): %s", cudaGetErrorString(e));
+  ctx->dj_part_floats = floats;
+  return TNVAN_OK;
+}
+
 static int ensure_grad_ws(tnvan_ctx* ctx, size_t floats) {
   if (floats <= ctx->grad_packed_floats) return TNVAN_OK;
   if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
@@ -1027,6 +1046,13 @@ int tnvan_reserve(tnvan_ctx* ctx, int max_batch) {
                                       (size_t)splits * ctx->inst.size() * (size_t)maxp));
     if (rc) return rc;
     rc = ensure_ws(ctx, tc_ws_floats(ctx, std::max(max_batch, 1)) * sizeof(float));
+    if (rc) return rc;
+    int max_edges = 0, ctas = 0;
+    for (const Instance& in : ctx->inst) {
+      max_edges = std::max(max_edges, in.m);
+      ctas += (std::max(max_batch, 1) + 127) / 128;
+    }
+    rc = ensure_dj_part(ctx, (size_t)ctas * ((max_edges + 3) & ~3));
     if (rc) return rc;
   }
   ctx->reserved_batch = std::max(ctx->reserved_batch, max_batch);
@@ -1141,8 +1167,6 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (d_dJ)
     for (const Instance& in : ctx->inst) {
-      if (in.kind == 2)
-        return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ is not implemented for general components (instance with %d spins)", in.n);
       if (in.kind == 0)
         for (const StripDev& sd : in.strip.strips)
           if (sd.L > 64) return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ supports strips of at most 64 rows (got %d)", sd.L);
@@ -1242,16 +1266,45 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
       else other = true;
     }
     if (any_strip) {
-      int sm = 0;
+      int sm = 0, max_edges = 0;
       for (const Instance& in : ctx->inst)
-        if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
+        if (in.kind == 0) {
+          sm = std::max(sm, strip_smem_bytes(in, 128) + 4 * in.m);
+          max_edges = std::max(max_edges, in.m);
+        }
+      const int stride = (max_edges + 3) & ~3;
+      if ((rc = ensure_dj_part(ctx, (size_t)lt.tile_begin[lt.n_inst] * stride))) return rc;
       PROF("strips_dJ", s);
-      CK(launch_strips_dJ(ctx->d_inst, lt, sm, d_spins, d_dJ, s), "strip adjoint kernel");
+      CK(launch_strips_dJ(ctx->d_inst, lt, sm, d_spins, ctx->d_dj_part, stride, d_dJ, s), "strip adjoint kernel");
     }
     if (other) {
       {
         PROF("dense_dJ", s);
         CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
+      }
+      int arena = 0, pairs = 0, steps = 0, Dm = 0, me = 0;
+      bool any_gen = false;
+      for (const Instance& in : ctx->inst)
+        if (in.kind == 2) {
+          any_gen = true;
+          arena = std::max(arena, in.g_max_entries);
+          pairs = std::max(pairs, in.g_npairs);
+          steps = std::max(steps, in.g_max_steps);
+          Dm = std::max(Dm, (int)in.W.size());
+          me = std::max(me, in.m);
+        }
+      if (any_gen) {
+        int T = 64;
+        while (T > 1 && general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T) > 200 * 1024) T /= 2;
+        const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T);
+        if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
+        LaunchInfo lg;
+        if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
+        const int stride = (me + 3) & ~3;
+        if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
+        PROF("general_dJ", s);
+        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, pairs, steps, d_spins, ctx->d_dj_part, stride, d_dJ, s),
+           "general adjoint kernel");
       }
     }
   }
@@ -1453,8 +1506,9 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     adj[in.ej[e]].push_back({in.ei[e], e});
   }
   std::vector<int> prog{(int)comps.size()};
-  std::vector<int> fld;
+  std::vector<int> fld, pairE, step_off, comp_step0;
   std::vector<float> fldJ, pairJ;
+  int max_steps = 0;
   double chat = 0;
   int arena_max = 0, width_max = 0;
   for (const auto& comp : comps) {
@@ -1475,6 +1529,7 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
           if (i < j) {
             pair_of[{i, j}] = (int)pairJ.size();
             pairJ.push_back((float)in.J[e]);
+            pairE.push_back(e);
             chat += fabs((double)(float)in.J[e]);
           }
         } else if (pos[u] >= 0) {
@@ -1517,6 +1572,8 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     std::set<std::pair<int, int>> edges_left;
     for (auto& kv : pair_of) edges_left.insert(kv.first);
     const size_t hdr = prog.size();
+    comp_step0.push_back((int)step_off.size());
+    max_steps = std::max(max_steps, n);
     prog.push_back(n);
     prog.push_back(0);  // arena size, patched below
     prog.push_back(0);  // final offset, patched below
@@ -1546,6 +1603,7 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
         if (var == v) return m;
         return (int)(std::lower_bound(out.begin(), out.end(), var) - out.begin());
       };
+      step_off.push_back((int)prog.size());
       prog.push_back(v);
       prog.push_back(fb[v]);
       prog.push_back(fc[v]);
@@ -1570,8 +1628,13 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     prog[hdr + 2] = last_off;
     arena_max = std::max(arena_max, (arena + 3) & ~3);  // keeps the float4 pair table aligned
   }
+  comp_step0.push_back((int)step_off.size());
   in.gprog.swap(prog);
   in.gfld.swap(fld);
+  in.gpairE.swap(pairE);
+  in.gstep_off.swap(step_off);
+  in.gcomp_step0.swap(comp_step0);
+  in.g_max_steps = max_steps;
   in.gfldJ.swap(fldJ);
   in.gpairJ.swap(pairJ);
   in.g_npairs = (int)in.gpairJ.size();

@@ -108,6 +108,10 @@ struct GenDev {
   const int* prog;       // packed int program
   int prog_len;
   const float* pairJ;    // couplings of R-R bonds referenced by the program
+  const int* pairE;      // edge id of each pair
+  const int* step_off;   // program offset of every step record, in program order
+  const int* comp_step0; // [n_comp + 1] first step index of each component
+  int max_steps;         // most steps of one component
   int n_pairs;
   const int* fld;        // per R spin: W-neighbour list (pos, edge id) packed
   const float* fldJ;
@@ -169,7 +173,8 @@ struct Instance {
   std::vector<int> eRR, eRW;
   double dense_chat = 0;
   // general
-  std::vector<int> gprog, gfld;
+  std::vector<int> gprog, gfld, gpairE, gstep_off, gcomp_step0;
+  int g_max_steps = 0;
   std::vector<float> gpairJ, gfldJ;
   int g_ncomp = 0, g_max_entries = 0, g_npairs = 0;
   double g_chat = 0;
@@ -209,6 +214,8 @@ struct tnvan_ctx {
   int reserved_batch = 0;
   float* d_grad_packed = nullptr;    // packed-layout gradient partials
   size_t grad_packed_floats = 0;
+  float* d_dj_part = nullptr;        // strip d/dJ partial rows [CTA][max edges]
+  size_t dj_part_floats = 0;
 };
 
 namespace tnvan {
@@ -222,13 +229,17 @@ cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_
 cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           const int8_t* spins, double* logZR, double* dbeta, cudaStream_t s);
 cudaError_t launch_strips_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
-                             const int8_t* spins, double* dJ, cudaStream_t s);
+                             const int8_t* spins, float* part, int part_stride, double* dJ, cudaStream_t s);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s);
 cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                            const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                            cudaStream_t s);
+cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena,
+                              int pairs, int steps, const int8_t* spins, float* part, int part_stride,
+                              double* dJ, cudaStream_t s);
+int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,

@@ -130,6 +130,206 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
   if (DB) dbeta[o] = dl + chf + (double)e1;
 }
 
+// ---------------------------------------------------------------------------
+// Reverse mode: d ln Z_c / d J_e for the bonds inside a component (beta <r r'>)
+// and its bonds to the width set (beta s_w <r>).  Per component the program
+// runs forward storing every (renormalised) table A_t and its scale 2^-e_t;
+// then the steps run backwards carrying adjoints Abar = d ln Z / d A of each
+// table entry, starting from 1 / A_final.  For step t with product terms
+// term(x, sigma) (field factor, bond factors, input tables):
+//   g(x, sigma)       = Abar_t[x] 2^-e_t term(x, sigma)
+//   Abar_in[idx]     += g / A_in[idx]
+//   d lnZ / d J_bond += beta sum g sigma sigma_u,  d lnZ / d J_field += beta s_w sum g sigma.
+// Bond sums are warp-reduced into per-CTA shared accumulators, written as one
+// row per CTA and added per instance in a fixed order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void acc_edge(float* acc, int e, float v, bool lane0) {
+  v = warp_sum(v);
+  if (lane0 && e >= 0) atomicAdd(acc + e, v);
+}
+
+__global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restrict__ inst,
+                                                        const LaunchInfo li, int arena_floats,
+                                                        int max_pairs, int max_steps,
+                                                        const int8_t* __restrict__ spins,
+                                                        float* __restrict__ part, int part_stride) {
+  extern __shared__ float sm[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  if (I.kind != 2) return;
+  const int T = li.tile, t = threadIdx.x;
+  const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
+  const float beta = (float)li.beta[k];
+  const int D = I.D, Dp = padded_bytes(D);
+  float* A = sm;                          // [arena][T]
+  float* Ab = A + arena_floats * T;       // [arena][T] adjoints
+  float* sc = Ab + arena_floats * T;      // [max_steps][T] scales 2^-e
+  float2* pt = reinterpret_cast<float2*>(sc + max_steps * T);  // [pairs] (a, b)
+  float* acc = reinterpret_cast<float*>(pt + max_pairs);       // [n_edges]
+  int8_t* ssp = reinterpret_cast<int8_t*>(acc + ((I.n_edges + 3) & ~3));
+  const GenDev& G = I.gen;
+  for (int p = t; p < G.n_pairs; p += T) {
+    const float J = G.pairJ[p], tt = expf(-2.f * beta * fabsf(J));
+    pt[p] = J >= 0.f ? make_float2(1.f, tt) : make_float2(tt, 1.f);
+  }
+  for (int e = t; e < I.n_edges; e += T) acc[e] = 0.f;
+  const int n_valid = min(T, li.batch - b0);
+  const int8_t* gsp = spins + I.spin_units * li.batch + (long long)b0 * D;
+  for (int e = t; e < n_valid * D; e += T) ssp[(e / D) * Dp + (e % D)] = gsp[e];
+  for (int e = n_valid * Dp + t; e < T * Dp; e += T) ssp[e] = 1;
+  __syncthreads();
+  const bool valid = b < li.batch;
+  const bool lane0 = (t & 31) == 0;
+  const int8_t* s = ssp + t * Dp;
+  const float wscale = valid ? beta / (float)li.batch : 0.f;
+  const int* P = G.prog;
+  int ip = 1;
+  for (int c = 0; c < G.n_comp; ++c) {
+    const int nsteps = P[ip], arena = P[ip + 1], fin = P[ip + 2];
+    ip += 3;
+    const int st0 = G.comp_step0[c];
+    // forward: tables and their scales
+    for (int st = 0; st < nsteps; ++st) {
+      const int r = G.step_off[st0 + st];
+      const int fb = P[r + 1], fc = P[r + 2], m = P[r + 3], out = P[r + 4], nin = P[r + 5], npair = P[r + 6];
+      int q = r + 7;
+      const int in0 = q;
+      for (int i = 0; i < nin; ++i) q += 2 + P[q + 1];
+      const int pq = q;
+      float h = 0.f;
+      for (int f = fb; f < fb + fc; ++f) h = fmaf(G.fldJ[f], (float)s[G.fld[2 * f]], h);
+      const float ah = fabsf(h);
+      const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
+      float mx = 0.f;
+      for (int x = 0; x < (1 << m); ++x) {
+        float accv = 0.f;
+        for (int sg = 0; sg < 2; ++sg) {
+          float pr = fv[sg];
+          const int ext = x | (sg << m);
+          for (int j = 0; j < npair; ++j) {
+            const float2 ab = pt[P[pq + 2 * j]];
+            pr *= (((x >> P[pq + 2 * j + 1]) & 1) == sg) ? ab.x : ab.y;
+          }
+          int qq = in0;
+          for (int i = 0; i < nin; ++i) {
+            const int off = P[qq], kk = P[qq + 1];
+            int idx = 0;
+            for (int j = 0; j < kk; ++j) idx |= ((ext >> P[qq + 2 + j]) & 1) << j;
+            pr *= A[(off + idx) * T + t];
+            qq += 2 + kk;
+          }
+          accv += pr;
+        }
+        A[(out + x) * T + t] = accv;
+        Ab[(out + x) * T + t] = 0.f;
+        mx = fmaxf(mx, accv);
+      }
+      const float scl = pow2i(-exponent_of(mx));
+      for (int x = 0; x < (1 << m); ++x) A[(out + x) * T + t] *= scl;
+      sc[st * T + t] = scl;
+    }
+    (void)arena;
+    Ab[fin * T + t] = 1.f / A[fin * T + t];
+    // backward
+    for (int st = nsteps - 1; st >= 0; --st) {
+      const int r = G.step_off[st0 + st];
+      const int fb = P[r + 1], fc = P[r + 2], m = P[r + 3], out = P[r + 4], nin = P[r + 5], npair = P[r + 6];
+      int q = r + 7;
+      const int in0 = q;
+      for (int i = 0; i < nin; ++i) q += 2 + P[q + 1];
+      const int pq = q;
+      float h = 0.f;
+      for (int f = fb; f < fb + fc; ++f) h = fmaf(G.fldJ[f], (float)s[G.fld[2 * f]], h);
+      const float ah = fabsf(h);
+      const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
+      const float scl = sc[st * T + t];
+      float gs = 0.f;       // sum g sigma_v
+      float gp[8];          // sum g sigma_v sigma_u per pair (at most 8 neighbours)
+      for (int j = 0; j < 8; ++j) gp[j] = 0.f;
+      for (int x = 0; x < (1 << m); ++x) {
+        const float abx = Ab[(out + x) * T + t] * scl;
+        for (int sg = 0; sg < 2; ++sg) {
+          float pr = fv[sg];
+          const int ext = x | (sg << m);
+          for (int j = 0; j < npair; ++j) {
+            const float2 ab = pt[P[pq + 2 * j]];
+            pr *= (((x >> P[pq + 2 * j + 1]) & 1) == sg) ? ab.x : ab.y;
+          }
+          int qq = in0;
+          for (int i = 0; i < nin; ++i) {
+            const int off = P[qq], kk = P[qq + 1];
+            int idx = 0;
+            for (int j = 0; j < kk; ++j) idx |= ((ext >> P[qq + 2 + j]) & 1) << j;
+            pr *= A[(off + idx) * T + t];
+            qq += 2 + kk;
+          }
+          const float g = abx * pr;
+          const float sv = sg ? -1.f : 1.f;
+          gs = fmaf(g, sv, gs);
+          for (int j = 0; j < npair && j < 8; ++j)
+            gp[j] = fmaf(g, ((((x >> P[pq + 2 * j + 1]) & 1) == sg) ? 1.f : -1.f), gp[j]);
+          qq = in0;
+          for (int i = 0; i < nin; ++i) {
+            const int off = P[qq], kk = P[qq + 1];
+            int idx = 0;
+            for (int j = 0; j < kk; ++j) idx |= ((ext >> P[qq + 2 + j]) & 1) << j;
+            const float a = A[(off + idx) * T + t];
+            if (a > 0.f) Ab[(off + idx) * T + t] += g / a;
+            qq += 2 + kk;
+          }
+        }
+      }
+      for (int f = fb; f < fb + fc; ++f)
+        acc_edge(acc, G.fld[2 * f + 1], wscale * gs * (float)s[G.fld[2 * f]], lane0);
+      for (int j = 0; j < npair && j < 8; ++j) acc_edge(acc, G.pairE[P[pq + 2 * j]], wscale * gp[j], lane0);
+    }
+    ip = G.step_off[st0 + nsteps - 1];
+    {
+      // advance ip past the last step record of this component
+      const int r = ip;
+      int q = r + 7;
+      for (int i = 0; i < P[r + 5]; ++i) q += 2 + P[q + 1];
+      ip = q + 2 * P[r + 6];
+    }
+  }
+  __syncthreads();
+  float* row = part + (long long)blockIdx.x * part_stride;
+  for (int e = t; e < I.n_edges; e += T) row[e] = acc[e];
+}
+
+__global__ void general_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                         const float* __restrict__ part, int part_stride,
+                                         double* __restrict__ dJ) {
+  const int k = blockIdx.y;
+  const InstDev& I = inst[k];
+  if (I.kind != 2) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.n_edges; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = li.tile_begin[k]; c < li.tile_begin[k + 1]; ++c) s += (double)part[(long long)c * part_stride + e];
+    dJ[I.edge_off + e] += s;
+  }
+}
+
+int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T) {
+  int w4 = (D + 3) / 4;
+  if ((w4 & 1) == 0) ++w4;
+  return (2 * arena + steps) * T * 4 + pairs * 8 + ((n_edges + 3) & ~3) * 4 + T * 4 * w4;
+}
+
+cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena,
+                              int pairs, int steps, const int8_t* spins, float* part, int part_stride,
+                              double* dJ, cudaStream_t s) {
+  const int nblk = li.tile_begin[li.n_inst];
+  if (nblk == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(general_dJ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  general_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, steps, spins, part, part_stride);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  general_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
+  return cudaGetLastError();
+}
+
 int general_smem_bytes(int arena, int pairs, int D, int T, bool db) {
   int w4 = (D + 3) / 4;
   if ((w4 & 1) == 0) ++w4;

@@ -239,14 +239,15 @@ cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_
 // ---------------------------------------------------------------------------
 #define STRIP_DJ_LMAX 64
 
-__device__ __forceinline__ void acc_bond(double* dJ, int e, float val, bool lane0) {
+// Warp-sum a bond contribution and add it to the CTA's shared accumulator.
+__device__ __forceinline__ void acc_bond(float* acc, int e, float val, bool lane0) {
   const float s = warp_sum(val);
-  if (lane0 && e >= 0) atomicAdd(dJ + e, (double)s);
+  if (lane0 && e >= 0) atomicAdd(acc + e, s);
 }
 
 template <int W>
 __device__ void strip_dJ(const float* tab, const StripRow* __restrict__ rows, int L,
-                         const int8_t* srow, bool valid, float scale, double* dJ, bool lane0) {
+                         const int8_t* srow, bool valid, float scale, float* dJ, bool lane0) {
   constexpr int NX = 1 << W;
   const float4* vert = reinterpret_cast<const float4*>(tab);
   const float* diag = tab + L * W * 4;
@@ -345,10 +346,13 @@ __device__ void strip_dJ(const float* tab, const StripRow* __restrict__ rows, in
   }
 }
 
+// One CTA per tile of samples: bond sums accumulate in shared memory (FP32,
+// n_edges floats), then the CTA writes its row of `part` [CTA][max edges];
+// strips_dJ_reduce_kernel adds the rows of each instance in a fixed order.
 __global__ void __launch_bounds__(128) strips_dJ_kernel(const InstDev* __restrict__ inst,
                                                         const LaunchInfo li,
                                                         const int8_t* __restrict__ spins,
-                                                        double* __restrict__ dJ) {
+                                                        float* __restrict__ part, int part_stride) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
@@ -359,6 +363,8 @@ __global__ void __launch_bounds__(128) strips_dJ_kernel(const InstDev* __restric
   const int D = I.D, Dp = padded_row_bytes(D);
   build_strip_tables(I, beta, sm, t, T);
   int8_t* ssp = reinterpret_cast<int8_t*>(sm + I.strip_tab_floats);
+  float* acc = reinterpret_cast<float*>(ssp + T * Dp);  // [n_edges]
+  for (int e = t; e < I.n_edges; e += T) acc[e] = 0.f;
   const int n_valid = min(T, li.batch - b0);
   stage_spins(spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, D, Dp, ssp, t, T);
   for (int e = n_valid * Dp + t; e < T * Dp; e += T) ssp[e] = 1;  // padding rows
@@ -366,29 +372,48 @@ __global__ void __launch_bounds__(128) strips_dJ_kernel(const InstDev* __restric
   const bool valid = b < li.batch;
   const int8_t* srow = ssp + t * Dp;
   const float scale = beta / (float)li.batch;
-  double* dJk = dJ + I.edge_off;
   const bool lane0 = (t & 31) == 0;
   for (int st = 0; st < I.n_strips; ++st) {
     const StripDev& sd = I.strips[st];
     const float* tab = sm + sd.tab_off;
     const StripRow* rows = I.rows + sd.row0;
     switch (sd.w) {
-      case 1: strip_dJ<1>(tab, rows, sd.L, srow, valid, scale, dJk, lane0); break;
-      case 2: strip_dJ<2>(tab, rows, sd.L, srow, valid, scale, dJk, lane0); break;
-      case 3: strip_dJ<3>(tab, rows, sd.L, srow, valid, scale, dJk, lane0); break;
-      default: strip_dJ<4>(tab, rows, sd.L, srow, valid, scale, dJk, lane0); break;
+      case 1: strip_dJ<1>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
+      case 2: strip_dJ<2>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
+      case 3: strip_dJ<3>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
+      default: strip_dJ<4>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
     }
+  }
+  __syncthreads();
+  float* row = part + (long long)blockIdx.x * part_stride;
+  for (int e = t; e < I.n_edges; e += T) row[e] = acc[e];
+}
+
+// dJ[edge] += sum over the instance's CTA rows, in CTA order (deterministic).
+__global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                        const float* __restrict__ part, int part_stride,
+                                        double* __restrict__ dJ) {
+  const int k = blockIdx.y;
+  const InstDev& I = inst[k];
+  if (I.kind != 0) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.n_edges; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = li.tile_begin[k]; c < li.tile_begin[k + 1]; ++c) s += (double)part[(long long)c * part_stride + e];
+    dJ[I.edge_off + e] += s;
   }
 }
 
 cudaError_t launch_strips_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
-                             const int8_t* spins, double* dJ, cudaStream_t s) {
+                             const int8_t* spins, float* part, int part_stride, double* dJ, cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(strips_dJ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem_bytes);
   if (e != cudaSuccess) return e;
-  strips_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, spins, dJ);
+  strips_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, spins, part, part_stride);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  strips_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
   return cudaGetLastError();
 }
 

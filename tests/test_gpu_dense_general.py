@@ -133,15 +133,45 @@ def test_general_small_graphs_against_enumeration():
         assert float((logZR[k * B:(k + 1) * B].cpu() - refs[k]).abs().max()) / graphs[k].n <= TOL_FP32
 
 
-def test_general_dJ_is_reported_unsupported():
-    w = wl.workload(4)
-    model = _model(w.graphs, w.widths_sets, w.hidden, w.betas)
-    B = 4
-    spins, logq, logZR = model.sample(B, 1, 0)
-    with pytest.raises(tv.TnvanError) as e:
-        model.ctx.backward(model.betas, B, spins, logZR, logq, tv.FP32, torch.empty_like(model.params), None,
-                           torch.empty(w.graphs[0].m, dtype=torch.float64, device="cuda"))
-    assert e.value.code == tv.E_UNSUPPORTED
+@pytest.mark.parametrize("which", ["rrg_workload", "small_graphs"])
+def test_general_adjoint_dJ_matches_oracle(which):
+    if which == "rrg_workload":
+        w = wl.workload(4)
+        graphs, Ws, betas, hidden = w.graphs, w.widths_sets, w.betas, w.hidden
+    else:
+        g1 = wl.random_regular(20, 3, 7)
+        g2 = wl.lattice(5, 4, "gauss", 9)
+        g2.topology = wl.GENERAL
+        graphs = [g1, g2]
+        Ws = [np.array([0, 5, 9, 13], np.int32), np.array([2, 7, 12, 17, 6], np.int32)]
+        betas, hidden = [1.0, 0.7], [10]
+    model = _model(graphs, Ws, hidden, betas)
+    B = 20
+    s_all, refs = [], []
+    for k in range(model.n):
+        g = graphs[k]
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_or, _, _ = oracle_samples(p32, model.D[k], hidden, 3, 0, k, B)
+        s_all.append(s_or.numpy().reshape(-1))
+        Jt = torch.tensor(g.J, dtype=torch.float64, requires_grad=True)
+        lz = general.log_zr_general(g.n, g.ei, g.ej, Jt, betas[k], Ws[k], s_or, enum_max=0)
+        (ref,) = torch.autograd.grad(lz.mean(), Jt)
+        refs.append(ref)
+    d_spins = to_dev_spins(np.concatenate(s_all))
+    n = model.n
+    logZR = torch.empty(n * B, dtype=torch.float64, device="cuda")
+    model.ctx.contract(model.betas, B, d_spins, tv.FP32, logZR)
+    dJ = torch.empty(sum(g.m for g in graphs), dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(model.params)
+    model.ctx.backward(model.betas, B, d_spins, logZR, torch.zeros(n * B, dtype=torch.float32, device="cuda"),
+                       tv.FP32, grad, None, dJ)
+    torch.cuda.synchronize()
+    off = 0
+    for k in range(n):
+        m = graphs[k].m
+        got = dJ[off:off + m].cpu()
+        assert float((got - refs[k]).abs().max()) <= 2e-5 * max(1.0, float(refs[k].abs().max()))
+        off += m
 
 
 def test_multi_instance_lattice_sizes_parity():
