@@ -10,7 +10,10 @@
 // where E'_RR(r) = sum_{i<j in R} J_ij r_i r_j and c_hat = sum |J_ij| (so C <= 1).
 // This is an exact regrouping of the 65536-term sum into a 256 x 256 bilinear
 // form, i.e. a batched dense contraction [samples x 256] x [256 x 256].
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace tnvan {
 
@@ -40,10 +43,11 @@ __global__ void __launch_bounds__(256) dense_table_kernel(const InstDev* __restr
   const float c = expf(beta * (E - ch));
   I.dense.C32[a * 256 + b] = c;
   I.dense.dC32[a * 256 + b] = c * (E - ch);
-  // bf16 copy, round to nearest even
+  // bf16 copy (round to nearest even) in the tensor cores' canonical K-major
+  // layout: row a, K index b, core matrices of 8 rows x 8 elements
   uint32_t u = __float_as_uint(c);
   u += 0x7fffu + ((u >> 16) & 1u);
-  I.dense.C16[a * 256 + b] = (uint16_t)(u >> 16);
+  I.dense.C16[(a >> 3) * 2048 + (b >> 3) * 64 + (a & 7) * 8 + (b & 7)] = (uint16_t)(u >> 16);
 }
 
 #define DN_T 16  // samples per CTA (forward)
@@ -290,6 +294,142 @@ __global__ void __launch_bounds__(256) dense_dJ_kernel(const InstDev* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 tensor-core form (precision TNVAN_BF16): per CTA a persistent walk over
+// 128-sample tiles of one instance.  C (256 x 256, BF16, canonical layout) is
+// bulk-copied into shared memory once; per tile every thread builds its
+// sample's g_B row (256 BF16 values from 2 x 16 partial products), one
+// elected thread issues the [128 x 256] x [256 x 256] product into TMEM
+// (16 tcgen05.mma of K = 16), and each thread finishes z = g_A . (C g_B) from
+// its TMEM lane, with g_A again from 2 x 16 partial products.
+// ---------------------------------------------------------------------------
+#define DTC_TILES_PER_CTA 8
+
+__device__ __forceinline__ void half_products(const float* h, float beta, float* lo, float* hi) {
+  // g(x) = exp(beta h.sigma(x) - beta |h|_1) over 8 spins = lo[x & 15] * hi[x >> 4]
+#pragma unroll
+  for (int x = 0; x < 16; ++x) {
+    float a = 0.f, c = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a += h[i] * sgn_bit(x, i) - fabsf(h[i]);
+      c += h[4 + i] * sgn_bit(x, i) - fabsf(h[4 + i]);
+    }
+    lo[x] = expf(beta * a);
+    hi[x] = expf(beta * c);
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                          const int8_t* __restrict__ spins,
+                                                          double* __restrict__ logZR) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  if (I.kind != 1) return;
+  const int t = threadIdx.x, w = t >> 5, D = I.D;
+  const int tiles = (li.batch + 127) / 128;
+  const int tile0 = (blockIdx.x - li.tile_begin[k]) * DTC_TILES_PER_CTA;
+  const int tile1 = min(tiles, tile0 + DTC_TILES_PER_CTA);
+  unsigned char* sC = smem;                   // 128 KB
+  unsigned char* sG = smem + 131072;          // [128 x 256] BF16, 64 KB
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 131072 + 65536);
+  uint64_t* cbar = bar + 1;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_init(cbar, 1);
+  }
+  if (w == 0) {
+    tc::tmem_alloc(slot, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (t == 0) {
+    mbar_expect_tx(cbar, 131072u);
+    bulk_g2s(sC, I.dense.C16, 131072u, cbar);
+  }
+  bool ok = mbar_wait(cbar, 0);
+  const uint32_t tmem = *slot;
+  const uint32_t lane_off = (uint32_t)(w * 32) << 16;
+  const uint32_t id = tc::idesc(128, 256, 1u);
+  const float beta = (float)li.beta[k];
+  const double bd = li.beta[k];
+  const double chf = (double)(float)I.dense.c_hat;
+  const double phantom = (16 - I.dense.nR) * 0.69314718055994530942;
+  uint32_t phase = 0;
+  for (int tile = tile0; tile < tile1 && ok; ++tile) {
+    const int b = tile * 128 + t;
+    const bool valid = b < li.batch;
+    const int8_t* st = spins + I.spin_units * li.batch + (long long)(valid ? b : 0) * D;
+    float h[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) h[r] = 0.f;
+    for (int wpos = 0; wpos < D; ++wpos) {
+      const float sw = (float)st[wpos];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) h[r] = fmaf(__ldg(I.dense.JRW + r * D + wpos), sw, h[r]);
+    }
+    float e1 = 0.f;
+    for (int e = 0; e < I.n_ww; ++e) {
+      const EdgeWW q = I.ww[e];
+      e1 = fmaf(q.J, (float)(st[q.a] * st[q.b]), e1);
+    }
+    float lo[16], hi[16];
+    half_products(h + 8, beta, lo, hi);  // g_B over the B half
+    for (int c = 0; c < 256; c += 8) {
+      __nv_bfloat162 p0 = __floats2bfloat162_rn(lo[(c + 0) & 15] * hi[c >> 4], lo[(c + 1) & 15] * hi[c >> 4]);
+      __nv_bfloat162 p1 = __floats2bfloat162_rn(lo[(c + 2) & 15] * hi[c >> 4], lo[(c + 3) & 15] * hi[c >> 4]);
+      __nv_bfloat162 p2 = __floats2bfloat162_rn(lo[(c + 4) & 15] * hi[c >> 4], lo[(c + 5) & 15] * hi[c >> 4]);
+      __nv_bfloat162 p3 = __floats2bfloat162_rn(lo[(c + 6) & 15] * hi[c >> 4], lo[(c + 7) & 15] * hi[c >> 4]);
+      uint4 u;
+      u.x = *reinterpret_cast<uint32_t*>(&p0);
+      u.y = *reinterpret_cast<uint32_t*>(&p1);
+      u.z = *reinterpret_cast<uint32_t*>(&p2);
+      u.w = *reinterpret_cast<uint32_t*>(&p3);
+      *reinterpret_cast<uint4*>(sG + (t >> 3) * 4096 + (c >> 3) * 128 + (t & 7) * 16) = u;
+    }
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+      for (int kk = 0; kk < 16; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc(smem_u32(sG) + kk * 256u, 128u, 4096u),
+                     tc::smem_desc(smem_u32(sC) + kk * 256u, 128u, 4096u), id, kk > 0 ? 1u : 0u);
+      tc::mma_commit(bar);
+    }
+    ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok) break;
+    half_products(h, beta, lo, hi);  // g_A over the A half
+    float z = 0.f;
+    for (int c = 0; c < 256; c += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + lane_off + (uint32_t)c, v);
+      float part = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) part = fmaf(lo[i], v[i], part);
+      z = fmaf(hi[c >> 4], part, z);
+    }
+    if (valid) {
+      double habs = 0.0;
+      for (int r = 0; r < 16; ++r) habs += fabs((double)h[r]);
+      logZR[(long long)k * li.batch + b] = bd * ((double)e1 + chf + habs) + (double)logf(z) - phantom;
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // TMEM read and G tile consumed before the next tile overwrites them
+    tc::fence_after_sync();
+  }
+  if (!ok && t == 0) atomicExch(li.status, 5);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, 256);
+}
+
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li_in, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s) {
@@ -309,6 +449,17 @@ cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li_in, int pre
   dense_table_kernel<<<dim3(256, li.n_inst), 256, 0, s>>>(d_inst, li);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (precision == TNVAN_BF16 && !dJ && !dbeta && logZR) {
+    LaunchInfo lt = li_in;
+    const int tiles = (li.batch + 127) / 128;
+    const int per = (tiles + DTC_TILES_PER_CTA - 1) / DTC_TILES_PER_CTA;
+    for (int k = 0; k <= lt.n_inst; ++k) lt.tile_begin[k] = k * per;
+    const int smem = 131072 + 65536 + 64;
+    e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dense_tc_kernel<<<lt.tile_begin[lt.n_inst], 128, smem, s>>>(d_inst, lt, spins, logZR);
+    return cudaGetLastError();
+  }
   max_d = TNVAN_MAX_D;
   if (dJ) {
     const int smem = (DJ_T * 256 * 2 + DJ_T * 16 + 8) * 4 + DJ_T * max_d;

@@ -211,3 +211,34 @@ def test_sampler_replay_sk_and_rrg():
             m = torch.as_tensor(same)
             lz = _oracle_logzr(g, W, s_or, beta)
             assert float((logZR[k * B:(k + 1) * B].cpu()[m] - lz[m]).abs().max()) / g.n <= TOL_FP32
+
+
+@pytest.mark.parametrize("case", ["sk_workload", "small_remainders"])
+def test_dense_block_bf16_tensor_cores(case):
+    if case == "sk_workload":
+        w = wl.workload(3)
+        graphs, Ws, betas = w.graphs, w.widths_sets, w.betas
+    else:
+        graphs, Ws = [], []
+        for n, nw, seed in [(20, 10, 1), (11, 8, 2), (9, 9, 3)]:
+            graphs.append(wl.sk(n, seed))
+            Ws.append(np.random.default_rng(seed).permutation(n)[:nw].astype(np.int32))
+        betas = [0.7, 1.3, 2.0]
+    model = _model(graphs, Ws, [16], betas)
+    B = 300  # three 128-sample tiles, the last one ragged
+    s_all, refs = [], []
+    for k in range(model.n):
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_or, _, _ = oracle_samples(p32, model.D[k], [16], 8, 0, k, B)
+        s_all.append(s_or.numpy().reshape(-1))
+        refs.append(dense.log_zr_dense(graphs[k].n, graphs[k].ei, graphs[k].ej, graphs[k].J, betas[k], Ws[k], s_or))
+    d_spins = to_dev_spins(np.concatenate(s_all))
+    logZR = torch.empty(model.n * B, dtype=torch.float64, device="cuda")
+    model.ctx.profile(True)
+    model.ctx.contract(model.betas, B, d_spins, tv.BF16, logZR)
+    torch.cuda.synchronize()
+    model.ctx.profile(False)
+    for k in range(model.n):
+        err = float((logZR[k * B:(k + 1) * B].cpu() - refs[k]).abs().max()) / graphs[k].n
+        print(f"{case} instance {k}: max |delta log Z_R| / N = {err:.2e}")
+        assert err <= 1e-3
