@@ -196,6 +196,25 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
                float* d_v, double lr, double beta1, double beta2, double eps, int64_t t,
                void* stream);
 
+/* Autotuner (not in the paper): times candidate launch shapes on a batch of
+ * `batch` samples drawn from the current networks -- the SIMT sampler's
+ * samples per CTA, the strip contraction's samples per CTA and the number of
+ * CTAs per instance of the fused BF16 backward -- with CUDA events on
+ * `stream`, and keeps the fastest in the context for later calls.  out (host
+ * int32[4], may be NULL) receives the choices (0 = heuristic, not tuned).
+ * Synchronous; allocates and frees temporary device buffers.
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM, TNVAN_E_CUDA. */
+int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision, void* stream,
+                   int32_t* out);
+
+/* Optional device step counter (not in the paper; for CUDA-graph capture).
+ * With d_counter non-NULL, every sampling launch uses the Philox step
+ * `step + *d_counter`, read on the device when the kernel runs, so a graph
+ * captured once draws fresh random numbers on each replay if the caller
+ * advances *d_counter between replays (e.g. inside the graph).  d_counter:
+ * borrowed device uint64; NULL restores host-only steps. */
+int tnvan_set_step_counter(tnvan_ctx* ctx, const uint64_t* d_counter);
+
 /* Per-kernel timing, a tracing aid (not in the paper).  enable = 1 clears the
  * records and starts bracketing every kernel launch of this context with a
  * pair of CUDA events on the launch stream; enable = 0 stops recording.

@@ -371,6 +371,7 @@ int check_ready(tnvan_ctx* ctx, bool need_made) {
 int fill_launch(tnvan_ctx* ctx, const double* betas, int batch, int tile, LaunchInfo& li) {
   memset(&li, 0, sizeof li);
   li.status = ctx->d_status;
+  li.step_dev = ctx->step_dev;
   li.n_inst = (int)ctx->inst.size();
   li.batch = batch;
   li.tile = tile;
@@ -393,6 +394,7 @@ int max_sample_smem(const tnvan_ctx* ctx, int tile) {
 }
 
 int pick_sample_tile(const tnvan_ctx* ctx) {
+  if (ctx->tune_sample_tile && max_sample_smem(ctx, ctx->tune_sample_tile) <= 227 * 1024) return ctx->tune_sample_tile;
   // largest tile that keeps two CTAs per SM, else the largest that fits
   for (int T : {64, 32})
     if (max_sample_smem(ctx, T) <= 113 * 1024) return T;
@@ -1189,7 +1191,7 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     // one CTA per chunk of 128-sample tiles, about one CTA per SM overall
     const int n_inst = (int)ctx->inst.size();
     const int tiles = (batch + 127) / 128;
-    const int ctas = std::max(1, std::min(tiles, (148 + n_inst - 1) / n_inst));
+    const int ctas = std::max(1, std::min(tiles, ctx->tune_bwd_ctas ? ctx->tune_bwd_ctas : (148 + n_inst - 1) / n_inst));
     const int per = (tiles + ctas - 1) / ctas;
     LaunchInfo lf;
     if ((rc = fill_launch(ctx, betas, batch, per, lf))) return rc;
@@ -1328,6 +1330,137 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
   return TNVAN_OK;
 }
 
+int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision, void* stream,
+                   int32_t* out) {
+  if (!ctx || batch < 1 || !betas) return ctx ? fail(ctx, TNVAN_E_ARG, "bad autotune arguments") : TNVAN_E_ARG;
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  long long spins_n = 0, params_n = 0;
+  for (const Instance& in : ctx->inst) {
+    spins_n += (long long)batch * (long long)in.W.size();
+    params_n += in.n_params;
+  }
+  const int n = (int)ctx->inst.size();
+  int8_t* sp = nullptr;
+  float *lq = nullptr, *gr = nullptr;
+  double* lz = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (sp) cudaFree(sp);
+    if (lq) cudaFree(lq);
+    if (gr) cudaFree(gr);
+    if (lz) cudaFree(lz);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&sp, spins_n) != cudaSuccess || cudaMalloc(&lq, sizeof(float) * n * batch) != cudaSuccess ||
+      cudaMalloc(&lz, sizeof(double) * n * batch) != cudaSuccess ||
+      cudaMalloc(&gr, sizeof(float) * params_n) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return fail(ctx, TNVAN_E_NOMEM, "autotune buffers");
+  }
+  // time fn: one warm-up call, then the mean of three
+  auto time_it = [&](auto fn, float* ms) -> int {
+    int r = fn();
+    if (r) return r;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < 3; ++i)
+      if ((r = fn())) return r;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    return TNVAN_OK;
+  };
+  auto sample = [&]() { return tnvan_sample_and_contract(ctx, betas, batch, 1, 0, precision, sp, lq, lz, stream); };
+  bool tc_sampler = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) tc_sampler = tc_sampler && in.dev.made.sample_tc_ok;
+  if (!tc_sampler) {
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int T : {16, 32, 64}) {
+      if (max_sample_smem(ctx, T) > 227 * 1024) continue;
+      ctx->tune_sample_tile = T;
+      float ms = 0.f;
+      if ((rc = time_it(sample, &ms))) {
+        cleanup();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = T;
+      }
+    }
+    ctx->tune_sample_tile = best;
+  }
+  if ((rc = sample())) {  // spins for the contraction and backward candidates
+    cleanup();
+    return rc;
+  }
+  bool any_strip = false;
+  for (const Instance& in : ctx->inst) any_strip = any_strip || in.kind == 0;
+  if (any_strip) {
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int T : {32, 64, 128}) {
+      ctx->tune_strip_tile = T;
+      float ms = 0.f;
+      auto contract = [&]() { return tnvan_contract(ctx, betas, batch, sp, precision, lz, nullptr, stream); };
+      if ((rc = time_it(contract, &ms))) {
+        cleanup();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = T;
+      }
+    }
+    ctx->tune_strip_tile = best;
+  }
+  bool fused = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) fused = fused && in.dev.made.fused_ok;
+  if (fused) {
+    int best = 0;
+    float best_ms = 1e30f;
+    const int base = (148 + n - 1) / n;
+    for (int c : {base / 2, base, 2 * base, 4 * base}) {
+      if (c < 1) continue;
+      ctx->tune_bwd_ctas = c;
+      float ms = 0.f;
+      auto bwd = [&]() {
+        return tnvan_backward(ctx, betas, batch, sp, lz, lq, precision, gr, nullptr, nullptr, stream);
+      };
+      if ((rc = time_it(bwd, &ms))) {
+        cleanup();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    ctx->tune_bwd_ctas = best;
+  }
+  if (out) {
+    out[0] = ctx->tune_sample_tile;
+    out[1] = ctx->tune_strip_tile;
+    out[2] = ctx->tune_bwd_ctas;
+    out[3] = 0;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  return TNVAN_OK;
+}
+
+int tnvan_set_step_counter(tnvan_ctx* ctx, const uint64_t* d_counter) {
+  if (!ctx) return TNVAN_E_ARG;
+  ctx->step_dev = reinterpret_cast<const unsigned long long*>(d_counter);
+  return TNVAN_OK;
+}
+
 int tnvan_profile(tnvan_ctx* ctx, int enable) {
   if (!ctx) return TNVAN_E_ARG;
   DeviceGuard g(ctx->device);
@@ -1420,12 +1553,13 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     k1 |= in.kind == 1;
     k2 |= in.kind == 2;
   }
+  const int stile = ctx->tune_strip_tile ? ctx->tune_strip_tile : 128;
   LaunchInfo li;
-  if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
+  if ((rc = fill_launch(ctx, betas, batch, stile, li))) return rc;
   if (k0) {
     int sm = 0;
     for (const Instance& in : ctx->inst)
-      if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, 128));
+      if (in.kind == 0) sm = std::max(sm, strip_smem_bytes(in, stile));
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "strip tables need %d B of shared memory", sm);
     PROF(d_dbeta ? (d_logZR ? "strips+dbeta" : "strips_dbeta") : "strips", s);
     CK(launch_strips(ctx->d_inst, li, sm, d_spins, d_logZR, d_dbeta, s), "strip kernel");

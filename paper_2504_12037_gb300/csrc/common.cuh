@@ -15,6 +15,12 @@ __device__ __forceinline__ int find_inst(const LaunchInfo& li, int blk) {
   return k;
 }
 
+// Philox step of a launch: the host value plus the optional device counter
+// (lets a captured CUDA graph draw new numbers on every replay).
+__device__ __forceinline__ uint32_t launch_step(const LaunchInfo& li) {
+  return (uint32_t)(li.step + (li.step_dev ? *li.step_dev : 0ull));
+}
+
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 round function
 // with the Weyl key schedule.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {

@@ -144,6 +144,7 @@ struct LaunchInfo {
   int tile;  // samples per CTA
   unsigned long long seed, step;
   int* status;  // device status word: nonzero after a bounded wait gave up
+  const unsigned long long* step_dev;  // optional device step counter added to `step`
   double beta[TNVAN_MAX_INST];
   int tile_begin[TNVAN_MAX_INST + 1];
 };
@@ -198,6 +199,9 @@ struct tnvan_prof_rec {
 
 struct tnvan_ctx {
   int device = 0;
+  const unsigned long long* step_dev = nullptr;  // tnvan_set_step_counter
+  // autotuned launch shapes (0 = built-in heuristic)
+  int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0;
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;

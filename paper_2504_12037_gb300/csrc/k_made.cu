@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(64) sample_kernel(const InstDev* __restrict__ 
   const float* biaso = md.packed + md.layer[nh].dst_off + (long long)D * md.Hl;
   const int* cL = nh == 1 ? md.c1 : md.c2;
   const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
+  const uint32_t step32 = launch_step(li);
   const int8_t* gv = given ? given + I.spin_units * li.batch + (long long)b * D : nullptr;
   const bool valid = b < li.batch;
   if (t == 0) mbar_init(bar, 1);
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(64) sample_kernel(const InstDev* __restrict__ 
     for (int i = i0; i < i1; ++i) {
       if ((i & 3) == 0)
         rnd = philox4x32_10(
-            make_uint4((uint32_t)b, (uint32_t)(i >> 2), (uint32_t)li.step, (uint32_t)k), key);
+            make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
       if (nh >= 1 && i >= 1) {
         for (int u = md.c1[i - 1]; u < md.c1[i]; ++u) {
           const float* w = TW1 + (u - u1lo) * gi;

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(128, 1) sample_tc_kernel(const InstDev* __rest
   const uint32_t lane_off = (uint32_t)(w * 32) << 16;
   const uint32_t id1 = tc::idesc(128, H1, 1u), id2 = tc::idesc(128, H2, 1u), ido = tc::idesc(128, D, 1u);
   const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
+  const uint32_t step32 = launch_step(li);
   const int8_t* gv = given ? given + I.spin_units * li.batch + (long long)b * D : nullptr;
   uint32_t phase = 0;
   bool init1 = false, init2 = false, inito = false;  // accumulator written by a fold yet
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(128, 1) sample_tc_kernel(const InstDev* __rest
     // in-group steps
     for (int i = i0; i < i1; ++i) {
       if ((i & 3) == 0)
-        rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), (uint32_t)li.step, (uint32_t)k), key);
+        rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
       const int q = i - i0;  // gc*[q] = c*[i-1], gc*[q+1] = c*[i]
       if (i >= 1) {
         const int ua = gc1[q], ub = gc1[q + 1];

@@ -45,6 +45,8 @@ SIGNATURES = {
     "tnvan_adam": (_c_int, [_vp, _c_i64, _vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "tnvan_free_energy_noalloc": (_c_int, [_c_int, _c_int, _dblp, _vp, _vp, _vp, _vp]),
     "tnvan_noalloc_last_error": (ctypes.c_char_p, []),
+    "tnvan_set_step_counter": (_c_int, [_vp, _vp]),
+    "tnvan_autotune": (_c_int, [_vp, _dblp, _c_int, _c_int, _vp, _i32p]),
     "tnvan_profile": (_c_int, [_vp, _c_int]),
     "tnvan_profile_read": (_c_int, [_vp, _c_int, ctypes.c_char_p, _c_int, _dblp, _i64p]),
 }
@@ -180,6 +182,17 @@ class Context:
         b, pb = _arr(betas, np.float64)
         self._check(lib().tnvan_backward(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq), precision,
                                          _ptr(grad), _ptr(dlogZR_dbeta), _ptr(dlogZR_dJ), _stream(stream)))
+
+    def set_step_counter(self, counter):
+        self._check(lib().tnvan_set_step_counter(self._h, None if counter is None else _ptr(counter)))
+
+    def autotune(self, betas, batch: int, precision: int, stream=None):
+        """Time candidate launch shapes on a synthetic batch and keep the fastest;
+        returns the chosen (sampler tile, strip tile, backward CTAs)."""
+        b, pb = _arr(betas, np.float64)
+        out = (ctypes.c_int32 * 4)()
+        self._check(lib().tnvan_autotune(self._h, pb, batch, precision, _stream(stream), out))
+        return tuple(out[:3])
 
     def profile(self, enable: bool):
         self._check(lib().tnvan_profile(self._h, int(enable)))

@@ -1,0 +1,79 @@
+"""CUDA-graph capture of the sampling + contraction + backward calls with a
+device step counter, and the autotuner (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2504_12037_gb300 import tnvan as tv
+from paper_2504_12037_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _model(cfg, n=None):
+    from paper_2504_12037_gb300.model import TNVAN
+
+    w = wl.workload(cfg)
+    n = len(w.graphs) if n is None else n
+    return w, TNVAN(w.graphs[:n], w.widths_sets[:n], w.hidden, w.betas[:n], seed=2)
+
+
+@pytest.mark.parametrize("prec", [tv.FP32, tv.BF16])
+def test_graph_replay_matches_eager_and_advances(prec):
+    w, m = _model(2, n=2)
+    B = 1000
+    m.ctx.reserve(B)
+    out = m.buffers(B)
+    grad = torch.empty_like(m.params)
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    m.ctx.set_step_counter(counter)
+
+    def step():
+        m.ctx.sample_and_contract(m.betas, B, 77, 0, prec, *out)
+        m.ctx.backward(m.betas, B, out[0], out[2], out[1], prec, grad)
+
+    step()  # warm-up outside capture (workspaces, descriptors)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+        counter.add_(1)
+    counter.fill_(5)
+    g.replay()
+    torch.cuda.synchronize()
+    spins_g, logq_g, lz_g = (x.clone() for x in out)
+    grad_g = grad.clone()
+    assert int(counter.item()) == 6
+    g.replay()
+    torch.cuda.synchronize()
+    assert not torch.equal(out[0], spins_g)  # a new step, new draws
+    # eager call with the same effective step (counter 5 + host step 0)
+    m.ctx.set_step_counter(None)
+    ref = m.buffers(B)
+    m.ctx.sample_and_contract(m.betas, B, 77, 5, prec, *ref)
+    grad_e = torch.empty_like(grad)
+    m.ctx.backward(m.betas, B, ref[0], ref[2], ref[1], prec, grad_e)
+    torch.cuda.synchronize()
+    assert torch.equal(ref[0], spins_g)
+    assert torch.equal(ref[1], logq_g)
+    assert torch.equal(ref[2], lz_g)
+    assert torch.allclose(grad_e, grad_g, rtol=0, atol=0)
+
+
+def test_autotune_picks_valid_shapes_and_results_unchanged():
+    w, m = _model(2, n=2)
+    B = 2048
+    out0 = m.buffers(B)
+    m.ctx.sample_and_contract(m.betas, B, 3, 1, tv.FP32, *out0)
+    torch.cuda.synchronize()
+    choice = m.ctx.autotune(m.betas, B, tv.FP32)
+    assert choice[0] in (16, 32, 64) and choice[1] in (32, 64, 128)
+    out1 = m.buffers(B)
+    m.ctx.sample_and_contract(m.betas, B, 3, 1, tv.FP32, *out1)
+    torch.cuda.synchronize()
+    # launch shapes change the schedule, not the arithmetic per sample
+    assert torch.equal(out0[0], out1[0])
+    assert torch.allclose(out0[1], out1[1], rtol=0, atol=1e-5)
+    assert torch.equal(out0[2], out1[2])
+    choice_bf = m.ctx.autotune(m.betas, B, tv.BF16)
+    assert choice_bf[2] >= 1
