@@ -38,7 +38,7 @@ SM_MAX_MHZ = 2070.0
 MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the same kernels on the same workload (see profiles/); None if not captured
-NCU_TRAFFIC = {"sample_tc": 479488, "bwd_fused": 6685696}
+NCU_TRAFFIC = {"sample_tc": 478976, "bwd_fused": 6690048}
 
 
 def args_():
@@ -51,6 +51,8 @@ def args_():
                     help="headline mode (bf16: network on the tensor cores, contractions FP32)")
     ap.add_argument("--compare", default="fp32", help="second mode timed beside the headline ('' = none)")
     ap.add_argument("--acc-steps", type=int, default=150, help="training steps before the accuracy estimate")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -169,9 +171,11 @@ def run_ours(a):
     def timed(mode: int, steps: int, warmup: int, sample_clocks: bool):
         model = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
         model.ctx.reserve(B)
+        tuned = None if a.no_autotune else model.ctx.autotune(model.betas, B, mode)
         bufs = model.buffers(B)
         dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
         dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+        model.tuned = tuned
 
         def step(i):
             model.train_step(B, seed, i, mode, 0.01, bufs, dbeta, dJ, stream)
@@ -216,6 +220,39 @@ def run_ours(a):
         _, _, _, _, _, ms_c, prof_c, _ = timed(PREC[a.compare], a.steps, a.warmup, False)
         compare = {"precision": a.compare, "value": samples_step / (ms_c / 1e3), "ms_per_step": ms_c,
                    "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof_c.items()}}
+
+    # ----- the same step as one CUDA-graph replay (device step counter) -----
+    graph = None
+    if not a.no_graph:
+        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+        model.ctx.set_step_counter(counter)
+        gstream = torch.cuda.Stream()
+        gstream.wait_stream(stream)
+        with torch.cuda.stream(gstream):
+            model.train_step(B, seed, 0, prec, 0.01, (spins, logq, logZR), dbeta, dJ, gstream)
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=gstream):
+            model.train_step(B, seed, 0, prec, 0.01, (spins, logq, logZR), dbeta, dJ, gstream)
+            counter.add_(1)
+        for _ in range(a.warmup):
+            cg.replay()
+        torch.cuda.synchronize()
+        gs = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+        ge = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+        for i in range(a.steps):
+            flush.zero_()
+            gs[i].record(stream)
+            cg.replay()
+            ge[i].record(stream)
+        torch.cuda.synchronize()
+        ms_g = sum(x.elapsed_time(y) for x, y in zip(gs, ge)) / a.steps
+        tg = torch.tensor([ms_g], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tg, op=dist.ReduceOp.MAX)
+        graph = {"value": samples_step / (float(tg.item()) / 1e3), "ms_per_step": float(tg.item()),
+                 "note": "whole training step captured once, replayed; Philox step from a device counter"}
+        model.ctx.set_step_counter(None)
 
     # ----- end to end through the public API with host buffers -----
     h_spins = torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True)
@@ -299,6 +336,9 @@ def run_ours(a):
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * a.steps)),
         "roofline": roofline, "kernels": kernels, "compare": compare, "accuracy": accuracy,
+        "graph": graph, "autotuned": {"sample_tile": None if not model.tuned else model.tuned[0],
+                                      "strip_tile": None if not model.tuned else model.tuned[1],
+                                      "bwd_ctas_per_instance": None if not model.tuned else model.tuned[2]},
     }
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
