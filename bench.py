@@ -291,7 +291,7 @@ def run_ours(a):
         "strips": strips * strip_flops(3, 16),
         "strips+dbeta": strips * 2 * strip_flops(3, 16),
         "strips_dbeta": strips * 2 * strip_flops(3, 16),
-        "strips_dJ": strips * 5 * strip_flops(3, 16),
+        "strips_adj": strips * 6 * strip_flops(3, 16),  # d/dbeta forward sweep (2x) + backward sweep (4x)
     }
     flop_launch = per_sample.get(dom_name, float("nan")) * n_inst * B
     achieved = flop_launch / (dom_ms / dom_n / 1e3) / 1e12 if dom_n else float("nan")
@@ -338,7 +338,8 @@ def run_ours(a):
         "roofline": roofline, "kernels": kernels, "compare": compare, "accuracy": accuracy,
         "graph": graph, "autotuned": {"sample_tile": None if not model.tuned else model.tuned[0],
                                       "strip_tile": None if not model.tuned else model.tuned[1],
-                                      "bwd_ctas_per_instance": None if not model.tuned else model.tuned[2]},
+                                      "bwd_ctas_per_instance": None if not model.tuned else model.tuned[2],
+                                      "strip_adjoint_tile": None if not model.tuned else model.tuned[3]},
     }
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)

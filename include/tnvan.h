@@ -198,10 +198,11 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
 
 /* Autotuner (not in the paper): times candidate launch shapes on a batch of
  * `batch` samples drawn from the current networks -- the SIMT sampler's
- * samples per CTA, the strip contraction's samples per CTA and the number of
- * CTAs per instance of the fused BF16 backward -- with CUDA events on
- * `stream`, and keeps the fastest in the context for later calls.  out (host
- * int32[4], may be NULL) receives the choices (0 = heuristic, not tuned).
+ * samples per CTA, the strip contraction's samples per CTA, the number of
+ * CTAs per instance of the fused BF16 backward and the strip adjoint's
+ * samples per CTA -- with CUDA events on `stream`, and keeps the fastest in
+ * the context for later calls.  out (host int32[4], may be NULL) receives the
+ * choices in that order (0 = heuristic, not tuned).
  * Synchronous; allocates and frees temporary device buffers.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM, TNVAN_E_CUDA. */
 int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision, void* stream,

@@ -404,8 +404,47 @@ int pick_sample_tile(const tnvan_ctx* ctx) {
 }
 
 
+// Launch shape of the strip adjoint: samples per CTA T in {128, 96, 64, 32}.
+// The left vectors of a strip take L 2^w T floats of shared memory, so T
+// sets the CTAs per SM; the default minimises (waves of CTAs) x (work an SM
+// does per wave) / (its issue rate, taken as saturating at 8 warps).  An
+// autotuned T (tnvan_autotune) takes precedence when it fits.
+int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats) {
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (n_sm < 1) n_sm = 1;
+  double best = 1e300;
+  *tile = 0;
+  for (int T : {128, 96, 64, 32}) {
+    int sm = 0, lv = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 0) lv = std::max(lv, strip_adj_lv_floats(in, T));
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 0) sm = std::max(sm, strip_adj_smem_bytes(in, T, lv));
+    if (sm > 227 * 1024) continue;
+    const int nb = strips_adj_occupancy(T, sm);
+    if (nb < 1) continue;
+    long long ctas = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 0) ctas += (batch + T - 1) / T;
+    const double waves = ceil((double)ctas / ((double)nb * n_sm));
+    const double warps = nb * T / 32.0;
+    const double cost = waves * nb * T / std::min(1.0, warps / 8.0);
+    const bool forced = ctx->tune_adj_tile == T;
+    if (forced || cost < best) {
+      best = cost;
+      *tile = T;
+      *smem = sm;
+      *lv_floats = lv;
+    }
+    if (forced) break;
+  }
+  if (!*tile) return fail(ctx, TNVAN_E_UNSUPPORTED, "strip adjoint needs more than 227 KB of shared memory");
+  return TNVAN_OK;
+}
+
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
-                 int precision, double* d_logZR, double* d_dbeta, cudaStream_t s);
+                 int precision, double* d_logZR, double* d_dbeta, cudaStream_t s, bool strips = true);
 int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s);
@@ -1167,12 +1206,17 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (d_dJ)
-    for (const Instance& in : ctx->inst) {
-      if (in.kind == 0)
-        for (const StripDev& sd : in.strip.strips)
-          if (sd.L > 64) return fail(ctx, TNVAN_E_UNSUPPORTED, "d/dJ supports strips of at most 64 rows (got %d)", sd.L);
-    }
+  // the strip adjoint (d/dbeta and d/dJ of strip instances in one pass) keeps
+  // a strip's left vectors in shared memory: 128, 64 or 32 samples per CTA
+  bool any_strip = false, other = false;
+  for (const Instance& in : ctx->inst) {
+    if (in.kind == 0) any_strip = true;
+    else other = true;
+  }
+  int adj_tile = 0, adj_smem = 0, adj_lv = 0;
+  if (any_strip && (d_dbeta || d_dJ)) {
+    if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv))) return rc;
+  }
   long long max_elems = 0;
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
   LaunchInfo li;
@@ -1248,38 +1292,37 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
          "gradient reduce kernel");
     }
   }
-  if (d_dbeta) {
-    // forward-mode d/dbeta: a second contraction pass that writes only the derivative
-    if ((rc = contract_all(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, s))) return rc;
-  }
   if (d_dJ) {
     long long ne = 0;
     for (const Instance& in : ctx->inst) ne += in.m;
     CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
+  }
+  if (d_dbeta && other) {
+    // forward-mode d/dbeta of dense and elimination instances: a second
+    // contraction pass that writes only the derivative
+    if ((rc = contract_all(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, s, false))) return rc;
+  }
+  if (adj_tile) {
+    LaunchInfo la;
+    if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
+    int max_edges = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 0) max_edges = std::max(max_edges, in.m);
+    const int stride = (max_edges + 3) & ~3;
+    if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
+    PROF(d_dJ ? "strips_adj" : "strips_dbeta", s);
+    CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_dbeta, d_dJ ? ctx->d_dj_part : nullptr,
+                         stride, d_dJ, s),
+       "strip adjoint kernel");
+  }
+  if (d_dJ) {
     LaunchInfo lt;
     if ((rc = fill_launch(ctx, betas, batch, 128, lt))) return rc;
-    {
-      PROF("ww_dJ", s);
-      CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
-    }
-    bool any_strip = false, other = false;
-    for (const Instance& in : ctx->inst) {
-      if (in.kind == 0) any_strip = true;
-      else other = true;
-    }
-    if (any_strip) {
-      int sm = 0, max_edges = 0;
-      for (const Instance& in : ctx->inst)
-        if (in.kind == 0) {
-          sm = std::max(sm, strip_smem_bytes(in, 128) + 4 * in.m);
-          max_edges = std::max(max_edges, in.m);
-        }
-      const int stride = (max_edges + 3) & ~3;
-      if ((rc = ensure_dj_part(ctx, (size_t)lt.tile_begin[lt.n_inst] * stride))) return rc;
-      PROF("strips_dJ", s);
-      CK(launch_strips_dJ(ctx->d_inst, lt, sm, d_spins, ctx->d_dj_part, stride, d_dJ, s), "strip adjoint kernel");
-    }
     if (other) {
+      {
+        PROF("ww_dJ", s);
+        CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
+      }
       {
         PROF("dense_dJ", s);
         CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
@@ -1443,11 +1486,41 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     }
     ctx->tune_bwd_ctas = best;
   }
+  if (any_strip) {
+    long long ne = 0;
+    for (const Instance& in : ctx->inst) ne += in.m;
+    double* dj = nullptr;
+    if (cudaMalloc(&dj, sizeof(double) * std::max(ne, 1LL)) != cudaSuccess) {
+      cleanup();
+      return fail(ctx, TNVAN_E_NOMEM, "autotune buffers");
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int T : {128, 96, 64, 32}) {
+      ctx->tune_adj_tile = T;
+      int t_used = 0, sm = 0, lv = 0;
+      if (plan_strip_adjoint(ctx, batch, &t_used, &sm, &lv) || t_used != T) continue;
+      float ms = 0.f;
+      auto adj = [&]() { return tnvan_backward(ctx, betas, batch, sp, lz, lq, precision, gr, nullptr, dj, stream); };
+      if ((rc = time_it(adj, &ms))) {
+        cudaFree(dj);
+        cleanup();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = T;
+      }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(dj);
+    ctx->tune_adj_tile = best;
+  }
   if (out) {
     out[0] = ctx->tune_sample_tile;
     out[1] = ctx->tune_strip_tile;
     out[2] = ctx->tune_bwd_ctas;
-    out[3] = 0;
+    out[3] = ctx->tune_adj_tile;
   }
   cudaError_t e = cudaStreamSynchronize(s);
   cleanup();
@@ -1545,11 +1618,11 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
 }
 
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
-                 int precision, double* d_logZR, double* d_dbeta, cudaStream_t s) {
+                 int precision, double* d_logZR, double* d_dbeta, cudaStream_t s, bool strips) {
   int rc;
   bool k0 = false, k1 = false, k2 = false;
   for (const Instance& in : ctx->inst) {
-    k0 |= in.kind == 0;
+    k0 |= in.kind == 0 && strips;
     k1 |= in.kind == 1;
     k2 |= in.kind == 2;
   }

@@ -201,7 +201,7 @@ struct tnvan_ctx {
   int device = 0;
   const unsigned long long* step_dev = nullptr;  // tnvan_set_step_counter
   // autotuned launch shapes (0 = built-in heuristic)
-  int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0;
+  int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0, tune_adj_tile = 0;
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
@@ -218,7 +218,7 @@ struct tnvan_ctx {
   int reserved_batch = 0;
   float* d_grad_packed = nullptr;    // packed-layout gradient partials
   size_t grad_packed_floats = 0;
-  float* d_dj_part = nullptr;        // strip d/dJ partial rows [CTA][max edges]
+  float* d_dj_part = nullptr;        // d/dJ partial rows [CTA][max edges]
   size_t dj_part_floats = 0;
 };
 
@@ -232,8 +232,9 @@ cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_
                           int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);
 cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           const int8_t* spins, double* logZR, double* dbeta, cudaStream_t s);
-cudaError_t launch_strips_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
-                             const int8_t* spins, float* part, int part_stride, double* dJ, cudaStream_t s);
+cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
+                              const int8_t* spins, double* dbeta, float* part, int part_stride, double* dJ,
+                              cudaStream_t s);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s);
@@ -271,5 +272,8 @@ cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* 
 int sample_smem_bytes(const Instance& in, int tile);
 int general_smem_bytes(int arena, int pairs, int D, int T, bool db);
 int strip_smem_bytes(const Instance& in, int tile);
+int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats);
+int strip_adj_lv_floats(const Instance& in, int tile);
+int strips_adj_occupancy(int tile, int smem_bytes);
 
 }  // namespace tnvan

@@ -19,23 +19,57 @@ namespace tnvan {
 //   diag  [L][4][2^w]   D_y for the 4 combinations of (s_L, s_R) signs
 //   ddiag [L][4][2^w]   d D_y / d beta
 //   pos   [L][2] int    AR positions of the left / right W neighbours (-1 none)
+// The adjoint kernel stores the same tables without ddiag, strip after strip.
 __host__ __device__ inline int strip_tab_floats(int w, int L) {
   int n = L * w * 4 + 2 * L * 4 * (1 << w) + 2 * L;
   return (n + 3) & ~3;
 }
+// The adjoint's tables carry no ddiag.
+__host__ __device__ inline int strip_tab_floats_adj(int w, int L) {
+  int n = L * w * 4 + L * 4 * (1 << w) + 2 * L;
+  return (n + 3) & ~3;
+}
+
+struct StripTab {
+  const float4* vert;
+  const float* diag;
+  const float* ddiag;  // nullptr in the adjoint's layout
+  const int* pos;
+};
+
+__device__ __forceinline__ StripTab strip_tab_at(const float* tab, int w, int L, bool with_ddiag) {
+  StripTab s;
+  const int nd = L * 4 * (1 << w);
+  s.vert = reinterpret_cast<const float4*>(tab);
+  s.diag = tab + L * w * 4;
+  s.ddiag = with_ddiag ? s.diag + nd : nullptr;
+  s.pos = reinterpret_cast<const int*>(s.diag + (with_ddiag ? 2 * nd : nd));
+  return s;
+}
+
+// Float offset of strip st's tables: the host-planned offset, or (adjoint
+// layout) the running sum of strip_tab_floats_adj over the earlier strips.
+__device__ __forceinline__ int strip_tab_offset(const InstDev& I, int st, bool with_ddiag) {
+  if (with_ddiag) return I.strips[st].tab_off;
+  int off = 0;
+  for (int j = 0; j < st; ++j) off += strip_tab_floats_adj(I.strips[j].w, I.strips[j].L);
+  return off;
+}
 
 __device__ __forceinline__ float spin_of(int x, int c) { return ((x >> c) & 1) ? -1.f : 1.f; }
 
-__device__ void build_strip_tables(const InstDev& I, float beta, float* sm, int t, int T) {
+__device__ void build_strip_tables(const InstDev& I, float beta, float* sm, int t, int T, bool with_ddiag = true) {
   for (int st = 0; st < I.n_strips; ++st) {
     const StripDev sd = I.strips[st];
-    const int w = sd.w, L = sd.L, nx = 1 << w;
-    float* tab = sm + sd.tab_off;
-    float4* vert = reinterpret_cast<float4*>(tab);
-    float* diag = tab + L * w * 4;
-    float* ddiag = diag + L * 4 * nx;
-    int* pos = reinterpret_cast<int*>(ddiag + L * 4 * nx);
+    const int w = sd.w, L = sd.L;
+    float* tab = sm + strip_tab_offset(I, st, with_ddiag);
+    const StripTab tb = strip_tab_at(tab, w, L, with_ddiag);
+    float4* vert = const_cast<float4*>(tb.vert);
+    float* diag = const_cast<float*>(tb.diag);
+    float* ddiag = const_cast<float*>(tb.ddiag);
+    int* pos = const_cast<int*>(tb.pos);
     const StripRow* rows = I.rows + sd.row0;
+    const int nx = 1 << w;
     for (int e = t; e < L * 4 * nx; e += T) {
       const int x = e % nx, idx = (e / nx) & 3, y = e / (4 * nx);
       const StripRow& R = rows[y];
@@ -54,7 +88,7 @@ __device__ void build_strip_tables(const InstDev& I, float beta, float* sm, int 
       }
       const float d = expf(beta * (ex - ch));
       diag[e] = d;
-      ddiag[e] = d * (ex - ch);
+      if (ddiag) ddiag[e] = d * (ex - ch);
     }
     for (int e = t; e < L * w; e += T) {
       const int y = e / w, c = e % w;
@@ -97,19 +131,22 @@ __device__ __forceinline__ int row_index(const int* pos, int y, const int8_t* sr
 
 // Contract one strip for one sample.  Returns ln Z_strip - beta*c_hat as
 // (float mantissa part, integer power-of-two exponent) and d/dbeta of it.
-template <int W, bool DB>
-__device__ void strip_chain(const float* tab, int L, const int8_t* srow, double& lnz, float& dl) {
+// With SAVE, row y's renormalised left vector is also written to
+// lvs[(y * 2^W + x) * T + t] (the adjoint's backward sweep reads it).
+template <int W, bool DB, bool SAVE = false>
+__device__ void strip_chain(const StripTab& tb, int L, const int8_t* srow, double& lnz, float& dl,
+                            float* lvs = nullptr, int t = 0, int T = 0) {
   constexpr int NX = 1 << W;
-  const float4* vert = reinterpret_cast<const float4*>(tab);
-  const float* diag = tab + L * W * 4;
-  const float* ddiag = diag + L * 4 * NX;
-  const int* pos = reinterpret_cast<const int*>(ddiag + L * 4 * NX);
+  const float4* vert = tb.vert;
+  const float* diag = tb.diag;
+  const float* ddiag = tb.ddiag;
+  const int* pos = tb.pos;
   float v[NX], g[NX];
   int e2 = 0;
   for (int y = 0; y < L; ++y) {
     const int idx = row_index(pos, y, srow);
     const float* dy = diag + (y * 4 + idx) * NX;
-    const float* gy = ddiag + (y * 4 + idx) * NX;
+    const float* gy = DB ? ddiag + (y * 4 + idx) * NX : dy;
     if (y == 0) {
 #pragma unroll
       for (int x = 0; x < NX; ++x) {
@@ -134,6 +171,7 @@ __device__ void strip_chain(const float* tab, int L, const int8_t* srow, double&
     for (int x = 0; x < NX; ++x) {
       v[x] *= sc;
       if (DB) g[x] *= sc;
+      if (SAVE) lvs[(y * NX + x) * T + t] = v[x];
     }
     e2 += e;
   }
@@ -183,14 +221,14 @@ __global__ void __launch_bounds__(128) strips_kernel(const InstDev* __restrict__
   double lz = 0.0, dl = 0.0, chat = 0.0;
   for (int st = 0; st < I.n_strips; ++st) {
     const StripDev& sd = I.strips[st];
-    const float* tab = sm + sd.tab_off;
+    const StripTab tb = strip_tab_at(sm + sd.tab_off, sd.w, sd.L, true);
     double l = 0.0;
     float d = 0.f;
     switch (sd.w) {
-      case 1: strip_chain<1, DB>(tab, sd.L, srow, l, d); break;
-      case 2: strip_chain<2, DB>(tab, sd.L, srow, l, d); break;
-      case 3: strip_chain<3, DB>(tab, sd.L, srow, l, d); break;
-      default: strip_chain<4, DB>(tab, sd.L, srow, l, d); break;
+      case 1: strip_chain<1, DB>(tb, sd.L, srow, l, d); break;
+      case 2: strip_chain<2, DB>(tb, sd.L, srow, l, d); break;
+      case 3: strip_chain<3, DB>(tb, sd.L, srow, l, d); break;
+      default: strip_chain<4, DB>(tb, sd.L, srow, l, d); break;
     }
     lz += l;
     dl += d;
@@ -232,105 +270,169 @@ cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_
 }
 
 // ---------------------------------------------------------------------------
-// Reverse mode: d ln Z_strip / d J_e = beta <s_i s_j> (bonds inside the strip)
-// or beta s_W <s_i> (bonds to a W neighbour), from stored left vectors and a
-// backward sweep of right vectors.  Accumulates (beta / batch) * value into
-// dJ[edge] (batch mean), one atomic per bond per warp.
+// Strip adjoint, fused.  For every sample, one forward sweep (the chain of
+// strips_kernel) keeps each row's renormalised left vector in shared
+// memory; one backward sweep of right vectors then gives every bond's local
+// expectation:
+//   d ln Z_strip / d J_e = beta <s_i s_j>   (bonds inside the strip)
+//                        = beta s_W <s_i>   (bonds to a W neighbour),
+// and the W-W bonds add d(-beta E_1)/d J_e = beta s_a s_b (Eq. 4
+// differentiated), and d log Z_R / d beta = sum_e J_e <.>_e - E_1(s) per
+// sample.  Batch sums are formed per CTA in shared memory, one row
+// of accumulators per warp so that the order of additions is fixed, and
+// strips_dJ_reduce_kernel adds the CTA rows in CTA order.
 // ---------------------------------------------------------------------------
-#define STRIP_DJ_LMAX 64
 
-// Warp-sum a bond contribution and add it to the CTA's shared accumulator.
-__device__ __forceinline__ void acc_bond(float* acc, int e, float val, bool lane0) {
-  const float s = warp_sum(val);
-  if (lane0 && e >= 0) atomicAdd(acc + e, s);
+// Sum NV per-lane values (NV a power of two, at most 32) over the warp by a
+// transpose reduction: NV - 1 exchanges halve the values each lane holds,
+// then log2(32 / NV) exchanges finish the sums.  On return the lanes with
+// lane % (32 / NV) == 0 each hold the warp total of value number `idx`.
+template <int NV>
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[NV], int lane, int& idx) {
+  idx = 0;
+#pragma unroll
+  for (int h = NV / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
+    const bool up = (lane & m) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float send = up ? v[j] : v[j + h];
+      const float keep = up ? v[j + h] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+    if (up) idx += h;
+  }
+  float s = v[0];
+#pragma unroll
+  for (int m = 16 / NV; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  return s;
 }
 
+// Edge id of bond slot j of a strip row: W-1 horizontal, left, right, W vertical.
+__device__ __forceinline__ int row_edge(const StripRow& R, int W, int j) {
+  if (j < W - 1) return R.eh[j];
+  if (j == W - 1) return R.eL;
+  if (j == W) return R.eR;
+  return R.ev[j - W - 1];
+}
+
+// Backward sweep of one strip for one sample (all 32 lanes of the warp take
+// part; `valid` zeroes the contribution of padding samples).  Adds each
+// bond's local expectation to the warp's accumulators and returns
+// d ln Z_strip / d beta = sum_e J_e <.>_e: every Boltzmann weight depends on
+// beta only through beta J_e, so the same expectations give the beta
+// derivative.
+//
+// Row y, with left vector l (rows 0..y, D_y included) and right vector
+// r = r_{y+1}: the message m = V_y r, P = l * m, Z = sum P.  For the vertical
+// bond of column c, with L_c = V_0..V_{c-1} l and R_c = V_{c+1}..V_{W-1} r,
+//   Z <s_c s'_c> = L_c^T V'_c R_c,  V'_c = [[a, -b], [-b, a]] on bit c,
+// so the W vertical bonds share 2W - 1 Kronecker-factor applications.
 template <int W>
-__device__ void strip_dJ(const float* tab, const StripRow* __restrict__ rows, int L,
-                         const int8_t* srow, bool valid, float scale, float* dJ, bool lane0) {
+__device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict__ rows, int L,
+                                 const int8_t* srow, const float* lvs, int t, int T, bool valid,
+                                 float* accw, int lane) {
   constexpr int NX = 1 << W;
-  const float4* vert = reinterpret_cast<const float4*>(tab);
-  const float* diag = tab + L * W * 4;
-  const int* pos = reinterpret_cast<const int*>(diag + 2 * L * 4 * NX);
-  float lv[STRIP_DJ_LMAX][NX];
-  float v[NX], dummy[NX];
-  for (int y = 0; y < L; ++y) {
-    const float* dy = diag + (y * 4 + row_index(pos, y, srow)) * NX;
-    if (y == 0) {
-#pragma unroll
-      for (int x = 0; x < NX; ++x) v[x] = dy[x];
-    } else {
-#pragma unroll
-      for (int c = 0; c < W; ++c) apply_pair<W, false>(v, dummy, c, vert[(y - 1) * W + c]);
-#pragma unroll
-      for (int x = 0; x < NX; ++x) v[x] *= dy[x];
-    }
-    float m = v[0];
-#pragma unroll
-    for (int x = 1; x < NX; ++x) m = fmaxf(m, v[x]);
-    const float sc = pow2i(-exponent_of(m));
-#pragma unroll
-    for (int x = 0; x < NX; ++x) {
-      v[x] *= sc;
-      lv[y][x] = v[x];
-    }
-  }
-  float r[NX];  // r_{y+1}
+  constexpr int NB = 2 * W + 1;
+  constexpr int NV = NB <= 4 ? 4 : (NB <= 8 ? 8 : 16);
+  const float4* vert = tb.vert;
+  const float* diag = tb.diag;
+  const int* pos = tb.pos;
+  const bool own = (lane & (32 / NV - 1)) == 0;
+  float r[NX];  // r_{y+1}, renormalised
+  float dlog = 0.f;
   for (int y = L - 1; y >= 0; --y) {
-    float msg[NX];
+    const StripRow& R = rows[y];
+    float lv[NX], msg[NX], dummy[NX];
+#pragma unroll
+    for (int x = 0; x < NX; ++x) lv[x] = lvs[(y * NX + x) * T + t];
+    float val[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) val[j] = 0.f;
+    float Z = 0.f;
     if (y == L - 1) {
 #pragma unroll
-      for (int x = 0; x < NX; ++x) msg[x] = 1.f;
+      for (int x = 0; x < NX; ++x) {
+        msg[x] = 1.f;
+        Z += lv[x];
+      }
     } else {
+      float4 q[W];
 #pragma unroll
-      for (int x = 0; x < NX; ++x) msg[x] = r[x];
+      for (int c = 0; c < W; ++c) q[c] = vert[y * W + c];
+      // suffix products R_c (R_{W-1} = r), kept for the vertical bonds
+      float Rc[W][NX];
 #pragma unroll
-      for (int c = 0; c < W; ++c) apply_pair<W, false>(msg, dummy, c, vert[y * W + c]);
+      for (int x = 0; x < NX; ++x) Rc[W - 1][x] = r[x];
+#pragma unroll
+      for (int c = W - 2; c >= 0; --c) {
+#pragma unroll
+        for (int x = 0; x < NX; ++x) Rc[c][x] = Rc[c + 1][x];
+        apply_pair<W, false>(Rc[c], dummy, c + 1, q[c + 1]);
+      }
+#pragma unroll
+      for (int x = 0; x < NX; ++x) msg[x] = Rc[0][x];
+      apply_pair<W, false>(msg, dummy, 0, q[0]);
+#pragma unroll
+      for (int x = 0; x < NX; ++x) Z += lv[x] * msg[x];
+      // prefix products L_c (L_0 = l)
+      float Lc[NX];
+#pragma unroll
+      for (int x = 0; x < NX; ++x) Lc[x] = lv[x];
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        if (c > 0) apply_pair<W, false>(Lc, dummy, c - 1, q[c - 1]);
+        float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+        for (int x = 0; x < NX; ++x) {
+          d0 = fmaf(Lc[x], Rc[c][x], d0);
+          d1 = fmaf(Lc[x], Rc[c][x ^ (1 << c)], d1);
+        }
+        val[W + 1 + c] = fmaf(q[c].x, d0, -q[c].y * d1);
+      }
     }
-    float Z = 0.f, P[NX];
+    float P[NX];
 #pragma unroll
-    for (int x = 0; x < NX; ++x) {
-      P[x] = lv[y][x] * msg[x];
-      Z += P[x];
-    }
-    const float iz = valid ? scale / Z : 0.f;
-    const StripRow& R = rows[y];
+    for (int x = 0; x < NX; ++x) P[x] = lv[x] * msg[x];
+    const float iz = 1.f / Z;
 #pragma unroll
     for (int c = 0; c + 1 < W; ++c) {
       float a = 0.f;
 #pragma unroll
       for (int x = 0; x < NX; ++x) a += P[x] * spin_of(x, c) * spin_of(x, c + 1);
-      acc_bond(dJ, R.eh[c], a * iz, lane0);
+      val[c] = a;
     }
-    if (R.posL >= 0) {
+    const int pL = pos[2 * y], pR = pos[2 * y + 1];
+    if (pL >= 0) {
       float a = 0.f;
 #pragma unroll
       for (int x = 0; x < NX; ++x) a += P[x] * spin_of(x, 0);
-      acc_bond(dJ, R.eL, a * iz * (float)srow[R.posL], lane0);
+      val[W - 1] = a * (float)srow[pL];
     }
-    if (R.posR >= 0) {
+    if (pR >= 0) {
       float a = 0.f;
 #pragma unroll
       for (int x = 0; x < NX; ++x) a += P[x] * spin_of(x, W - 1);
-      acc_bond(dJ, R.eR, a * iz * (float)srow[R.posR], lane0);
+      val[W] = a * (float)srow[pR];
     }
+    // expectations, their beta-weighted sum, and the masked values for d/dJ
+    float dJb = 0.f;
+#pragma unroll
+    for (int c = 0; c + 1 < W; ++c) dJb = fmaf(R.Jh[c], val[c], dJb);
+    dJb = fmaf(R.JL, val[W - 1], dJb);
+    dJb = fmaf(R.JR, val[W], dJb);
     if (y + 1 < L) {
 #pragma unroll
-      for (int c = 0; c < W; ++c) {
-        float u[NX];
+      for (int c = 0; c < W; ++c) dJb = fmaf(R.Jv[c], val[W + 1 + c], dJb);
+    }
+    dlog = fmaf(dJb, iz, dlog);
+    const float vz = valid ? iz : 0.f;
 #pragma unroll
-        for (int x = 0; x < NX; ++x) u[x] = r[x];
-#pragma unroll
-        for (int c2 = 0; c2 < W; ++c2) {
-          float4 q = vert[y * W + c2];
-          if (c2 == c) q = make_float4(q.x, -q.y, q.z, -q.w);
-          apply_pair<W, false>(u, dummy, c2, q);
-        }
-        float a = 0.f;
-#pragma unroll
-        for (int x = 0; x < NX; ++x) a += lv[y][x] * u[x];
-        acc_bond(dJ, R.ev[c], a * iz, lane0);
-      }
+    for (int j = 0; j < NB; ++j) val[j] *= vz;
+    int vi;
+    const float sum = warp_transpose_sum<NV>(val, lane, vi);
+    if (own && vi < NB && (vi <= W || y + 1 < L)) {
+      const int e = row_edge(R, W, vi);
+      if (e >= 0) accw[e] += sum;
     }
     // r_y = D_y * msg, renormalised
     const float* dy = diag + (y * 4 + row_index(pos, y, srow)) * NX;
@@ -344,49 +446,97 @@ __device__ void strip_dJ(const float* tab, const StripRow* __restrict__ rows, in
 #pragma unroll
     for (int x = 0; x < NX; ++x) r[x] *= sc;
   }
+  return dlog;
 }
 
-// One CTA per tile of samples: bond sums accumulate in shared memory (FP32,
-// n_edges floats), then the CTA writes its row of `part` [CTA][max edges];
-// strips_dJ_reduce_kernel adds the rows of each instance in a fixed order.
-__global__ void __launch_bounds__(128) strips_dJ_kernel(const InstDev* __restrict__ inst,
-                                                        const LaunchInfo li,
-                                                        const int8_t* __restrict__ spins,
-                                                        float* __restrict__ part, int part_stride) {
+// Shared memory of strips_adj_kernel: strip tables, the tile's spins, the
+// left vectors of one strip [L][2^w][T] and (T/32) rows of n_edges
+// accumulators.
+__host__ __device__ inline int strip_adj_lv_offset(int tab_floats, int T, int Dp) {
+  return tab_floats + ((T * Dp + 15) & ~15) / 4;
+}
+
+__global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                         int lv_floats, const int8_t* __restrict__ spins,
+                                                         double* __restrict__ dbeta, float* __restrict__ part,
+                                                         int part_stride) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
-  if (I.kind != 0) return;
-  const int T = li.tile, t = threadIdx.x;
+  if (I.kind != 0) return;  // another adjoint kernel owns this instance
+  const int T = li.tile, t = threadIdx.x, lane = t & 31;
   const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_row_bytes(D);
-  build_strip_tables(I, beta, sm, t, T);
-  int8_t* ssp = reinterpret_cast<int8_t*>(sm + I.strip_tab_floats);
-  float* acc = reinterpret_cast<float*>(ssp + T * Dp);  // [n_edges]
-  for (int e = t; e < I.n_edges; e += T) acc[e] = 0.f;
+  build_strip_tables(I, beta, sm, t, T, false);
+  const int tabn = strip_tab_offset(I, I.n_strips, false);
+  int8_t* ssp = reinterpret_cast<int8_t*>(sm + tabn);
+  float* lvs = sm + strip_adj_lv_offset(tabn, T, Dp);
+  float* acc = lvs + lv_floats;
+  const int ne = I.n_edges;
+  for (int e = t; e < (T >> 5) * ne; e += T) acc[e] = 0.f;
   const int n_valid = min(T, li.batch - b0);
   stage_spins(spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, D, Dp, ssp, t, T);
   for (int e = n_valid * Dp + t; e < T * Dp; e += T) ssp[e] = 1;  // padding rows
   __syncthreads();
   const bool valid = b < li.batch;
   const int8_t* srow = ssp + t * Dp;
-  const float scale = beta / (float)li.batch;
-  const bool lane0 = (t & 31) == 0;
-  for (int st = 0; st < I.n_strips; ++st) {
+  float* accw = acc + (t >> 5) * ne;
+  double dl = 0.0;
+  for (int st = 0, off = 0; st < I.n_strips; ++st) {
     const StripDev& sd = I.strips[st];
-    const float* tab = sm + sd.tab_off;
+    const StripTab tab = strip_tab_at(sm + off, sd.w, sd.L, false);
+    off += strip_tab_floats_adj(sd.w, sd.L);
     const StripRow* rows = I.rows + sd.row0;
+    double l = 0.0;
+    float d = 0.f;
     switch (sd.w) {
-      case 1: strip_dJ<1>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
-      case 2: strip_dJ<2>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
-      case 3: strip_dJ<3>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
-      default: strip_dJ<4>(tab, rows, sd.L, srow, valid, scale, acc, lane0); break;
+      case 1:
+        strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        break;
+      case 2:
+        strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        break;
+      case 3:
+        strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        break;
+      default:
+        strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        break;
     }
+    dl += d;
   }
+  // W-W bonds: -beta E_1 for d/dbeta, s_a s_b for d/dJ (eight bonds per warp reduction)
+  float e1 = 0.f;
+  for (int e0 = 0; e0 < I.n_ww; e0 += 8) {
+    float val[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      val[j] = 0.f;
+      if (e0 + j < I.n_ww) {
+        const EdgeWW q = I.ww[e0 + j];
+        const float ss = (float)(srow[q.a] * srow[q.b]);
+        e1 = fmaf(q.J, ss, e1);
+        if (valid) val[j] = ss;
+      }
+    }
+    int vi;
+    const float sum = warp_transpose_sum<8>(val, lane, vi);
+    if ((lane & 3) == 0 && e0 + vi < I.n_ww) accw[I.ww[e0 + vi].e] += sum;
+  }
+  if (dbeta && valid) dbeta[(long long)k * li.batch + b] = dl + (double)e1;
   __syncthreads();
+  const float scale = beta / (float)li.batch;
   float* row = part + (long long)blockIdx.x * part_stride;
-  for (int e = t; e < I.n_edges; e += T) row[e] = acc[e];
+  for (int e = t; e < ne; e += T) {
+    float s = 0.f;
+    for (int w = 0; w < (T >> 5); ++w) s += acc[w * ne + e];
+    row[e] = s * scale;
+  }
 }
 
 // dJ[edge] += sum over the instance's CTA rows, in CTA order (deterministic).
@@ -403,26 +553,54 @@ __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const 
   }
 }
 
-cudaError_t launch_strips_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
-                             const int8_t* spins, float* part, int part_stride, double* dJ, cudaStream_t s) {
+int strip_adj_lv_floats(const Instance& in, int tile) {
+  int lv = 0;
+  for (const StripDev& sd : in.strip.strips) lv = std::max(lv, sd.L << sd.w);
+  return lv * tile;
+}
+
+// lv_floats: the launch-wide left-vector region (the maximum over instances)
+int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats) {
+  const int D = (int)in.W.size();
+  int w4 = (D + 3) / 4;
+  if ((w4 & 1) == 0) ++w4;
+  int tabn = 0;
+  for (const StripDev& sd : in.strip.strips) tabn += strip_tab_floats_adj(sd.w, sd.L);
+  return 4 * strip_adj_lv_offset(tabn, tile, 4 * w4) + 4 * lv_floats + 4 * (tile / 32) * in.m;
+}
+
+// CTAs of `tile` threads with `smem_bytes` of shared memory resident per SM.
+int strips_adj_occupancy(int tile, int smem_bytes) {
+  if (cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, strips_adj_kernel, tile, smem_bytes) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
+                              const int8_t* spins, double* dbeta, float* part, int part_stride, double* dJ,
+                              cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(strips_dJ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_bytes);
+  if (li.tile % 32 != 0 || li.tile > 128) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  strips_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, spins, part, part_stride);
+  strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, lv_floats, spins, dbeta, part, part_stride);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !dJ) return e;
   strips_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
   return cudaGetLastError();
 }
 
-// W-W bonds: d(-beta E_1)/d J_e = beta s_a s_b, batch mean.  One CTA per
-// (instance, bond chunk); threads stride over samples.
+// W-W bonds of dense and elimination instances: d(-beta E_1)/d J_e =
+// beta s_a s_b, batch mean.  One CTA per (instance, bond chunk); threads
+// stride over samples.
 __global__ void ww_dJ_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                              const int8_t* __restrict__ spins, double* __restrict__ dJ) {
   const int k = blockIdx.y;
   const InstDev& I = inst[k];
+  if (I.kind == 0) return;  // strips_adj_kernel covers the W-W bonds of strip instances
   const int8_t* sp = spins + I.spin_units * li.batch;
   __shared__ int red[32];
   for (int e = blockIdx.x; e < I.n_ww; e += gridDim.x) {

@@ -188,11 +188,11 @@ class Context:
 
     def autotune(self, betas, batch: int, precision: int, stream=None):
         """Time candidate launch shapes on a synthetic batch and keep the fastest;
-        returns the chosen (sampler tile, strip tile, backward CTAs)."""
+        returns the chosen (sampler tile, strip tile, backward CTAs, strip adjoint tile)."""
         b, pb = _arr(betas, np.float64)
         out = (ctypes.c_int32 * 4)()
         self._check(lib().tnvan_autotune(self._h, pb, batch, precision, _stream(stream), out))
-        return tuple(out[:3])
+        return tuple(out[:4])
 
     def profile(self, enable: bool):
         self._check(lib().tnvan_profile(self._h, int(enable)))

@@ -201,11 +201,51 @@ def test_contraction_adjoint_beta_and_J(cfg, batch):
         ref = db_ref[k]
         got = dbeta[k * batch:(k + 1) * batch].cpu()
         assert float((got - ref).abs().max()) <= 2e-5 * float(ref.abs().max())
-        assert torch.equal(got, db2[k * batch:(k + 1) * batch].cpu())
+        # the backward pass forms d/dbeta from the bond expectations of its
+        # reverse sweep (sum_e J_e <s s>_e - E_1), not by forward mode
+        got2 = db2[k * batch:(k + 1) * batch].cpu()
+        assert float((got2 - ref).abs().max()) <= 2e-5 * float(ref.abs().max())
         m = w.graphs[k].m
         gj = dJ[eo:eo + m].cpu()
         assert float((gj - dj_ref[k]).abs().max()) <= 2e-5 * max(1.0, float(dj_ref[k].abs().max()))
         eo += m
+
+
+def test_strip_adjoint_all_widths_tall_strips():
+    # strips of width 1, 2, 3 and 4 and 20 rows (more than one 16-row pass),
+    # a ragged batch of 40 seeded spin rows: d/dbeta per sample and the
+    # batch-mean d/dJ against FP64 autograd through the oracle's contraction
+    Lx, Ly, beta, batch = 14, 20, 0.7, 40
+    g = wl.lattice(Lx, Ly, "gauss", seed=91)
+    W = wl.width_columns(Lx, Ly, [1, 4, 8, 13])
+    from paper_2504_12037_gb300.model import TNVAN
+
+    model = TNVAN([g], [W], [32, 32], [beta], seed=5)
+    D = len(W)
+    s = np.where(np.random.default_rng(17).random((batch, D)) < 0.5, 1.0, -1.0)
+    s_t = torch.as_tensor(s)
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    Jt = torch.tensor(g.J, dtype=torch.float64, requires_grad=True)
+    lz = transfer.log_zr_lattice(g.n, g.ei, g.ej, Jt, bt, W, s_t, g.Lx)
+    db_ref = torch.stack([torch.autograd.grad(lz[b], bt, retain_graph=True)[0] for b in range(batch)])
+    (dj_ref,) = torch.autograd.grad(lz.mean(), Jt)
+    d_spins = to_dev_spins(s.reshape(-1))
+    logZR = torch.empty(batch, dtype=torch.float64, device="cuda")
+    model.ctx.contract(model.betas, batch, d_spins, tv.FP32, logZR)
+    logq = torch.zeros(batch, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(model.params)
+    dbeta = torch.empty(batch, dtype=torch.float64, device="cuda")
+    dJ = torch.empty(g.m, dtype=torch.float64, device="cuda")
+    model.ctx.backward(model.betas, batch, d_spins, logZR, logq, tv.FP32, grad, dbeta, dJ)
+    torch.cuda.synchronize()
+    assert float((logZR.cpu() - lz.detach()).abs().max()) / g.n <= TOL_FP32
+    assert float((dbeta.cpu() - db_ref).abs().max()) <= 2e-5 * float(db_ref.abs().max())
+    assert float((dJ.cpu() - dj_ref).abs().max()) <= 2e-5 * max(1.0, float(dj_ref.abs().max()))
+    # d/dJ alone (no d/dbeta requested) is the same launch without the per-sample output
+    dJ2 = torch.empty_like(dJ)
+    model.ctx.backward(model.betas, batch, d_spins, logZR, logq, tv.FP32, grad, None, dJ2)
+    torch.cuda.synchronize()
+    assert torch.equal(dJ, dJ2)
 
 
 def test_full_size_launch_sampled_rows():
@@ -231,6 +271,41 @@ def test_full_size_launch_sampled_rows():
         lz = logZR[k * B:(k + 1) * B].cpu()[rows]
         assert float((lq[m] - lq_or[m]).abs().max()) / g.n <= TOL_FP32
         assert float((lz[m] - lz_or[m]).abs().max()) / g.n <= TOL_FP32
+
+
+def test_full_size_adjoint_sampled_rows_and_identity():
+    # The strip adjoint at the full 16x16 batch (the launch shape the planner
+    # picks for 5 x 16384 samples): d/dbeta of sampled rows against FP64
+    # autograd of the oracle, and for the batch-mean d/dJ the identity
+    #   sum_e J_e dlogZR/dJ_e = beta * mean_b dlogZR/dbeta   (Eq. 4: weights depend on beta J only)
+    w = wl.workload(2)
+    model = _model(w)
+    B = w.batch
+    seed, step = 778, 4
+    spins, logq, logZR = model.sample(B, seed, step)
+    grad = torch.empty_like(model.params)
+    dbeta = torch.empty(model.n * B, dtype=torch.float64, device="cuda")
+    dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+    model.ctx.backward(model.betas, B, spins, logZR, logq, tv.FP32, grad, dbeta, dJ)
+    torch.cuda.synchronize()
+    rows = np.unique(np.concatenate([np.arange(0, B, 2039), [B - 1, 95, 96, 127, 128]]))
+    eo = 0
+    for k in range(model.n):
+        g, W, D, beta = w.graphs[k], w.widths_sets[k], model.D[k], w.betas[k]
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_or, p_or, u = oracle_samples(p32, D, w.hidden, seed, step, k, B, rows=rows)
+        s_gpu = model.spins_of(spins, k, B).cpu().numpy()[rows].astype(np.float64)
+        same = check_sample_agreement(s_gpu, s_or.numpy(), u, p_or.numpy(), max_flip_frac=0.1)
+        bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+        lz = transfer.log_zr_lattice(g.n, g.ei, g.ej, g.J, bt, W, s_or, g.Lx)
+        db_or = torch.stack([torch.autograd.grad(lz[i], bt, retain_graph=True)[0] for i in range(len(rows))])
+        db = dbeta[k * B:(k + 1) * B].cpu()[rows]
+        m = torch.as_tensor(same)
+        assert float((db[m] - db_or[m]).abs().max()) <= 2e-5 * float(db_or.abs().max())
+        lhs = float((torch.as_tensor(g.J) * dJ[eo:eo + g.m].cpu()).sum())
+        rhs = beta * float(dbeta[k * B:(k + 1) * B].mean())
+        assert abs(lhs - rhs) <= 1e-5 * max(1.0, abs(rhs))
+        eo += g.m
 
 
 def test_train_step_runs_and_adam_matches_oracle():
