@@ -920,7 +920,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
     auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
     std::vector<int> grp, src;
-    int ug1 = 0, ug2 = 0, ugo = 0, wmax = 0;
+    int ug1 = 0, ug2 = 0, ugo = 0, wmax = 0, twmax = 0, tcw1 = 16, tcw2 = 16;
     const int Hl = md.Hl;
     auto pad4 = [&]() {
       while (src.size() % 4) src.push_back(-1);
@@ -966,6 +966,9 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       pad4();
       const int gsize = (int)src.size() - gstart;
       wmax = std::max(wmax, gsize);
+      if (n_hidden >= 1) twmax = std::max(twmax, gsize - (t1 - gstart));
+      tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
+      tcw2 = std::max(tcw2, ((u2hi + 15) & ~15) - (u2lo & ~15));
       grp.insert(grp.end(), {i0, i1, u1lo, u1hi, u2lo, u2hi, n_hidden >= 1 ? off1 - gstart : 0,
                              n_hidden >= 2 ? off2 - gstart : 0, offo - gstart, gstart, gsize, 0,
                              n_hidden >= 1 ? t1 - gstart : 0, n_hidden >= 2 ? t2 - gstart : 0,
@@ -984,8 +987,11 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     }
     md.n_groups = (int)grp.size() / GROUP_INTS;
     md.wmax = wmax;
-    md.sample_tc_ok = md.wtiles != nullptr && ug1 <= 32 && ug2 <= 32 && ugo <= 16 &&
-                      sample_tc_smem_bytes(D, H[0], H[1], wmax) <= 227 * 1024;
+    md.twmax = twmax;
+    md.tcw1 = tcw1;
+    md.tcw2 = tcw2;
+    md.sample_tc_ok = md.wtiles != nullptr && ug1 <= 32 && ug2 <= 32 && ugo <= 16 && D <= 128 &&
+                      sample_tc_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
     md.groups = dgrp;
     md.ug1 = ug1;
     md.ug2 = ug2;
@@ -1602,7 +1608,8 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
     li.step = step;
     int smem = 0;
     for (const Instance& in : ctx->inst)
-      smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], in.dev.made.wmax));
+      smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], in.dev.made.tcw1,
+                                                 in.dev.made.tcw2, in.dev.made.twmax));
     PROF(given ? "log_prob_tc" : "sample_tc", s);
     CK(launch_sample_tc(ctx->d_inst, li, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
     return TNVAN_OK;

@@ -50,6 +50,8 @@ struct MadeDev {
   const int* groups;      // [n_groups][GROUP_INTS], see k_made.cu
   int ug1, ug2, ugo;      // largest group unit counts per layer
   int wmax;               // largest per-group weight block (floats)
+  int twmax;              // largest per-group triangle tiles (floats)
+  int tcw1, tcw2;         // widest 16-aligned unit window of a group, layers 1 and 2
   float* blocks;          // blocked weights (gathered from `packed` every call)
   const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
   long long n_blk;
@@ -265,7 +267,7 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
 int fused_bwd_smem_bytes(int D, int H1, int H2);
 cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int8_t* spins,
                              float* logq, const int8_t* given, cudaStream_t s);
-int sample_tc_smem_bytes(int D, int H1, int H2, int wmax);
+int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 

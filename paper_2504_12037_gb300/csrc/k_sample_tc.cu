@@ -1,19 +1,30 @@
 // BF16 ancestral sampler on tcgen05 (Eq. 6-8) for networks with two hidden
 // layers of at most 128 units and at most 128 inputs.
 //
-// One CTA (128 threads, thread = sample = TMEM lane) draws 128 samples.
-// TMEM holds, for every unit not yet evaluated, its pre-activation from all
-// inputs fixed so far: P1 [128 x H1], P2 [128 x H2], PO [128 x D].  The steps
-// are processed in the host's step groups; inside a group, each step adds the
-// few in-group contributions on the CUDA cores (FP32 triangle tiles of the
-// group, bulk-copied into shared memory), evaluates the units that complete at
-// that step and draws s_i = +1 iff u < sigmoid(x_i).  After the group, its
-// new spins and hidden values (BF16 tiles, zero outside the group) are folded
-// into every accumulator at once:
-//   P1 += S_g W1_g^T,   P2 += H1_g W2_g^T,   PO += H2_g Wo_g^T
-// -- three short tcgen05.mma chains whose K windows are the group's spins and
-// units rounded out to multiples of 16, against BF16 weight tiles that were
-// laid out once per call in the canonical K-major form and bulk-copied in.
+// One CTA (128 threads, thread = sample = TMEM lane) draws 128 samples; its
+// TMEM footprint is at most 256 columns and its shared memory about 100 KB
+// for the 64-128-128-64 network, so two CTAs share an SM.  TMEM holds
+//   P1g [128 x w1]  layer-1 pre-activations of the current step group's units
+//                   from every spin before the group, recomputed per group as
+//                   S W1_g^T (S = the spin tile so far, zero beyond);
+//   P2  [128 x H2]  layer-2 pre-activations, accumulated over the groups;
+//   PO  [128 x D]   output pre-activations, accumulated over the groups.
+// Steps are processed in the host's step groups.  Inside a group, each step
+// reads the pre-activations of the units completing at that step straight
+// from TMEM (tcgen05.ld), adds the in-group contributions on the CUDA cores
+// (FP32 triangle tiles of the group, bulk-copied into shared memory; in-group
+// spins from a register bitmask, in-group hidden values from the BF16 fold
+// tiles), and draws s_i = +1 iff u < sigmoid(x_i).  After the group one
+// tcgen05.mma chain folds its hidden values into the accumulators and
+// recomputes P1g for the next group:
+//   P2 += H1_g W2_g^T,  PO += H2_g Wo_g^T,  P1g' = S W1_g'^T.
+// Every hidden value enters every later product as BF16 with FP32
+// accumulation; in-group arithmetic is FP32 on the same BF16 values.
+//
+// The spin tile S and the fold tiles H1_g, H2_g are MN-major MMA operands in
+// which consecutive 8-sample core-matrix groups are 16 bytes apart modulo
+// 128, so the per-sample stores and loads (one 2-byte element per thread)
+// are free of bank conflicts.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -23,32 +34,73 @@ namespace tnvan {
 
 namespace {
 
-__device__ __forceinline__ uint32_t koff(int r, int c, uint32_t rowbytes) {
-  return (uint32_t)(r >> 3) * (rowbytes / 16u) * 128u + (uint32_t)(c >> 3) * 128u + (uint32_t)(r & 7) * 16u +
-         (uint32_t)(c & 7) * 2u;
+// MN-major operand tile of 128 rows (samples) and kw columns (K, a multiple
+// of 16): element (m, k) at (m >> 3) * sbo + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2.
+__host__ __device__ __forceinline__ uint32_t mn_sbo(int kw) { return (uint32_t)kw * 16u + 16u; }
+__device__ __forceinline__ uint32_t mn_off(int m, int k, uint32_t sbo) {
+  return (uint32_t)(m >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 16u + (uint32_t)(m & 7) * 2u;
 }
-__device__ __forceinline__ void stb(unsigned char* base, uint32_t o, float v) {
+__device__ __forceinline__ void st_bf16(unsigned char* base, uint32_t o, float v) {
   *reinterpret_cast<__nv_bfloat16*>(base + o) = __float2bfloat16(v);
+}
+__device__ __forceinline__ float ld_bf16(const unsigned char* base, uint32_t o) {
+  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + o));
+}
+
+// One TMEM column of the warp's 32 lanes into a register, without waiting;
+// tmem_wait9 / tmem_wait1 order every later use of the destinations after
+// the wait.
+__device__ __forceinline__ void tmem_ld1_nowait(uint32_t taddr, uint32_t& r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait9(uint32_t (&a)[4], uint32_t (&b)[4], uint32_t& c) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                 "+r"(c)::"memory");
+}
+__device__ __forceinline__ void tmem_wait1(uint32_t& c) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(c)::"memory");
+}
+__device__ __forceinline__ float pick4(const uint32_t (&r)[4], int j) {
+  const uint32_t v = j == 0 ? r[0] : (j == 1 ? r[1] : (j == 2 ? r[2] : r[3]));
+  return __uint_as_float(v);
 }
 
 }  // namespace
 
-#define STC_WIN 64  // widest K window of a fold (units)
-#define STC_UG 32   // most units of one layer completing inside a group
-#define STC_GI 16   // most steps in a group
+#define STC_UG 32  // most units of one layer completing inside a group
+#define STC_GI 16  // most steps in a group
 
-__host__ __device__ inline int sample_tc_smem(int D, int H1, int H2, int wmax) {
-  const int weights = 2 * (H1 * D + H2 * H1 + D * H2);
-  const int folds = 2 * 128 * (32 + STC_WIN + STC_WIN);           // S_g, H1_g, H2_g (BF16)
-  const int pre = 4 * 128 * (STC_UG + STC_UG + STC_GI);           // P1, P2, PO of the group's units
-  const int vals = 4 * 128 * (STC_GI + STC_UG + STC_UG);          // in-group s, h1, h2 (FP32)
-  const int tri = 4 * ((wmax + 3) & ~3);                          // triangle tiles of a group
-  const int sp = 128 * D;
-  const int small = 4 * (STC_UG + STC_UG + STC_GI + 2 * (STC_GI + 1));
-  return weights + folds + pre + vals + tri + sp + small + 64;
+struct SampleTcLayout {
+  int wbytes, oS, oH1, oH2, oTW, oTab, oBar, total;
+};
+
+__host__ __device__ inline SampleTcLayout sample_tc_layout(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
+  SampleTcLayout L;
+  L.wbytes = 2 * (H1 * D + H2 * H1 + D * H2);
+  int p = (L.wbytes + 127) & ~127;
+  L.oS = p;
+  p += 16 * (int)mn_sbo(D);
+  L.oH1 = p;
+  p += 16 * (int)mn_sbo(tcw1);
+  L.oH2 = p;
+  p += 16 * (int)mn_sbo(tcw2);
+  L.oTW = p;
+  p += 4 * ((twmax + 3) & ~3);
+  L.oTab = p;
+  p += 4 * (STC_UG + STC_UG + STC_GI + 2 * (STC_GI + 1));
+  p = (p + 15) & ~15;
+  L.oBar = p;
+  p += 32;
+  L.total = p;
+  return L;
 }
 
-__global__ void __launch_bounds__(128, 1) sample_tc_kernel(const InstDev* __restrict__ inst,
+__host__ __device__ inline int sample_tc_tmem_cols(int D, int H2, int tcw1) {
+  return tcw1 + H2 + D <= 256 ? 256 : 512;
+}
+
+__global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __restrict__ inst,
                                                            const LaunchInfo li, int8_t* __restrict__ spins,
                                                            float* __restrict__ logq,
                                                            const int8_t* __restrict__ given) {
@@ -60,79 +112,87 @@ __global__ void __launch_bounds__(128, 1) sample_tc_kernel(const InstDev* __rest
   const int t = threadIdx.x, w = t >> 5;
   const int b = (blockIdx.x - li.tile_begin[k]) * 128 + t;
   const bool valid = b < li.batch;
-  const int wbytes = 2 * (H1 * D + H2 * H1 + D * H2);
-  unsigned char* p = smem;
-  unsigned char* sW1 = p;
+  const SampleTcLayout LY = sample_tc_layout(D, H1, H2, md.tcw1, md.tcw2, md.twmax);
+  unsigned char* sW1 = smem;
   unsigned char* sW2 = sW1 + 2 * H1 * D;
   unsigned char* sWo = sW2 + 2 * H2 * H1;
-  p += (wbytes + 127) & ~127;
-  unsigned char* sS = p; p += 2 * 128 * 32;
-  unsigned char* sH1 = p; p += 2 * 128 * STC_WIN;
-  unsigned char* sH2 = p; p += 2 * 128 * STC_WIN;
-  float* P1 = reinterpret_cast<float*>(p); p += 4 * 128 * STC_UG;
-  float* P2 = reinterpret_cast<float*>(p); p += 4 * 128 * STC_UG;
-  float* PO = reinterpret_cast<float*>(p); p += 4 * 128 * STC_GI;
-  float* Sf = reinterpret_cast<float*>(p); p += 4 * 128 * STC_GI;
-  float* H1f = reinterpret_cast<float*>(p); p += 4 * 128 * STC_UG;
-  float* H2f = reinterpret_cast<float*>(p); p += 4 * 128 * STC_UG;
-  float* TW = reinterpret_cast<float*>(p); p += 4 * ((md.wmax + 3) & ~3);
-  float* gb1 = reinterpret_cast<float*>(p); p += 4 * STC_UG;   // biases of the group's units
-  float* gb2 = reinterpret_cast<float*>(p); p += 4 * STC_UG;
-  float* gbo = reinterpret_cast<float*>(p); p += 4 * STC_GI;
-  int* gc1 = reinterpret_cast<int*>(p); p += 4 * (STC_GI + 1);  // c1[i], c2[i] for i = i0-1 .. i1-1
-  int* gc2 = reinterpret_cast<int*>(p); p += 4 * (STC_GI + 1);
-  int8_t* sp = reinterpret_cast<int8_t*>(p); p += 128 * D;
-  p = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 7) & ~uintptr_t(7));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(p);   // MMA completion
-  uint64_t* cbar = bar + 1;                         // bulk copies
+  unsigned char* sS = smem + LY.oS;
+  unsigned char* sH1 = smem + LY.oH1;
+  unsigned char* sH2 = smem + LY.oH2;
+  float* TW = reinterpret_cast<float*>(smem + LY.oTW);
+  float* gb1 = reinterpret_cast<float*>(smem + LY.oTab);  // biases of the group's units
+  float* gb2 = gb1 + STC_UG;
+  float* gbo = gb2 + STC_UG;
+  int* gc1 = reinterpret_cast<int*>(gbo + STC_GI);  // c1[i], c2[i] for i = i0-1 .. i1-1
+  int* gc2 = gc1 + (STC_GI + 1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + LY.oBar);  // MMA completion
+  uint64_t* cbar = bar + 1;                                     // bulk copies
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
-  const uint32_t rbW1 = 2u * D, rbW2 = 2u * H1, rbWo = 2u * H2;
+  const uint32_t sboS = mn_sbo(D), sbo1 = mn_sbo(md.tcw1), sbo2 = mn_sbo(md.tcw2);
+  const uint32_t kbW1 = 2u * D / 16u * 128u, kbW2 = 2u * H1 / 16u * 128u, kbWo = 2u * H2 / 16u * 128u;
   const float* b1 = md.packed + md.layer[0].dst_off + (long long)H1 * D;
   const float* b2 = md.packed + md.layer[1].dst_off + (long long)H2 * H1;
   const float* bo = md.packed + md.layer[2].dst_off + (long long)D * H2;
+  const int ncols = sample_tc_tmem_cols(D, H2, md.tcw1);
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_init(cbar, 1);
   }
   if (w == 0) {
-    tc::tmem_alloc(slot, 512);
+    tc::tmem_alloc(slot, (uint32_t)ncols);
     tc::tmem_relinquish();
   }
+  // the spin tile starts at zero (spins not drawn yet contribute nothing)
+  for (int o = t * 16; o < 16 * (int)sboS; o += 128 * 16)
+    *reinterpret_cast<uint4*>(sS + o) = make_uint4(0, 0, 0, 0);
+  fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   uint32_t cphase = 0;
+  bool copy_pending = false, mma_pending = false;
   if (t == 0) {
-    mbar_expect_tx(cbar, (uint32_t)wbytes);
-    bulk_g2s(sW1, md.wtiles, (uint32_t)wbytes, cbar);
+    const int* G0 = md.groups;
+    const uint32_t tb0 = (uint32_t)(G0[10] - G0[12]) * 4u;
+    mbar_expect_tx(cbar, (uint32_t)LY.wbytes + tb0);
+    bulk_g2s(sW1, md.wtiles, (uint32_t)LY.wbytes, cbar);
+    if (tb0) bulk_g2s(TW, md.blocks + G0[9] + G0[12], tb0, cbar);
   }
-  bool ok = mbar_wait(cbar, cphase);
-  cphase ^= 1u;
+  copy_pending = true;
   const uint32_t tmem = *slot;
-  const uint32_t tP1 = tmem, tP2 = tmem + 128, tPO = tmem + 256;
   const uint32_t lane_off = (uint32_t)(w * 32) << 16;
-  const uint32_t id1 = tc::idesc(128, H1, 1u), id2 = tc::idesc(128, H2, 1u), ido = tc::idesc(128, D, 1u);
+  const uint32_t tP1 = tmem + lane_off, tP2 = tP1 + (uint32_t)md.tcw1, tPO = tP2 + (uint32_t)H2;
+  const uint32_t idA = 1u << 15;  // A operand MN-major
+  const uint32_t id2 = tc::idesc(128, H2, 1u) | idA, ido = tc::idesc(128, D, 1u) | idA;
   const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
   const uint32_t step32 = launch_step(li);
   const int8_t* gv = given ? given + I.spin_units * li.batch + (long long)b * D : nullptr;
   uint32_t phase = 0;
-  bool init1 = false, init2 = false, inito = false;  // accumulator written by a fold yet
+  bool ok = true;
+  bool p1ok = false, init2 = false, inito = false;  // accumulator holds data
   float lq = 0.f;
   uint4 rnd = make_uint4(0, 0, 0, 0);
-  for (int g = 0; g < md.n_groups && ok; ++g) {
+  unsigned long long sb0 = 0ull, sb1 = 0ull;  // spin i is +1 iff bit i is set
+  for (int g = 0; g < md.n_groups; ++g) {
     const int* G = md.groups + GROUP_INTS * g;
     const int i0 = G[0], i1 = G[1], u1lo = G[2], u1hi = G[3], u2lo = G[4], u2hi = G[5];
     const int gi = i1 - i0, n1g = u1hi - u1lo, n2g = u2hi - u2lo;
-    const int s0 = i0 & ~15, w1 = u1lo & ~15, w2 = u2lo & ~15;
-    const int sN = ((i1 + 15) & ~15) - s0, n1 = ((u1hi + 15) & ~15) - w1, n2 = ((u2hi + 15) & ~15) - w2;
-    // previous fold done (its operand tiles are free, the accumulators final)
-    if (g > 0) {
-      ok = mbar_wait(bar, phase);
-      phase ^= 1u;
+    const int w1 = u1lo & ~15, w2 = u2lo & ~15;
+    const int n1 = ((u1hi + 15) & ~15) - w1, n2 = ((u2hi + 15) & ~15) - w2;
+    // the previous MMA chain is done: fold tiles free, accumulators and P1g final
+    if (mma_pending) {
+      if (mbar_wait(bar, phase)) {
+        phase ^= 1u;
+        mma_pending = false;
+      } else {
+        ok = false;
+      }
       tc::fence_after_sync();
-      if (!ok) break;
     }
-    __syncthreads();  // everyone is done with the previous triangle tiles and group tables
+    for (int o = t * 16; o < 16 * (int)sbo1; o += 128 * 16)
+      *reinterpret_cast<uint4*>(sH1 + o) = make_uint4(0, 0, 0, 0);
+    for (int o = t * 16; o < 16 * (int)sbo2; o += 128 * 16)
+      *reinterpret_cast<uint4*>(sH2 + o) = make_uint4(0, 0, 0, 0);
     if (t < n1g) gb1[t] = __ldg(b1 + u1lo + t);
     if (t >= 32 && t - 32 < n2g) gb2[t - 32] = __ldg(b2 + u2lo + t - 32);
     if (t >= 64 && t - 64 < gi) gbo[t - 64] = __ldg(bo + i0 + t - 64);
@@ -141,158 +201,182 @@ __global__ void __launch_bounds__(128, 1) sample_tc_kernel(const InstDev* __rest
       gc1[t - 96] = i >= 0 ? md.c1[i] : 0;
       gc2[t - 96] = i >= 0 ? md.c2[i] : 0;
     }
-    const int tstart = G[12];
-    const uint32_t tbytes = (uint32_t)(G[10] - tstart) * 4u;
-    if (t == 0 && tbytes) {
-      fence_proxy_async_smem();
-      mbar_expect_tx(cbar, tbytes);
-      bulk_g2s(TW, md.blocks + G[9] + tstart, tbytes, cbar);
-    }
-    // accumulated pre-activations of the group's units -> FP32 [unit][T];
-    // TMEM loads go in statically indexed pairs, one wait per pair
-    auto take = [&](const uint32_t (&r)[16], int c0, int lo, int hi, float* dst) {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = c0 + i;
-        if (c >= lo && c < hi) dst[(c - lo) * 128 + t] = __uint_as_float(r[i]);
-      }
-    };
-    auto load_window = [&](uint32_t tbase, int wlo, int wn, int lo, int hi, float* dst) {
-      for (int c = 0; c < wn; c += 32) {
-        uint32_t ra[16], rb[16];
-        tc::tmem_ld16_nowait(tbase + lane_off + (uint32_t)(wlo + c), ra);
-        const bool two = c + 16 < wn;
-        if (two) tc::tmem_ld16_nowait(tbase + lane_off + (uint32_t)(wlo + c + 16), rb);
-        tc::tmem_wait_ld();
-        take(ra, wlo + c, lo, hi, dst);
-        if (two) take(rb, wlo + c + 16, lo, hi, dst);
-      }
-    };
-    if (init1) load_window(tP1, w1, n1, u1lo, u1hi, P1);
-    else for (int u = 0; u < n1g; ++u) P1[u * 128 + t] = 0.f;
-    if (init2) load_window(tP2, w2, n2, u2lo, u2hi, P2);
-    else for (int u = 0; u < n2g; ++u) P2[u * 128 + t] = 0.f;
-    if (inito) load_window(tPO, s0, sN, i0, i1, PO);
-    else for (int i = 0; i < gi; ++i) PO[i * 128 + t] = 0.f;
-    // zero this thread's rows of the fold tiles
-    for (int c = 0; c < 32; c += 8) *reinterpret_cast<uint4*>(sS + koff(t, c, 64u)) = make_uint4(0, 0, 0, 0);
-    for (int c = 0; c < STC_WIN; c += 8) {
-      *reinterpret_cast<uint4*>(sH1 + koff(t, c, 2u * STC_WIN)) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(sH2 + koff(t, c, 2u * STC_WIN)) = make_uint4(0, 0, 0, 0);
-    }
-    if (tbytes) {
-      ok = mbar_wait(cbar, cphase);
+    if (mbar_wait(cbar, cphase)) {  // this group's triangle tiles (first: the weights too)
       cphase ^= 1u;
-      if (!ok) break;
+      copy_pending = false;
+    } else {
+      ok = false;
     }
+    ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles and group tables visible; one verdict
+    if (!ok) break;
     const float* TW1 = TW;
-    const float* TW2 = TW + (G[13] - tstart);
-    const float* TWo = TW + (G[14] - tstart);
-    __syncthreads();  // group tables visible
-    // in-group steps
+    const float* TW2 = TW + (G[13] - G[12]);
+    const float* TWo = TW + (G[14] - G[12]);
+    uint32_t gbits = 0;  // in-group spins
     for (int i = i0; i < i1; ++i) {
       if ((i & 3) == 0)
         rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
       const int q = i - i0;  // gc*[q] = c*[i-1], gc*[q+1] = c*[i]
-      if (i >= 1) {
-        const int ua = gc1[q], ub = gc1[q + 1];
-        for (int u = ua; u < ub; ++u) {
-          const float* wr = TW1 + (u - u1lo) * gi;
-          float a0 = P1[(u - u1lo) * 128 + t] + gb1[u - u1lo], a1 = 0.f;
-          int j = 0;
-          for (; j + 2 <= q; j += 2) {
-            a0 = fmaf(wr[j], Sf[j * 128 + t], a0);
-            a1 = fmaf(wr[j + 1], Sf[(j + 1) * 128 + t], a1);
-          }
-          if (j < q) a0 = fmaf(wr[j], Sf[j * 128 + t], a0);
-          const float a = fmaxf(a0 + a1, 0.f);
-          H1f[(u - u1lo) * 128 + t] = a;
-          stb(sH1, koff(t, u - w1, 2u * STC_WIN), a);
+      const int ua = gc1[q], ub = gc1[q + 1], va = gc2[q], vb = gc2[q + 1];
+      // pre-activations of the units completing at step i (up to four per layer at once)
+      uint32_t ra[4] = {0u, 0u, 0u, 0u}, rb[4] = {0u, 0u, 0u, 0u}, rc = 0u;
+      if (p1ok) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (ua + j < ub) tmem_ld1_nowait(tP1 + (uint32_t)(ua + j - w1), ra[j]);
+      }
+      if (init2) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (va + j < vb) tmem_ld1_nowait(tP2 + (uint32_t)(va + j), rb[j]);
+      }
+      if (inito) tmem_ld1_nowait(tPO + (uint32_t)i, rc);
+      tmem_wait9(ra, rb, rc);
+      for (int u = ua; u < ub; ++u) {
+        float a0;
+        if (u - ua < 4) {
+          a0 = pick4(ra, u - ua);
+        } else {  // more than four units at one step
+          uint32_t rx = 0u;
+          if (p1ok) tmem_ld1_nowait(tP1 + (uint32_t)(u - w1), rx);
+          tmem_wait1(rx);
+          a0 = __uint_as_float(rx);
         }
-        const int n1i = ub - u1lo;
-        for (int v = gc2[q]; v < gc2[q + 1]; ++v) {
-          const float* wr = TW2 + (v - u2lo) * n1g;
-          float a0 = P2[(v - u2lo) * 128 + t] + gb2[v - u2lo], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-          int u = 0;
-          for (; u + 4 <= n1i; u += 4) {
-            a0 = fmaf(wr[u], H1f[u * 128 + t], a0);
-            a1 = fmaf(wr[u + 1], H1f[(u + 1) * 128 + t], a1);
-            a2 = fmaf(wr[u + 2], H1f[(u + 2) * 128 + t], a2);
-            a3 = fmaf(wr[u + 3], H1f[(u + 3) * 128 + t], a3);
-          }
-          for (; u < n1i; ++u) a0 = fmaf(wr[u], H1f[u * 128 + t], a0);
-          const float a = fmaxf((a0 + a1) + (a2 + a3), 0.f);
-          H2f[(v - u2lo) * 128 + t] = a;
-          stb(sH2, koff(t, v - w2, 2u * STC_WIN), a);
+        a0 += gb1[u - u1lo];
+        const float* wr = TW1 + (u - u1lo) * gi;
+        float a1 = 0.f;
+        int j = 0;
+        for (; j + 2 <= q; j += 2) {
+          a0 += ((gbits >> j) & 1u) ? wr[j] : -wr[j];
+          a1 += ((gbits >> (j + 1)) & 1u) ? wr[j + 1] : -wr[j + 1];
         }
+        if (j < q) a0 += ((gbits >> j) & 1u) ? wr[j] : -wr[j];
+        st_bf16(sH1, mn_off(t, u - w1, sbo1), fmaxf(a0 + a1, 0.f));
+      }
+      for (int v = va; v < vb; ++v) {
+        float a0;
+        if (v - va < 4) {
+          a0 = pick4(rb, v - va);
+        } else {
+          uint32_t rx = 0u;
+          if (init2) tmem_ld1_nowait(tP2 + (uint32_t)v, rx);
+          tmem_wait1(rx);
+          a0 = __uint_as_float(rx);
+        }
+        a0 += gb2[v - u2lo];
+        const float* wr = TW2 + (v - u2lo) * n1g;
+        float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int u = u1lo;
+        for (; u + 4 <= ub; u += 4) {
+          a0 = fmaf(wr[u - u1lo], ld_bf16(sH1, mn_off(t, u - w1, sbo1)), a0);
+          a1 = fmaf(wr[u + 1 - u1lo], ld_bf16(sH1, mn_off(t, u + 1 - w1, sbo1)), a1);
+          a2 = fmaf(wr[u + 2 - u1lo], ld_bf16(sH1, mn_off(t, u + 2 - w1, sbo1)), a2);
+          a3 = fmaf(wr[u + 3 - u1lo], ld_bf16(sH1, mn_off(t, u + 3 - w1, sbo1)), a3);
+        }
+        for (; u < ub; ++u) a0 = fmaf(wr[u - u1lo], ld_bf16(sH1, mn_off(t, u - w1, sbo1)), a0);
+        st_bf16(sH2, mn_off(t, v - w2, sbo2), fmaxf((a0 + a1) + (a2 + a3), 0.f));
       }
       float x;
       {
         const float* wr = TWo + q * n2g;
-        const int n2i = gc2[q + 1] - u2lo;
-        float a0 = PO[q * 128 + t] + gbo[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int v = 0;
-        for (; v + 4 <= n2i; v += 4) {
-          a0 = fmaf(wr[v], H2f[v * 128 + t], a0);
-          a1 = fmaf(wr[v + 1], H2f[(v + 1) * 128 + t], a1);
-          a2 = fmaf(wr[v + 2], H2f[(v + 2) * 128 + t], a2);
-          a3 = fmaf(wr[v + 3], H2f[(v + 3) * 128 + t], a3);
+        float a0 = __uint_as_float(rc) + gbo[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int v = u2lo;
+        for (; v + 4 <= vb; v += 4) {
+          a0 = fmaf(wr[v - u2lo], ld_bf16(sH2, mn_off(t, v - w2, sbo2)), a0);
+          a1 = fmaf(wr[v + 1 - u2lo], ld_bf16(sH2, mn_off(t, v + 1 - w2, sbo2)), a1);
+          a2 = fmaf(wr[v + 2 - u2lo], ld_bf16(sH2, mn_off(t, v + 2 - w2, sbo2)), a2);
+          a3 = fmaf(wr[v + 3 - u2lo], ld_bf16(sH2, mn_off(t, v + 3 - w2, sbo2)), a3);
         }
-        for (; v < n2i; ++v) a0 = fmaf(wr[v], H2f[v * 128 + t], a0);
+        for (; v < vb; ++v) a0 = fmaf(wr[v - u2lo], ld_bf16(sH2, mn_off(t, v - w2, sbo2)), a0);
         x = (a0 + a1) + (a2 + a3);
       }
       const float pr = 1.f / (1.f + expf(-x));
       const uint32_t word = (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
       const float u = (float)(word >> 8) * 5.9604644775390625e-08f;
-      float s = u < pr ? 1.f : -1.f;
-      if (gv) s = valid ? (float)gv[i] : 1.f;
-      Sf[q * 128 + t] = s;
-      stb(sS, koff(t, i - s0, 64u), s);
-      sp[t * D + i] = (int8_t)s;
+      bool up = u < pr;
+      if (gv) up = valid ? gv[i] > 0 : true;
+      const float s = up ? 1.f : -1.f;
+      if (up) {
+        gbits |= 1u << q;
+        if (i < 64) sb0 |= 1ull << i;
+        else sb1 |= 1ull << (i - 64);
+      }
+      st_bf16(sS, mn_off(t, i, sboS), s);
       lq -= softplusf(-s * x);
     }
-    // fold the group into every accumulator
+    // fold the group; recompute P1g for the next group
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
     if (g + 1 < md.n_groups) {
-      fence_proxy_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
+      const int* Gn = G + GROUP_INTS;
+      const int w1n = Gn[2] & ~15, n1n = ((Gn[3] + 15) & ~15) - w1n;
+      const int kS = (i1 + 15) & ~15;  // spins 0 .. i1-1 (zero beyond)
       if (t == 0) {
         const uint32_t aS = smem_u32(sS), aH1 = smem_u32(sH1), aH2 = smem_u32(sH2);
-        for (int kk = 0; kk < sN / 16; ++kk)
-          tc::mma_bf16(tP1, tc::smem_desc(aS + kk * 256u, 128u, 4u * 128u),
-                       tc::smem_desc(smem_u32(sW1) + (uint32_t)((s0 >> 4) + kk) * 256u, 128u, rbW1 / 16u * 128u), id1,
-                       (init1 || kk > 0) ? 1u : 0u);
         for (int kk = 0; kk < n1 / 16; ++kk)
-          tc::mma_bf16(tP2, tc::smem_desc(aH1 + kk * 256u, 128u, (2u * STC_WIN) / 16u * 128u),
-                       tc::smem_desc(smem_u32(sW2) + (uint32_t)((w1 >> 4) + kk) * 256u, 128u, rbW2 / 16u * 128u), id2,
+          tc::mma_bf16(tmem + (uint32_t)md.tcw1, tc::smem_desc(aH1 + kk * 256u, 128u, sbo1),
+                       tc::smem_desc(smem_u32(sW2) + (uint32_t)((w1 >> 4) + kk) * 256u, 128u, kbW2), id2,
                        (init2 || kk > 0) ? 1u : 0u);
         for (int kk = 0; kk < n2 / 16; ++kk)
-          tc::mma_bf16(tPO, tc::smem_desc(aH2 + kk * 256u, 128u, (2u * STC_WIN) / 16u * 128u),
-                       tc::smem_desc(smem_u32(sWo) + (uint32_t)((w2 >> 4) + kk) * 256u, 128u, rbWo / 16u * 128u), ido,
+          tc::mma_bf16(tmem + (uint32_t)(md.tcw1 + H2), tc::smem_desc(aH2 + kk * 256u, 128u, sbo2),
+                       tc::smem_desc(smem_u32(sWo) + (uint32_t)((w2 >> 4) + kk) * 256u, 128u, kbWo), ido,
                        (inito || kk > 0) ? 1u : 0u);
+        if (n1n > 0) {
+          const uint32_t id1 = tc::idesc(128, n1n, 1u) | idA;
+          for (int kk = 0; kk < kS / 16; ++kk)
+            tc::mma_bf16(tmem,
+                         tc::smem_desc(aS + kk * 256u, 128u, sboS),
+                         tc::smem_desc(smem_u32(sW1) + (uint32_t)(w1n >> 3) * kbW1 + (uint32_t)kk * 256u, 128u, kbW1),
+                         id1, kk > 0 ? 1u : 0u);
+        }
         tc::mma_commit(bar);
+        const uint32_t tbn = (uint32_t)(Gn[10] - Gn[12]) * 4u;
+        mbar_expect_tx(cbar, tbn);
+        if (tbn) bulk_g2s(TW, md.blocks + Gn[9] + Gn[12], tbn, cbar);
       }
-      init1 = init1 || sN > 0;
+      mma_pending = copy_pending = true;
       init2 = init2 || n1 > 0;
       inito = inito || n2 > 0;
+      p1ok = n1n > 0;
     }
   }
-  if (!ok && t == 0) atomicExch(li.status, 4);
-  __syncthreads();
+  if (!ok) {
+    // give the work still in flight a bounded time to finish before TMEM is freed
+    if (mma_pending) mbar_wait(bar, phase);
+    if (copy_pending) mbar_wait(cbar, cphase);
+    if (t == 0) atomicExch(li.status, 4);
+  }
   if (ok && valid) {
     if (spins) {
-      int8_t* out = spins + I.spin_units * li.batch + (long long)b * D;
-      for (int i = 0; i < D; ++i) out[i] = sp[t * D + i];
+      uint32_t* out = reinterpret_cast<uint32_t*>(spins + I.spin_units * li.batch + (long long)b * D);
+      for (int i = 0; i < D; i += 4) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int ii = i + j;
+          const bool up = ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0;
+          v |= (up ? 0x01u : 0xFFu) << (8 * j);
+        }
+        out[i >> 2] = v;
+      }
     }
     logq[(long long)k * li.batch + b] = lq;
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (w == 0) tc::tmem_dealloc(tmem, 512);
+  if (w == 0) tc::tmem_dealloc(tmem, (uint32_t)ncols);
 }
 
-int sample_tc_smem_bytes(int D, int H1, int H2, int wmax) { return sample_tc_smem(D, H1, H2, wmax); }
+int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
+  const int need = sample_tc_layout(D, H1, H2, tcw1, tcw2, twmax).total;
+  // never more resident CTAs per SM than the TMEM columns allow (228 KB of
+  // shared memory per SM, 1 KB of it reserved per CTA)
+  const int per_sm = sample_tc_tmem_cols(D, H2, tcw1) <= 256 ? 2 : 1;
+  const int floor_bytes = 228 * 1024 / (per_sm + 1) - 1024 + 16;
+  return need > floor_bytes ? need : floor_bytes;
+}
 
 cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int8_t* spins,
                              float* logq, const int8_t* given, cudaStream_t s) {
