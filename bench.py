@@ -339,7 +339,8 @@ def run_ours(a):
         "graph": graph, "autotuned": {"sample_tile": None if not model.tuned else model.tuned[0],
                                       "strip_tile": None if not model.tuned else model.tuned[1],
                                       "bwd_ctas_per_instance": None if not model.tuned else model.tuned[2],
-                                      "strip_adjoint_tile": None if not model.tuned else model.tuned[3]},
+                                      "strip_adjoint_tile": None if not model.tuned else model.tuned[3],
+                                      "tc_sampler_group_steps": None if not model.tuned else model.tuned[4]},
     }
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)

@@ -448,6 +448,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
 int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s);
+int pick_tc_plan(const tnvan_ctx* ctx);
 
 }  // namespace
 
@@ -920,7 +921,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
     auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
     std::vector<int> grp, src;
-    int ug1 = 0, ug2 = 0, ugo = 0, wmax = 0, twmax = 0, tcw1 = 16, tcw2 = 16;
+    int ug1 = 0, ug2 = 0, ugo = 0, wmax = 0;
     const int Hl = md.Hl;
     auto pad4 = [&]() {
       while (src.size() % 4) src.push_back(-1);
@@ -966,9 +967,6 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       pad4();
       const int gsize = (int)src.size() - gstart;
       wmax = std::max(wmax, gsize);
-      if (n_hidden >= 1) twmax = std::max(twmax, gsize - (t1 - gstart));
-      tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
-      tcw2 = std::max(tcw2, ((u2hi + 15) & ~15) - (u2lo & ~15));
       grp.insert(grp.end(), {i0, i1, u1lo, u1hi, u2lo, u2hi, n_hidden >= 1 ? off1 - gstart : 0,
                              n_hidden >= 2 ? off2 - gstart : 0, offo - gstart, gstart, gsize, 0,
                              n_hidden >= 1 ? t1 - gstart : 0, n_hidden >= 2 ? t2 - gstart : 0,
@@ -987,11 +985,6 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     }
     md.n_groups = (int)grp.size() / GROUP_INTS;
     md.wmax = wmax;
-    md.twmax = twmax;
-    md.tcw1 = tcw1;
-    md.tcw2 = tcw2;
-    md.sample_tc_ok = md.wtiles != nullptr && ug1 <= 32 && ug2 <= 32 && ugo <= 16 && D <= 128 &&
-                      sample_tc_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
     md.groups = dgrp;
     md.ug1 = ug1;
     md.ug2 = ug2;
@@ -1000,6 +993,67 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     md.blk_src = dsrc;
     md.n_blk = (long long)src.size();
   }
+  // Step groups of the tensor-core sampler, one plan per group-size limit
+  // (kTcGroupMax; the autotuner picks one): at most that many steps and 32
+  // units of each hidden layer completing inside a group.  Per group only the
+  // in-group triangles, each row padded to a multiple of 4 floats.
+  for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+    MadeDev::TcPlan& P = md.tc[p];
+    P = MadeDev::TcPlan{};
+    if (!md.wtiles || n_hidden != 2) continue;
+    const int GMAX = kTcGroupMax[p], UGMAX = 32;
+    auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
+    auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
+    std::vector<int> grp, src;
+    int twmax = 0, tcw1 = 16, tcw2 = 16;
+    bool fits = true;
+    auto add_tile = [&](int rlo, int rhi, int clo, int chi, long long wofs, int stride) {
+      const int off = (int)src.size();
+      const int rw = (chi - clo + 3) & ~3;
+      for (int r = rlo; r < rhi; ++r)
+        for (int c = 0; c < rw; ++c) src.push_back(c < chi - clo ? (int)(wofs + (long long)r * stride + clo + c) : -1);
+      return off;
+    };
+    for (int i0 = 0; i0 < D;) {
+      int i1 = i0 + 1;
+      while (i1 < D && i1 - i0 < GMAX && cnt(c1, i0, i1 + 1) <= UGMAX && cnt(c2, i0, i1 + 1) <= UGMAX) ++i1;
+      const int u1lo = before(c1, i0), u1hi = before(c1, i1);
+      const int u2lo = before(c2, i0), u2hi = before(c2, i1);
+      fits = fits && u1hi - u1lo <= UGMAX && u2hi - u2lo <= UGMAX;
+      const int gstart = (int)src.size();
+      const int t1 = add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
+      const int t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
+      const int to = add_tile(i0, i1, u2lo, u2hi, md.layer[2].dst_off, H[1]);
+      const int gsize = (int)src.size() - gstart;
+      twmax = std::max(twmax, gsize);
+      tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
+      tcw2 = std::max(tcw2, ((u2hi + 15) & ~15) - (u2lo & ~15));
+      grp.insert(grp.end(), {i0, i1, u1lo, u1hi, u2lo, u2hi, 0, 0, 0, gstart, gsize, 0, t1 - gstart, t2 - gstart,
+                             to - gstart});
+      i0 = i1;
+    }
+    int* dgrp = nullptr;
+    if ((rc = upload(ctx, in, grp, &dgrp))) return rc;
+    int* dsrc = nullptr;
+    if ((rc = upload(ctx, in, src, &dsrc))) return rc;
+    void* blk = nullptr;
+    if (!src.empty()) {
+      cudaError_t e2 = cudaMalloc(&blk, src.size() * sizeof(float));
+      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler triangles): %s", cudaGetErrorString(e2));
+      in.dev_allocs.push_back(blk);
+    }
+    P.n_groups = (int)grp.size() / GROUP_INTS;
+    P.groups = dgrp;
+    P.blocks = static_cast<float*>(blk);
+    P.src = dsrc;
+    P.n_blk = (long long)src.size();
+    P.twmax = twmax;
+    P.tcw1 = tcw1;
+    P.tcw2 = tcw2;
+    P.ok = fits && D <= 128 && sample_tc_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
+  }
+  md.sample_tc_ok = 0;
+  for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tc_ok = md.sample_tc_ok || md.tc[p].ok;
   void* packed = nullptr;
   cudaError_t e = cudaMalloc(&packed, off * sizeof(float));
   if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(packed params): %s", cudaGetErrorString(e));
@@ -1123,6 +1177,7 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
   for (const Instance& in : ctx->inst) {
     max_elems = std::max(max_elems, in.n_params);
     max_blk = std::max(max_blk, in.dev.made.n_blk);
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) max_blk = std::max(max_blk, in.dev.made.tc[p].n_blk);
   }
   {
     PROF("pack", s);
@@ -1147,6 +1202,7 @@ int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precisi
   for (const Instance& in : ctx->inst) {
     max_elems = std::max(max_elems, in.n_params);
     max_blk = std::max(max_blk, in.dev.made.n_blk);
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) max_blk = std::max(max_blk, in.dev.made.tc[p].n_blk);
   }
   CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
   std::vector<double> ones(ctx->inst.size(), 1.0);
@@ -1426,6 +1482,24 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
   auto sample = [&]() { return tnvan_sample_and_contract(ctx, betas, batch, 1, 0, precision, sp, lq, lz, stream); };
   bool tc_sampler = precision == TNVAN_BF16;
   for (const Instance& in : ctx->inst) tc_sampler = tc_sampler && in.dev.made.sample_tc_ok;
+  if (tc_sampler) {
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+      ctx->tune_tc_plan = p;
+      if (pick_tc_plan(ctx) != p) continue;
+      float ms = 0.f;
+      if ((rc = time_it(sample, &ms))) {
+        cleanup();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = p;
+      }
+    }
+    ctx->tune_tc_plan = best;
+  }
   if (!tc_sampler) {
     int best = 0;
     float best_ms = 1e30f;
@@ -1527,10 +1601,34 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     out[1] = ctx->tune_strip_tile;
     out[2] = ctx->tune_bwd_ctas;
     out[3] = ctx->tune_adj_tile;
+    out[4] = ctx->tune_tc_plan >= 0 ? kTcGroupMax[ctx->tune_tc_plan] : 0;
   }
   cudaError_t e = cudaStreamSynchronize(s);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  return TNVAN_OK;
+}
+
+int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (!c) return fail(ctx, TNVAN_E_ARG, "NULL tuning");
+  auto in = [](int v, std::initializer_list<int> ok) {
+    if (v == 0) return true;
+    for (int o : ok)
+      if (v == o) return true;
+    return false;
+  };
+  int plan = -1;
+  for (int p = 0; p < TNVAN_TC_PLANS; ++p)
+    if (kTcGroupMax[p] == c[4]) plan = p;
+  if (!in(c[0], {16, 32, 64}) || !in(c[1], {32, 64, 128}) || c[2] < 0 || !in(c[3], {32, 64, 96, 128}) ||
+      (c[4] != 0 && plan < 0))
+    return fail(ctx, TNVAN_E_ARG, "tuning value outside the autotuner's candidates");
+  ctx->tune_sample_tile = c[0];
+  ctx->tune_strip_tile = c[1];
+  ctx->tune_bwd_ctas = c[2];
+  ctx->tune_adj_tile = c[3];
+  ctx->tune_tc_plan = plan;
   return TNVAN_OK;
 }
 
@@ -1595,23 +1693,41 @@ int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s) {
   return TNVAN_OK;
 }
 
+// Tensor-core sampler plan usable by every instance: the autotuned one, else
+// the largest group-size limit that fits, else -1 (SIMT sampler).
+int pick_tc_plan(const tnvan_ctx* ctx) {
+  auto usable = [&](int p) {
+    if (p < 0 || p >= TNVAN_TC_PLANS) return false;
+    for (const Instance& in : ctx->inst)
+      if (!in.dev.made.tc[p].ok) return false;
+    return true;
+  };
+  if (usable(ctx->tune_tc_plan)) return ctx->tune_tc_plan;
+  for (int p = TNVAN_TC_PLANS - 1; p >= 0; --p)
+    if (usable(p)) return p;
+  return -1;
+}
+
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s) {
   int rc;
   bool tc_all = precision == TNVAN_BF16;
   for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
-  if (tc_all) {
+  int plan = -1;
+  if (tc_all) plan = pick_tc_plan(ctx);
+  if (plan >= 0) {
     if ((rc = pack_weight_tiles(ctx, s))) return rc;
     LaunchInfo li;
     if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
     li.seed = seed;
     li.step = step;
     int smem = 0;
-    for (const Instance& in : ctx->inst)
-      smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], in.dev.made.tcw1,
-                                                 in.dev.made.tcw2, in.dev.made.twmax));
+    for (const Instance& in : ctx->inst) {
+      const MadeDev::TcPlan& P = in.dev.made.tc[plan];
+      smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax));
+    }
     PROF(given ? "log_prob_tc" : "sample_tc", s);
-    CK(launch_sample_tc(ctx->d_inst, li, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
+    CK(launch_sample_tc(ctx->d_inst, li, plan, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
     return TNVAN_OK;
   }
   const int tile = pick_sample_tile(ctx);

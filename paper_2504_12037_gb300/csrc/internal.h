@@ -15,6 +15,7 @@
 #define TNVAN_MAX_STRIP_W 4
 #define TNVAN_MAX_ELIM_W 8
 #define GROUP_INTS 15
+#define TNVAN_TC_PLANS 3  // step-group size limits of the tensor-core sampler: 4, 6, 8
 
 namespace tnvan {
 
@@ -50,8 +51,19 @@ struct MadeDev {
   const int* groups;      // [n_groups][GROUP_INTS], see k_made.cu
   int ug1, ug2, ugo;      // largest group unit counts per layer
   int wmax;               // largest per-group weight block (floats)
-  int twmax;              // largest per-group triangle tiles (floats)
-  int tcw1, tcw2;         // widest 16-aligned unit window of a group, layers 1 and 2
+  // Tensor-core sampler: one step-group plan per group-size limit.  Per
+  // group only the in-group triangles, rows padded to 4 floats:
+  //   TW1 [n1g][r4(gi)], TW2 [n2g][r4(n1g)], TWo [gi][r4(n2g)].
+  struct TcPlan {
+    int ok;               // eligible (unit counts within the kernel's limits)
+    int n_groups;
+    const int* groups;    // [n_groups][GROUP_INTS]: i0 i1 u1lo u1hi u2lo u2hi - - - start size - TW1 TW2 TWo
+    float* blocks;        // gathered from `packed` on every call
+    const int* src;       // [n_blk] index into `packed`, -1 = zero
+    long long n_blk;
+    int twmax;            // largest group (floats)
+    int tcw1, tcw2;       // widest 16-aligned unit window of a group, layers 1 and 2
+  } tc[TNVAN_TC_PLANS];
   float* blocks;          // blocked weights (gathered from `packed` every call)
   const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
   long long n_blk;
@@ -204,6 +216,7 @@ struct tnvan_ctx {
   const unsigned long long* step_dev = nullptr;  // tnvan_set_step_counter
   // autotuned launch shapes (0 = built-in heuristic)
   int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0, tune_adj_tile = 0;
+  int tune_tc_plan = -1;  // tensor-core sampler step-group plan (-1 = default)
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
@@ -265,9 +278,10 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
                              const double* stats, float* partials, long long part_stride, int* status,
                              cudaStream_t s);
 int fused_bwd_smem_bytes(int D, int H1, int H2);
-cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int8_t* spins,
+cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
                              float* logq, const int8_t* given, cudaStream_t s);
 int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
+extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
                         float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 

@@ -32,12 +32,17 @@ __global__ void pack_kernel(const InstDev* __restrict__ inst) {
 }
 
 // Gather the blocked sampler weights from the packed layout.
+// blockIdx.z: 0 = the SIMT sampler's blocks, 1.. = the tensor-core plans' triangles
 __global__ void pack_blocks_kernel(const InstDev* __restrict__ inst) {
   const MadeDev& md = inst[blockIdx.y].made;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= md.n_blk) return;
-  const int src = md.blk_src[e];
-  md.blocks[e] = src >= 0 ? md.packed[src] : 0.f;
+  const int z = blockIdx.z;
+  const int* src = z == 0 ? md.blk_src : md.tc[z - 1].src;
+  float* dst = z == 0 ? md.blocks : md.tc[z - 1].blocks;
+  const long long n = z == 0 ? md.n_blk : md.tc[z - 1].n_blk;
+  if (e >= n) return;
+  const int j = src[e];
+  dst[e] = j >= 0 ? md.packed[j] : 0.f;
 }
 
 cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, long long max_blk,
@@ -46,7 +51,7 @@ cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, 
   pack_kernel<<<dim3((unsigned)((max_elems + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || max_blk == 0) return e;
-  pack_blocks_kernel<<<dim3((unsigned)((max_blk + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
+  pack_blocks_kernel<<<dim3((unsigned)((max_blk + 255) / 256), n_inst, 1 + TNVAN_TC_PLANS), 256, 0, s>>>(d_inst);
   return cudaGetLastError();
 }
 

@@ -35,11 +35,9 @@ namespace tnvan {
 namespace {
 
 // MN-major operand tile of 128 rows (samples) and kw columns (K, a multiple
-// of 16): element (m, k) at (m >> 3) * sbo + (k >> 3) * 128 + (k & 7) * 16 + (m & 7) * 2.
+// of 16): element (m, k) at (m >> 3) * sbo + (k >> 3) * 128 + (k & 7) * 16 +
+// (m & 7) * 2 = (m >> 3) * sbo + (m & 7) * 2 + 16 k.
 __host__ __device__ __forceinline__ uint32_t mn_sbo(int kw) { return (uint32_t)kw * 16u + 16u; }
-__device__ __forceinline__ uint32_t mn_off(int m, int k, uint32_t sbo) {
-  return (uint32_t)(m >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 16u + (uint32_t)(m & 7) * 2u;
-}
 __device__ __forceinline__ void st_bf16(unsigned char* base, uint32_t o, float v) {
   *reinterpret_cast<__nv_bfloat16*>(base + o) = __float2bfloat16(v);
 }
@@ -69,7 +67,9 @@ __device__ __forceinline__ float pick4(const uint32_t (&r)[4], int j) {
 }  // namespace
 
 #define STC_UG 32  // most units of one layer completing inside a group
-#define STC_GI 16  // most steps in a group
+#define STC_GI 8   // most steps in a group
+
+const int kTcGroupMax[TNVAN_TC_PLANS] = {4, 6, 8};
 
 struct SampleTcLayout {
   int wbytes, oS, oH1, oH2, oTW, oTab, oBar, total;
@@ -82,9 +82,9 @@ __host__ __device__ inline SampleTcLayout sample_tc_layout(int D, int H1, int H2
   L.oS = p;
   p += 16 * (int)mn_sbo(D);
   L.oH1 = p;
-  p += 16 * (int)mn_sbo(tcw1);
+  p += 16 * (int)mn_sbo(tcw1) + 64;  // + zeroed tail read by the 4-wide in-group loops
   L.oH2 = p;
-  p += 16 * (int)mn_sbo(tcw2);
+  p += 16 * (int)mn_sbo(tcw2) + 64;
   L.oTW = p;
   p += 4 * ((twmax + 3) & ~3);
   L.oTab = p;
@@ -101,18 +101,19 @@ __host__ __device__ inline int sample_tc_tmem_cols(int D, int H2, int tcw1) {
 }
 
 __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __restrict__ inst,
-                                                           const LaunchInfo li, int8_t* __restrict__ spins,
-                                                           float* __restrict__ logq,
+                                                           const LaunchInfo li, int plan,
+                                                           int8_t* __restrict__ spins, float* __restrict__ logq,
                                                            const int8_t* __restrict__ given) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
   const MadeDev& md = I.made;
+  const MadeDev::TcPlan& P = md.tc[plan];
   const int D = md.D, H1 = md.H1, H2 = md.H2;
   const int t = threadIdx.x, w = t >> 5;
   const int b = (blockIdx.x - li.tile_begin[k]) * 128 + t;
   const bool valid = b < li.batch;
-  const SampleTcLayout LY = sample_tc_layout(D, H1, H2, md.tcw1, md.tcw2, md.twmax);
+  const SampleTcLayout LY = sample_tc_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax);
   unsigned char* sW1 = smem;
   unsigned char* sW2 = sW1 + 2 * H1 * D;
   unsigned char* sWo = sW2 + 2 * H2 * H1;
@@ -128,12 +129,16 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + LY.oBar);  // MMA completion
   uint64_t* cbar = bar + 1;                                     // bulk copies
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
-  const uint32_t sboS = mn_sbo(D), sbo1 = mn_sbo(md.tcw1), sbo2 = mn_sbo(md.tcw2);
+  const uint32_t sboS = mn_sbo(D), sbo1 = mn_sbo(P.tcw1), sbo2 = mn_sbo(P.tcw2);
+  // this thread's row in the MN-major tiles: element k at row base + 16 k
+  const uint32_t rowb = (uint32_t)(t & 7) * 2u;
+  const uint32_t rbS = (uint32_t)(t >> 3) * sboS + rowb, rb1 = (uint32_t)(t >> 3) * sbo1 + rowb,
+                 rb2 = (uint32_t)(t >> 3) * sbo2 + rowb;
   const uint32_t kbW1 = 2u * D / 16u * 128u, kbW2 = 2u * H1 / 16u * 128u, kbWo = 2u * H2 / 16u * 128u;
   const float* b1 = md.packed + md.layer[0].dst_off + (long long)H1 * D;
   const float* b2 = md.packed + md.layer[1].dst_off + (long long)H2 * H1;
   const float* bo = md.packed + md.layer[2].dst_off + (long long)D * H2;
-  const int ncols = sample_tc_tmem_cols(D, H2, md.tcw1);
+  const int ncols = sample_tc_tmem_cols(D, H2, P.tcw1);
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_init(cbar, 1);
@@ -152,16 +157,16 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   uint32_t cphase = 0;
   bool copy_pending = false, mma_pending = false;
   if (t == 0) {
-    const int* G0 = md.groups;
+    const int* G0 = P.groups;
     const uint32_t tb0 = (uint32_t)(G0[10] - G0[12]) * 4u;
     mbar_expect_tx(cbar, (uint32_t)LY.wbytes + tb0);
     bulk_g2s(sW1, md.wtiles, (uint32_t)LY.wbytes, cbar);
-    if (tb0) bulk_g2s(TW, md.blocks + G0[9] + G0[12], tb0, cbar);
+    if (tb0) bulk_g2s(TW, P.blocks + G0[9] + G0[12], tb0, cbar);
   }
   copy_pending = true;
   const uint32_t tmem = *slot;
   const uint32_t lane_off = (uint32_t)(w * 32) << 16;
-  const uint32_t tP1 = tmem + lane_off, tP2 = tP1 + (uint32_t)md.tcw1, tPO = tP2 + (uint32_t)H2;
+  const uint32_t tP1 = tmem + lane_off, tP2 = tP1 + (uint32_t)P.tcw1, tPO = tP2 + (uint32_t)H2;
   const uint32_t idA = 1u << 15;  // A operand MN-major
   const uint32_t id2 = tc::idesc(128, H2, 1u) | idA, ido = tc::idesc(128, D, 1u) | idA;
   const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
@@ -173,8 +178,8 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   float lq = 0.f;
   uint4 rnd = make_uint4(0, 0, 0, 0);
   unsigned long long sb0 = 0ull, sb1 = 0ull;  // spin i is +1 iff bit i is set
-  for (int g = 0; g < md.n_groups; ++g) {
-    const int* G = md.groups + GROUP_INTS * g;
+  for (int g = 0; g < P.n_groups; ++g) {
+    const int* G = P.groups + GROUP_INTS * g;
     const int i0 = G[0], i1 = G[1], u1lo = G[2], u1hi = G[3], u2lo = G[4], u2hi = G[5];
     const int gi = i1 - i0, n1g = u1hi - u1lo, n2g = u2hi - u2lo;
     const int w1 = u1lo & ~15, w2 = u2lo & ~15;
@@ -189,9 +194,9 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
       }
       tc::fence_after_sync();
     }
-    for (int o = t * 16; o < 16 * (int)sbo1; o += 128 * 16)
+    for (int o = t * 16; o < 16 * (int)sbo1 + 64; o += 128 * 16)
       *reinterpret_cast<uint4*>(sH1 + o) = make_uint4(0, 0, 0, 0);
-    for (int o = t * 16; o < 16 * (int)sbo2; o += 128 * 16)
+    for (int o = t * 16; o < 16 * (int)sbo2 + 64; o += 128 * 16)
       *reinterpret_cast<uint4*>(sH2 + o) = make_uint4(0, 0, 0, 0);
     if (t < n1g) gb1[t] = __ldg(b1 + u1lo + t);
     if (t >= 32 && t - 32 < n2g) gb2[t - 32] = __ldg(b2 + u2lo + t - 32);
@@ -212,7 +217,10 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
     const float* TW1 = TW;
     const float* TW2 = TW + (G[13] - G[12]);
     const float* TWo = TW + (G[14] - G[12]);
-    uint32_t gbits = 0;  // in-group spins
+    const int s1 = (gi + 3) & ~3, s2 = (n1g + 3) & ~3, so = (n2g + 3) & ~3;  // triangle row strides
+    float sg[STC_GI];  // in-group spins (0 until drawn)
+#pragma unroll
+    for (int j = 0; j < STC_GI; ++j) sg[j] = 0.f;
     for (int i = i0; i < i1; ++i) {
       if ((i & 3) == 0)
         rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
@@ -232,6 +240,7 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
       }
       if (inito) tmem_ld1_nowait(tPO + (uint32_t)i, rc);
       tmem_wait9(ra, rb, rc);
+      // layer 1: + in-group spins (q <= 7 of them; sg is 0 for the rest)
       for (int u = ua; u < ub; ++u) {
         float a0;
         if (u - ua < 4) {
@@ -243,16 +252,22 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
           a0 = __uint_as_float(rx);
         }
         a0 += gb1[u - u1lo];
-        const float* wr = TW1 + (u - u1lo) * gi;
-        float a1 = 0.f;
-        int j = 0;
-        for (; j + 2 <= q; j += 2) {
-          a0 += ((gbits >> j) & 1u) ? wr[j] : -wr[j];
-          a1 += ((gbits >> (j + 1)) & 1u) ? wr[j + 1] : -wr[j + 1];
-        }
-        if (j < q) a0 += ((gbits >> j) & 1u) ? wr[j] : -wr[j];
-        st_bf16(sH1, mn_off(t, u - w1, sbo1), fmaxf(a0 + a1, 0.f));
+        const float4* wr = reinterpret_cast<const float4*>(TW1 + (u - u1lo) * s1);
+        const float4 wa = wr[0];
+        const float4 wb = s1 > 4 ? wr[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float a1 = wa.y * sg[1];
+        a0 = fmaf(wa.x, sg[0], a0);
+        a0 = fmaf(wa.z, sg[2], a0);
+        a1 = fmaf(wa.w, sg[3], a1);
+        a0 = fmaf(wb.x, sg[4], a0);
+        a1 = fmaf(wb.y, sg[5], a1);
+        a0 = fmaf(wb.z, sg[6], a0);
+        a1 = fmaf(wb.w, sg[7], a1);
+        st_bf16(sH1, rb1 + 16u * (uint32_t)(u - w1), fmaxf(a0 + a1, 0.f));
       }
+      // layer 2: + in-group layer-1 units completed so far (BF16 values, 4 at a time;
+      // units not computed yet read as 0 and carry masked weights)
+      const uint32_t o1 = rb1 + 16u * (uint32_t)(u1lo - w1);
       for (int v = va; v < vb; ++v) {
         float a0;
         if (v - va < 4) {
@@ -264,30 +279,31 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
           a0 = __uint_as_float(rx);
         }
         a0 += gb2[v - u2lo];
-        const float* wr = TW2 + (v - u2lo) * n1g;
+        const float* wr = TW2 + (v - u2lo) * s2;
         float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int u = u1lo;
-        for (; u + 4 <= ub; u += 4) {
-          a0 = fmaf(wr[u - u1lo], ld_bf16(sH1, mn_off(t, u - w1, sbo1)), a0);
-          a1 = fmaf(wr[u + 1 - u1lo], ld_bf16(sH1, mn_off(t, u + 1 - w1, sbo1)), a1);
-          a2 = fmaf(wr[u + 2 - u1lo], ld_bf16(sH1, mn_off(t, u + 2 - w1, sbo1)), a2);
-          a3 = fmaf(wr[u + 3 - u1lo], ld_bf16(sH1, mn_off(t, u + 3 - w1, sbo1)), a3);
+        for (int c = 0; c < ub - u1lo; c += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+          const uint32_t o = o1 + 16u * (uint32_t)c;
+          a0 = fmaf(w4.x, ld_bf16(sH1, o), a0);
+          a1 = fmaf(w4.y, ld_bf16(sH1, o + 16u), a1);
+          a2 = fmaf(w4.z, ld_bf16(sH1, o + 32u), a2);
+          a3 = fmaf(w4.w, ld_bf16(sH1, o + 48u), a3);
         }
-        for (; u < ub; ++u) a0 = fmaf(wr[u - u1lo], ld_bf16(sH1, mn_off(t, u - w1, sbo1)), a0);
-        st_bf16(sH2, mn_off(t, v - w2, sbo2), fmaxf((a0 + a1) + (a2 + a3), 0.f));
+        st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf((a0 + a1) + (a2 + a3), 0.f));
       }
       float x;
       {
-        const float* wr = TWo + q * n2g;
+        const float* wr = TWo + q * so;
+        const uint32_t o2 = rb2 + 16u * (uint32_t)(u2lo - w2);
         float a0 = __uint_as_float(rc) + gbo[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int v = u2lo;
-        for (; v + 4 <= vb; v += 4) {
-          a0 = fmaf(wr[v - u2lo], ld_bf16(sH2, mn_off(t, v - w2, sbo2)), a0);
-          a1 = fmaf(wr[v + 1 - u2lo], ld_bf16(sH2, mn_off(t, v + 1 - w2, sbo2)), a1);
-          a2 = fmaf(wr[v + 2 - u2lo], ld_bf16(sH2, mn_off(t, v + 2 - w2, sbo2)), a2);
-          a3 = fmaf(wr[v + 3 - u2lo], ld_bf16(sH2, mn_off(t, v + 3 - w2, sbo2)), a3);
+        for (int c = 0; c < vb - u2lo; c += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+          const uint32_t o = o2 + 16u * (uint32_t)c;
+          a0 = fmaf(w4.x, ld_bf16(sH2, o), a0);
+          a1 = fmaf(w4.y, ld_bf16(sH2, o + 16u), a1);
+          a2 = fmaf(w4.z, ld_bf16(sH2, o + 32u), a2);
+          a3 = fmaf(w4.w, ld_bf16(sH2, o + 48u), a3);
         }
-        for (; v < vb; ++v) a0 = fmaf(wr[v - u2lo], ld_bf16(sH2, mn_off(t, v - w2, sbo2)), a0);
         x = (a0 + a1) + (a2 + a3);
       }
       const float pr = 1.f / (1.f + expf(-x));
@@ -296,12 +312,13 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
       bool up = u < pr;
       if (gv) up = valid ? gv[i] > 0 : true;
       const float s = up ? 1.f : -1.f;
+#pragma unroll
+      for (int j = 0; j < STC_GI; ++j) sg[j] = j == q ? s : sg[j];
       if (up) {
-        gbits |= 1u << q;
         if (i < 64) sb0 |= 1ull << i;
         else sb1 |= 1ull << (i - 64);
       }
-      st_bf16(sS, mn_off(t, i, sboS), s);
+      st_bf16(sS, rbS + 16u * (uint32_t)i, s);
       lq -= softplusf(-s * x);
     }
     // fold the group; recompute P1g for the next group
@@ -309,18 +326,18 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (g + 1 < md.n_groups) {
+    if (g + 1 < P.n_groups) {
       const int* Gn = G + GROUP_INTS;
       const int w1n = Gn[2] & ~15, n1n = ((Gn[3] + 15) & ~15) - w1n;
       const int kS = (i1 + 15) & ~15;  // spins 0 .. i1-1 (zero beyond)
       if (t == 0) {
         const uint32_t aS = smem_u32(sS), aH1 = smem_u32(sH1), aH2 = smem_u32(sH2);
         for (int kk = 0; kk < n1 / 16; ++kk)
-          tc::mma_bf16(tmem + (uint32_t)md.tcw1, tc::smem_desc(aH1 + kk * 256u, 128u, sbo1),
+          tc::mma_bf16(tmem + (uint32_t)P.tcw1, tc::smem_desc(aH1 + kk * 256u, 128u, sbo1),
                        tc::smem_desc(smem_u32(sW2) + (uint32_t)((w1 >> 4) + kk) * 256u, 128u, kbW2), id2,
                        (init2 || kk > 0) ? 1u : 0u);
         for (int kk = 0; kk < n2 / 16; ++kk)
-          tc::mma_bf16(tmem + (uint32_t)(md.tcw1 + H2), tc::smem_desc(aH2 + kk * 256u, 128u, sbo2),
+          tc::mma_bf16(tmem + (uint32_t)(P.tcw1 + H2), tc::smem_desc(aH2 + kk * 256u, 128u, sbo2),
                        tc::smem_desc(smem_u32(sWo) + (uint32_t)((w2 >> 4) + kk) * 256u, 128u, kbWo), ido,
                        (inito || kk > 0) ? 1u : 0u);
         if (n1n > 0) {
@@ -334,7 +351,7 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
         tc::mma_commit(bar);
         const uint32_t tbn = (uint32_t)(Gn[10] - Gn[12]) * 4u;
         mbar_expect_tx(cbar, tbn);
-        if (tbn) bulk_g2s(TW, md.blocks + Gn[9] + Gn[12], tbn, cbar);
+        if (tbn) bulk_g2s(TW, P.blocks + Gn[9] + Gn[12], tbn, cbar);
       }
       mma_pending = copy_pending = true;
       init2 = init2 || n1 > 0;
@@ -378,13 +395,13 @@ int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
   return need > floor_bytes ? need : floor_bytes;
 }
 
-cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int8_t* spins,
+cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
                              float* logq, const int8_t* given, cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  sample_tc_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, li, spins, logq, given);
+  sample_tc_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, li, plan, spins, logq, given);
   return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ SIGNATURES = {
     "tnvan_noalloc_last_error": (ctypes.c_char_p, []),
     "tnvan_set_step_counter": (_c_int, [_vp, _vp]),
     "tnvan_autotune": (_c_int, [_vp, _dblp, _c_int, _c_int, _vp, _i32p]),
+    "tnvan_set_tuning": (_c_int, [_vp, _i32p]),
     "tnvan_profile": (_c_int, [_vp, _c_int]),
     "tnvan_profile_read": (_c_int, [_vp, _c_int, ctypes.c_char_p, _c_int, _dblp, _i64p]),
 }
@@ -188,11 +189,19 @@ class Context:
 
     def autotune(self, betas, batch: int, precision: int, stream=None):
         """Time candidate launch shapes on a synthetic batch and keep the fastest;
-        returns the chosen (sampler tile, strip tile, backward CTAs, strip adjoint tile)."""
+        returns the chosen (sampler tile, strip tile, backward CTAs, strip adjoint tile,
+        tensor-core sampler step-group size)."""
         b, pb = _arr(betas, np.float64)
-        out = (ctypes.c_int32 * 4)()
+        out = (ctypes.c_int32 * 5)()
         self._check(lib().tnvan_autotune(self._h, pb, batch, precision, _stream(stream), out))
-        return tuple(out[:4])
+        return tuple(out[:5])
+
+    def set_tuning(self, choices):
+        """Reuse launch shapes (the 5-tuple autotune returns; 0 = heuristic)."""
+        c, pc = _arr(list(choices), np.int32)
+        if c.shape[0] != 5:
+            raise ValueError("expected 5 tuning values")
+        self._check(lib().tnvan_set_tuning(self._h, pc))
 
     def profile(self, enable: bool):
         self._check(lib().tnvan_profile(self._h, int(enable)))
