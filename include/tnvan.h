@@ -144,6 +144,22 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
                               uint64_t step, int precision, int8_t* d_spins, float* d_logq,
                               double* d_logZR, void* stream);
 
+/* tnvan_sample_and_contract plus the contraction adjoint of tnvan_backward
+ * (Eq. 4 differentiated) in the same pass: for strip instances one kernel
+ * sweeps each strip forward (log Z_R, identical to tnvan_contract's) and
+ * backward (d log Z_R / d beta per sample, d log Z_R / d J_e as the batch
+ * mean).  A training step then calls tnvan_backward with d_dbeta and d_dJ
+ * NULL.  Not a separate step of the paper: the same quantities, computed
+ * together.
+ *   d_dbeta   device double out [n_instances * batch], or NULL.
+ *   d_dJ      device double out [sum_k n_edges_k] (instances back to back,
+ *             input edge order), or NULL.
+ * Other arguments and errors as tnvan_sample_and_contract; TNVAN_E_UNSUPPORTED
+ * if a strip's left vectors do not fit in shared memory. */
+int tnvan_sample_contract_adjoint(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed,
+                                  uint64_t step, int precision, int8_t* d_spins, float* d_logq,
+                                  double* d_logZR, double* d_dbeta, double* d_dJ, void* stream);
+
 /* Eq. 6 and 8 alone: log q_theta(s) for caller-given width-set
  * configurations d_spins (device int8 +-1, layout above), by the same
  * masked forward the sampler of that precision runs (teacher forcing).

@@ -445,7 +445,10 @@ int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_
 
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s, bool strips = true);
-int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s);
+int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, int precision,
+                double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s);
+int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s);
+int sampler_pack_mask(const tnvan_ctx* ctx, int precision);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s);
 int pick_tc_plan(const tnvan_ctx* ctx);
@@ -667,8 +670,8 @@ int tnvan_create(tnvan_ctx** out, int device) {
   if (!ctx) return fail(nullptr, TNVAN_E_NOMEM, "host allocation failed");
   ctx->device = device;
   DeviceGuard g(device);
-  e = cudaMalloc(&ctx->d_status, 4 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 4 * sizeof(int));
+  e = cudaMalloc(&ctx->d_status, (4 + TNVAN_MAX_INST) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, (4 + TNVAN_MAX_INST) * sizeof(int));
   if (e != cudaSuccess) {
     delete ctx;
     return fail(nullptr, TNVAN_E_NOMEM, "cudaMalloc(status): %s", cudaGetErrorString(e));
@@ -1173,18 +1176,28 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
   if (rc) return rc;
   if (batch == 0) return TNVAN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  long long max_elems = 0, max_blk = 0;
-  for (const Instance& in : ctx->inst) {
-    max_elems = std::max(max_elems, in.n_params);
-    max_blk = std::max(max_blk, in.dev.made.n_blk);
-    for (int p = 0; p < TNVAN_TC_PLANS; ++p) max_blk = std::max(max_blk, in.dev.made.tc[p].n_blk);
-  }
-  {
-    PROF("pack", s);
-    CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
-  }
+  if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision), s))) return rc;
   if ((rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s))) return rc;
   return contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
+}
+
+int tnvan_sample_contract_adjoint(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed,
+                                  uint64_t step, int precision, int8_t* d_spins, float* d_logq,
+                                  double* d_logZR, double* d_dbeta, double* d_dJ, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (!d_dbeta && !d_dJ)
+    return tnvan_sample_and_contract(ctx, betas, batch, seed, step, precision, d_spins, d_logq, d_logZR, stream);
+  if (batch < 0) return fail(ctx, TNVAN_E_ARG, "batch < 0");
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
+  if (batch > 0 && (!d_spins || !d_logq || !d_logZR)) return fail(ctx, TNVAN_E_ARG, "NULL output");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (batch == 0) return TNVAN_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision), s))) return rc;
+  if ((rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s))) return rc;
+  return run_adjoint(ctx, betas, batch, d_spins, precision, d_logZR, d_dbeta, d_dJ, s);
 }
 
 int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precision, float* d_logq,
@@ -1198,13 +1211,7 @@ int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precisi
   if (rc) return rc;
   if (batch == 0) return TNVAN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  long long max_elems = 0, max_blk = 0;
-  for (const Instance& in : ctx->inst) {
-    max_elems = std::max(max_elems, in.n_params);
-    max_blk = std::max(max_blk, in.dev.made.n_blk);
-    for (int p = 0; p < TNVAN_TC_PLANS; ++p) max_blk = std::max(max_blk, in.dev.made.tc[p].n_blk);
-  }
-  CK(launch_pack(ctx->d_inst, (int)ctx->inst.size(), max_elems, max_blk, s), "pack kernel");
+  if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision), s))) return rc;
   std::vector<double> ones(ctx->inst.size(), 1.0);
   return run_sampler(ctx, ones.data(), batch, 0, 0, precision, nullptr, d_logq, d_spins, s);
 }
@@ -1236,7 +1243,7 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   {
     PROF("reduce", s);
-    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernels");
   }
   const int n = li.n_inst;
   std::vector<double> st(8 * n);
@@ -1268,31 +1275,17 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the strip adjoint (d/dbeta and d/dJ of strip instances in one pass) keeps
-  // a strip's left vectors in shared memory: 128, 64 or 32 samples per CTA
-  bool any_strip = false, other = false;
-  for (const Instance& in : ctx->inst) {
-    if (in.kind == 0) any_strip = true;
-    else other = true;
-  }
-  int adj_tile = 0, adj_smem = 0, adj_lv = 0;
-  if (any_strip && (d_dbeta || d_dJ)) {
-    if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv))) return rc;
-  }
   long long max_elems = 0;
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
-  {
-    PROF("pack", s);
-    CK(launch_pack(ctx->d_inst, li.n_inst, max_elems, 0, s), "pack kernel");
-  }
-  {
-    PROF("reduce", s);
-    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, s), "reduce kernels");
-  }
   bool all_fused = precision == TNVAN_BF16;
   for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
+  if ((rc = pack_network(ctx, PACK_FLAT | (all_fused ? PACK_TILES : 0), s))) return rc;
+  {
+    PROF("reduce", s);
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernels");
+  }
   if (all_fused) {
     // one CTA per chunk of 128-sample tiles, about one CTA per SM overall
     const int n_inst = (int)ctx->inst.size();
@@ -1304,7 +1297,6 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     for (int k = 0; k <= lf.n_inst; ++k) lf.tile_begin[k] = k * ((tiles + per - 1) / per);
     lf.tile = per;
     if ((rc = ensure_grad_ws(ctx, (size_t)lf.tile_begin[lf.n_inst] * (size_t)max_elems))) return rc;
-    if ((rc = pack_weight_tiles(ctx, s))) return rc;
     int smem = 0;
     for (const Instance& in : ctx->inst)
       smem = std::max(smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
@@ -1354,67 +1346,7 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
          "gradient reduce kernel");
     }
   }
-  if (d_dJ) {
-    long long ne = 0;
-    for (const Instance& in : ctx->inst) ne += in.m;
-    CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
-  }
-  if (d_dbeta && other) {
-    // forward-mode d/dbeta of dense and elimination instances: a second
-    // contraction pass that writes only the derivative
-    if ((rc = contract_all(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, s, false))) return rc;
-  }
-  if (adj_tile) {
-    LaunchInfo la;
-    if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
-    int max_edges = 0;
-    for (const Instance& in : ctx->inst)
-      if (in.kind == 0) max_edges = std::max(max_edges, in.m);
-    const int stride = (max_edges + 3) & ~3;
-    if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
-    PROF(d_dJ ? "strips_adj" : "strips_dbeta", s);
-    CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_dbeta, d_dJ ? ctx->d_dj_part : nullptr,
-                         stride, d_dJ, s),
-       "strip adjoint kernel");
-  }
-  if (d_dJ) {
-    LaunchInfo lt;
-    if ((rc = fill_launch(ctx, betas, batch, 128, lt))) return rc;
-    if (other) {
-      {
-        PROF("ww_dJ", s);
-        CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
-      }
-      {
-        PROF("dense_dJ", s);
-        CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
-      }
-      int arena = 0, pairs = 0, steps = 0, Dm = 0, me = 0;
-      bool any_gen = false;
-      for (const Instance& in : ctx->inst)
-        if (in.kind == 2) {
-          any_gen = true;
-          arena = std::max(arena, in.g_max_entries);
-          pairs = std::max(pairs, in.g_npairs);
-          steps = std::max(steps, in.g_max_steps);
-          Dm = std::max(Dm, (int)in.W.size());
-          me = std::max(me, in.m);
-        }
-      if (any_gen) {
-        int T = 64;
-        while (T > 1 && general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T) > 200 * 1024) T /= 2;
-        const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T);
-        if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
-        LaunchInfo lg;
-        if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
-        const int stride = (me + 3) & ~3;
-        if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
-        PROF("general_dJ", s);
-        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, pairs, steps, d_spins, ctx->d_dj_part, stride, d_dJ, s),
-           "general adjoint kernel");
-      }
-    }
-  }
+  if (d_dbeta || d_dJ) return run_adjoint(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, d_dJ, s);
   return TNVAN_OK;
 }
 
@@ -1682,15 +1614,21 @@ int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, doub
 
 namespace {
 
-int pack_weight_tiles(tnvan_ctx* ctx, cudaStream_t s) {
+// Rebuild what the kernels read from the networks (segments in `mask`).
+int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s) {
   long long mx = 0;
-  for (const Instance& in : ctx->inst) {
-    const MadeDev& md = in.dev.made;
-    if (md.wtiles) mx = std::max(mx, (long long)md.H1 * md.D + (long long)md.H2 * md.H1 + (long long)md.D * md.H2);
-  }
-  PROF("pack_tiles", s);
-  CK(launch_pack_tiles(ctx->d_inst, (int)ctx->inst.size(), mx, s), "weight tile kernel");
+  for (const Instance& in : ctx->inst) mx = std::max(mx, pack_elems(in.dev.made, mask));
+  PROF("pack", s);
+  CK(launch_pack_all(ctx->d_inst, (int)ctx->inst.size(), mx, mask, s), "pack kernel");
   return TNVAN_OK;
+}
+
+// Segments the sampler of this precision reads.
+int sampler_pack_mask(const tnvan_ctx* ctx, int precision) {
+  bool tc_all = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
+  if (tc_all && pick_tc_plan(ctx) >= 0) return PACK_FLAT | PACK_TILES | PACK_TC;
+  return PACK_FLAT | PACK_SIMT;
 }
 
 // Tensor-core sampler plan usable by every instance: the autotuned one, else
@@ -1716,7 +1654,6 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
   int plan = -1;
   if (tc_all) plan = pick_tc_plan(ctx);
   if (plan >= 0) {
-    if ((rc = pack_weight_tiles(ctx, s))) return rc;
     LaunchInfo li;
     if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
     li.seed = seed;
@@ -1784,6 +1721,88 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
   }
   return TNVAN_OK;
 }
+
+// Contraction adjoint (Eq. 4 differentiated): d log Z_R / d beta per sample
+// and the batch-mean d log Z_R / d J, each optional; with d_logZR non-NULL
+// also log Z_R itself (strip instances from the adjoint's own forward sweep,
+// the other kinds from their contraction kernels).
+int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, int precision,
+                double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s) {
+  int rc;
+  bool any_strip = false, other = false;
+  for (const Instance& in : ctx->inst) {
+    if (in.kind == 0) any_strip = true;
+    else other = true;
+  }
+  // the strip adjoint keeps a strip's left vectors in shared memory: 128,
+  // 96, 64 or 32 samples per CTA
+  int adj_tile = 0, adj_smem = 0, adj_lv = 0;
+  if (any_strip && (rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv))) return rc;
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  if (d_dJ) {
+    long long ne = 0;
+    for (const Instance& in : ctx->inst) ne += in.m;
+    CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
+  }
+  if (other && (d_logZR || d_dbeta)) {
+    // dense and elimination instances: log Z_R and forward-mode d/dbeta
+    if ((rc = contract_all(ctx, betas, batch, d_spins, precision, d_logZR, d_dbeta, s, false))) return rc;
+  }
+  if (adj_tile) {
+    LaunchInfo la;
+    if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
+    int max_edges = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 0) max_edges = std::max(max_edges, in.m);
+    const int stride = (max_edges + 3) & ~3;
+    if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
+    PROF(d_dJ ? "strips_adj" : "strips_dbeta", s);
+    CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
+                         d_dJ ? ctx->d_dj_part : nullptr, stride, d_dJ, s),
+       "strip adjoint kernel");
+  }
+  if (d_dJ) {
+    LaunchInfo lt;
+    if ((rc = fill_launch(ctx, betas, batch, 128, lt))) return rc;
+    if (other) {
+      {
+        PROF("ww_dJ", s);
+        CK(launch_ww(ctx->d_inst, li, d_spins, d_dJ, s), "W-W adjoint kernel");
+      }
+      {
+        PROF("dense_dJ", s);
+        CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
+      }
+      int arena = 0, pairs = 0, steps = 0, Dm = 0, me = 0;
+      bool any_gen = false;
+      for (const Instance& in : ctx->inst)
+        if (in.kind == 2) {
+          any_gen = true;
+          arena = std::max(arena, in.g_max_entries);
+          pairs = std::max(pairs, in.g_npairs);
+          steps = std::max(steps, in.g_max_steps);
+          Dm = std::max(Dm, (int)in.W.size());
+          me = std::max(me, in.m);
+        }
+      if (any_gen) {
+        int T = 64;
+        while (T > 1 && general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T) > 200 * 1024) T /= 2;
+        const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T);
+        if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
+        LaunchInfo lg;
+        if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
+        const int stride = (me + 3) & ~3;
+        if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
+        PROF("general_dJ", s);
+        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, pairs, steps, d_spins, ctx->d_dj_part, stride, d_dJ, s),
+           "general adjoint kernel");
+      }
+    }
+  }
+  return TNVAN_OK;
+}
+
 
 // Dense leftover block: R (|R| <= 16, in index order) split in halves A = R[0..7]
 // and B = R[8..15]; missing spins are free phantoms (no couplings).

@@ -227,7 +227,7 @@ struct tnvan_ctx {
   bool dirty = true;                 // descriptors changed since last upload
   // workspaces (grown on demand, or by tnvan_reserve)
   double* d_stats = nullptr;         // [n_inst][8]
-  int* d_status = nullptr;           // [4] device status words
+  int* d_status = nullptr;           // [4] device status words, then [TNVAN_MAX_INST] reduction counters
   size_t ws_bytes = 0;
   void* d_ws = nullptr;              // general workspace
   int reserved_batch = 0;
@@ -240,16 +240,16 @@ struct tnvan_ctx {
 namespace tnvan {
 
 // Kernel launchers (defined in the .cu files).  All return a cudaError_t.
-cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, long long max_blk,
-                        cudaStream_t s);
-cudaError_t launch_pack_tiles(const InstDev* d_inst, int n_inst, long long max_tile_elems, cudaStream_t s);
+enum { PACK_FLAT = 1, PACK_TILES = 2, PACK_SIMT = 4, PACK_TC = 8 };
+long long pack_elems(const MadeDev& md, int mask);
+cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s);
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);
 cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           const int8_t* spins, double* logZR, double* dbeta, cudaStream_t s);
 cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
-                              const int8_t* spins, double* dbeta, float* part, int part_stride, double* dJ,
-                              cudaStream_t s);
+                              const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
+                              double* dJ, cudaStream_t s);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s);
@@ -263,7 +263,7 @@ int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, i
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
-                          const float* logq, double* stats, cudaStream_t s);
+                          const float* logq, double* stats, int* counters, cudaStream_t s);
 cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                             int precision, const int8_t* spins, const double* logZR,
                             const float* logq, const double* stats, float* partials,

@@ -1,7 +1,8 @@
 // Fused BF16 backward of the MADE network on tcgen05 (Eq. 10), for networks
 // with two hidden layers of at most 128 units and at most 128 inputs.
 //
-// One CTA (128 threads, thread = sample = TMEM lane) walks the 128-sample
+// One CTA (256 threads: two warpgroups, each thread one sample = TMEM lane
+// and every other 16-column chunk of each epilogue) walks the 128-sample
 // tiles of its chunk.  Per tile, everything stays on chip:
 //   A1 = relu(S W1^T + b1), A2 = relu(A1 W2^T + b2), X = A2 Wo^T + bo,
 //   dX = w_b s sigmoid(-s x), dA2 = (dX Wo) 1[A2 > 0], dA1 = (dA2 W2) 1[A1 > 0],
@@ -52,11 +53,24 @@ __device__ __forceinline__ void store8(unsigned char* sm_base, uint32_t rowbytes
   *reinterpret_cast<uint4*>(sm_base + o) = u;
 }
 
-__device__ __forceinline__ float load1(const unsigned char* sm_base, uint32_t rowbytes, int r, int c) {
-  const uint32_t o = (uint32_t)(r >> 3) * (rowbytes / 16u) * 128u + (uint32_t)(c >> 3) * 128u +
-                     (uint32_t)(r & 7) * 16u + (uint32_t)(c & 7) * 2u;
-  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sm_base + o));
-}
+// Per-thread bit masks of up to 128 columns (4 words): set / get 16 bits
+// at a column c that is a multiple of 16.
+struct Mask128 {
+  uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+  __device__ __forceinline__ void put16(int c, uint32_t m16) {
+    const uint32_t v = m16 << (c & 16);
+    const int j = c >> 5;
+    w0 |= j == 0 ? v : 0u;
+    w1 |= j == 1 ? v : 0u;
+    w2 |= j == 2 ? v : 0u;
+    w3 |= j == 3 ? v : 0u;
+  }
+  __device__ __forceinline__ uint32_t get16(int c) const {
+    const int j = c >> 5;
+    const uint32_t w = j == 0 ? w0 : (j == 1 ? w1 : (j == 2 ? w2 : w3));
+    return (w >> (c & 16)) & 0xFFFFu;
+  }
+};
 
 }  // namespace
 
@@ -74,10 +88,10 @@ struct FusedBwdArgs {
 __host__ __device__ inline int fused_bwd_smem(int D, int H1, int H2) {
   const int w = H1 * D + H2 * H1 + D * H2;                        // weights
   const int a = 128 * ((D + 16) + (H1 + 16) + (H2 + 16) + D + H2);  // S, A1, A2/dA1, dX, dA2
-  return 2 * (w + a) + 64;  // + barriers and the TMEM slot
+  return 2 * (w + a) + 4 * (H1 + H2 + D) + 64;  // + biases, barriers and the TMEM slot
 }
 
-__global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
+__global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
                                                            const LaunchInfo li, FusedBwdArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int k = find_inst(li, blockIdx.x);
@@ -85,7 +99,9 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   const MadeDev& md = I.made;
   if (!md.fused_ok) return;
   const int D = md.D, H1 = md.H1, H2 = md.H2;
-  const int t = threadIdx.x, w = t >> 5;
+  // two warpgroups: thread (g, r) owns TMEM lane / sample row r and the
+  // 16-column chunks c with (c / 16) % 2 == g of every epilogue
+  const int tid = threadIdx.x, w = tid >> 5, t = tid & 127, g = tid >> 7;
   const int B = li.batch;
   const int tiles_total = (B + 127) / 128;
   const int c_idx = blockIdx.x - li.tile_begin[k];
@@ -101,6 +117,9 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   unsigned char* sA2 = p; p += 128 * (H2 + 16) * 2;  // later dA1 (128 x H1)
   unsigned char* sdX = p; p += 128 * D * 2;           // must precede sdA2 (MN view overruns into it)
   unsigned char* sdA2 = p; p += 128 * H2 * 2;
+  float* sb1 = reinterpret_cast<float*>(p); p += 4 * H1;  // biases
+  float* sb2 = reinterpret_cast<float*>(p); p += 4 * H2;
+  float* sbo = reinterpret_cast<float*>(p); p += 4 * D;
   uint64_t* bar = reinterpret_cast<uint64_t*>(p);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);  // cbar is bar + 2
   const Tile tW1{smem_u32(sW1), D}, tW2{smem_u32(sW2), H1}, tWo{smem_u32(sWo), H2};
@@ -116,7 +135,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   // BF16 weight tiles (laid out once per call in the canonical K-major form)
   // arrive with one bulk copy; W1, W2, Wo are contiguous in both places
   uint64_t* cbar = bar + 2;
-  if (t == 0) {
+  if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(cbar, 1);
   }
@@ -124,10 +143,13 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
     tc::tmem_alloc(slot, 512);
     tc::tmem_relinquish();
   }
+  for (int u = tid; u < H1; u += 256) sb1[u] = __ldg(b1 + u);
+  for (int u = tid; u < H2; u += 256) sb2[u] = __ldg(b2 + u);
+  for (int u = tid; u < D; u += 256) sbo[u] = __ldg(bo + u);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (t == 0) {
+  if (tid == 0) {
     const uint32_t wbytes = 2u * (uint32_t)(H1 * D + H2 * H1 + D * H2);
     mbar_expect_tx(cbar, wbytes);
     bulk_g2s(sW1, md.wtiles, wbytes, cbar);
@@ -135,7 +157,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   const bool weights_ok = mbar_wait(cbar, 0);
   const uint32_t tmem = *slot;
   const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)(D + 16), tGo = tG2 + (uint32_t)(H1 + 16);
-  const uint32_t lane_off = (uint32_t)(w * 32) << 16;
+  const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
   const uint32_t id_fwd1 = tc::idesc(128, H1, 1u), id_fwd2 = tc::idesc(128, H2, 1u), id_fwd3 = tc::idesc(128, D, 1u);
   const uint32_t id_d2 = tc::idesc(128, H2, 1u) | (1u << 16);         // B MN-major
   const uint32_t id_d1 = tc::idesc(128, H1, 1u) | (1u << 16);
@@ -148,7 +170,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
   uint32_t phase = 0;
   bool ok = weights_ok;
   auto mma_wait = [&]() -> bool {
-    if (t == 0) tc::mma_commit(bar);
+    if (tid == 0) tc::mma_commit(bar);
     const bool r = mbar_wait(bar, phase);
     phase ^= 1u;
     tc::fence_after_sync();
@@ -165,62 +187,84 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
     const int b = tile * 128 + t;
     const bool valid = b < B;
     const float vf = valid ? 1.f : 0.f;
-    // spins -> S tile (+ ones column)
-    float sp[8];
-    for (int c = 0; c < D + 16; c += 8) {
+    // spins -> S tile (+ ones column), 16 per vector load; mS bit f = (s_f > 0)
+    Mask128 mS, m1, m2;
+    for (int c = 16 * g; c < D; c += 32) {
+      uint4 raw = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+      if (valid) raw = *reinterpret_cast<const uint4*>(Sg + (long long)b * D + c);
+      const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+      float sp[16];
+      uint32_t m16 = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int f = c + i;
-        sp[i] = f < D ? (valid ? (float)Sg[(long long)b * D + f] : 0.f) : (f == D ? vf : 0.f);
+      for (int i = 0; i < 16; ++i) {
+        const int8_t sv = (int8_t)((wv[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+        sp[i] = valid ? (float)sv : 0.f;
+        m16 |= (sv > 0 ? 1u : 0u) << i;
       }
+      mS.put16(c, m16);
       store8(sS, tS.rowbytes(), t, c, sp);
+      store8(sS, tS.rowbytes(), t, c + 8, sp + 8);
+    }
+    if (((D >> 4) & 1) == g) {
+      float sp[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) sp[i] = i == 0 ? vf : 0.f;
+      store8(sS, tS.rowbytes(), t, D, sp);
+      store8(sS, tS.rowbytes(), t, D + 8, sp + 8);
     }
     const float wb = valid ? (float)(wsc * (args.logZR[(long long)k * B + b] - (double)args.logq[(long long)k * B + b] - mean)) : 0.f;
     sync_for_mma();
     // fwd1: scratch = S W1^T
-    if (t == 0)
+    if (tid == 0)
       for (int kk = 0; kk < D / 16; ++kk) tc::mma_bf16(tScr, tS.kdesc(kk), tW1.kdesc(kk), id_fwd1, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 0; c < H1 + 16; c += 16) {
+    for (int c = 16 * g; c < H1 + 16; c += 32) {
       float v[16];
       if (c < H1) tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+      uint32_t m16 = 0;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int u = c + i;
-        v[i] = u < H1 ? fmaxf(v[i] + __ldg(b1 + u), 0.f) * vf : (u == H1 ? vf : 0.f);
+        v[i] = u < H1 ? fmaxf(v[i] + sb1[u], 0.f) * vf : (u == H1 ? vf : 0.f);
+        m16 |= (u < H1 && v[i] > 0.f ? 1u : 0u) << i;
       }
+      if (c < H1) m1.put16(c, m16);
       store8(sA1, tA1.rowbytes(), t, c, v);
       store8(sA1, tA1.rowbytes(), t, c + 8, v + 8);
     }
     sync_for_mma();
     // fwd2: scratch = A1 W2^T
-    if (t == 0)
+    if (tid == 0)
       for (int kk = 0; kk < H1 / 16; ++kk) tc::mma_bf16(tScr, tA1.kdesc(kk), tW2.kdesc(kk), id_fwd2, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 0; c < H2 + 16; c += 16) {
+    for (int c = 16 * g; c < H2 + 16; c += 32) {
       float v[16];
       if (c < H2) tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+      uint32_t m16 = 0;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int u = c + i;
-        v[i] = u < H2 ? fmaxf(v[i] + __ldg(b2 + u), 0.f) * vf : (u == H2 ? vf : 0.f);
+        v[i] = u < H2 ? fmaxf(v[i] + sb2[u], 0.f) * vf : (u == H2 ? vf : 0.f);
+        m16 |= (u < H2 && v[i] > 0.f ? 1u : 0u) << i;
       }
+      if (c < H2) m2.put16(c, m16);
       store8(sA2, tA2.rowbytes(), t, c, v);
       store8(sA2, tA2.rowbytes(), t, c + 8, v + 8);
     }
     sync_for_mma();
     // fwd3: scratch = A2 Wo^T ; epilogue dX
-    if (t == 0)
+    if (tid == 0)
       for (int kk = 0; kk < H2 / 16; ++kk) tc::mma_bf16(tScr, tA2.kdesc(kk), tWo.kdesc(kk), id_fwd3, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 0; c < D; c += 16) {
+    for (int c = 16 * g; c < D; c += 32) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+      const uint32_t ms = mS.get16(c);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int f = c + i;
-        const float x = v[i] + __ldg(bo + f);
-        const float s = load1(sS, tS.rowbytes(), t, f);
+        const float x = v[i] + sbo[f];
+        const float s = ((ms >> i) & 1u) ? 1.f : -1.f;
         v[i] = wb * s / (1.f + expf(s * x));
       }
       store8(sdX, tdX.rowbytes(), t, c, v);
@@ -228,40 +272,42 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
     }
     sync_for_mma();
     // scratch = dX Wo (B = Wo read MN-major);  GWo += dX^T [A2 | 1]
-    if (t == 0) {
+    if (tid == 0) {
       for (int kk = 0; kk < D / 16; ++kk) tc::mma_bf16(tScr, tdX.kdesc(kk), tWo.mndesc(kk), id_d2, kk > 0);
       for (int kk = 0; kk < 8; ++kk)
         tc::mma_bf16(tGo, tdX.mndesc(kk), tA2.mndesc(kk), id_go, (!first || kk > 0) ? 1u : 0u);
     }
     if (!(ok = mma_wait())) break;
-    for (int c = 0; c < H2; c += 16) {
+    for (int c = 16 * g; c < H2; c += 32) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+      const uint32_t mk = m2.get16(c);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = load1(sA2, tA2.rowbytes(), t, c + i) > 0.f ? v[i] : 0.f;
+      for (int i = 0; i < 16; ++i) v[i] = ((mk >> i) & 1u) ? v[i] : 0.f;
       store8(sdA2, tdA2.rowbytes(), t, c, v);
       store8(sdA2, tdA2.rowbytes(), t, c + 8, v + 8);
     }
     sync_for_mma();
     // scratch = dA2 W2 (B = W2 read MN-major);  GW2 += dA2^T [A1 | 1]
-    if (t == 0) {
+    if (tid == 0) {
       for (int kk = 0; kk < H2 / 16; ++kk) tc::mma_bf16(tScr, tdA2.kdesc(kk), tW2.mndesc(kk), id_d1, kk > 0);
       for (int kk = 0; kk < 8; ++kk)
         tc::mma_bf16(tG2, tdA2.mndesc(kk), tA1.mndesc(kk), id_g2, (!first || kk > 0) ? 1u : 0u);
     }
     if (!(ok = mma_wait())) break;
-    for (int c = 0; c < H1; c += 16) {
+    for (int c = 16 * g; c < H1; c += 32) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
+      const uint32_t mk = m1.get16(c);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = load1(sA1, tA1.rowbytes(), t, c + i) > 0.f ? v[i] : 0.f;
+      for (int i = 0; i < 16; ++i) v[i] = ((mk >> i) & 1u) ? v[i] : 0.f;
       // dA1 overwrites A2 (GWo and the dA2 mask have consumed it)
       store8(sA2, tdA1.rowbytes(), t, c, v);
       store8(sA2, tdA1.rowbytes(), t, c + 8, v + 8);
     }
     sync_for_mma();
     // GW1 += dA1^T [S | 1]
-    if (t == 0)
+    if (tid == 0)
       for (int kk = 0; kk < 8; ++kk)
         tc::mma_bf16(tG1, tdA1.mndesc(kk), tS.mndesc(kk), id_g1, (!first || kk > 0) ? 1u : 0u);
     if (!(ok = mma_wait())) break;
@@ -269,12 +315,12 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
     tc::fence_before_sync();
     __syncthreads();
   }
-  if (!ok && t == 0) atomicExch(args.status, 3);
+  if (!ok && tid == 0) atomicExch(args.status, 3);
   // ---- flush the gradient partials of this CTA ----
   float* G = args.partials + (long long)blockIdx.x * args.part_stride;
   if (ok && !first) {
     // GW1 rows u (lane t < H1): [D weights | bias]
-    for (int c = 0; c < D + 16; c += 16) {
+    for (int c = 16 * g; c < D + 16; c += 32) {
       float v[16];
       tc::tmem_ld16(tG1 + lane_off + (uint32_t)c, v);
       if (t < H1)
@@ -284,7 +330,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
           else if (j == D) G[md.layer[0].dst_off + (long long)H1 * D + t] = v[i];
         }
     }
-    for (int c = 0; c < H1 + 16; c += 16) {
+    for (int c = 16 * g; c < H1 + 16; c += 32) {
       float v[16];
       tc::tmem_ld16(tG2 + lane_off + (uint32_t)c, v);
       if (t < H2)
@@ -294,7 +340,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
           else if (u == H1) G[md.layer[1].dst_off + (long long)H2 * H1 + t] = v[i];
         }
     }
-    for (int c = 0; c < H2 + 16; c += 16) {
+    for (int c = 16 * g; c < H2 + 16; c += 32) {
       float v[16];
       tc::tmem_ld16(tGo + lane_off + (uint32_t)c, v);
       if (t < D)
@@ -305,7 +351,7 @@ __global__ void __launch_bounds__(128, 1) bwd_fused_kernel(const InstDev* __rest
         }
     }
   } else {
-    for (long long e = t; e < md.n_params; e += 128) G[e] = 0.f;
+    for (long long e = tid; e < md.n_params; e += 256) G[e] = 0.f;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -321,7 +367,7 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
   cudaError_t e = cudaFuncSetAttribute(bwd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   FusedBwdArgs a{spins, logZR, logq, stats, partials, part_stride, status};
-  bwd_fused_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, li, a);
+  bwd_fused_kernel<<<nblk, 256, smem_bytes, s>>>(d_inst, li, a);
   return cudaGetLastError();
 }
 

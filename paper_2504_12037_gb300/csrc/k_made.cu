@@ -3,97 +3,115 @@
 
 namespace tnvan {
 
-// Build the packed copy of every instance's network: each layer's [nout][nin]
-// block with MADE masks applied and hidden units sorted by degree, then the
-// biases in the same order.  grid = (ceil(max_elems / 256), n_inst).
-__global__ void pack_kernel(const InstDev* __restrict__ inst) {
-  const MadeDev& md = inst[blockIdx.y].made;
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Value of the packed network at flat index j: each layer's [nout][nin]
+// block with the MADE masks applied and hidden units sorted by degree, then
+// its biases in the same order (layer offsets dst_off), read from the
+// caller's natural layout.
+__device__ __forceinline__ float packed_value(const MadeDev& md, long long j) {
   for (int l = 0; l < md.n_layers; ++l) {
     const LayerDev& L = md.layer[l];
-    long long nw = (long long)L.nout * L.nin;
-    if (e < nw) {
-      int o = (int)(e / L.nin), i = (int)(e % L.nin);
-      int no = L.perm_out ? L.perm_out[o] : o;
-      int ni = L.perm_in ? L.perm_in[i] : i;
-      int dout = L.deg_out[o], din = L.deg_in[i];
-      bool conn = L.strict ? (dout > din) : (dout >= din);
-      md.packed[L.dst_off + e] = conn ? md.raw[L.src_off + (long long)no * L.nin + ni] : 0.f;
-      return;
+    const long long nw = (long long)L.nout * L.nin;
+    if (j < nw) {
+      const int o = (int)(j / L.nin), i = (int)(j % L.nin);
+      const int no = L.perm_out ? L.perm_out[o] : o;
+      const int ni = L.perm_in ? L.perm_in[i] : i;
+      const int dout = L.deg_out[o], din = L.deg_in[i];
+      const bool conn = L.strict ? (dout > din) : (dout >= din);
+      return conn ? md.raw[L.src_off + (long long)no * L.nin + ni] : 0.f;
     }
-    e -= nw;
-    if (e < L.nout) {
-      int no = L.perm_out ? L.perm_out[e] : (int)e;
-      md.packed[L.dst_off + nw + e] = md.raw[L.src_off + nw + no];
-      return;
-    }
-    e -= L.nout;
+    j -= nw;
+    if (j < L.nout) return md.raw[L.src_off + nw + (L.perm_out ? L.perm_out[j] : (int)j)];
+    j -= L.nout;
   }
+  return 0.f;
 }
 
-// Gather the blocked sampler weights from the packed layout.
-// blockIdx.z: 0 = the SIMT sampler's blocks, 1.. = the tensor-core plans' triangles
-__global__ void pack_blocks_kernel(const InstDev* __restrict__ inst) {
+__host__ __device__ inline long long tile_elems(const MadeDev& md) {
+  return md.wtiles ? (long long)md.H1 * md.D + (long long)md.H2 * md.H1 + (long long)md.D * md.H2 : 0;
+}
+
+// Everything the kernels read from the network, rebuilt from the caller's
+// parameters in one launch (grid = (ceil(max_total / 256), n_inst)); the
+// segments selected by `mask`, back to back in a flat index:
+//   PACK_FLAT  the packed copy (FP32, natural order of packed_value)
+//   PACK_TILES BF16 tiles in the tensor cores' canonical K-major layout (no
+//              swizzle): W1 [H1 x D], W2 [H2 x H1], Wo [D x H2]
+//   PACK_SIMT  the blocked SIMT sampler's weight blocks
+//   PACK_TC    the tensor-core sampler plans' triangle tiles
+__global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
   const MadeDev& md = inst[blockIdx.y].made;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int z = blockIdx.z;
-  const int* src = z == 0 ? md.blk_src : md.tc[z - 1].src;
-  float* dst = z == 0 ? md.blocks : md.tc[z - 1].blocks;
-  const long long n = z == 0 ? md.n_blk : md.tc[z - 1].n_blk;
-  if (e >= n) return;
-  const int j = src[e];
-  dst[e] = j >= 0 ? md.packed[j] : 0.f;
-}
-
-cudaError_t launch_pack(const InstDev* d_inst, int n_inst, long long max_elems, long long max_blk,
-                        cudaStream_t s) {
-  if (n_inst == 0 || max_elems == 0) return cudaSuccess;
-  pack_kernel<<<dim3((unsigned)((max_elems + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || max_blk == 0) return e;
-  pack_blocks_kernel<<<dim3((unsigned)((max_blk + 255) / 256), n_inst, 1 + TNVAN_TC_PLANS), 256, 0, s>>>(d_inst);
-  return cudaGetLastError();
-}
-
-// BF16 weight tiles in the tensor cores' canonical K-major layout (no
-// swizzle): W1 [H1 x D], W2 [H2 x H1], Wo [D x H2], back to back.
-__global__ void pack_tiles_kernel(const InstDev* __restrict__ inst) {
-  const MadeDev& md = inst[blockIdx.y].made;
-  if (!md.wtiles) return;
-  const int D = md.D, H1 = md.H1, H2 = md.H2;
-  const long long n1 = (long long)H1 * D, n2 = (long long)H2 * H1, no = (long long)D * H2;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const float* src;
-  int cols;
-  long long base;
-  if (e < n1) {
-    src = md.packed + md.layer[0].dst_off;
-    cols = D;
-    base = 0;
-  } else if (e < n1 + n2) {
-    e -= n1;
-    src = md.packed + md.layer[1].dst_off;
-    cols = H1;
-    base = n1;
-  } else if (e < n1 + n2 + no) {
-    e -= n1 + n2;
-    src = md.packed + md.layer[2].dst_off;
-    cols = H2;
-    base = n1 + n2;
-  } else {
-    return;
+  if (mask & PACK_FLAT) {
+    if (e < md.n_params) {
+      md.packed[e] = packed_value(md, e);
+      return;
+    }
+    e -= md.n_params;
   }
-  const int r = (int)(e / cols), c = (int)(e % cols);
-  const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
-  const float v = src[e];
-  uint32_t u = __float_as_uint(v);
-  u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
-  md.wtiles[o] = (uint16_t)(u >> 16);
+  if (mask & PACK_TILES) {
+    const long long nt = tile_elems(md);
+    if (e < nt) {
+      const int D = md.D, H1 = md.H1, H2 = md.H2;
+      const long long n1 = (long long)H1 * D, n2 = (long long)H2 * H1;
+      int cols;
+      long long base, src;
+      if (e < n1) {
+        cols = D;
+        base = 0;
+        src = md.layer[0].dst_off + e;
+      } else if (e < n1 + n2) {
+        cols = H1;
+        base = n1;
+        src = md.layer[1].dst_off + (e - n1);
+      } else {
+        cols = H2;
+        base = n1 + n2;
+        src = md.layer[2].dst_off + (e - n1 - n2);
+      }
+      const long long le = e - base;
+      const int r = (int)(le / cols), c = (int)(le % cols);
+      const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
+      uint32_t u = __float_as_uint(packed_value(md, src));
+      u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+      md.wtiles[o] = (uint16_t)(u >> 16);
+      return;
+    }
+    e -= nt;
+  }
+  if (mask & PACK_SIMT) {
+    if (e < md.n_blk) {
+      const int j = md.blk_src[e];
+      md.blocks[e] = j >= 0 ? packed_value(md, j) : 0.f;
+      return;
+    }
+    e -= md.n_blk;
+  }
+  if (mask & PACK_TC) {
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+      const MadeDev::TcPlan& P = md.tc[p];
+      if (e < P.n_blk) {
+        const int j = P.src[e];
+        P.blocks[e] = j >= 0 ? packed_value(md, j) : 0.f;
+        return;
+      }
+      e -= P.n_blk;
+    }
+  }
 }
 
-cudaError_t launch_pack_tiles(const InstDev* d_inst, int n_inst, long long max_tile_elems, cudaStream_t s) {
-  if (n_inst == 0 || max_tile_elems == 0) return cudaSuccess;
-  pack_tiles_kernel<<<dim3((unsigned)((max_tile_elems + 255) / 256), n_inst), 256, 0, s>>>(d_inst);
+long long pack_elems(const MadeDev& md, int mask) {
+  long long n = 0;
+  if (mask & PACK_FLAT) n += md.n_params;
+  if (mask & PACK_TILES) n += tile_elems(md);
+  if (mask & PACK_SIMT) n += md.n_blk;
+  if (mask & PACK_TC)
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) n += md.tc[p].n_blk;
+  return n;
+}
+
+cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s) {
+  if (n_inst == 0 || max_total == 0) return cudaSuccess;
+  pack_all_kernel<<<dim3((unsigned)((max_total + 255) / 256), n_inst), 256, 0, s>>>(d_inst, mask);
   return cudaGetLastError();
 }
 

@@ -278,7 +278,8 @@ cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_
 //                        = beta s_W <s_i>   (bonds to a W neighbour),
 // and the W-W bonds add d(-beta E_1)/d J_e = beta s_a s_b (Eq. 4
 // differentiated), and d log Z_R / d beta = sum_e J_e <.>_e - E_1(s) per
-// sample.  Batch sums are formed per CTA in shared memory, one row
+// sample; optionally log Z_R itself (the forward sweep's value, as
+// strips_kernel computes it).  Batch sums are formed per CTA in shared memory, one row
 // of accumulators per warp so that the order of additions is fixed, and
 // strips_dJ_reduce_kernel adds the CTA rows in CTA order.
 // ---------------------------------------------------------------------------
@@ -458,8 +459,8 @@ __host__ __device__ inline int strip_adj_lv_offset(int tab_floats, int T, int Dp
 
 __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                                          int lv_floats, const int8_t* __restrict__ spins,
-                                                         double* __restrict__ dbeta, float* __restrict__ part,
-                                                         int part_stride) {
+                                                         double* __restrict__ logZR, double* __restrict__ dbeta,
+                                                         float* __restrict__ part, int part_stride) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
   const bool valid = b < li.batch;
   const int8_t* srow = ssp + t * Dp;
   float* accw = acc + (t >> 5) * ne;
-  double dl = 0.0;
+  double dl = 0.0, lz = 0.0, chat = 0.0;
   for (int st = 0, off = 0; st < I.n_strips; ++st) {
     const StripDev& sd = I.strips[st];
     const StripTab tab = strip_tab_at(sm + off, sd.w, sd.L, false);
@@ -509,8 +510,10 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
         break;
     }
     dl += d;
+    lz += l;
+    chat += sd.c_hat;
   }
-  // W-W bonds: -beta E_1 for d/dbeta, s_a s_b for d/dJ (eight bonds per warp reduction)
+  // W-W bonds: -beta E_1 for log Z_R and d/dbeta, s_a s_b for d/dJ (eight bonds per warp reduction)
   float e1 = 0.f;
   for (int e0 = 0; e0 < I.n_ww; e0 += 8) {
     float val[8];
@@ -529,6 +532,7 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
     if ((lane & 3) == 0 && e0 + vi < I.n_ww) accw[I.ww[e0 + vi].e] += sum;
   }
   if (dbeta && valid) dbeta[(long long)k * li.batch + b] = dl + (double)e1;
+  if (logZR && valid) logZR[(long long)k * li.batch + b] = lz + li.beta[k] * (chat + (double)e1);
   __syncthreads();
   const float scale = beta / (float)li.batch;
   float* row = part + (long long)blockIdx.x * part_stride;
@@ -539,18 +543,20 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
   }
 }
 
-// dJ[edge] += sum over the instance's CTA rows, in CTA order (deterministic).
+// dJ[edge] += sum over the instance's CTA rows: one warp per edge, lane l
+// adding rows l, l+32, ... in FP64, then a fixed xor tree (deterministic).
 __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                         const float* __restrict__ part, int part_stride,
                                         double* __restrict__ dJ) {
   const int k = blockIdx.y;
   const InstDev& I = inst[k];
   if (I.kind != 0) return;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < I.n_edges; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = li.tile_begin[k]; c < li.tile_begin[k + 1]; ++c) s += (double)part[(long long)c * part_stride + e];
-    dJ[I.edge_off + e] += s;
-  }
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (e >= I.n_edges) return;
+  double s = 0.0;
+  for (int c = li.tile_begin[k] + lane; c < li.tile_begin[k + 1]; c += 32) s += (double)part[(long long)c * part_stride + e];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) dJ[I.edge_off + e] += s;
 }
 
 int strip_adj_lv_floats(const Instance& in, int tile) {
@@ -579,17 +585,18 @@ int strips_adj_occupancy(int tile, int smem_bytes) {
 }
 
 cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
-                              const int8_t* spins, double* dbeta, float* part, int part_stride, double* dJ,
-                              cudaStream_t s) {
+                              const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
+                              double* dJ, cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
   if (li.tile % 32 != 0 || li.tile > 128) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, lv_floats, spins, dbeta, part, part_stride);
+  strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, lv_floats, spins, logZR, dbeta, part, part_stride);
   e = cudaGetLastError();
   if (e != cudaSuccess || !dJ) return e;
-  strips_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
+  strips_dJ_reduce_kernel<<<dim3((unsigned)((part_stride + 7) / 8), li.n_inst), 256, 0, s>>>(d_inst, li, part,
+                                                                                            part_stride, dJ);
   return cudaGetLastError();
 }
 

@@ -125,18 +125,98 @@ __global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const doubl
   s[7] = n;
 }
 
+// Both passes in one launch: every CTA reduces its chunk (as
+// reduce_part_kernel) and counts itself done on counters[k]; the last CTA of
+// an instance merges the instance's n_part (<= 64) tuples with one warp --
+// a fixed tree over the chunk index, so the result does not depend on which
+// CTA finishes last -- writes the statistics and re-arms the counter.
+__device__ __forceinline__ Tuple ld_tuple(const double* o) {
+  return Tuple{__ldcg(o), __ldcg(o + 1), __ldcg(o + 2), __ldcg(o + 3), __ldcg(o + 4), __ldcg(o + 5)};
+}
+
+__global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
+                                                     const float* __restrict__ logq, double* __restrict__ part,
+                                                     double* __restrict__ stats, int* __restrict__ counters) {
+  const int k = blockIdx.y, p = blockIdx.x, B = li.batch;
+  const long long base = (long long)k * B;
+  const double K = logZR[base] - (double)logq[base];
+  const int chunk = (B + n_part - 1) / n_part;
+  const int lo = p * chunk, hi = min(B, lo + chunk);
+  Tuple acc = {0, 0, 0, 0, 0, 0};
+  for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+    const double l = logZR[base + b] - (double)logq[base + b];
+    if (!isfinite(l)) {
+      acc.bad += 1.0;
+      continue;
+    }
+    const double d = l - K;
+    acc.n += 1.0;
+    acc.s1 += d;
+    acc.s2 += d * d;
+    if (acc.se == 0.0) {
+      acc.m = l;
+      acc.se = 1.0;
+    } else if (l > acc.m) {
+      acc.se = acc.se * (double)expf((float)(acc.m - l)) + 1.0;
+      acc.m = l;
+    } else {
+      acc.se += (double)expf((float)(l - acc.m));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc = merge(acc, shfl_tuple(acc, o));
+  __shared__ Tuple red[8];
+  __shared__ int last;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Tuple r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = merge(r, red[w]);
+    double* o = part + ((long long)k * n_part + p) * 6;
+    o[0] = r.n;
+    o[1] = r.s1;
+    o[2] = r.s2;
+    o[3] = r.m;
+    o[4] = r.se;
+    o[5] = r.bad;
+    __threadfence();
+    last = atomicAdd(counters + k, 1) == n_part - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
+  const int l = threadIdx.x;
+  Tuple r = {0, 0, 0, 0, 0, 0};
+  if (l < n_part) r = ld_tuple(part + ((long long)k * n_part + l) * 6);
+  if (l + 32 < n_part) r = merge(r, ld_tuple(part + ((long long)k * n_part + l + 32) * 6));
+  for (int o = 16; o > 0; o >>= 1) r = merge(r, shfl_tuple(r, o));
+  if (l != 0) return;
+  const double beta = li.beta[k];
+  const double n = r.n;
+  const double mean_d = r.s1 / n;
+  const double var = n > 1.0 ? fmax(r.s2 - r.s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
+  const double mean = K + mean_d;
+  const double lz = r.m + log(r.se) - log(n);
+  double* st = stats + 8 * k;
+  st[0] = -mean / beta;
+  st[1] = -lz / beta;
+  st[2] = sqrt(var) / (beta * sqrt(n));
+  st[3] = lz;
+  st[4] = mean;
+  st[5] = r.bad;
+  st[6] = var;
+  st[7] = n;
+  counters[k] = 0;
+}
+
 cudaError_t launch_reduce(const InstDev*, const LaunchInfo& li, const double* logZR,
-                          const float* logq, double* stats, cudaStream_t s) {
+                          const float* logq, double* stats, int* counters, cudaStream_t s) {
   // n_part chosen so every instance gets >= 1 CTA of >= 1024 samples.
   int n_part = (li.batch + 1023) / 1024;
   if (n_part > 64) n_part = 64;
   if (n_part < 1) n_part = 1;
   // partial tuples live right after the stats block
   double* part = stats + 8 * TNVAN_MAX_INST;
-  reduce_part_kernel<<<dim3(n_part, li.n_inst), 256, 0, s>>>(li, n_part, logZR, logq, part);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  reduce_final_kernel<<<li.n_inst, 32, 0, s>>>(li, n_part, logZR, logq, part, stats);
+  reduce_kernel<<<dim3(n_part, li.n_inst), 256, 0, s>>>(li, n_part, logZR, logq, part, stats, counters);
   return cudaGetLastError();
 }
 
@@ -353,8 +433,16 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
   const int p0 = li.tile_begin[k], p1 = li.tile_begin[k + 1];
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < md.n_params;
        e += (long long)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int p = p0; p < p1; ++p) s += partials[(long long)p * part_stride + e];
+    // eight independent partial sums keep eight loads in flight; fixed order
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int p = p0;
+    for (; p + 8 <= p1; p += 8)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] += partials[(long long)(p + j) * part_stride + e];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (p + j < p1) a[j] += partials[(long long)(p + j) * part_stride + e];
+    const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     long long r = e;
     for (int l = 0; l < md.n_layers; ++l) {
       const LayerDev& L = md.layer[l];

@@ -66,9 +66,12 @@ class TNVAN:
 
     def train_step(self, batch: int, seed: int, step: int, precision: int = tv.FP32, lr: float = 0.01,
                    out=None, dbeta=None, dJ=None, stream=None):
-        """One iteration of Algorithm 1: sample, contract, gradient, Adam."""
-        spins, logq, logZR = self.sample(batch, seed, step, precision, out, stream)
-        self.ctx.backward(self.betas, batch, spins, logZR, logq, precision, self.grad, dbeta, dJ, stream)
+        """One iteration of Algorithm 1: sample, contract, gradient, Adam.  With
+        dbeta / dJ given, the contraction adjoint runs in the sampling pass."""
+        spins, logq, logZR = out if out is not None else self.buffers(batch)
+        self.ctx.sample_contract_adjoint(self.betas, batch, seed, step, precision, spins, logq, logZR, dbeta, dJ,
+                                         stream)
+        self.ctx.backward(self.betas, batch, spins, logZR, logq, precision, self.grad, None, None, stream)
         self.t += 1
         self.ctx.adam(self.params, self.grad, self.m, self.v, lr, 0.9, 0.999, 1e-8, self.t, stream)
         return spins, logq, logZR

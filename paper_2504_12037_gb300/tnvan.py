@@ -38,6 +38,8 @@ SIGNATURES = {
     "tnvan_instance_info": (_c_int, [_vp, _c_int, _i32p]),
     "tnvan_reserve": (_c_int, [_vp, _c_int]),
     "tnvan_sample_and_contract": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp]),
+    "tnvan_sample_contract_adjoint": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
+                                               _vp, _vp]),
     "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp]),
     "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
@@ -161,6 +163,13 @@ class Context:
         b, pb = _arr(betas, np.float64)
         self._check(lib().tnvan_sample_and_contract(self._h, pb, batch, seed, step, precision, _ptr(spins),
                                                     _ptr(logq), _ptr(logZR), _stream(stream)))
+
+    def sample_contract_adjoint(self, betas, batch: int, seed: int, step: int, precision: int, spins, logq,
+                                logZR, dbeta=None, dJ=None, stream=None):
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_sample_contract_adjoint(self._h, pb, batch, seed, step, precision, _ptr(spins),
+                                                        _ptr(logq), _ptr(logZR), _ptr(dbeta), _ptr(dJ),
+                                                        _stream(stream)))
 
     def log_prob(self, batch: int, spins, logq, precision: int = FP32, stream=None):
         self._check(lib().tnvan_log_prob(self._h, batch, _ptr(spins), precision, _ptr(logq), _stream(stream)))

@@ -308,6 +308,28 @@ def test_full_size_adjoint_sampled_rows_and_identity():
         eo += g.m
 
 
+@pytest.mark.parametrize("prec", [tv.FP32, tv.BF16])
+def test_sample_contract_adjoint_equals_separate_calls(prec):
+    # one pass (sampling, log Z_R from the adjoint's forward sweep, d/dbeta,
+    # d/dJ) against sample_and_contract + contract + backward on the same draw
+    w = wl.workload(2)
+    model = _model(w, n_inst=3)
+    B = 1000
+    spins, logq, logZR = model.buffers(B)
+    dbeta = torch.empty(model.n * B, dtype=torch.float64, device="cuda")
+    dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+    model.ctx.sample_contract_adjoint(model.betas, B, 31, 2, prec, spins, logq, logZR, dbeta, dJ)
+    s2, lq2, lz2 = model.sample(B, 31, 2, precision=prec)
+    lz3 = torch.empty_like(lz2)
+    model.ctx.contract(model.betas, B, s2, tv.FP32, lz3)
+    db2, dJ2 = torch.empty_like(dbeta), torch.empty_like(dJ)
+    model.ctx.backward(model.betas, B, s2, lz2, lq2, prec, torch.empty_like(model.params), db2, dJ2)
+    torch.cuda.synchronize()
+    assert torch.equal(spins, s2) and torch.equal(logq, lq2)
+    assert torch.equal(logZR, lz2) and torch.equal(logZR, lz3)  # same forward arithmetic
+    assert torch.equal(dbeta, db2) and torch.equal(dJ, dJ2)
+
+
 def test_train_step_runs_and_adam_matches_oracle():
     w = wl.workload(1)
     model = _model(w)
