@@ -125,13 +125,98 @@ __global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const doubl
   s[7] = n;
 }
 
-// Both passes in one launch: every CTA reduces its chunk (as
-// reduce_part_kernel) and counts itself done on counters[k]; the last CTA of
-// an instance merges the instance's n_part (<= 64) tuples with one warp --
-// a fixed tree over the chunk index, so the result does not depend on which
-// CTA finishes last -- writes the statistics and re-arms the counter.
-__device__ __forceinline__ Tuple ld_tuple(const double* o) {
-  return Tuple{__ldcg(o), __ldcg(o + 1), __ldcg(o + 2), __ldcg(o + 3), __ldcg(o + 4), __ldcg(o + 5)};
+// ---------------------------------------------------------------------------
+// The same reduction in one launch, in float-float arithmetic: FP64 is a
+// narrow unit on this part, so the per-sample sums and the merges carry each
+// value as an unevaluated sum hi + lo of two floats (error-free transforms:
+// Knuth's TwoSum, Dekker's FastTwoSum, the FMA product error), about 48
+// significant bits; only the final statistics are formed in FP64.
+// Every CTA reduces its chunk and counts itself done on counters[k]; the
+// last CTA of an instance merges the instance's n_part (<= 64) tuples with
+// one warp -- a fixed tree over the chunk index, so the result does not
+// depend on which CTA finishes last -- writes the statistics and re-arms the
+// counter.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  FF s = ff_two_sum(x.hi, y.hi);
+  const FF t = ff_two_sum(x.lo, y.lo);
+  s = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
+__device__ __forceinline__ bool ff_gt(FF a, FF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+// double -> float-float with integer operations: hi = the top 24 significand
+// bits (truncated, exact), lo = the next 29 bits rounded to a float.
+__device__ __forceinline__ FF ff_from_double(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  const int E = (int)((u >> 52) & 0x7FFull);
+  const int fe = E - 1023 + 127;
+  if (E == 0x7FF) return FF{x != x ? __int_as_float(0x7FC00000) : __int_as_float((int)(sign | 0x7F800000u)), 0.f};
+  if (fe <= 0 || fe >= 255) return FF{(float)x, 0.f};  // zero, tiny or huge: not met by log-likelihoods
+  const unsigned long long M = u & 0xFFFFFFFFFFFFFull;
+  const float hi = __int_as_float((int)(sign | ((unsigned)fe << 23) | (unsigned)(M >> 29)));
+  const int le = E - 1075 + 127;  // 2^(E - 1023 - 52)
+  const float lo = le > 0 ? __uint2float_rn((unsigned)(M & 0x1FFFFFFFull)) * __int_as_float(le << 23) : 0.f;
+  return FF{hi, sign ? -lo : lo};
+}
+__device__ __forceinline__ double ff_to_double(FF x) { return (double)x.hi + (double)x.lo; }
+
+struct TupleFF {
+  int n, bad;
+  FF s1, s2, m, se;
+};
+__device__ __forceinline__ TupleFF merge_ff(const TupleFF& a, const TupleFF& b) {
+  if (a.n == 0) return TupleFF{b.n, a.bad + b.bad, b.s1, b.s2, b.m, b.se};
+  if (b.n == 0) return TupleFF{a.n, a.bad + b.bad, a.s1, a.s2, a.m, a.se};
+  TupleFF r;
+  r.n = a.n + b.n;
+  r.bad = a.bad + b.bad;
+  r.s1 = ff_add(a.s1, b.s1);
+  r.s2 = ff_add(a.s2, b.s2);
+  r.m = ff_gt(a.m, b.m) ? a.m : b.m;
+  const float ea = expf(ff_add(a.m, ff_neg(r.m)).hi), eb = expf(ff_add(b.m, ff_neg(r.m)).hi);
+  r.se = ff_add(ff_mul(a.se, FF{ea, 0.f}), ff_mul(b.se, FF{eb, 0.f}));
+  return r;
+}
+__device__ __forceinline__ FF shfl_ff(FF x, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+__device__ __forceinline__ TupleFF shfl_tuple_ff(const TupleFF& t, int o) {
+  return TupleFF{__shfl_xor_sync(0xffffffffu, t.n, o), __shfl_xor_sync(0xffffffffu, t.bad, o), shfl_ff(t.s1, o),
+                 shfl_ff(t.s2, o), shfl_ff(t.m, o), shfl_ff(t.se, o)};
+}
+// partial tuples as 10 words in a 12-word (6-double) slot
+__device__ __forceinline__ void st_tuple_ff(double* slot, const TupleFF& t) {
+  float* f = reinterpret_cast<float*>(slot);
+  reinterpret_cast<int*>(f)[0] = t.n;
+  reinterpret_cast<int*>(f)[1] = t.bad;
+  f[2] = t.s1.hi, f[3] = t.s1.lo, f[4] = t.s2.hi, f[5] = t.s2.lo;
+  f[6] = t.m.hi, f[7] = t.m.lo, f[8] = t.se.hi, f[9] = t.se.lo;
+}
+__device__ __forceinline__ TupleFF ld_tuple_ff(const double* slot) {
+  const float* f = reinterpret_cast<const float*>(slot);
+  const int* q = reinterpret_cast<const int*>(slot);
+  return TupleFF{__ldcg(q), __ldcg(q + 1), FF{__ldcg(f + 2), __ldcg(f + 3)}, FF{__ldcg(f + 4), __ldcg(f + 5)},
+                 FF{__ldcg(f + 6), __ldcg(f + 7)}, FF{__ldcg(f + 8), __ldcg(f + 9)}};
 }
 
 __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
@@ -139,70 +224,76 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
                                                      double* __restrict__ stats, int* __restrict__ counters) {
   const int k = blockIdx.y, p = blockIdx.x, B = li.batch;
   const long long base = (long long)k * B;
-  const double K = logZR[base] - (double)logq[base];
+  const FF K = ff_add(ff_from_double(logZR[base]), FF{-logq[base], 0.f});
+  const FF negK = ff_neg(K);
   const int chunk = (B + n_part - 1) / n_part;
   const int lo = p * chunk, hi = min(B, lo + chunk);
-  Tuple acc = {0, 0, 0, 0, 0, 0};
+  TupleFF acc = {0, 0, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
-    const double l = logZR[base + b] - (double)logq[base + b];
-    if (!isfinite(l)) {
-      acc.bad += 1.0;
+    const FF l = ff_add(ff_from_double(logZR[base + b]), FF{-logq[base + b], 0.f});
+    if (!isfinite(l.hi) || !isfinite(l.lo)) {
+      acc.bad += 1;
       continue;
     }
-    const double d = l - K;
-    acc.n += 1.0;
-    acc.s1 += d;
-    acc.s2 += d * d;
-    if (acc.se == 0.0) {
+    const FF d = ff_add(l, negK);
+    acc.s1 = ff_add(acc.s1, d);
+    acc.s2 = ff_add(acc.s2, ff_mul(d, d));
+    if (acc.n == 0) {
       acc.m = l;
-      acc.se = 1.0;
-    } else if (l > acc.m) {
-      acc.se = acc.se * (double)expf((float)(acc.m - l)) + 1.0;
+      acc.se = FF{1.f, 0.f};
+    } else if (ff_gt(l, acc.m)) {
+      acc.se = ff_add(ff_mul(acc.se, FF{expf(ff_add(acc.m, ff_neg(l)).hi), 0.f}), FF{1.f, 0.f});
       acc.m = l;
     } else {
-      acc.se += (double)expf((float)(l - acc.m));
+      acc.se = ff_add(acc.se, FF{expf(ff_add(l, ff_neg(acc.m)).hi), 0.f});
     }
+    acc.n += 1;
   }
-  for (int o = 16; o > 0; o >>= 1) acc = merge(acc, shfl_tuple(acc, o));
-  __shared__ Tuple red[8];
+  for (int o = 16; o > 0; o >>= 1) acc = merge_ff(acc, shfl_tuple_ff(acc, o));
+  __shared__ TupleFF red[8];
   __shared__ int last;
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  const int l = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+  if (l == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    Tuple r = red[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = merge(r, red[w]);
-    double* o = part + ((long long)k * n_part + p) * 6;
-    o[0] = r.n;
-    o[1] = r.s1;
-    o[2] = r.s2;
-    o[3] = r.m;
-    o[4] = r.se;
-    o[5] = r.bad;
-    __threadfence();
-    last = atomicAdd(counters + k, 1) == n_part - 1;
+  if (threadIdx.x < 32) {  // the CTA's warps merged by one warp (tree over warp index)
+    TupleFF r = l < nw ? red[l] : TupleFF{0, 0, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int o = 4; o > 0; o >>= 1) r = merge_ff(r, shfl_tuple_ff(r, o));
+    if (l == 0) {
+      st_tuple_ff(part + ((long long)k * n_part + p) * 6, r);
+      __threadfence();
+      last = atomicAdd(counters + k, 1) == n_part - 1;
+    }
   }
   __syncthreads();
   if (!last || threadIdx.x >= 32) return;
   __threadfence();
-  const int l = threadIdx.x;
-  Tuple r = {0, 0, 0, 0, 0, 0};
-  if (l < n_part) r = ld_tuple(part + ((long long)k * n_part + l) * 6);
-  if (l + 32 < n_part) r = merge(r, ld_tuple(part + ((long long)k * n_part + l + 32) * 6));
-  for (int o = 16; o > 0; o >>= 1) r = merge(r, shfl_tuple(r, o));
-  if (l != 0) return;
+  TupleFF r = {0, 0, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  if (l < n_part) r = ld_tuple_ff(part + ((long long)k * n_part + l) * 6);
+  if (l + 32 < n_part) r = merge_ff(r, ld_tuple_ff(part + ((long long)k * n_part + l + 32) * 6));
+  for (int o = 16; o > 0; o >>= 1) r = merge_ff(r, shfl_tuple_ff(r, o));
+  // FP64 statistics; the transcendental tails in parallel lanes
   const double beta = li.beta[k];
-  const double n = r.n;
-  const double mean_d = r.s1 / n;
-  const double var = n > 1.0 ? fmax(r.s2 - r.s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
-  const double mean = K + mean_d;
-  const double lz = r.m + log(r.se) - log(n);
+  const double n = (double)r.n;
+  const double s1 = ff_to_double(r.s1), s2 = ff_to_double(r.s2);
+  const double mean_d = s1 / n;
+  const double var = r.n > 1 ? fmax(s2 - s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
+  double f = 0.0;
+  if (l == 1) f = log(ff_to_double(r.se));
+  else if (l == 2) f = log(n);
+  else if (l == 3) f = sqrt(var);
+  else if (l == 4) f = sqrt(n);
+  const double lse = __shfl_sync(0xffffffffu, f, 1), ln_n = __shfl_sync(0xffffffffu, f, 2);
+  const double sd = __shfl_sync(0xffffffffu, f, 3), sn = __shfl_sync(0xffffffffu, f, 4);
+  if (l != 0) return;
+  const double mean = ff_to_double(K) + mean_d;
+  const double lz = ff_to_double(r.m) + lse - ln_n;
   double* st = stats + 8 * k;
   st[0] = -mean / beta;
   st[1] = -lz / beta;
-  st[2] = sqrt(var) / (beta * sqrt(n));
+  st[2] = sd / (beta * sn);
   st[3] = lz;
   st[4] = mean;
-  st[5] = r.bad;
+  st[5] = (double)r.bad;
   st[6] = var;
   st[7] = n;
   counters[k] = 0;
@@ -210,8 +301,8 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
 
 cudaError_t launch_reduce(const InstDev*, const LaunchInfo& li, const double* logZR,
                           const float* logq, double* stats, int* counters, cudaStream_t s) {
-  // n_part chosen so every instance gets >= 1 CTA of >= 1024 samples.
-  int n_part = (li.batch + 1023) / 1024;
+  // n_part: chunks of >= 256 samples, at most 64 per instance
+  int n_part = (li.batch + 255) / 256;
   if (n_part > 64) n_part = 64;
   if (n_part < 1) n_part = 1;
   // partial tuples live right after the stats block
