@@ -268,17 +268,44 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
       // layer 2: + in-group layer-1 units completed so far (BF16 values, 4 at a time;
       // units not computed yet read as 0 and carry masked weights)
       const uint32_t o1 = rb1 + 16u * (uint32_t)(u1lo - w1);
-      for (int v = va; v < vb; ++v) {
-        float a0;
+      auto pre2 = [&](int v) -> float {  // accumulated pre-activation + bias of layer-2 unit v
+        float a;
         if (v - va < 4) {
-          a0 = pick4(rb, v - va);
+          a = pick4(rb, v - va);
         } else {
           uint32_t rx = 0u;
           if (init2) tmem_ld1_nowait(tP2 + (uint32_t)v, rx);
           tmem_wait1(rx);
-          a0 = __uint_as_float(rx);
+          a = __uint_as_float(rx);
         }
-        a0 += gb2[v - u2lo];
+        return a + gb2[v - u2lo];
+      };
+      int v = va;
+      for (; v + 2 <= vb; v += 2) {  // two units of one step share the in-group H1 values
+        float a0 = pre2(v), b0 = pre2(v + 1);
+        const float* wr = TW2 + (v - u2lo) * s2;
+        const float* wq = wr + s2;
+        float a1 = 0.f, b1 = 0.f;
+        for (int c = 0; c < ub - u1lo; c += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+          const float4 q4 = *reinterpret_cast<const float4*>(wq + c);
+          const uint32_t o = o1 + 16u * (uint32_t)c;
+          const float h0 = ld_bf16(sH1, o), h1 = ld_bf16(sH1, o + 16u), h2 = ld_bf16(sH1, o + 32u),
+                      h3 = ld_bf16(sH1, o + 48u);
+          a0 = fmaf(w4.x, h0, a0);
+          b0 = fmaf(q4.x, h0, b0);
+          a1 = fmaf(w4.y, h1, a1);
+          b1 = fmaf(q4.y, h1, b1);
+          a0 = fmaf(w4.z, h2, a0);
+          b0 = fmaf(q4.z, h2, b0);
+          a1 = fmaf(w4.w, h3, a1);
+          b1 = fmaf(q4.w, h3, b1);
+        }
+        st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf(a0 + a1, 0.f));
+        st_bf16(sH2, rb2 + 16u * (uint32_t)(v + 1 - w2), fmaxf(b0 + b1, 0.f));
+      }
+      if (v < vb) {
+        float a0 = pre2(v);
         const float* wr = TW2 + (v - u2lo) * s2;
         float a1 = 0.f, a2 = 0.f, a3 = 0.f;
         for (int c = 0; c < ub - u1lo; c += 4) {
