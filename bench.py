@@ -38,7 +38,7 @@ SM_MAX_MHZ = 2070.0
 MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the same kernels on the same workload (see profiles/); None if not captured
-NCU_TRAFFIC = {"sample_tc": 478976, "bwd_fused": 6690048}
+NCU_TRAFFIC = {}
 
 
 def args_():
@@ -291,18 +291,25 @@ def run_ours(a):
         "strips": strips * strip_flops(3, 16),
         "strips+dbeta": strips * 2 * strip_flops(3, 16),
         "strips_dbeta": strips * 2 * strip_flops(3, 16),
-        "strips_adj": strips * 6 * strip_flops(3, 16),  # d/dbeta forward sweep (2x) + backward sweep (4x)
+        "strips_adj": strips * 4 * strip_flops(3, 16),  # forward sweep (1x) + backward sweep (3x)
     }
     flop_launch = per_sample.get(dom_name, float("nan")) * n_inst * B
     achieved = flop_launch / (dom_ms / dom_n / 1e3) / 1e12 if dom_n else float("nan")
-    if dom_name == "bwd_fused":
+    note = None
+    if dom_name in ("sample_tc", "bwd_fused"):
+        # BF16 operands on tcgen05: the tensor roofline (the sampler is bound by its
+        # chain of D dependent steps per sample, Eq. 8, far below it)
         peak, bound, src = MEASURED_BF16_TFLOPS, "tensor", "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+        if dom_name == "sample_tc":
+            note = f"latency-bound: {D} dependent steps per sample; masked MACs counted once"
     else:
         peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         bound, src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
     roofline = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom_name), "peak_source": src,
                 "flop_per_launch": flop_launch, "ms_per_launch": dom_ms / dom_n}
+    if note:
+        roofline["note"] = note
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()}
     launches_per_step = sum(v[1] for v in prof.values()) / a.steps
 
