@@ -38,7 +38,7 @@ SM_MAX_MHZ = 2070.0
 MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
 # the same kernels on the same workload (see profiles/); None if not captured
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"sample_tc": 479744, "strips_adj": 5341184, "bwd_fused": 6882816, "reduce": 1035776}
 
 
 def args_():
