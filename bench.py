@@ -278,6 +278,24 @@ def run_ours(a):
            "h2d_bytes_per_step": 8 * n_inst,
            "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 32 * n_inst)}
 
+    # ----- per-kernel durations: the same step with the overlapped side-stream
+    # schedule off, so that every kernel's events bracket it alone -----
+    base = tuple(model.tuned) if model.tuned else (0, 0, 0, 0, 0, 0)
+    model.ctx.set_tuning(base[:5] + (1,))
+    for i in range(2):
+        step(2 * 10 ** 6 + i)
+    torch.cuda.synchronize()
+    model.ctx.profile(True)
+    for i in range(3):
+        flush.zero_()
+        step(2 * 10 ** 6 + 2 + i)
+    torch.cuda.synchronize()
+    model.ctx.profile(False)
+    prof_seq = model.ctx.profile_read()
+    model.ctx.set_tuning(base)
+    prof_overlapped = prof
+    prof = prof_seq
+
     # ----- roofline of the dominant kernel -----
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_n) = dom
@@ -311,7 +329,7 @@ def run_ours(a):
     if note:
         roofline["note"] = note
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()}
-    launches_per_step = sum(v[1] for v in prof.values()) / a.steps
+    launches_per_step = sum(v[1] for v in prof_overlapped.values()) / a.steps
 
     # ----- accuracy: both modes trained from the same start, then F_q / N -----
     accuracy = None
@@ -342,12 +360,15 @@ def run_ours(a):
                    "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * a.steps)),
-        "roofline": roofline, "kernels": kernels, "compare": compare, "accuracy": accuracy,
+        "roofline": roofline, "kernels": kernels,
+        "kernels_note": "per-launch CUDA-event times of 3 steps with the overlapped side-stream schedule off",
+        "compare": compare, "accuracy": accuracy,
         "graph": graph, "autotuned": {"sample_tile": None if not model.tuned else model.tuned[0],
                                       "strip_tile": None if not model.tuned else model.tuned[1],
                                       "bwd_ctas_per_instance": None if not model.tuned else model.tuned[2],
                                       "strip_adjoint_tile": None if not model.tuned else model.tuned[3],
-                                      "tc_sampler_group_steps": None if not model.tuned else model.tuned[4]},
+                                      "tc_sampler_group_steps": None if not model.tuned else model.tuned[4],
+                                      "overlapped_schedule": None if not model.tuned else model.tuned[5] == 2},
     }
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)

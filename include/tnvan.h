@@ -216,23 +216,25 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
  * `batch` samples drawn from the current networks -- the SIMT sampler's
  * samples per CTA, the strip contraction's samples per CTA, the number of
  * CTAs per instance of the fused BF16 backward, the strip adjoint's samples
- * per CTA and the BF16 tensor-core sampler's step-group size limit -- with
- * CUDA events on `stream`, and keeps the fastest in the context for later
- * calls.  out (host int32[5], may be NULL) receives the choices in that order
- * (0 = heuristic, not tuned).
+ * per CTA, the BF16 tensor-core sampler's step-group size limit and whether
+ * tnvan_sample_contract_adjoint overlaps sampling and the strip adjoint on
+ * side streams (2 = on, 1 = off) -- with CUDA events on `stream`, and keeps
+ * the fastest in the context for later calls.  out (host int32[6], may be
+ * NULL) receives the choices in that order (0 = heuristic, not tuned).
  * Synchronous; allocates and frees temporary device buffers.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM, TNVAN_E_CUDA. */
 int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision, void* stream,
                    int32_t* out);
 
 /* Sets the launch shapes that tnvan_autotune chooses, in the same order and
- * units as its `out` (host int32[5]: SIMT sampler samples per CTA, strip
+ * units as its `out` (host int32[6]: SIMT sampler samples per CTA, strip
  * samples per CTA, fused-backward CTAs per instance, strip-adjoint samples
- * per CTA, tensor-core sampler step-group size limit); 0 restores the
- * built-in heuristic for that entry.  Lets a caller reuse an earlier tuning
- * without re-timing.  Not in the paper.
+ * per CTA, tensor-core sampler step-group size limit, overlapped schedule
+ * 2 on / 1 off); 0 restores the built-in default for that entry (the
+ * overlapped schedule is on by default).  Lets a caller reuse an earlier
+ * tuning without re-timing.  Not in the paper.
  * Errors: TNVAN_E_ARG (NULL, or a value outside the candidates the autotuner
- * tries: {16,32,64}, {32,64,128}, >= 1, {32,64,96,128}, {4,6,8}). */
+ * tries: {16,32,64}, {32,64,128}, >= 1, {32,64,96,128}, {4,6,8}, {1,2}). */
 int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* choices);
 
 /* Optional device step counter (not in the paper; for CUDA-graph capture).

@@ -447,6 +447,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s, bool strips = true);
 int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, int precision,
                 double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s);
+int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats);
 int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s);
 int sampler_pack_mask(const tnvan_ctx* ctx, int precision);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
@@ -697,6 +698,15 @@ int tnvan_destroy(tnvan_ctx* ctx) {
       cudaEventDestroy(pr.second);
     }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  for (cudaStream_t st : ctx->side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaStream_t st : ctx->side_lo)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ctx->chunk_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (cudaEvent_t e : ctx->join_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->d_inst) cudaFree(ctx->d_inst);
   if (ctx->d_stats) cudaFree(ctx->d_stats);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -1181,6 +1191,88 @@ int tnvan_sample_and_contract(tnvan_ctx* ctx, const double* betas, int batch, ui
   return contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
 }
 
+// Side streams and events of the overlapped schedule (created once).
+static int ensure_side_streams(tnvan_ctx* ctx) {
+  if (ctx->side[0]) return TNVAN_OK;
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  for (cudaStream_t& st : ctx->side)
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi);
+  for (cudaStream_t& st : ctx->side_lo)
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : ctx->join_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : ctx->chunk_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "side streams");
+  return TNVAN_OK;
+}
+
+// Sampling and the strip adjoint as an overlapped schedule: the instances are
+// cut into up to 8 chunks, each with its own side stream on which the chunk
+// is sampled and then contracted (adjoint pass).  All samplers start at once
+// (the same CTAs as one launch); the adjoint of a chunk starts as soon as its
+// samples exist and shares the SMs with the samplers still running (a
+// sampler CTA and an adjoint CTA fit on one SM together), filling the
+// sampler's tail.  The caller's stream forks to the side streams and joins
+// them again, so stream order (and CUDA graph capture) behave as for one
+// launch.
+static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
+                                     int plan, int8_t* d_spins, float* d_logq, double* d_logZR,
+                                     double* d_dbeta, double* d_dJ, cudaStream_t s) {
+  int rc;
+  int adj_tile = 0, adj_smem = 0, adj_lv = 0;
+  if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv))) return rc;
+  LaunchInfo li, la;
+  if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
+  li.seed = seed;
+  li.step = step;
+  if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
+  int smem = 0, max_edges = 0;
+  for (const Instance& in : ctx->inst) {
+    const MadeDev::TcPlan& P = in.dev.made.tc[plan];
+    smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax));
+    max_edges = std::max(max_edges, in.m);
+  }
+  const int stride = (max_edges + 3) & ~3;
+  if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
+  if ((rc = ensure_side_streams(ctx))) return rc;
+  if (d_dJ) {
+    long long ne = 0;
+    for (const Instance& in : ctx->inst) ne += in.m;
+    CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
+  }
+  const int n = li.n_inst, nc = std::min(n, 8);
+  CK(cudaEventRecord(ctx->fork_ev, s), "fork");
+  for (int c = 0; c < nc; ++c) CK(cudaStreamWaitEvent(ctx->side[c], ctx->fork_ev, 0), "fork wait");
+  for (int c = 0; c < nc; ++c) {  // samplers on high-priority streams, adjoints behind them
+    const int k0 = c * n / nc, k1 = (c + 1) * n / nc;
+    {
+      PROF("sample_tc", ctx->side[c]);
+      CK(launch_sample_tc(ctx->d_inst, li, plan, smem, d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
+                          li.tile_begin[k1]),
+         "tensor-core sample kernel");
+    }
+    CK(cudaEventRecord(ctx->chunk_ev[c], ctx->side[c]), "chunk event");
+    CK(cudaStreamWaitEvent(ctx->side_lo[c], ctx->chunk_ev[c], 0), "chunk wait");
+    PROF("strips_adj", ctx->side_lo[c]);
+    CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
+                         d_dJ ? ctx->d_dj_part : nullptr, stride, nullptr, ctx->side_lo[c], la.tile_begin[k0],
+                         la.tile_begin[k1]),
+       "strip adjoint kernel");
+  }
+  for (int c = 0; c < nc; ++c) {
+    CK(cudaEventRecord(ctx->join_ev[c], ctx->side_lo[c]), "join");
+    CK(cudaStreamWaitEvent(s, ctx->join_ev[c], 0), "join wait");
+  }
+  if (d_dJ) {
+    PROF("strips_dJ_reduce", s);
+    CK(launch_strips_dJ_reduce(ctx->d_inst, la, ctx->d_dj_part, stride, d_dJ, s), "d/dJ reduce");
+  }
+  return TNVAN_OK;
+}
+
 int tnvan_sample_contract_adjoint(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed,
                                   uint64_t step, int precision, int8_t* d_spins, float* d_logq,
                                   double* d_logZR, double* d_dbeta, double* d_dJ, void* stream) {
@@ -1196,6 +1288,13 @@ int tnvan_sample_contract_adjoint(tnvan_ctx* ctx, const double* betas, int batch
   if (batch == 0) return TNVAN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision), s))) return rc;
+  bool strips_only = ctx->inst.size() >= 2;
+  for (const Instance& in : ctx->inst) strips_only = strips_only && in.kind == 0;
+  bool tc_all = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
+  const int plan = tc_all ? pick_tc_plan(ctx) : -1;
+  if (strips_only && plan >= 0 && ctx->tune_overlap)
+    return sample_adjoint_overlapped(ctx, betas, batch, seed, step, plan, d_spins, d_logq, d_logZR, d_dbeta, d_dJ, s);
   if ((rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s))) return rc;
   return run_adjoint(ctx, betas, batch, d_spins, precision, d_logZR, d_dbeta, d_dJ, s);
 }
@@ -1528,12 +1627,42 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     cudaFree(dj);
     ctx->tune_adj_tile = best;
   }
+  if (any_strip && tc_sampler) {  // overlapped schedule on or off, timed on the combined pass
+    long long ne = 0;
+    for (const Instance& in : ctx->inst) ne += in.m;
+    double *dj = nullptr, *db = nullptr;
+    if (cudaMalloc(&dj, sizeof(double) * std::max(ne, 1LL)) != cudaSuccess ||
+        cudaMalloc(&db, sizeof(double) * (size_t)n * batch) != cudaSuccess) {
+      if (dj) cudaFree(dj);
+      cleanup();
+      return fail(ctx, TNVAN_E_NOMEM, "autotune buffers");
+    }
+    float ms_on = 0.f, ms_off = 0.f;
+    auto pass = [&]() {
+      return tnvan_sample_contract_adjoint(ctx, betas, batch, 1, 0, precision, sp, lq, lz, db, dj, stream);
+    };
+    ctx->tune_overlap = 1;
+    rc = time_it(pass, &ms_on);
+    if (!rc) {
+      ctx->tune_overlap = 0;
+      rc = time_it(pass, &ms_off);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(dj);
+    cudaFree(db);
+    if (rc) {
+      cleanup();
+      return rc;
+    }
+    ctx->tune_overlap = ms_on <= ms_off ? 1 : 0;
+  }
   if (out) {
     out[0] = ctx->tune_sample_tile;
     out[1] = ctx->tune_strip_tile;
     out[2] = ctx->tune_bwd_ctas;
     out[3] = ctx->tune_adj_tile;
     out[4] = ctx->tune_tc_plan >= 0 ? kTcGroupMax[ctx->tune_tc_plan] : 0;
+    out[5] = ctx->tune_overlap ? 2 : 1;
   }
   cudaError_t e = cudaStreamSynchronize(s);
   cleanup();
@@ -1554,13 +1683,14 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
   for (int p = 0; p < TNVAN_TC_PLANS; ++p)
     if (kTcGroupMax[p] == c[4]) plan = p;
   if (!in(c[0], {16, 32, 64}) || !in(c[1], {32, 64, 128}) || c[2] < 0 || !in(c[3], {32, 64, 96, 128}) ||
-      (c[4] != 0 && plan < 0))
+      (c[4] != 0 && plan < 0) || c[5] < 0 || c[5] > 2)
     return fail(ctx, TNVAN_E_ARG, "tuning value outside the autotuner's candidates");
   ctx->tune_sample_tile = c[0];
   ctx->tune_strip_tile = c[1];
   ctx->tune_bwd_ctas = c[2];
   ctx->tune_adj_tile = c[3];
   ctx->tune_tc_plan = plan;
+  ctx->tune_overlap = c[5] != 1;  // 0 and 2 (default) on, 1 off
   return TNVAN_OK;
 }
 

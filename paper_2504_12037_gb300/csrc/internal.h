@@ -156,6 +156,7 @@ struct LaunchInfo {
   int n_inst;
   int batch;
   int tile;  // samples per CTA
+  int blk0;  // launch-wide block offset: a launch may cover a sub-range of the blocks
   unsigned long long seed, step;
   int* status;  // device status word: nonzero after a bounded wait gave up
   const unsigned long long* step_dev;  // optional device step counter added to `step`
@@ -217,6 +218,11 @@ struct tnvan_ctx {
   // autotuned launch shapes (0 = built-in heuristic)
   int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0, tune_adj_tile = 0;
   int tune_tc_plan = -1;  // tensor-core sampler step-group plan (-1 = default)
+  int tune_overlap = 1;   // overlapped sampling + adjoint schedule (1 on, 0 off)
+  // side streams and events of the overlapped sampling + adjoint schedule
+  cudaStream_t side[8] = {};  // samplers (highest stream priority)
+  cudaStream_t side_lo[8] = {};  // adjoints (default priority)
+  cudaEvent_t fork_ev = nullptr, join_ev[8] = {}, chunk_ev[8] = {};
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
@@ -249,7 +255,9 @@ cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_
                           const int8_t* spins, double* logZR, double* dbeta, cudaStream_t s);
 cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
                               const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
-                              double* dJ, cudaStream_t s);
+                              double* dJ, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
+cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* part, int part_stride,
+                                    double* dJ, cudaStream_t s);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s);
@@ -279,7 +287,7 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
                              cudaStream_t s);
 int fused_bwd_smem_bytes(int D, int H1, int H2);
 cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
-                             float* logq, const int8_t* given, cudaStream_t s);
+                             float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
 int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,

@@ -105,13 +105,14 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
                                                            int8_t* __restrict__ spins, float* __restrict__ logq,
                                                            const int8_t* __restrict__ given) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int k = find_inst(li, blockIdx.x);
+  const int gblk = blockIdx.x + li.blk0;
+  const int k = find_inst(li, gblk);
   const InstDev& I = inst[k];
   const MadeDev& md = I.made;
   const MadeDev::TcPlan& P = md.tc[plan];
   const int D = md.D, H1 = md.H1, H2 = md.H2;
   const int t = threadIdx.x, w = t >> 5;
-  const int b = (blockIdx.x - li.tile_begin[k]) * 128 + t;
+  const int b = (gblk - li.tile_begin[k]) * 128 + t;
   const bool valid = b < li.batch;
   const SampleTcLayout LY = sample_tc_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax);
   unsigned char* sW1 = smem;
@@ -422,13 +423,17 @@ int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
   return need > floor_bytes ? need : floor_bytes;
 }
 
+// Blocks [blk_begin, blk_end) of the launch (blk_end < 0: all).
 cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
-                             float* logq, const int8_t* given, cudaStream_t s) {
-  const int nblk = li.tile_begin[li.n_inst];
-  if (nblk == 0) return cudaSuccess;
+                             float* logq, const int8_t* given, cudaStream_t s, int blk_begin, int blk_end) {
+  if (blk_end < 0) blk_end = li.tile_begin[li.n_inst];
+  const int nblk = blk_end - blk_begin;
+  if (nblk <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  sample_tc_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, li, plan, spins, logq, given);
+  LaunchInfo lc = li;
+  lc.blk0 = blk_begin;
+  sample_tc_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, lc, plan, spins, logq, given);
   return cudaGetLastError();
 }
 

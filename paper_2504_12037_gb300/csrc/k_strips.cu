@@ -462,11 +462,12 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
                                                          double* __restrict__ logZR, double* __restrict__ dbeta,
                                                          float* __restrict__ part, int part_stride) {
   extern __shared__ float sm[];
-  const int k = find_inst(li, blockIdx.x);
+  const int gblk = blockIdx.x + li.blk0;
+  const int k = find_inst(li, gblk);
   const InstDev& I = inst[k];
   if (I.kind != 0) return;  // another adjoint kernel owns this instance
   const int T = li.tile, t = threadIdx.x, lane = t & 31;
-  const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
+  const int b0 = (gblk - li.tile_begin[k]) * T, b = b0 + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_row_bytes(D);
   build_strip_tables(I, beta, sm, t, T, false);
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
   if (logZR && valid) logZR[(long long)k * li.batch + b] = lz + li.beta[k] * (chat + (double)e1);
   __syncthreads();
   const float scale = beta / (float)li.batch;
-  float* row = part + (long long)blockIdx.x * part_stride;
+  float* row = part + (long long)gblk * part_stride;
   for (int e = t; e < ne; e += T) {
     float s = 0.f;
     for (int w = 0; w < (T >> 5); ++w) s += acc[w * ne + e];
@@ -584,17 +585,29 @@ int strips_adj_occupancy(int tile, int smem_bytes) {
   return nb;
 }
 
+// Blocks [blk_begin, blk_end) of the launch (blk_end < 0: all, followed by
+// the d/dJ reduction when dJ is given; a partial launch leaves the reduction
+// to launch_strips_dJ_reduce once every block has run).
 cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
                               const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
-                              double* dJ, cudaStream_t s) {
-  const int nblk = li.tile_begin[li.n_inst];
-  if (nblk == 0) return cudaSuccess;
+                              double* dJ, cudaStream_t s, int blk_begin, int blk_end) {
+  const bool whole = blk_end < 0;
+  if (whole) blk_end = li.tile_begin[li.n_inst];
+  const int nblk = blk_end - blk_begin;
+  if (nblk <= 0) return cudaSuccess;
   if (li.tile % 32 != 0 || li.tile > 128) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, lv_floats, spins, logZR, dbeta, part, part_stride);
+  LaunchInfo lc = li;
+  lc.blk0 = blk_begin;
+  strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part, part_stride);
   e = cudaGetLastError();
-  if (e != cudaSuccess || !dJ) return e;
+  if (e != cudaSuccess || !dJ || !whole) return e;
+  return launch_strips_dJ_reduce(d_inst, li, part, part_stride, dJ, s);
+}
+
+cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* part, int part_stride,
+                                    double* dJ, cudaStream_t s) {
   strips_dJ_reduce_kernel<<<dim3((unsigned)((part_stride + 7) / 8), li.n_inst), 256, 0, s>>>(d_inst, li, part,
                                                                                             part_stride, dJ);
   return cudaGetLastError();

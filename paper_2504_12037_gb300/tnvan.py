@@ -199,17 +199,17 @@ class Context:
     def autotune(self, betas, batch: int, precision: int, stream=None):
         """Time candidate launch shapes on a synthetic batch and keep the fastest;
         returns the chosen (sampler tile, strip tile, backward CTAs, strip adjoint tile,
-        tensor-core sampler step-group size)."""
+        tensor-core sampler step-group size, overlapped schedule 2 on / 1 off)."""
         b, pb = _arr(betas, np.float64)
-        out = (ctypes.c_int32 * 5)()
+        out = (ctypes.c_int32 * 6)()
         self._check(lib().tnvan_autotune(self._h, pb, batch, precision, _stream(stream), out))
-        return tuple(out[:5])
+        return tuple(out[:6])
 
     def set_tuning(self, choices):
-        """Reuse launch shapes (the 5-tuple autotune returns; 0 = heuristic)."""
+        """Reuse launch shapes (the 6-tuple autotune returns; 0 = default)."""
         c, pc = _arr(list(choices), np.int32)
-        if c.shape[0] != 5:
-            raise ValueError("expected 5 tuning values")
+        if c.shape[0] != 6:
+            raise ValueError("expected 6 tuning values")
         self._check(lib().tnvan_set_tuning(self._h, pc))
 
     def profile(self, enable: bool):

@@ -308,12 +308,14 @@ def test_full_size_adjoint_sampled_rows_and_identity():
         eo += g.m
 
 
-@pytest.mark.parametrize("prec", [tv.FP32, tv.BF16])
-def test_sample_contract_adjoint_equals_separate_calls(prec):
+@pytest.mark.parametrize("prec,overlap", [(tv.FP32, 2), (tv.BF16, 2), (tv.BF16, 1)])
+def test_sample_contract_adjoint_equals_separate_calls(prec, overlap):
     # one pass (sampling, log Z_R from the adjoint's forward sweep, d/dbeta,
-    # d/dJ) against sample_and_contract + contract + backward on the same draw
+    # d/dJ), with the overlapped side-stream schedule on (2) or off (1),
+    # against sample_and_contract + contract + backward on the same draw
     w = wl.workload(2)
     model = _model(w, n_inst=3)
+    model.ctx.set_tuning((0, 0, 0, 0, 0, overlap))
     B = 1000
     spins, logq, logZR = model.buffers(B)
     dbeta = torch.empty(model.n * B, dtype=torch.float64, device="cuda")
@@ -406,7 +408,7 @@ def test_bf16_tensor_core_sampler_log_prob_matches_oracle(group):
     # every step-group plan of the tensor-core sampler (the autotuner picks one)
     w = wl.workload(2)
     model = _model(w, scale=1.5)
-    model.ctx.set_tuning((0, 0, 0, 0, group))
+    model.ctx.set_tuning((0, 0, 0, 0, group, 0))
     batch = 96
     s_all, refs = [], []
     for k in range(model.n):
