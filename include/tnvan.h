@@ -229,12 +229,13 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
 /* Sets the launch shapes that tnvan_autotune chooses, in the same order and
  * units as its `out` (host int32[6]: SIMT sampler samples per CTA, strip
  * samples per CTA, fused-backward CTAs per instance, strip-adjoint samples
- * per CTA, tensor-core sampler step-group size limit, overlapped schedule
- * 2 on / 1 off); 0 restores the built-in default for that entry (the
- * overlapped schedule is on by default).  Lets a caller reuse an earlier
- * tuning without re-timing.  Not in the paper.
+ * per CTA (1 = one warp per strip over 32 samples), tensor-core sampler
+ * step-group size limit, overlapped schedule 2 on / 1 off); 0 restores the
+ * built-in default for that entry (the overlapped schedule is on by
+ * default).  Lets a caller reuse an earlier tuning without re-timing.  Not in
+ * the paper.
  * Errors: TNVAN_E_ARG (NULL, or a value outside the candidates the autotuner
- * tries: {16,32,64}, {32,64,128}, >= 1, {32,64,96,128}, {4,6,8}, {1,2}). */
+ * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {4,6,8}, {1,2}). */
 int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* choices);
 
 /* Optional device step counter (not in the paper; for CUDA-graph capture).

@@ -404,42 +404,70 @@ int pick_sample_tile(const tnvan_ctx* ctx) {
 }
 
 
-// Launch shape of the strip adjoint: samples per CTA T in {128, 96, 64, 32}.
-// The left vectors of a strip take L 2^w T floats of shared memory, so T
-// sets the CTAs per SM; the default minimises (waves of CTAs) x (work an SM
-// does per wave) / (its issue rate, taken as saturating at 8 warps).  An
-// autotuned T (tnvan_autotune) takes precedence when it fits.
-int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats) {
+// Launch shape of the strip adjoint: one thread per sample with T in
+// {128, 96, 64, 32} samples per CTA (all strips in turn), or one warp per
+// strip over 32 samples per CTA (ws_threads = 32 x strips; tuning value 1).
+// The left vectors of a strip take L 2^w floats per thread of shared memory,
+// so the shape sets the CTAs per SM; the default minimises (waves of CTAs) x
+// (strips a thread sweeps) / (the SM's issue rate, taken as saturating at 8
+// warps).  An autotuned shape (tnvan_autotune) takes precedence when it fits.
+int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats, int* ws_threads) {
+  auto& c = ctx->adj_plan;
+  if (c.valid && !ctx->dirty && c.batch == batch && c.tune == ctx->tune_adj_tile) {
+    *tile = c.tile;
+    *smem = c.smem;
+    *lv_floats = c.lv;
+    *ws_threads = c.ws;
+    return TNVAN_OK;
+  }
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (n_sm < 1) n_sm = 1;
+  int max_strips = 0, n_strip_inst = 0;
+  for (const Instance& in : ctx->inst)
+    if (in.kind == 0) {
+      max_strips = std::max(max_strips, (int)in.strip.strips.size());
+      ++n_strip_inst;
+    }
   double best = 1e300;
   *tile = 0;
-  for (int T : {128, 96, 64, 32}) {
+  *ws_threads = 0;
+  for (int T : {1, 128, 96, 64, 32}) {
+    const bool ws = T == 1;
+    const int threads = ws ? strip_adj_ws_threads(ctx) : T;
+    const int spc = ws ? 32 : T;  // samples per CTA
+    if (threads < 32 || threads > (ws ? 256 : 128)) continue;
     int sm = 0, lv = 0;
     for (const Instance& in : ctx->inst)
-      if (in.kind == 0) lv = std::max(lv, strip_adj_lv_floats(in, T));
+      if (in.kind == 0) lv = std::max(lv, ws ? strip_adj_ws_lv_floats(in, threads) : strip_adj_lv_floats(in, T));
     for (const Instance& in : ctx->inst)
-      if (in.kind == 0) sm = std::max(sm, strip_adj_smem_bytes(in, T, lv));
+      if (in.kind == 0)
+        sm = std::max(sm, ws ? strip_adj_ws_smem_bytes(in, threads, lv) : strip_adj_smem_bytes(in, T, lv));
     if (sm > 227 * 1024) continue;
-    const int nb = strips_adj_occupancy(T, sm);
+    const int nb = ws ? strips_adj_ws_occupancy(threads, sm) : strips_adj_occupancy(T, sm);
     if (nb < 1) continue;
-    long long ctas = 0;
-    for (const Instance& in : ctx->inst)
-      if (in.kind == 0) ctas += (batch + T - 1) / T;
+    const long long ctas = (long long)n_strip_inst * ((batch + spc - 1) / spc);
     const double waves = ceil((double)ctas / ((double)nb * n_sm));
-    const double warps = nb * T / 32.0;
-    const double cost = waves * nb * T / std::min(1.0, warps / 8.0);
+    const double warps = nb * threads / 32.0;
+    const double cost = waves * (ws ? 1 : max_strips) / std::min(1.0, warps / 8.0);
     const bool forced = ctx->tune_adj_tile == T;
     if (forced || cost < best) {
       best = cost;
-      *tile = T;
+      *tile = spc;
       *smem = sm;
       *lv_floats = lv;
+      *ws_threads = ws ? threads : 0;
     }
     if (forced) break;
   }
   if (!*tile) return fail(ctx, TNVAN_E_UNSUPPORTED, "strip adjoint needs more than 227 KB of shared memory");
+  c.valid = !ctx->dirty;
+  c.batch = batch;
+  c.tune = ctx->tune_adj_tile;
+  c.tile = *tile;
+  c.smem = *smem;
+  c.lv = *lv_floats;
+  c.ws = *ws_threads;
   return TNVAN_OK;
 }
 
@@ -447,7 +475,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s, bool strips = true);
 int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, int precision,
                 double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s);
-int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats);
+int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats, int* ws_threads);
 int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s);
 int sampler_pack_mask(const tnvan_ctx* ctx, int precision);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
@@ -758,6 +786,7 @@ int tnvan_init_graph(tnvan_ctx* ctx, int instance, int n_spins, int n_edges, con
   in.W.clear();
   in.n_params = 0;
   ctx->dirty = true;
+  ctx->adj_plan.valid = 0;
   return TNVAN_OK;
 }
 
@@ -811,6 +840,7 @@ int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w)
   in.has_ws = true;
   in.has_made = false;
   ctx->dirty = true;
+  ctx->adj_plan.valid = 0;
   return TNVAN_OK;
 }
 
@@ -1080,6 +1110,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   in.n_params = off;
   in.has_made = true;
   ctx->dirty = true;
+  ctx->adj_plan.valid = 0;
   return TNVAN_OK;
 }
 
@@ -1222,8 +1253,8 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
                                      int plan, int8_t* d_spins, float* d_logq, double* d_logZR,
                                      double* d_dbeta, double* d_dJ, cudaStream_t s) {
   int rc;
-  int adj_tile = 0, adj_smem = 0, adj_lv = 0;
-  if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv))) return rc;
+  int adj_tile = 0, adj_smem = 0, adj_lv = 0, adj_ws = 0;
+  if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv, &adj_ws))) return rc;
   LaunchInfo li, la;
   if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
   li.seed = seed;
@@ -1259,7 +1290,7 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
     PROF("strips_adj", ctx->side_lo[c]);
     CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
                          d_dJ ? ctx->d_dj_part : nullptr, stride, nullptr, ctx->side_lo[c], la.tile_begin[k0],
-                         la.tile_begin[k1]),
+                         la.tile_begin[k1], adj_ws),
        "strip adjoint kernel");
   }
   for (int c = 0; c < nc; ++c) {
@@ -1598,36 +1629,9 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     ctx->tune_bwd_ctas = best;
   }
   if (any_strip) {
-    long long ne = 0;
-    for (const Instance& in : ctx->inst) ne += in.m;
-    double* dj = nullptr;
-    if (cudaMalloc(&dj, sizeof(double) * std::max(ne, 1LL)) != cudaSuccess) {
-      cleanup();
-      return fail(ctx, TNVAN_E_NOMEM, "autotune buffers");
-    }
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int T : {128, 96, 64, 32}) {
-      ctx->tune_adj_tile = T;
-      int t_used = 0, sm = 0, lv = 0;
-      if (plan_strip_adjoint(ctx, batch, &t_used, &sm, &lv) || t_used != T) continue;
-      float ms = 0.f;
-      auto adj = [&]() { return tnvan_backward(ctx, betas, batch, sp, lz, lq, precision, gr, nullptr, dj, stream); };
-      if ((rc = time_it(adj, &ms))) {
-        cudaFree(dj);
-        cleanup();
-        return rc;
-      }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = T;
-      }
-    }
-    cudaStreamSynchronize(s);
-    cudaFree(dj);
-    ctx->tune_adj_tile = best;
-  }
-  if (any_strip && tc_sampler) {  // overlapped schedule on or off, timed on the combined pass
+    // the strip adjoint's launch shape, and (tensor-core sampler) whether
+    // sampling and the adjoint overlap on side streams: timed together on the
+    // combined pass a training step runs
     long long ne = 0;
     for (const Instance& in : ctx->inst) ne += in.m;
     double *dj = nullptr, *db = nullptr;
@@ -1637,24 +1641,37 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
       cleanup();
       return fail(ctx, TNVAN_E_NOMEM, "autotune buffers");
     }
-    float ms_on = 0.f, ms_off = 0.f;
     auto pass = [&]() {
       return tnvan_sample_contract_adjoint(ctx, betas, batch, 1, 0, precision, sp, lq, lz, db, dj, stream);
     };
-    ctx->tune_overlap = 1;
-    rc = time_it(pass, &ms_on);
-    if (!rc) {
-      ctx->tune_overlap = 0;
-      rc = time_it(pass, &ms_off);
+    int best_t = 0, best_o = 1;
+    float best_ms = 1e30f;
+    for (int ov : {1, 0}) {
+      if (ov == 0 && !tc_sampler) continue;
+      for (int T : {1, 128, 96, 64, 32}) {
+        ctx->tune_adj_tile = T;
+        ctx->tune_overlap = ov;
+        int t_used = 0, sm = 0, lv = 0, ws = 0;
+        if (plan_strip_adjoint(ctx, batch, &t_used, &sm, &lv, &ws) || (ws ? 1 : t_used) != T) continue;
+        float ms = 0.f;
+        if ((rc = time_it(pass, &ms))) {
+          cudaFree(dj);
+          cudaFree(db);
+          cleanup();
+          return rc;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_t = T;
+          best_o = ov;
+        }
+      }
     }
     cudaStreamSynchronize(s);
     cudaFree(dj);
     cudaFree(db);
-    if (rc) {
-      cleanup();
-      return rc;
-    }
-    ctx->tune_overlap = ms_on <= ms_off ? 1 : 0;
+    ctx->tune_adj_tile = best_t;
+    ctx->tune_overlap = best_o;
   }
   if (out) {
     out[0] = ctx->tune_sample_tile;
@@ -1682,7 +1699,7 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
   int plan = -1;
   for (int p = 0; p < TNVAN_TC_PLANS; ++p)
     if (kTcGroupMax[p] == c[4]) plan = p;
-  if (!in(c[0], {16, 32, 64}) || !in(c[1], {32, 64, 128}) || c[2] < 0 || !in(c[3], {32, 64, 96, 128}) ||
+  if (!in(c[0], {16, 32, 64}) || !in(c[1], {32, 64, 128}) || c[2] < 0 || !in(c[3], {1, 32, 64, 96, 128}) ||
       (c[4] != 0 && plan < 0) || c[5] < 0 || c[5] > 2)
     return fail(ctx, TNVAN_E_ARG, "tuning value outside the autotuner's candidates");
   ctx->tune_sample_tile = c[0];
@@ -1866,8 +1883,8 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   }
   // the strip adjoint keeps a strip's left vectors in shared memory: 128,
   // 96, 64 or 32 samples per CTA
-  int adj_tile = 0, adj_smem = 0, adj_lv = 0;
-  if (any_strip && (rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv))) return rc;
+  int adj_tile = 0, adj_smem = 0, adj_lv = 0, adj_ws = 0;
+  if (any_strip && (rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv, &adj_ws))) return rc;
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
   if (d_dJ) {
@@ -1889,7 +1906,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
     PROF(d_dJ ? "strips_adj" : "strips_dbeta", s);
     CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
-                         d_dJ ? ctx->d_dj_part : nullptr, stride, d_dJ, s),
+                         d_dJ ? ctx->d_dj_part : nullptr, stride, d_dJ, s, 0, -1, adj_ws),
        "strip adjoint kernel");
   }
   if (d_dJ) {

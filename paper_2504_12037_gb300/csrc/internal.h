@@ -219,6 +219,10 @@ struct tnvan_ctx {
   int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0, tune_adj_tile = 0;
   int tune_tc_plan = -1;  // tensor-core sampler step-group plan (-1 = default)
   int tune_overlap = 1;   // overlapped sampling + adjoint schedule (1 on, 0 off)
+  // last strip-adjoint launch plan (valid while batch, tuning and instances are unchanged)
+  struct {
+    int valid = 0, batch = 0, tune = 0, tile = 0, smem = 0, lv = 0, ws = 0;
+  } adj_plan;
   // side streams and events of the overlapped sampling + adjoint schedule
   cudaStream_t side[8] = {};  // samplers (highest stream priority)
   cudaStream_t side_lo[8] = {};  // adjoints (default priority)
@@ -255,7 +259,7 @@ cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_
                           const int8_t* spins, double* logZR, double* dbeta, cudaStream_t s);
 cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
                               const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
-                              double* dJ, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
+                              double* dJ, cudaStream_t s, int blk_begin = 0, int blk_end = -1, int ws_threads = 0);
 cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* part, int part_stride,
                                     double* dJ, cudaStream_t s);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
@@ -299,5 +303,9 @@ int strip_smem_bytes(const Instance& in, int tile);
 int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats);
 int strip_adj_lv_floats(const Instance& in, int tile);
 int strips_adj_occupancy(int tile, int smem_bytes);
+int strip_adj_ws_threads(const tnvan_ctx* ctx);
+int strip_adj_ws_lv_floats(const Instance& in, int threads);
+int strip_adj_ws_smem_bytes(const Instance& in, int threads, int lv_floats);
+int strips_adj_ws_occupancy(int threads, int smem_bytes);
 
 }  // namespace tnvan

@@ -544,6 +544,110 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
   }
 }
 
+// The same pass with one warp per strip (at most 8 strips): a CTA takes 32 samples, warp st
+// contracts strip st for all of them (thread = (strip, sample)), so a CTA
+// lasts one strip's sweeps instead of all strips' -- a short CTA that fills
+// the tail of a launch and the gaps beside other kernels.  log Z_R and d/dbeta
+// are assembled by warp 0 from the per-strip partials in strip order (the same
+// arithmetic as strips_adj_kernel); W-W bond chunks are spread over the warps.
+// Shared memory: tables | spins | left vectors [L][2^w][blockDim] | one row
+// of n_edges accumulators per warp | per-(strip, sample) partials.
+__global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                             int lv_floats, const int8_t* __restrict__ spins,
+                                                             double* __restrict__ logZR, double* __restrict__ dbeta,
+                                                             float* __restrict__ part, int part_stride) {
+  extern __shared__ float sm[];
+  const int gblk = blockIdx.x + li.blk0;
+  const int k = find_inst(li, gblk);
+  const InstDev& I = inst[k];
+  if (I.kind != 0) return;
+  const int NT = blockDim.x, NW = NT >> 5, tid = threadIdx.x, lane = tid & 31, st = tid >> 5;
+  const int b0 = (gblk - li.tile_begin[k]) * 32, b = b0 + lane;
+  const float beta = (float)li.beta[k];
+  const int D = I.D, Dp = padded_row_bytes(D);
+  build_strip_tables(I, beta, sm, tid, NT, false);
+  const int tabn = strip_tab_offset(I, I.n_strips, false);
+  int8_t* ssp = reinterpret_cast<int8_t*>(sm + tabn);
+  float* lvs = sm + strip_adj_lv_offset(tabn, 32, Dp);
+  float* acc = lvs + lv_floats;
+  const int ne = I.n_edges;
+  double* pl = reinterpret_cast<double*>(acc + ((NW * ne + 1) & ~1));
+  float* pd = reinterpret_cast<float*>(pl + NW * 32);
+  for (int e = tid; e < NW * ne; e += NT) acc[e] = 0.f;
+  const int n_valid = min(32, li.batch - b0);
+  stage_spins(spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, D, Dp, ssp, tid, NT);
+  for (int e = n_valid * Dp + tid; e < 32 * Dp; e += NT) ssp[e] = 1;  // padding rows
+  __syncthreads();
+  const bool valid = b < li.batch;
+  const int8_t* srow = ssp + lane * Dp;
+  float* accw = acc + st * ne;
+  if (st < I.n_strips) {
+    const StripDev& sd = I.strips[st];
+    const StripTab tab = strip_tab_at(sm + strip_tab_offset(I, st, false), sd.w, sd.L, false);
+    const StripRow* rows = I.rows + sd.row0;
+    double l = 0.0;
+    float d = 0.f;
+    switch (sd.w) {
+      case 1:
+        strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        break;
+      case 2:
+        strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        break;
+      case 3:
+        strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        break;
+      default:
+        strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        break;
+    }
+    pl[st * 32 + lane] = l;
+    pd[st * 32 + lane] = d;
+  }
+  // W-W bonds for d/dJ: chunks of eight bonds, one warp per chunk
+  for (int e0 = st * 8; e0 < I.n_ww; e0 += NW * 8) {
+    float val[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      val[j] = 0.f;
+      if (valid && e0 + j < I.n_ww) {
+        const EdgeWW q = I.ww[e0 + j];
+        val[j] = (float)(srow[q.a] * srow[q.b]);
+      }
+    }
+    int vi;
+    const float sum = warp_transpose_sum<8>(val, lane, vi);
+    if ((lane & 3) == 0 && e0 + vi < I.n_ww) accw[I.ww[e0 + vi].e] += sum;
+  }
+  __syncthreads();
+  if (st == 0 && valid) {  // strips in order, then -beta E_1 (as strips_adj_kernel)
+    double dl = 0.0, lz = 0.0, chat = 0.0;
+    for (int j = 0; j < I.n_strips; ++j) {
+      dl += pd[j * 32 + lane];
+      lz += pl[j * 32 + lane];
+      chat += I.strips[j].c_hat;
+    }
+    float e1 = 0.f;
+    for (int e = 0; e < I.n_ww; ++e) {
+      const EdgeWW q = I.ww[e];
+      e1 = fmaf(q.J, (float)(srow[q.a] * srow[q.b]), e1);
+    }
+    if (dbeta) dbeta[(long long)k * li.batch + b] = dl + (double)e1;
+    if (logZR) logZR[(long long)k * li.batch + b] = lz + li.beta[k] * (chat + (double)e1);
+  }
+  const float scale = beta / (float)li.batch;
+  float* row = part + (long long)gblk * part_stride;
+  for (int e = tid; e < ne; e += NT) {
+    float s = 0.f;
+    for (int w = 0; w < NW; ++w) s += acc[w * ne + e];
+    row[e] = s * scale;
+  }
+}
+
 // dJ[edge] += sum over the instance's CTA rows: one warp per edge, lane l
 // adding rows l, l+32, ... in FP64, then a fixed xor tree (deterministic).
 __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
@@ -576,6 +680,38 @@ int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats) {
   return 4 * strip_adj_lv_offset(tabn, tile, 4 * w4) + 4 * lv_floats + 4 * (tile / 32) * in.m;
 }
 
+// Warp-per-strip variant: threads per CTA (32 x the most strips of an
+// instance), left-vector floats per launch and shared memory per instance.
+int strip_adj_ws_threads(const tnvan_ctx* ctx) {
+  int nw = 0;
+  for (const Instance& in : ctx->inst)
+    if (in.kind == 0) nw = std::max(nw, (int)in.strip.strips.size());
+  return 32 * nw;
+}
+int strip_adj_ws_lv_floats(const Instance& in, int threads) {
+  int lv = 0;
+  for (const StripDev& sd : in.strip.strips) lv = std::max(lv, sd.L << sd.w);
+  return lv * threads;
+}
+int strip_adj_ws_smem_bytes(const Instance& in, int threads, int lv_floats) {
+  const int D = (int)in.W.size();
+  int w4 = (D + 3) / 4;
+  if ((w4 & 1) == 0) ++w4;
+  int tabn = 0;
+  for (const StripDev& sd : in.strip.strips) tabn += strip_tab_floats_adj(sd.w, sd.L);
+  const int nw = threads / 32;
+  return 4 * strip_adj_lv_offset(tabn, 32, 4 * w4) + 4 * lv_floats + 4 * ((nw * in.m + 1) & ~1) + 12 * nw * 32;
+}
+int strips_adj_ws_occupancy(int threads, int smem_bytes) {
+  if (cudaFuncSetAttribute(strips_adj_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+      cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, strips_adj_ws_kernel, threads, smem_bytes) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
 // CTAs of `tile` threads with `smem_bytes` of shared memory resident per SM.
 int strips_adj_occupancy(int tile, int smem_bytes) {
   if (cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
@@ -590,17 +726,27 @@ int strips_adj_occupancy(int tile, int smem_bytes) {
 // to launch_strips_dJ_reduce once every block has run).
 cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int lv_floats,
                               const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
-                              double* dJ, cudaStream_t s, int blk_begin, int blk_end) {
+                              double* dJ, cudaStream_t s, int blk_begin, int blk_end, int ws_threads) {
   const bool whole = blk_end < 0;
   if (whole) blk_end = li.tile_begin[li.n_inst];
   const int nblk = blk_end - blk_begin;
   if (nblk <= 0) return cudaSuccess;
-  if (li.tile % 32 != 0 || li.tile > 128) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  if (e != cudaSuccess) return e;
   LaunchInfo lc = li;
   lc.blk0 = blk_begin;
-  strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part, part_stride);
+  cudaError_t e;
+  if (ws_threads > 0) {
+    if (li.tile != 32 || ws_threads % 32 != 0 || ws_threads > 256) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(strips_adj_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    strips_adj_ws_kernel<<<nblk, ws_threads, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part,
+                                                              part_stride);
+  } else {
+    if (li.tile % 32 != 0 || li.tile > 128) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part,
+                                                        part_stride);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess || !dJ || !whole) return e;
   return launch_strips_dJ_reduce(d_inst, li, part, part_stride, dJ, s);

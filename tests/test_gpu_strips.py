@@ -211,16 +211,20 @@ def test_contraction_adjoint_beta_and_J(cfg, batch):
         eo += m
 
 
-def test_strip_adjoint_all_widths_tall_strips():
+@pytest.mark.parametrize("shape", [0, 1, 32, 128])
+def test_strip_adjoint_all_widths_tall_strips(shape):
     # strips of width 1, 2, 3 and 4 and 20 rows (more than one 16-row pass),
     # a ragged batch of 40 seeded spin rows: d/dbeta per sample and the
-    # batch-mean d/dJ against FP64 autograd through the oracle's contraction
+    # batch-mean d/dJ against FP64 autograd through the oracle's contraction;
+    # every launch shape of the adjoint (0 = default, 1 = one warp per strip,
+    # else samples per CTA)
     Lx, Ly, beta, batch = 14, 20, 0.7, 40
     g = wl.lattice(Lx, Ly, "gauss", seed=91)
     W = wl.width_columns(Lx, Ly, [1, 4, 8, 13])
     from paper_2504_12037_gb300.model import TNVAN
 
     model = TNVAN([g], [W], [32, 32], [beta], seed=5)
+    model.ctx.set_tuning((0, 0, 0, shape, 0, 0))
     D = len(W)
     s = np.where(np.random.default_rng(17).random((batch, D)) < 0.5, 1.0, -1.0)
     s_t = torch.as_tensor(s)
@@ -273,13 +277,15 @@ def test_full_size_launch_sampled_rows():
         assert float((lz[m] - lz_or[m]).abs().max()) / g.n <= TOL_FP32
 
 
-def test_full_size_adjoint_sampled_rows_and_identity():
-    # The strip adjoint at the full 16x16 batch (the launch shape the planner
-    # picks for 5 x 16384 samples): d/dbeta of sampled rows against FP64
-    # autograd of the oracle, and for the batch-mean d/dJ the identity
+@pytest.mark.parametrize("shape", [0, 1])
+def test_full_size_adjoint_sampled_rows_and_identity(shape):
+    # The strip adjoint at the full 16x16 batch (5 x 16384 samples; the
+    # planner's launch shape, and one warp per strip): d/dbeta of sampled rows
+    # against FP64 autograd of the oracle, and for the batch-mean d/dJ the identity
     #   sum_e J_e dlogZR/dJ_e = beta * mean_b dlogZR/dbeta   (Eq. 4: weights depend on beta J only)
     w = wl.workload(2)
     model = _model(w)
+    model.ctx.set_tuning((0, 0, 0, shape, 0, 0))
     B = w.batch
     seed, step = 778, 4
     spins, logq, logZR = model.sample(B, seed, step)
@@ -308,14 +314,15 @@ def test_full_size_adjoint_sampled_rows_and_identity():
         eo += g.m
 
 
-@pytest.mark.parametrize("prec,overlap", [(tv.FP32, 2), (tv.BF16, 2), (tv.BF16, 1)])
-def test_sample_contract_adjoint_equals_separate_calls(prec, overlap):
+@pytest.mark.parametrize("prec,overlap,shape", [(tv.FP32, 2, 0), (tv.BF16, 2, 1), (tv.BF16, 2, 96), (tv.BF16, 1, 1)])
+def test_sample_contract_adjoint_equals_separate_calls(prec, overlap, shape):
     # one pass (sampling, log Z_R from the adjoint's forward sweep, d/dbeta,
-    # d/dJ), with the overlapped side-stream schedule on (2) or off (1),
-    # against sample_and_contract + contract + backward on the same draw
+    # d/dJ), with the overlapped side-stream schedule on (2) or off (1) and
+    # the adjoint's launch shape, against sample_and_contract + contract +
+    # backward on the same draw
     w = wl.workload(2)
     model = _model(w, n_inst=3)
-    model.ctx.set_tuning((0, 0, 0, 0, 0, overlap))
+    model.ctx.set_tuning((0, 0, 0, shape, 0, overlap))
     B = 1000
     spins, logq, logZR = model.buffers(B)
     dbeta = torch.empty(model.n * B, dtype=torch.float64, device="cuda")
