@@ -212,20 +212,10 @@ def run_ours(a):
         return model, bufs, dbeta, dJ, step, float(t.item()), prof, clocks
 
     def graph_time(model, mode, bufs, dbeta, dJ):
-        """The same step as one CUDA-graph replay (device step counter); ms per step."""
-        counter = torch.zeros(1, dtype=torch.int64, device="cuda")
-        model.ctx.set_step_counter(counter)
-        gstream = torch.cuda.Stream()
-        gstream.wait_stream(stream)
-        with torch.cuda.stream(gstream):
-            model.train_step(B, seed, 0, mode, 0.01, bufs, dbeta, dJ, gstream)
-        torch.cuda.synchronize()
-        cg = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(cg, stream=gstream):
-            model.train_step(B, seed, 0, mode, 0.01, bufs, dbeta, dJ, gstream)
-            counter.add_(1)
+        """The same step as one CUDA-graph replay (model.capture_train_step); ms per step."""
+        cs = model.capture_train_step(B, seed, mode, 0.01, bufs, dbeta, dJ)
         for _ in range(a.warmup):
-            cg.replay()
+            cs.replay()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -234,22 +224,22 @@ def run_ours(a):
         for i in range(a.steps):
             flush.zero_()  # evict L2 between replays (outside the timed interval)
             gs[i].record(stream)
-            cg.replay()
+            cs.replay()
             ge[i].record(stream)
         torch.cuda.synchronize()
         ms_g = sum(x.elapsed_time(y) for x, y in zip(gs, ge)) / a.steps
         tg = torch.tensor([ms_g], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(tg, op=dist.ReduceOp.MAX)
-        model.ctx.set_step_counter(None)
-        return float(tg.item())
+        return float(tg.item()), cs
 
     # clocks are sampled from before the eager timed steps to after the graph replays
     model, (spins, logq, logZR), dbeta, dJ, step, ms_eager, prof, clocks = timed(prec, a.steps, a.warmup, True)
     samples_step = n_inst * B * world
     graph = None
+    captured = None
     if not a.no_graph:
-        ms_g = graph_time(model, prec, (spins, logq, logZR), dbeta, dJ)
+        ms_g, captured = graph_time(model, prec, (spins, logq, logZR), dbeta, dJ)
         graph = {"value": samples_step / (ms_g / 1e3), "ms_per_step": ms_g,
                  "note": "whole training step captured once, replayed; Philox step from a device counter"}
     clk = clocks.stop() if clocks else None
@@ -261,7 +251,7 @@ def run_ours(a):
     compare = None
     if a.compare and a.compare != a.precision:
         m_c, b_c, db_c, dj_c, _, ms_c, prof_c, _ = timed(PREC[a.compare], a.steps, a.warmup, False)
-        ms_cg = None if a.no_graph else graph_time(m_c, PREC[a.compare], b_c, db_c, dj_c)
+        ms_cg = None if a.no_graph else graph_time(m_c, PREC[a.compare], b_c, db_c, dj_c)[0]
         ms_ch = ms_cg if ms_cg else ms_c
         compare = {"precision": a.compare, "value": samples_step / (ms_ch / 1e3), "ms_per_step": ms_ch,
                    "eager_ms_per_step": ms_c,
@@ -275,9 +265,16 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     fe_last = None
+    h_ctr = torch.zeros(1, dtype=torch.int64, pin_memory=True)
     t0 = time.perf_counter()
     for i in range(a.e2e_steps):
-        step(10 ** 6 + i)
+        if captured is not None:
+            # the step's input from the host: which Philox step (and Adam t) to run
+            h_ctr[0] = 10 ** 6 + i
+            captured.counter.copy_(h_ctr, non_blocking=True)
+            captured.replay()  # the captured step (public model.capture_train_step)
+        else:
+            step(10 ** 6 + i)
         fe_last = model.free_energy(B, logZR, logq, stream)  # D2H of the per-instance results (syncs)
         h_spins.copy_(spins, non_blocking=True)
         h_logq.copy_(logq, non_blocking=True)
@@ -288,7 +285,8 @@ def run_ours(a):
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e = {"value": samples_step / float(te.item()), "unit": UNIT,
-           "h2d_bytes_per_step": 8 * n_inst,
+           "h2d_bytes_per_step": 8 if captured is not None else 8 * n_inst,
+           "path": "model.capture_train_step replay" if captured is not None else "model.train_step",
            "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 32 * n_inst)}
 
     # ----- per-kernel durations: the same step with the overlapped side-stream

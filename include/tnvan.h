@@ -242,8 +242,10 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* choices);
  * With d_counter non-NULL, every sampling launch uses the Philox step
  * `step + *d_counter`, read on the device when the kernel runs, so a graph
  * captured once draws fresh random numbers on each replay if the caller
- * advances *d_counter between replays (e.g. inside the graph).  d_counter:
- * borrowed device uint64; NULL restores host-only steps. */
+ * advances *d_counter between replays (e.g. inside the graph).  tnvan_adam
+ * then takes its step as t + *d_counter, with the bias corrections formed on
+ * the device.  d_counter: borrowed device uint64; NULL restores host-only
+ * steps. */
 int tnvan_set_step_counter(tnvan_ctx* ctx, const uint64_t* d_counter);
 
 /* Per-kernel timing, a tracing aid (not in the paper).  enable = 1 clears the

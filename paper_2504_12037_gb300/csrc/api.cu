@@ -1492,7 +1492,7 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
   const double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
   PROF("adam", static_cast<cudaStream_t>(stream));
   CK(launch_adam(n, d_params, d_grad, d_m, d_v, (float)lr, (float)beta1, (float)beta2, (float)eps,
-                 (float)bc1, (float)bc2, static_cast<cudaStream_t>(stream)),
+                 (float)bc1, (float)bc2, static_cast<cudaStream_t>(stream), ctx->step_dev, (long long)t),
      "adam kernel");
   return TNVAN_OK;
 }

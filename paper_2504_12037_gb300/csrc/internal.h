@@ -295,7 +295,8 @@ cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int pl
 int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
-                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
+                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s,
+                        const unsigned long long* t_dev = nullptr, long long t_base = 0);
 
 int sample_smem_bytes(const Instance& in, int tile);
 int general_smem_bytes(int arena, int pairs, int D, int T, bool db);

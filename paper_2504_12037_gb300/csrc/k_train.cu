@@ -586,9 +586,23 @@ cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const 
 }
 
 // Adam (Kingma & Ba 2015), bias corrections bc1 = 1 - b1^t, bc2 = 1 - b2^t.
+// With t_dev, the step is t_base + *t_dev (a device step counter, for
+// replayed CUDA graphs) and the bias corrections are formed here.
 __global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, float lr, float b1,
-                            float b2, float eps, float bc1, float bc2) {
+                            float b2, float eps, float bc1, float bc2, const unsigned long long* t_dev,
+                            long long t_base) {
+  if (t_dev) {  // one thread per CTA forms them (FP64 is a narrow unit here)
+    __shared__ float bc[2];
+    if (threadIdx.x == 0) {
+      const double t = (double)(t_base + (long long)*t_dev);
+      bc[0] = (float)(1.0 - exp(t * log((double)b1)));
+      bc[1] = (float)(1.0 - exp(t * log((double)b2)));
+    }
+    __syncthreads();
+    bc1 = bc[0];
+    bc2 = bc[1];
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const float gi = g[i];
@@ -601,11 +615,12 @@ __global__ void adam_kernel(long long n, float* __restrict__ p, const float* __r
 }
 
 cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
-                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s) {
+                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s,
+                        const unsigned long long* t_dev, long long t_base) {
   if (n == 0) return cudaSuccess;
   long long nb = (n + 255) / 256;
   if (nb > 1216) nb = 1216;
-  adam_kernel<<<(int)nb, 256, 0, s>>>(n, p, g, m, v, lr, b1, b2, eps, bc1, bc2);
+  adam_kernel<<<(int)nb, 256, 0, s>>>(n, p, g, m, v, lr, b1, b2, eps, bc1, bc2, t_dev, t_base);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,11 @@ class TNVAN:
         self.ctx.sample_and_contract(self.betas, batch, seed, step, precision, spins, logq, logZR, stream)
         return spins, logq, logZR
 
+    def capture_train_step(self, batch: int, seed: int, precision: int = tv.FP32, lr: float = 0.01, out=None,
+                           dbeta=None, dJ=None) -> "CapturedStep":
+        """The training step as a replayable CUDA graph (see CapturedStep)."""
+        return CapturedStep(self, batch, seed, precision, lr, out, dbeta, dJ)
+
     def free_energy(self, batch: int, logZR, logq, stream=None) -> np.ndarray:
         """[n_inst, 4]: F_q, F_IS, stderr, logZ_IS (per instance, not per spin)."""
         return self.ctx.free_energy(self.betas, batch, logZR, logq, stream)
@@ -75,6 +80,43 @@ class TNVAN:
         self.t += 1
         self.ctx.adam(self.params, self.grad, self.m, self.v, lr, 0.9, 0.999, 1e-8, self.t, stream)
         return spins, logq, logZR
+
+
+class CapturedStep:
+    """One training step (Algorithm 1 (a)-(d): sample, contract with the
+    adjoint, REINFORCE gradient, Adam) captured once as a CUDA graph.
+
+    Each replay() runs the whole step on the device with no host work: the
+    Philox step of the sampler and Adam's t advance through a device counter
+    (tnvan_set_step_counter), so every replay draws fresh samples into the
+    same buffers (`out`, `dbeta`, `dJ`).  Construction takes one eager step
+    (workspaces and launch plans settle) before capturing."""
+
+    def __init__(self, model: "TNVAN", batch: int, seed: int, precision: int = tv.FP32, lr: float = 0.01,
+                 out=None, dbeta=None, dJ=None):
+        self.model = model
+        self.out = out if out is not None else model.buffers(batch)
+        self.dbeta, self.dJ = dbeta, dJ
+        self.counter = torch.zeros(1, dtype=torch.int64, device=model.device)
+        self.stream = torch.cuda.Stream(device=model.device)
+        self.stream.wait_stream(torch.cuda.current_stream(model.device))
+        model.ctx.reserve(batch)
+        with torch.cuda.stream(self.stream):
+            model.train_step(batch, seed, 0, precision, lr, self.out, dbeta, dJ, self.stream)
+        self.stream.synchronize()
+        model.ctx.set_step_counter(self.counter)
+        self.graph = torch.cuda.CUDAGraph()
+        t0 = model.t
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            model.train_step(batch, seed, 1, precision, lr, self.out, dbeta, dJ, self.stream)
+            self.counter.add_(1)
+        model.t = t0  # the graph's step is t0 + 1 + counter
+        model.ctx.set_step_counter(None)
+
+    def replay(self):
+        """One training step, queued on the current stream."""
+        self.graph.replay()
+        self.model.t += 1
 
 
 class FreeEnergyFunction(torch.autograd.Function):

@@ -80,3 +80,34 @@ def test_autotune_picks_valid_shapes_and_results_unchanged():
     m.ctx.set_tuning(choice_bf)  # round trip
     with pytest.raises(tv.TnvanError):
         m.ctx.set_tuning((0, 0, 0, 0, 5, 0))
+
+
+def test_captured_train_step_matches_eager_steps():
+    # model.capture_train_step: replay k draws Philox step 1 + k with Adam's
+    # t = 2 + k (counter on the device); the eager step with the same step and
+    # t gives the same samples and, up to the bias corrections' rounding (formed
+    # on the device from FP32 betas), the same parameters
+    w = wl.workload(2)
+    from paper_2504_12037_gb300.model import TNVAN
+
+    B = 1000
+    mk = lambda: TNVAN(w.graphs[:2], w.widths_sets[:2], w.hidden, w.betas[:2], seed=3)
+    a, b = mk(), mk()
+    dba = torch.empty(2 * B, dtype=torch.float64, device="cuda")
+    dja = torch.empty(sum(a.n_edges), dtype=torch.float64, device="cuda")
+    dbb, djb = torch.empty_like(dba), torch.empty_like(dja)
+    outa = a.buffers(B)
+    a.train_step(B, 9, 0, tv.BF16, 0.01, outa, dba, dja)
+    a.train_step(B, 9, 1, tv.BF16, 0.01, outa, dba, dja)
+    torch.cuda.synchronize()
+    cs = b.capture_train_step(B, 9, tv.BF16, 0.01, None, dbb, djb)  # takes the eager step 0
+    cs.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(cs.out[0], outa[0]) and torch.equal(cs.out[2], outa[2])
+    assert torch.equal(djb, dja) and torch.equal(dbb, dba)
+    assert b.t == a.t == 2
+    assert torch.allclose(a.params, b.params, rtol=1e-5, atol=1e-7)
+    s1 = cs.out[0].clone()
+    cs.replay()  # the next step: fresh draws
+    torch.cuda.synchronize()
+    assert b.t == 3 and not torch.equal(cs.out[0], s1)
