@@ -935,6 +935,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     off += (long long)L.nout * L.nin + L.nout;
   }
   md.n_params = off;
+  if (off >= (1LL << 30)) return fail(ctx, TNVAN_E_UNSUPPORTED, "network too large (%lld parameters)", off);
   md.fused_ok = n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
                 H[0] <= 128 && H[1] <= 128 && 128 + (D + 16) + (H[0] + 16) + (H[1] + 16) <= 512 &&
                 fused_bwd_smem_bytes(D, H[0], H[1]) <= 227 * 1024;

@@ -7,12 +7,13 @@ namespace tnvan {
 // block with the MADE masks applied and hidden units sorted by degree, then
 // its biases in the same order (layer offsets dst_off), read from the
 // caller's natural layout.
-__device__ __forceinline__ float packed_value(const MadeDev& md, long long j) {
+__device__ __forceinline__ float packed_value(const MadeDev& md, long long jj) {
+  int j = (int)jj;  // a network's parameter count fits in 32 bits (checked at set-up)
   for (int l = 0; l < md.n_layers; ++l) {
     const LayerDev& L = md.layer[l];
-    const long long nw = (long long)L.nout * L.nin;
+    const int nw = L.nout * L.nin;
     if (j < nw) {
-      const int o = (int)(j / L.nin), i = (int)(j % L.nin);
+      const int o = j / L.nin, i = j - o * L.nin;
       const int no = L.perm_out ? L.perm_out[o] : o;
       const int ni = L.perm_in ? L.perm_in[i] : i;
       const int dout = L.deg_out[o], din = L.deg_in[i];
@@ -20,7 +21,7 @@ __device__ __forceinline__ float packed_value(const MadeDev& md, long long j) {
       return conn ? md.raw[L.src_off + (long long)no * L.nin + ni] : 0.f;
     }
     j -= nw;
-    if (j < L.nout) return md.raw[L.src_off + nw + (L.perm_out ? L.perm_out[j] : (int)j)];
+    if (j < L.nout) return md.raw[L.src_off + nw + (L.perm_out ? L.perm_out[j] : j)];
     j -= L.nout;
   }
   return 0.f;
@@ -68,8 +69,8 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
         base = n1 + n2;
         src = md.layer[2].dst_off + (e - n1 - n2);
       }
-      const long long le = e - base;
-      const int r = (int)(le / cols), c = (int)(le % cols);
+      const int le = (int)(e - base);
+      const int r = le / cols, c = le - r * cols;
       const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
       uint32_t u = __float_as_uint(packed_value(md, src));
       u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even

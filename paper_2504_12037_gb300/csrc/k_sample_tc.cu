@@ -334,7 +334,11 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
         }
         x = (a0 + a1) + (a2 + a3);
       }
-      const float pr = 1.f / (1.f + expf(-x));
+      // one exponential for both sigmoid(x) and softplus(-s x) (fast-math forms:
+      // this kernel is the reduced-precision mode)
+      const float ex = __expf(-fabsf(x));  // in (0, 1]
+      const float rcp = __frcp_rn(1.f + ex);
+      const float pr = x >= 0.f ? rcp : ex * rcp;
       const uint32_t word = (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
       const float u = (float)(word >> 8) * 5.9604644775390625e-08f;
       bool up = u < pr;
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
         else sb1 |= 1ull << (i - 64);
       }
       st_bf16(sS, rbS + 16u * (uint32_t)i, s);
-      lq -= softplusf(-s * x);
+      lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
     }
     // fold the group; recompute P1g for the next group
     fence_proxy_async_smem();
