@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
         const int f = c + i;
         const float x = v[i] + sbo[f];
         const float s = ((ms >> i) & 1u) ? 1.f : -1.f;
-        v[i] = wb * s / (1.f + expf(s * x));
+        v[i] = wb * s * __frcp_rn(1.f + __expf(s * x));
       }
       store8(sdX, tdX.rowbytes(), t, c, v);
       store8(sdX, tdX.rowbytes(), t, c + 8, v + 8);
