@@ -1039,8 +1039,10 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   }
   // Step groups of the tensor-core sampler, one plan per group-size limit
   // (kTcGroupMax; the autotuner picks one): at most that many steps and 32
-  // units of each hidden layer completing inside a group.  Per group only the
-  // in-group triangles, each row padded to a multiple of 4 floats.
+  // units of each hidden layer completing inside a group.  Per group the
+  // in-group triangles and the group's biases, each row padded to a multiple
+  // of 4 floats, and a record of TNVAN_TCG_INTS ints (bounds, offsets and the
+  // per-step unit counts) that the kernel bulk-copies one group ahead.
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
     MadeDev::TcPlan& P = md.tc[p];
     P = MadeDev::TcPlan{};
@@ -1065,15 +1067,24 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       const int u2lo = before(c2, i0), u2hi = before(c2, i1);
       fits = fits && u1hi - u1lo <= UGMAX && u2hi - u2lo <= UGMAX;
       const int gstart = (int)src.size();
-      const int t1 = add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
+      add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
       const int t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
       const int to = add_tile(i0, i1, u2lo, u2hi, md.layer[2].dst_off, H[1]);
+      // the group's biases (gathered with the triangles)
+      const int b1o = add_tile(0, 1, u1lo, u1hi, md.layer[0].dst_off + (long long)H[0] * D, 0);
+      const int b2o = add_tile(0, 1, u2lo, u2hi, md.layer[1].dst_off + (long long)H[1] * H[0], 0);
+      const int boo = add_tile(0, 1, i0, i1, md.layer[2].dst_off + (long long)D * H[1], 0);
       const int gsize = (int)src.size() - gstart;
       twmax = std::max(twmax, gsize);
       tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
       tcw2 = std::max(tcw2, ((u2hi + 15) & ~15) - (u2lo & ~15));
-      grp.insert(grp.end(), {i0, i1, u1lo, u1hi, u2lo, u2hi, 0, 0, 0, gstart, gsize, 0, t1 - gstart, t2 - gstart,
-                             to - gstart});
+      int rec[TNVAN_TCG_INTS] = {i0, i1, u1lo, u1hi, u2lo, u2hi, gstart, gsize, t2 - gstart, to - gstart,
+                                 b1o - gstart, b2o - gstart, boo - gstart};
+      for (int q = 0; q <= i1 - i0; ++q) {  // units with degree < i0 + q
+        rec[13 + q] = before(c1, i0 + q);
+        rec[22 + q] = before(c2, i0 + q);
+      }
+      grp.insert(grp.end(), rec, rec + TNVAN_TCG_INTS);
       i0 = i1;
     }
     int* dgrp = nullptr;
@@ -1086,7 +1097,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler triangles): %s", cudaGetErrorString(e2));
       in.dev_allocs.push_back(blk);
     }
-    P.n_groups = (int)grp.size() / GROUP_INTS;
+    P.n_groups = (int)grp.size() / TNVAN_TCG_INTS;
     P.groups = dgrp;
     P.blocks = static_cast<float*>(blk);
     P.src = dsrc;

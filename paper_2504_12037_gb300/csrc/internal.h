@@ -16,6 +16,10 @@
 #define TNVAN_MAX_ELIM_W 8
 #define GROUP_INTS 15
 #define TNVAN_TC_PLANS 3  // step-group size limits of the tensor-core sampler: 4, 6, 8
+// Tensor-core sampler group record: i0 i1 u1lo u1hi u2lo u2hi, block start and
+// size (floats), offsets of TW2 TWo b1 b2 bo in the block, then c1 and c2 at
+// the group's steps (9 each: units with degree < i0 + q, q = 0..8), pad.
+#define TNVAN_TCG_INTS 32
 
 namespace tnvan {
 
@@ -57,7 +61,7 @@ struct MadeDev {
   struct TcPlan {
     int ok;               // eligible (unit counts within the kernel's limits)
     int n_groups;
-    const int* groups;    // [n_groups][GROUP_INTS]: i0 i1 u1lo u1hi u2lo u2hi - - - start size - TW1 TW2 TWo
+    const int* groups;    // [n_groups][TNVAN_TCG_INTS], see TNVAN_TCG_INTS
     float* blocks;        // gathered from `packed` on every call
     const int* src;       // [n_blk] index into `packed`, -1 = zero
     long long n_blk;

@@ -72,7 +72,7 @@ __device__ __forceinline__ float pick4(const uint32_t (&r)[4], int j) {
 const int kTcGroupMax[TNVAN_TC_PLANS] = {4, 6, 8};
 
 struct SampleTcLayout {
-  int wbytes, oS, oH1, oH2, oTW, oTab, oBar, total;
+  int wbytes, oS, oH1, oH2, oBuf, buf, oBar, total;
 };
 
 __host__ __device__ inline SampleTcLayout sample_tc_layout(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
@@ -85,10 +85,11 @@ __host__ __device__ inline SampleTcLayout sample_tc_layout(int D, int H1, int H2
   p += 16 * (int)mn_sbo(tcw1) + 64;  // + zeroed tail read by the 4-wide in-group loops
   L.oH2 = p;
   p += 16 * (int)mn_sbo(tcw2) + 64;
-  L.oTW = p;
-  p += 4 * ((twmax + 3) & ~3);
-  L.oTab = p;
-  p += 4 * (STC_UG + STC_UG + STC_GI + 2 * (STC_GI + 1));
+  // two group buffers (this group's, the next group's): the record then the
+  // triangles and biases
+  L.oBuf = p;
+  L.buf = 4 * TNVAN_TCG_INTS + 4 * ((twmax + 3) & ~3);
+  p += 2 * L.buf;
   p = (p + 15) & ~15;
   L.oBar = p;
   p += 32;
@@ -121,12 +122,8 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   unsigned char* sS = smem + LY.oS;
   unsigned char* sH1 = smem + LY.oH1;
   unsigned char* sH2 = smem + LY.oH2;
-  float* TW = reinterpret_cast<float*>(smem + LY.oTW);
-  float* gb1 = reinterpret_cast<float*>(smem + LY.oTab);  // biases of the group's units
-  float* gb2 = gb1 + STC_UG;
-  float* gbo = gb2 + STC_UG;
-  int* gc1 = reinterpret_cast<int*>(gbo + STC_GI);  // c1[i], c2[i] for i = i0-1 .. i1-1
-  int* gc2 = gc1 + (STC_GI + 1);
+  unsigned char* gbuf0 = smem + LY.oBuf;
+  unsigned char* gbuf1 = gbuf0 + LY.buf;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + LY.oBar);  // MMA completion
   uint64_t* cbar = bar + 1;                                     // bulk copies
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
@@ -136,9 +133,6 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   const uint32_t rbS = (uint32_t)(t >> 3) * sboS + rowb, rb1 = (uint32_t)(t >> 3) * sbo1 + rowb,
                  rb2 = (uint32_t)(t >> 3) * sbo2 + rowb;
   const uint32_t kbW1 = 2u * D / 16u * 128u, kbW2 = 2u * H1 / 16u * 128u, kbWo = 2u * H2 / 16u * 128u;
-  const float* b1 = md.packed + md.layer[0].dst_off + (long long)H1 * D;
-  const float* b2 = md.packed + md.layer[1].dst_off + (long long)H2 * H1;
-  const float* bo = md.packed + md.layer[2].dst_off + (long long)D * H2;
   const int ncols = sample_tc_tmem_cols(D, H2, P.tcw1);
   if (t == 0) {
     mbar_init(bar, 1);
@@ -157,12 +151,18 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   tc::fence_after_sync();
   uint32_t cphase = 0;
   bool copy_pending = false, mma_pending = false;
+  // group gg's record and block into a group buffer (one thread; the caller
+  // has armed cbar for `extra` more bytes)
+  auto copy_group = [&](int gg, unsigned char* dst, uint32_t extra) {
+    const int* Gg = P.groups + TNVAN_TCG_INTS * gg;
+    const uint32_t nb = (uint32_t)__ldg(Gg + 7) * 4u;
+    mbar_expect_tx(cbar, extra + 4u * TNVAN_TCG_INTS + nb);
+    bulk_g2s(dst, Gg, 4u * TNVAN_TCG_INTS, cbar);
+    if (nb) bulk_g2s(dst + 4 * TNVAN_TCG_INTS, P.blocks + __ldg(Gg + 6), nb, cbar);
+  };
   if (t == 0) {
-    const int* G0 = P.groups;
-    const uint32_t tb0 = (uint32_t)(G0[10] - G0[12]) * 4u;
-    mbar_expect_tx(cbar, (uint32_t)LY.wbytes + tb0);
+    copy_group(0, gbuf0, (uint32_t)LY.wbytes);
     bulk_g2s(sW1, md.wtiles, (uint32_t)LY.wbytes, cbar);
-    if (tb0) bulk_g2s(TW, P.blocks + G0[9] + G0[12], tb0, cbar);
   }
   copy_pending = true;
   const uint32_t tmem = *slot;
@@ -180,7 +180,18 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   uint4 rnd = make_uint4(0, 0, 0, 0);
   unsigned long long sb0 = 0ull, sb1 = 0ull;  // spin i is +1 iff bit i is set
   for (int g = 0; g < P.n_groups; ++g) {
-    const int* G = P.groups + GROUP_INTS * g;
+    unsigned char* gb = (g & 1) ? gbuf1 : gbuf0;      // this group's buffer
+    unsigned char* gbn = (g & 1) ? gbuf0 : gbuf1;     // the next group's
+    if (copy_pending) {  // group 0 (with the weights); later groups arrived during the previous group
+      if (mbar_wait(cbar, cphase)) {
+        cphase ^= 1u;
+        copy_pending = false;
+      } else {
+        ok = false;
+      }
+    }
+    const int* G = reinterpret_cast<const int*>(gb);
+    const float* TWb = reinterpret_cast<const float*>(gb + 4 * TNVAN_TCG_INTS);
     const int i0 = G[0], i1 = G[1], u1lo = G[2], u1hi = G[3], u2lo = G[4], u2hi = G[5];
     const int gi = i1 - i0, n1g = u1hi - u1lo, n2g = u2hi - u2lo;
     const int w1 = u1lo & ~15, w2 = u2lo & ~15;
@@ -199,25 +210,20 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
       *reinterpret_cast<uint4*>(sH1 + o) = make_uint4(0, 0, 0, 0);
     for (int o = t * 16; o < 16 * (int)sbo2 + 64; o += 128 * 16)
       *reinterpret_cast<uint4*>(sH2 + o) = make_uint4(0, 0, 0, 0);
-    if (t < n1g) gb1[t] = __ldg(b1 + u1lo + t);
-    if (t >= 32 && t - 32 < n2g) gb2[t - 32] = __ldg(b2 + u2lo + t - 32);
-    if (t >= 64 && t - 64 < gi) gbo[t - 64] = __ldg(bo + i0 + t - 64);
-    if (t >= 96 && t - 96 <= gi) {
-      const int i = i0 - 1 + (t - 96);
-      gc1[t - 96] = i >= 0 ? md.c1[i] : 0;
-      gc2[t - 96] = i >= 0 ? md.c2[i] : 0;
-    }
-    if (mbar_wait(cbar, cphase)) {  // this group's triangle tiles (first: the weights too)
-      cphase ^= 1u;
-      copy_pending = false;
-    } else {
-      ok = false;
-    }
-    ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles and group tables visible; one verdict
+    ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles visible; one verdict
     if (!ok) break;
-    const float* TW1 = TW;
-    const float* TW2 = TW + (G[13] - G[12]);
-    const float* TWo = TW + (G[14] - G[12]);
+    if (t == 0 && g + 1 < P.n_groups) {  // the next group's data, while this group runs
+      copy_group(g + 1, gbn, 0u);
+    }
+    if (g + 1 < P.n_groups) copy_pending = true;
+    const float* TW1 = TWb;
+    const float* TW2 = TWb + G[8];
+    const float* TWo = TWb + G[9];
+    const float* gb1 = TWb + G[10];  // biases of the group's units
+    const float* gb2 = TWb + G[11];
+    const float* gbo = TWb + G[12];
+    const int* gc1 = G + 13;  // c1[i], c2[i] for i = i0-1 .. i1-1
+    const int* gc2 = G + 22;
     const int s1 = (gi + 3) & ~3, s2 = (n1g + 3) & ~3, so = (n2g + 3) & ~3;  // triangle row strides
     float sg[STC_GI];  // in-group spins (0 until drawn)
 #pragma unroll
@@ -359,7 +365,17 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
     __syncthreads();
     tc::fence_after_sync();
     if (g + 1 < P.n_groups) {
-      const int* Gn = G + GROUP_INTS;
+      if (mbar_wait(cbar, cphase)) {  // the next group's record (issued at this group's start)
+        cphase ^= 1u;
+        copy_pending = false;
+      } else {
+        ok = false;
+      }
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      const int* Gn = reinterpret_cast<const int*>(gbn);
       const int w1n = Gn[2] & ~15, n1n = ((Gn[3] + 15) & ~15) - w1n;
       const int kS = (i1 + 15) & ~15;  // spins 0 .. i1-1 (zero beyond)
       if (t == 0) {
@@ -381,11 +397,8 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
                          id1, kk > 0 ? 1u : 0u);
         }
         tc::mma_commit(bar);
-        const uint32_t tbn = (uint32_t)(Gn[10] - Gn[12]) * 4u;
-        mbar_expect_tx(cbar, tbn);
-        if (tbn) bulk_g2s(TW, P.blocks + Gn[9] + Gn[12], tbn, cbar);
       }
-      mma_pending = copy_pending = true;
+      mma_pending = true;
       init2 = init2 || n1 > 0;
       inito = inito || n2 > 0;
       p1ok = n1n > 0;
