@@ -142,9 +142,14 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
     tc::tmem_alloc(slot, (uint32_t)ncols);
     tc::tmem_relinquish();
   }
-  // the spin tile starts at zero (spins not drawn yet contribute nothing)
+  // the spin tile starts at zero (spins not drawn yet contribute nothing);
+  // the fold tiles too (later groups zero only the columns they do not write)
   for (int o = t * 16; o < 16 * (int)sboS; o += 128 * 16)
     *reinterpret_cast<uint4*>(sS + o) = make_uint4(0, 0, 0, 0);
+  for (int o = t * 16; o < 16 * (int)sbo1 + 64; o += 128 * 16)
+    *reinterpret_cast<uint4*>(sH1 + o) = make_uint4(0, 0, 0, 0);
+  for (int o = t * 16; o < 16 * (int)sbo2 + 64; o += 128 * 16)
+    *reinterpret_cast<uint4*>(sH2 + o) = make_uint4(0, 0, 0, 0);
   fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -206,10 +211,19 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
       }
       tc::fence_after_sync();
     }
-    for (int o = t * 16; o < 16 * (int)sbo1 + 64; o += 128 * 16)
-      *reinterpret_cast<uint4*>(sH1 + o) = make_uint4(0, 0, 0, 0);
-    for (int o = t * 16; o < 16 * (int)sbo2 + 64; o += 128 * 16)
-      *reinterpret_cast<uint4*>(sH2 + o) = make_uint4(0, 0, 0, 0);
+    // the fold's K windows must be zero outside the units this group writes:
+    // columns [0, u_lo - w) and [u_hi - w, n) of every 8-sample row group
+    {
+      const int lo1 = u1lo - w1, hi1 = u1hi - w1, p1 = lo1 + (n1 - hi1);
+      const int lo2 = u2lo - w2, hi2 = u2hi - w2, p2 = lo2 + (n2 - hi2);
+      for (int e = t; e < 16 * (p1 + p2); e += 128) {
+        const bool l1 = e < 16 * p1;
+        const int f = l1 ? e : e - 16 * p1, pn = l1 ? p1 : p2, lo = l1 ? lo1 : lo2, hi = l1 ? hi1 : hi2;
+        const int rg = f / pn, j = f - rg * pn;
+        const int col = j < lo ? j : hi + (j - lo);
+        *reinterpret_cast<uint4*>((l1 ? sH1 : sH2) + rg * (l1 ? sbo1 : sbo2) + 16 * col) = make_uint4(0, 0, 0, 0);
+      }
+    }
     ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles visible; one verdict
     if (!ok) break;
     if (t == 0 && g + 1 < P.n_groups) {  // the next group's data, while this group runs
