@@ -36,9 +36,12 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from ncu captures of
-# the same kernels on the same workload (see profiles/); None if not captured
-NCU_TRAFFIC = {"sample_tc": 479744, "strips_adj": 5341184, "bwd_fused": 6882816, "reduce": 1035776}
+# dram__bytes_read.sum + dram__bytes_write.sum per whole-batch launch from ncu
+# captures of the same kernels on the same workload (see profiles/); None if not
+# captured.  sample_tc and strips_adj were captured as one instance chunk of the
+# overlapped schedule and are scaled by the 5 instances (each chunk reads its own
+# network and couplings, so the traffic grows in proportion).
+NCU_TRAFFIC = {"sample_tc": 5 * 144640, "strips_adj": 5 * 1121024, "bwd_fused": 6877184, "reduce": 1033728}
 
 
 def args_():
@@ -53,6 +56,9 @@ def args_():
     ap.add_argument("--acc-steps", type=int, default=150, help="training steps before the accuracy estimate")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="six comma-separated ints for Context.set_tuning instead of autotuning "
+                         "(sample tile, strip tile, backward CTAs, adjoint tile, TC group, overlap 2=on 1=off)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -171,7 +177,11 @@ def run_ours(a):
     def timed(mode: int, steps: int, warmup: int, sample_clocks: bool):
         model = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
         model.ctx.reserve(B)
-        tuned = None if a.no_autotune else model.ctx.autotune(model.betas, B, mode)
+        if a.tuning:
+            tuned = tuple(int(v) for v in a.tuning.split(","))
+            model.ctx.set_tuning(tuned)
+        else:
+            tuned = None if a.no_autotune else model.ctx.autotune(model.betas, B, mode)
         bufs = model.buffers(B)
         dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
         dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
