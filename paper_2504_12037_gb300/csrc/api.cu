@@ -146,6 +146,7 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
   };
   std::vector<char> used(in.m, 0);
   HostStripPlan plan;
+  plan.edge_sign.assign(in.m, 1.f);
   int tab = 0;
   for (int x = 0; x < Lx;) {
     if (colW[x]) {
@@ -163,6 +164,12 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
     sd.row0 = (int)plan.rows.size();
     sd.tab_off = tab;
     double chat = 0;
+    // Gauge: spin (y, c) of the strip is replaced by tau_c(y) * spin with
+    // tau_c(0) = 1 and tau_c(y+1) = tau_c(y) * sign(Jv(y, c)), which makes every
+    // vertical bond ferromagnetic (its normalised factor is [[1, t], [t, 1]]) and
+    // leaves Z_strip unchanged; the other couplings of the row take the signs.
+    float tau[TNVAN_MAX_STRIP_W];
+    for (int c = 0; c < TNVAN_MAX_STRIP_W; ++c) tau[c] = 1.f;
     for (int y = 0; y < Ly; ++y) {
       StripRow R{};
       for (int c = 0; c < TNVAN_MAX_STRIP_W - 1; ++c) R.eh[c] = -1;
@@ -172,7 +179,8 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
       for (int c = 0; c + 1 < w; ++c) {
         int e = eid(y * Lx + x0 + c, y * Lx + x0 + c + 1);
         if (e >= 0) {
-          R.Jh[c] = (float)in.J[e];
+          R.Jh[c] = (float)in.J[e] * tau[c] * tau[c + 1];
+          plan.edge_sign[e] = tau[c] * tau[c + 1];
           R.eh[c] = e;
           used[e] = 1;
           chat += fabs((double)R.Jh[c]);
@@ -181,7 +189,8 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
       if (x0 > 0) {
         int e = eid(y * Lx + x0 - 1, y * Lx + x0);
         if (e >= 0) {
-          R.JL = (float)in.J[e];
+          R.JL = (float)in.J[e] * tau[0];
+          plan.edge_sign[e] = tau[0];
           R.posL = pos[y * Lx + x0 - 1];
           R.eL = e;
           used[e] = 1;
@@ -191,7 +200,8 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
       if (x0 + w < Lx) {
         int e = eid(y * Lx + x0 + w - 1, y * Lx + x0 + w);
         if (e >= 0) {
-          R.JR = (float)in.J[e];
+          R.JR = (float)in.J[e] * tau[w - 1];
+          plan.edge_sign[e] = tau[w - 1];
           R.posR = pos[y * Lx + x0 + w];
           R.eR = e;
           used[e] = 1;
@@ -202,7 +212,10 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
         for (int c = 0; c < w; ++c) {
           int e = eid(y * Lx + x0 + c, (y + 1) * Lx + x0 + c);
           if (e >= 0) {
-            R.Jv[c] = (float)in.J[e];
+            const float sg = in.J[e] < 0 ? -1.f : 1.f;
+            R.Jv[c] = (float)fabs(in.J[e]);
+            plan.edge_sign[e] = sg;
+            tau[c] *= sg;
             R.ev[c] = e;
             used[e] = 1;
             chat += fabs((double)R.Jv[c]);
@@ -263,10 +276,13 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
   if (in.kind == 0) {
     StripDev* ds = nullptr;
     StripRow* dr = nullptr;
+    float* dsg = nullptr;
     if ((rc = upload(ctx, in, in.strip.strips, &ds))) return rc;
     if ((rc = upload(ctx, in, in.strip.rows, &dr))) return rc;
+    if ((rc = upload(ctx, in, in.strip.edge_sign, &dsg))) return rc;
     in.dev.strips = ds;
     in.dev.rows = dr;
+    in.dev.edge_sign = dsg;
     in.dev.n_strips = (int)in.strip.strips.size();
   } else if (in.kind == 1) {
     float *jrw = nullptr, *jrr = nullptr;

@@ -148,6 +148,7 @@ struct InstDev {
   int n_strips;
   const StripDev* strips;
   const StripRow* rows;
+  const float* edge_sign;  // gauge sign per edge (see HostStripPlan)
   int strip_tab_floats;  // shared-memory floats for all strip tables
   // dense
   DenseDev dense;
@@ -174,6 +175,10 @@ struct LaunchInfo {
 struct HostStripPlan {
   std::vector<StripDev> strips;
   std::vector<StripRow> rows;
+  // Per edge, the gauge sign that maps an expectation of the strip rows (all
+  // vertical bonds made ferromagnetic by flipping spins) back to the model's
+  // variables: tau_i tau_j for R-R bonds, tau_r for R-W bonds, 1 for W-W.
+  std::vector<float> edge_sign;
 };
 
 struct Instance {

@@ -9,13 +9,18 @@
 // V_y is the Kronecker product of the w vertical 2x2 Boltzmann matrices
 // B(+,+) = B(-,-) = e^{beta J}, B(+,-) = e^{-beta J} (Eq. 2).  Each factor is
 // stored normalised (largest entry 1) and the removed constant
-// beta * c_hat is added back in FP64 at the end.
+// beta * c_hat is added back in FP64 at the end.  The planner hands over the
+// strip in a gauge where every vertical coupling is >= 0 (spins flipped
+// column by column, the horizontal and W-neighbour couplings carrying the
+// signs), so every normalised vertical factor is [[1, t], [t, 1]] with
+// t = e^{-2 beta |J|}; bond expectations come back to the model's spins
+// through the per-edge sign (I.edge_sign).
 #include "common.cuh"
 
 namespace tnvan {
 
 // Per-strip table layout in shared memory (floats, offset tab_off):
-//   vert  [L][w] float4 (a, b, da/dbeta, db/dbeta): 2x2 factor [[a,b],[b,a]]
+//   vert  [L][w] float4 (1, t, 0, dt/dbeta): 2x2 factor [[1,t],[t,1]]
 //   diag  [L][4][2^w]   D_y for the 4 combinations of (s_L, s_R) signs
 //   ddiag [L][4][2^w]   d D_y / d beta
 //   pos   [L][2] int    AR positions of the left / right W neighbours (-1 none)
@@ -92,10 +97,10 @@ __device__ void build_strip_tables(const InstDev& I, float beta, float* sm, int 
     }
     for (int e = t; e < L * w; e += T) {
       const int y = e / w, c = e % w;
-      const float J = rows[y].Jv[c], aj = fabsf(J);
+      const float aj = rows[y].Jv[c];  // >= 0 in the planner's gauge
       const float tt = (y + 1 < L) ? expf(-2.f * beta * aj) : 1.f;
       const float dt = -2.f * aj * tt;
-      vert[e] = J >= 0.f ? make_float4(1.f, tt, 0.f, dt) : make_float4(tt, 1.f, dt, 0.f);
+      vert[e] = make_float4(1.f, tt, 0.f, dt);
     }
     for (int y = t; y < L; y += T) {
       pos[2 * y] = rows[y].posL;
@@ -104,7 +109,8 @@ __device__ void build_strip_tables(const InstDev& I, float beta, float* sm, int 
   }
 }
 
-// Apply [[a,b],[b,a]] on bit c of the state index (and its beta-derivative).
+// Apply [[1,t],[t,1]] (t = q.y) on bit c of the state index, and its
+// beta-derivative (dt/dbeta = q.w).
 template <int W, bool DB>
 __device__ __forceinline__ void apply_pair(float (&v)[1 << W], float (&g)[1 << W], int c, float4 q) {
 #pragma unroll
@@ -114,11 +120,11 @@ __device__ __forceinline__ void apply_pair(float (&v)[1 << W], float (&g)[1 << W
     const float v0 = v[x], v1 = v[x1];
     if (DB) {
       const float g0 = g[x], g1 = g[x1];
-      g[x] = fmaf(q.x, g0, fmaf(q.y, g1, fmaf(q.z, v0, q.w * v1)));
-      g[x1] = fmaf(q.y, g0, fmaf(q.x, g1, fmaf(q.w, v0, q.z * v1)));
+      g[x] = fmaf(q.y, g1, fmaf(q.w, v1, g0));
+      g[x1] = fmaf(q.y, g0, fmaf(q.w, v0, g1));
     }
-    v[x] = fmaf(q.x, v0, q.y * v1);
-    v[x1] = fmaf(q.y, v0, q.x * v1);
+    v[x] = fmaf(q.y, v1, v0);
+    v[x1] = fmaf(q.y, v0, v1);
   }
 }
 
@@ -325,9 +331,11 @@ __device__ __forceinline__ int row_edge(const StripRow& R, int W, int j) {
 //
 // Row y, with left vector l (rows 0..y, D_y included) and right vector
 // r = r_{y+1}: the message m = V_y r, P = l * m, Z = sum P.  For the vertical
-// bond of column c, with L_c = V_0..V_{c-1} l and R_c = V_{c+1}..V_{W-1} r,
-//   Z <s_c s'_c> = L_c^T V'_c R_c,  V'_c = [[a, -b], [-b, a]] on bit c,
-// so the W vertical bonds share 2W - 1 Kronecker-factor applications.
+// bond of column c, with L_c = V_0..V_{c-1} l and R_c = V_{c+1}..V_{W-1} r and
+// the factor on bit c being I + t X,
+//   Z = L_c^T R_c + t L_c^T X R_c,  Z <s_c s'_c> = L_c^T R_c - t L_c^T X R_c,
+// so Z <s_c s'_c> = 2 L_c^T R_c - Z, and the W vertical bonds share 2W - 1
+// Kronecker-factor applications and one dot product each.
 template <int W>
 __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict__ rows, int L,
                                  const int8_t* srow, const float* lvs, int t, int T, bool valid,
@@ -382,13 +390,10 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         if (c > 0) apply_pair<W, false>(Lc, dummy, c - 1, q[c - 1]);
-        float d0 = 0.f, d1 = 0.f;
+        float d0 = 0.f;
 #pragma unroll
-        for (int x = 0; x < NX; ++x) {
-          d0 = fmaf(Lc[x], Rc[c][x], d0);
-          d1 = fmaf(Lc[x], Rc[c][x ^ (1 << c)], d1);
-        }
-        val[W + 1 + c] = fmaf(q[c].x, d0, -q[c].y * d1);
+        for (int x = 0; x < NX; ++x) d0 = fmaf(Lc[x], Rc[c][x], d0);
+        val[W + 1 + c] = fmaf(2.f, d0, -Z);
       }
     }
     float P[NX];
@@ -661,7 +666,7 @@ __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const 
   double s = 0.0;
   for (int c = li.tile_begin[k] + lane; c < li.tile_begin[k + 1]; c += 32) s += (double)part[(long long)c * part_stride + e];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) dJ[I.edge_off + e] += s;
+  if (lane == 0) dJ[I.edge_off + e] += (double)I.edge_sign[e] * s;
 }
 
 int strip_adj_lv_floats(const Instance& in, int tile) {
