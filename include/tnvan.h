@@ -212,6 +212,28 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
                float* d_v, double lr, double beta1, double beta2, double eps, int64_t t,
                void* stream);
 
+/* One whole iteration of Algorithm 1 (a)-(d) in one call, asynchronous on
+ * `stream`: tnvan_sample_contract_adjoint (tnvan_sample_and_contract when
+ * d_dbeta and d_dJ are both NULL), the REINFORCE gradient of tnvan_backward
+ * (Eq. 10) into d_grad_params, and Adam on every instance's own parameters
+ * (the d_params pointers given to tnvan_set_made, which this call updates in
+ * place).  Equal to those calls in sequence, with tnvan_adam run over the
+ * packed gradient layout; here the network is packed once for the whole
+ * step and the gradient reduction and Adam are one kernel.
+ *   d_spins, d_logq, d_logZR, d_dbeta, d_dJ   as tnvan_sample_contract_adjoint.
+ *   d_grad_params   device float [total params] out, layout of tnvan_n_params.
+ *   d_m, d_v        device float [total params] Adam moments in that layout
+ *                   (in/out).
+ *   lr, beta1, beta2, eps, t   as tnvan_adam (t >= 1); with a step counter
+ *                   (tnvan_set_step_counter) the Philox step is step +
+ *                   *d_counter and Adam's step t + *d_counter.
+ * Errors: TNVAN_E_ARG (batch < 1, NULL pointer, bad Adam arguments),
+ * TNVAN_E_STATE, TNVAN_E_UNSUPPORTED, TNVAN_E_CUDA. */
+int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
+                     int precision, int8_t* d_spins, float* d_logq, double* d_logZR, double* d_dbeta,
+                     double* d_dJ, float* d_grad_params, float* d_m, float* d_v, double lr,
+                     double beta1, double beta2, double eps, int64_t t, void* stream);
+
 /* Autotuner (not in the paper): times candidate launch shapes on a batch of
  * `batch` samples drawn from the current networks -- the SIMT sampler's
  * samples per CTA, the strip contraction's samples per CTA, the number of

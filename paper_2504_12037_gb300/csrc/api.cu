@@ -222,6 +222,22 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
           }
         }
       }
+      for (int j = 0; j < TNVAN_STRIP_SLOTS; ++j) {
+        R.Js[j] = 0.f;
+        R.es[j] = -1;
+      }
+      for (int c = 0; c + 1 < w; ++c) {
+        R.Js[c] = R.Jh[c];
+        R.es[c] = R.eh[c];
+      }
+      R.Js[w - 1] = R.JL;
+      R.es[w - 1] = R.eL;
+      R.Js[w] = R.JR;
+      R.es[w] = R.eR;
+      for (int c = 0; c < w; ++c) {
+        R.Js[w + 1 + c] = R.Jv[c];
+        R.es[w + 1 + c] = R.ev[c];
+      }
       plan.rows.push_back(R);
     }
     sd.c_hat = chat;
@@ -497,6 +513,15 @@ int sampler_pack_mask(const tnvan_ctx* ctx, int precision);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s);
 int pick_tc_plan(const tnvan_ctx* ctx);
+int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, const double* d_logZR,
+                  const float* d_logq, int precision, float* d_grad_params, double* d_dbeta, double* d_dJ,
+                  cudaStream_t s, bool pack, const AdamArgs* adam, bool stats_ready = false);
+AdamArgs adam_args(const tnvan_ctx* ctx, float* d_m, float* d_v, double lr, double beta1, double beta2, double eps,
+                   int64_t t);
+int sample_contract_adjoint_impl(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
+                                 int precision, int8_t* d_spins, float* d_logq, double* d_logZR, double* d_dbeta,
+                                 double* d_dJ, cudaStream_t s, bool* dj_deferred = nullptr,
+                                 bool* stats_done = nullptr);
 
 }  // namespace
 
@@ -749,6 +774,7 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   for (cudaEvent_t e : ctx->chunk_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->dj_ev) cudaEventDestroy(ctx->dj_ev);
   for (cudaEvent_t e : ctx->join_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->d_inst) cudaFree(ctx->d_inst);
@@ -1260,6 +1286,7 @@ static int ensure_side_streams(tnvan_ctx* ctx) {
   for (cudaStream_t& st : ctx->side_lo)
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->dj_ev, cudaEventDisableTiming);
   for (cudaEvent_t& ev : ctx->join_ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   for (cudaEvent_t& ev : ctx->chunk_ev)
@@ -1277,9 +1304,14 @@ static int ensure_side_streams(tnvan_ctx* ctx) {
 // sampler's tail.  The caller's stream forks to the side streams and joins
 // them again, so stream order (and CUDA graph capture) behave as for one
 // launch.
+// With defer_dj the d/dJ reduction runs on a side stream (beside whatever the
+// caller queues next) and the caller waits on ctx->dj_ev before it is done;
+// with chunk_stats each chunk's F_q reduction (tnvan_backward's first kernel)
+// follows its adjoint on the chunk's stream.
 static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
                                      int plan, int8_t* d_spins, float* d_logq, double* d_logZR,
-                                     double* d_dbeta, double* d_dJ, cudaStream_t s) {
+                                     double* d_dbeta, double* d_dJ, cudaStream_t s, bool defer_dj,
+                                     bool chunk_stats) {
   int rc;
   int adj_tile = 0, adj_smem = 0, adj_lv = 0, adj_ws = 0;
   if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv, &adj_ws))) return rc;
@@ -1297,11 +1329,8 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
   const int stride = (max_edges + 3) & ~3;
   if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
   if ((rc = ensure_side_streams(ctx))) return rc;
-  if (d_dJ) {
-    long long ne = 0;
-    for (const Instance& in : ctx->inst) ne += in.m;
-    CK(cudaMemsetAsync(d_dJ, 0, ne * sizeof(double), s), "dJ memset");
-  }
+  LaunchInfo lr;
+  if (chunk_stats && (rc = fill_launch(ctx, betas, batch, 1, lr))) return rc;
   const int n = li.n_inst, nc = std::min(n, 8);
   CK(cudaEventRecord(ctx->fork_ev, s), "fork");
   for (int c = 0; c < nc; ++c) CK(cudaStreamWaitEvent(ctx->side[c], ctx->fork_ev, 0), "fork wait");
@@ -1320,14 +1349,27 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
                          d_dJ ? ctx->d_dj_part : nullptr, stride, nullptr, ctx->side_lo[c], la.tile_begin[k0],
                          la.tile_begin[k1], adj_ws),
        "strip adjoint kernel");
+    if (chunk_stats) {
+      PROF("reduce", ctx->side_lo[c]);
+      CK(launch_reduce(ctx->d_inst, lr, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, ctx->side_lo[c], k0, k1),
+         "reduce kernels");
+    }
   }
   for (int c = 0; c < nc; ++c) {
     CK(cudaEventRecord(ctx->join_ev[c], ctx->side_lo[c]), "join");
     CK(cudaStreamWaitEvent(s, ctx->join_ev[c], 0), "join wait");
   }
-  if (d_dJ) {
-    PROF("strips_dJ_reduce", s);
-    CK(launch_strips_dJ_reduce(ctx->d_inst, la, ctx->d_dj_part, stride, d_dJ, s), "d/dJ reduce");
+  if (d_dJ) {  // every edge's sum overwrites d_dJ: no clearing pass
+    cudaStream_t sr = s;
+    if (defer_dj) {
+      sr = ctx->side_lo[0];
+      for (int c = 1; c < nc; ++c) CK(cudaStreamWaitEvent(sr, ctx->join_ev[c], 0), "join wait");
+    }
+    {
+      PROF("strips_dJ_reduce", sr);
+      CK(launch_strips_dJ_reduce(ctx->d_inst, la, ctx->d_dj_part, stride, d_dJ, sr, true), "d/dJ reduce");
+    }
+    if (defer_dj) CK(cudaEventRecord(ctx->dj_ev, sr), "d/dJ event");
   }
   return TNVAN_OK;
 }
@@ -1347,16 +1389,82 @@ int tnvan_sample_contract_adjoint(tnvan_ctx* ctx, const double* betas, int batch
   if (batch == 0) return TNVAN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision), s))) return rc;
+  return sample_contract_adjoint_impl(ctx, betas, batch, seed, step, precision, d_spins, d_logq, d_logZR, d_dbeta,
+                                      d_dJ, s);
+}
+
+int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
+                     int8_t* d_spins, float* d_logq, double* d_logZR, double* d_dbeta, double* d_dJ,
+                     float* d_grad_params, float* d_m, float* d_v, double lr, double beta1, double beta2,
+                     double eps, int64_t t, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
+  if (!d_spins || !d_logq || !d_logZR || !d_grad_params || !d_m || !d_v)
+    return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  if (t < 1 || !(beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps >= 0))
+    return fail(ctx, TNVAN_E_ARG, "bad Adam arguments");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // one pack serves the sampler and the backward (the parameters change only
+  // in the last kernel of the step)
+  bool all_fused = precision == TNVAN_BF16;
+  for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
+  if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision) | PACK_FLAT | (all_fused ? PACK_TILES : 0), s)))
+    return rc;
+  // the overlapped schedule runs each chunk's F_q reduction behind its
+  // adjoint, and the d/dJ reduction (it reads only the adjoint's partial
+  // rows) beside the backward; the step ends after both
+  bool dj_deferred = false, stats_done = false;
+  if (d_dbeta || d_dJ)
+    rc = sample_contract_adjoint_impl(ctx, betas, batch, seed, step, precision, d_spins, d_logq, d_logZR, d_dbeta,
+                                      d_dJ, s, &dj_deferred, &stats_done);
+  else if (!(rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s)))
+    rc = contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
+  if (rc) return rc;
+  const AdamArgs a = adam_args(ctx, d_m, d_v, lr, beta1, beta2, eps, t);
+  rc = backward_impl(ctx, betas, batch, d_spins, d_logZR, d_logq, precision, d_grad_params, nullptr, nullptr, s,
+                     false, &a, stats_done);
+  if (dj_deferred) CK(cudaStreamWaitEvent(s, ctx->dj_ev, 0), "d/dJ join");
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Sampling, then the contraction with its adjoint (overlapped on side
+// streams where every instance is a strip instance and the tensor-core
+// sampler runs), on a network the caller has packed.
+int sample_contract_adjoint_impl(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
+                                 int precision, int8_t* d_spins, float* d_logq, double* d_logZR, double* d_dbeta,
+                                 double* d_dJ, cudaStream_t s, bool* dj_deferred, bool* stats_done) {
+  int rc;
+  if (dj_deferred) *dj_deferred = false;
+  if (stats_done) *stats_done = false;
   bool strips_only = ctx->inst.size() >= 2;
   for (const Instance& in : ctx->inst) strips_only = strips_only && in.kind == 0;
   bool tc_all = precision == TNVAN_BF16;
   for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
   const int plan = tc_all ? pick_tc_plan(ctx) : -1;
-  if (strips_only && plan >= 0 && ctx->tune_overlap)
-    return sample_adjoint_overlapped(ctx, betas, batch, seed, step, plan, d_spins, d_logq, d_logZR, d_dbeta, d_dJ, s);
+  if (strips_only && plan >= 0 && ctx->tune_overlap) {
+    const bool defer = dj_deferred && d_dJ;
+    if ((rc = sample_adjoint_overlapped(ctx, betas, batch, seed, step, plan, d_spins, d_logq, d_logZR, d_dbeta, d_dJ,
+                                        s, defer, stats_done != nullptr)))
+      return rc;
+    if (defer) *dj_deferred = true;
+    if (stats_done) *stats_done = true;
+    return TNVAN_OK;
+  }
   if ((rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s))) return rc;
   return run_adjoint(ctx, betas, batch, d_spins, precision, d_logZR, d_dbeta, d_dJ, s);
 }
+
+}  // namespace
+
+extern "C" {
 
 int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precision, float* d_logq,
                    void* stream) {
@@ -1432,15 +1540,30 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
   DeviceGuard g(ctx->device);
   int rc = check_ready(ctx, true);
   if (rc) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return backward_impl(ctx, betas, batch, d_spins, d_logZR, d_logq, precision, d_grad_params, d_dbeta, d_dJ,
+                       static_cast<cudaStream_t>(stream), true, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Eq. 10 and (optionally) the contraction adjoint, after argument checks:
+// with `pack` false the caller has packed the network for this call; with
+// `adam` the gradient reduction also takes Adam's step on every instance's
+// parameters.
+int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, const double* d_logZR,
+                  const float* d_logq, int precision, float* d_grad_params, double* d_dbeta, double* d_dJ,
+                  cudaStream_t s, bool pack, const AdamArgs* adam, bool stats_ready) {
+  int rc;
   long long max_elems = 0;
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
   bool all_fused = precision == TNVAN_BF16;
   for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
-  if ((rc = pack_network(ctx, PACK_FLAT | (all_fused ? PACK_TILES : 0), s))) return rc;
-  {
+  if (pack && (rc = pack_network(ctx, PACK_FLAT | (all_fused ? PACK_TILES : 0), s))) return rc;
+  if (!stats_ready) {
     PROF("reduce", s);
     CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernels");
   }
@@ -1466,7 +1589,7 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     }
     {
       PROF("grad_reduce", s);
-      CK(launch_grad_reduce(ctx->d_inst, lf, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+      CK(launch_grad_reduce(ctx->d_inst, lf, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam, true),
          "gradient reduce kernel");
     }
   } else if (precision != TNVAN_FP32) {
@@ -1480,7 +1603,7 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     for (int k = 0; k <= lr.n_inst; ++k) lr.tile_begin[k] = k * splits;
     {
       PROF("grad_reduce", s);
-      CK(launch_grad_reduce(ctx->d_inst, lr, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+      CK(launch_grad_reduce(ctx->d_inst, lr, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam),
          "gradient reduce kernel");
     }
   }
@@ -1500,13 +1623,33 @@ int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
     }
     {
       PROF("grad_reduce", s);
-      CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s),
+      CK(launch_grad_reduce(ctx->d_inst, lb, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam),
          "gradient reduce kernel");
     }
   }
   if (d_dbeta || d_dJ) return run_adjoint(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, d_dJ, s);
   return TNVAN_OK;
 }
+
+AdamArgs adam_args(const tnvan_ctx* ctx, float* d_m, float* d_v, double lr, double beta1, double beta2, double eps,
+                   int64_t t) {
+  AdamArgs a;
+  a.m = d_m;
+  a.v = d_v;
+  a.lr = (float)lr;
+  a.b1 = (float)beta1;
+  a.b2 = (float)beta2;
+  a.eps = (float)eps;
+  a.bc1 = (float)(1.0 - pow(beta1, (double)t));
+  a.bc2 = (float)(1.0 - pow(beta2, (double)t));
+  a.t_dev = ctx->step_dev;
+  a.t_base = (long long)t;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
 
 int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, float* d_m,
                float* d_v, double lr, double beta1, double beta2, double eps, int64_t t,
@@ -1517,11 +1660,9 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
   if (!(beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps >= 0))
     return fail(ctx, TNVAN_E_ARG, "bad Adam hyper-parameters");
   DeviceGuard g(ctx->device);
-  const double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+  const AdamArgs a = adam_args(ctx, d_m, d_v, lr, beta1, beta2, eps, t);
   PROF("adam", static_cast<cudaStream_t>(stream));
-  CK(launch_adam(n, d_params, d_grad, d_m, d_v, (float)lr, (float)beta1, (float)beta2, (float)eps,
-                 (float)bc1, (float)bc2, static_cast<cudaStream_t>(stream), ctx->step_dev, (long long)t),
-     "adam kernel");
+  CK(launch_adam(n, d_params, d_grad, a, static_cast<cudaStream_t>(stream)), "adam kernel");
   return TNVAN_OK;
 }
 

@@ -44,7 +44,7 @@ struct MadeDev {
   int D, nh, H1, H2, Hl;  // Hl = width feeding the output layer (D if nh == 0)
   int n_layers;
   LayerDev layer[3];
-  const float* raw;       // borrowed natural-layout parameters
+  float* raw;             // borrowed natural-layout parameters (written only by the fused Adam step)
   float* packed;          // packed, masked, degree-sorted copy (W then b per layer)
   const int* c1;          // [D+1] number of layer-1 units with degree <= d
   const int* c2;          // [D+1] number of layer-2 units with degree <= d
@@ -80,8 +80,13 @@ struct MadeDev {
 
 // Lattice strip: w whole columns x0..x0+w-1, L rows.  Row y has horizontal
 // bonds Jh[c] (c, c+1), left/right W neighbours at AR positions posL/posR
-// (-1 = none), and vertical bonds Jv[c] to row y+1.
-struct StripRow {
+// (-1 = none), and vertical bonds Jv[c] to row y+1.  The same bonds by slot
+// (w-1 horizontal, left, right, w vertical), as the adjoint reads them: Js the
+// coupling (0 = no bond), es the edge id (-1 = none).
+#define TNVAN_STRIP_SLOTS 12  // >= 2 * TNVAN_MAX_STRIP_W + 1, a multiple of 4
+struct alignas(16) StripRow {
+  float Js[TNVAN_STRIP_SLOTS];
+  int es[TNVAN_STRIP_SLOTS];
   float Jh[TNVAN_MAX_STRIP_W - 1];
   float JL, JR;
   int posL, posR;
@@ -235,7 +240,7 @@ struct tnvan_ctx {
   // side streams and events of the overlapped sampling + adjoint schedule
   cudaStream_t side[8] = {};  // samplers (highest stream priority)
   cudaStream_t side_lo[8] = {};  // adjoints (default priority)
-  cudaEvent_t fork_ev = nullptr, join_ev[8] = {}, chunk_ev[8] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[8] = {}, chunk_ev[8] = {}, dj_ev = nullptr;
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
@@ -270,7 +275,7 @@ cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int s
                               const int8_t* spins, double* logZR, double* dbeta, float* part, int part_stride,
                               double* dJ, cudaStream_t s, int blk_begin = 0, int blk_end = -1, int ws_threads = 0);
 cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* part, int part_stride,
-                                    double* dJ, cudaStream_t s);
+                                    double* dJ, cudaStream_t s, bool assign);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s);
@@ -283,15 +288,30 @@ cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int s
 int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);
+// Instances [k0, k1) (k1 < 0: all) of the launch.
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
-                          const float* logq, double* stats, int* counters, cudaStream_t s);
+                          const float* logq, double* stats, int* counters, cudaStream_t s, int k0 = 0,
+                          int k1 = -1);
 cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                             int precision, const int8_t* spins, const double* logZR,
                             const float* logq, const double* stats, float* partials,
                             int part_stride, cudaStream_t s);
+// Adam's state and hyper-parameters for one launch (moments in the packed
+// all-instances gradient layout).  With t_dev the step is t_base + *t_dev and
+// bc1/bc2 are formed on the device.
+struct AdamArgs {
+  float* m;
+  float* v;
+  float lr, b1, b2, eps, bc1, bc2;
+  const unsigned long long* t_dev;
+  long long t_base;
+};
+// With adam non-NULL the reduction also applies Adam to every instance's own
+// parameters (the fused optimizer step of tnvan_train_step); cols: the
+// partials are in the fused backward's column-major layer blocks.
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                const float* partials, int part_stride, float* grad,
-                               cudaStream_t s);
+                               cudaStream_t s, const AdamArgs* adam = nullptr, bool cols = false);
 cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
                                const double* stats, float* w, cudaStream_t s);
 cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
@@ -303,9 +323,7 @@ cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int pl
                              float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
 int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
-cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
-                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s,
-                        const unsigned long long* t_dev = nullptr, long long t_base = 0);
+cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 
 int sample_smem_bytes(const Instance& in, int tile);
 int general_smem_bytes(int arena, int pairs, int D, int T, bool db);

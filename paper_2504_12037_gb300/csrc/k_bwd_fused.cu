@@ -317,39 +317,25 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   }
   if (!ok && tid == 0) atomicExch(args.status, 3);
   // ---- flush the gradient partials of this CTA ----
+  // Each layer's [nout x (nin + 1)] accumulator (TMEM lane = output unit,
+  // column = input, the last column the bias) goes out column-major, entry
+  // (o, i) at dst_off + i * nout + o, so a warp's 32 lanes store 32
+  // consecutive floats per column.
   float* G = args.partials + (long long)blockIdx.x * args.part_stride;
   if (ok && !first) {
-    // GW1 rows u (lane t < H1): [D weights | bias]
-    for (int c = 16 * g; c < D + 16; c += 32) {
-      float v[16];
-      tc::tmem_ld16(tG1 + lane_off + (uint32_t)c, v);
-      if (t < H1)
-        for (int i = 0; i < 16; ++i) {
-          const int j = c + i;
-          if (j < D) G[md.layer[0].dst_off + (long long)t * D + j] = v[i];
-          else if (j == D) G[md.layer[0].dst_off + (long long)H1 * D + t] = v[i];
-        }
-    }
-    for (int c = 16 * g; c < H1 + 16; c += 32) {
-      float v[16];
-      tc::tmem_ld16(tG2 + lane_off + (uint32_t)c, v);
-      if (t < H2)
-        for (int i = 0; i < 16; ++i) {
-          const int u = c + i;
-          if (u < H1) G[md.layer[1].dst_off + (long long)t * H1 + u] = v[i];
-          else if (u == H1) G[md.layer[1].dst_off + (long long)H2 * H1 + t] = v[i];
-        }
-    }
-    for (int c = 16 * g; c < H2 + 16; c += 32) {
-      float v[16];
-      tc::tmem_ld16(tGo + lane_off + (uint32_t)c, v);
-      if (t < D)
-        for (int i = 0; i < 16; ++i) {
-          const int u = c + i;
-          if (u < H2) G[md.layer[2].dst_off + (long long)t * H2 + u] = v[i];
-          else if (u == H2) G[md.layer[2].dst_off + (long long)D * H2 + t] = v[i];
-        }
-    }
+    auto flush = [&](uint32_t tacc, int nin, int nout, long long off) {
+      for (int c = 16 * g; c < nin + 16; c += 32) {
+        float v[16];
+        tc::tmem_ld16(tacc + lane_off + (uint32_t)c, v);
+        if (t < nout)
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c + i <= nin) G[off + (long long)(c + i) * nout + t] = v[i];
+      }
+    };
+    flush(tG1, D, H1, md.layer[0].dst_off);
+    flush(tG2, H1, H2, md.layer[1].dst_off);
+    flush(tGo, H2, D, md.layer[2].dst_off);
   } else {
     for (long long e = tid; e < md.n_params; e += 256) G[e] = 0.f;
   }

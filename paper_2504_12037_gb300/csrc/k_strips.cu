@@ -322,6 +322,17 @@ __device__ __forceinline__ int row_edge(const StripRow& R, int W, int j) {
   return R.ev[j - W - 1];
 }
 
+// Bond slot whose warp total this lane holds after warp_transpose_sum<NV>
+// (a function of the lane only).
+template <int NV>
+__device__ __forceinline__ int transpose_slot(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int h = NV / 2, m = 16; h >= 1; h >>= 1, m >>= 1)
+    if (lane & m) idx += h;
+  return idx;
+}
+
 // Backward sweep of one strip for one sample (all 32 lanes of the warp take
 // part; `valid` zeroes the contribution of padding samples).  Adds each
 // bond's local expectation to the warp's accumulators and returns
@@ -330,16 +341,18 @@ __device__ __forceinline__ int row_edge(const StripRow& R, int W, int j) {
 // derivative.
 //
 // Row y, with left vector l (rows 0..y, D_y included) and right vector
-// r = r_{y+1}: the message m = V_y r, P = l * m, Z = sum P.  For the vertical
-// bond of column c, with L_c = V_0..V_{c-1} l and R_c = V_{c+1}..V_{W-1} r and
-// the factor on bit c being I + t X,
+// r = r_{y+1}: the message m = V_y r, P = l * m, Z = sum P; the horizontal
+// and W-neighbour bonds are signed sums of P.  For the vertical bond of
+// column c, with L_c = V_0..V_{c-1} l and R_c = V_{c+1}..V_{W-1} r and the
+// factor on bit c being I + t X,
 //   Z = L_c^T R_c + t L_c^T X R_c,  Z <s_c s'_c> = L_c^T R_c - t L_c^T X R_c,
 // so Z <s_c s'_c> = 2 L_c^T R_c - Z, and the W vertical bonds share 2W - 1
-// Kronecker-factor applications and one dot product each.
+// Kronecker-factor applications and one dot product each.  The row's bonds
+// are read by slot (StripRow::Js, es), absent bonds carrying J = 0.
 template <int W>
 __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict__ rows, int L,
-                                 const int8_t* srow, const float* lvs, int t, int T, bool valid,
-                                 float* accw, int lane) {
+                                 const int8_t* srow, const float* lvs, int t, int T, bool valid, float* accw,
+                                 int lane) {
   constexpr int NX = 1 << W;
   constexpr int NB = 2 * W + 1;
   constexpr int NV = NB <= 4 ? 4 : (NB <= 8 ? 8 : 16);
@@ -347,28 +360,31 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
   const float* diag = tb.diag;
   const int* pos = tb.pos;
   const bool own = (lane & (32 / NV - 1)) == 0;
+  const int slot = transpose_slot<NV>(lane);
+  const bool has_slot = own && slot < NB;
   float r[NX];  // r_{y+1}, renormalised
   float dlog = 0.f;
   for (int y = L - 1; y >= 0; --y) {
-    const StripRow& R = rows[y];
+    float Js[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) Js[j] = rows[y].Js[j];
+    const int ecur = has_slot ? rows[y].es[slot] : -1;
+    const int idx = row_index(pos, y, srow);
     float lv[NX], msg[NX], dummy[NX];
 #pragma unroll
     for (int x = 0; x < NX; ++x) lv[x] = lvs[(y * NX + x) * T + t];
     float val[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) val[j] = 0.f;
-    float Z = 0.f;
+    float d0[W];  // L_c^T R_c of the vertical bonds
     if (y == L - 1) {
 #pragma unroll
-      for (int x = 0; x < NX; ++x) {
-        msg[x] = 1.f;
-        Z += lv[x];
-      }
+      for (int x = 0; x < NX; ++x) msg[x] = 1.f;
     } else {
       float4 q[W];
 #pragma unroll
       for (int c = 0; c < W; ++c) q[c] = vert[y * W + c];
-      // suffix products R_c (R_{W-1} = r), kept for the vertical bonds
+      // suffix products R_c (R_{W-1} = r)
       float Rc[W][NX];
 #pragma unroll
       for (int x = 0; x < NX; ++x) Rc[W - 1][x] = r[x];
@@ -381,8 +397,6 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
 #pragma unroll
       for (int x = 0; x < NX; ++x) msg[x] = Rc[0][x];
       apply_pair<W, false>(msg, dummy, 0, q[0]);
-#pragma unroll
-      for (int x = 0; x < NX; ++x) Z += lv[x] * msg[x];
       // prefix products L_c (L_0 = l)
       float Lc[NX];
 #pragma unroll
@@ -390,16 +404,19 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         if (c > 0) apply_pair<W, false>(Lc, dummy, c - 1, q[c - 1]);
-        float d0 = 0.f;
+        float d = 0.f;
 #pragma unroll
-        for (int x = 0; x < NX; ++x) d0 = fmaf(Lc[x], Rc[c][x], d0);
-        val[W + 1 + c] = fmaf(2.f, d0, -Z);
+        for (int x = 0; x < NX; ++x) d = fmaf(Lc[x], Rc[c][x], d);
+        d0[c] = d;
       }
     }
     float P[NX];
+    float Z = 0.f;
 #pragma unroll
-    for (int x = 0; x < NX; ++x) P[x] = lv[x] * msg[x];
-    const float iz = 1.f / Z;
+    for (int x = 0; x < NX; ++x) {
+      P[x] = lv[x] * msg[x];
+      Z = fmaf(lv[x], msg[x], Z);
+    }
 #pragma unroll
     for (int c = 0; c + 1 < W; ++c) {
       float a = 0.f;
@@ -407,41 +424,35 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
       for (int x = 0; x < NX; ++x) a += P[x] * spin_of(x, c) * spin_of(x, c + 1);
       val[c] = a;
     }
-    const int pL = pos[2 * y], pR = pos[2 * y + 1];
-    if (pL >= 0) {
-      float a = 0.f;
+    {
+      float a = 0.f, b = 0.f;
 #pragma unroll
-      for (int x = 0; x < NX; ++x) a += P[x] * spin_of(x, 0);
-      val[W - 1] = a * (float)srow[pL];
+      for (int x = 0; x < NX; ++x) {
+        a += P[x] * spin_of(x, 0);
+        b += P[x] * spin_of(x, W - 1);
+      }
+      val[W - 1] = (idx & 1) ? -a : a;  // s_L s_0
+      val[W] = (idx & 2) ? -b : b;      // s_R s_{W-1}
     }
-    if (pR >= 0) {
-      float a = 0.f;
-#pragma unroll
-      for (int x = 0; x < NX; ++x) a += P[x] * spin_of(x, W - 1);
-      val[W] = a * (float)srow[pR];
-    }
-    // expectations, their beta-weighted sum, and the masked values for d/dJ
-    float dJb = 0.f;
-#pragma unroll
-    for (int c = 0; c + 1 < W; ++c) dJb = fmaf(R.Jh[c], val[c], dJb);
-    dJb = fmaf(R.JL, val[W - 1], dJb);
-    dJb = fmaf(R.JR, val[W], dJb);
     if (y + 1 < L) {
 #pragma unroll
-      for (int c = 0; c < W; ++c) dJb = fmaf(R.Jv[c], val[W + 1 + c], dJb);
+      for (int c = 0; c < W; ++c) val[W + 1 + c] = fmaf(2.f, d0[c], -Z);
     }
+    // the beta-weighted sum (absent bonds carry J = 0), then the masked
+    // values for d/dJ
+    const float iz = 1.f / Z;
+    float dJb = 0.f;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) dJb = fmaf(Js[j], val[j], dJb);
     dlog = fmaf(dJb, iz, dlog);
     const float vz = valid ? iz : 0.f;
 #pragma unroll
     for (int j = 0; j < NB; ++j) val[j] *= vz;
     int vi;
     const float sum = warp_transpose_sum<NV>(val, lane, vi);
-    if (own && vi < NB && (vi <= W || y + 1 < L)) {
-      const int e = row_edge(R, W, vi);
-      if (e >= 0) accw[e] += sum;
-    }
+    if (has_slot && ecur >= 0) accw[ecur] += sum;
     // r_y = D_y * msg, renormalised
-    const float* dy = diag + (y * 4 + row_index(pos, y, srow)) * NX;
+    const float* dy = diag + (y * 4 + idx) * NX;
     float m = 0.f;
 #pragma unroll
     for (int x = 0; x < NX; ++x) {
@@ -653,11 +664,13 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
   }
 }
 
-// dJ[edge] += sum over the instance's CTA rows: one warp per edge, lane l
+// dJ[edge] (+)= sum over the instance's CTA rows: one warp per edge, lane l
 // adding rows l, l+32, ... in FP64, then a fixed xor tree (deterministic).
+// With `assign` the sum overwrites dJ (every edge of a strip instance has a
+// column in the rows, W-W bonds included).
 __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                         const float* __restrict__ part, int part_stride,
-                                        double* __restrict__ dJ) {
+                                        double* __restrict__ dJ, bool assign) {
   const int k = blockIdx.y;
   const InstDev& I = inst[k];
   if (I.kind != 0) return;
@@ -666,7 +679,10 @@ __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const 
   double s = 0.0;
   for (int c = li.tile_begin[k] + lane; c < li.tile_begin[k + 1]; c += 32) s += (double)part[(long long)c * part_stride + e];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) dJ[I.edge_off + e] += (double)I.edge_sign[e] * s;
+  if (lane == 0) {
+    const double v = (double)I.edge_sign[e] * s;
+    dJ[I.edge_off + e] = assign ? v : dJ[I.edge_off + e] + v;
+  }
 }
 
 int strip_adj_lv_floats(const Instance& in, int tile) {
@@ -754,13 +770,13 @@ cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int s
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || !dJ || !whole) return e;
-  return launch_strips_dJ_reduce(d_inst, li, part, part_stride, dJ, s);
+  return launch_strips_dJ_reduce(d_inst, li, part, part_stride, dJ, s, false);
 }
 
 cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* part, int part_stride,
-                                    double* dJ, cudaStream_t s) {
+                                    double* dJ, cudaStream_t s, bool assign) {
   strips_dJ_reduce_kernel<<<dim3((unsigned)((part_stride + 7) / 8), li.n_inst), 256, 0, s>>>(d_inst, li, part,
-                                                                                            part_stride, dJ);
+                                                                                            part_stride, dJ, assign);
   return cudaGetLastError();
 }
 

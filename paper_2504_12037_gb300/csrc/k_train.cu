@@ -221,8 +221,9 @@ __device__ __forceinline__ TupleFF ld_tuple_ff(const double* slot) {
 
 __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
                                                      const float* __restrict__ logq, double* __restrict__ part,
-                                                     double* __restrict__ stats, int* __restrict__ counters) {
-  const int k = blockIdx.y, p = blockIdx.x, B = li.batch;
+                                                     double* __restrict__ stats, int* __restrict__ counters,
+                                                     int k0) {
+  const int k = blockIdx.y + k0, p = blockIdx.x, B = li.batch;
   const long long base = (long long)k * B;
   const FF K = ff_add(ff_from_double(logZR[base]), FF{-logq[base], 0.f});
   const FF negK = ff_neg(K);
@@ -300,14 +301,16 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
 }
 
 cudaError_t launch_reduce(const InstDev*, const LaunchInfo& li, const double* logZR,
-                          const float* logq, double* stats, int* counters, cudaStream_t s) {
+                          const float* logq, double* stats, int* counters, cudaStream_t s, int k0, int k1) {
+  if (k1 < 0) k1 = li.n_inst;
+  if (k1 <= k0) return cudaSuccess;
   // n_part: chunks of >= 256 samples, at most 64 per instance
   int n_part = (li.batch + 255) / 256;
   if (n_part > 64) n_part = 64;
   if (n_part < 1) n_part = 1;
   // partial tuples live right after the stats block
   double* part = stats + 8 * TNVAN_MAX_INST;
-  reduce_kernel<<<dim3(n_part, li.n_inst), 256, 0, s>>>(li, n_part, logZR, logq, part, stats, counters);
+  reduce_kernel<<<dim3(n_part, k1 - k0), 256, 0, s>>>(li, n_part, logZR, logq, part, stats, counters, k0);
   return cudaGetLastError();
 }
 
@@ -513,14 +516,54 @@ cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int sme
   return cudaGetLastError();
 }
 
+// Adam (Kingma & Ba 2015) on one entry, bias corrections bc1 = 1 - b1^t,
+// bc2 = 1 - b2^t.  The one definition both Adam kernels use.
+__device__ __forceinline__ void adam_entry(float& p, float& m, float& v, float g, const AdamArgs& a, float bc1,
+                                           float bc2) {
+  const float mi = a.b1 * m + (1.f - a.b1) * g;
+  const float vi = a.b2 * v + (1.f - a.b2) * g * g;
+  m = mi;
+  v = vi;
+  p -= a.lr * (mi / bc1) / (sqrtf(vi / bc2) + a.eps);
+}
+
+// The bias corrections of this launch: the host's, or (device step counter)
+// formed by one thread of the CTA in FP64 (a narrow unit here) from
+// t = t_base + *t_dev.
+__device__ __forceinline__ void adam_corrections(const AdamArgs& a, float& bc1, float& bc2) {
+  bc1 = a.bc1;
+  bc2 = a.bc2;
+  if (a.t_dev) {
+    __shared__ float bc[2];
+    if (threadIdx.x == 0) {
+      const double t = (double)(a.t_base + (long long)*a.t_dev);
+      bc[0] = (float)(1.0 - exp(t * log((double)a.b1)));
+      bc[1] = (float)(1.0 - exp(t * log((double)a.b2)));
+    }
+    __syncthreads();
+    bc1 = bc[0];
+    bc2 = bc[1];
+  }
+}
+
 // Sum the chunk partials of every instance (fixed order: deterministic) and
 // scatter from the packed, degree-sorted layout to the caller's natural
-// layout; entries outside the MADE masks get 0.
+// layout; entries outside the MADE masks get 0.  With COLS the partials hold
+// each layer's [nout x (nin + 1)] block (weights, then the bias column)
+// column-major (entry (o, i) at i * nout + o), the order in which the fused
+// backward writes its accumulators with coalesced stores; otherwise the
+// packed order (row-major weights, then biases).  With ADAM the same thread
+// then applies Adam to that entry of the instance's own parameters
+// (tnvan_set_made's pointer) with the moments at the gradient's offset, so a
+// training step needs no separate optimizer pass over the gradient.
+template <bool ADAM, bool COLS>
 __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                    const float* __restrict__ partials, long long part_stride,
-                                   float* __restrict__ grad) {
+                                   float* __restrict__ grad, const AdamArgs adam) {
   const int k = blockIdx.y;
   const MadeDev& md = inst[k].made;
+  float bc1 = 1.f, bc2 = 1.f;
+  if (ADAM) adam_corrections(adam, bc1, bc2);
   const int p0 = li.tile_begin[k], p1 = li.tile_begin[k + 1];
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < md.n_params;
        e += (long long)gridDim.x * blockDim.x) {
@@ -534,33 +577,56 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
     for (int j = 0; j < 8; ++j)
       if (p + j < p1) a[j] += partials[(long long)(p + j) * part_stride + e];
     const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    long long r = e;
+    long long r = e, nat = -1;
+    float gv = s;
     for (int l = 0; l < md.n_layers; ++l) {
       const LayerDev& L = md.layer[l];
       const long long nw = (long long)L.nout * L.nin;
-      if (r < nw) {
-        const int o = (int)(r / L.nin), i = (int)(r % L.nin);
+      if (r < nw + L.nout) {
+        int o, i;
+        if (COLS) {
+          i = (int)(r / L.nout);
+          o = (int)(r - (long long)i * L.nout);
+        } else if (r < nw) {
+          o = (int)(r / L.nin);
+          i = (int)(r - (long long)o * L.nin);
+        } else {
+          o = (int)(r - nw);
+          i = L.nin;
+        }
         const int no = L.perm_out ? L.perm_out[o] : o;
-        const int ni = L.perm_in ? L.perm_in[i] : i;
-        const bool conn = L.strict ? (L.deg_out[o] > L.deg_in[i]) : (L.deg_out[o] >= L.deg_in[i]);
-        grad[md.param_off + L.src_off + (long long)no * L.nin + ni] = conn ? s : 0.f;
+        if (i == L.nin) {  // bias
+          nat = L.src_off + nw + no;
+        } else {
+          const int ni = L.perm_in ? L.perm_in[i] : i;
+          const bool conn = L.strict ? (L.deg_out[o] > L.deg_in[i]) : (L.deg_out[o] >= L.deg_in[i]);
+          nat = L.src_off + (long long)no * L.nin + ni;
+          gv = conn ? s : 0.f;
+        }
         break;
       }
-      r -= nw;
-      if (r < L.nout) {
-        const int no = L.perm_out ? L.perm_out[r] : (int)r;
-        grad[md.param_off + L.src_off + nw + no] = s;
-        break;
-      }
-      r -= L.nout;
+      r -= nw + L.nout;
     }
+    if (nat < 0) continue;
+    const long long o = md.param_off + nat;
+    grad[o] = gv;
+    if (ADAM) adam_entry(md.raw[nat], adam.m[o], adam.v[o], gv, adam, bc1, bc2);
   }
 }
 
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* partials,
-                               int part_stride, float* grad, cudaStream_t s) {
+                               int part_stride, float* grad, cudaStream_t s, const AdamArgs* adam, bool cols) {
   if (li.n_inst == 0) return cudaSuccess;
-  grad_reduce_kernel<<<dim3(64, li.n_inst), 256, 0, s>>>(d_inst, li, partials, part_stride, grad);
+  const dim3 grid(64, li.n_inst);
+  const AdamArgs none{};
+  if (adam && cols)
+    grad_reduce_kernel<true, true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam);
+  else if (adam)
+    grad_reduce_kernel<true, false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam);
+  else if (cols)
+    grad_reduce_kernel<false, true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, none);
+  else
+    grad_reduce_kernel<false, false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, none);
   return cudaGetLastError();
 }
 
@@ -585,42 +651,21 @@ cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const 
   return cudaGetLastError();
 }
 
-// Adam (Kingma & Ba 2015), bias corrections bc1 = 1 - b1^t, bc2 = 1 - b2^t.
-// With t_dev, the step is t_base + *t_dev (a device step counter, for
-// replayed CUDA graphs) and the bias corrections are formed here.
-__global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g,
-                            float* __restrict__ m, float* __restrict__ v, float lr, float b1,
-                            float b2, float eps, float bc1, float bc2, const unsigned long long* t_dev,
-                            long long t_base) {
-  if (t_dev) {  // one thread per CTA forms them (FP64 is a narrow unit here)
-    __shared__ float bc[2];
-    if (threadIdx.x == 0) {
-      const double t = (double)(t_base + (long long)*t_dev);
-      bc[0] = (float)(1.0 - exp(t * log((double)b1)));
-      bc[1] = (float)(1.0 - exp(t * log((double)b2)));
-    }
-    __syncthreads();
-    bc1 = bc[0];
-    bc2 = bc[1];
-  }
+// Adam over a flat array (tnvan_adam).  With t_dev, the step is
+// t_base + *t_dev (a device step counter, for replayed CUDA graphs).
+__global__ void adam_kernel(long long n, float* __restrict__ p, const float* __restrict__ g, const AdamArgs a) {
+  float bc1, bc2;
+  adam_corrections(a, bc1, bc2);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    adam_entry(p[i], a.m[i], a.v[i], g[i], a, bc1, bc2);
 }
 
-cudaError_t launch_adam(long long n, float* p, const float* g, float* m, float* v, float lr,
-                        float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s,
-                        const unsigned long long* t_dev, long long t_base) {
+cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   long long nb = (n + 255) / 256;
   if (nb > 1216) nb = 1216;
-  adam_kernel<<<(int)nb, 256, 0, s>>>(n, p, g, m, v, lr, b1, b2, eps, bc1, bc2, t_dev, t_base);
+  adam_kernel<<<(int)nb, 256, 0, s>>>(n, p, g, a);
   return cudaGetLastError();
 }
 

@@ -71,8 +71,19 @@ class TNVAN:
 
     def train_step(self, batch: int, seed: int, step: int, precision: int = tv.FP32, lr: float = 0.01,
                    out=None, dbeta=None, dJ=None, stream=None):
-        """One iteration of Algorithm 1: sample, contract, gradient, Adam.  With
-        dbeta / dJ given, the contraction adjoint runs in the sampling pass."""
+        """One iteration of Algorithm 1: sample, contract, gradient, Adam, in one
+        library call (tnvan_train_step).  With dbeta / dJ given, the
+        contraction adjoint runs in the sampling pass."""
+        spins, logq, logZR = out if out is not None else self.buffers(batch)
+        self.t += 1
+        self.ctx.train_step(self.betas, batch, seed, step, precision, spins, logq, logZR, dbeta, dJ, self.grad,
+                            self.m, self.v, lr, 0.9, 0.999, 1e-8, self.t, stream)
+        return spins, logq, logZR
+
+    def train_step_separate(self, batch: int, seed: int, step: int, precision: int = tv.FP32, lr: float = 0.01,
+                            out=None, dbeta=None, dJ=None, stream=None):
+        """train_step through the separate entry points (sampling with the
+        adjoint, backward, Adam): the same step, three calls."""
         spins, logq, logZR = out if out is not None else self.buffers(batch)
         self.ctx.sample_contract_adjoint(self.betas, batch, seed, step, precision, spins, logq, logZR, dbeta, dJ,
                                          stream)

@@ -40,6 +40,8 @@ SIGNATURES = {
     "tnvan_sample_and_contract": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp]),
     "tnvan_sample_contract_adjoint": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp,
                                                _vp, _vp]),
+    "tnvan_train_step": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp]),
     "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
@@ -170,6 +172,15 @@ class Context:
         self._check(lib().tnvan_sample_contract_adjoint(self._h, pb, batch, seed, step, precision, _ptr(spins),
                                                         _ptr(logq), _ptr(logZR), _ptr(dbeta), _ptr(dJ),
                                                         _stream(stream)))
+
+    def train_step(self, betas, batch: int, seed: int, step: int, precision: int, spins, logq, logZR, dbeta, dJ,
+                   grad, m, v, lr: float, beta1: float, beta2: float, eps: float, t: int, stream=None):
+        """Sampling with the contraction adjoint, the REINFORCE gradient and
+        Adam on the networks' own parameters, in one call."""
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_train_step(self._h, pb, batch, seed, step, precision, _ptr(spins), _ptr(logq),
+                                           _ptr(logZR), _ptr(dbeta), _ptr(dJ), _ptr(grad), _ptr(m), _ptr(v),
+                                           lr, beta1, beta2, eps, t, _stream(stream)))
 
     def log_prob(self, batch: int, spins, logq, precision: int = FP32, stream=None):
         self._check(lib().tnvan_log_prob(self._h, batch, _ptr(spins), precision, _ptr(logq), _stream(stream)))

@@ -111,3 +111,34 @@ def test_captured_train_step_matches_eager_steps():
     cs.replay()  # the next step: fresh draws
     torch.cuda.synchronize()
     assert b.t == 3 and not torch.equal(cs.out[0], s1)
+
+
+@pytest.mark.parametrize("precision", [tv.BF16, tv.FP32])
+def test_fused_train_step_matches_separate_calls(precision):
+    # tnvan_train_step (one pack, gradient reduction and Adam in one kernel,
+    # Adam on the networks' own parameters) against sample_contract_adjoint +
+    # backward + adam: the same samples, contraction, adjoint and gradient,
+    # and the same parameters and moments after Adam
+    w = wl.workload(2)
+    from paper_2504_12037_gb300.model import TNVAN
+
+    B = 700
+    mk = lambda: TNVAN(w.graphs[:3], w.widths_sets[:3], w.hidden, w.betas[:3], seed=4)
+    a, b = mk(), mk()
+    dba = torch.empty(3 * B, dtype=torch.float64, device="cuda")
+    dja = torch.empty(sum(a.n_edges), dtype=torch.float64, device="cuda")
+    dbb, djb = torch.empty_like(dba), torch.empty_like(dja)
+    outa, outb = a.buffers(B), b.buffers(B)
+    for step in range(2):
+        a.train_step(B, 21, step, precision, 0.01, outa, dba, dja)
+        b.train_step_separate(B, 21, step, precision, 0.01, outb, dbb, djb)
+        torch.cuda.synchronize()
+        for x, y in zip(outa, outb):
+            assert torch.equal(x, y)
+        assert torch.equal(dba, dbb) and torch.equal(dja, djb)
+        assert torch.equal(a.grad, b.grad)
+        for x, y in ((a.params, b.params), (a.m, b.m), (a.v, b.v)):
+            assert torch.allclose(x, y, rtol=1e-6, atol=1e-9)
+            y.copy_(x)  # the next step starts from one state (b's networks are views of b.params)
+    assert a.t == b.t == 2
+    assert not torch.equal(a.params, mk().params)  # Adam moved the registered parameters
