@@ -1589,7 +1589,7 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
     }
     {
       PROF("grad_reduce", s);
-      CK(launch_grad_reduce(ctx->d_inst, lf, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam, true),
+      CK(launch_grad_reduce(ctx->d_inst, lf, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam),
          "gradient reduce kernel");
     }
   } else if (precision != TNVAN_FP32) {

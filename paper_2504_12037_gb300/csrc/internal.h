@@ -307,11 +307,10 @@ struct AdamArgs {
   long long t_base;
 };
 // With adam non-NULL the reduction also applies Adam to every instance's own
-// parameters (the fused optimizer step of tnvan_train_step); cols: the
-// partials are in the fused backward's column-major layer blocks.
+// parameters (the fused optimizer step of tnvan_train_step).
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                const float* partials, int part_stride, float* grad,
-                               cudaStream_t s, const AdamArgs* adam = nullptr, bool cols = false);
+                               cudaStream_t s, const AdamArgs* adam = nullptr);
 cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
                                const double* stats, float* w, cudaStream_t s);
 cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,

@@ -317,20 +317,25 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   }
   if (!ok && tid == 0) atomicExch(args.status, 3);
   // ---- flush the gradient partials of this CTA ----
-  // Each layer's [nout x (nin + 1)] accumulator (TMEM lane = output unit,
-  // column = input, the last column the bias) goes out column-major, entry
-  // (o, i) at dst_off + i * nout + o, so a warp's 32 lanes store 32
-  // consecutive floats per column.
+  // Each layer's accumulator (TMEM lane = packed output unit, column =
+  // packed input, the last column the bias) goes out in the packed layout:
+  // every thread writes its 16 columns of a row as four 16-byte stores (the
+  // row-major layer blocks need no transpose), the bias column as one float.
   float* G = args.partials + (long long)blockIdx.x * args.part_stride;
   if (ok && !first) {
     auto flush = [&](uint32_t tacc, int nin, int nout, long long off) {
       for (int c = 16 * g; c < nin + 16; c += 32) {
         float v[16];
         tc::tmem_ld16(tacc + lane_off + (uint32_t)c, v);
-        if (t < nout)
+        if (t < nout) {
+          if (c < nin) {
+            float4* row = reinterpret_cast<float4*>(G + off + (long long)t * nin + c);
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c + i <= nin) G[off + (long long)(c + i) * nout + t] = v[i];
+            for (int q = 0; q < 4; ++q) row[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          } else {
+            G[off + (long long)nout * nin + t] = v[0];  // c == nin: the bias column
+          }
+        }
       }
     };
     flush(tG1, D, H1, md.layer[0].dst_off);

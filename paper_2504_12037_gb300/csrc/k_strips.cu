@@ -137,8 +137,9 @@ __device__ __forceinline__ int row_index(const int* pos, int y, const int8_t* sr
 
 // Contract one strip for one sample.  Returns ln Z_strip - beta*c_hat as
 // (float mantissa part, integer power-of-two exponent) and d/dbeta of it.
-// With SAVE, row y's renormalised left vector is also written to
-// lvs[(y * 2^W + x) * T + t] (the adjoint's backward sweep reads it).
+// With SAVE, the renormalised left vector of every even row y is also
+// written to lvs[((y / 2) * 2^W + x) * T + t] (the adjoint's backward sweep
+// reads it and recomputes the odd rows from it).
 template <int W, bool DB, bool SAVE = false>
 __device__ void strip_chain(const StripTab& tb, int L, const int8_t* srow, double& lnz, float& dl,
                             float* lvs = nullptr, int t = 0, int T = 0) {
@@ -177,7 +178,7 @@ __device__ void strip_chain(const StripTab& tb, int L, const int8_t* srow, doubl
     for (int x = 0; x < NX; ++x) {
       v[x] *= sc;
       if (DB) g[x] *= sc;
-      if (SAVE) lvs[(y * NX + x) * T + t] = v[x];
+      if (SAVE && !(y & 1)) lvs[((y >> 1) * NX + x) * T + t] = v[x];
     }
     e2 += e;
   }
@@ -348,7 +349,11 @@ __device__ __forceinline__ int transpose_slot(int lane) {
 //   Z = L_c^T R_c + t L_c^T X R_c,  Z <s_c s'_c> = L_c^T R_c - t L_c^T X R_c,
 // so Z <s_c s'_c> = 2 L_c^T R_c - Z, and the W vertical bonds share 2W - 1
 // Kronecker-factor applications and one dot product each.  The row's bonds
-// are read by slot (StripRow::Js, es), absent bonds carrying J = 0.
+// are read by slot (StripRow::Js, es), absent bonds carrying J = 0.  Only the
+// even rows' left vectors are stored: an odd row's is recomputed from the
+// row before it as D_y V_{y-1} l_{y-1}, without the renormalisation (a power
+// of two that every ratio below cancels exactly), and that stored row is
+// kept in registers for the next iteration.
 template <int W>
 __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict__ rows, int L,
                                  const int8_t* srow, const float* lvs, int t, int T, bool valid, float* accw,
@@ -363,6 +368,7 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
   const int slot = transpose_slot<NV>(lane);
   const bool has_slot = own && slot < NB;
   float r[NX];  // r_{y+1}, renormalised
+  float lkeep[NX];  // l_{y} of an even row, loaded while recomputing row y + 1
   float dlog = 0.f;
   for (int y = L - 1; y >= 0; --y) {
     float Js[NB];
@@ -371,8 +377,23 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
     const int ecur = has_slot ? rows[y].es[slot] : -1;
     const int idx = row_index(pos, y, srow);
     float lv[NX], msg[NX], dummy[NX];
+    if (y & 1) {
 #pragma unroll
-    for (int x = 0; x < NX; ++x) lv[x] = lvs[(y * NX + x) * T + t];
+      for (int x = 0; x < NX; ++x) lkeep[x] = lvs[(((y - 1) >> 1) * NX + x) * T + t];
+#pragma unroll
+      for (int x = 0; x < NX; ++x) lv[x] = lkeep[x];
+#pragma unroll
+      for (int c = 0; c < W; ++c) apply_pair<W, false>(lv, dummy, c, vert[(y - 1) * W + c]);
+      const float* dyl = diag + (y * 4 + idx) * NX;
+#pragma unroll
+      for (int x = 0; x < NX; ++x) lv[x] *= dyl[x];
+    } else if (y == L - 1) {
+#pragma unroll
+      for (int x = 0; x < NX; ++x) lv[x] = lvs[((y >> 1) * NX + x) * T + t];
+    } else {
+#pragma unroll
+      for (int x = 0; x < NX; ++x) lv[x] = lkeep[x];
+    }
     float val[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) val[j] = 0.f;
@@ -467,13 +488,13 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
 }
 
 // Shared memory of strips_adj_kernel: strip tables, the tile's spins, the
-// left vectors of one strip [L][2^w][T] and (T/32) rows of n_edges
+// left vectors of one strip's even rows [ceil(L/2)][2^w][T] and (T/32) rows of n_edges
 // accumulators.
 __host__ __device__ inline int strip_adj_lv_offset(int tab_floats, int T, int Dp) {
   return tab_floats + ((T * Dp + 15) & ~15) / 4;
 }
 
-__global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+__global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                                          int lv_floats, const int8_t* __restrict__ spins,
                                                          double* __restrict__ logZR, double* __restrict__ dbeta,
                                                          float* __restrict__ part, int part_stride) {
@@ -566,7 +587,7 @@ __global__ void __launch_bounds__(128) strips_adj_kernel(const InstDev* __restri
 // the tail of a launch and the gaps beside other kernels.  log Z_R and d/dbeta
 // are assembled by warp 0 from the per-strip partials in strip order (the same
 // arithmetic as strips_adj_kernel); W-W bond chunks are spread over the warps.
-// Shared memory: tables | spins | left vectors [L][2^w][blockDim] | one row
+// Shared memory: tables | spins | even-row left vectors [ceil(L/2)][2^w][blockDim] | one row
 // of n_edges accumulators per warp | per-(strip, sample) partials.
 __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                                              int lv_floats, const int8_t* __restrict__ spins,
@@ -687,7 +708,7 @@ __global__ void strips_dJ_reduce_kernel(const InstDev* __restrict__ inst, const 
 
 int strip_adj_lv_floats(const Instance& in, int tile) {
   int lv = 0;
-  for (const StripDev& sd : in.strip.strips) lv = std::max(lv, sd.L << sd.w);
+  for (const StripDev& sd : in.strip.strips) lv = std::max(lv, ((sd.L + 1) / 2) << sd.w);  // even rows
   return lv * tile;
 }
 
@@ -711,7 +732,7 @@ int strip_adj_ws_threads(const tnvan_ctx* ctx) {
 }
 int strip_adj_ws_lv_floats(const Instance& in, int threads) {
   int lv = 0;
-  for (const StripDev& sd : in.strip.strips) lv = std::max(lv, sd.L << sd.w);
+  for (const StripDev& sd : in.strip.strips) lv = std::max(lv, ((sd.L + 1) / 2) << sd.w);  // even rows
   return lv * threads;
 }
 int strip_adj_ws_smem_bytes(const Instance& in, int threads, int lv_floats) {

@@ -548,15 +548,11 @@ __device__ __forceinline__ void adam_corrections(const AdamArgs& a, float& bc1, 
 
 // Sum the chunk partials of every instance (fixed order: deterministic) and
 // scatter from the packed, degree-sorted layout to the caller's natural
-// layout; entries outside the MADE masks get 0.  With COLS the partials hold
-// each layer's [nout x (nin + 1)] block (weights, then the bias column)
-// column-major (entry (o, i) at i * nout + o), the order in which the fused
-// backward writes its accumulators with coalesced stores; otherwise the
-// packed order (row-major weights, then biases).  With ADAM the same thread
+// layout; entries outside the MADE masks get 0.  With ADAM the same thread
 // then applies Adam to that entry of the instance's own parameters
 // (tnvan_set_made's pointer) with the moments at the gradient's offset, so a
 // training step needs no separate optimizer pass over the gradient.
-template <bool ADAM, bool COLS>
+template <bool ADAM>
 __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                    const float* __restrict__ partials, long long part_stride,
                                    float* __restrict__ grad, const AdamArgs adam) {
@@ -582,30 +578,21 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
     for (int l = 0; l < md.n_layers; ++l) {
       const LayerDev& L = md.layer[l];
       const long long nw = (long long)L.nout * L.nin;
-      if (r < nw + L.nout) {
-        int o, i;
-        if (COLS) {
-          i = (int)(r / L.nout);
-          o = (int)(r - (long long)i * L.nout);
-        } else if (r < nw) {
-          o = (int)(r / L.nin);
-          i = (int)(r - (long long)o * L.nin);
-        } else {
-          o = (int)(r - nw);
-          i = L.nin;
-        }
+      if (r < nw) {
+        const int o = (int)(r / L.nin), i = (int)(r % L.nin);
         const int no = L.perm_out ? L.perm_out[o] : o;
-        if (i == L.nin) {  // bias
-          nat = L.src_off + nw + no;
-        } else {
-          const int ni = L.perm_in ? L.perm_in[i] : i;
-          const bool conn = L.strict ? (L.deg_out[o] > L.deg_in[i]) : (L.deg_out[o] >= L.deg_in[i]);
-          nat = L.src_off + (long long)no * L.nin + ni;
-          gv = conn ? s : 0.f;
-        }
+        const int ni = L.perm_in ? L.perm_in[i] : i;
+        const bool conn = L.strict ? (L.deg_out[o] > L.deg_in[i]) : (L.deg_out[o] >= L.deg_in[i]);
+        nat = L.src_off + (long long)no * L.nin + ni;
+        gv = conn ? s : 0.f;
         break;
       }
-      r -= nw + L.nout;
+      r -= nw;
+      if (r < L.nout) {
+        nat = L.src_off + nw + (L.perm_out ? L.perm_out[r] : (int)r);
+        break;
+      }
+      r -= L.nout;
     }
     if (nat < 0) continue;
     const long long o = md.param_off + nat;
@@ -615,18 +602,13 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
 }
 
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* partials,
-                               int part_stride, float* grad, cudaStream_t s, const AdamArgs* adam, bool cols) {
+                               int part_stride, float* grad, cudaStream_t s, const AdamArgs* adam) {
   if (li.n_inst == 0) return cudaSuccess;
   const dim3 grid(64, li.n_inst);
-  const AdamArgs none{};
-  if (adam && cols)
-    grad_reduce_kernel<true, true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam);
-  else if (adam)
-    grad_reduce_kernel<true, false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam);
-  else if (cols)
-    grad_reduce_kernel<false, true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, none);
+  if (adam)
+    grad_reduce_kernel<true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam);
   else
-    grad_reduce_kernel<false, false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, none);
+    grad_reduce_kernel<false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, AdamArgs{});
   return cudaGetLastError();
 }
 
