@@ -38,10 +38,8 @@ SM_MAX_MHZ = 2070.0
 MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
 # dram__bytes_read.sum + dram__bytes_write.sum per whole-batch launch from ncu
 # captures of the same kernels on the same workload (see profiles/); None if not
-# captured.  sample_tc and strips_adj were captured as one instance chunk of the
-# overlapped schedule and are scaled by the 5 instances (each chunk reads its own
-# network and couplings, so the traffic grows in proportion).
-NCU_TRAFFIC = {"sample_tc": 5 * 144640, "strips_adj": 5 * 1121024, "bwd_fused": 6877184, "reduce": 1033728}
+# captured
+NCU_TRAFFIC = {"sample_tc": 483840, "strips_adj": 5371136, "bwd_fused": 6673664, "reduce": 1035776, "grad_reduce": 19230464}
 
 
 def args_():
