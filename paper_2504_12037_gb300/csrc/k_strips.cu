@@ -461,7 +461,7 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
     }
     // the beta-weighted sum (absent bonds carry J = 0), then the masked
     // values for d/dJ
-    const float iz = 1.f / Z;
+    const float iz = __fdividef(1.f, Z);  // Z is a normal number well inside the fast path's range
     float dJb = 0.f;
 #pragma unroll
     for (int j = 0; j < NB; ++j) dJb = fmaf(Js[j], val[j], dJb);
