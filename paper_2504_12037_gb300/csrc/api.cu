@@ -518,10 +518,26 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
                   cudaStream_t s, bool pack, const AdamArgs* adam, bool stats_ready = false);
 AdamArgs adam_args(const tnvan_ctx* ctx, float* d_m, float* d_v, double lr, double beta1, double beta2, double eps,
                    int64_t t);
+// The fused BF16 backward's launch shape: CTAs of `per` 128-sample tiles,
+// about one CTA per SM overall; the gradient workspace holds one row per CTA.
+struct FusedBwdPlan {
+  LaunchInfo lf;
+  int smem;
+  long long max_elems;
+};
+int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan& p);
+// Backward and Adam of each instance chunk, queued behind that chunk's
+// adjoint and F_q reduction in the overlapped schedule.
+struct ChunkBackward {
+  const FusedBwdPlan* plan;
+  float* d_grad;
+  const AdamArgs* adam;
+};
 int sample_contract_adjoint_impl(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
                                  int precision, int8_t* d_spins, float* d_logq, double* d_logZR, double* d_dbeta,
                                  double* d_dJ, cudaStream_t s, bool* dj_deferred = nullptr,
-                                 bool* stats_done = nullptr);
+                                 bool* stats_done = nullptr, const ChunkBackward* cb = nullptr,
+                                 bool* bwd_done = nullptr);
 
 }  // namespace
 
@@ -772,6 +788,8 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   for (cudaStream_t st : ctx->side_lo)
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t e : ctx->chunk_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->adj_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->dj_ev) cudaEventDestroy(ctx->dj_ev);
@@ -1291,6 +1309,8 @@ static int ensure_side_streams(tnvan_ctx* ctx) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   for (cudaEvent_t& ev : ctx->chunk_ev)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  for (cudaEvent_t& ev : ctx->adj_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "side streams");
   return TNVAN_OK;
 }
@@ -1308,10 +1328,13 @@ static int ensure_side_streams(tnvan_ctx* ctx) {
 // caller queues next) and the caller waits on ctx->dj_ev before it is done;
 // with chunk_stats each chunk's F_q reduction (tnvan_backward's first kernel)
 // follows its adjoint on the chunk's stream.
+// With cb (implies chunk_stats) each chunk's fused backward and gradient
+// reduction with Adam follow too, so a chunk's whole training step runs as
+// soon as its samples exist.
 static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
                                      int plan, int8_t* d_spins, float* d_logq, double* d_logZR,
                                      double* d_dbeta, double* d_dJ, cudaStream_t s, bool defer_dj,
-                                     bool chunk_stats) {
+                                     bool chunk_stats, const ChunkBackward* cb) {
   int rc;
   int adj_tile = 0, adj_smem = 0, adj_lv = 0, adj_ws = 0;
   if ((rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv, &adj_ws))) return rc;
@@ -1349,10 +1372,24 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
                          d_dJ ? ctx->d_dj_part : nullptr, stride, nullptr, ctx->side_lo[c], la.tile_begin[k0],
                          la.tile_begin[k1], adj_ws),
        "strip adjoint kernel");
-    if (chunk_stats) {
+    CK(cudaEventRecord(ctx->adj_ev[c], ctx->side_lo[c]), "adjoint event");
+    if (chunk_stats || cb) {
       PROF("reduce", ctx->side_lo[c]);
       CK(launch_reduce(ctx->d_inst, lr, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, ctx->side_lo[c], k0, k1),
          "reduce kernels");
+    }
+    if (cb) {
+      const FusedBwdPlan& fp = *cb->plan;
+      {
+        PROF("bwd_fused", ctx->side_lo[c]);
+        CK(launch_bwd_fused(ctx->d_inst, fp.lf, fp.smem, d_spins, d_logZR, d_logq, ctx->d_stats, ctx->d_grad_packed,
+                            fp.max_elems, ctx->d_status, ctx->side_lo[c], fp.lf.tile_begin[k0], fp.lf.tile_begin[k1]),
+           "fused backward kernel");
+      }
+      PROF("grad_reduce", ctx->side_lo[c]);
+      CK(launch_grad_reduce(ctx->d_inst, fp.lf, ctx->d_grad_packed, (int)fp.max_elems, cb->d_grad, ctx->side_lo[c],
+                            cb->adam, k0, k1),
+         "gradient reduce kernel");
     }
   }
   for (int c = 0; c < nc; ++c) {
@@ -1361,9 +1398,9 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
   }
   if (d_dJ) {  // every edge's sum overwrites d_dJ: no clearing pass
     cudaStream_t sr = s;
-    if (defer_dj) {
-      sr = ctx->side_lo[0];
-      for (int c = 1; c < nc; ++c) CK(cudaStreamWaitEvent(sr, ctx->join_ev[c], 0), "join wait");
+    if (defer_dj) {  // after every chunk's adjoint, beside what follows them
+      sr = ctx->side[0];
+      for (int c = 0; c < nc; ++c) CK(cudaStreamWaitEvent(sr, ctx->adj_ev[c], 0), "adjoint wait");
     }
     {
       PROF("strips_dJ_reduce", sr);
@@ -1416,17 +1453,23 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
     return rc;
   // the overlapped schedule runs each chunk's F_q reduction behind its
   // adjoint, and the d/dJ reduction (it reads only the adjoint's partial
-  // rows) beside the backward; the step ends after both
-  bool dj_deferred = false, stats_done = false;
+  // rows) beside the backward; the step ends after both.
+  // With the fused BF16 backward the chunks' backward and Adam follow their
+  // reductions too.
+  bool dj_deferred = false, stats_done = false, bwd_done = false;
+  const AdamArgs a = adam_args(ctx, d_m, d_v, lr, beta1, beta2, eps, t);
+  FusedBwdPlan fp;
+  ChunkBackward cb{&fp, d_grad_params, &a};
+  if (all_fused && (rc = plan_fused_bwd(ctx, betas, batch, fp))) return rc;
   if (d_dbeta || d_dJ)
     rc = sample_contract_adjoint_impl(ctx, betas, batch, seed, step, precision, d_spins, d_logq, d_logZR, d_dbeta,
-                                      d_dJ, s, &dj_deferred, &stats_done);
+                                      d_dJ, s, &dj_deferred, &stats_done, all_fused ? &cb : nullptr, &bwd_done);
   else if (!(rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s)))
     rc = contract_all(ctx, betas, batch, d_spins, precision, d_logZR, nullptr, s);
   if (rc) return rc;
-  const AdamArgs a = adam_args(ctx, d_m, d_v, lr, beta1, beta2, eps, t);
-  rc = backward_impl(ctx, betas, batch, d_spins, d_logZR, d_logq, precision, d_grad_params, nullptr, nullptr, s,
-                     false, &a, stats_done);
+  if (!bwd_done)
+    rc = backward_impl(ctx, betas, batch, d_spins, d_logZR, d_logq, precision, d_grad_params, nullptr, nullptr, s,
+                       false, &a, stats_done);
   if (dj_deferred) CK(cudaStreamWaitEvent(s, ctx->dj_ev, 0), "d/dJ join");
   return rc;
 }
@@ -1440,10 +1483,12 @@ namespace {
 // sampler runs), on a network the caller has packed.
 int sample_contract_adjoint_impl(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step,
                                  int precision, int8_t* d_spins, float* d_logq, double* d_logZR, double* d_dbeta,
-                                 double* d_dJ, cudaStream_t s, bool* dj_deferred, bool* stats_done) {
+                                 double* d_dJ, cudaStream_t s, bool* dj_deferred, bool* stats_done,
+                                 const ChunkBackward* cb, bool* bwd_done) {
   int rc;
   if (dj_deferred) *dj_deferred = false;
   if (stats_done) *stats_done = false;
+  if (bwd_done) *bwd_done = false;
   bool strips_only = ctx->inst.size() >= 2;
   for (const Instance& in : ctx->inst) strips_only = strips_only && in.kind == 0;
   bool tc_all = precision == TNVAN_BF16;
@@ -1452,10 +1497,11 @@ int sample_contract_adjoint_impl(tnvan_ctx* ctx, const double* betas, int batch,
   if (strips_only && plan >= 0 && ctx->tune_overlap) {
     const bool defer = dj_deferred && d_dJ;
     if ((rc = sample_adjoint_overlapped(ctx, betas, batch, seed, step, plan, d_spins, d_logq, d_logZR, d_dbeta, d_dJ,
-                                        s, defer, stats_done != nullptr)))
+                                        s, defer, stats_done != nullptr, cb)))
       return rc;
     if (defer) *dj_deferred = true;
     if (stats_done) *stats_done = true;
+    if (bwd_done) *bwd_done = cb != nullptr;
     return TNVAN_OK;
   }
   if ((rc = run_sampler(ctx, betas, batch, seed, step, precision, d_spins, d_logq, nullptr, s))) return rc;
@@ -1568,28 +1614,17 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
     CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernels");
   }
   if (all_fused) {
-    // one CTA per chunk of 128-sample tiles, about one CTA per SM overall
-    const int n_inst = (int)ctx->inst.size();
-    const int tiles = (batch + 127) / 128;
-    const int ctas = std::max(1, std::min(tiles, ctx->tune_bwd_ctas ? ctx->tune_bwd_ctas : (148 + n_inst - 1) / n_inst));
-    const int per = (tiles + ctas - 1) / ctas;
-    LaunchInfo lf;
-    if ((rc = fill_launch(ctx, betas, batch, per, lf))) return rc;
-    for (int k = 0; k <= lf.n_inst; ++k) lf.tile_begin[k] = k * ((tiles + per - 1) / per);
-    lf.tile = per;
-    if ((rc = ensure_grad_ws(ctx, (size_t)lf.tile_begin[lf.n_inst] * (size_t)max_elems))) return rc;
-    int smem = 0;
-    for (const Instance& in : ctx->inst)
-      smem = std::max(smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
+    FusedBwdPlan fp;
+    if ((rc = plan_fused_bwd(ctx, betas, batch, fp))) return rc;
     {
       PROF("bwd_fused", s);
-      CK(launch_bwd_fused(ctx->d_inst, lf, smem, d_spins, d_logZR, d_logq, ctx->d_stats, ctx->d_grad_packed,
-                          max_elems, ctx->d_status, s),
+      CK(launch_bwd_fused(ctx->d_inst, fp.lf, fp.smem, d_spins, d_logZR, d_logq, ctx->d_stats, ctx->d_grad_packed,
+                          fp.max_elems, ctx->d_status, s),
          "fused backward kernel");
     }
     {
       PROF("grad_reduce", s);
-      CK(launch_grad_reduce(ctx->d_inst, lf, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam),
+      CK(launch_grad_reduce(ctx->d_inst, fp.lf, ctx->d_grad_packed, (int)fp.max_elems, d_grad_params, s, adam),
          "gradient reduce kernel");
     }
   } else if (precision != TNVAN_FP32) {
@@ -1629,6 +1664,24 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
   }
   if (d_dbeta || d_dJ) return run_adjoint(ctx, betas, batch, d_spins, precision, nullptr, d_dbeta, d_dJ, s);
   return TNVAN_OK;
+}
+
+int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan& p) {
+  int rc;
+  p.max_elems = 0;
+  p.smem = 0;
+  for (const Instance& in : ctx->inst) {
+    p.max_elems = std::max(p.max_elems, in.n_params);
+    p.smem = std::max(p.smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
+  }
+  const int n_inst = (int)ctx->inst.size();
+  const int tiles = (batch + 127) / 128;
+  const int ctas = std::max(1, std::min(tiles, ctx->tune_bwd_ctas ? ctx->tune_bwd_ctas : (148 + n_inst - 1) / n_inst));
+  const int per = (tiles + ctas - 1) / ctas;
+  if ((rc = fill_launch(ctx, betas, batch, per, p.lf))) return rc;
+  for (int k = 0; k <= p.lf.n_inst; ++k) p.lf.tile_begin[k] = k * ((tiles + per - 1) / per);
+  p.lf.tile = per;
+  return ensure_grad_ws(ctx, (size_t)p.lf.tile_begin[p.lf.n_inst] * (size_t)p.max_elems);
 }
 
 AdamArgs adam_args(const tnvan_ctx* ctx, float* d_m, float* d_v, double lr, double beta1, double beta2, double eps,

@@ -240,7 +240,7 @@ struct tnvan_ctx {
   // side streams and events of the overlapped sampling + adjoint schedule
   cudaStream_t side[8] = {};  // samplers (highest stream priority)
   cudaStream_t side_lo[8] = {};  // adjoints (default priority)
-  cudaEvent_t fork_ev = nullptr, join_ev[8] = {}, chunk_ev[8] = {}, dj_ev = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev[8] = {}, chunk_ev[8] = {}, adj_ev[8] = {}, dj_ev = nullptr;
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
@@ -310,13 +310,13 @@ struct AdamArgs {
 // parameters (the fused optimizer step of tnvan_train_step).
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                const float* partials, int part_stride, float* grad,
-                               cudaStream_t s, const AdamArgs* adam = nullptr);
+                               cudaStream_t s, const AdamArgs* adam = nullptr, int k0 = 0, int k1 = -1);
 cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
                                const double* stats, float* w, cudaStream_t s);
 cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                              const int8_t* spins, const double* logZR, const float* logq,
                              const double* stats, float* partials, long long part_stride, int* status,
-                             cudaStream_t s);
+                             cudaStream_t s, int blk_begin = 0, int blk_end = -1);
 int fused_bwd_smem_bytes(int D, int H1, int H2);
 cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
                              float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);

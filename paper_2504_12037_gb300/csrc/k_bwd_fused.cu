@@ -94,7 +94,8 @@ __host__ __device__ inline int fused_bwd_smem(int D, int H1, int H2) {
 __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
                                                            const LaunchInfo li, FusedBwdArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int k = find_inst(li, blockIdx.x);
+  const int gblk = blockIdx.x + li.blk0;  // a launch may cover a sub-range of the blocks
+  const int k = find_inst(li, gblk);
   const InstDev& I = inst[k];
   const MadeDev& md = I.made;
   if (!md.fused_ok) return;
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 127, g = tid >> 7;
   const int B = li.batch;
   const int tiles_total = (B + 127) / 128;
-  const int c_idx = blockIdx.x - li.tile_begin[k];
+  const int c_idx = gblk - li.tile_begin[k];
   const int per = li.tile;  // tiles per CTA
   const int tile0 = c_idx * per, tile1 = min(tiles_total, tile0 + per);
   // ---- shared memory carve ----
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   // packed input, the last column the bias) goes out in the packed layout:
   // every thread writes its 16 columns of a row as four 16-byte stores (the
   // row-major layer blocks need no transpose), the bias column as one float.
-  float* G = args.partials + (long long)blockIdx.x * args.part_stride;
+  float* G = args.partials + (long long)gblk * args.part_stride;
   if (ok && !first) {
     auto flush = [&](uint32_t tacc, int nin, int nout, long long off) {
       for (int c = 16 * g; c < nin + 16; c += 32) {
@@ -352,13 +353,16 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
 cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                              const int8_t* spins, const double* logZR, const float* logq,
                              const double* stats, float* partials, long long part_stride, int* status,
-                             cudaStream_t s) {
-  const int nblk = li.tile_begin[li.n_inst];
-  if (nblk == 0) return cudaSuccess;
+                             cudaStream_t s, int blk_begin, int blk_end) {
+  if (blk_end < 0) blk_end = li.tile_begin[li.n_inst];
+  const int nblk = blk_end - blk_begin;
+  if (nblk <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(bwd_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
+  LaunchInfo lc = li;
+  lc.blk0 = blk_begin;
   FusedBwdArgs a{spins, logZR, logq, stats, partials, part_stride, status};
-  bwd_fused_kernel<<<nblk, 256, smem_bytes, s>>>(d_inst, li, a);
+  bwd_fused_kernel<<<nblk, 256, smem_bytes, s>>>(d_inst, lc, a);
   return cudaGetLastError();
 }
 

@@ -555,8 +555,8 @@ __device__ __forceinline__ void adam_corrections(const AdamArgs& a, float& bc1, 
 template <bool ADAM>
 __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                    const float* __restrict__ partials, long long part_stride,
-                                   float* __restrict__ grad, const AdamArgs adam) {
-  const int k = blockIdx.y;
+                                   float* __restrict__ grad, const AdamArgs adam, int k0) {
+  const int k = blockIdx.y + k0;
   const MadeDev& md = inst[k].made;
   float bc1 = 1.f, bc2 = 1.f;
   if (ADAM) adam_corrections(adam, bc1, bc2);
@@ -602,13 +602,14 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
 }
 
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, const float* partials,
-                               int part_stride, float* grad, cudaStream_t s, const AdamArgs* adam) {
-  if (li.n_inst == 0) return cudaSuccess;
-  const dim3 grid(64, li.n_inst);
+                               int part_stride, float* grad, cudaStream_t s, const AdamArgs* adam, int k0, int k1) {
+  if (k1 < 0) k1 = li.n_inst;
+  if (k1 <= k0) return cudaSuccess;
+  const dim3 grid(64, k1 - k0);
   if (adam)
-    grad_reduce_kernel<true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam);
+    grad_reduce_kernel<true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam, k0);
   else
-    grad_reduce_kernel<false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, AdamArgs{});
+    grad_reduce_kernel<false><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, AdamArgs{}, k0);
   return cudaGetLastError();
 }
 
