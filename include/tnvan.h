@@ -241,7 +241,11 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
  * per CTA, the BF16 tensor-core sampler's step-group size limit and whether
  * tnvan_sample_contract_adjoint overlaps sampling and the strip adjoint on
  * side streams (2 = on, 1 = off) -- with CUDA events on `stream`, and keeps
- * the fastest in the context for later calls.  out (host int32[6], may be
+ * the fastest in the context for later calls.  With the overlapped schedule
+ * and the fused backward, the backward's CTA count and the adjoint's shape
+ * are finally re-timed together on whole tnvan_train_step calls, captured
+ * in a CUDA graph on a private stream and replayed, with learning rate 0 and
+ * scratch moments, so the networks are left as they were.  out (host int32[6], may be
  * NULL) receives the choices in that order (0 = heuristic, not tuned).
  * Synchronous; allocates and frees temporary device buffers.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM, TNVAN_E_CUDA. */

@@ -1889,11 +1889,109 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
         }
       }
     }
+    ctx->tune_adj_tile = best_t;
+    ctx->tune_overlap = best_o;
+    if (fused && tc_sampler && best_o) {
+      // the overlapped training step runs each chunk's backward behind its
+      // adjoint, so the backward's CTA count and the adjoint's shape are
+      // re-timed together on whole training steps (learning rate 0 on
+      // scratch moments: the networks do not move)
+      float *m = nullptr, *v = nullptr;
+      if (cudaMalloc(&m, sizeof(float) * params_n) != cudaSuccess ||
+          cudaMalloc(&v, sizeof(float) * params_n) != cudaSuccess) {
+        if (m) cudaFree(m);
+        cudaFree(dj);
+        cudaFree(db);
+        cleanup();
+        return fail(ctx, TNVAN_E_NOMEM, "autotune buffers");
+      }
+      cudaMemsetAsync(m, 0, sizeof(float) * params_n, s);
+      cudaMemsetAsync(v, 0, sizeof(float) * params_n, s);
+      cudaStreamSynchronize(s);
+      // the step as it is meant to run: captured once in a CUDA graph on a
+      // private stream (an eager call first sizes the workspaces), then
+      // replayed; the time of one replay
+      cudaStream_t sc = nullptr;
+      if (cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(m);
+        cudaFree(v);
+        cudaFree(dj);
+        cudaFree(db);
+        cleanup();
+        return fail(ctx, TNVAN_E_CUDA, "autotune stream");
+      }
+      auto step_on = [&](cudaStream_t st) {
+        return tnvan_train_step(ctx, betas, batch, 1, 0, precision, sp, lq, lz, db, dj, gr, m, v, 0.0, 0.9, 0.999,
+                                1.0, 1, st);
+      };
+      auto graph_time = [&](float* ms) -> int {
+        int r = step_on(sc);
+        if (r) return r;
+        if (cudaStreamSynchronize(sc) != cudaSuccess) return fail(ctx, TNVAN_E_CUDA, "autotune step");
+        cudaGraph_t gph = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        if (cudaStreamBeginCapture(sc, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+          return fail(ctx, TNVAN_E_CUDA, "autotune capture");
+        r = step_on(sc);
+        const cudaError_t ec = cudaStreamEndCapture(sc, &gph);
+        if (r || ec != cudaSuccess) {
+          if (gph) cudaGraphDestroy(gph);
+          return r ? r : fail(ctx, TNVAN_E_CUDA, "autotune capture: %s", cudaGetErrorString(ec));
+        }
+        if (cudaGraphInstantiate(&ex, gph, 0) != cudaSuccess) {
+          cudaGraphDestroy(gph);
+          return fail(ctx, TNVAN_E_CUDA, "autotune graph");
+        }
+        cudaGraphLaunch(ex, sc);
+        cudaEventRecord(e0, sc);
+        for (int i = 0; i < 5; ++i) cudaGraphLaunch(ex, sc);
+        cudaEventRecord(e1, sc);
+        const cudaError_t es = cudaEventSynchronize(e1);
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, e0, e1);
+        *ms = tot / 5.f;
+        cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(gph);
+        return es == cudaSuccess ? TNVAN_OK : fail(ctx, TNVAN_E_CUDA, "autotune replay: %s", cudaGetErrorString(es));
+      };
+      const int tiles = (batch + 127) / 128;
+      int best_c = ctx->tune_bwd_ctas, best_a = best_t;
+      float best_step = 1e30f;
+      for (int per : {2, 3, 4, 5, 6}) {
+        const int c = (tiles + per - 1) / per;
+        if (c < 1 || (per > 2 && c == (tiles + per - 2) / (per - 1))) continue;  // same launch as per - 1
+        for (int T : {best_t, 1, 128, 96}) {
+          ctx->tune_bwd_ctas = c;
+          ctx->tune_adj_tile = T;
+          int t_used = 0, sm = 0, lv = 0, ws = 0;
+          if (plan_strip_adjoint(ctx, batch, &t_used, &sm, &lv, &ws) || (ws ? 1 : t_used) != T) continue;
+          float ms = 0.f;
+          if ((rc = graph_time(&ms))) {
+            cudaStreamDestroy(sc);
+            cudaFree(m);
+            cudaFree(v);
+            cudaFree(dj);
+            cudaFree(db);
+            cleanup();
+            return rc;
+          }
+          if (ms < best_step) {
+            best_step = ms;
+            best_c = c;
+            best_a = T;
+          }
+        }
+      }
+      cudaStreamSynchronize(sc);
+      cudaStreamDestroy(sc);
+      cudaFree(m);
+      cudaFree(v);
+      ctx->tune_bwd_ctas = best_c;
+      ctx->tune_adj_tile = best_a;
+    }
     cudaStreamSynchronize(s);
     cudaFree(dj);
     cudaFree(db);
-    ctx->tune_adj_tile = best_t;
-    ctx->tune_overlap = best_o;
   }
   if (out) {
     out[0] = ctx->tune_sample_tile;

@@ -75,7 +75,10 @@ def test_autotune_picks_valid_shapes_and_results_unchanged():
     assert torch.equal(out0[0], out1[0])
     assert torch.allclose(out0[1], out1[1], rtol=0, atol=1e-5)
     assert torch.equal(out0[2], out1[2])
+    p0 = m.params.clone()
     choice_bf = m.ctx.autotune(m.betas, B, tv.BF16)
+    torch.cuda.synchronize()
+    assert torch.equal(m.params, p0)  # whole training steps are timed with the networks held fixed
     assert choice_bf[2] >= 1 and choice_bf[4] in (4, 6, 8) and choice_bf[5] in (1, 2)
     m.ctx.set_tuning(choice_bf)  # round trip
     with pytest.raises(tv.TnvanError):
