@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   const int B = li.batch;
   const int tiles_total = (B + 127) / 128;
   const int c_idx = gblk - li.tile_begin[k];
-  const int per = li.tile;  // tiles per CTA
+  // tiles per CTA: this instance's tiles over its CTAs (instances may differ)
+  const int nblk_k = li.tile_begin[k + 1] - li.tile_begin[k];
+  const int per = (tiles_total + nblk_k - 1) / nblk_k;
   const int tile0 = c_idx * per, tile1 = min(tiles_total, tile0 + per);
   // ---- shared memory carve ----
   unsigned char* p = smem;

@@ -31,50 +31,77 @@ __host__ __device__ inline long long tile_elems(const MadeDev& md) {
   return md.wtiles ? (long long)md.H1 * md.D + (long long)md.H2 * md.H1 + (long long)md.D * md.H2 : 0;
 }
 
+// The tensor-core sampler plan a mask selects (bits 8 and up hold plan + 1;
+// 0 = every plan).
+__host__ __device__ inline int pack_tc_plan(int mask) { return (mask >> 8) - 1; }
+
+// BF16 copy of packed weight (r, c) of layer l (l < 3) into the tensor cores'
+// canonical K-major tiles: W1 [H1 x D], W2 [H2 x H1], Wo [D x H2], no swizzle.
+__device__ __forceinline__ void store_tile(const MadeDev& md, int l, int r, int c, float v) {
+  const int D = md.D, H1 = md.H1, H2 = md.H2;
+  const long long n1 = (long long)H1 * D, n2 = (long long)H2 * H1;
+  const int cols = l == 0 ? D : (l == 1 ? H1 : H2);
+  const long long base = l == 0 ? 0 : (l == 1 ? n1 : n1 + n2);
+  const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
+  uint32_t u = __float_as_uint(v);
+  u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+  md.wtiles[o] = (uint16_t)(u >> 16);
+}
+
 // Everything the kernels read from the network, rebuilt from the caller's
 // parameters in one launch (grid = (ceil(max_total / 256), n_inst)); the
 // segments selected by `mask`, back to back in a flat index:
-//   PACK_FLAT  the packed copy (FP32, natural order of packed_value)
+//   PACK_FLAT  the packed copy (FP32, natural order of packed_value); with
+//              PACK_TILES too, the same thread writes each weight's BF16 tile
+//              entry, so the tiles need no segment of their own
 //   PACK_TILES BF16 tiles in the tensor cores' canonical K-major layout (no
 //              swizzle): W1 [H1 x D], W2 [H2 x H1], Wo [D x H2]
 //   PACK_SIMT  the blocked SIMT sampler's weight blocks
-//   PACK_TC    the tensor-core sampler plans' triangle tiles
+//   PACK_TC    the tensor-core sampler plans' triangle tiles (one plan, or
+//              all, per pack_tc_plan)
 __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
   const MadeDev& md = inst[blockIdx.y].made;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool tiles = (mask & PACK_TILES) && md.wtiles && md.n_layers == 3;
   if (mask & PACK_FLAT) {
     if (e < md.n_params) {
-      md.packed[e] = packed_value(md, e);
+      const float v = packed_value(md, e);
+      md.packed[e] = v;
+      if (tiles) {  // weights of layer l at [dst_off, dst_off + nout * nin), row-major
+        int j = (int)e;
+        for (int l = 0; l < 3; ++l) {
+          const LayerDev& L = md.layer[l];
+          const int nw = L.nout * L.nin;
+          if (j < nw) {
+            const int r = j / L.nin;
+            store_tile(md, l, r, j - r * L.nin, v);
+            break;
+          }
+          j -= nw + L.nout;
+          if (j < 0) break;  // a bias
+        }
+      }
       return;
     }
     e -= md.n_params;
   }
-  if (mask & PACK_TILES) {
+  if (tiles && !(mask & PACK_FLAT)) {
     const long long nt = tile_elems(md);
     if (e < nt) {
       const int D = md.D, H1 = md.H1, H2 = md.H2;
       const long long n1 = (long long)H1 * D, n2 = (long long)H2 * H1;
-      int cols;
-      long long base, src;
+      int l, cols;
+      long long base;
       if (e < n1) {
-        cols = D;
-        base = 0;
-        src = md.layer[0].dst_off + e;
+        l = 0, cols = D, base = 0;
       } else if (e < n1 + n2) {
-        cols = H1;
-        base = n1;
-        src = md.layer[1].dst_off + (e - n1);
+        l = 1, cols = H1, base = n1;
       } else {
-        cols = H2;
-        base = n1 + n2;
-        src = md.layer[2].dst_off + (e - n1 - n2);
+        l = 2, cols = H2, base = n1 + n2;
       }
       const int le = (int)(e - base);
       const int r = le / cols, c = le - r * cols;
-      const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
-      uint32_t u = __float_as_uint(packed_value(md, src));
-      u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
-      md.wtiles[o] = (uint16_t)(u >> 16);
+      store_tile(md, l, r, c, packed_value(md, md.layer[l].dst_off + le));
       return;
     }
     e -= nt;
@@ -88,7 +115,9 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
     e -= md.n_blk;
   }
   if (mask & PACK_TC) {
+    const int only = pack_tc_plan(mask);
     for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+      if (only >= 0 && p != only) continue;
       const MadeDev::TcPlan& P = md.tc[p];
       if (e < P.n_blk) {
         const int j = P.src[e];
@@ -102,11 +131,15 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
 
 long long pack_elems(const MadeDev& md, int mask) {
   long long n = 0;
+  const bool tiles = (mask & PACK_TILES) && md.wtiles && md.n_layers == 3;
   if (mask & PACK_FLAT) n += md.n_params;
-  if (mask & PACK_TILES) n += tile_elems(md);
+  if (tiles && !(mask & PACK_FLAT)) n += tile_elems(md);
   if (mask & PACK_SIMT) n += md.n_blk;
-  if (mask & PACK_TC)
-    for (int p = 0; p < TNVAN_TC_PLANS; ++p) n += md.tc[p].n_blk;
+  if (mask & PACK_TC) {
+    const int only = pack_tc_plan(mask);
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p)
+      if (only < 0 || p == only) n += md.tc[p].n_blk;
+  }
   return n;
 }
 
