@@ -439,7 +439,7 @@ int pick_sample_tile(const tnvan_ctx* ctx) {
 // Launch shape of the strip adjoint: one thread per sample with T in
 // {128, 96, 64, 32} samples per CTA (all strips in turn), or one warp per
 // strip over 32 samples per CTA (ws_threads = 32 x strips; tuning value 1).
-// The left vectors of a strip take L 2^w floats per thread of shared memory,
+// The left vectors of a strip's even rows take ceil(L/2) 2^w floats per thread of shared memory,
 // so the shape sets the CTAs per SM; the default minimises (waves of CTAs) x
 // (strips a thread sweeps) / (the SM's issue rate, taken as saturating at 8
 // warps).  An autotuned shape (tnvan_autotune) takes precedence when it fits.

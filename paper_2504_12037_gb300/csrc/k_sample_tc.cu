@@ -216,10 +216,14 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
     {
       const int lo1 = u1lo - w1, hi1 = u1hi - w1, p1 = lo1 + (n1 - hi1);
       const int lo2 = u2lo - w2, hi2 = u2hi - w2, p2 = lo2 + (n2 - hi2);
+      // f / pn by a multiply and a shift: f < 16 pn <= 512 and r = ceil(2^16 / pn)
+      // give floor(f r / 2^16) = floor(f / pn) exactly
+      const uint32_t r1 = p1 ? (65535u + (uint32_t)p1) / (uint32_t)p1 : 0u;
+      const uint32_t r2 = p2 ? (65535u + (uint32_t)p2) / (uint32_t)p2 : 0u;
       for (int e = t; e < 16 * (p1 + p2); e += 128) {
         const bool l1 = e < 16 * p1;
         const int f = l1 ? e : e - 16 * p1, pn = l1 ? p1 : p2, lo = l1 ? lo1 : lo2, hi = l1 ? hi1 : hi2;
-        const int rg = f / pn, j = f - rg * pn;
+        const int rg = (int)(((uint32_t)f * (l1 ? r1 : r2)) >> 16), j = f - rg * pn;
         const int col = j < lo ? j : hi + (j - lo);
         *reinterpret_cast<uint4*>((l1 ? sH1 : sH2) + rg * (l1 ? sbo1 : sbo2) + 16 * col) = make_uint4(0, 0, 0, 0);
       }

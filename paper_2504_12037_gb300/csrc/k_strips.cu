@@ -494,6 +494,9 @@ __host__ __device__ inline int strip_adj_lv_offset(int tab_floats, int T, int Dp
   return tab_floats + ((T * Dp + 15) & ~15) / 4;
 }
 
+// TT: samples per CTA (= li.tile), a compile-time constant so that the
+// left-vector addressing folds into immediate offsets.
+template <int TT>
 __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                                          int lv_floats, const int8_t* __restrict__ spins,
                                                          double* __restrict__ logZR, double* __restrict__ dbeta,
@@ -503,7 +506,8 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
   const int k = find_inst(li, gblk);
   const InstDev& I = inst[k];
   if (I.kind != 0) return;  // another adjoint kernel owns this instance
-  const int T = li.tile, t = threadIdx.x, lane = t & 31;
+  constexpr int T = TT;
+  const int t = threadIdx.x, lane = t & 31;
   const int b0 = (gblk - li.tile_begin[k]) * T, b = b0 + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_row_bytes(D);
@@ -754,12 +758,25 @@ int strips_adj_ws_occupancy(int threads, int smem_bytes) {
   return nb;
 }
 
+// The instance of strips_adj_kernel for `tile` samples per CTA (nullptr if none).
+static void (*strips_adj_for(int tile))(const InstDev*, const LaunchInfo, int, const int8_t*, double*, double*, float*,
+                                        int) {
+  switch (tile) {
+    case 32: return strips_adj_kernel<32>;
+    case 64: return strips_adj_kernel<64>;
+    case 96: return strips_adj_kernel<96>;
+    case 128: return strips_adj_kernel<128>;
+    default: return nullptr;
+  }
+}
+
 // CTAs of `tile` threads with `smem_bytes` of shared memory resident per SM.
 int strips_adj_occupancy(int tile, int smem_bytes) {
-  if (cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
+  auto kern = strips_adj_for(tile);
+  if (!kern || cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, strips_adj_kernel, tile, smem_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, tile, smem_bytes) != cudaSuccess) return 0;
   return nb;
 }
 
@@ -783,11 +800,11 @@ cudaError_t launch_strips_adj(const InstDev* d_inst, const LaunchInfo& li, int s
     strips_adj_ws_kernel<<<nblk, ws_threads, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part,
                                                               part_stride);
   } else {
-    if (li.tile % 32 != 0 || li.tile > 128) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(strips_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    auto kern = strips_adj_for(li.tile);
+    if (!kern) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    strips_adj_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part,
-                                                        part_stride);
+    kern<<<nblk, li.tile, smem_bytes, s>>>(d_inst, lc, lv_floats, spins, logZR, dbeta, part, part_stride);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess || !dJ || !whole) return e;
