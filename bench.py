@@ -57,7 +57,7 @@ def args_():
     ap.add_argument("--tuning", default="",
                     help="six comma-separated ints for Context.set_tuning instead of autotuning "
                          "(sample tile, strip tile, backward CTAs, adjoint tile, TC group, overlap 2=on 1=off)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -266,35 +266,73 @@ def run_ours(a):
                    "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof_c.items()}}
 
     # ----- end to end through the public API with host buffers -----
-    h_spins = torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True)
-    h_logq = torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True)
-    h_logZR = torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)
+    # Every step: the step's input from pinned host memory (which Philox step
+    # and Adam t to run, into the captured step's device counter), the step,
+    # and the step's results read back to pinned host memory (samples, log q,
+    # log Z_R) with F_q / F_IS / stderr / log Z_IS per instance read on the
+    # host (model.free_energy).  With a captured step the outputs alternate
+    # between two captures of the step (two buffer sets), so step i's
+    # read-back runs on a copy stream while step i + 1 computes.
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     fe_last = None
-    h_ctr = torch.zeros(1, dtype=torch.int64, pin_memory=True)
-    t0 = time.perf_counter()
-    for i in range(a.e2e_steps):
-        if captured is not None:
-            # the step's input from the host: which Philox step (and Adam t) to run
-            h_ctr[0] = 10 ** 6 + i
-            captured.counter.copy_(h_ctr, non_blocking=True)
-            captured.replay()  # the captured step (public model.capture_train_step)
-        else:
-            step(10 ** 6 + i)
-        fe_last = model.free_energy(B, logZR, logq, stream)  # D2H of the per-instance results (syncs)
-        h_spins.copy_(spins, non_blocking=True)
-        h_logq.copy_(logq, non_blocking=True)
-        h_logZR.copy_(logZR, non_blocking=True)
+    if captured is not None:
+        db2 = torch.empty_like(dbeta)
+        dj2 = torch.empty_like(dJ)
+        slots = [captured, model.capture_train_step(B, seed, prec, 0.01, model.buffers(B), db2, dj2)]
+        cs = torch.cuda.Stream()
+        h_out = [(torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True),
+                  torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True),
+                  torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)) for _ in range(2)]
+        h_ctr = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        ran = [torch.cuda.Event() for _ in range(2)]
+        read = [torch.cuda.Event() for _ in range(2)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(a.e2e_steps + 1):
+            if i < a.e2e_steps:
+                j = i % 2
+                if i >= 2:
+                    stream.wait_event(read[j])  # slot j's buffers have been read back
+                h_ctr[j][0] = 10 ** 6 + i
+                slots[j].counter.copy_(h_ctr[j], non_blocking=True)
+                slots[j].replay()
+                ran[j].record(stream)
+            if i >= 1:
+                jp = (i - 1) % 2
+                sp_, lq_, lz_ = slots[jp].out
+                cs.wait_event(ran[jp])
+                fe_last = model.free_energy(B, lz_, lq_, cs)  # host read of the step's statistics
+                with torch.cuda.stream(cs):
+                    h_out[jp][0].copy_(sp_, non_blocking=True)
+                    h_out[jp][1].copy_(lq_, non_blocking=True)
+                    h_out[jp][2].copy_(lz_, non_blocking=True)
+                read[jp].record(cs)
+        cs.synchronize()
         stream.synchronize()
-    t_e2e = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
+        t_e2e = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
+    else:
+        h_spins = torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True)
+        h_logq = torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True)
+        h_logZR = torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(a.e2e_steps):
+            step(10 ** 6 + i)
+            fe_last = model.free_energy(B, logZR, logq, stream)  # D2H of the per-instance results (syncs)
+            h_spins.copy_(spins, non_blocking=True)
+            h_logq.copy_(logq, non_blocking=True)
+            h_logZR.copy_(logZR, non_blocking=True)
+            stream.synchronize()
+        t_e2e = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
     te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e = {"value": samples_step / float(te.item()), "unit": UNIT,
            "h2d_bytes_per_step": 8 if captured is not None else 8 * n_inst,
-           "path": "model.capture_train_step replay" if captured is not None else "model.train_step",
+           "path": ("model.capture_train_step replays (two buffer sets; read-back of step i beside step i + 1)"
+                    if captured is not None else "model.train_step"),
            "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 32 * n_inst)}
 
     # ----- per-kernel durations: the same step with the overlapped side-stream

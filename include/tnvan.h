@@ -182,8 +182,12 @@ int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
  *   h_out[4k+2] stderr   = std_b(l_b) / (beta sqrt(batch))   (ddof 1)
  *   h_out[4k+3] logZ_IS  =  logsumexp_b l_b - ln batch
  * reduced in FP64 on the device.  h_out: host double [4 * n_instances].
- * Synchronises `stream`.  Errors: TNVAN_E_ARG (batch < 1),
- * TNVAN_E_OVERFLOW (a non-finite l_b), TNVAN_E_CUDA. */
+ * Synchronises `stream`.  The reduction has a workspace of its own, so the
+ * call may run on one stream while a training step of the same context runs
+ * on another (e.g. the statistics of step i beside step i + 1, on separate
+ * output buffers); two tnvan_free_energy calls on one context must not
+ * overlap.  Errors: TNVAN_E_ARG (batch < 1), TNVAN_E_OVERFLOW (a non-finite
+ * l_b), TNVAN_E_CUDA. */
 int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR,
                       const float* d_logq, double* h_out, void* stream);
 

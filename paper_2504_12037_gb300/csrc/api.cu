@@ -756,14 +756,17 @@ int tnvan_create(tnvan_ctx** out, int device) {
   if (!ctx) return fail(nullptr, TNVAN_E_NOMEM, "host allocation failed");
   ctx->device = device;
   DeviceGuard g(device);
-  e = cudaMalloc(&ctx->d_status, (4 + TNVAN_MAX_INST) * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, (4 + TNVAN_MAX_INST) * sizeof(int));
+  // status words, then the reduction counters of the training path, then
+  // those of tnvan_free_energy (its own, so that it may run beside a step)
+  e = cudaMalloc(&ctx->d_status, (4 + 2 * TNVAN_MAX_INST) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, (4 + 2 * TNVAN_MAX_INST) * sizeof(int));
   if (e != cudaSuccess) {
     delete ctx;
     return fail(nullptr, TNVAN_E_NOMEM, "cudaMalloc(status): %s", cudaGetErrorString(e));
   }
   const size_t stats_doubles = 8 * TNVAN_MAX_INST + (size_t)TNVAN_MAX_INST * 64 * 6;
-  e = cudaMalloc(&ctx->d_stats, stats_doubles * sizeof(double));
+  e = cudaMalloc(&ctx->d_stats, 2 * stats_doubles * sizeof(double));  // training path | tnvan_free_energy
+  ctx->d_stats_fe = e == cudaSuccess ? ctx->d_stats + stats_doubles : nullptr;
   if (e != cudaSuccess) {
     delete ctx;
     return fail(nullptr, TNVAN_E_NOMEM, "cudaMalloc(stats): %s", cudaGetErrorString(e));
@@ -1555,11 +1558,13 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   {
     PROF("reduce", s);
-    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernels");
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats_fe, ctx->d_status + 4 + TNVAN_MAX_INST, s),
+       "reduce kernels");
   }
   const int n = li.n_inst;
   std::vector<double> st(8 * n);
-  CK(cudaMemcpyAsync(st.data(), ctx->d_stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "stats copy");
+  CK(cudaMemcpyAsync(st.data(), ctx->d_stats_fe, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+     "stats copy");
   int status[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(status, ctx->d_status, sizeof status, cudaMemcpyDeviceToHost, s), "status copy");
   CK(cudaStreamSynchronize(s), "stream sync");

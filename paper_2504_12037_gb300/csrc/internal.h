@@ -250,7 +250,8 @@ struct tnvan_ctx {
   int d_inst_cap = 0;
   bool dirty = true;                 // descriptors changed since last upload
   // workspaces (grown on demand, or by tnvan_reserve)
-  double* d_stats = nullptr;         // [n_inst][8]
+  double* d_stats = nullptr;         // [n_inst][8] + partial tuples (training path)
+  double* d_stats_fe = nullptr;      // the same for tnvan_free_energy (inside d_stats' allocation)
   int* d_status = nullptr;           // [4] device status words, then [TNVAN_MAX_INST] reduction counters
   size_t ws_bytes = 0;
   void* d_ws = nullptr;              // general workspace
