@@ -125,6 +125,12 @@ int check_inst(tnvan_ctx* ctx, int instance, bool allow_append) {
   return TNVAN_OK;
 }
 
+// strip_tab_floats_adj of the kernels: tables without d/dbeta rows.
+int strip_tab_floats_adj_host(int w, int L) {
+  int n = L * w * 4 + L * 4 * (1 << w) + 2 * L;
+  return (n + 3) & ~3;
+}
+
 int host_strip_tab_floats(int w, int L) {
   int n = L * w * 4 + 2 * L * 4 * (1 << w) + 2 * L;
   return (n + 3) & ~3;
@@ -299,6 +305,12 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     in.dev.strips = ds;
     in.dev.rows = dr;
     in.dev.edge_sign = dsg;
+    int tabn = 0;
+    for (const StripDev& sd : in.strip.strips) tabn += strip_tab_floats_adj_host(sd.w, sd.L);
+    std::vector<float> zt((size_t)std::max(tabn, 4), 0.f);
+    float* dt = nullptr;
+    if ((rc = upload(ctx, in, zt, &dt))) return rc;
+    in.dev.adj_tab = dt;
     in.dev.n_strips = (int)in.strip.strips.size();
   } else if (in.kind == 1) {
     float *jrw = nullptr, *jrr = nullptr;
@@ -1369,6 +1381,9 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
          "tensor-core sample kernel");
     }
     CK(cudaEventRecord(ctx->chunk_ev[c], ctx->side[c]), "chunk event");
+    // the chunk's strip tables need no samples: built while its sampler runs
+    CK(cudaStreamWaitEvent(ctx->side_lo[c], ctx->fork_ev, 0), "fork wait");
+    CK(launch_strip_tables(ctx->d_inst, la, k0, k1, ctx->side_lo[c]), "strip tables");
     CK(cudaStreamWaitEvent(ctx->side_lo[c], ctx->chunk_ev[c], 0), "chunk wait");
     PROF("strips_adj", ctx->side_lo[c]);
     CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
@@ -2240,6 +2255,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
       if (in.kind == 0) max_edges = std::max(max_edges, in.m);
     const int stride = (max_edges + 3) & ~3;
     if (d_dJ && (rc = ensure_dj_part(ctx, (size_t)la.tile_begin[la.n_inst] * stride))) return rc;
+    CK(launch_strip_tables(ctx->d_inst, la, 0, la.n_inst, s), "strip tables");
     PROF(d_dJ ? "strips_adj" : "strips_dbeta", s);
     CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
                          d_dJ ? ctx->d_dj_part : nullptr, stride, d_dJ, s, 0, -1, adj_ws),

@@ -154,6 +154,7 @@ struct InstDev {
   const StripDev* strips;
   const StripRow* rows;
   const float* edge_sign;  // gauge sign per edge (see HostStripPlan)
+  float* adj_tab;          // the adjoint's strip tables for the current beta (strips_tab_kernel)
   int strip_tab_floats;  // shared-memory floats for all strip tables
   // dense
   DenseDev dense;
@@ -289,6 +290,10 @@ cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int s
 int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);
+// The strip adjoint's tables (Boltzmann factors of every strip row at the
+// launch's betas) of instances [k0, k1), into each instance's adj_tab; the
+// adjoint kernels copy them instead of building them per CTA.
+cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int k0, int k1, cudaStream_t s);
 // Instances [k0, k1) (k1 < 0: all) of the launch.
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
                           const float* logq, double* stats, int* counters, cudaStream_t s, int k0 = 0,

@@ -109,6 +109,29 @@ __device__ void build_strip_tables(const InstDev& I, float beta, float* sm, int 
   }
 }
 
+// The adjoint's tables of instance I (built by strips_tab_kernel for this
+// launch's beta) into shared memory: n floats, a multiple of 4.
+__device__ __forceinline__ void copy_strip_tables(const InstDev& I, float* sm, int n, int t, int T) {
+  const float4* src = reinterpret_cast<const float4*>(I.adj_tab);
+  float4* dst = reinterpret_cast<float4*>(sm);
+  for (int e = t; e < n / 4; e += T) dst[e] = __ldg(src + e);
+}
+
+// One CTA per instance of [k0, k1): the adjoint's strip tables at the
+// instance's beta, into I.adj_tab (the layout the adjoint kernels use).
+__global__ void strips_tab_kernel(const InstDev* __restrict__ inst, const LaunchInfo li, int k0) {
+  const int k = blockIdx.x + k0;
+  const InstDev& I = inst[k];
+  if (I.kind != 0) return;
+  build_strip_tables(I, (float)li.beta[k], I.adj_tab, threadIdx.x, blockDim.x, false);
+}
+
+cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int k0, int k1, cudaStream_t s) {
+  if (k1 <= k0) return cudaSuccess;
+  strips_tab_kernel<<<k1 - k0, 256, 0, s>>>(d_inst, li, k0);
+  return cudaGetLastError();
+}
+
 // Apply [[1,t],[t,1]] (t = q.y) on bit c of the state index, and its
 // beta-derivative (dt/dbeta = q.w).
 template <int W, bool DB>
@@ -511,8 +534,8 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
   const int b0 = (gblk - li.tile_begin[k]) * T, b = b0 + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_row_bytes(D);
-  build_strip_tables(I, beta, sm, t, T, false);
   const int tabn = strip_tab_offset(I, I.n_strips, false);
+  copy_strip_tables(I, sm, tabn, t, T);
   int8_t* ssp = reinterpret_cast<int8_t*>(sm + tabn);
   float* lvs = sm + strip_adj_lv_offset(tabn, T, Dp);
   float* acc = lvs + lv_floats;
@@ -606,8 +629,8 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
   const int b0 = (gblk - li.tile_begin[k]) * 32, b = b0 + lane;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_row_bytes(D);
-  build_strip_tables(I, beta, sm, tid, NT, false);
   const int tabn = strip_tab_offset(I, I.n_strips, false);
+  copy_strip_tables(I, sm, tabn, tid, NT);
   int8_t* ssp = reinterpret_cast<int8_t*>(sm + tabn);
   float* lvs = sm + strip_adj_lv_offset(tabn, 32, Dp);
   float* acc = lvs + lv_floats;

@@ -145,3 +145,29 @@ def test_fused_train_step_matches_separate_calls(precision):
             y.copy_(x)  # the next step starts from one state (b's networks are views of b.params)
     assert a.t == b.t == 2
     assert not torch.equal(a.params, mk().params)  # Adam moved the registered parameters
+
+
+@pytest.mark.parametrize("config,n_inst,precision", [(3, None, tv.BF16), (4, None, tv.FP32), (5, 4, tv.BF16)])
+def test_train_step_matches_separate_calls_other_graphs(config, n_inst, precision):
+    # dense (SK), elimination (random regular) and mixed-size strip instances:
+    # the one-call step against the separate entry points, one step
+    w = wl.workload(config, n_inst) if n_inst else wl.workload(config)
+    from paper_2504_12037_gb300.model import TNVAN
+
+    n = len(w.graphs)
+    B = 300
+    mk = lambda: TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, seed=6)
+    a, b = mk(), mk()
+    dba = torch.empty(n * B, dtype=torch.float64, device="cuda")
+    dja = torch.empty(sum(a.n_edges), dtype=torch.float64, device="cuda")
+    dbb, djb = torch.empty_like(dba), torch.empty_like(dja)
+    outa, outb = a.buffers(B), b.buffers(B)
+    a.train_step(B, 5, 0, precision, 0.01, outa, dba, dja)
+    b.train_step_separate(B, 5, 0, precision, 0.01, outb, dbb, djb)
+    torch.cuda.synchronize()
+    for x, y in zip(outa, outb):
+        assert torch.equal(x, y)
+    assert torch.equal(dba, dbb)
+    assert torch.allclose(dja, djb, rtol=1e-12, atol=1e-12)
+    assert torch.equal(a.grad, b.grad)
+    assert torch.allclose(a.params, b.params, rtol=1e-6, atol=1e-9)
