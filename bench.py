@@ -59,6 +59,8 @@ def args_():
                          "(sample tile, strip tile, backward CTAs, adjoint tile, TC group, overlap 2=on 1=off)")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the captured step over per-instance batches 2^8 .. 2^18 (the asymptote)")
     return ap.parse_args()
 
 
@@ -429,6 +431,34 @@ def run_ours(a):
                                       "tc_sampler_group_steps": None if not model.tuned else model.tuned[4],
                                       "overlapped_schedule": None if not model.tuned else model.tuned[5] == 2},
     }
+    if a.sweep:
+        # samples/s of the whole captured step against the batch: per-instance
+        # batches 2^8 .. 2^18 (5 instances: 1,280 .. 1,310,720 samples per step),
+        # each autotuned, L2 flushed between replays
+        sweep = []
+        for lb in range(8, 19, 2):
+            Bs = 1 << lb
+            ms_ = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 3)
+            ms_.ctx.reserve(Bs)
+            ms_.ctx.autotune(ms_.betas, Bs, prec)
+            dbs = torch.empty(n_inst * Bs, dtype=torch.float64, device="cuda")
+            djs = torch.empty(sum(ms_.n_edges), dtype=torch.float64, device="cuda")
+            cap = ms_.capture_train_step(Bs, seed, prec, 0.01, ms_.buffers(Bs), dbs, djs)
+            for _ in range(3):
+                cap.replay()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(stream)
+                cap.replay()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+            sweep.append({"batch_per_instance": Bs, "samples_per_step": n_inst * Bs * world, "ms_per_step": t_ms,
+                          "value": n_inst * Bs * world / (t_ms / 1e3)})
+            del cap, ms_
+        out["sweep"] = sweep
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
         # the oracle's exact free energy of the lattice (single-site transfer matrix, 2^16 states)
