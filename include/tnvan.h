@@ -191,6 +191,29 @@ int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
 int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR,
                       const float* d_logq, double* h_out, void* stream);
 
+/* Observables from one batch (the paper notes that samples of the trained
+ * network give magnetisation, correlations and susceptibility, Sec. 3, and
+ * leaves correlation functions to future work, Sec. 4): with the
+ * self-normalised importance weights w_b = exp(l_b) / sum_b' exp(l_b'),
+ * l_b = log Z_R(s_b) - log q(s_b), which make averages over q estimates of
+ * Boltzmann averages, and the exact conditional energy of each sample,
+ * E_b = -d log Z_R(s_b) / d beta = E_1(s_b) + <E_2>_{r|s_b} (Eq. 4):
+ *   h_out[3k+0] U    = sum_b w_b E_b   (internal energy, importance-weighted)
+ *   h_out[3k+1] U_q  = mean_b E_b      (the same under q)
+ *   h_out[3k+2] ESS  = 1 / sum_b w_b^2 (effective sample size of the weights)
+ *   d_corr          device double [sum_k n_edges_k] out, or NULL: per edge
+ *                   sum_b w_b d log Z_R(s_b) / d J_e = beta sum_b w_b <s_i s_j>_{r|s_b}
+ *                   (instances back to back, input edge order); divide by
+ *                   beta for the bond correlation.  Strip instances only.
+ * h_out: host double [3 * n_instances].  FP32 contraction.  Uses the
+ * reduction workspace of tnvan_free_energy (do not overlap the two) and
+ * allocates a workspace of its own on growth.  Synchronises `stream`.
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_UNSUPPORTED (d_corr with a
+ * dense or elimination instance), TNVAN_E_NOMEM, TNVAN_E_CUDA. */
+int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                      const double* d_logZR, const float* d_logq, double* d_corr, double* h_out,
+                      void* stream);
+
 /* Eq. 10: REINFORCE gradient of F_q for every instance,
  *   grad = sum_b w_b grad_theta log q(s_b),  w_b = -(l_b - mean_b l) / (beta batch),
  * (the batch mean is the baseline; it leaves the expectation unchanged), by a

@@ -518,7 +518,7 @@ int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_
 int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                  int precision, double* d_logZR, double* d_dbeta, cudaStream_t s, bool strips = true);
 int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, int precision,
-                double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s);
+                double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s, const float* wmul = nullptr);
 int plan_strip_adjoint(tnvan_ctx* ctx, int batch, int* tile, int* smem, int* lv_floats, int* ws_threads);
 int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s);
 int sampler_pack_mask(const tnvan_ctx* ctx, int precision);
@@ -815,6 +815,7 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
   if (ctx->d_ws) cudaFree(ctx->d_ws);
+  if (ctx->d_obs) cudaFree(ctx->d_obs);
   if (ctx->d_dj_part) cudaFree(ctx->d_dj_part);
   delete ctx;
   return TNVAN_OK;
@@ -1596,6 +1597,50 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
   return TNVAN_OK;
 }
 
+int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                      const double* d_logZR, const float* d_logq, double* d_corr, double* h_out, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (!d_spins || !d_logZR || !d_logq || !h_out) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (d_corr)
+    for (const Instance& in : ctx->inst)
+      if (in.kind != 0)
+        return fail(ctx, TNVAN_E_UNSUPPORTED, "bond correlations are computed for strip instances only");
+  const int n = (int)ctx->inst.size();
+  const size_t nb = (size_t)n * batch;
+  const size_t bytes = nb * sizeof(double) + nb * sizeof(float) + 3 * (size_t)n * sizeof(double) + 64;
+  if (bytes > ctx->obs_bytes) {
+    if (ctx->d_obs) cudaFree(ctx->d_obs);
+    ctx->d_obs = nullptr;
+    ctx->obs_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_obs, bytes);
+    if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(observables): %s", cudaGetErrorString(e));
+    ctx->obs_bytes = bytes;
+  }
+  double* d_db = static_cast<double*>(ctx->d_obs);
+  double* d_sums = d_db + nb;
+  float* d_w = reinterpret_cast<float*>(d_sums + 3 * n);
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the importance weights need logZ_IS: the F_q reduction in
+  // tnvan_free_energy's own workspace
+  CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats_fe, ctx->d_status + 4 + TNVAN_MAX_INST, s),
+     "reduce kernels");
+  CK(launch_observables(li, d_logZR, d_logq, ctx->d_stats_fe, nullptr, d_w, nullptr, false, s), "weights kernel");
+  // per-sample energies (d/dbeta) and the weighted bond sums
+  if ((rc = run_adjoint(ctx, betas, batch, d_spins, TNVAN_FP32, nullptr, d_db, d_corr, s, d_w))) return rc;
+  CK(launch_observables(li, d_logZR, d_logq, ctx->d_stats_fe, d_db, d_w, d_sums, true, s), "energy kernel");
+  std::vector<double> sums(3 * n);
+  CK(cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "sums copy");
+  CK(cudaStreamSynchronize(s), "stream sync");
+  for (int k = 0; k < 3 * n; ++k) h_out[k] = sums[k];
+  return TNVAN_OK;
+}
+
 int tnvan_backward(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                    const double* d_logZR, const float* d_logq, int precision,
                    float* d_grad_params, double* d_dbeta, double* d_dJ, void* stream) {
@@ -2225,7 +2270,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
 // also log Z_R itself (strip instances from the adjoint's own forward sweep,
 // the other kinds from their contraction kernels).
 int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, int precision,
-                double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s) {
+                double* d_logZR, double* d_dbeta, double* d_dJ, cudaStream_t s, const float* wmul) {
   int rc;
   bool any_strip = false, other = false;
   for (const Instance& in : ctx->inst) {
@@ -2250,6 +2295,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if (adj_tile) {
     LaunchInfo la;
     if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
+    la.wmul = wmul;
     int max_edges = 0;
     for (const Instance& in : ctx->inst)
       if (in.kind == 0) max_edges = std::max(max_edges, in.m);

@@ -171,6 +171,7 @@ struct LaunchInfo {
   unsigned long long seed, step;
   int* status;  // device status word: nonzero after a bounded wait gave up
   const unsigned long long* step_dev;  // optional device step counter added to `step`
+  const float* wmul;  // optional per-sample multipliers [n_inst * batch] of the adjoint's bond sums
   double beta[TNVAN_MAX_INST];
   int tile_begin[TNVAN_MAX_INST + 1];
 };
@@ -261,6 +262,8 @@ struct tnvan_ctx {
   size_t grad_packed_floats = 0;
   float* d_dj_part = nullptr;        // d/dJ partial rows [CTA][max edges]
   size_t dj_part_floats = 0;
+  void* d_obs = nullptr;             // tnvan_observables: weights, d/dbeta, sums
+  size_t obs_bytes = 0;
 };
 
 namespace tnvan {
@@ -294,6 +297,11 @@ cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t*
 // launch's betas) of instances [k0, k1), into each instance's adj_tab; the
 // adjoint kernels copy them instead of building them per CTA.
 cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int k0, int k1, cudaStream_t s);
+// tnvan_observables: energies = false writes the importance-weight
+// multipliers B w_b into wmul (from the statistics' logZ_IS); energies = true
+// reduces dbeta and wmul to out[3k..3k+2] = U, U_q, effective sample size.
+cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const float* logq, const double* stats,
+                               const double* dbeta, float* wmul, double* out, bool energies, cudaStream_t s);
 // Instances [k0, k1) (k1 < 0: all) of the launch.
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
                           const float* logq, double* stats, int* counters, cudaStream_t s, int k0 = 0,

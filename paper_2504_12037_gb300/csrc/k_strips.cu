@@ -358,7 +358,8 @@ __device__ __forceinline__ int transpose_slot(int lane) {
 }
 
 // Backward sweep of one strip for one sample (all 32 lanes of the warp take
-// part; `valid` zeroes the contribution of padding samples).  Adds each
+// part; the sample's bond values enter the sums times wv: 1, a caller's
+// weight, or 0 for padding samples).  Adds each
 // bond's local expectation to the warp's accumulators and returns
 // d ln Z_strip / d beta = sum_e J_e <.>_e: every Boltzmann weight depends on
 // beta only through beta J_e, so the same expectations give the beta
@@ -379,7 +380,7 @@ __device__ __forceinline__ int transpose_slot(int lane) {
 // kept in registers for the next iteration.
 template <int W>
 __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict__ rows, int L,
-                                 const int8_t* srow, const float* lvs, int t, int T, bool valid, float* accw,
+                                 const int8_t* srow, const float* lvs, int t, int T, float wv, float* accw,
                                  int lane) {
   constexpr int NX = 1 << W;
   constexpr int NB = 2 * W + 1;
@@ -489,7 +490,7 @@ __device__ float strip_backsweep(const StripTab& tb, const StripRow* __restrict_
 #pragma unroll
     for (int j = 0; j < NB; ++j) dJb = fmaf(Js[j], val[j], dJb);
     dlog = fmaf(dJb, iz, dlog);
-    const float vz = valid ? iz : 0.f;
+    const float vz = wv * iz;
 #pragma unroll
     for (int j = 0; j < NB; ++j) val[j] *= vz;
     int vi;
@@ -546,6 +547,9 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
   for (int e = n_valid * Dp + t; e < T * Dp; e += T) ssp[e] = 1;  // padding rows
   __syncthreads();
   const bool valid = b < li.batch;
+  // this sample's weight in the bond sums: 1, or the caller's multiplier
+  // (importance weights of tnvan_observables); 0 for padding samples
+  const float wv = !valid ? 0.f : (li.wmul ? li.wmul[(long long)k * li.batch + b] : 1.f);
   const int8_t* srow = ssp + t * Dp;
   float* accw = acc + (t >> 5) * ne;
   double dl = 0.0, lz = 0.0, chat = 0.0;
@@ -559,19 +563,19 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
     switch (sd.w) {
       case 1:
         strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
         break;
       case 2:
         strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
         break;
       case 3:
         strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
         break;
       default:
         strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, t, T, valid, accw, lane);
+        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
         break;
     }
     dl += d;
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
         const EdgeWW q = I.ww[e0 + j];
         const float ss = (float)(srow[q.a] * srow[q.b]);
         e1 = fmaf(q.J, ss, e1);
-        if (valid) val[j] = ss;
+        val[j] = ss * wv;
       }
     }
     int vi;
@@ -599,6 +603,7 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
   if (dbeta && valid) dbeta[(long long)k * li.batch + b] = dl + (double)e1;
   if (logZR && valid) logZR[(long long)k * li.batch + b] = lz + li.beta[k] * (chat + (double)e1);
   __syncthreads();
+  if (!part) return;  // d/dbeta only: no bond sums wanted
   const float scale = beta / (float)li.batch;
   float* row = part + (long long)gblk * part_stride;
   for (int e = t; e < ne; e += T) {
@@ -643,6 +648,9 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
   for (int e = n_valid * Dp + tid; e < 32 * Dp; e += NT) ssp[e] = 1;  // padding rows
   __syncthreads();
   const bool valid = b < li.batch;
+  // this sample's weight in the bond sums: 1, or the caller's multiplier
+  // (importance weights of tnvan_observables); 0 for padding samples
+  const float wv = !valid ? 0.f : (li.wmul ? li.wmul[(long long)k * li.batch + b] : 1.f);
   const int8_t* srow = ssp + lane * Dp;
   float* accw = acc + st * ne;
   if (st < I.n_strips) {
@@ -654,19 +662,19 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
     switch (sd.w) {
       case 1:
         strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
         break;
       case 2:
         strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
         break;
       case 3:
         strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
         break;
       default:
         strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, tid, NT, valid, accw, lane);
+        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
         break;
     }
     pl[st * 32 + lane] = l;
@@ -680,7 +688,7 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
       val[j] = 0.f;
       if (valid && e0 + j < I.n_ww) {
         const EdgeWW q = I.ww[e0 + j];
-        val[j] = (float)(srow[q.a] * srow[q.b]);
+        val[j] = (float)(srow[q.a] * srow[q.b]) * wv;
       }
     }
     int vi;
@@ -703,6 +711,7 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
     if (dbeta) dbeta[(long long)k * li.batch + b] = dl + (double)e1;
     if (logZR) logZR[(long long)k * li.batch + b] = lz + li.beta[k] * (chat + (double)e1);
   }
+  if (!part) return;  // d/dbeta only: no bond sums wanted
   const float scale = beta / (float)li.batch;
   float* row = part + (long long)gblk * part_stride;
   for (int e = tid; e < ne; e += NT) {

@@ -613,6 +613,62 @@ cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, cons
   return cudaGetLastError();
 }
 
+// Importance weights of tnvan_observables as multipliers B w_b =
+// exp(l_b - logZ_IS), w_b = exp(l_b) / sum_b' exp(l_b') (self-normalised;
+// logZ_IS = logsumexp_b l_b - ln B from the F_q reduction's statistics).
+__global__ void obs_weights_kernel(const LaunchInfo li, const double* __restrict__ logZR,
+                                   const float* __restrict__ logq, const double* __restrict__ stats,
+                                   float* __restrict__ wmul) {
+  const int k = blockIdx.y;
+  const double lz = stats[8 * k + 3];
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < li.batch; b += gridDim.x * blockDim.x) {
+    const long long o = (long long)k * li.batch + b;
+    wmul[o] = (float)exp(logZR[o] - (double)logq[o] - lz);
+  }
+}
+
+// Per instance (one CTA each): sum_b m_b E_b, sum_b E_b and sum_b m_b^2 with
+// E_b = -dbeta_b and m_b the multipliers above, in a fixed order (FP64).
+__global__ void obs_energy_kernel(const LaunchInfo li, const double* __restrict__ dbeta,
+                                  const float* __restrict__ wmul, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double a = 0.0, e = 0.0, q = 0.0;
+  for (int b = threadIdx.x; b < li.batch; b += blockDim.x) {
+    const long long o = (long long)k * li.batch + b;
+    const double E = -dbeta[o], m = (double)wmul[o];
+    a += m * E;
+    e += E;
+    q += m * m;
+  }
+  __shared__ double red[3][256];
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = e;
+  red[2][threadIdx.x] = q;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int j = 0; j < 3; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double B = (double)li.batch;
+    out[3 * k + 0] = red[0][0] / B;      // U  = sum_b w_b E_b
+    out[3 * k + 1] = red[1][0] / B;      // U_q = mean_b E_b
+    out[3 * k + 2] = B * B / red[2][0];  // effective sample size 1 / sum_b w_b^2
+  }
+}
+
+cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const float* logq, const double* stats,
+                               const double* dbeta, float* wmul, double* out, bool energies, cudaStream_t s) {
+  if (li.n_inst == 0 || li.batch == 0) return cudaSuccess;
+  if (!energies) {
+    obs_weights_kernel<<<dim3(32, li.n_inst), 256, 0, s>>>(li, logZR, logq, stats, wmul);
+    return cudaGetLastError();
+  }
+  obs_energy_kernel<<<li.n_inst, 256, 0, s>>>(li, dbeta, wmul, out);
+  return cudaGetLastError();
+}
+
 // REINFORCE weights w_b = -(l_b - mean_b l) / (beta B) per instance (Eq. 10
 // with the batch-mean baseline), FP32 copy for the tensor-core backward.
 __global__ void reinforce_w_kernel(const LaunchInfo li, const double* __restrict__ logZR,

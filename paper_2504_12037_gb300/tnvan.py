@@ -42,6 +42,7 @@ SIGNATURES = {
                                                _vp, _vp]),
     "tnvan_train_step": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
+    "tnvan_observables": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _vp, _dblp, _vp]),
     "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp]),
     "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
@@ -189,6 +190,16 @@ class Context:
         b, pb = _arr(betas, np.float64)
         self._check(lib().tnvan_contract(self._h, pb, batch, _ptr(spins), precision, _ptr(logZR),
                                          _ptr(dlogZR_dbeta), _stream(stream)))
+
+    def observables(self, betas, batch: int, spins, logZR, logq, corr=None, stream=None) -> np.ndarray:
+        """[n_inst, 3]: importance-weighted internal energy U, its mean under q,
+        and the weights' effective sample size; with `corr` (device double
+        [sum n_edges]) also the weighted beta * <s_i s_j> per edge."""
+        b, pb = _arr(betas, np.float64)
+        out = np.zeros(3 * len(b))
+        self._check(lib().tnvan_observables(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq), _ptr(corr),
+                                            out.ctypes.data_as(_dblp), _stream(stream)))
+        return out.reshape(len(b), 3)
 
     def free_energy(self, betas, batch: int, logZR, logq, stream=None) -> np.ndarray:
         b, pb = _arr(betas, np.float64)

@@ -145,6 +145,14 @@ def test_fused_train_step_matches_separate_calls(precision):
             y.copy_(x)  # the next step starts from one state (b's networks are views of b.params)
     assert a.t == b.t == 2
     assert not torch.equal(a.params, mk().params)  # Adam moved the registered parameters
+    # the combined pass with d/dbeta only (no d/dJ) gives the same per-sample values
+    sp1, lq1, lz1 = a.buffers(B)
+    a.ctx.sample_contract_adjoint(a.betas, B, 21, 7, precision, sp1, lq1, lz1, dba, dja)
+    sp2, lq2, lz2 = a.buffers(B)
+    db_only = torch.empty_like(dba)
+    a.ctx.sample_contract_adjoint(a.betas, B, 21, 7, precision, sp2, lq2, lz2, db_only, None)
+    torch.cuda.synchronize()
+    assert torch.equal(sp1, sp2) and torch.equal(lz1, lz2) and torch.equal(dba, db_only)
 
 
 @pytest.mark.parametrize("config,n_inst,precision", [(3, None, tv.BF16), (4, None, tv.FP32), (5, 4, tv.BF16)])

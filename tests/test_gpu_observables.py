@@ -1,0 +1,97 @@
+"""GPU parity of tnvan_observables (importance-weighted internal energy and
+bond correlations from one batch) against the FP64 oracle, through the
+C-ABI.  Samples and log q are seeded inputs; the oracle contracts every
+sample exactly and differentiates it with autograd."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import transfer
+from paper_2504_12037_gb300 import tnvan as tv
+from paper_2504_12037_gb300 import workloads as wl
+
+from gpu_helpers import to_dev_spins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape", [0, 1, 32, 128])
+def test_observables_match_oracle(shape):
+    # strips of width 1-4, 20 rows, a ragged batch of 40 rows
+    Lx, Ly, beta, batch = 14, 20, 0.7, 40
+    g = wl.lattice(Lx, Ly, "gauss", seed=93)
+    W = wl.width_columns(Lx, Ly, [1, 4, 8, 13])
+    from paper_2504_12037_gb300.model import TNVAN
+
+    model = TNVAN([g], [W], [32, 32], [beta], seed=5)
+    model.ctx.set_tuning((0, 0, 0, shape, 0, 0))
+    D = len(W)
+    rng = np.random.default_rng(23)
+    s = np.where(rng.random((batch, D)) < 0.5, 1.0, -1.0)
+    lq = rng.normal(-D * np.log(2.0), 3.0, size=batch).astype(np.float32)
+    # oracle: exact log Z_R per sample, self-normalised weights, d/dbeta and
+    # the weighted d/dJ by autograd
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    Jt = torch.tensor(g.J, dtype=torch.float64, requires_grad=True)
+    lz = transfer.log_zr_lattice(g.n, g.ei, g.ej, Jt, bt, W, torch.as_tensor(s), g.Lx)
+    l = lz.detach() - torch.as_tensor(lq, dtype=torch.float64)
+    wts = torch.softmax(l, 0)
+    db = torch.stack([torch.autograd.grad(lz[b], bt, retain_graph=True)[0] for b in range(batch)])
+    (corr_ref,) = torch.autograd.grad((wts * lz).sum(), Jt)
+    E = -db
+    U_ref, Uq_ref, ess_ref = float((wts * E).sum()), float(E.mean()), float(1.0 / (wts ** 2).sum())
+    # GPU
+    d_spins = to_dev_spins(s.reshape(-1))
+    logZR = torch.empty(batch, dtype=torch.float64, device="cuda")
+    model.ctx.contract(model.betas, batch, d_spins, tv.FP32, logZR)
+    logq = torch.as_tensor(lq).cuda()
+    corr = torch.full((g.m,), float("nan"), dtype=torch.float64, device="cuda")
+    out = model.ctx.observables(model.betas, batch, d_spins, logZR, logq, corr)
+    torch.cuda.synchronize()
+    U, Uq, ess = out[0]
+    assert abs(U - U_ref) <= 2e-5 * abs(U_ref)
+    assert abs(Uq - Uq_ref) <= 2e-5 * abs(Uq_ref)
+    assert abs(ess - ess_ref) <= 1e-4 * ess_ref
+    assert 1.0 <= ess <= batch
+    assert float((corr.cpu() - corr_ref).abs().max()) <= 2e-5 * max(1.0, float(corr_ref.abs().max()))
+    # energies alone are the same numbers
+    out2 = model.ctx.observables(model.betas, batch, d_spins, logZR, logq)
+    torch.cuda.synchronize()
+    assert np.array_equal(out, out2)
+
+
+def test_observables_uniform_weights_reduce_to_batch_means():
+    # equal l_b (log q = log Z_R) make every weight 1/B: U = U_q, ESS = B, and
+    # the weighted d/dJ equals tnvan_backward's batch-mean d/dJ
+    w = wl.workload(2)
+    from paper_2504_12037_gb300.model import TNVAN
+
+    model = TNVAN(w.graphs[:2], w.widths_sets[:2], w.hidden, w.betas[:2], seed=8)
+    B = 500
+    spins, logq, logZR = model.sample(B, 4, 2, tv.FP32)
+    lq_eq = logZR.float()  # l_b = 0 up to the FP32 rounding of log q
+    corr = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
+    out = model.ctx.observables(model.betas, B, spins, logZR, lq_eq, corr)
+    grad = torch.empty_like(model.params)
+    dJ = torch.empty_like(corr)
+    model.ctx.backward(model.betas, B, spins, logZR, lq_eq, tv.FP32, grad, None, dJ)
+    torch.cuda.synchronize()
+    for k in range(2):
+        U, Uq, ess = out[k]
+        assert abs(U - Uq) <= 1e-3 * abs(Uq)
+        assert abs(ess - B) <= 1e-2 * B
+    assert float((corr - dJ).abs().max()) <= 1e-3 * float(dJ.abs().max())
+
+
+def test_observables_reject_correlations_for_dense_instances():
+    w = wl.workload(3)
+    from paper_2504_12037_gb300.model import TNVAN
+
+    model = TNVAN(w.graphs[:1], w.widths_sets[:1], w.hidden, w.betas[:1], seed=2)
+    B = 64
+    spins, logq, logZR = model.sample(B, 1, 1, tv.FP32)
+    corr = torch.empty(model.n_edges[0], dtype=torch.float64, device="cuda")
+    with pytest.raises(tv.TnvanError):
+        model.ctx.observables(model.betas, B, spins, logZR, logq, corr)
+    out = model.ctx.observables(model.betas, B, spins, logZR, logq)  # energies are supported
+    assert np.all(np.isfinite(out))

@@ -250,6 +250,11 @@ def test_strip_adjoint_all_widths_tall_strips(shape):
     model.ctx.backward(model.betas, batch, d_spins, logZR, logq, tv.FP32, grad, None, dJ2)
     torch.cuda.synchronize()
     assert torch.equal(dJ, dJ2)
+    # and d/dbeta alone: the same per-sample values, no bond sums written
+    db2 = torch.empty_like(dbeta)
+    model.ctx.backward(model.betas, batch, d_spins, logZR, logq, tv.FP32, grad, db2, None)
+    torch.cuda.synchronize()
+    assert torch.equal(dbeta, db2)
 
 
 def test_full_size_launch_sampled_rows():
