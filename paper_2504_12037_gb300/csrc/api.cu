@@ -367,6 +367,21 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     g.fld = fld;
     g.fldJ = fj;
     g.c_hat = in.g_chat;
+    int *ct = nullptr, *bp = nullptr, *tc = nullptr;
+    if ((rc = upload(ctx, in, in.gctab, &ct))) return rc;
+    if ((rc = upload(ctx, in, in.gbpos, &bp))) return rc;
+    if ((rc = upload(ctx, in, in.gtabc, &tc))) return rc;
+    g.ctab = ct;
+    g.bpos = bp;
+    g.tabc = tc;
+    g.n_tabc = (int)in.gtabc.size();
+    g.n_tab = in.g_ntab;
+    g.tab_lz = g.tab_db = nullptr;
+    if (in.g_ntab > 0) {
+      std::vector<double> zt((size_t)in.g_ntab, 0.0);
+      if ((rc = upload(ctx, in, zt, &g.tab_lz))) return rc;
+      if ((rc = upload(ctx, in, zt, &g.tab_db))) return rc;
+    }
   }
   return TNVAN_OK;
 }
@@ -2259,6 +2274,14 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     LaunchInfo lg;
     if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
     lg.seed = (unsigned long long)arena | ((unsigned long long)pairs << 32);
+    // components with small boundaries: tables when they are smaller than the batch
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 2 && in.g_ntab > 0 && in.g_ntab <= batch)
+        lg.gen_tab = std::max(lg.gen_tab, in.g_ntab);
+    if (lg.gen_tab > 0) {
+      PROF("general_tables", s);
+      CK(launch_general_tables(ctx->d_inst, lg, sm, d_dbeta != nullptr, s), "general tables kernel");
+    }
     PROF(d_dbeta ? "general_dbeta" : "general", s);
     CK(launch_general(ctx->d_inst, lg, sm, d_spins, d_logZR, d_dbeta, nullptr, s), "general kernel");
   }
@@ -2400,7 +2423,8 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     adj[in.ej[e]].push_back({in.ei[e], e});
   }
   std::vector<int> prog{(int)comps.size()};
-  std::vector<int> fld, pairE, step_off, comp_step0;
+  std::vector<int> fld, pairE, step_off, comp_step0, ctab, bpos, tabc;
+  int n_tab = 0;
   std::vector<float> fldJ, pairJ;
   int max_steps = 0;
   double chat = 0;
@@ -2466,6 +2490,24 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     std::set<std::pair<int, int>> edges_left;
     for (auto& kv : pair_of) edges_left.insert(kv.first);
     const size_t hdr = prog.size();
+    // the component's width-set boundary; tabulated when small
+    {
+      std::set<int> bset;
+      for (int i = 0; i < n; ++i)
+        for (int f = fb[i]; f < fb[i] + fc[i]; ++f) bset.insert(fld[2 * f]);
+      const int kb = (int)bset.size();
+      const int toff = kb <= TNVAN_TAB_MAX_K ? n_tab : -1;
+      if (toff >= 0) {
+        n_tab += 1 << kb;
+        tabc.push_back((int)ctab.size() / 5);
+      }
+      ctab.push_back((int)hdr);
+      ctab.push_back(0);  // program end, patched below
+      ctab.push_back(kb);
+      ctab.push_back((int)bpos.size());
+      ctab.push_back(toff);
+      bpos.insert(bpos.end(), bset.begin(), bset.end());
+    }
     comp_step0.push_back((int)step_off.size());
     max_steps = std::max(max_steps, n);
     prog.push_back(n);
@@ -2520,6 +2562,7 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     }
     prog[hdr + 1] = arena;
     prog[hdr + 2] = last_off;
+    ctab[ctab.size() - 4] = (int)prog.size();
     arena_max = std::max(arena_max, (arena + 3) & ~3);  // keeps the float4 pair table aligned
   }
   comp_step0.push_back((int)step_off.size());
@@ -2536,6 +2579,10 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
   in.g_max_entries = arena_max;
   in.g_chat = chat;
   in.max_width = width_max;
+  in.gctab.swap(ctab);
+  in.gbpos.swap(bpos);
+  in.gtabc.swap(tabc);
+  in.g_ntab = n_tab;
   in.kind = 2;
   return TNVAN_OK;
 }

@@ -139,7 +139,18 @@ struct GenDev {
   const int* fld;        // per R spin: W-neighbour list (pos, edge id) packed
   const float* fldJ;
   double c_hat;          // constant log-offset / beta
+  // components with at most TNVAN_TAB_MAX_K width-set neighbours can be
+  // tabulated: log Z_c (and d/dbeta) over every boundary configuration
+  const int* ctab;       // [n_comp][5]: program header, program end, k, boundary list offset,
+                         // table offset (-1: not tabulated)
+  const int* bpos;       // boundary lists (AR positions of the W neighbours), bit j of the index = spin j
+  const int* tabc;       // the tabulated components
+  int n_tabc;
+  int n_tab;             // entries of all tables (sum of 2^k)
+  double* tab_lz;        // [n_tab] log Z_c at the current call's beta (general_tab_kernel)
+  double* tab_db;        // [n_tab] its beta-derivative
 };
+#define TNVAN_TAB_MAX_K 12
 
 struct InstDev {
   int kind;  // 0 strips, 1 dense, 2 general
@@ -172,6 +183,7 @@ struct LaunchInfo {
   int* status;  // device status word: nonzero after a bounded wait gave up
   const unsigned long long* step_dev;  // optional device step counter added to `step`
   const float* wmul;  // optional per-sample multipliers [n_inst * batch] of the adjoint's bond sums
+  int gen_tab;        // elimination instances: > 0 = build and use the component tables (the largest n_tab)
   double beta[TNVAN_MAX_INST];
   int tile_begin[TNVAN_MAX_INST + 1];
 };
@@ -207,6 +219,8 @@ struct Instance {
   // general
   std::vector<int> gprog, gfld, gpairE, gstep_off, gcomp_step0;
   int g_max_steps = 0;
+  std::vector<int> gctab, gbpos, gtabc;  // component tables (GenDev)
+  int g_ntab = 0;
   std::vector<float> gpairJ, gfldJ;
   int g_ncomp = 0, g_max_entries = 0, g_npairs = 0;
   double g_chat = 0;
@@ -340,6 +354,8 @@ cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a
 
 int sample_smem_bytes(const Instance& in, int tile);
 int general_smem_bytes(int arena, int pairs, int D, int T, bool db);
+cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
+                                  cudaStream_t s);
 int strip_smem_bytes(const Instance& in, int tile);
 int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats);
 int strip_adj_lv_floats(const Instance& in, int tile);

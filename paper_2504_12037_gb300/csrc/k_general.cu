@@ -22,6 +22,83 @@ __device__ __forceinline__ int padded_bytes(int D) {
   return 4 * w4;
 }
 
+// One component's program (starting at its header P[ip]) for this thread's
+// spin row s: adds its log Z_c (and with DB its beta-derivative) to lz / dl
+// and returns the offset just past the program.
+template <bool DB>
+__device__ __forceinline__ int run_component(const GenDev& G, const int* P, int ip, const int8_t* s, float* A,
+                                             float* dA, const float4* pt, int T, int t, float beta, double& lz,
+                                             double& dl) {
+  const int nsteps = P[ip], fin = P[ip + 2];
+  ip += 3;
+  for (int st = 0; st < nsteps; ++st) {
+    const int fb = P[ip + 1], fc = P[ip + 2], m = P[ip + 3], out = P[ip + 4];
+    const int nin = P[ip + 5], npair = P[ip + 6];
+    ip += 7;
+    const int in0 = ip;
+    int q = ip;
+    for (int i = 0; i < nin; ++i) q += 2 + P[q + 1];
+    const int pq = q;
+    ip = q + 2 * npair;
+    float h = 0.f;
+    for (int f = fb; f < fb + fc; ++f) h = fmaf(G.fldJ[f], (float)s[G.fld[2 * f]], h);
+    const float ah = fabsf(h);
+    lz += (double)beta * (double)ah;
+    if (DB) dl += (double)ah;
+    const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
+    const float fr[2] = {h - ah, -h - ah};
+    float mx = 0.f;
+    for (int x = 0; x < (1 << m); ++x) {
+      float acc = 0.f, dacc = 0.f;
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        float p = fv[sg], r = fr[sg];
+        const int ext = x | (sg << m);
+        for (int j = 0; j < npair; ++j) {
+          const float4 ab = pt[P[pq + 2 * j]];
+          const bool same = ((x >> P[pq + 2 * j + 1]) & 1) == sg;
+          p *= same ? ab.x : ab.y;
+          r += same ? ab.z : ab.w;
+        }
+        int qq = in0;
+        for (int i = 0; i < nin; ++i) {
+          const int off = P[qq], kk = P[qq + 1];
+          int idx = 0;
+          for (int j = 0; j < kk; ++j) idx |= ((ext >> P[qq + 2 + j]) & 1) << j;
+          const float val = A[(off + idx) * T + t];
+          p *= val;
+          if (DB) r += dA[(off + idx) * T + t] / val;
+          qq += 2 + kk;
+        }
+        acc += p;
+        if (DB) dacc = fmaf(p, r, dacc);
+      }
+      A[(out + x) * T + t] = acc;
+      if (DB) dA[(out + x) * T + t] = dacc;
+      mx = fmaxf(mx, acc);
+    }
+    const int e = exponent_of(mx);
+    const float sc = pow2i(-e);
+    for (int x = 0; x < (1 << m); ++x) {
+      A[(out + x) * T + t] *= sc;
+      if (DB) dA[(out + x) * T + t] *= sc;
+    }
+    lz += (double)e * 0.69314718055994530942;
+  }
+  const float z = A[fin * T + t];
+  lz += (double)logf(z);
+  if (DB) dl += (double)(dA[fin * T + t] / z);
+  return ip;
+}
+
+// Boundary index of component c for spin row s: bit j set iff its j-th
+// width-set neighbour (ctab boundary list) is -1.
+__device__ __forceinline__ int boundary_index(const GenDev& G, const int* cr, const int8_t* s) {
+  int idx = 0;
+  for (int j = 0; j < cr[2]; ++j) idx |= (s[G.bpos[cr[3] + j]] < 0 ? 1 : 0) << j;
+  return idx;
+}
+
 template <bool DB>
 __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__ inst,
                                                      const LaunchInfo li, int arena_floats,
@@ -55,69 +132,20 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
   if (b >= li.batch) return;
   const int8_t* s = ssp + t * Dp;
   const int* P = G.prog;
-  int ip = 1;
+  const bool tab = li.gen_tab && G.n_tab > 0 && G.n_tab <= li.batch;  // tables built for this call
   double lz = 0.0, dl = 0.0;
   const int ncomp = P[0];
+  int ip = 1;
   for (int c = 0; c < ncomp; ++c) {
-    const int nsteps = P[ip], fin = P[ip + 2];
-    ip += 3;
-    for (int st = 0; st < nsteps; ++st) {
-      const int fb = P[ip + 1], fc = P[ip + 2], m = P[ip + 3], out = P[ip + 4];
-      const int nin = P[ip + 5], npair = P[ip + 6];
-      ip += 7;
-      const int in0 = ip;
-      int q = ip;
-      for (int i = 0; i < nin; ++i) q += 2 + P[q + 1];
-      const int pq = q;
-      ip = q + 2 * npair;
-      float h = 0.f;
-      for (int f = fb; f < fb + fc; ++f) h = fmaf(G.fldJ[f], (float)s[G.fld[2 * f]], h);
-      const float ah = fabsf(h);
-      lz += (double)beta * (double)ah;
-      if (DB) dl += (double)ah;
-      const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
-      const float fr[2] = {h - ah, -h - ah};
-      float mx = 0.f;
-      for (int x = 0; x < (1 << m); ++x) {
-        float acc = 0.f, dacc = 0.f;
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-          float p = fv[sg], r = fr[sg];
-          const int ext = x | (sg << m);
-          for (int j = 0; j < npair; ++j) {
-            const float4 ab = pt[P[pq + 2 * j]];
-            const bool same = ((x >> P[pq + 2 * j + 1]) & 1) == sg;
-            p *= same ? ab.x : ab.y;
-            r += same ? ab.z : ab.w;
-          }
-          int qq = in0;
-          for (int i = 0; i < nin; ++i) {
-            const int off = P[qq], kk = P[qq + 1];
-            int idx = 0;
-            for (int j = 0; j < kk; ++j) idx |= ((ext >> P[qq + 2 + j]) & 1) << j;
-            const float val = A[(off + idx) * T + t];
-            p *= val;
-            if (DB) r += dA[(off + idx) * T + t] / val;
-            qq += 2 + kk;
-          }
-          acc += p;
-          if (DB) dacc = fmaf(p, r, dacc);
-        }
-        A[(out + x) * T + t] = acc;
-        if (DB) dA[(out + x) * T + t] = dacc;
-        mx = fmaxf(mx, acc);
-      }
-      const int e = exponent_of(mx);
-      const float sc = pow2i(-e);
-      for (int x = 0; x < (1 << m); ++x) {
-        A[(out + x) * T + t] *= sc;
-        if (DB) dA[(out + x) * T + t] *= sc;
-      }
-      lz += (double)e * 0.69314718055994530942;
+    const int* cr = G.ctab + 5 * c;
+    if (tab && cr[4] >= 0) {  // a tabulated component: one lookup
+      const int x = boundary_index(G, cr, s);
+      lz += G.tab_lz[cr[4] + x];
+      if (DB) dl += G.tab_db[cr[4] + x];
+      ip = cr[1];
+    } else {
+      ip = run_component<DB>(G, P, ip, s, A, dA, pt, T, t, beta, lz, dl);
     }
-    const float z = A[fin * T + t];
-    lz += (double)logf(z);
-    if (DB) dl += (double)(dA[fin * T + t] / z);
   }
   float e1 = 0.f;
   for (int e = 0; e < I.n_ww; ++e) {
@@ -128,6 +156,58 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
   const long long o = (long long)k * li.batch + b;
   if (logZR) logZR[o] = lz + li.beta[k] * (chf + (double)e1);
   if (DB) dbeta[o] = dl + chf + (double)e1;
+}
+
+// The tables of the tabulated components (at most TNVAN_TAB_MAX_K width-set
+// neighbours, f1 of the build's next rows): thread g of instance k takes
+// entry g of the concatenated tables, i.e. one component c and one boundary
+// configuration x, sets the boundary spins of a spin row from the bits of x
+// (the other spins do not enter c) and runs c's program alone, so that
+// tab_lz[toff_c + x] = log Z_c and tab_db[..] its beta-derivative.  Built
+// per call (they depend on beta) when they are smaller than the batch.
+template <bool DB>
+__global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                         int arena_floats, int max_pairs) {
+  extern __shared__ float sm[];
+  const int k = blockIdx.y;
+  const InstDev& I = inst[k];
+  if (I.kind != 2) return;
+  const GenDev& G = I.gen;
+  if (G.n_tab == 0 || G.n_tab > li.batch) return;
+  const int T = blockDim.x, t = threadIdx.x;
+  const int g = blockIdx.x * T + t;
+  const float beta = (float)li.beta[k];
+  const int D = I.D, Dp = padded_bytes(D);
+  float* A = sm;
+  float* dA = A + arena_floats * T;
+  float4* pt = reinterpret_cast<float4*>(dA + (DB ? arena_floats * T : 0));
+  int8_t* ssp = reinterpret_cast<int8_t*>(pt + max_pairs);
+  for (int p = t; p < G.n_pairs; p += T) {
+    const float J = G.pairJ[p], aj = fabsf(J);
+    const float tt = expf(-2.f * beta * aj);
+    pt[p] = J >= 0.f ? make_float4(1.f, tt, 0.f, -2.f * aj) : make_float4(tt, 1.f, -2.f * aj, 0.f);
+  }
+  int8_t* s = ssp + t * Dp;
+  for (int j = 0; j < D; ++j) s[j] = 1;
+  __syncthreads();
+  if (blockIdx.x * T >= G.n_tab || g >= G.n_tab) return;
+  // which tabulated component and configuration
+  int c = -1, x = 0;
+  for (int j = 0; j < G.n_tabc; ++j) {
+    const int* cr = G.ctab + 5 * G.tabc[j];
+    if (g >= cr[4] && g < cr[4] + (1 << cr[2])) {
+      c = G.tabc[j];
+      x = g - cr[4];
+      break;
+    }
+  }
+  if (c < 0) return;
+  const int* cr = G.ctab + 5 * c;
+  for (int j = 0; j < cr[2]; ++j) s[G.bpos[cr[3] + j]] = ((x >> j) & 1) ? -1 : 1;
+  double lz = 0.0, dl = 0.0;
+  run_component<DB>(G, G.prog, cr[0], s, A, dA, pt, T, t, beta, lz, dl);
+  G.tab_lz[g] = lz;
+  if (DB) G.tab_db[g] = dl;
 }
 
 // ---------------------------------------------------------------------------
@@ -327,6 +407,26 @@ cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int s
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   general_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
+  return cudaGetLastError();
+}
+
+// The components' tables at this call's betas (li.gen_tab: the largest
+// table; general_kernel then looks them up).
+cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
+                                  cudaStream_t s) {
+  if (li.gen_tab <= 0) return cudaSuccess;
+  const int arena = (int)(li.seed & 0xffffffffull), pairs = (int)(li.seed >> 32);
+  const dim3 tg((unsigned)((li.gen_tab + li.tile - 1) / li.tile), li.n_inst);
+  cudaError_t e;
+  if (db) {
+    e = cudaFuncSetAttribute(general_tab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    general_tab_kernel<true><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs);
+  } else {
+    e = cudaFuncSetAttribute(general_tab_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    general_tab_kernel<false><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs);
+  }
   return cudaGetLastError();
 }
 

@@ -111,6 +111,48 @@ def test_rrg_general_components_parity():
     _parity(model, w.graphs, w.widths_sets, w.hidden, w.betas, batch=24)
 
 
+@pytest.mark.parametrize("with_db", [False, True])
+def test_rrg_component_tables_large_batch(with_db):
+    # components with at most 12 width-set neighbours are tabulated over their
+    # boundary configurations (log Z_c and d/dbeta at the call's beta) when the
+    # tables are smaller than the batch; the large batch (tables) against the
+    # same rows contracted as a small batch (elimination per sample) and, on
+    # sampled rows, against the oracle
+    w = wl.workload(4)
+    g, W, beta = w.graphs[0], w.widths_sets[0], w.betas[0]
+    model = _model(w.graphs, w.widths_sets, w.hidden, w.betas)
+    D = model.D[0]
+    B = 1 << 16
+    s = np.where(np.random.default_rng(31).random((B, D)) < 0.5, 1, -1).astype(np.int8)
+    d_spins = to_dev_spins(s.reshape(-1))
+    logZR = torch.empty(B, dtype=torch.float64, device="cuda")
+    dbeta = torch.empty(B, dtype=torch.float64, device="cuda") if with_db else None
+    model.ctx.profile(True)
+    model.ctx.contract(model.betas, B, d_spins, tv.FP32, logZR, dbeta)
+    torch.cuda.synchronize()
+    model.ctx.profile(False)
+    assert "general_tables" in model.ctx.profile_read()
+    n_small = 24
+    lz_small = torch.empty(n_small, dtype=torch.float64, device="cuda")
+    db_small = torch.empty(n_small, dtype=torch.float64, device="cuda") if with_db else None
+    model.ctx.profile(True)
+    model.ctx.contract(model.betas, n_small, to_dev_spins(s[:n_small].reshape(-1)), tv.FP32, lz_small, db_small)
+    torch.cuda.synchronize()
+    model.ctx.profile(False)
+    model.ctx.profile_read()
+    assert float((logZR[:n_small] - lz_small).abs().max()) <= 1e-9 * float(lz_small.abs().max())
+    if with_db:
+        assert float((dbeta[:n_small] - db_small).abs().max()) <= 1e-6 * max(1.0, float(db_small.abs().max()))
+    rows = [0, 1, 2, 777, 4096, 30001, B - 2, B - 1]
+    s_or = torch.as_tensor(s[rows].astype(np.float64))
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    lz = general.log_zr_general(g.n, g.ei, g.ej, g.J, bt, W, s_or)
+    assert float((logZR[rows].cpu() - lz.detach()).abs().max()) / g.n <= TOL_FP32
+    if with_db:
+        db_ref = torch.stack([torch.autograd.grad(lz[i], bt, retain_graph=True)[0] for i in range(len(rows))])
+        assert float((dbeta[rows].cpu() - db_ref).abs().max()) <= 2e-5 * max(1.0, float(db_ref.abs().max()))
+
+
 def test_general_small_graphs_against_enumeration():
     graphs = [wl.random_regular(20, 3, 7), wl.random_regular(24, 4, 8, "gauss"), wl.lattice(5, 4, "gauss", 9)]
     graphs[2].topology = wl.GENERAL  # a lattice contracted as a general graph
