@@ -9,6 +9,10 @@ reading: log Z_R includes -beta E_1, so Etilde = -log Z_R / beta):
   grad     = sum_b w_b grad_theta log q(s_b)  (Eq. 10)
 Exact (enumerated) F_q and its gradient over all 2^D width-set states pin the
 sampled forms.  Adam follows Kingma & Ba (2015), Algorithm 1.
+Observables (Sec. 3: samples of the trained network give Boltzmann averages):
+self-normalised importance weights w_b = exp(l_b) / sum_b' exp(l_b') and the
+exact conditional energy of a sample E_b = -d log Z_R(s_b) / d beta (Eq. 4)
+give U = sum_b w_b E_b, its mean under q, and ESS = 1 / sum_b w_b^2.
 """
 import math
 
@@ -26,6 +30,14 @@ def free_energies(log_zr, logq, beta):
     lz = torch.logsumexp(l, 0) - math.log(B)
     se = (l.std(unbiased=True) / (beta * math.sqrt(B))) if B > 1 else torch.zeros((), dtype=DT)
     return {"F_q": float(fq), "F_IS": float(-lz / beta), "stderr": float(se), "logZ_IS": float(lz)}
+
+
+def is_observables(log_zr, logq, energy):
+    """(U, U_q, ESS) of one batch: energy = E_b = -d log Z_R(s_b) / d beta."""
+    l = torch.as_tensor(log_zr, dtype=DT) - torch.as_tensor(logq, dtype=DT)
+    w = torch.softmax(l, 0)
+    E = torch.as_tensor(energy, dtype=DT)
+    return float((w * E).sum()), float(E.mean()), float(1.0 / (w * w).sum())
 
 
 def reinforce_weights(log_zr, logq, beta):

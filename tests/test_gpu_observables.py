@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import estimators as est
 from oracle import transfer
 from paper_2504_12037_gb300 import tnvan as tv
 from paper_2504_12037_gb300 import workloads as wl
@@ -38,8 +39,7 @@ def test_observables_match_oracle(shape):
     wts = torch.softmax(l, 0)
     db = torch.stack([torch.autograd.grad(lz[b], bt, retain_graph=True)[0] for b in range(batch)])
     (corr_ref,) = torch.autograd.grad((wts * lz).sum(), Jt)
-    E = -db
-    U_ref, Uq_ref, ess_ref = float((wts * E).sum()), float(E.mean()), float(1.0 / (wts ** 2).sum())
+    U_ref, Uq_ref, ess_ref = est.is_observables(lz.detach(), torch.as_tensor(lq, dtype=torch.float64), -db)
     # GPU
     d_spins = to_dev_spins(s.reshape(-1))
     logZR = torch.empty(batch, dtype=torch.float64, device="cuda")

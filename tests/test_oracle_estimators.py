@@ -101,3 +101,36 @@ def test_adam_first_step_is_signed_lr():
     g = np.array([0.3, -2.0, 1e-3])
     p, m, v = est.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
     assert np.allclose(p, -0.01 * np.sign(g), atol=1e-15)
+
+
+def test_is_energy_over_all_width_states_is_the_exact_internal_energy():
+    # every width-set state once with the uniform log q = -D ln 2: the weights
+    # are Z_R(s) / sum Z_R = the exact marginal of s, so sum_s w_s E_s with
+    # E_s = -d log Z_R(s) / d beta is the exact <E> = -d log Z / d beta
+    g, W, _ = _cfg1()
+    D = len(W)
+    for beta in (0.4, 1.0, 1.7):
+        bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+        lzr = ising.log_zr_enum(g.n, g.ei, g.ej, g.J, bt, W, ising.all_configs(D))
+        E = -torch.stack([torch.autograd.grad(lzr[i], bt, retain_graph=True)[0] for i in range(lzr.shape[0])])
+        U, Uq, ess = est.is_observables(lzr.detach(), torch.full((lzr.shape[0],), -D * math.log(2.0)), E)
+        b2 = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+        (dlz,) = torch.autograd.grad(ising.log_z_brute(g.n, g.ei, g.ej, g.J, b2), b2)
+        assert abs(U - (-float(dlz))) < 1e-10 * max(1.0, abs(U))
+        assert 1.0 <= ess <= lzr.shape[0]
+        # the conditional energy is the Boltzmann mean of E(s, r) over r given s (brute force)
+        s0 = ising.all_configs(D)[3:4]
+        n_r = g.n - D
+        R = [v for v in range(g.n) if v not in set(int(x) for x in W)]
+        full = torch.empty((1 << n_r, g.n), dtype=torch.float64)
+        full[:, W] = s0
+        full[:, R] = ising.all_configs(n_r)
+        en = ising.energy(g.ei, g.ej, g.J, full)
+        p = torch.softmax(-beta * en, 0)
+        assert abs(float((p * en).sum()) - float(E[3])) < 1e-10 * max(1.0, abs(float(E[3])))
+
+
+def test_is_uniform_weights():
+    lz = torch.linspace(-3.0, 2.0, 7, dtype=torch.float64)
+    U, Uq, ess = est.is_observables(lz, lz, torch.arange(7, dtype=torch.float64))
+    assert abs(U - Uq) < 1e-12 and abs(ess - 7.0) < 1e-12
