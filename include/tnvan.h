@@ -171,7 +171,11 @@ int tnvan_log_prob(tnvan_ctx* ctx, int batch, const int8_t* d_spins, int precisi
 /* Eq. 3-4 alone: log Z_R(s) for caller-given width-set configurations
  * d_spins (device int8, layout above) of every instance.  Optional
  * d_dlogZR_dbeta (device double [n_inst*batch], may be NULL) receives
- * d log Z_R / d beta = -E_1(s) - <E_2(s, r)>_{r|s}.  Asynchronous. */
+ * d log Z_R / d beta = -E_1(s) - <E_2(s, r)>_{r|s}.  For elimination
+ * instances, leftover components with at most 12 width-set neighbours are
+ * tabulated over their boundary configurations at the call's beta when the
+ * tables (sum of 2^k entries) are no larger than the batch, and looked up per
+ * sample (the same values up to FP64 rounding).  Asynchronous. */
 int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                    int precision, double* d_logZR, double* d_dlogZR_dbeta, void* stream);
 
