@@ -554,7 +554,7 @@ struct FusedBwdPlan {
 };
 int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan& p);
 // Backward and Adam of each instance chunk, queued behind that chunk's
-// adjoint and F_q reduction in the overlapped schedule.
+// adjoint and baseline mean (Eq. 10) in the overlapped schedule.
 struct ChunkBackward {
   const FusedBwdPlan* plan;
   float* d_grad;
@@ -1357,7 +1357,7 @@ static int ensure_side_streams(tnvan_ctx* ctx) {
 // launch.
 // With defer_dj the d/dJ reduction runs on a side stream (beside whatever the
 // caller queues next) and the caller waits on ctx->dj_ev before it is done;
-// with chunk_stats each chunk's F_q reduction (tnvan_backward's first kernel)
+// with chunk_stats each chunk's baseline mean (tnvan_backward's first kernel)
 // follows its adjoint on the chunk's stream.
 // With cb (implies chunk_stats) each chunk's fused backward and gradient
 // reduction with Adam follow too, so a chunk's whole training step runs as
@@ -1408,9 +1408,8 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
        "strip adjoint kernel");
     CK(cudaEventRecord(ctx->adj_ev[c], ctx->side_lo[c]), "adjoint event");
     if (chunk_stats || cb) {
-      PROF("reduce", ctx->side_lo[c]);
-      CK(launch_reduce(ctx->d_inst, lr, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, ctx->side_lo[c], k0, k1),
-         "reduce kernels");
+      PROF("mean", ctx->side_lo[c]);
+      CK(launch_mean(lr, d_logZR, d_logq, ctx->d_stats, ctx->side_lo[c], k0, k1), "mean kernel");
     }
     if (cb) {
       const FusedBwdPlan& fp = *cb->plan;
@@ -1485,7 +1484,7 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
   for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
   if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision) | PACK_FLAT | (all_fused ? PACK_TILES : 0), s)))
     return rc;
-  // the overlapped schedule runs each chunk's F_q reduction behind its
+  // the overlapped schedule runs each chunk's baseline mean behind its
   // adjoint, and the d/dJ reduction (it reads only the adjoint's partial
   // rows) beside the backward; the step ends after both.
   // With the fused BF16 backward the chunks' backward and Adam follow their
@@ -1690,8 +1689,8 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
   for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
   if (pack && (rc = pack_network(ctx, PACK_FLAT | (all_fused ? PACK_TILES : 0), s))) return rc;
   if (!stats_ready) {
-    PROF("reduce", s);
-    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernels");
+    PROF("mean", s);
+    CK(launch_mean(li, d_logZR, d_logq, ctx->d_stats, s), "mean kernel");
   }
   if (all_fused) {
     FusedBwdPlan fp;

@@ -316,6 +316,9 @@ cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int
 // reduces dbeta and wmul to out[3k..3k+2] = U, U_q, effective sample size.
 cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const float* logq, const double* stats,
                                const double* dbeta, float* wmul, double* out, bool energies, cudaStream_t s);
+// The backward's baseline mean_b l_b of instances [k0, k1) into stats[8k + 4].
+cudaError_t launch_mean(const LaunchInfo& li, const double* logZR, const float* logq, double* stats,
+                        cudaStream_t s, int k0 = 0, int k1 = -1);
 // Instances [k0, k1) (k1 < 0: all) of the launch.
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
                           const float* logq, double* stats, int* counters, cudaStream_t s, int k0 = 0,

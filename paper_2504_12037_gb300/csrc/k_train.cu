@@ -314,6 +314,72 @@ cudaError_t launch_reduce(const InstDev*, const LaunchInfo& li, const double* lo
   return cudaGetLastError();
 }
 
+// The backward's baseline alone (Eq. 10): stats[8k + 4] = mean_b l_b over the
+// finite l_b and stats[8k + 7] their count, one 1024-thread CTA per instance
+// of [k0, k0 + gridDim.x): float-float sums of l_b - l_0 (eight loads in
+// flight per thread, then the sums in sample order), an xor tree per warp,
+// the warps in order -- a fixed order, so the result does not depend on the
+// launch.  The training path needs only this; tnvan_free_energy keeps the
+// full reduction.
+__global__ void __launch_bounds__(1024) mean_kernel(const LaunchInfo li, const double* __restrict__ logZR,
+                                                    const float* __restrict__ logq, double* __restrict__ stats,
+                                                    int k0) {
+  const int k = blockIdx.x + k0, B = li.batch, tid = threadIdx.x;
+  const double* lz = logZR + (long long)k * B;
+  const float* lq = logq + (long long)k * B;
+  const FF K = ff_add(ff_from_double(lz[0]), FF{-lq[0], 0.f});
+  const FF negK = ff_neg(K);
+  FF s1{0.f, 0.f};
+  int nn = 0;
+  for (int b0 = tid; b0 < B; b0 += 1024 * 8) {
+    double z[8];
+    float q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int b = b0 + 1024 * j;
+      z[j] = b < B ? lz[b] : 0.0;
+      q[j] = b < B ? lq[b] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (b0 + 1024 * j >= B) break;
+      const FF l = ff_add(ff_from_double(z[j]), FF{-q[j], 0.f});
+      if (!isfinite(l.hi) || !isfinite(l.lo)) continue;
+      s1 = ff_add(s1, ff_add(l, negK));
+      ++nn;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 = ff_add(s1, shfl_ff(s1, o));
+    nn += __shfl_xor_sync(0xffffffffu, nn, o);
+  }
+  __shared__ FF red_s[32];
+  __shared__ int red_n[32];
+  if ((tid & 31) == 0) {
+    red_s[tid >> 5] = s1;
+    red_n[tid >> 5] = nn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    FF S = red_s[0];
+    int N = red_n[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      S = ff_add(S, red_s[w]);
+      N += red_n[w];
+    }
+    stats[8 * k + 4] = ff_to_double(K) + ff_to_double(S) / (double)N;
+    stats[8 * k + 7] = (double)N;
+  }
+}
+
+cudaError_t launch_mean(const LaunchInfo& li, const double* logZR, const float* logq, double* stats,
+                        cudaStream_t s, int k0, int k1) {
+  if (k1 < 0) k1 = li.n_inst;
+  if (k1 <= k0 || li.batch < 1) return cudaSuccess;
+  mean_kernel<<<k1 - k0, 1024, 0, s>>>(li, logZR, logq, stats, k0);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // K2 + K3: teacher-forced forward and hand-written backward of
 //   sum_b w_b log q(s_b),   w_b = -(l_b - mean l) / (beta B)       (Eq. 10)
