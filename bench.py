@@ -39,7 +39,7 @@ MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
 # dram__bytes_read.sum + dram__bytes_write.sum per whole-batch launch from ncu
 # captures of the same kernels on the same workload (see profiles/); None if not
 # captured
-NCU_TRAFFIC = {"sample_tc": 483584, "strips_adj": 5435392, "bwd_fused": 6664704, "reduce": 1035776, "grad_reduce": 27437056}
+NCU_TRAFFIC = {"sample_tc": 483840, "strips_adj": 5431552, "bwd_fused": 6674176, "reduce": 1035776, "grad_reduce": 27437056}
 
 
 def args_():
