@@ -98,6 +98,50 @@ int tnvan_init_graph(tnvan_ctx* ctx, int instance, int n_spins, int n_edges, con
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no graph), TNVAN_E_UNSUPPORTED. */
 int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w);
 
+/* As tnvan_set_width_set, with the elimination order of R given for GENERAL
+ * instances (e.g. the order tnvan_find_width_set returns): r_order is a host
+ * array [n_spins - n_w] listing every spin not in W exactly once; each
+ * component is eliminated in the order its spins appear there (instead of
+ * the planner's min-fill order).  r_order == NULL is tnvan_set_width_set.
+ * Errors: as tnvan_set_width_set; TNVAN_E_ARG when r_order is not a
+ * permutation of R, or is given for a LATTICE2D / DENSE plan;
+ * TNVAN_E_UNSUPPORTED when the order needs elimination width > 8. */
+int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w,
+                                const int32_t* r_order);
+
+/* Width-set finder (Sec. 2: a contraction order is searched, then spins are
+ * sliced out of it -- "dynamic slicing" -- until the remaining network has
+ * width <= w_u, and sliced spins are returned to R one at a time in random
+ * order while the width stays <= w_u).  Width: eliminating a spin of R
+ * creates a factor over its neighbours at that point (fill edges included);
+ * the width of an order is the largest such factor.  w_u = 1 leaves a
+ * forest, i.e. W is a feedback vertex set; the GPU elimination kernels accept
+ * w_u <= 8.  Host only (no device work, no context, callable without a GPU).
+ *   n_spins <= TNVAN_FIND_MAX_N; edges as in tnvan_init_graph.
+ *   w_u        width bound (>= 0).
+ *   restarts   number of randomised trials per search (>= 1);
+ *   seed       seed of the trials' tie-breaking.
+ *   mode       TNVAN_SLICE_FIXED: min-fill order of the whole graph, then
+ *              slicing along it (the spin in the most maximum-width factors
+ *              first); TNVAN_SLICE_GREEDY: order and slicing built together
+ *              (eliminate the least-fill spin of degree <= w_u, else slice the
+ *              spin of largest degree); TNVAN_SLICE_BEST: both, smaller W wins.
+ *   out_w      [n_spins] receives W in slicing order (use it as the
+ *              autoregressive order);
+ *   out_order  [n_spins] receives R's elimination order (n_spins - n_w
+ *              entries; pass it to tnvan_set_width_set_ordered);
+ *   out_info   [3] receives n_w, the order's width, and the winning trial
+ *              (2 * restart + (search == GREEDY)).
+ * Deterministic for a given seed (integer arithmetic only).
+ * Errors: TNVAN_E_ARG. */
+#define TNVAN_FIND_MAX_N 16384
+#define TNVAN_SLICE_FIXED 1
+#define TNVAN_SLICE_GREEDY 2
+#define TNVAN_SLICE_BEST 3
+int tnvan_find_width_set(int n_spins, int n_edges, const int32_t* ei, const int32_t* ej, int w_u,
+                         int restarts, uint64_t seed, int mode, int32_t* out_w, int32_t* out_order,
+                         int32_t* out_info);
+
 /* Attach the MADE network of `instance` (Eq. 7, Fig. 1(d)): D = n_w inputs and
  * outputs, n_hidden (0..2) ReLU hidden layers of widths[0..n_hidden-1]
  * (each <= 512).  d_params: borrowed device pointer to float32 parameters,

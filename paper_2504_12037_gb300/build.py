@@ -1,6 +1,6 @@
 """Build libtnvan.so (the C-ABI library) in-tree for sm_103a with nvcc.
 
-Each .cu file is compiled to an object in parallel, then linked into one
+Each .cu (and host-only .cpp) file is compiled to an object in parallel, then linked into one
 shared library next to this file.  Used by __graft_entry__.build() and by
 `python -m paper_2504_12037_gb300.build`.
 """
@@ -26,7 +26,7 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def build(verbose: bool = False, extra=()) -> str:
@@ -36,7 +36,7 @@ def build(verbose: bool = False, extra=()) -> str:
     srcs = sources()
 
     def compile_one(src):
-        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [cc, *FLAGS, *ARCH, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -287,7 +287,7 @@ std::vector<std::vector<int>> r_components(const Instance& in, const std::vector
 }
 
 int plan_dense(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos);
-int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos);
+int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos, const std::vector<int>& rank);
 
 int upload_plan(tnvan_ctx* ctx, Instance& in) {
   int rc;
@@ -882,6 +882,11 @@ int tnvan_init_graph(tnvan_ctx* ctx, int instance, int n_spins, int n_edges, con
 }
 
 int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w) {
+  return tnvan_set_width_set_ordered(ctx, instance, n_w, w, nullptr);
+}
+
+int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w,
+                                const int32_t* r_order) {
   int rc = check_inst(ctx, instance, false);
   if (rc) return rc;
   Instance& in = ctx->inst[instance];
@@ -892,6 +897,16 @@ int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w)
     if (w[i] < 0 || w[i] >= in.n) return fail(ctx, TNVAN_E_ARG, "w[%d] = %d out of range", i, w[i]);
     if (pos[w[i]] >= 0) return fail(ctx, TNVAN_E_ARG, "w[%d] = %d repeated", i, w[i]);
     pos[w[i]] = i;
+  }
+  std::vector<int> rank;
+  if (r_order) {
+    rank.assign(in.n, -1);
+    for (int k = 0; k < in.n - n_w; ++k) {
+      const int v = r_order[k];
+      if (v < 0 || v >= in.n || pos[v] >= 0 || rank[v] >= 0)
+        return fail(ctx, TNVAN_E_ARG, "r_order[%d] = %d is not a spin of R or repeated", k, v);
+      rank[v] = k;
+    }
   }
   DeviceGuard g(ctx->device);
   reset_plan(in);
@@ -922,9 +937,10 @@ int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w)
     rc = plan_dense(ctx, in, pos);
     if (rc != TNVAN_OK && rc != TNVAN_E_UNSUPPORTED) return rc;
   }
+  if (rc == TNVAN_OK && r_order) return fail(ctx, TNVAN_E_ARG, "r_order is only used by elimination plans");
   if (rc == TNVAN_E_UNSUPPORTED) {
     ctx->err.clear();
-    rc = plan_general(ctx, in, pos);
+    rc = plan_general(ctx, in, pos, rank);
     if (rc) return rc;
   }
   if ((rc = upload_plan(ctx, in))) return rc;
@@ -2408,13 +2424,14 @@ int plan_dense(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
 
 // General leftover components: each connected component of R is compiled into
 // a variable-elimination program (order: min-fill on the component graph, ties
-// to the lowest local index).  Program layout (ints), per component:
+// to the lowest local index; or, when `rank` is non-empty, the order of the
+// component's spins by rank).  Program layout (ints), per component:
 //   n_steps, arena_floats, final_offset, then per step:
 //   v, fld_begin, fld_count, m, out_off, n_in, n_pair,
 //   n_in x { in_off, k, pos_0 .. pos_{k-1} }  (pos in the extended scope out+{v})
 //   n_pair x { pair_id, pos_u }                (pos of the neighbour in the out scope)
 // fld: per W-neighbour bond of an R spin, (AR position, edge id); fldJ its coupling.
-int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
+int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos, const std::vector<int>& rank) {
   auto comps = r_components(in, pos);
   std::vector<std::vector<std::pair<int, int>>> adj(in.n);  // (neighbour, edge)
   for (int e = 0; e < in.m; ++e) {
@@ -2461,7 +2478,11 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos) {
     std::vector<std::set<int>> h = g;
     std::vector<char> gone(n, 0);
     std::vector<int> order;
-    for (int step = 0; step < n; ++step) {
+    if (!rank.empty()) {
+      for (int i = 0; i < n; ++i) order.push_back(i);
+      std::sort(order.begin(), order.end(), [&](int a, int b) { return rank[comp[a]] < rank[comp[b]]; });
+    }
+    for (int step = (int)order.size(); step < n; ++step) {
       int best = -1;
       long best_fill = -1;
       for (int v = 0; v < n; ++v) {

@@ -19,6 +19,7 @@ OK = 0
 E_ARG, E_NOMEM, E_CUDA, E_TIMEOUT, E_OVERFLOW, E_STATE, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 LATTICE2D, DENSE, GENERAL = 0, 1, 2
 FP32, TF32, BF16 = 0, 1, 2
+SLICE_FIXED, SLICE_GREEDY, SLICE_BEST = 1, 2, 3
 
 _c_int, _c_i64, _c_u64, _c_dbl, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -33,6 +34,9 @@ SIGNATURES = {
     "tnvan_last_error": (ctypes.c_char_p, [_vp]),
     "tnvan_init_graph": (_c_int, [_vp, _c_int, _c_int, _c_int, _i32p, _i32p, _dblp, _c_int, _c_int, _c_int, _c_int]),
     "tnvan_set_width_set": (_c_int, [_vp, _c_int, _c_int, _i32p]),
+    "tnvan_set_width_set_ordered": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p]),
+    "tnvan_find_width_set": (_c_int, [_c_int, _c_int, _i32p, _i32p, _c_int, _c_int, _c_u64, _c_int, _i32p, _i32p,
+                                      _i32p]),
     "tnvan_set_made": (_c_int, [_vp, _c_int, _c_int, _i32p, _vp]),
     "tnvan_n_params": (_c_int, [_vp, _c_int, _i64p, _i64p]),
     "tnvan_instance_info": (_c_int, [_vp, _c_int, _i32p]),
@@ -104,6 +108,23 @@ def _arr(a, dtype):
     return a, a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
+def find_width_set(n_spins: int, ei, ej, w_u: int, restarts: int = 4, seed: int = 0, mode: int = SLICE_BEST):
+    """Width-set finder (tnvan_find_width_set): returns (W in slicing order,
+    R's elimination order, achieved width, winning trial).  Host only."""
+    ei, pi = _arr(ei, np.int32)
+    ej, pj = _arr(ej, np.int32)
+    out_w = np.zeros(n_spins, np.int32)
+    out_o = np.zeros(n_spins, np.int32)
+    info = np.zeros(3, np.int32)
+    rc = lib().tnvan_find_width_set(n_spins, ei.shape[0], pi, pj, w_u, restarts, seed, mode,
+                                    out_w.ctypes.data_as(_i32p), out_o.ctypes.data_as(_i32p),
+                                    info.ctypes.data_as(_i32p))
+    if rc != OK:
+        raise TnvanError(rc, "tnvan_find_width_set: invalid argument")
+    nw = int(info[0])
+    return out_w[:nw].copy(), out_o[:n_spins - nw].copy(), int(info[1]), int(info[2])
+
+
 class Context:
     """Owns one tnvan_ctx.  Method names follow the C-ABI."""
 
@@ -138,9 +159,13 @@ class Context:
         self._check(lib().tnvan_init_graph(self._h, instance, n_spins, ei.shape[0], pi, pj, pJ, topology,
                                            Lx, Ly, int(periodic)))
 
-    def set_width_set(self, instance: int, w):
+    def set_width_set(self, instance: int, w, r_order=None):
         w, pw = _arr(w, np.int32)
-        self._check(lib().tnvan_set_width_set(self._h, instance, w.shape[0], pw))
+        if r_order is None:
+            self._check(lib().tnvan_set_width_set(self._h, instance, w.shape[0], pw))
+        else:
+            r_order, po = _arr(r_order, np.int32)
+            self._check(lib().tnvan_set_width_set_ordered(self._h, instance, w.shape[0], pw, po))
 
     def set_made(self, instance: int, hidden: Sequence[int], d_params):
         h, ph = _arr(list(hidden) if len(hidden) else [0], np.int32)
