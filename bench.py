@@ -59,6 +59,9 @@ def args_():
                          "(sample tile, strip tile, backward CTAs, adjoint tile, TC group, overlap 2=on 1=off)")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--planned", action="store_true",
+                    help="also time the training step on random regular graphs (n = 1000, d = 3) whose width "
+                         "sets come from the width-set finder")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the captured step over per-instance batches 2^8 .. 2^18 (the asymptote)")
     return ap.parse_args()
@@ -459,6 +462,42 @@ def run_ours(a):
                           "value": n_inst * Bs * world / (t_ms / 1e3)})
             del cap, ms_
         out["sweep"] = sweep
+    if a.planned:
+        # random regular graph, n = 1000, d = 3, J = +-1, beta = 0.5 (the paper's
+        # Fig. 3(a,b) setting), batch 10,000; W and R's elimination order from
+        # tnvan_find_width_set at several width bounds; the captured training
+        # step (BF16 sampler, elimination contraction, d/dbeta, d/dJ, Adam)
+        planned = []
+        g = wl.random_regular(1000, 3, 12037 + 7000)
+        Bp = 10000
+        for wu in (1, 4, 8):
+            t0 = time.time()
+            Wp, op, wp, _ = tv.find_width_set(g.n, g.ei, g.ej, wu, restarts=4, seed=1)
+            t_plan = time.time() - t0
+            mp = TNVAN([g], [Wp], [128, 128], [0.5], device=local, seed=1000 * rank + 5, elim_orders=[op])
+            info = mp.ctx.instance_info(0)
+            mp.ctx.reserve(Bp)
+            mp.ctx.autotune(mp.betas, Bp, prec)
+            dbs = torch.empty(Bp, dtype=torch.float64, device="cuda")
+            djs = torch.empty(g.m, dtype=torch.float64, device="cuda")
+            cap = mp.capture_train_step(Bp, seed, prec, 0.01, mp.buffers(Bp), dbs, djs)
+            for _ in range(3):
+                cap.replay()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record(stream)
+                cap.replay()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+            planned.append({"w_u": wu, "n_w": len(Wp), "width": wp, "finder_s": t_plan,
+                            "components": info["n_components"], "max_component": info["max_component"],
+                            "arena_floats": info["arena"], "arena_live_floats": info["arena_live"],
+                            "batch": Bp * world, "ms_per_step": t_ms, "value": Bp * world / (t_ms / 1e3)})
+            del cap, mp
+        out["planned_rrg_n1000_d3"] = planned
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
         # the oracle's exact free energy of the lattice (single-site transfer matrix, 2^16 states)

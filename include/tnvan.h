@@ -160,7 +160,9 @@ int tnvan_n_params(const tnvan_ctx* ctx, int instance, int64_t* n_params, int64_
 /* Plan summary of `instance`: info[0] n_spins, [1] n_edges, [2] n_w (D),
  * [3] contraction kind (0 strips, 1 dense, 2 general), [4] number of R
  * components, [5] largest component (spins), [6] largest elimination width,
- * [7] number of W-W edges.  info: host array [8]. */
+ * [7] number of W-W edges, [8] per-sample table arena of elimination plans
+ * (floats, every table kept: reverse sweeps), [9] the same with consumed
+ * tables' space reused (forward passes).  info: host array [10]. */
 int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info);
 
 /* Pre-allocate the context's internal workspaces for batches up to

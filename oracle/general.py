@@ -61,20 +61,24 @@ def _comp_elim(J, beta, comp, inner, h, order=None, order_rule="min_degree"):
         factors.append(([a, b], t[None].expand(B, 2, 2)))
     logacc = torch.zeros(B, dtype=DT)
     remaining = set(range(len(comp)))
+    # neighbours of each variable: the other variables it shares a factor with
+    # (the bonds, then the scopes of the tables created so far)
+    nbrs = {k: set() for k in range(len(comp))}
+    for e, a, b in inner:
+        nbrs[a].add(b)
+        nbrs[b].add(a)
     while remaining:
         if order is None:
-            def nbrs(v):
-                s = set()
-                for vs, _ in factors:
-                    if v in vs:
-                        s.update(vs)
-                s.discard(v)
-                return s
             cand = sorted(remaining, reverse=(order_rule == "min_degree_high"))
-            v = min(cand, key=lambda u: len(nbrs(u)))
+            v = min(cand, key=lambda u: len(nbrs[u]))
         else:
             v = next(u for u in order if u in remaining)
         remaining.discard(v)
+        for a in nbrs[v]:
+            nbrs[a] |= nbrs[v]
+            nbrs[a].discard(a)
+            nbrs[a].discard(v)
+        del nbrs[v]
         use = [f for f in factors if v in f[0]]
         factors = [f for f in factors if v not in f[0]]
         vars_out = sorted(set(x for vs, _ in use for x in vs) - {v})

@@ -350,13 +350,17 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     if ((rc = upload(ctx, in, in.gstep_off, &so))) return rc;
     if ((rc = upload(ctx, in, in.gcomp_step0, &cs))) return rc;
     if ((rc = upload(ctx, in, in.gprog, &prog))) return rc;
+    int* prog_fwd = nullptr;
+    if ((rc = upload(ctx, in, in.gprog_fwd, &prog_fwd))) return rc;
     if ((rc = upload(ctx, in, in.gfld, &fld))) return rc;
     if ((rc = upload(ctx, in, in.gpairJ, &pj))) return rc;
     if ((rc = upload(ctx, in, in.gfldJ, &fj))) return rc;
     GenDev& g = in.dev.gen;
     g.n_comp = in.g_ncomp;
     g.max_entries = in.g_max_entries;
+    g.max_live = in.g_max_live;
     g.prog = prog;
+    g.prog_fwd = prog_fwd;
     g.prog_len = (int)in.gprog.size();
     g.pairJ = pj;
     g.pairE = pe;
@@ -1253,6 +1257,8 @@ int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info) {
   info[5] = in.max_comp;
   info[6] = in.max_width;
   info[7] = (int)in.ww.size();
+  info[8] = in.kind == 2 ? in.g_max_entries : 0;
+  info[9] = in.kind == 2 ? in.g_max_live : 0;
   return TNVAN_OK;
 }
 
@@ -2278,7 +2284,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     int arena = 0, pairs = 0, Dm = 0;
     for (const Instance& in : ctx->inst)
       if (in.kind == 2) {
-        arena = std::max(arena, in.g_max_entries);
+        arena = std::max(arena, in.g_max_live);
         pairs = std::max(pairs, in.g_npairs);
         Dm = std::max(Dm, (int)in.W.size());
       }
@@ -2586,6 +2592,75 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos, cons
     arena_max = std::max(arena_max, (arena + 3) & ~3);  // keeps the float4 pair table aligned
   }
   comp_step0.push_back((int)step_off.size());
+  // Forward-only passes keep a table only until the step that consumes it:
+  // the same program with offsets from a first-fit allocator over the
+  // arena (the new table is placed before its inputs are released).
+  std::vector<int> fwd(prog);
+  int live_max = 0;
+  for (size_t c = 0; c < comps.size(); ++c) {
+    std::map<int, int> free_;          // start -> length
+    std::map<int, std::pair<int, int>> where;  // full offset -> (live offset, size)
+    std::vector<int> owner;            // self-check: live entry -> step + 1
+    int top = 0;
+    auto alloc = [&](int sz) {
+      for (auto it = free_.begin(); it != free_.end(); ++it)
+        if (it->second >= sz) {
+          const int off = it->first, len = it->second;
+          free_.erase(it);
+          if (len > sz) free_[off + sz] = len - sz;
+          return off;
+        }
+      const int off = top;
+      top += sz;
+      return off;
+    };
+    auto release = [&](int off, int sz) {
+      auto nx = free_.lower_bound(off);
+      if (nx != free_.end() && nx->first == off + sz) {
+        sz += nx->second;
+        free_.erase(nx);
+      }
+      auto pv = free_.lower_bound(off);
+      if (pv != free_.begin()) {
+        --pv;
+        if (pv->first + pv->second == off) {
+          off = pv->first;
+          sz += pv->second;
+          free_.erase(pv);
+        }
+      }
+      free_[off] = sz;
+    };
+    for (int st = comp_step0[c]; st < comp_step0[c + 1]; ++st) {
+      const int r = step_off[st];
+      const int m = prog[r + 3], out = prog[r + 4], nin = prog[r + 5];
+      const int lo = alloc(1 << m);
+      if ((int)owner.size() < top) owner.resize(top, 0);
+      for (int x = 0; x < (1 << m); ++x) {
+        if (owner[lo + x]) return fail(ctx, TNVAN_E_UNSUPPORTED, "internal: overlapping tables in the live layout");
+        owner[lo + x] = st + 1;
+      }
+      where[out] = {lo, 1 << m};
+      fwd[r + 4] = lo;
+      int q = r + 7;
+      for (int i = 0; i < nin; ++i) {
+        auto it = where.find(prog[q]);
+        if (it == where.end()) return fail(ctx, TNVAN_E_UNSUPPORTED, "internal: table consumed before it is made");
+        fwd[q] = it->second.first;
+        for (int x = 0; x < it->second.second; ++x) owner[it->second.first + x] = 0;
+        release(it->second.first, it->second.second);
+        where.erase(it);
+        q += 2 + prog[q + 1];
+      }
+    }
+    const int hdr = ctab[5 * c];
+    auto it = where.find(prog[hdr + 2]);
+    if (it == where.end()) return fail(ctx, TNVAN_E_UNSUPPORTED, "internal: no final table");
+    fwd[hdr + 2] = it->second.first;
+    live_max = std::max(live_max, (top + 3) & ~3);
+  }
+  in.gprog_fwd.swap(fwd);
+  in.g_max_live = live_max;
   in.gprog.swap(prog);
   in.gfld.swap(fld);
   in.gpairE.swap(pairE);

@@ -127,8 +127,10 @@ struct DenseDev {
 // General components: elimination programs (see k_general.cu).
 struct GenDev {
   int n_comp;
-  int max_entries;       // per-sample table arena size (floats)
-  const int* prog;       // packed int program
+  int max_entries;       // per-sample table arena size (floats), every table kept
+  int max_live;          // the same with a table's space reused once it is consumed
+  const int* prog;       // packed int program, every table at its own offset (reverse sweeps)
+  const int* prog_fwd;   // the same program with reused offsets (forward-only passes)
   int prog_len;
   const float* pairJ;    // couplings of R-R bonds referenced by the program
   const int* pairE;      // edge id of each pair
@@ -217,12 +219,12 @@ struct Instance {
   std::vector<int> eRR, eRW;
   double dense_chat = 0;
   // general
-  std::vector<int> gprog, gfld, gpairE, gstep_off, gcomp_step0;
+  std::vector<int> gprog, gprog_fwd, gfld, gpairE, gstep_off, gcomp_step0;
   int g_max_steps = 0;
   std::vector<int> gctab, gbpos, gtabc;  // component tables (GenDev)
   int g_ntab = 0;
   std::vector<float> gpairJ, gfldJ;
-  int g_ncomp = 0, g_max_entries = 0, g_npairs = 0;
+  int g_ncomp = 0, g_max_entries = 0, g_max_live = 0, g_npairs = 0;
   double g_chat = 0;
   // network
   int nh = 0, H[2] = {0, 0};

@@ -8,7 +8,9 @@
 // sums v out, giving a table over its remaining neighbours (at most 2^8
 // entries).  Tables live in a per-sample arena in shared memory, laid out
 // [entry][sample] so that the threads of a warp (one sample each) touch
-// consecutive words.  Every new table is renormalised by a power of two.
+// consecutive words; the forward passes run the program with reused offsets
+// (a table's space is free once the step that consumes it has run), the
+// reverse sweep keeps every table.  Every new table is renormalised by a power of two.
 // Factors are stored normalised (largest entry 1); the removed constants
 // (beta |h_v| per field, beta |J| per bond) are added back in FP64.
 // With DB, every table entry carries its beta-derivative (forward mode).
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
   __syncthreads();
   if (b >= li.batch) return;
   const int8_t* s = ssp + t * Dp;
-  const int* P = G.prog;
+  const int* P = G.prog_fwd;
   const bool tab = li.gen_tab && G.n_tab > 0 && G.n_tab <= li.batch;  // tables built for this call
   double lz = 0.0, dl = 0.0;
   const int ncomp = P[0];
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restri
   const int* cr = G.ctab + 5 * c;
   for (int j = 0; j < cr[2]; ++j) s[G.bpos[cr[3] + j]] = ((x >> j) & 1) ? -1 : 1;
   double lz = 0.0, dl = 0.0;
-  run_component<DB>(G, G.prog, cr[0], s, A, dA, pt, T, t, beta, lz, dl);
+  run_component<DB>(G, G.prog_fwd, cr[0], s, A, dA, pt, T, t, beta, lz, dl);
   G.tab_lz[g] = lz;
   if (DB) G.tab_db[g] = dl;
 }
@@ -223,9 +225,15 @@ __global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restri
 // Bond sums are warp-reduced into per-CTA shared accumulators, written as one
 // row per CTA and added per instance in a fixed order.
 // ---------------------------------------------------------------------------
+// (blocks of fewer than 32 threads -- large tables -- have one partial warp:
+// no shuffles there, every thread adds its own term)
 __device__ __forceinline__ void acc_edge(float* acc, int e, float v, bool lane0) {
-  v = warp_sum(v);
-  if (lane0 && e >= 0) atomicAdd(acc + e, v);
+  if (blockDim.x >= 32) {
+    v = warp_sum(v);
+    if (lane0 && e >= 0) atomicAdd(acc + e, v);
+  } else if (e >= 0) {
+    atomicAdd(acc + e, v);
+  }
 }
 
 __global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restrict__ inst,

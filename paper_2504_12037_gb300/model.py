@@ -19,7 +19,7 @@ from .workloads import Graph, made_param_count, made_params
 class TNVAN:
     def __init__(self, graphs: Sequence[Graph], width_sets: Sequence[np.ndarray], hidden: Sequence[int],
                  betas: Sequence[float], device: int = 0, seed: int = 0, init_scale: float = 1.0,
-                 params: Optional[np.ndarray] = None):
+                 params: Optional[np.ndarray] = None, elim_orders: Optional[Sequence] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("TNVAN needs a CUDA device")
         self.device = torch.device("cuda", device)
@@ -31,7 +31,7 @@ class TNVAN:
         self.graphs = list(graphs)
         for k, (g, W) in enumerate(zip(graphs, width_sets)):
             self.ctx.init_graph(k, g.n, g.ei, g.ej, g.J, g.topology, g.Lx, g.Ly, g.periodic)
-            self.ctx.set_width_set(k, W)
+            self.ctx.set_width_set(k, W, None if elim_orders is None else elim_orders[k])
         sizes = [made_param_count(D, hidden) for D in self.D]
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         if params is None:
