@@ -836,6 +836,8 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   if (ctx->d_ws) cudaFree(ctx->d_ws);
   if (ctx->d_obs) cudaFree(ctx->d_obs);
   if (ctx->d_dj_part) cudaFree(ctx->d_dj_part);
+  for (float* p : ctx->d_gen_scratch)
+    if (p) cudaFree(p);
   delete ctx;
   return TNVAN_OK;
 }
@@ -1270,6 +1272,20 @@ static int ensure_dj_part(tnvan_ctx* ctx, size_t floats) {
   cudaError_t e = cudaMalloc(&ctx->d_dj_part, floats * sizeof(float));
   if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(d/dJ partials): %s", cudaGetErrorString(e));
   ctx->dj_part_floats = floats;
+  return TNVAN_OK;
+}
+
+// Global table scratch of the elimination kernels (which: 0 forward, 1
+// reverse sweep); grows only, kept for the context's lifetime.
+static int ensure_gen_scratch(tnvan_ctx* ctx, int which, size_t floats) {
+  if (floats <= ctx->gen_scratch_floats[which]) return TNVAN_OK;
+  if (ctx->d_gen_scratch[which]) cudaFree(ctx->d_gen_scratch[which]);
+  ctx->d_gen_scratch[which] = nullptr;
+  ctx->gen_scratch_floats[which] = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_gen_scratch[which], floats * sizeof(float));
+  if (e != cudaSuccess)
+    return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(elimination tables, %zu floats): %s", floats, cudaGetErrorString(e));
+  ctx->gen_scratch_floats[which] = floats;
   return TNVAN_OK;
 }
 
@@ -2288,9 +2304,14 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
         pairs = std::max(pairs, in.g_npairs);
         Dm = std::max(Dm, (int)in.W.size());
       }
+    // tables in shared memory while 32 samples per CTA fit, else in global
+    // scratch with 64 samples per CTA
+    const bool db = d_dbeta != nullptr;
     int T = 64;
-    while (T > 1 && general_smem_bytes(arena, pairs, Dm, T, d_dbeta != nullptr) > 200 * 1024) T /= 2;
-    const int sm = general_smem_bytes(arena, pairs, Dm, T, d_dbeta != nullptr);
+    while (T > 1 && general_smem_bytes(arena, pairs, Dm, T, db, false) > 200 * 1024) T /= 2;
+    const bool glob = T < 32;
+    if (glob) T = 64;
+    const int sm = general_smem_bytes(arena, pairs, Dm, T, db, glob);
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
     LaunchInfo lg;
     if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
@@ -2299,12 +2320,17 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     for (const Instance& in : ctx->inst)
       if (in.kind == 2 && in.g_ntab > 0 && in.g_ntab <= batch)
         lg.gen_tab = std::max(lg.gen_tab, in.g_ntab);
+    float* gs = nullptr;
+    if (glob) {
+      if ((rc = ensure_gen_scratch(ctx, 0, general_scratch_floats(lg, arena, db)))) return rc;
+      gs = ctx->d_gen_scratch[0];
+    }
     if (lg.gen_tab > 0) {
       PROF("general_tables", s);
-      CK(launch_general_tables(ctx->d_inst, lg, sm, d_dbeta != nullptr, s), "general tables kernel");
+      CK(launch_general_tables(ctx->d_inst, lg, sm, db, gs, s), "general tables kernel");
     }
     PROF(d_dbeta ? "general_dbeta" : "general", s);
-    CK(launch_general(ctx->d_inst, lg, sm, d_spins, d_logZR, d_dbeta, nullptr, s), "general kernel");
+    CK(launch_general(ctx->d_inst, lg, sm, d_spins, d_logZR, d_dbeta, gs, s), "general kernel");
   }
   return TNVAN_OK;
 }
@@ -2376,15 +2402,23 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         }
       if (any_gen) {
         int T = 64;
-        while (T > 1 && general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T) > 200 * 1024) T /= 2;
-        const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T);
+        while (T > 1 && general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T, false) > 200 * 1024) T /= 2;
+        const bool glob = T < 32;  // tables in global scratch, 64 samples per CTA
+        if (glob) T = 64;
+        const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T, glob);
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
         if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
         const int stride = (me + 3) & ~3;
         if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
+        float* gs = nullptr;
+        if (glob) {
+          if ((rc = ensure_gen_scratch(ctx, 1, general_dJ_scratch_floats(arena, steps, T, lg.tile_begin[lg.n_inst]))))
+            return rc;
+          gs = ctx->d_gen_scratch[1];
+        }
         PROF("general_dJ", s);
-        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, pairs, steps, d_spins, ctx->d_dj_part, stride, d_dJ, s),
+        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, pairs, steps, d_spins, ctx->d_dj_part, stride, d_dJ, gs, s),
            "general adjoint kernel");
       }
     }

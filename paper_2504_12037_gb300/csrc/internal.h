@@ -278,6 +278,8 @@ struct tnvan_ctx {
   size_t grad_packed_floats = 0;
   float* d_dj_part = nullptr;        // d/dJ partial rows [CTA][max edges]
   size_t dj_part_floats = 0;
+  float* d_gen_scratch[2] = {nullptr, nullptr};  // global elimination tables: forward, reverse sweep
+  size_t gen_scratch_floats[2] = {0, 0};
   void* d_obs = nullptr;             // tnvan_observables: weights, d/dbeta, sums
   size_t obs_bytes = 0;
 };
@@ -300,13 +302,18 @@ cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li,
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
                          cudaStream_t s);
+// Elimination kernels keep their tables in shared memory, or (garena
+// non-NULL: arenas too large for 32 samples per CTA) in a global scratch
+// buffer of general_scratch_floats / general_dJ_scratch_floats floats.
 cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
-                           const int8_t* spins, double* logZR, double* dbeta, double* dJ,
+                           const int8_t* spins, double* logZR, double* dbeta, float* garena,
                            cudaStream_t s);
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena,
                               int pairs, int steps, const int8_t* spins, float* part, int part_stride,
-                              double* dJ, cudaStream_t s);
-int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T);
+                              double* dJ, float* garena, cudaStream_t s);
+int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T, bool glob);
+size_t general_dJ_scratch_floats(int arena, int steps, int T, int nblk);
+size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);
 // The strip adjoint's tables (Boltzmann factors of every strip row at the
@@ -358,9 +365,9 @@ extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 
 int sample_smem_bytes(const Instance& in, int tile);
-int general_smem_bytes(int arena, int pairs, int D, int T, bool db);
+int general_smem_bytes(int arena, int pairs, int D, int T, bool db, bool glob);
 cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
-                                  cudaStream_t s);
+                                  float* garena, cudaStream_t s);
 int strip_smem_bytes(const Instance& in, int tile);
 int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats);
 int strip_adj_lv_floats(const Instance& in, int tile);

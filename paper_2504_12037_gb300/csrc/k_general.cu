@@ -14,6 +14,8 @@
 // Factors are stored normalised (largest entry 1); the removed constants
 // (beta |h_v| per field, beta |J| per bond) are added back in FP64.
 // With DB, every table entry carries its beta-derivative (forward mode).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tnvan {
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
                                                      int max_pairs,
                                                      const int8_t* __restrict__ spins,
                                                      double* __restrict__ logZR,
-                                                     double* __restrict__ dbeta) {
+                                                     double* __restrict__ dbeta, float* __restrict__ garena) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
@@ -116,9 +118,12 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
   const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  float* A = sm;                                   // [arena][T]
-  float* dA = A + arena_floats * T;                // [arena][T] (DB)
-  float4* pt = reinterpret_cast<float4*>(dA + (DB ? arena_floats * T : 0));  // [pairs]
+  // tables [arena][T] (and their beta-derivatives) in shared memory, or for
+  // large arenas in this CTA's slice of a global scratch buffer
+  const size_t cta_floats = (size_t)arena_floats * T * (DB ? 2 : 1);
+  float* A = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
+  float* dA = A + arena_floats * T;
+  float4* pt = reinterpret_cast<float4*>(garena ? sm : sm + cta_floats);  // [pairs]
   int8_t* ssp = reinterpret_cast<int8_t*>(pt + max_pairs);
   const GenDev& G = I.gen;
   for (int p = t; p < G.n_pairs; p += T) {
@@ -169,7 +174,8 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
 // per call (they depend on beta) when they are smaller than the batch.
 template <bool DB>
 __global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
-                                                         int arena_floats, int max_pairs) {
+                                                         int arena_floats, int max_pairs,
+                                                         float* __restrict__ garena) {
   extern __shared__ float sm[];
   const int k = blockIdx.y;
   const InstDev& I = inst[k];
@@ -180,9 +186,10 @@ __global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restri
   const int g = blockIdx.x * T + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  float* A = sm;
+  const size_t cta_floats = (size_t)arena_floats * T * (DB ? 2 : 1);
+  float* A = garena ? garena + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * cta_floats : sm;
   float* dA = A + arena_floats * T;
-  float4* pt = reinterpret_cast<float4*>(dA + (DB ? arena_floats * T : 0));
+  float4* pt = reinterpret_cast<float4*>(garena ? sm : sm + cta_floats);
   int8_t* ssp = reinterpret_cast<int8_t*>(pt + max_pairs);
   for (int p = t; p < G.n_pairs; p += T) {
     const float J = G.pairJ[p], aj = fabsf(J);
@@ -240,7 +247,8 @@ __global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restric
                                                         const LaunchInfo li, int arena_floats,
                                                         int max_pairs, int max_steps,
                                                         const int8_t* __restrict__ spins,
-                                                        float* __restrict__ part, int part_stride) {
+                                                        float* __restrict__ part, int part_stride,
+                                                        float* __restrict__ garena) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
@@ -249,10 +257,13 @@ __global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restric
   const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  float* A = sm;                          // [arena][T]
+  // tables, adjoints and scales in shared memory, or for large arenas in this
+  // CTA's slice of a global scratch buffer
+  const size_t cta_floats = (size_t)(2 * arena_floats + max_steps) * T;
+  float* A = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;  // [arena][T]
   float* Ab = A + arena_floats * T;       // [arena][T] adjoints
   float* sc = Ab + arena_floats * T;      // [max_steps][T] scales 2^-e
-  float2* pt = reinterpret_cast<float2*>(sc + max_steps * T);  // [pairs] (a, b)
+  float2* pt = reinterpret_cast<float2*>(garena ? sm : sm + cta_floats);  // [pairs] (a, b)
   float* acc = reinterpret_cast<float*>(pt + max_pairs);       // [n_edges]
   int8_t* ssp = reinterpret_cast<int8_t*>(acc + ((I.n_edges + 3) & ~3));
   const GenDev& G = I.gen;
@@ -398,20 +409,25 @@ __global__ void general_dJ_reduce_kernel(const InstDev* __restrict__ inst, const
   }
 }
 
-int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T) {
+int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T, bool glob) {
   int w4 = (D + 3) / 4;
   if ((w4 & 1) == 0) ++w4;
-  return (2 * arena + steps) * T * 4 + pairs * 8 + ((n_edges + 3) & ~3) * 4 + T * 4 * w4;
+  return (glob ? 0 : (2 * arena + steps) * T * 4) + pairs * 8 + ((n_edges + 3) & ~3) * 4 + T * 4 * w4;
+}
+
+size_t general_dJ_scratch_floats(int arena, int steps, int T, int nblk) {
+  return (size_t)(2 * arena + steps) * T * nblk;
 }
 
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena,
                               int pairs, int steps, const int8_t* spins, float* part, int part_stride,
-                              double* dJ, cudaStream_t s) {
+                              double* dJ, float* garena, cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(general_dJ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  general_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, steps, spins, part, part_stride);
+  general_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, steps, spins, part, part_stride,
+                                                      garena);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   general_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
@@ -421,7 +437,7 @@ cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int s
 // The components' tables at this call's betas (li.gen_tab: the largest
 // table; general_kernel then looks them up).
 cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
-                                  cudaStream_t s) {
+                                  float* garena, cudaStream_t s) {
   if (li.gen_tab <= 0) return cudaSuccess;
   const int arena = (int)(li.seed & 0xffffffffull), pairs = (int)(li.seed >> 32);
   const dim3 tg((unsigned)((li.gen_tab + li.tile - 1) / li.tile), li.n_inst);
@@ -429,23 +445,32 @@ cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, i
   if (db) {
     e = cudaFuncSetAttribute(general_tab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_tab_kernel<true><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs);
+    general_tab_kernel<true><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, garena);
   } else {
     e = cudaFuncSetAttribute(general_tab_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_tab_kernel<false><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs);
+    general_tab_kernel<false><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, garena);
   }
   return cudaGetLastError();
 }
 
-int general_smem_bytes(int arena, int pairs, int D, int T, bool db) {
+int general_smem_bytes(int arena, int pairs, int D, int T, bool db, bool glob) {
   int w4 = (D + 3) / 4;
   if ((w4 & 1) == 0) ++w4;
-  return arena * T * 4 * (db ? 2 : 1) + pairs * 16 + T * 4 * w4;
+  return (glob ? 0 : arena * T * 4 * (db ? 2 : 1)) + pairs * 16 + T * 4 * w4;
+}
+
+// Scratch of the global-table mode: one [arena][T] slice (two with d/dbeta)
+// per CTA of the contraction and of the tables kernel.
+size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db) {
+  const size_t per = (size_t)arena * li.tile * (db ? 2 : 1);
+  size_t ctas = (size_t)li.tile_begin[li.n_inst];
+  if (li.gen_tab > 0) ctas = std::max(ctas, (size_t)((li.gen_tab + li.tile - 1) / li.tile) * li.n_inst);
+  return per * ctas;
 }
 
 cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
-                           const int8_t* spins, double* logZR, double* dbeta, double*,
+                           const int8_t* spins, double* logZR, double* dbeta, float* garena,
                            cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
@@ -455,11 +480,12 @@ cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem
   if (dbeta) {
     e = cudaFuncSetAttribute(general_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_kernel<true><<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, spins, logZR, dbeta);
+    general_kernel<true><<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, spins, logZR, dbeta, garena);
   } else {
     e = cudaFuncSetAttribute(general_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_kernel<false><<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, spins, logZR, dbeta);
+    general_kernel<false><<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, pairs, spins, logZR, dbeta,
+                                                            garena);
   }
   return cudaGetLastError();
 }
