@@ -492,7 +492,15 @@ def run_ours(a):
                 e1.record(stream)
             torch.cuda.synchronize()
             t_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
-            planned.append({"w_u": wu, "n_w": len(Wp), "width": wp, "finder_s": t_plan,
+            # per-kernel device times of two eager steps (profiling hooks)
+            bp = mp.buffers(Bp)
+            mp.ctx.profile(True)
+            for i in range(2):
+                mp.train_step(Bp, seed, 10 ** 6 + i, prec, 0.01, bp, dbs, djs, stream)
+            torch.cuda.synchronize()
+            mp.ctx.profile(False)
+            kern = {k: round(v[0] / v[1], 4) for k, v in mp.ctx.profile_read().items()}
+            planned.append({"w_u": wu, "ms_per_launch": kern, "n_w": len(Wp), "width": wp, "finder_s": t_plan,
                             "components": info["n_components"], "max_component": info["max_component"],
                             "arena_floats": info["arena"], "arena_live_floats": info["arena_live"],
                             "batch": Bp * world, "ms_per_step": t_ms, "value": Bp * world / (t_ms / 1e3)})
