@@ -1275,6 +1275,25 @@ static int ensure_dj_part(tnvan_ctx* ctx, size_t floats) {
   return TNVAN_OK;
 }
 
+// Where the elimination kernels keep their per-sample tables (floats_per_
+// sample of them): shared memory while 32 samples per CTA fit in 200 KB
+// (the largest power-of-two tile up to 64), else a global scratch slice per
+// CTA with 64 samples.  smem(T, global) gives a launch's shared bytes.
+extern "C++" {
+template <class F>
+bool gen_tables_global(int floats_per_sample, F smem, int* T) {
+  (void)floats_per_sample;
+  int t = 64;
+  while (t > 1 && smem(t, false) > 200 * 1024) t /= 2;
+  if (t >= 32) {
+    *T = t;
+    return false;
+  }
+  *T = 64;
+  return true;
+}
+}  // extern "C++"
+
 // Global table scratch of the elimination kernels (which: 0 forward, 1
 // reverse sweep); grows only, kept for the context's lifetime.
 static int ensure_gen_scratch(tnvan_ctx* ctx, int which, size_t floats) {
@@ -2304,13 +2323,11 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
         pairs = std::max(pairs, in.g_npairs);
         Dm = std::max(Dm, (int)in.W.size());
       }
-    // tables in shared memory while 32 samples per CTA fit, else in global
-    // scratch with 64 samples per CTA
     const bool db = d_dbeta != nullptr;
     int T = 64;
-    while (T > 1 && general_smem_bytes(arena, pairs, Dm, T, db, false) > 200 * 1024) T /= 2;
-    const bool glob = T < 32;
-    if (glob) T = 64;
+    const bool glob = gen_tables_global(arena * (db ? 2 : 1), [&](int t, bool g) {
+      return general_smem_bytes(arena, pairs, Dm, t, db, g);
+    }, &T);
     const int sm = general_smem_bytes(arena, pairs, Dm, T, db, glob);
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
     LaunchInfo lg;
@@ -2402,9 +2419,9 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         }
       if (any_gen) {
         int T = 64;
-        while (T > 1 && general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T, false) > 200 * 1024) T /= 2;
-        const bool glob = T < 32;  // tables in global scratch, 64 samples per CTA
-        if (glob) T = 64;
+        const bool glob = gen_tables_global(2 * arena + steps, [&](int t, bool g) {
+          return general_dJ_smem_bytes(arena, pairs, steps, Dm, me, t, g);
+        }, &T);
         const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T, glob);
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
