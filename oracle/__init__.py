@@ -16,6 +16,8 @@ Modules and the passages they restate:
   dense      Eq. 4 for a fully connected leftover block: plain 2^|R| sum.
   general    Eq. 4 for general leftover components: enumeration, or variable
              elimination in its own min-degree order.
+  slicing    Sec. 2 width sets: the width of an elimination order, exact
+             treewidth and smallest width sets of small graphs.
   made       Eq. 6-8 (MADE conditionals, log q, ancestral sampling).
   estimators Eq. 5, 9, 10 (F_q, importance-sampled log Z, REINFORCE weights
              and gradient, exact enumeration of F_q) and the Adam update.
