@@ -357,6 +357,22 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     if ((rc = upload(ctx, in, in.gfldJ, &fj))) return rc;
     GenDev& g = in.dev.gen;
     g.n_comp = in.g_ncomp;
+    int *fp = nullptr, *fhd = nullptr, *fst = nullptr;
+    unsigned short* mpd = nullptr;
+    if ((rc = upload(ctx, in, in.gfprog, &fp))) return rc;
+    if ((rc = upload(ctx, in, in.gfhdr, &fhd))) return rc;
+    if ((rc = upload(ctx, in, in.gfstep, &fst))) return rc;
+    if ((rc = upload(ctx, in, in.gmap, &mpd))) return rc;
+    std::vector<float> zpp(2 * (size_t)std::max(in.g_npp, 1), 0.f);
+    float* ppd = nullptr;
+    if ((rc = upload(ctx, in, zpp, &ppd))) return rc;
+    g.fprog = fp;
+    g.fhdr = fhd;
+    g.fstep = fst;
+    g.map = mpd;
+    g.pp = ppd;
+    g.n_pp = in.g_npp;
+    g.n_steps = (int)in.gfstep.size();
     g.max_entries = in.g_max_entries;
     g.max_live = in.g_max_live;
     g.prog = prog;
@@ -2316,23 +2332,27 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s), "dense kernel");
   }
   if (k2) {
-    int arena = 0, pairs = 0, Dm = 0;
+    int arena = 0, Dm = 0, nsteps = 0;
     for (const Instance& in : ctx->inst)
       if (in.kind == 2) {
         arena = std::max(arena, in.g_max_live);
-        pairs = std::max(pairs, in.g_npairs);
         Dm = std::max(Dm, (int)in.W.size());
+        nsteps = std::max(nsteps, (int)in.gfstep.size());
       }
     const bool db = d_dbeta != nullptr;
     int T = 64;
     const bool glob = gen_tables_global(arena * (db ? 2 : 1), [&](int t, bool g) {
-      return general_smem_bytes(arena, pairs, Dm, t, db, g);
+      return general_smem_bytes(arena, Dm, t, db, g);
     }, &T);
-    const int sm = general_smem_bytes(arena, pairs, Dm, T, db, glob);
+    const int sm = general_smem_bytes(arena, Dm, T, db, glob);
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
     LaunchInfo lg;
     if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
-    lg.seed = (unsigned long long)arena | ((unsigned long long)pairs << 32);
+    lg.seed = (unsigned long long)arena;
+    {
+      PROF("general_pp", s);
+      CK(launch_general_pp(ctx->d_inst, lg, nsteps, s), "elimination bond products");
+    }
     // components with small boundaries: tables when they are smaller than the batch
     for (const Instance& in : ctx->inst)
       if (in.kind == 2 && in.g_ntab > 0 && in.g_ntab <= batch)
@@ -2406,23 +2426,23 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         PROF("dense_dJ", s);
         CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
       }
-      int arena = 0, pairs = 0, steps = 0, Dm = 0, me = 0;
+      int arena = 0, steps = 0, Dm = 0, me = 0, nsteps = 0;
       bool any_gen = false;
       for (const Instance& in : ctx->inst)
         if (in.kind == 2) {
           any_gen = true;
           arena = std::max(arena, in.g_max_entries);
-          pairs = std::max(pairs, in.g_npairs);
           steps = std::max(steps, in.g_max_steps);
           Dm = std::max(Dm, (int)in.W.size());
           me = std::max(me, in.m);
+          nsteps = std::max(nsteps, (int)in.gfstep.size());
         }
       if (any_gen) {
         int T = 64;
         const bool glob = gen_tables_global(2 * arena + steps, [&](int t, bool g) {
-          return general_dJ_smem_bytes(arena, pairs, steps, Dm, me, t, g);
+          return general_dJ_smem_bytes(arena, steps, Dm, me, t, g);
         }, &T);
-        const int sm = general_dJ_smem_bytes(arena, pairs, steps, Dm, me, T, glob);
+        const int sm = general_dJ_smem_bytes(arena, steps, Dm, me, T, glob);
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
         if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
@@ -2434,8 +2454,12 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
             return rc;
           gs = ctx->d_gen_scratch[1];
         }
+        {
+          PROF("general_pp", s);
+          CK(launch_general_pp(ctx->d_inst, lg, nsteps, s), "elimination bond products");
+        }
         PROF("general_dJ", s);
-        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, pairs, steps, d_spins, ctx->d_dj_part, stride, d_dJ, gs, s),
+        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, steps, d_spins, ctx->d_dj_part, stride, d_dJ, gs, s),
            "general adjoint kernel");
       }
     }
@@ -2709,6 +2733,55 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos, cons
     if (it == where.end()) return fail(ctx, TNVAN_E_UNSUPPORTED, "internal: no final table");
     fwd[hdr + 2] = it->second.first;
     live_max = std::max(live_max, (top + 3) & ~3);
+  }
+  // compiled step records and input index maps
+  {
+    std::vector<int> F, fh, fs(step_off.size());
+    std::vector<unsigned short> mp;
+    int npp = 0;
+    for (size_t c = 0; c < comps.size(); ++c) {
+      const int hdr = ctab[5 * c];
+      fh.push_back((int)F.size());
+      F.push_back(prog[hdr]);
+      F.push_back(fwd[hdr + 2]);
+      F.push_back(prog[hdr + 2]);
+      for (int st = comp_step0[c]; st < comp_step0[c + 1]; ++st) {
+        const int r = step_off[st];
+        const int m = prog[r + 3], nin = prog[r + 5], npair = prog[r + 6], E = 2 << m;
+        fs[st] = (int)F.size();
+        F.push_back(m);
+        F.push_back(prog[r + 1]);
+        F.push_back(prog[r + 2]);
+        F.push_back(nin);
+        F.push_back(npair);
+        F.push_back(npp);
+        F.push_back((int)mp.size());
+        F.push_back(fwd[r + 4]);
+        F.push_back(prog[r + 4]);
+        npp += E;
+        int q = r + 7;
+        for (int i = 0; i < nin; ++i) {
+          const int k = prog[q + 1];
+          F.push_back(fwd[q]);
+          F.push_back(prog[q]);
+          for (int ext = 0; ext < E; ++ext) {
+            int idx = 0;
+            for (int j = 0; j < k; ++j) idx |= ((ext >> prog[q + 2 + j]) & 1) << j;
+            mp.push_back((unsigned short)idx);
+          }
+          q += 2 + k;
+        }
+        for (int j = 0; j < npair; ++j) {
+          F.push_back(prog[q + 2 * j]);
+          F.push_back(prog[q + 2 * j + 1]);
+        }
+      }
+    }
+    in.gfprog.swap(F);
+    in.gfhdr.swap(fh);
+    in.gfstep.swap(fs);
+    in.gmap.swap(mp);
+    in.g_npp = npp;
   }
   in.gprog_fwd.swap(fwd);
   in.g_max_live = live_max;

@@ -131,6 +131,22 @@ struct GenDev {
   int max_live;          // the same with a table's space reused once it is consumed
   const int* prog;       // packed int program, every table at its own offset (reverse sweeps)
   const int* prog_fwd;   // the same program with reused offsets (forward-only passes)
+  // Compiled form run by the kernels.  Per component c, at fhdr[c]:
+  //   n_steps, final table (live offset), final table (full offset);
+  // per step (global step index g, record at fstep[g]):
+  //   m, fld_begin, fld_count, n_in, n_pair, pp_off, map_off, out_live, out_full,
+  //   n_in x (in_live, in_full), n_pair x (pair_id, pos_u).
+  // map[map_off + i * 2^(m+1) + ext]: entry of input i at extended index ext
+  // (bit j of ext: out-scope spin j, bit m: the eliminated spin).
+  // pp[pp_off + ext]: product of the step's bond factors at ext (this
+  // call's beta, general_pp_kernel); pp[n_pp + pp_off + ext] its d ln / d beta.
+  const int* fprog;
+  const int* fhdr;
+  const int* fstep;
+  const unsigned short* map;
+  float* pp;
+  int n_pp;
+  int n_steps;           // steps of all components
   int prog_len;
   const float* pairJ;    // couplings of R-R bonds referenced by the program
   const int* pairE;      // edge id of each pair
@@ -220,6 +236,9 @@ struct Instance {
   double dense_chat = 0;
   // general
   std::vector<int> gprog, gprog_fwd, gfld, gpairE, gstep_off, gcomp_step0;
+  std::vector<int> gfprog, gfhdr, gfstep;  // compiled step records (GenDev::fprog)
+  std::vector<unsigned short> gmap;       // input index maps (GenDev::map)
+  int g_npp = 0;
   int g_max_steps = 0;
   std::vector<int> gctab, gbpos, gtabc;  // component tables (GenDev)
   int g_ntab = 0;
@@ -308,10 +327,12 @@ cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precis
 cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                            const int8_t* spins, double* logZR, double* dbeta, float* garena,
                            cudaStream_t s);
-cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena,
-                              int pairs, int steps, const int8_t* spins, float* part, int part_stride,
-                              double* dJ, float* garena, cudaStream_t s);
-int general_dJ_smem_bytes(int arena, int pairs, int steps, int D, int n_edges, int T, bool glob);
+cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int steps,
+                              const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
+                              cudaStream_t s);
+// bond products of every elimination step at li.beta (before the kernels above)
+cudaError_t launch_general_pp(const InstDev* d_inst, const LaunchInfo& li, int max_steps, cudaStream_t s);
+int general_dJ_smem_bytes(int arena, int steps, int D, int n_edges, int T, bool glob);
 size_t general_dJ_scratch_floats(int arena, int steps, int T, int nblk);
 size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
@@ -365,7 +386,7 @@ extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 
 int sample_smem_bytes(const Instance& in, int tile);
-int general_smem_bytes(int arena, int pairs, int D, int T, bool db, bool glob);
+int general_smem_bytes(int arena, int D, int T, bool db, bool glob);
 cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
                                   float* garena, cudaStream_t s);
 int strip_smem_bytes(const Instance& in, int tile);
