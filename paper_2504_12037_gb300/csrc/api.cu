@@ -1291,22 +1291,24 @@ static int ensure_dj_part(tnvan_ctx* ctx, size_t floats) {
   return TNVAN_OK;
 }
 
-// Where the elimination kernels keep their per-sample tables (floats_per_
-// sample of them): shared memory while 32 samples per CTA fit in 200 KB
-// (the largest power-of-two tile up to 64), else a global scratch slice per
-// CTA with 64 samples.  smem(T, global) gives a launch's shared bytes.
+// Elimination launch shape: GL lanes share a sample (the largest power of two
+// up to 16 not above the instances' mean table size) and a CTA has 128
+// threads, so 128 / GL samples.  The tables stay in shared memory when a CTA
+// needs at most 100 KB of it (two CTAs per SM), else they go to a global
+// scratch slice per CTA.  smem(S, global) gives a launch's shared bytes.
 extern "C++" {
+int gen_lanes(const tnvan_ctx* ctx) {
+  double mean = 1;
+  for (const Instance& in : ctx->inst)
+    if (in.kind == 2) mean = std::max(mean, in.g_mean_entries);
+  int gl = 1;
+  while (gl < 16 && 2 * gl <= mean) gl *= 2;
+  return gl;
+}
+
 template <class F>
-bool gen_tables_global(int floats_per_sample, F smem, int* T) {
-  (void)floats_per_sample;
-  int t = 64;
-  while (t > 1 && smem(t, false) > 200 * 1024) t /= 2;
-  if (t >= 32) {
-    *T = t;
-    return false;
-  }
-  *T = 64;
-  return true;
+bool gen_tables_global(int S, F smem) {
+  return smem(S, false) > 100 * 1024;
 }
 }  // extern "C++"
 
@@ -2339,11 +2341,10 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
         Dm = std::max(Dm, (int)in.W.size());
         nsteps = std::max(nsteps, (int)in.gfstep.size());
       }
+    arena |= 1;  // odd per-sample stride: samples of a warp fall in different banks
     const bool db = d_dbeta != nullptr;
-    int T = 64;
-    const bool glob = gen_tables_global(arena * (db ? 2 : 1), [&](int t, bool g) {
-      return general_smem_bytes(arena, Dm, t, db, g);
-    }, &T);
+    const int GL = gen_lanes(ctx), T = 128 / GL;
+    const bool glob = gen_tables_global(T, [&](int t, bool g) { return general_smem_bytes(arena, Dm, t, db, g); });
     const int sm = general_smem_bytes(arena, Dm, T, db, glob);
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
     LaunchInfo lg;
@@ -2364,10 +2365,10 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     }
     if (lg.gen_tab > 0) {
       PROF("general_tables", s);
-      CK(launch_general_tables(ctx->d_inst, lg, sm, db, gs, s), "general tables kernel");
+      CK(launch_general_tables(ctx->d_inst, lg, sm, db, GL, gs, s), "general tables kernel");
     }
     PROF(d_dbeta ? "general_dbeta" : "general", s);
-    CK(launch_general(ctx->d_inst, lg, sm, d_spins, d_logZR, d_dbeta, gs, s), "general kernel");
+    CK(launch_general(ctx->d_inst, lg, sm, GL, d_spins, d_logZR, d_dbeta, gs, s), "general kernel");
   }
   return TNVAN_OK;
 }
@@ -2438,10 +2439,10 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
           nsteps = std::max(nsteps, (int)in.gfstep.size());
         }
       if (any_gen) {
-        int T = 64;
-        const bool glob = gen_tables_global(2 * arena + steps, [&](int t, bool g) {
-          return general_dJ_smem_bytes(arena, steps, Dm, me, t, g);
-        }, &T);
+        if (((2 * arena + steps) & 1) == 0) ++steps;  // odd per-sample stride (banks)
+        const int GL = gen_lanes(ctx), T = 128 / GL;
+        const bool glob =
+            gen_tables_global(T, [&](int t, bool g) { return general_dJ_smem_bytes(arena, steps, Dm, me, t, g); });
         const int sm = general_dJ_smem_bytes(arena, steps, Dm, me, T, glob);
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
@@ -2459,7 +2460,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
           CK(launch_general_pp(ctx->d_inst, lg, nsteps, s), "elimination bond products");
         }
         PROF("general_dJ", s);
-        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, steps, d_spins, ctx->d_dj_part, stride, d_dJ, gs, s),
+        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, steps, GL, d_spins, ctx->d_dj_part, stride, d_dJ, gs, s),
            "general adjoint kernel");
       }
     }
@@ -2776,6 +2777,11 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos, cons
           F.push_back(prog[q + 2 * j + 1]);
         }
       }
+    }
+    {
+      double tot = 0;
+      for (size_t st = 0; st < step_off.size(); ++st) tot += (double)(1 << prog[step_off[st] + 3]);
+      in.g_mean_entries = step_off.empty() ? 1.0 : tot / (double)step_off.size();
     }
     in.gfprog.swap(F);
     in.gfhdr.swap(fh);

@@ -239,6 +239,7 @@ struct Instance {
   std::vector<int> gfprog, gfhdr, gfstep;  // compiled step records (GenDev::fprog)
   std::vector<unsigned short> gmap;       // input index maps (GenDev::map)
   int g_npp = 0;
+  double g_mean_entries = 1;  // mean table size (entries) of the elimination steps
   int g_max_steps = 0;
   std::vector<int> gctab, gbpos, gtabc;  // component tables (GenDev)
   int g_ntab = 0;
@@ -324,11 +325,13 @@ cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precis
 // Elimination kernels keep their tables in shared memory, or (garena
 // non-NULL: arenas too large for 32 samples per CTA) in a global scratch
 // buffer of general_scratch_floats / general_dJ_scratch_floats floats.
-cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+// li.tile = samples per CTA, GL lanes per sample (li.tile * GL threads, a
+// multiple of 32).
+cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int GL,
                            const int8_t* spins, double* logZR, double* dbeta, float* garena,
                            cudaStream_t s);
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int steps,
-                              const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
+                              int GL, const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
                               cudaStream_t s);
 // bond products of every elimination step at li.beta (before the kernels above)
 cudaError_t launch_general_pp(const InstDev* d_inst, const LaunchInfo& li, int max_steps, cudaStream_t s);
@@ -387,7 +390,7 @@ cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a
 
 int sample_smem_bytes(const Instance& in, int tile);
 int general_smem_bytes(int arena, int D, int T, bool db, bool glob);
-cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
+cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db, int GL,
                                   float* garena, cudaStream_t s);
 int strip_smem_bytes(const Instance& in, int tile);
 int strip_adj_smem_bytes(const Instance& in, int tile, int lv_floats);

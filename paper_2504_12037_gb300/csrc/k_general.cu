@@ -11,9 +11,9 @@
 // the input's entry; the product of a step's bond factors depends only on
 // that index and beta and is tabulated once per call (general_pp_kernel), so
 // a table entry costs one field factor, one bond product and one load per
-// input.  Tables live in a per-sample arena, laid out [entry][sample] so that
-// the threads of a warp (one sample each) touch consecutive words: in shared
-// memory, or for large arenas in a per-CTA slice of global scratch.  Forward
+// input.  A group of lanes shares one sample and splits each table's entries;
+// tables live in a per-sample arena (sample-major) in shared memory, or for
+// large arenas in a per-CTA slice of global scratch.  Forward
 // passes use reused offsets (a table's space is free once the step that
 // consumes it has run); the reverse sweep keeps every table.  Every new table
 // is renormalised by a power of two.  Factors are stored normalised (largest
@@ -21,6 +21,7 @@
 // are added back in FP64.  With DB, every table entry carries its
 // beta-derivative (forward mode).
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 
@@ -93,11 +94,23 @@ __global__ void __launch_bounds__(256) general_pp_kernel(const InstDev* __restri
   }
 }
 
-// Component c for this thread's spin row s (forward, live offsets): adds
-// log Z_c (and with DB its beta-derivative) to lz / dl.
+// Lanes per sample: a group of GL consecutive lanes (a power of two, at most
+// 32, so that a group lies inside one warp) shares one sample; lane l of the
+// group computes the table entries x = l, l + GL, ...  Every lane of a block
+// runs the same program (invalid samples run on a dummy row), so the
+// group-wide maximum and __syncwarp between steps see full warps.
+__device__ __forceinline__ float group_max(float v, int GL) {
+  for (int o = GL >> 1; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Component c for the sample whose tables start at A (sample-major: entry e
+// at A[e]; with DB the beta-derivatives at dA[e]); forward, live offsets.
+// Adds log Z_c (and with DB its beta-derivative) to lz / dl (the same value
+// on every lane of the group).
 template <bool DB>
-__device__ __forceinline__ void run_component(const GenDev& G, int c, const int8_t* s, float* A, float* dA, int T,
-                                              int t, float beta, double& lz, double& dl) {
+__device__ __forceinline__ void run_component(const GenDev& G, int c, const int8_t* s, float* A, float* dA, int lane,
+                                              int GL, float beta, double& lz, double& dl) {
   const int* H = G.fprog + G.fhdr[c];
   const int nsteps = H[0], fin = H[1];
   const int g0 = G.comp_step0[c];
@@ -115,7 +128,7 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
     const unsigned short* mp = G.map + r.mo;
     const int out = r.out_live;
     float mx = 0.f;
-    for (int x = 0; x < M; ++x) {
+    for (int x = lane; x < M; x += GL) {
       float acc = 0.f, dacc = 0.f;
 #pragma unroll
       for (int sg = 0; sg < 2; ++sg) {
@@ -123,7 +136,7 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
         float p = fv[sg] * pp[ext];
         float rr = DB ? fr[sg] + pd[ext] : 0.f;
         for (int i = 0; i < r.nin; ++i) {
-          const int a = (r.io[2 * i] + mp[i * E + ext]) * T + t;
+          const int a = r.io[2 * i] + mp[i * E + ext];
           const float val = A[a];
           p *= val;
           if (DB) rr += dA[a] / val;
@@ -131,21 +144,23 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
         acc += p;
         if (DB) dacc = fmaf(p, rr, dacc);
       }
-      A[(out + x) * T + t] = acc;
-      if (DB) dA[(out + x) * T + t] = dacc;
+      A[out + x] = acc;
+      if (DB) dA[out + x] = dacc;
       mx = fmaxf(mx, acc);
     }
+    mx = group_max(mx, GL);
     const int e = exponent_of(mx);
     const float sc = pow2i(-e);
-    for (int x = 0; x < M; ++x) {
-      A[(out + x) * T + t] *= sc;
-      if (DB) dA[(out + x) * T + t] *= sc;
+    for (int x = lane; x < M; x += GL) {
+      A[out + x] *= sc;
+      if (DB) dA[out + x] *= sc;
     }
     lz += (double)e * 0.69314718055994530942;
+    __syncwarp();
   }
-  const float z = A[fin * T + t];
+  const float z = A[fin];
   lz += (double)logf(z);
-  if (DB) dl += (double)(dA[fin * T + t] / z);
+  if (DB) dl += (double)(dA[fin] / z);
 }
 
 // Boundary index of component c for spin row s: bit j set iff its j-th
@@ -156,33 +171,40 @@ __device__ __forceinline__ int boundary_index(const GenDev& G, const int* cr, co
   return idx;
 }
 
+// Stage the spin rows of this CTA's samples in shared memory (rows of
+// samples past the batch set to +1).
+__device__ __forceinline__ void stage_spins(int8_t* ssp, const int8_t* gsp, int n_valid, int S, int D, int Dp) {
+  for (int e = threadIdx.x; e < n_valid * D; e += blockDim.x) ssp[(e / D) * Dp + (e % D)] = gsp[e];
+  for (int e = n_valid * Dp + threadIdx.x; e < S * Dp; e += blockDim.x) ssp[e] = 1;
+}
+
+// li.tile = samples per CTA (S); blockDim.x = S * GL.
 template <bool DB>
-__global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__ inst,
-                                                     const LaunchInfo li, int arena_floats,
-                                                     const int8_t* __restrict__ spins,
-                                                     double* __restrict__ logZR,
-                                                     double* __restrict__ dbeta, float* __restrict__ garena) {
+__global__ void __launch_bounds__(128) general_kernel(const InstDev* __restrict__ inst,
+                                                      const LaunchInfo li, int arena_floats, int GL,
+                                                      const int8_t* __restrict__ spins,
+                                                      double* __restrict__ logZR,
+                                                      double* __restrict__ dbeta, float* __restrict__ garena) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
   if (I.kind != 2) return;
-  const int T = li.tile, t = threadIdx.x;
-  const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
+  const int S = li.tile, slot = threadIdx.x / GL, lane = threadIdx.x % GL;
+  const int b0 = (blockIdx.x - li.tile_begin[k]) * S, b = b0 + slot;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  // tables [arena][T] (and their beta-derivatives) in shared memory, or for
-  // large arenas in this CTA's slice of a global scratch buffer
-  const size_t cta_floats = (size_t)arena_floats * T * (DB ? 2 : 1);
-  float* A = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
-  float* dA = A + arena_floats * T;
+  // tables [sample][arena] (then their beta-derivatives) in shared memory, or
+  // for large arenas in this CTA's slice of a global scratch buffer
+  const size_t cta_floats = (size_t)arena_floats * S * (DB ? 2 : 1);
+  float* base = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
+  float* A = base + (size_t)slot * arena_floats;
+  float* dA = A + (size_t)S * arena_floats;
   int8_t* ssp = reinterpret_cast<int8_t*>(garena ? sm : sm + cta_floats);
   const GenDev& G = I.gen;
-  const int n_valid = min(T, li.batch - b0);
-  const int8_t* gsp = spins + I.spin_units * li.batch + (long long)b0 * D;
-  for (int e = t; e < n_valid * D; e += T) ssp[(e / D) * Dp + (e % D)] = gsp[e];
+  const int n_valid = min(S, li.batch - b0);
+  stage_spins(ssp, spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, S, D, Dp);
   __syncthreads();
-  if (b >= li.batch) return;
-  const int8_t* s = ssp + t * Dp;
+  const int8_t* s = ssp + slot * Dp;
   const bool tab = li.gen_tab && G.n_tab > 0 && G.n_tab <= li.batch;  // tables built for this call
   double lz = 0.0, dl = 0.0;
   for (int c = 0; c < G.n_comp; ++c) {
@@ -192,9 +214,10 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
       lz += G.tab_lz[cr[4] + x];
       if (DB) dl += G.tab_db[cr[4] + x];
     } else {
-      run_component<DB>(G, c, s, A, dA, T, t, beta, lz, dl);
+      run_component<DB>(G, c, s, A, dA, lane, GL, beta, lz, dl);
     }
   }
+  if (lane != 0 || b >= li.batch) return;
   float e1 = 0.f;
   for (int e = 0; e < I.n_ww; ++e) {
     const EdgeWW q = I.ww[e];
@@ -207,33 +230,36 @@ __global__ void __launch_bounds__(64) general_kernel(const InstDev* __restrict__
 }
 
 // The tables of the tabulated components (at most TNVAN_TAB_MAX_K width-set
-// neighbours): thread g of instance k takes entry g of the concatenated
+// neighbours): group g of instance k takes entry g of the concatenated
 // tables, i.e. one component c and one boundary configuration x, sets the
 // boundary spins of a spin row from the bits of x (the other spins do not
 // enter c) and runs c's program alone, so that tab_lz[toff_c + x] = log Z_c
 // and tab_db[..] its beta-derivative.  Built per call (they depend on beta)
 // when they are smaller than the batch.
 template <bool DB>
-__global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
-                                                         int arena_floats, float* __restrict__ garena) {
+__global__ void __launch_bounds__(128) general_tab_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                          int arena_floats, int GL, float* __restrict__ garena) {
   extern __shared__ float sm[];
   const int k = blockIdx.y;
   const InstDev& I = inst[k];
   if (I.kind != 2) return;
   const GenDev& G = I.gen;
   if (G.n_tab == 0 || G.n_tab > li.batch) return;
-  const int T = blockDim.x, t = threadIdx.x;
-  const int g = blockIdx.x * T + t;
+  const int S = li.tile, slot = threadIdx.x / GL, lane = threadIdx.x % GL;
+  const int g = blockIdx.x * S + slot;
+  if (blockIdx.x * S >= G.n_tab) return;  // whole CTA idle (uniform)
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  const size_t cta_floats = (size_t)arena_floats * T * (DB ? 2 : 1);
-  float* A = garena ? garena + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * cta_floats : sm;
-  float* dA = A + arena_floats * T;
+  const size_t cta_floats = (size_t)arena_floats * S * (DB ? 2 : 1);
+  float* base = garena ? garena + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * cta_floats : sm;
+  float* A = base + (size_t)slot * arena_floats;
+  float* dA = A + (size_t)S * arena_floats;
   int8_t* ssp = reinterpret_cast<int8_t*>(garena ? sm : sm + cta_floats);
-  int8_t* s = ssp + t * Dp;
-  for (int j = 0; j < D; ++j) s[j] = 1;
-  if (blockIdx.x * T >= G.n_tab || g >= G.n_tab) return;
-  // which tabulated component and configuration
+  int8_t* s = ssp + slot * Dp;
+  for (int j = lane; j < D; j += GL) s[j] = 1;
+  __syncwarp();
+  // which tabulated component and configuration (entries past the tables
+  // run the first tabulated component on the all-up row, unwritten)
   int c = -1, x = 0;
   for (int j = 0; j < G.n_tabc; ++j) {
     const int* cr = G.ctab + 5 * G.tabc[j];
@@ -243,13 +269,32 @@ __global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restri
       break;
     }
   }
-  if (c < 0) return;
-  const int* cr = G.ctab + 5 * c;
-  for (int j = 0; j < cr[2]; ++j) s[G.bpos[cr[3] + j]] = ((x >> j) & 1) ? -1 : 1;
-  double lz = 0.0, dl = 0.0;
-  run_component<DB>(G, c, s, A, dA, T, t, beta, lz, dl);
-  G.tab_lz[g] = lz;
-  if (DB) G.tab_db[g] = dl;
+  const bool live = c >= 0;
+  // every group of a warp must run the same component (shuffles, syncwarp):
+  // the components of one warp's entries may differ, so a warp walks the
+  // distinct components of its groups in turn
+  const unsigned wmask = 0xffffffffu;
+  int cc = live ? c : G.tabc[0];
+  __syncwarp();
+  for (;;) {
+    // the smallest component index still to run in this warp
+    int want = cc;
+    for (int o = 16; o > 0; o >>= 1) want = min(want, __shfl_xor_sync(wmask, want, o));
+    if (want == INT_MAX) break;
+    const bool mine = cc == want;
+    const int* cr = G.ctab + 5 * want;
+    if (mine && live && lane == 0)
+      for (int j = 0; j < cr[2]; ++j) s[G.bpos[cr[3] + j]] = ((x >> j) & 1) ? -1 : 1;
+    __syncwarp();
+    double lz = 0.0, dl = 0.0;
+    run_component<DB>(G, want, s, A, dA, lane, GL, beta, lz, dl);
+    if (mine && live && lane == 0) {
+      G.tab_lz[g] = lz;
+      if (DB) G.tab_db[g] = dl;
+    }
+    if (mine) cc = INT_MAX;
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -260,53 +305,48 @@ __global__ void __launch_bounds__(64) general_tab_kernel(const InstDev* __restri
 // entry, starting from 1 / A_final.  For step t with product terms
 // term(x, sigma) (field factor, bond factors, input tables):
 //   g(x, sigma)       = Abar_t[x] 2^-e_t term(x, sigma)
-//   Abar_in[idx]     += g / A_in[idx]
+//   Abar_in[idx]     += g / A_in[idx]   (atomic: lanes of a group share inputs)
 //   d lnZ / d J_bond += beta sum g sigma sigma_u,  d lnZ / d J_field += beta s_w sum g sigma.
-// Bond sums are warp-reduced into per-CTA shared accumulators, written as one
-// row per CTA and added per instance in a fixed order.
+// Bond sums are warp-reduced (over samples and lanes) into per-CTA shared
+// accumulators, written as one row per CTA and added per instance in a fixed
+// order.
 // ---------------------------------------------------------------------------
-// (blocks of fewer than 32 threads have one partial warp: no shuffles there,
-// every thread adds its own term)
 __device__ __forceinline__ void acc_edge(float* acc, int e, float v, bool lane0) {
-  if (blockDim.x >= 32) {
-    v = warp_sum(v);
-    if (lane0 && e >= 0) atomicAdd(acc + e, v);
-  } else if (e >= 0) {
-    atomicAdd(acc + e, v);
-  }
+  v = warp_sum(v);
+  if (lane0 && e >= 0) atomicAdd(acc + e, v);
 }
 
-__global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restrict__ inst,
-                                                        const LaunchInfo li, int arena_floats, int max_steps,
-                                                        const int8_t* __restrict__ spins,
-                                                        float* __restrict__ part, int part_stride,
-                                                        float* __restrict__ garena) {
+__global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restrict__ inst,
+                                                         const LaunchInfo li, int arena_floats, int max_steps,
+                                                         int GL, const int8_t* __restrict__ spins,
+                                                         float* __restrict__ part, int part_stride,
+                                                         float* __restrict__ garena) {
   extern __shared__ float sm[];
   const int k = find_inst(li, blockIdx.x);
   const InstDev& I = inst[k];
   if (I.kind != 2) return;
-  const int T = li.tile, t = threadIdx.x;
-  const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
+  const int S = li.tile, slot = threadIdx.x / GL, lane = threadIdx.x % GL;
+  const int b0 = (blockIdx.x - li.tile_begin[k]) * S, b = b0 + slot;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  // tables, adjoints and scales in shared memory, or for large arenas in this
-  // CTA's slice of a global scratch buffer
-  const size_t cta_floats = (size_t)(2 * arena_floats + max_steps) * T;
-  float* A = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;  // [arena][T]
-  float* Ab = A + arena_floats * T;       // [arena][T] adjoints
-  float* sc = Ab + arena_floats * T;      // [max_steps][T] scales 2^-e
+  // per sample: tables, adjoints, scales (sample-major), in shared memory or
+  // for large arenas in this CTA's slice of a global scratch buffer
+  const size_t per = (size_t)(2 * arena_floats + max_steps);
+  const size_t cta_floats = per * S;
+  float* base = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
+  float* A = base + (size_t)slot * per;   // [arena]
+  float* Ab = A + arena_floats;           // [arena] adjoints
+  float* sc = Ab + arena_floats;          // [max_steps] scales 2^-e
   float* acc = garena ? sm : sm + cta_floats;  // [n_edges]
   int8_t* ssp = reinterpret_cast<int8_t*>(acc + ((I.n_edges + 3) & ~3));
   const GenDev& G = I.gen;
-  for (int e = t; e < I.n_edges; e += T) acc[e] = 0.f;
-  const int n_valid = min(T, li.batch - b0);
-  const int8_t* gsp = spins + I.spin_units * li.batch + (long long)b0 * D;
-  for (int e = t; e < n_valid * D; e += T) ssp[(e / D) * Dp + (e % D)] = gsp[e];
-  for (int e = n_valid * Dp + t; e < T * Dp; e += T) ssp[e] = 1;
+  for (int e = threadIdx.x; e < I.n_edges; e += blockDim.x) acc[e] = 0.f;
+  const int n_valid = min(S, li.batch - b0);
+  stage_spins(ssp, spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, S, D, Dp);
   __syncthreads();
   const bool valid = b < li.batch;
-  const bool lane0 = (t & 31) == 0;
-  const int8_t* s = ssp + t * Dp;
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  const int8_t* s = ssp + slot * Dp;
   const float wscale = valid ? beta / (float)li.batch : 0.f;
   for (int c = 0; c < G.n_comp; ++c) {
     const int* H = G.fprog + G.fhdr[c];
@@ -323,23 +363,26 @@ __global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restric
       const unsigned short* mp = G.map + r.mo;
       const int out = r.out_full;
       float mx = 0.f;
-      for (int x = 0; x < M; ++x) {
+      for (int x = lane; x < M; x += GL) {
         float accv = 0.f;
         for (int sg = 0; sg < 2; ++sg) {
           const int ext = x | (sg << r.m);
           float pr = fv[sg] * pp[ext];
-          for (int i = 0; i < r.nin; ++i) pr *= A[(r.io[2 * i + 1] + mp[i * E + ext]) * T + t];
+          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[2 * i + 1] + mp[i * E + ext]];
           accv += pr;
         }
-        A[(out + x) * T + t] = accv;
-        Ab[(out + x) * T + t] = 0.f;
+        A[out + x] = accv;
+        Ab[out + x] = 0.f;
         mx = fmaxf(mx, accv);
       }
+      mx = group_max(mx, GL);
       const float scl = pow2i(-exponent_of(mx));
-      for (int x = 0; x < M; ++x) A[(out + x) * T + t] *= scl;
-      sc[st * T + t] = scl;
+      for (int x = lane; x < M; x += GL) A[out + x] *= scl;
+      if (lane == 0) sc[st] = scl;
+      __syncwarp();
     }
-    Ab[fin * T + t] = 1.f / A[fin * T + t];
+    if (lane == 0) Ab[fin] = 1.f / A[fin];
+    __syncwarp();
     // backward
     for (int st = nsteps - 1; st >= 0; --st) {
       const StepRec r = step_at(G, g0 + st);
@@ -350,7 +393,7 @@ __global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restric
       const float* pp = G.pp + r.ppo;
       const unsigned short* mp = G.map + r.mo;
       const int out = r.out_full;
-      const float scl = sc[st * T + t];
+      const float scl = sc[st];
       const int np = min(r.npair, 8);  // at most 8 neighbours remain
       int pos[8];
 #pragma unroll
@@ -359,32 +402,36 @@ __global__ void __launch_bounds__(64) general_dJ_kernel(const InstDev* __restric
       float gp[8];          // sum g sigma_v sigma_u per pair
 #pragma unroll
       for (int j = 0; j < 8; ++j) gp[j] = 0.f;
-      for (int x = 0; x < M; ++x) {
-        const float abx = Ab[(out + x) * T + t] * scl;
+      for (int x = lane; x < M; x += GL) {
+        const float abx = Ab[out + x] * scl;
         for (int sg = 0; sg < 2; ++sg) {
           const int ext = x | (sg << r.m);
           float pr = fv[sg] * pp[ext];
-          for (int i = 0; i < r.nin; ++i) pr *= A[(r.io[2 * i + 1] + mp[i * E + ext]) * T + t];
+          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[2 * i + 1] + mp[i * E + ext]];
           const float g = abx * pr;
           gs = fmaf(g, sg ? -1.f : 1.f, gs);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (j < np) gp[j] = fmaf(g, (((x >> pos[j]) & 1) == sg) ? 1.f : -1.f, gp[j]);
           for (int i = 0; i < r.nin; ++i) {
-            const int a = (r.io[2 * i + 1] + mp[i * E + ext]) * T + t;
+            const int a = r.io[2 * i + 1] + mp[i * E + ext];
             const float av = A[a];
-            if (av > 0.f) Ab[a] += g / av;
+            if (av > 0.f) {
+              if (GL == 1) Ab[a] += g / av;
+              else atomicAdd(Ab + a, g / av);
+            }
           }
         }
       }
       for (int f = r.fb; f < r.fb + r.fc; ++f)
         acc_edge(acc, G.fld[2 * f + 1], wscale * gs * (float)s[G.fld[2 * f]], lane0);
       for (int j = 0; j < np; ++j) acc_edge(acc, G.pairE[r.pr[2 * j]], wscale * gp[j], lane0);
+      __syncwarp();
     }
   }
   __syncthreads();
   float* row = part + (long long)blockIdx.x * part_stride;
-  for (int e = t; e < I.n_edges; e += T) row[e] = acc[e];
+  for (int e = threadIdx.x; e < I.n_edges; e += blockDim.x) row[e] = acc[e];
 }
 
 __global__ void general_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
@@ -417,13 +464,14 @@ size_t general_dJ_scratch_floats(int arena, int steps, int T, int nblk) {
 }
 
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int steps,
-                              const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
+                              int GL, const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
                               cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(general_dJ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  general_dJ_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, steps, spins, part, part_stride, garena);
+  general_dJ_kernel<<<nblk, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, steps, GL, spins, part, part_stride,
+                                                           garena);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   general_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
@@ -432,7 +480,7 @@ cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int s
 
 // The components' tables at this call's betas (li.gen_tab: the largest
 // table; general_kernel then looks them up).
-cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db,
+cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db, int GL,
                                   float* garena, cudaStream_t s) {
   if (li.gen_tab <= 0) return cudaSuccess;
   const int arena = (int)(li.seed & 0xffffffffull);
@@ -441,11 +489,11 @@ cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, i
   if (db) {
     e = cudaFuncSetAttribute(general_tab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_tab_kernel<true><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, garena);
+    general_tab_kernel<true><<<tg, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, GL, garena);
   } else {
     e = cudaFuncSetAttribute(general_tab_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_tab_kernel<false><<<tg, li.tile, smem_bytes, s>>>(d_inst, li, arena, garena);
+    general_tab_kernel<false><<<tg, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, GL, garena);
   }
   return cudaGetLastError();
 }
@@ -456,8 +504,8 @@ int general_smem_bytes(int arena, int D, int T, bool db, bool glob) {
   return (glob ? 0 : arena * T * 4 * (db ? 2 : 1)) + T * 4 * w4;
 }
 
-// Scratch of the global-table mode: one [arena][T] slice (two with d/dbeta)
-// per CTA of the contraction and of the tables kernel.
+// Scratch of the global-table mode: one [sample][arena] slice (two with
+// d/dbeta) per CTA of the contraction and of the tables kernel.
 size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db) {
   const size_t per = (size_t)arena * li.tile * (db ? 2 : 1);
   size_t ctas = (size_t)li.tile_begin[li.n_inst];
@@ -465,7 +513,7 @@ size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db) {
   return per * ctas;
 }
 
-cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
+cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int GL,
                            const int8_t* spins, double* logZR, double* dbeta, float* garena,
                            cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
@@ -476,11 +524,12 @@ cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem
   if (dbeta) {
     e = cudaFuncSetAttribute(general_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_kernel<true><<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, spins, logZR, dbeta, garena);
+    general_kernel<true><<<nblk, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, GL, spins, logZR, dbeta, garena);
   } else {
     e = cudaFuncSetAttribute(general_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    general_kernel<false><<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, arena, spins, logZR, dbeta, garena);
+    general_kernel<false><<<nblk, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, GL, spins, logZR, dbeta,
+                                                                 garena);
   }
   return cudaGetLastError();
 }
