@@ -2427,7 +2427,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         PROF("dense_dJ", s);
         CK(launch_dense(ctx->d_inst, lt, precision, d_spins, nullptr, nullptr, d_dJ, s), "dense adjoint kernel");
       }
-      int arena = 0, steps = 0, Dm = 0, me = 0, nsteps = 0;
+      int arena = 0, steps = 0, Dm = 0, me = 0, nsteps = 0, mw = 0;
       bool any_gen = false;
       for (const Instance& in : ctx->inst)
         if (in.kind == 2) {
@@ -2437,13 +2437,16 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
           Dm = std::max(Dm, (int)in.W.size());
           me = std::max(me, in.m);
           nsteps = std::max(nsteps, (int)in.gfstep.size());
+          mw = std::max(mw, in.max_width);
         }
       if (any_gen) {
-        if (((2 * arena + steps) & 1) == 0) ++steps;  // odd per-sample stride (banks)
+        const int gmax = 2 << mw;  // g of one step: 2^(m+1) extended indices
+        if (((2 * arena + steps + gmax) & 1) == 0) ++steps;  // odd per-sample stride (banks)
+        const int per = 2 * arena + steps + gmax;
         const int GL = gen_lanes(ctx), T = 128 / GL;
         const bool glob =
-            gen_tables_global(T, [&](int t, bool g) { return general_dJ_smem_bytes(arena, steps, Dm, me, t, g); });
-        const int sm = general_dJ_smem_bytes(arena, steps, Dm, me, T, glob);
+            gen_tables_global(T, [&](int t, bool g) { return general_dJ_smem_bytes(per, Dm, me, t, 128, g); });
+        const int sm = general_dJ_smem_bytes(per, Dm, me, T, 128, glob);
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
         if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
@@ -2451,7 +2454,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
         float* gs = nullptr;
         if (glob) {
-          if ((rc = ensure_gen_scratch(ctx, 1, general_dJ_scratch_floats(arena, steps, T, lg.tile_begin[lg.n_inst]))))
+          if ((rc = ensure_gen_scratch(ctx, 1, general_dJ_scratch_floats(per, T, lg.tile_begin[lg.n_inst]))))
             return rc;
           gs = ctx->d_gen_scratch[1];
         }
@@ -2460,7 +2463,8 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
           CK(launch_general_pp(ctx->d_inst, lg, nsteps, s), "elimination bond products");
         }
         PROF("general_dJ", s);
-        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, steps, GL, d_spins, ctx->d_dj_part, stride, d_dJ, gs, s),
+        CK(launch_general_dJ(ctx->d_inst, lg, sm, arena, steps, gmax, GL, d_spins, ctx->d_dj_part, stride, d_dJ, gs,
+                             s),
            "general adjoint kernel");
       }
     }
@@ -2761,16 +2765,33 @@ int plan_general(tnvan_ctx* ctx, Instance& in, const std::vector<int>& pos, cons
         F.push_back(prog[r + 4]);
         npp += E;
         int q = r + 7;
+        std::vector<std::vector<int>> idx_of(nin, std::vector<int>(E));
+        std::vector<int> kin(nin);
         for (int i = 0; i < nin; ++i) {
           const int k = prog[q + 1];
+          kin[i] = k;
           F.push_back(fwd[q]);
           F.push_back(prog[q]);
+          F.push_back(k);
           for (int ext = 0; ext < E; ++ext) {
             int idx = 0;
             for (int j = 0; j < k; ++j) idx |= ((ext >> prog[q + 2 + j]) & 1) << j;
+            idx_of[i][ext] = idx;
             mp.push_back((unsigned short)idx);
           }
           q += 2 + k;
+        }
+        // inverse maps: per input, the extended indices of each entry (E >> k
+        // of them, increasing), entry-major
+        for (int i = 0; i < nin; ++i) {
+          std::vector<unsigned short> inv(E);
+          std::vector<int> fill_(1 << kin[i], 0);
+          const int R = E >> kin[i];
+          for (int ext = 0; ext < E; ++ext) {
+            const int e = idx_of[i][ext];
+            inv[e * R + fill_[e]++] = (unsigned short)ext;
+          }
+          mp.insert(mp.end(), inv.begin(), inv.end());
         }
         for (int j = 0; j < npair; ++j) {
           F.push_back(prog[q + 2 * j]);

@@ -135,9 +135,11 @@ struct GenDev {
   //   n_steps, final table (live offset), final table (full offset);
   // per step (global step index g, record at fstep[g]):
   //   m, fld_begin, fld_count, n_in, n_pair, pp_off, map_off, out_live, out_full,
-  //   n_in x (in_live, in_full), n_pair x (pair_id, pos_u).
+  //   n_in x (in_live, in_full, k_in), n_pair x (pair_id, pos_u).
   // map[map_off + i * 2^(m+1) + ext]: entry of input i at extended index ext
-  // (bit j of ext: out-scope spin j, bit m: the eliminated spin).
+  // (bit j of ext: out-scope spin j, bit m: the eliminated spin); then
+  // map[map_off + (n_in + i) * 2^(m+1) + e * 2^(m+1-k_in) + f]: the f-th
+  // extended index that reads entry e of input i (the inverse map).
   // pp[pp_off + ext]: product of the step's bond factors at ext (this
   // call's beta, general_pp_kernel); pp[n_pp + pp_off + ext] its d ln / d beta.
   const int* fprog;
@@ -331,12 +333,12 @@ cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem
                            const int8_t* spins, double* logZR, double* dbeta, float* garena,
                            cudaStream_t s);
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int steps,
-                              int GL, const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
-                              cudaStream_t s);
+                              int gmax, int GL, const int8_t* spins, float* part, int part_stride, double* dJ,
+                              float* garena, cudaStream_t s);
 // bond products of every elimination step at li.beta (before the kernels above)
 cudaError_t launch_general_pp(const InstDev* d_inst, const LaunchInfo& li, int max_steps, cudaStream_t s);
-int general_dJ_smem_bytes(int arena, int steps, int D, int n_edges, int T, bool glob);
-size_t general_dJ_scratch_floats(int arena, int steps, int T, int nblk);
+int general_dJ_smem_bytes(int per_sample, int D, int n_edges, int T, int threads, bool glob);
+size_t general_dJ_scratch_floats(int per_sample, int T, int nblk);
 size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);

@@ -36,7 +36,7 @@ __device__ __forceinline__ int padded_bytes(int D) {
 // One compiled elimination step (layout in GenDev).
 struct StepRec {
   int m, fb, fc, nin, npair, ppo, mo, out_live, out_full;
-  const int* io;  // n_in x (live offset, full offset)
+  const int* io;  // n_in x (live offset, full offset, spins of the input)
   const int* pr;  // n_pair x (pair id, position of the neighbour in the out scope)
 };
 
@@ -53,7 +53,7 @@ __device__ __forceinline__ StepRec step_at(const GenDev& G, int g) {
   r.out_live = F[7];
   r.out_full = F[8];
   r.io = F + 9;
-  r.pr = F + 9 + 2 * r.nin;
+  r.pr = F + 9 + 3 * r.nin;
   return r;
 }
 
@@ -136,7 +136,7 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
         float p = fv[sg] * pp[ext];
         float rr = DB ? fr[sg] + pd[ext] : 0.f;
         for (int i = 0; i < r.nin; ++i) {
-          const int a = r.io[2 * i] + mp[i * E + ext];
+          const int a = r.io[3 * i] + mp[i * E + ext];
           const float val = A[a];
           p *= val;
           if (DB) rr += dA[a] / val;
@@ -305,20 +305,22 @@ __global__ void __launch_bounds__(128) general_tab_kernel(const InstDev* __restr
 // entry, starting from 1 / A_final.  For step t with product terms
 // term(x, sigma) (field factor, bond factors, input tables):
 //   g(x, sigma)       = Abar_t[x] 2^-e_t term(x, sigma)
-//   Abar_in[idx]     += g / A_in[idx]   (atomic: lanes of a group share inputs)
+//   Abar_in[idx]     += g / A_in[idx]
 //   d lnZ / d J_bond += beta sum g sigma sigma_u,  d lnZ / d J_field += beta s_w sum g sigma.
-// Bond sums are warp-reduced (over samples and lanes) into per-CTA shared
-// accumulators, written as one row per CTA and added per instance in a fixed
-// order.
+// The input adjoints are gathered per input entry (inverse maps) from the
+// step's stored g values, in a fixed order.  Bond sums are warp-reduced (over
+// samples and lanes) into per-warp shared rows, added in warp order into one
+// row per CTA, and the rows added per instance in a fixed order: the result
+// does not depend on scheduling.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void acc_edge(float* acc, int e, float v, bool lane0) {
+__device__ __forceinline__ void acc_edge(float* acc_w, int e, float v, bool lane0) {
   v = warp_sum(v);
-  if (lane0 && e >= 0) atomicAdd(acc + e, v);
+  if (lane0 && e >= 0) acc_w[e] += v;
 }
 
 __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restrict__ inst,
                                                          const LaunchInfo li, int arena_floats, int max_steps,
-                                                         int GL, const int8_t* __restrict__ spins,
+                                                         int gmax, int GL, const int8_t* __restrict__ spins,
                                                          float* __restrict__ part, int part_stride,
                                                          float* __restrict__ garena) {
   extern __shared__ float sm[];
@@ -331,16 +333,19 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
   const int D = I.D, Dp = padded_bytes(D);
   // per sample: tables, adjoints, scales (sample-major), in shared memory or
   // for large arenas in this CTA's slice of a global scratch buffer
-  const size_t per = (size_t)(2 * arena_floats + max_steps);
+  const size_t per = (size_t)(2 * arena_floats + max_steps + gmax);
   const size_t cta_floats = per * S;
   float* base = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
   float* A = base + (size_t)slot * per;   // [arena]
   float* Ab = A + arena_floats;           // [arena] adjoints
   float* sc = Ab + arena_floats;          // [max_steps] scales 2^-e
-  float* acc = garena ? sm : sm + cta_floats;  // [n_edges]
-  int8_t* ssp = reinterpret_cast<int8_t*>(acc + ((I.n_edges + 3) & ~3));
+  float* gb = sc + max_steps;             // [gmax] g of the current step
+  const int ne4 = (I.n_edges + 3) & ~3, nw = blockDim.x >> 5;
+  float* acc = garena ? sm : sm + cta_floats;  // [warps][n_edges]
+  float* acc_w = acc + (threadIdx.x >> 5) * ne4;
+  int8_t* ssp = reinterpret_cast<int8_t*>(acc + nw * ne4);
   const GenDev& G = I.gen;
-  for (int e = threadIdx.x; e < I.n_edges; e += blockDim.x) acc[e] = 0.f;
+  for (int e = threadIdx.x; e < nw * ne4; e += blockDim.x) acc[e] = 0.f;
   const int n_valid = min(S, li.batch - b0);
   stage_spins(ssp, spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, S, D, Dp);
   __syncthreads();
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
         for (int sg = 0; sg < 2; ++sg) {
           const int ext = x | (sg << r.m);
           float pr = fv[sg] * pp[ext];
-          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[2 * i + 1] + mp[i * E + ext]];
+          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[3 * i + 1] + mp[i * E + ext]];
           accv += pr;
         }
         A[out + x] = accv;
@@ -407,31 +412,44 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
         for (int sg = 0; sg < 2; ++sg) {
           const int ext = x | (sg << r.m);
           float pr = fv[sg] * pp[ext];
-          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[2 * i + 1] + mp[i * E + ext]];
+          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[3 * i + 1] + mp[i * E + ext]];
           const float g = abx * pr;
+          gb[ext] = g;
           gs = fmaf(g, sg ? -1.f : 1.f, gs);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             if (j < np) gp[j] = fmaf(g, (((x >> pos[j]) & 1) == sg) ? 1.f : -1.f, gp[j]);
-          for (int i = 0; i < r.nin; ++i) {
-            const int a = r.io[2 * i + 1] + mp[i * E + ext];
-            const float av = A[a];
-            if (av > 0.f) {
-              if (GL == 1) Ab[a] += g / av;
-              else atomicAdd(Ab + a, g / av);
-            }
+        }
+      }
+      __syncwarp();
+      // input adjoints: each entry gathers the g of the extended indices that
+      // read it (inverse map), lanes split the entries
+      for (int i = 0; i < r.nin; ++i) {
+        const int in = r.io[3 * i + 1], kk = r.io[3 * i + 2];
+        const int R = E >> kk;
+        const unsigned short* inv = mp + (r.nin + i) * E;
+        for (int e = lane; e < (1 << kk); e += GL) {
+          const float av = A[in + e];
+          if (av > 0.f) {
+            float sum = 0.f;
+            for (int f = 0; f < R; ++f) sum += gb[inv[e * R + f]];
+            Ab[in + e] += sum / av;
           }
         }
       }
       for (int f = r.fb; f < r.fb + r.fc; ++f)
-        acc_edge(acc, G.fld[2 * f + 1], wscale * gs * (float)s[G.fld[2 * f]], lane0);
-      for (int j = 0; j < np; ++j) acc_edge(acc, G.pairE[r.pr[2 * j]], wscale * gp[j], lane0);
+        acc_edge(acc_w, G.fld[2 * f + 1], wscale * gs * (float)s[G.fld[2 * f]], lane0);
+      for (int j = 0; j < np; ++j) acc_edge(acc_w, G.pairE[r.pr[2 * j]], wscale * gp[j], lane0);
       __syncwarp();
     }
   }
   __syncthreads();
   float* row = part + (long long)blockIdx.x * part_stride;
-  for (int e = threadIdx.x; e < I.n_edges; e += blockDim.x) row[e] = acc[e];
+  for (int e = threadIdx.x; e < I.n_edges; e += blockDim.x) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += acc[w * ne4 + e];
+    row[e] = v;
+  }
 }
 
 __global__ void general_dJ_reduce_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
@@ -453,25 +471,24 @@ cudaError_t launch_general_pp(const InstDev* d_inst, const LaunchInfo& li, int m
   return cudaGetLastError();
 }
 
-int general_dJ_smem_bytes(int arena, int steps, int D, int n_edges, int T, bool glob) {
+// per-sample floats: 2 * arena + steps + gmax (tables, adjoints, scales, g)
+int general_dJ_smem_bytes(int per_sample, int D, int n_edges, int T, int threads, bool glob) {
   int w4 = (D + 3) / 4;
   if ((w4 & 1) == 0) ++w4;
-  return (glob ? 0 : (2 * arena + steps) * T * 4) + ((n_edges + 3) & ~3) * 4 + T * 4 * w4;
+  return (glob ? 0 : per_sample * T * 4) + (threads / 32) * ((n_edges + 3) & ~3) * 4 + T * 4 * w4;
 }
 
-size_t general_dJ_scratch_floats(int arena, int steps, int T, int nblk) {
-  return (size_t)(2 * arena + steps) * T * nblk;
-}
+size_t general_dJ_scratch_floats(int per_sample, int T, int nblk) { return (size_t)per_sample * T * nblk; }
 
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int steps,
-                              int GL, const int8_t* spins, float* part, int part_stride, double* dJ, float* garena,
-                              cudaStream_t s) {
+                              int gmax, int GL, const int8_t* spins, float* part, int part_stride, double* dJ,
+                              float* garena, cudaStream_t s) {
   const int nblk = li.tile_begin[li.n_inst];
   if (nblk == 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(general_dJ_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
-  general_dJ_kernel<<<nblk, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, steps, GL, spins, part, part_stride,
-                                                           garena);
+  general_dJ_kernel<<<nblk, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, steps, gmax, GL, spins, part,
+                                                           part_stride, garena);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   general_dJ_reduce_kernel<<<dim3(4, li.n_inst), 256, 0, s>>>(d_inst, li, part, part_stride, dJ);
