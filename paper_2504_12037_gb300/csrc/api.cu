@@ -2341,11 +2341,11 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
         Dm = std::max(Dm, (int)in.W.size());
         nsteps = std::max(nsteps, (int)in.gfstep.size());
       }
-    arena |= 1;  // odd per-sample stride: samples of a warp fall in different banks
     const bool db = d_dbeta != nullptr;
     const int GL = gen_lanes(ctx), T = 128 / GL;
-    const bool glob = gen_tables_global(T, [&](int t, bool g) { return general_smem_bytes(arena, Dm, t, db, g); });
-    const int sm = general_smem_bytes(arena, Dm, T, db, glob);
+    const bool glob =
+        gen_tables_global(T, [&](int t, bool g) { return general_smem_bytes(arena, Dm, t, GL, db, g); });
+    const int sm = general_smem_bytes(arena, Dm, T, GL, db, glob);
     if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
     LaunchInfo lg;
     if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
@@ -2360,7 +2360,7 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
         lg.gen_tab = std::max(lg.gen_tab, in.g_ntab);
     float* gs = nullptr;
     if (glob) {
-      if ((rc = ensure_gen_scratch(ctx, 0, general_scratch_floats(lg, arena, db)))) return rc;
+      if ((rc = ensure_gen_scratch(ctx, 0, general_scratch_floats(lg, arena, GL, db)))) return rc;
       gs = ctx->d_gen_scratch[0];
     }
     if (lg.gen_tab > 0) {
@@ -2441,12 +2441,11 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         }
       if (any_gen) {
         const int gmax = 2 << mw;  // g of one step: 2^(m+1) extended indices
-        if (((2 * arena + steps + gmax) & 1) == 0) ++steps;  // odd per-sample stride (banks)
         const int per = 2 * arena + steps + gmax;
         const int GL = gen_lanes(ctx), T = 128 / GL;
         const bool glob =
-            gen_tables_global(T, [&](int t, bool g) { return general_dJ_smem_bytes(per, Dm, me, t, 128, g); });
-        const int sm = general_dJ_smem_bytes(per, Dm, me, T, 128, glob);
+            gen_tables_global(T, [&](int t, bool g) { return general_dJ_smem_bytes(per, Dm, me, t, GL, g); });
+        const int sm = general_dJ_smem_bytes(per, Dm, me, T, GL, glob);
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
         if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
@@ -2454,7 +2453,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
         float* gs = nullptr;
         if (glob) {
-          if ((rc = ensure_gen_scratch(ctx, 1, general_dJ_scratch_floats(per, T, lg.tile_begin[lg.n_inst]))))
+          if ((rc = ensure_gen_scratch(ctx, 1, general_dJ_scratch_floats(per, T, GL, lg.tile_begin[lg.n_inst]))))
             return rc;
           gs = ctx->d_gen_scratch[1];
         }

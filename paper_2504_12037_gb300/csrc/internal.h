@@ -337,9 +337,9 @@ cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int s
                               float* garena, cudaStream_t s);
 // bond products of every elimination step at li.beta (before the kernels above)
 cudaError_t launch_general_pp(const InstDev* d_inst, const LaunchInfo& li, int max_steps, cudaStream_t s);
-int general_dJ_smem_bytes(int per_sample, int D, int n_edges, int T, int threads, bool glob);
-size_t general_dJ_scratch_floats(int per_sample, int T, int nblk);
-size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db);
+int general_dJ_smem_bytes(int per_sample, int D, int n_edges, int T, int GL, bool glob);
+size_t general_dJ_scratch_floats(int per_sample, int T, int GL, int nblk);
+size_t general_scratch_floats(const LaunchInfo& li, int arena, int GL, bool db);
 cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t* spins,
                       double* dJ, cudaStream_t s);
 // The strip adjoint's tables (Boltzmann factors of every strip row at the
@@ -391,7 +391,7 @@ extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 
 int sample_smem_bytes(const Instance& in, int tile);
-int general_smem_bytes(int arena, int D, int T, bool db, bool glob);
+int general_smem_bytes(int arena, int D, int T, int GL, bool db, bool glob);
 cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, bool db, int GL,
                                   float* garena, cudaStream_t s);
 int strip_smem_bytes(const Instance& in, int tile);

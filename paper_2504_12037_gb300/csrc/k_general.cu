@@ -12,8 +12,9 @@
 // that index and beta and is tabulated once per call (general_pp_kernel), so
 // a table entry costs one field factor, one bond product and one load per
 // input.  A group of lanes shares one sample and splits each table's entries;
-// tables live in a per-sample arena (sample-major) in shared memory, or for
-// large arenas in a per-CTA slice of global scratch.  Forward
+// tables are laid out [entry][sample] per CTA (consecutive samples in
+// consecutive words), in shared memory, or for large arenas in a per-CTA
+// slice of global scratch.  Forward
 // passes use reused offsets (a table's space is free once the step that
 // consumes it has run); the reverse sweep keeps every table.  Every new table
 // is renormalised by a power of two.  Factors are stored normalised (largest
@@ -99,18 +100,23 @@ __global__ void __launch_bounds__(256) general_pp_kernel(const InstDev* __restri
 // group computes the table entries x = l, l + GL, ...  Every lane of a block
 // runs the same program (invalid samples run on a dummy row), so the
 // group-wide maximum and __syncwarp between steps see full warps.
+// Row stride of the [entry][sample] tables: S samples plus 32 / GL floats,
+// so that the GL consecutive entries written by a group and the 32 / GL
+// samples of a warp fall in 32 different shared-memory banks.
+__host__ __device__ __forceinline__ int gen_row_stride(int S, int GL) { return S + 32 / GL; }
+
 __device__ __forceinline__ float group_max(float v, int GL) {
   for (int o = GL >> 1; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
-// Component c for the sample whose tables start at A (sample-major: entry e
-// at A[e]; with DB the beta-derivatives at dA[e]); forward, live offsets.
+// Component c for the sample whose tables start at A (entry e at A[e * RS];
+// with DB the beta-derivatives at dA[e * RS]); forward, live offsets.
 // Adds log Z_c (and with DB its beta-derivative) to lz / dl (the same value
 // on every lane of the group).
 template <bool DB>
-__device__ __forceinline__ void run_component(const GenDev& G, int c, const int8_t* s, float* A, float* dA, int lane,
-                                              int GL, float beta, double& lz, double& dl) {
+__device__ __forceinline__ void run_component(const GenDev& G, int c, const int8_t* s, float* A, float* dA, int RS,
+                                              int lane, int GL, float beta, double& lz, double& dl) {
   const int* H = G.fprog + G.fhdr[c];
   const int nsteps = H[0], fin = H[1];
   const int g0 = G.comp_step0[c];
@@ -136,7 +142,7 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
         float p = fv[sg] * pp[ext];
         float rr = DB ? fr[sg] + pd[ext] : 0.f;
         for (int i = 0; i < r.nin; ++i) {
-          const int a = r.io[3 * i] + mp[i * E + ext];
+          const int a = (r.io[3 * i] + mp[i * E + ext]) * RS;
           const float val = A[a];
           p *= val;
           if (DB) rr += dA[a] / val;
@@ -144,23 +150,23 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
         acc += p;
         if (DB) dacc = fmaf(p, rr, dacc);
       }
-      A[out + x] = acc;
-      if (DB) dA[out + x] = dacc;
+      A[(out + x) * RS] = acc;
+      if (DB) dA[(out + x) * RS] = dacc;
       mx = fmaxf(mx, acc);
     }
     mx = group_max(mx, GL);
     const int e = exponent_of(mx);
     const float sc = pow2i(-e);
     for (int x = lane; x < M; x += GL) {
-      A[out + x] *= sc;
-      if (DB) dA[out + x] *= sc;
+      A[(out + x) * RS] *= sc;
+      if (DB) dA[(out + x) * RS] *= sc;
     }
     lz += (double)e * 0.69314718055994530942;
     __syncwarp();
   }
-  const float z = A[fin];
+  const float z = A[fin * RS];
   lz += (double)logf(z);
-  if (DB) dl += (double)(dA[fin] / z);
+  if (DB) dl += (double)(dA[fin * RS] / z);
 }
 
 // Boundary index of component c for spin row s: bit j set iff its j-th
@@ -193,12 +199,14 @@ __global__ void __launch_bounds__(128) general_kernel(const InstDev* __restrict_
   const int b0 = (blockIdx.x - li.tile_begin[k]) * S, b = b0 + slot;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  // tables [sample][arena] (then their beta-derivatives) in shared memory, or
-  // for large arenas in this CTA's slice of a global scratch buffer
-  const size_t cta_floats = (size_t)arena_floats * S * (DB ? 2 : 1);
+  // tables [entry][sample] (rows of RS floats; then their beta-derivatives)
+  // in shared memory, or for large arenas in this CTA's slice of a global
+  // scratch buffer
+  const int RS = gen_row_stride(S, GL);
+  const size_t cta_floats = (size_t)arena_floats * RS * (DB ? 2 : 1);
   float* base = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
-  float* A = base + (size_t)slot * arena_floats;
-  float* dA = A + (size_t)S * arena_floats;
+  float* A = base + slot;
+  float* dA = A + (size_t)arena_floats * RS;
   int8_t* ssp = reinterpret_cast<int8_t*>(garena ? sm : sm + cta_floats);
   const GenDev& G = I.gen;
   const int n_valid = min(S, li.batch - b0);
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(128) general_kernel(const InstDev* __restrict_
       lz += G.tab_lz[cr[4] + x];
       if (DB) dl += G.tab_db[cr[4] + x];
     } else {
-      run_component<DB>(G, c, s, A, dA, lane, GL, beta, lz, dl);
+      run_component<DB>(G, c, s, A, dA, RS, lane, GL, beta, lz, dl);
     }
   }
   if (lane != 0 || b >= li.batch) return;
@@ -250,10 +258,11 @@ __global__ void __launch_bounds__(128) general_tab_kernel(const InstDev* __restr
   if (blockIdx.x * S >= G.n_tab) return;  // whole CTA idle (uniform)
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  const size_t cta_floats = (size_t)arena_floats * S * (DB ? 2 : 1);
+  const int RS = gen_row_stride(S, GL);
+  const size_t cta_floats = (size_t)arena_floats * RS * (DB ? 2 : 1);
   float* base = garena ? garena + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * cta_floats : sm;
-  float* A = base + (size_t)slot * arena_floats;
-  float* dA = A + (size_t)S * arena_floats;
+  float* A = base + slot;
+  float* dA = A + (size_t)arena_floats * RS;
   int8_t* ssp = reinterpret_cast<int8_t*>(garena ? sm : sm + cta_floats);
   int8_t* s = ssp + slot * Dp;
   for (int j = lane; j < D; j += GL) s[j] = 1;
@@ -287,7 +296,7 @@ __global__ void __launch_bounds__(128) general_tab_kernel(const InstDev* __restr
       for (int j = 0; j < cr[2]; ++j) s[G.bpos[cr[3] + j]] = ((x >> j) & 1) ? -1 : 1;
     __syncwarp();
     double lz = 0.0, dl = 0.0;
-    run_component<DB>(G, want, s, A, dA, lane, GL, beta, lz, dl);
+    run_component<DB>(G, want, s, A, dA, RS, lane, GL, beta, lz, dl);
     if (mine && live && lane == 0) {
       G.tab_lz[g] = lz;
       if (DB) G.tab_db[g] = dl;
@@ -331,15 +340,16 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
   const int b0 = (blockIdx.x - li.tile_begin[k]) * S, b = b0 + slot;
   const float beta = (float)li.beta[k];
   const int D = I.D, Dp = padded_bytes(D);
-  // per sample: tables, adjoints, scales (sample-major), in shared memory or
-  // for large arenas in this CTA's slice of a global scratch buffer
-  const size_t per = (size_t)(2 * arena_floats + max_steps + gmax);
-  const size_t cta_floats = per * S;
+  // tables, adjoints, scales and the step's g values, each [entry][sample]
+  // (rows of RS floats), in shared memory or for large arenas in this CTA's
+  // slice of a global scratch buffer
+  const int RS = gen_row_stride(S, GL);
+  const size_t cta_floats = (size_t)(2 * arena_floats + max_steps + gmax) * RS;
   float* base = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
-  float* A = base + (size_t)slot * per;   // [arena]
-  float* Ab = A + arena_floats;           // [arena] adjoints
-  float* sc = Ab + arena_floats;          // [max_steps] scales 2^-e
-  float* gb = sc + max_steps;             // [gmax] g of the current step
+  float* A = base + slot;                          // [arena]
+  float* Ab = A + (size_t)arena_floats * RS;       // [arena] adjoints
+  float* sc = Ab + (size_t)arena_floats * RS;      // [max_steps] scales 2^-e
+  float* gb = sc + (size_t)max_steps * RS;         // [gmax] g of the current step
   const int ne4 = (I.n_edges + 3) & ~3, nw = blockDim.x >> 5;
   float* acc = garena ? sm : sm + cta_floats;  // [warps][n_edges]
   float* acc_w = acc + (threadIdx.x >> 5) * ne4;
@@ -373,20 +383,20 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
         for (int sg = 0; sg < 2; ++sg) {
           const int ext = x | (sg << r.m);
           float pr = fv[sg] * pp[ext];
-          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[3 * i + 1] + mp[i * E + ext]];
+          for (int i = 0; i < r.nin; ++i) pr *= A[(r.io[3 * i + 1] + mp[i * E + ext]) * RS];
           accv += pr;
         }
-        A[out + x] = accv;
-        Ab[out + x] = 0.f;
+        A[(out + x) * RS] = accv;
+        Ab[(out + x) * RS] = 0.f;
         mx = fmaxf(mx, accv);
       }
       mx = group_max(mx, GL);
       const float scl = pow2i(-exponent_of(mx));
-      for (int x = lane; x < M; x += GL) A[out + x] *= scl;
-      if (lane == 0) sc[st] = scl;
+      for (int x = lane; x < M; x += GL) A[(out + x) * RS] *= scl;
+      if (lane == 0) sc[st * RS] = scl;
       __syncwarp();
     }
-    if (lane == 0) Ab[fin] = 1.f / A[fin];
+    if (lane == 0) Ab[fin * RS] = 1.f / A[fin * RS];
     __syncwarp();
     // backward
     for (int st = nsteps - 1; st >= 0; --st) {
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
       const float* pp = G.pp + r.ppo;
       const unsigned short* mp = G.map + r.mo;
       const int out = r.out_full;
-      const float scl = sc[st];
+      const float scl = sc[st * RS];
       const int np = min(r.npair, 8);  // at most 8 neighbours remain
       int pos[8];
 #pragma unroll
@@ -408,13 +418,13 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
 #pragma unroll
       for (int j = 0; j < 8; ++j) gp[j] = 0.f;
       for (int x = lane; x < M; x += GL) {
-        const float abx = Ab[out + x] * scl;
+        const float abx = Ab[(out + x) * RS] * scl;
         for (int sg = 0; sg < 2; ++sg) {
           const int ext = x | (sg << r.m);
           float pr = fv[sg] * pp[ext];
-          for (int i = 0; i < r.nin; ++i) pr *= A[r.io[3 * i + 1] + mp[i * E + ext]];
+          for (int i = 0; i < r.nin; ++i) pr *= A[(r.io[3 * i + 1] + mp[i * E + ext]) * RS];
           const float g = abx * pr;
-          gb[ext] = g;
+          gb[ext * RS] = g;
           gs = fmaf(g, sg ? -1.f : 1.f, gs);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
@@ -429,11 +439,11 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
         const int R = E >> kk;
         const unsigned short* inv = mp + (r.nin + i) * E;
         for (int e = lane; e < (1 << kk); e += GL) {
-          const float av = A[in + e];
+          const float av = A[(in + e) * RS];
           if (av > 0.f) {
             float sum = 0.f;
-            for (int f = 0; f < R; ++f) sum += gb[inv[e * R + f]];
-            Ab[in + e] += sum / av;
+            for (int f = 0; f < R; ++f) sum += gb[inv[e * R + f] * RS];
+            Ab[(in + e) * RS] += sum / av;
           }
         }
       }
@@ -472,13 +482,16 @@ cudaError_t launch_general_pp(const InstDev* d_inst, const LaunchInfo& li, int m
 }
 
 // per-sample floats: 2 * arena + steps + gmax (tables, adjoints, scales, g)
-int general_dJ_smem_bytes(int per_sample, int D, int n_edges, int T, int threads, bool glob) {
+int general_dJ_smem_bytes(int per_sample, int D, int n_edges, int T, int GL, bool glob) {
   int w4 = (D + 3) / 4;
   if ((w4 & 1) == 0) ++w4;
-  return (glob ? 0 : per_sample * T * 4) + (threads / 32) * ((n_edges + 3) & ~3) * 4 + T * 4 * w4;
+  return (glob ? 0 : per_sample * gen_row_stride(T, GL) * 4) + (T * GL / 32) * ((n_edges + 3) & ~3) * 4 +
+         T * 4 * w4;
 }
 
-size_t general_dJ_scratch_floats(int per_sample, int T, int nblk) { return (size_t)per_sample * T * nblk; }
+size_t general_dJ_scratch_floats(int per_sample, int T, int GL, int nblk) {
+  return (size_t)per_sample * gen_row_stride(T, GL) * nblk;
+}
 
 cudaError_t launch_general_dJ(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int steps,
                               int gmax, int GL, const int8_t* spins, float* part, int part_stride, double* dJ,
@@ -515,16 +528,16 @@ cudaError_t launch_general_tables(const InstDev* d_inst, const LaunchInfo& li, i
   return cudaGetLastError();
 }
 
-int general_smem_bytes(int arena, int D, int T, bool db, bool glob) {
+int general_smem_bytes(int arena, int D, int T, int GL, bool db, bool glob) {
   int w4 = (D + 3) / 4;
   if ((w4 & 1) == 0) ++w4;
-  return (glob ? 0 : arena * T * 4 * (db ? 2 : 1)) + T * 4 * w4;
+  return (glob ? 0 : arena * gen_row_stride(T, GL) * 4 * (db ? 2 : 1)) + T * 4 * w4;
 }
 
-// Scratch of the global-table mode: one [sample][arena] slice (two with
+// Scratch of the global-table mode: one [arena][row stride] slice (two with
 // d/dbeta) per CTA of the contraction and of the tables kernel.
-size_t general_scratch_floats(const LaunchInfo& li, int arena, bool db) {
-  const size_t per = (size_t)arena * li.tile * (db ? 2 : 1);
+size_t general_scratch_floats(const LaunchInfo& li, int arena, int GL, bool db) {
+  const size_t per = (size_t)arena * gen_row_stride(li.tile, GL) * (db ? 2 : 1);
   size_t ctas = (size_t)li.tile_begin[li.n_inst];
   if (li.gen_tab > 0) ctas = std::max(ctas, (size_t)((li.gen_tab + li.tile - 1) / li.tile) * li.n_inst);
   return per * ctas;
