@@ -112,20 +112,26 @@ __device__ __forceinline__ float group_max(float v, int GL) {
 
 // Component c for the sample whose tables start at A (entry e at A[e * RS];
 // with DB the beta-derivatives at dA[e * RS]); forward, live offsets.
-// Adds log Z_c (and with DB its beta-derivative) to lz / dl (the same value
-// on every lane of the group).
+// Adds log Z_c (and with DB its beta-derivative) to lz / dl on lane 0 of the
+// group.
 template <bool DB>
 __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8_t* s, float* A, float* dA, int RS,
                                               int lane, int GL, float beta, double& lz, double& dl) {
   const int* H = G.fprog + G.fhdr[c];
   const int nsteps = H[0], fin = H[1];
   const int g0 = G.comp_step0[c];
+  // the group's lanes compute identical log-scale terms: lane 0 alone keeps
+  // the FP64 sums; the power-of-two scales add up exactly as an integer
+  const bool keep = lane == 0;
+  int esum = 0;
   for (int st = 0; st < nsteps; ++st) {
     const StepRec r = step_at(G, g0 + st);
     const float h = field_of(G, r.fb, r.fc, s);
     const float ah = fabsf(h);
-    lz += (double)beta * (double)ah;
-    if (DB) dl += (double)ah;
+    if (keep) {
+      lz += (double)beta * (double)ah;
+      if (DB) dl += (double)ah;
+    }
     const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
     const float fr[2] = {h - ah, -h - ah};
     const int M = 1 << r.m, E = 2 * M;
@@ -161,12 +167,14 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
       A[(out + x) * RS] *= sc;
       if (DB) dA[(out + x) * RS] *= sc;
     }
-    lz += (double)e * 0.69314718055994530942;
+    esum += e;
     __syncwarp();
   }
-  const float z = A[fin * RS];
-  lz += (double)logf(z);
-  if (DB) dl += (double)(dA[fin * RS] / z);
+  if (keep) {
+    const float z = A[fin * RS];
+    lz += (double)esum * 0.69314718055994530942 + (double)logf(z);
+    if (DB) dl += (double)(dA[fin * RS] / z);
+  }
 }
 
 // Boundary index of component c for spin row s: bit j set iff its j-th
