@@ -102,3 +102,32 @@ def test_ordered_width_set_arguments():
         ctx.set_width_set(1, Wl, Rl)
     assert e.value.code == tv.E_ARG
     ctx.close()
+
+
+def test_planned_rrg_full_size_sampled_rows():
+    """The bench's planned workload at full size (n = 1000, d = 3, w_u = 8,
+    batch 10,000, global tables, lane groups): log Z_R and d/dbeta on sampled
+    rows against the oracle, and sum_e J_e dlogZ/dJ_e = beta dlogZ/dbeta over
+    the whole batch (log Z_R depends on beta and J only through beta J)."""
+    g = wl.random_regular(1000, 3, 12037 + 7000)
+    W, order, _, _ = tv.find_width_set(g.n, g.ei, g.ej, 8, restarts=4, seed=1)
+    beta = 0.5
+    model = TNVAN([g], [W], [128, 128], [beta], seed=5, elim_orders=[order])
+    B = 10000
+    spins, logq, logZR = model.sample(B, seed=3, step=1, precision=tv.BF16)
+    dbeta = torch.empty(B, dtype=torch.float64, device="cuda")
+    model.ctx.contract(model.betas, B, spins, tv.FP32, logZR, dbeta)
+    dJ = torch.empty(g.m, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(model.params)
+    model.ctx.backward(model.betas, B, spins, logZR, logq, tv.FP32, grad, None, dJ)
+    torch.cuda.synchronize()
+    rows = [0, 1, 4321, 9998, B - 1]
+    s = model.spins_of(spins, 0, B)[rows].cpu().to(torch.float64)
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    lz = general.log_zr_general(g.n, g.ei, g.ej, g.J, bt, W, s)
+    db_ref = torch.stack([torch.autograd.grad(lz[i], bt, retain_graph=True)[0] for i in range(len(rows))])
+    assert float((logZR[rows].cpu() - lz.detach()).abs().max()) / g.n <= 1e-6
+    assert float((dbeta[rows].cpu() - db_ref).abs().max()) <= 2e-5 * max(1.0, float(db_ref.abs().max()))
+    lhs = float((torch.as_tensor(g.J, dtype=torch.float64) * dJ.cpu()).sum())
+    rhs = beta * float(dbeta.mean())
+    assert abs(lhs - rhs) <= 1e-5 * max(1.0, abs(rhs))
