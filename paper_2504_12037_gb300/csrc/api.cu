@@ -1700,8 +1700,8 @@ int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8
   if (rc) return rc;
   if (d_corr)
     for (const Instance& in : ctx->inst)
-      if (in.kind != 0)
-        return fail(ctx, TNVAN_E_UNSUPPORTED, "bond correlations are computed for strip instances only");
+      if (in.kind == 1)
+        return fail(ctx, TNVAN_E_UNSUPPORTED, "bond correlations are computed for strip and elimination instances");
   const int n = (int)ctx->inst.size();
   const size_t nb = (size_t)n * batch;
   const size_t bytes = nb * sizeof(double) + nb * sizeof(float) + 3 * (size_t)n * sizeof(double) + 64;
@@ -2395,6 +2395,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if (any_strip && (rc = plan_strip_adjoint(ctx, batch, &adj_tile, &adj_smem, &adj_lv, &adj_ws))) return rc;
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  li.wmul = wmul;  // weighted bond sums (W-W bonds)
   if (d_dJ) {
     long long ne = 0;
     for (const Instance& in : ctx->inst) ne += in.m;
@@ -2453,6 +2454,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
         if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination adjoint needs %d B of shared memory", sm);
         LaunchInfo lg;
         if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
+        lg.wmul = wmul;
         const int stride = (me + 3) & ~3;
         if ((rc = ensure_dj_part(ctx, (size_t)lg.tile_begin[lg.n_inst] * stride))) return rc;
         float* gs = nullptr;

@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
   const bool valid = b < li.batch;
   const bool lane0 = (threadIdx.x & 31) == 0;
   const int8_t* s = ssp + slot * Dp;
-  const float wscale = valid ? beta / (float)li.batch : 0.f;
+  // per-sample weight of the bond sums (importance multipliers when given)
+  const float wscale =
+      valid ? beta / (float)li.batch * (li.wmul ? li.wmul[(long long)k * li.batch + b] : 1.f) : 0.f;
   for (int c = 0; c < G.n_comp; ++c) {
     const int* H = G.fprog + G.fhdr[c];
     const int nsteps = H[0], fin = H[2];

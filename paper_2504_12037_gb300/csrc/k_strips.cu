@@ -851,27 +851,36 @@ cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li,
 }
 
 // W-W bonds of dense and elimination instances: d(-beta E_1)/d J_e =
-// beta s_a s_b, batch mean.  One CTA per (instance, bond chunk); threads
-// stride over samples.
+// beta s_a s_b, batch mean (with li.wmul, each sample b weighted by
+// wmul[b]).  One CTA per (instance, bond chunk); threads stride over samples;
+// the sums are exact integers, or FP64 in a fixed order when weighted.
 __global__ void ww_dJ_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                              const int8_t* __restrict__ spins, double* __restrict__ dJ) {
   const int k = blockIdx.y;
   const InstDev& I = inst[k];
   if (I.kind == 0) return;  // strips_adj_kernel covers the W-W bonds of strip instances
   const int8_t* sp = spins + I.spin_units * li.batch;
-  __shared__ int red[32];
+  const float* wm = li.wmul ? li.wmul + (long long)k * li.batch : nullptr;
+  __shared__ double red[32];
   for (int e = blockIdx.x; e < I.n_ww; e += gridDim.x) {
     const EdgeWW q = I.ww[e];
-    int acc = 0;
-    for (int b = threadIdx.x; b < li.batch; b += blockDim.x)
-      acc += sp[(long long)b * I.D + q.a] * sp[(long long)b * I.D + q.b];
+    double acc = 0.0;
+    if (wm) {
+      for (int b = threadIdx.x; b < li.batch; b += blockDim.x)
+        acc += (double)wm[b] * (double)(sp[(long long)b * I.D + q.a] * sp[(long long)b * I.D + q.b]);
+    } else {
+      int ia = 0;
+      for (int b = threadIdx.x; b < li.batch; b += blockDim.x)
+        ia += sp[(long long)b * I.D + q.a] * sp[(long long)b * I.D + q.b];
+      acc = (double)ia;
+    }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-      int v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0;
+      double v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
       v = warp_sum(v);
-      if (threadIdx.x == 0) dJ[I.edge_off + q.e] += li.beta[k] * (double)v / (double)li.batch;
+      if (threadIdx.x == 0) dJ[I.edge_off + q.e] += li.beta[k] * v / (double)li.batch;
     }
     __syncthreads();
   }

@@ -1,13 +1,13 @@
 """GPU parity of tnvan_observables (importance-weighted internal energy and
-bond correlations from one batch) against the FP64 oracle, through the
-C-ABI.  Samples and log q are seeded inputs; the oracle contracts every
+bond correlations from one batch; strip and elimination instances) against
+the FP64 oracle, through the C-ABI.  Samples and log q are seeded inputs; the oracle contracts every
 sample exactly and differentiates it with autograd."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import estimators as est
-from oracle import transfer
+from oracle import general, transfer
 from paper_2504_12037_gb300 import tnvan as tv
 from paper_2504_12037_gb300 import workloads as wl
 
@@ -95,3 +95,39 @@ def test_observables_reject_correlations_for_dense_instances():
         model.ctx.observables(model.betas, B, spins, logZR, logq, corr)
     out = model.ctx.observables(model.betas, B, spins, logZR, logq)  # energies are supported
     assert np.all(np.isfinite(out))
+
+
+@pytest.mark.parametrize("wu", [2, 6])
+def test_observables_elimination_instance_match_oracle(wu):
+    # a random regular graph with a finder-planned width set: the weighted
+    # bond sums of the elimination reverse sweep and of the W-W bonds
+    g = wl.random_regular(120, 3, 12037 + 8100 + wu)
+    W, order, _, _ = tv.find_width_set(g.n, g.ei, g.ej, wu, restarts=2, seed=3)
+    beta, batch = 0.8, 52
+    from paper_2504_12037_gb300.model import TNVAN
+
+    model = TNVAN([g], [W], [16], [beta], seed=5, elim_orders=[order])
+    D = len(W)
+    rng = np.random.default_rng(29)
+    s = np.where(rng.random((batch, D)) < 0.5, 1.0, -1.0)
+    lq = rng.normal(-D * np.log(2.0), 3.0, size=batch).astype(np.float32)
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    Jt = torch.tensor(g.J, dtype=torch.float64, requires_grad=True)
+    lz = general.log_zr_general(g.n, g.ei, g.ej, Jt, bt, W, torch.as_tensor(s))
+    l = lz.detach() - torch.as_tensor(lq, dtype=torch.float64)
+    wts = torch.softmax(l, 0)
+    db = torch.stack([torch.autograd.grad(lz[b], bt, retain_graph=True)[0] for b in range(batch)])
+    (corr_ref,) = torch.autograd.grad((wts * lz).sum(), Jt)
+    U_ref, Uq_ref, ess_ref = est.is_observables(lz.detach(), torch.as_tensor(lq, dtype=torch.float64), -db)
+    d_spins = to_dev_spins(s.reshape(-1))
+    logZR = torch.empty(batch, dtype=torch.float64, device="cuda")
+    model.ctx.contract(model.betas, batch, d_spins, tv.FP32, logZR)
+    logq = torch.as_tensor(lq).cuda()
+    corr = torch.full((g.m,), float("nan"), dtype=torch.float64, device="cuda")
+    out = model.ctx.observables(model.betas, batch, d_spins, logZR, logq, corr)
+    torch.cuda.synchronize()
+    U, Uq, ess = out[0]
+    assert abs(U - U_ref) <= 2e-5 * abs(U_ref)
+    assert abs(Uq - Uq_ref) <= 2e-5 * abs(Uq_ref)
+    assert abs(ess - ess_ref) <= 1e-4 * ess_ref
+    assert float((corr.cpu() - corr_ref).abs().max()) <= 2e-5 * max(1.0, float(corr_ref.abs().max()))
