@@ -344,14 +344,10 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     dd.C16 = c16;
     dd.c0 = c0;
   } else {
-    int *prog = nullptr, *fld = nullptr, *pe = nullptr, *so = nullptr, *cs = nullptr;
+    int *fld = nullptr, *pe = nullptr, *cs = nullptr;
     float *pj = nullptr, *fj = nullptr;
     if ((rc = upload(ctx, in, in.gpairE, &pe))) return rc;
-    if ((rc = upload(ctx, in, in.gstep_off, &so))) return rc;
     if ((rc = upload(ctx, in, in.gcomp_step0, &cs))) return rc;
-    if ((rc = upload(ctx, in, in.gprog, &prog))) return rc;
-    int* prog_fwd = nullptr;
-    if ((rc = upload(ctx, in, in.gprog_fwd, &prog_fwd))) return rc;
     if ((rc = upload(ctx, in, in.gfld, &fld))) return rc;
     if ((rc = upload(ctx, in, in.gpairJ, &pj))) return rc;
     if ((rc = upload(ctx, in, in.gfldJ, &fj))) return rc;
@@ -373,17 +369,9 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
     g.pp = ppd;
     g.n_pp = in.g_npp;
     g.n_steps = (int)in.gfstep.size();
-    g.max_entries = in.g_max_entries;
-    g.max_live = in.g_max_live;
-    g.prog = prog;
-    g.prog_fwd = prog_fwd;
-    g.prog_len = (int)in.gprog.size();
     g.pairJ = pj;
     g.pairE = pe;
-    g.step_off = so;
     g.comp_step0 = cs;
-    g.max_steps = in.g_max_steps;
-    g.n_pairs = in.g_npairs;
     g.fld = fld;
     g.fldJ = fj;
     g.c_hat = in.g_chat;

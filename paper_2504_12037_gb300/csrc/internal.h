@@ -127,11 +127,8 @@ struct DenseDev {
 // General components: elimination programs (see k_general.cu).
 struct GenDev {
   int n_comp;
-  int max_entries;       // per-sample table arena size (floats), every table kept
-  int max_live;          // the same with a table's space reused once it is consumed
-  const int* prog;       // packed int program, every table at its own offset (reverse sweeps)
-  const int* prog_fwd;   // the same program with reused offsets (forward-only passes)
-  // Compiled form run by the kernels.  Per component c, at fhdr[c]:
+  // Compiled elimination program (built by the host planner from its packed
+  // per-component programs).  Per component c, at fhdr[c]:
   //   n_steps, final table (live offset), final table (full offset);
   // per step (global step index g, record at fstep[g]):
   //   m, fld_begin, fld_count, n_in, n_pair, pp_off, map_off, out_live, out_full,
@@ -149,13 +146,9 @@ struct GenDev {
   float* pp;
   int n_pp;
   int n_steps;           // steps of all components
-  int prog_len;
   const float* pairJ;    // couplings of R-R bonds referenced by the program
   const int* pairE;      // edge id of each pair
-  const int* step_off;   // program offset of every step record, in program order
   const int* comp_step0; // [n_comp + 1] first step index of each component
-  int max_steps;         // most steps of one component
-  int n_pairs;
   const int* fld;        // per R spin: W-neighbour list (pos, edge id) packed
   const float* fldJ;
   double c_hat;          // constant log-offset / beta
