@@ -254,13 +254,11 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
  *   d_corr          device double [sum_k n_edges_k] out, or NULL: per edge
  *                   sum_b w_b d log Z_R(s_b) / d J_e = beta sum_b w_b <s_i s_j>_{r|s_b}
  *                   (instances back to back, input edge order); divide by
- *                   beta for the bond correlation.  Strip and elimination
- *                   (GENERAL) instances.
+ *                   beta for the bond correlation.  Every contraction kind.
  * h_out: host double [3 * n_instances].  FP32 contraction.  Uses the
  * reduction workspace of tnvan_free_energy (do not overlap the two) and
  * allocates a workspace of its own on growth.  Synchronises `stream`.
- * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_UNSUPPORTED (d_corr with a
- * dense instance), TNVAN_E_NOMEM, TNVAN_E_CUDA. */
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM, TNVAN_E_CUDA. */
 int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                       const double* d_logZR, const float* d_logq, double* d_corr, double* h_out,
                       void* stream);

@@ -1686,10 +1686,6 @@ int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8
   DeviceGuard g(ctx->device);
   int rc = check_ready(ctx, false);
   if (rc) return rc;
-  if (d_corr)
-    for (const Instance& in : ctx->inst)
-      if (in.kind == 1)
-        return fail(ctx, TNVAN_E_UNSUPPORTED, "bond correlations are computed for strip and elimination instances");
   const int n = (int)ctx->inst.size();
   const size_t nb = (size_t)n * batch;
   const size_t bytes = nb * sizeof(double) + nb * sizeof(float) + 3 * (size_t)n * sizeof(double) + 64;
@@ -2411,6 +2407,7 @@ int run_adjoint(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if (d_dJ) {
     LaunchInfo lt;
     if ((rc = fill_launch(ctx, betas, batch, 128, lt))) return rc;
+    lt.wmul = wmul;
     if (other) {
       {
         PROF("ww_dJ", s);

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) dense_kernel(const InstDev* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // Reverse mode: d ln Z_R / d J = beta <r_i r_j> (R-R) or beta s_w <r_i> (R-W),
-// batch mean accumulated into dJ.  Marginals of the factored form:
+// batch mean accumulated into dJ (each sample weighted by li.wmul when given).  Marginals of the factored form:
 //   P(a, b) = g_A(a) C(a,b) g_B(b) / z
 // needs Y_j = C (g_B * sigma_j) for the 8 B spins, Y_0 = C g_B and U = C^T g_A.
 // ---------------------------------------------------------------------------
@@ -267,7 +267,9 @@ __global__ void __launch_bounds__(256) dense_dJ_kernel(const InstDev* __restrict
     if (tt >= nv) break;  // uniform across the block
     const float ga = gA[tt * 256 + t];
     const float z = block_sum256(ga * y[tt][0], scratch, t);
-    const float iz = scale / z;
+    // per-sample weight of the bond sums (importance multipliers when given)
+    const float wv = li.wmul ? li.wmul[(long long)k * li.batch + b0 + tt] : 1.f;
+    const float iz = scale * wv / z;
     const int8_t* st = sp + tt * D;
     // single-spin marginals -> R-W bonds
     for (int r = 0; r < 16; ++r) {

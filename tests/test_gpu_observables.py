@@ -1,7 +1,8 @@
 """GPU parity of tnvan_observables (importance-weighted internal energy and
-bond correlations from one batch; strip and elimination instances) against
-the FP64 oracle, through the C-ABI.  Samples and log q are seeded inputs; the oracle contracts every
-sample exactly and differentiates it with autograd."""
+bond correlations from one batch; strip, dense and elimination instances)
+against the FP64 oracle, through the C-ABI.  Samples and log q are seeded
+inputs; the oracle contracts every sample exactly and differentiates it with
+autograd."""
 import numpy as np
 import pytest
 import torch
@@ -83,18 +84,40 @@ def test_observables_uniform_weights_reduce_to_batch_means():
     assert float((corr - dJ).abs().max()) <= 1e-3 * float(dJ.abs().max())
 
 
-def test_observables_reject_correlations_for_dense_instances():
-    w = wl.workload(3)
+def test_observables_dense_instance_match_oracle():
+    # SK block: the dense adjoint's weighted pair and single-spin marginals
+    # and the weighted W-W bond sums
+    from oracle import dense
     from paper_2504_12037_gb300.model import TNVAN
 
-    model = TNVAN(w.graphs[:1], w.widths_sets[:1], w.hidden, w.betas[:1], seed=2)
-    B = 64
-    spins, logq, logZR = model.sample(B, 1, 1, tv.FP32)
-    corr = torch.empty(model.n_edges[0], dtype=torch.float64, device="cuda")
-    with pytest.raises(tv.TnvanError):
-        model.ctx.observables(model.betas, B, spins, logZR, logq, corr)
-    out = model.ctx.observables(model.betas, B, spins, logZR, logq)  # energies are supported
-    assert np.all(np.isfinite(out))
+    g = wl.sk(18, 4)
+    W = np.arange(6, 18, dtype=np.int32)
+    beta, batch = 1.1, 37
+    model = TNVAN([g], [W], [16], [beta], seed=2)
+    D = len(W)
+    rng = np.random.default_rng(31)
+    s = np.where(rng.random((batch, D)) < 0.5, 1.0, -1.0)
+    lq = rng.normal(-D * np.log(2.0), 2.0, size=batch).astype(np.float32)
+    bt = torch.tensor(beta, dtype=torch.float64, requires_grad=True)
+    Jt = torch.tensor(g.J, dtype=torch.float64, requires_grad=True)
+    lz = dense.log_zr_dense(g.n, g.ei, g.ej, Jt, bt, W, torch.as_tensor(s))
+    l = lz.detach() - torch.as_tensor(lq, dtype=torch.float64)
+    wts = torch.softmax(l, 0)
+    db = torch.stack([torch.autograd.grad(lz[b], bt, retain_graph=True)[0] for b in range(batch)])
+    (corr_ref,) = torch.autograd.grad((wts * lz).sum(), Jt)
+    U_ref, Uq_ref, ess_ref = est.is_observables(lz.detach(), torch.as_tensor(lq, dtype=torch.float64), -db)
+    d_spins = to_dev_spins(s.reshape(-1))
+    logZR = torch.empty(batch, dtype=torch.float64, device="cuda")
+    model.ctx.contract(model.betas, batch, d_spins, tv.FP32, logZR)
+    logq = torch.as_tensor(lq).cuda()
+    corr = torch.full((g.m,), float("nan"), dtype=torch.float64, device="cuda")
+    out = model.ctx.observables(model.betas, batch, d_spins, logZR, logq, corr)
+    torch.cuda.synchronize()
+    U, Uq, ess = out[0]
+    assert abs(U - U_ref) <= 2e-5 * abs(U_ref)
+    assert abs(Uq - Uq_ref) <= 2e-5 * abs(Uq_ref)
+    assert abs(ess - ess_ref) <= 1e-4 * ess_ref
+    assert float((corr.cpu() - corr_ref).abs().max()) <= 2e-5 * max(1.0, float(corr_ref.abs().max()))
 
 
 @pytest.mark.parametrize("wu", [2, 6])
