@@ -126,12 +126,18 @@ int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int
  *              first); TNVAN_SLICE_GREEDY: order and slicing built together
  *              (eliminate the least-fill spin of degree <= w_u, else slice the
  *              spin of largest degree); TNVAN_SLICE_BEST: both, smaller W wins.
- *   out_w      [n_spins] receives W in slicing order (use it as the
+ *   anneal_iters  >= 0: moves of simulated annealing applied to the winner
+ *              (one sliced spin returns to R, a greedy elimination with
+ *              slicing repairs the width, Metropolis acceptance on |W| under a
+ *              linearly falling temperature from 0.5; the smallest feasible
+ *              set is kept); 0 = none.
+ *   out_w      [n_spins] receives W (slicing order, or for annealed sets the
+ *              order in which spins entered W; use it as the
  *              autoregressive order);
  *   out_order  [n_spins] receives R's elimination order (n_spins - n_w
  *              entries; pass it to tnvan_set_width_set_ordered);
  *   out_info   [3] receives n_w, the order's width, and the winning trial
- *              (2 * restart + (search == GREEDY)).
+ *              of the searches (2 * restart + (search == GREEDY)).
  * Deterministic for a given seed (integer arithmetic only).
  * Errors: TNVAN_E_ARG. */
 #define TNVAN_FIND_MAX_N 16384
@@ -139,8 +145,8 @@ int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int
 #define TNVAN_SLICE_GREEDY 2
 #define TNVAN_SLICE_BEST 3
 int tnvan_find_width_set(int n_spins, int n_edges, const int32_t* ei, const int32_t* ej, int w_u,
-                         int restarts, uint64_t seed, int mode, int32_t* out_w, int32_t* out_order,
-                         int32_t* out_info);
+                         int restarts, uint64_t seed, int mode, int anneal_iters, int32_t* out_w,
+                         int32_t* out_order, int32_t* out_info);
 
 /* Attach the MADE network of `instance` (Eq. 7, Fig. 1(d)): D = n_w inputs and
  * outputs, n_hidden (0..2) ReLU hidden layers of widths[0..n_hidden-1]

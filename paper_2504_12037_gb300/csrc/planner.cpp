@@ -18,8 +18,14 @@
 //    degree <= w_u (least fill first) while there is one, otherwise slice the
 //    spin of largest degree -- then the same return step, each trial checked
 //    by a fresh greedy elimination without slicing.
-// The smaller W over all trials wins.  Host code only: no device work.
+// The smaller W over all trials wins.  Optionally the winner is then
+// annealed (the paper also anneals): a random sliced spin returns to R, a
+// greedy elimination with slicing repairs the width (possibly slicing
+// others), and the move is accepted by the Metropolis rule on |W| under a
+// linearly falling temperature; the smallest set seen is kept.  Host code
+// only: no device work.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -285,13 +291,50 @@ Result search_greedy(const Graph& G, int wu, Rng& rng) {
   return r;
 }
 
+Result search_anneal(const Graph& G, int wu, Rng& rng, const Result& start, int iters, double T0) {
+  const int n = G.n;
+  std::vector<char> inW(n, 0);
+  for (int u : start.W) inW[u] = 1;
+  std::vector<int> cur(start.W), ord, extra;
+  Result best = start;
+  for (int it = 0; it < iters && !cur.empty(); ++it) {
+    const double T = T0 * (1.0 - (double)it / iters) + 1e-3;
+    const int pick = rng.below((int)cur.size());
+    const int u = cur[pick];
+    std::vector<char> removed(inW);
+    removed[u] = 0;
+    extra.clear();
+    greedy(G, removed, wu, true, &rng, &ord, &extra);
+    const int delta = (int)extra.size() - 1;
+    const double accept = delta <= 0 ? 1.0 : std::exp(-delta / T);
+    const double r = (double)(rng.next() >> 11) * (1.0 / 9007199254740992.0);
+    if (r < accept) {
+      inW[u] = 0;
+      cur.erase(cur.begin() + pick);
+      for (int v : extra) {
+        inW[v] = 1;
+        cur.push_back(v);
+      }
+      if (cur.size() < best.W.size()) {
+        best.W = cur;
+        best.order = ord;
+      }
+    }
+  }
+  std::vector<char> removed(n, 0);
+  for (int u : best.W) removed[u] = 1;
+  best.width = width_along(G, best.order, removed, nullptr);
+  return best;
+}
+
 }  // namespace
 
 extern "C" int tnvan_find_width_set(int n_spins, int n_edges, const int32_t* ei, const int32_t* ej, int w_u,
-                                    int restarts, uint64_t seed, int mode, int32_t* out_w,
+                                    int restarts, uint64_t seed, int mode, int anneal_iters, int32_t* out_w,
                                     int32_t* out_order, int32_t* out_info) {
   if (n_spins < 1 || n_spins > TNVAN_FIND_MAX_N || n_edges < 0 || (n_edges > 0 && (!ei || !ej)) || w_u < 0 ||
-      restarts < 1 || mode < TNVAN_SLICE_FIXED || mode > TNVAN_SLICE_BEST || !out_w || !out_order || !out_info)
+      restarts < 1 || mode < TNVAN_SLICE_FIXED || mode > TNVAN_SLICE_BEST || anneal_iters < 0 || !out_w ||
+      !out_order || !out_info)
     return TNVAN_E_ARG;
   Graph G;
   G.n = n_spins;
@@ -315,6 +358,10 @@ extern "C" int tnvan_find_width_set(int n_spins, int n_edges, const int32_t* ei,
         best_tag = 2 * t + (m == TNVAN_SLICE_GREEDY);
       }
     }
+  }
+  if (anneal_iters > 0) {
+    Rng rng{seed ^ 0x5851f42d4c957f2dull};
+    best = search_anneal(G, w_u, rng, best, anneal_iters, 0.5);
   }
   std::copy(best.W.begin(), best.W.end(), out_w);
   std::copy(best.order.begin(), best.order.end(), out_order);

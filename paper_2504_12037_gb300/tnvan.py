@@ -35,8 +35,8 @@ SIGNATURES = {
     "tnvan_init_graph": (_c_int, [_vp, _c_int, _c_int, _c_int, _i32p, _i32p, _dblp, _c_int, _c_int, _c_int, _c_int]),
     "tnvan_set_width_set": (_c_int, [_vp, _c_int, _c_int, _i32p]),
     "tnvan_set_width_set_ordered": (_c_int, [_vp, _c_int, _c_int, _i32p, _i32p]),
-    "tnvan_find_width_set": (_c_int, [_c_int, _c_int, _i32p, _i32p, _c_int, _c_int, _c_u64, _c_int, _i32p, _i32p,
-                                      _i32p]),
+    "tnvan_find_width_set": (_c_int, [_c_int, _c_int, _i32p, _i32p, _c_int, _c_int, _c_u64, _c_int, _c_int, _i32p,
+                                      _i32p, _i32p]),
     "tnvan_set_made": (_c_int, [_vp, _c_int, _c_int, _i32p, _vp]),
     "tnvan_n_params": (_c_int, [_vp, _c_int, _i64p, _i64p]),
     "tnvan_instance_info": (_c_int, [_vp, _c_int, _i32p]),
@@ -108,15 +108,17 @@ def _arr(a, dtype):
     return a, a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
-def find_width_set(n_spins: int, ei, ej, w_u: int, restarts: int = 4, seed: int = 0, mode: int = SLICE_BEST):
-    """Width-set finder (tnvan_find_width_set): returns (W in slicing order,
-    R's elimination order, achieved width, winning trial).  Host only."""
+def find_width_set(n_spins: int, ei, ej, w_u: int, restarts: int = 4, seed: int = 0, mode: int = SLICE_BEST,
+                   anneal: int = 0):
+    """Width-set finder (tnvan_find_width_set): returns (W, R's elimination
+    order, achieved width, winning trial); `anneal` annealing moves refine the
+    winner.  Host only."""
     ei, pi = _arr(ei, np.int32)
     ej, pj = _arr(ej, np.int32)
     out_w = np.zeros(n_spins, np.int32)
     out_o = np.zeros(n_spins, np.int32)
     info = np.zeros(3, np.int32)
-    rc = lib().tnvan_find_width_set(n_spins, ei.shape[0], pi, pj, w_u, restarts, seed, mode,
+    rc = lib().tnvan_find_width_set(n_spins, ei.shape[0], pi, pj, w_u, restarts, seed, mode, anneal,
                                     out_w.ctypes.data_as(_i32p), out_o.ctypes.data_as(_i32p),
                                     info.ctypes.data_as(_i32p))
     if rc != OK:

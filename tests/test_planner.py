@@ -126,4 +126,18 @@ def test_bad_arguments_are_rejected():
         tv.find_width_set(3, np.array([0], np.int32), np.array([1], np.int32), 1, restarts=0)
     with pytest.raises(tv.TnvanError):
         tv.find_width_set(3, np.array([0], np.int32), np.array([1], np.int32), 1, mode=4)
-    assert L.tnvan_find_width_set(0, 0, None, None, 1, 1, 0, 3, None, None, None) == tv.E_ARG
+    with pytest.raises(tv.TnvanError):
+        tv.find_width_set(3, np.array([0], np.int32), np.array([1], np.int32), 1, anneal=-1)
+    assert L.tnvan_find_width_set(0, 0, None, None, 1, 1, 0, 3, 0, None, None, None) == tv.E_ARG
+
+
+@pytest.mark.parametrize("graph,wu", [("rrg300d4", 3), ("rrg300d4", 8), ("rrg256d3", 6)])
+def test_annealing_keeps_valid_sets_and_never_grows_them(graph, wu):
+    g = wl.random_regular(300, 4, 12037) if graph == "rrg300d4" else wl.random_regular(256, 3, 12037)
+    ei, ej = np.asarray(g.ei, np.int32), np.asarray(g.ej, np.int32)
+    base = tv.find_width_set(g.n, ei, ej, wu, restarts=2, seed=7)
+    W, order, width, _ = tv.find_width_set(g.n, ei, ej, wu, restarts=2, seed=7, anneal=400)
+    _check(g.n, ei, ej, wu, W, order, width)
+    assert len(W) <= len(base[0])
+    again = tv.find_width_set(g.n, ei, ej, wu, restarts=2, seed=7, anneal=400)
+    assert np.array_equal(again[0], W) and np.array_equal(again[1], order)
