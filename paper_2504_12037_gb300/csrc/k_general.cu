@@ -120,17 +120,20 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
   const int* H = G.fprog + G.fhdr[c];
   const int nsteps = H[0], fin = H[1];
   const int g0 = G.comp_step0[c];
-  // the group's lanes compute identical log-scale terms: lane 0 alone keeps
-  // the FP64 sums; the power-of-two scales add up exactly as an integer
-  const bool keep = lane == 0;
+  // log-scale terms of the component: the power-of-two scales add up exactly
+  // as an integer, the field offsets |h_v| in a compensated FP32 sum (Kahan),
+  // both added to the FP64 result once per component
   int esum = 0;
+  float hs = 0.f, hc = 0.f;
   for (int st = 0; st < nsteps; ++st) {
     const StepRec r = step_at(G, g0 + st);
     const float h = field_of(G, r.fb, r.fc, s);
     const float ah = fabsf(h);
-    if (keep) {
-      lz += (double)beta * (double)ah;
-      if (DB) dl += (double)ah;
+    {
+      const float y = ah - hc;
+      const float t2 = hs + y;
+      hc = (t2 - hs) - y;
+      hs = t2;
     }
     const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
     const float fr[2] = {h - ah, -h - ah};
@@ -170,10 +173,11 @@ __device__ __forceinline__ void run_component(const GenDev& G, int c, const int8
     esum += e;
     __syncwarp();
   }
-  if (keep) {
+  if (lane == 0) {
+    const double hsum = (double)hs - (double)hc;
     const float z = A[fin * RS];
-    lz += (double)esum * 0.69314718055994530942 + (double)logf(z);
-    if (DB) dl += (double)(dA[fin * RS] / z);
+    lz += (double)beta * hsum + (double)esum * 0.69314718055994530942 + (double)logf(z);
+    if (DB) dl += hsum + (double)(dA[fin * RS] / z);
   }
 }
 
