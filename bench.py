@@ -275,41 +275,37 @@ def run_ours(a):
     # and Adam t to run, into the captured step's device counter), the step,
     # and the step's results read back to pinned host memory (samples, log q,
     # log Z_R) with F_q / F_IS / stderr / log Z_IS per instance read on the
-    # host (model.free_energy).  With a captured step the outputs rotate over
-    # three captures of the step (three buffer sets) and the host reads step
-    # i's results after launching step i + 2, so the read-back runs on a copy
-    # stream while later steps compute and host jitter does not idle the GPU.
+    # host (model.free_energy).  With a captured step the outputs alternate
+    # between two captures of the step (two buffer sets), so step i's
+    # read-back runs on a copy stream while step i + 1 computes.
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     fe_last = None
     if captured is not None:
-        K, LAG = 3, 2
-        slots = [captured] + [model.capture_train_step(B, seed, prec, 0.01, model.buffers(B),
-                                                       torch.empty_like(dbeta), torch.empty_like(dJ))
-                              for _ in range(K - 1)]
+        db2 = torch.empty_like(dbeta)
+        dj2 = torch.empty_like(dJ)
+        slots = [captured, model.capture_train_step(B, seed, prec, 0.01, model.buffers(B), db2, dj2)]
         cs = torch.cuda.Stream()
         h_out = [(torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True),
                   torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True),
-                  torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)) for _ in range(K)]
-        h_ctr = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(K)]
-        ran = [torch.cuda.Event() for _ in range(K)]
-        read = [torch.cuda.Event() for _ in range(K)]
+                  torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)) for _ in range(2)]
+        h_ctr = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        ran = [torch.cuda.Event() for _ in range(2)]
+        read = [torch.cuda.Event() for _ in range(2)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(a.e2e_steps + LAG):
+        for i in range(a.e2e_steps + 1):
             if i < a.e2e_steps:
-                j = i % K
-                if i >= K:
+                j = i % 2
+                if i >= 2:
                     stream.wait_event(read[j])  # slot j's buffers have been read back
-                # the host counter of slot j is free: step i - K was read back
-                # (host-synchronised) in an earlier iteration, after its copy
                 h_ctr[j][0] = 10 ** 6 + i
                 slots[j].counter.copy_(h_ctr[j], non_blocking=True)
                 slots[j].replay()
                 ran[j].record(stream)
-            if i >= LAG:
-                jp = (i - LAG) % K
+            if i >= 1:
+                jp = (i - 1) % 2
                 sp_, lq_, lz_ = slots[jp].out
                 cs.wait_event(ran[jp])
                 fe_last = model.free_energy(B, lz_, lq_, cs)  # host read of the step's statistics
@@ -340,8 +336,7 @@ def run_ours(a):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e = {"value": samples_step / float(te.item()), "unit": UNIT,
            "h2d_bytes_per_step": 8 if captured is not None else 8 * n_inst,
-           "path": ("model.capture_train_step replays (three buffer sets; step i read back after step i + 2 "
-                    "is launched)"
+           "path": ("model.capture_train_step replays (two buffer sets; read-back of step i beside step i + 1)"
                     if captured is not None else "model.train_step"),
            "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 32 * n_inst)}
 
