@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
         *reinterpret_cast<uint4*>((l1 ? sH1 : sH2) + rg * (l1 ? sbo1 : sbo2) + 16 * col) = make_uint4(0, 0, 0, 0);
       }
     }
-    ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles visible; one verdict
+    ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles visible; one agreed flag
     if (!ok) break;
     if (t == 0 && g + 1 < P.n_groups) {  // the next group's data, while this group runs
       copy_group(g + 1, gbn, 0u);
