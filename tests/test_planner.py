@@ -141,3 +141,20 @@ def test_annealing_keeps_valid_sets_and_never_grows_them(graph, wu):
     assert len(W) <= len(base[0])
     again = tv.find_width_set(g.n, ei, ej, wu, restarts=2, seed=7, anneal=400)
     assert np.array_equal(again[0], W) and np.array_equal(again[1], order)
+
+
+def test_zero_width_leaves_an_independent_set():
+    """w_u = 0: every spin of R is summed alone, so R has no bonds and W is a
+    vertex cover; on bipartite graphs the smallest cover has the size of a
+    maximum matching (Konig), which the brute force confirms."""
+    for seed in range(6):
+        G = nx.bipartite.random_graph(5, 5, 0.4, seed=seed)
+        n, ei, ej = _g(G)
+        W, order, width, _ = tv.find_width_set(n, ei, ej, 0, restarts=4, seed=seed)
+        _check(n, ei, ej, 0, W, order, width)
+        Wset = set(int(x) for x in W)
+        assert all(a in Wset or b in Wset for a, b in zip(ei.tolist(), ej.tolist()))
+        best = len(sl.min_width_set(n, ei, ej, 0))
+        matching = len(nx.max_weight_matching(nx.convert_node_labels_to_integers(G), maxcardinality=True))
+        assert best == matching
+        assert best <= len(W) <= best + 1
