@@ -94,7 +94,7 @@ int tnvan_init_graph(tnvan_ctx* ctx, int instance, int n_spins, int n_edges, con
  * order (Eq. 6's "predetermined order").  The host planner then builds the
  * contraction plan of R: lattice strips (W must then be whole columns),
  * a dense block (|R| <= 16), or per-component elimination programs
- * (elimination width <= 8).  Plans are independent of beta.
+ * (elimination width <= 12).  Plans are independent of beta.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no graph), TNVAN_E_UNSUPPORTED. */
 int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w);
 
@@ -105,7 +105,7 @@ int tnvan_set_width_set(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w)
  * the planner's min-fill order).  r_order == NULL is tnvan_set_width_set.
  * Errors: as tnvan_set_width_set; TNVAN_E_ARG when r_order is not a
  * permutation of R, or is given for a LATTICE2D / DENSE plan;
- * TNVAN_E_UNSUPPORTED when the order needs elimination width > 8. */
+ * TNVAN_E_UNSUPPORTED when the order needs elimination width > 12. */
 int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int32_t* w,
                                 const int32_t* r_order);
 
@@ -116,7 +116,7 @@ int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int
  * creates a factor over its neighbours at that point (fill edges included);
  * the width of an order is the largest such factor.  w_u = 1 leaves a
  * forest, i.e. W is a feedback vertex set; the GPU elimination kernels accept
- * w_u <= 8.  Host only (no device work, no context, callable without a GPU).
+ * w_u <= 12.  Host only (no device work, no context, callable without a GPU).
  *   n_spins <= TNVAN_FIND_MAX_N; edges as in tnvan_init_graph.
  *   w_u        width bound (>= 0).
  *   restarts   number of randomised trials per search (>= 1);

@@ -13,7 +13,7 @@
 #define TNVAN_MAX_HIDDEN 512
 #define TNVAN_MAX_D 1024
 #define TNVAN_MAX_STRIP_W 4
-#define TNVAN_MAX_ELIM_W 8
+#define TNVAN_MAX_ELIM_W 12
 #define GROUP_INTS 15
 #define TNVAN_TC_PLANS 3  // step-group size limits of the tensor-core sampler: 4, 6, 8
 // Tensor-core sampler group record: i0 i1 u1lo u1hi u2lo u2hi, block start and

@@ -5,8 +5,8 @@
 // Eliminating spin v multiplies every factor that contains v -- its field
 // factor exp(beta h_v(s) r_v) from the width set, the Boltzmann matrices of its
 // remaining bonds (Eq. 2) and the intermediate tables that contain it -- and
-// sums v out, giving a table over its remaining neighbours (at most 2^8
-// entries).  The host compiles each step into a record and, per input table,
+// sums v out, giving a table over its remaining neighbours (at most
+// 2^TNVAN_MAX_ELIM_W entries).  The host compiles each step into a record and, per input table,
 // an index map from the step's extended index (its out-scope spins and v) to
 // the input's entry; the product of a step's bond factors depends only on
 // that index and beta and is tabulated once per call (general_pp_kernel), so
@@ -423,14 +423,15 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
       const unsigned short* mp = G.map + r.mo;
       const int out = r.out_full;
       const float scl = sc[st * RS];
-      const int np = min(r.npair, 8);  // at most 8 neighbours remain
-      int pos[8];
+      constexpr int MW = TNVAN_MAX_ELIM_W;
+      const int np = min(r.npair, MW);  // at most MW neighbours remain
+      int pos[MW];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) pos[j] = j < np ? r.pr[2 * j + 1] : 0;
+      for (int j = 0; j < MW; ++j) pos[j] = j < np ? r.pr[2 * j + 1] : 0;
       float gs = 0.f;       // sum g sigma_v
-      float gp[8];          // sum g sigma_v sigma_u per pair
+      float gp[MW];         // sum g sigma_v sigma_u per pair
 #pragma unroll
-      for (int j = 0; j < 8; ++j) gp[j] = 0.f;
+      for (int j = 0; j < MW; ++j) gp[j] = 0.f;
       for (int x = lane; x < M; x += GL) {
         const float abx = Ab[(out + x) * RS] * scl;
         for (int sg = 0; sg < 2; ++sg) {
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(128) general_dJ_kernel(const InstDev* __restri
           gb[ext * RS] = g;
           gs = fmaf(g, sg ? -1.f : 1.f, gs);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
+          for (int j = 0; j < MW; ++j)
             if (j < np) gp[j] = fmaf(g, (((x >> pos[j]) & 1) == sg) ? 1.f : -1.f, gp[j]);
         }
       }

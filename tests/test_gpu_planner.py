@@ -27,7 +27,7 @@ def _planned(n, d, wu, seed):
     return g, W, order, width
 
 
-@pytest.mark.parametrize("n,d,wu", [(1000, 3, 8), (1000, 3, 2), (256, 3, 8), (300, 4, 5)])
+@pytest.mark.parametrize("n,d,wu", [(1000, 3, 8), (1000, 3, 2), (256, 3, 8), (300, 4, 5), (300, 3, 12)])
 def test_planned_rrg_contraction_parity(n, d, wu):
     g, W, order, width = _planned(n, d, wu, 12037 + 6000 + n + d)
     model = TNVAN([g], [W], HIDDEN, [1.0], seed=5, init_scale=1.5, elim_orders=[order])
@@ -37,8 +37,9 @@ def test_planned_rrg_contraction_parity(n, d, wu):
     _parity(model, [g], [W], HIDDEN, [1.0], batch=40)
 
 
-def test_planned_rrg_dJ_parity():
-    g, W, order, _ = _planned(1000, 3, 8, 12037 + 6000 + 1003)
+@pytest.mark.parametrize("n,wu", [(1000, 8), (300, 12)])
+def test_planned_rrg_dJ_parity(n, wu):
+    g, W, order, _ = _planned(n, 3, wu, 12037 + 6000 + n + 3)
     beta = 0.7
     model = TNVAN([g], [W], HIDDEN, [beta], seed=5, init_scale=1.5, elim_orders=[order])
     B = 20
@@ -87,12 +88,12 @@ def test_ordered_width_set_arguments():
     assert e.value.code == tv.E_ARG
     ctx.set_width_set(0, W, order)
     assert ctx.instance_info(0)["max_width"] <= 8
-    # an order whose width exceeds the kernels' limit is refused
-    W1, o1, w1, _ = tv.find_width_set(g.n, g.ei, g.ej, 12, restarts=1, seed=1)
-    if w1 > 8:
-        with pytest.raises(tv.TnvanError) as e:
-            ctx.set_width_set(0, W1, o1)
-        assert e.value.code == tv.E_UNSUPPORTED
+    # an order whose width exceeds the kernels' limit (12) is refused
+    W1, o1, w1, _ = tv.find_width_set(g.n, g.ei, g.ej, 16, restarts=1, seed=1)
+    assert w1 > 12
+    with pytest.raises(tv.TnvanError) as e:
+        ctx.set_width_set(0, W1, o1)
+    assert e.value.code == tv.E_UNSUPPORTED
     # lattice plans take no order
     lat = wl.lattice(8, 8, "gauss", seed=1)
     Wl = wl.width_columns(8, 8, [3])
