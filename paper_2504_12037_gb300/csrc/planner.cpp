@@ -6,7 +6,7 @@
 // fill edges of the earlier eliminations) produces a factor over v's current
 // neighbours; the width of an order is the largest such neighbour count.
 // w_u = 1 leaves a forest (W is a feedback vertex set); the GPU elimination
-// kernels take widths up to 8.
+// kernels take widths up to 12.
 //
 // Two searches, each restarted with different random tie-breaks:
 //  * fixed order (the paper's route): a min-fill order of the whole graph,
