@@ -134,3 +134,98 @@ def test_is_uniform_weights():
     lz = torch.linspace(-3.0, 2.0, 7, dtype=torch.float64)
     U, Uq, ess = est.is_observables(lz, lz, torch.arange(7, dtype=torch.float64))
     assert abs(U - Uq) < 1e-12 and abs(ess - 7.0) < 1e-12
+
+
+# --- free_energies: the -ln B of log Z_IS, the ddof of the stderr, the mean ---
+
+def test_constant_l_gives_equal_free_energies_and_zero_stderr():
+    # l_b = c for every sample: mean = c and logsumexp - ln B = c + ln B - ln B,
+    # so F_q = F_IS = -c / beta whatever B is; a dropped (or doubled) ln B moves
+    # F_IS by ln B / beta.  The spread is zero.
+    for B in (1, 2, 7, 1000):
+        for c, beta in ((-3.25, 0.5), (41.0, 2.0)):
+            lz = np.full(B, c + 1.5)
+            lq = np.full(B, 1.5)
+            r = est.free_energies(lz, lq, beta)
+            assert abs(r["F_q"] - (-c / beta)) < 1e-12
+            assert abs(r["F_IS"] - (-c / beta)) < 1e-12
+            assert abs(r["logZ_IS"] - c) < 1e-12
+            assert r["stderr"] == 0.0
+
+
+def test_three_sample_hand_values():
+    # l = (0, ln 2, ln 6): the mean importance weight is (1 + 2 + 6) / 3 = 3,
+    # so log Z_IS = ln 3; the mean of l is ln 12 / 3.
+    l = np.array([0.0, math.log(2.0), math.log(6.0)])
+    r = est.free_energies(l, np.zeros(3), 0.5)
+    assert abs(r["logZ_IS"] - math.log(3.0)) < 1e-14
+    assert abs(r["F_IS"] - (-2.0 * math.log(3.0))) < 1e-14
+    assert abs(r["F_q"] - (-2.0 * math.log(12.0) / 3.0)) < 1e-14
+    # l = (1, 2, 6), beta = 2: mean 3, squared deviations 4 + 1 + 9 = 14, so the
+    # unbiased variance (ddof 1) is 7 and stderr = sqrt(7) / (2 sqrt(3)); the
+    # biased form would give sqrt(14/3) / (2 sqrt(3)).
+    r = est.free_energies(np.array([1.0, 2.0, 6.0]), np.zeros(3), 2.0)
+    assert abs(r["F_q"] - (-1.5)) < 1e-14
+    assert abs(r["stderr"] - math.sqrt(7.0) / (2.0 * math.sqrt(3.0))) < 1e-14
+
+
+def test_is_estimate_is_exact_for_exact_q_and_for_a_full_uniform_census():
+    # Eq. 5 / Eq. 9: if q(s) equals the Boltzmann marginal p(s) = Z_R(s) / Z of
+    # the width set, every l_b = log Z_R(s_b) - log p(s_b) = ln Z, so F_q = F_IS
+    # = F (brute force) on any samples and the stderr vanishes.
+    g, W, lzr = _cfg1()
+    D = len(W)
+    logZ = float(ising.log_z_brute(g.n, g.ei, g.ej, g.J, 1.0))
+    F = -logZ
+    log_p = lzr - torch.logsumexp(lzr, 0)
+    idx = np.random.default_rng(5).integers(0, 2 ** D, size=333)
+    r = est.free_energies(lzr[idx], log_p[idx], 1.0)
+    assert abs(r["F_q"] - F) < 1e-12 and abs(r["F_IS"] - F) < 1e-12
+    assert r["stderr"] < 1e-12
+    # Uniform q (log q = -D ln 2) over every width-set state once, B = 2^D:
+    # logsumexp(l) = ln sum_s Z_R(s) + D ln 2 = ln Z + ln B (Eq. 3), so F_IS = F
+    # exactly while F_q >= F (Jensen).
+    r = est.free_energies(lzr, torch.full_like(lzr, -D * math.log(2.0)), 1.0)
+    assert abs(r["F_IS"] - F) < 1e-12
+    assert r["F_q"] > F
+
+
+def test_is_estimate_converges_on_uniform_samples():
+    # B = 2^15 uniform draws of the 16 width states of the 4x4 workload: F_IS
+    # approaches the brute-force F; the gap is far below the per-sample spread
+    g, W, lzr = _cfg1()
+    D = len(W)
+    F = -float(ising.log_z_brute(g.n, g.ei, g.ej, g.J, 1.0))
+    idx = np.random.default_rng(8).integers(0, 2 ** D, size=1 << 15)
+    r = est.free_energies(lzr[idx], torch.full((idx.size,), -D * math.log(2.0), dtype=torch.float64), 1.0)
+    assert abs(r["F_IS"] - F) < 4.0 * r["stderr"]
+    assert r["F_IS"] <= r["F_q"]
+
+
+# --- adam_step beyond the first step ---
+
+def test_adam_constant_gradient_closed_form():
+    # With g_t = g for every t: m_t = g (1 - b1^t) and v_t = g^2 (1 - b2^t), so
+    # the bias-corrected moments are g and g^2 at every t and each update is
+    # lr g / (|g| + eps): after t steps p = -t lr g / (|g| + eps).  eps = 0.1
+    # makes the placement of eps (outside the square root) visible.
+    g = np.array([0.5, -2.0, 3e-3])
+    lr, eps = 0.05, 0.1
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 6):
+        p, m, v = est.adam_step(p, g, m, v, t, lr=lr, eps=eps)
+        assert np.allclose(p, -t * lr * g / (np.abs(g) + eps), rtol=1e-13, atol=0)
+
+
+def test_adam_zero_then_g_closed_form():
+    # g_1 = 0, g_2 = g: m_2 = (1 - b1) g, v_2 = (1 - b2) g^2; corrected by
+    # 1 - b1^2 = (1 - b1)(1 + b1) and 1 - b2^2 = (1 - b2)(1 + b2) they are
+    # g / (1 + b1) and g^2 / (1 + b2), so the second update is
+    # lr (g / (1 + b1)) / (|g| / sqrt(1 + b2) + eps).
+    b1, b2, lr, eps = 0.9, 0.999, 0.01, 0.05
+    g = np.array([1.25, -0.4])
+    p, m, v = est.adam_step(np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2), 1, lr=lr, b1=b1, b2=b2, eps=eps)
+    assert np.all(p == 0.0)
+    p, m, v = est.adam_step(p, g, m, v, 2, lr=lr, b1=b1, b2=b2, eps=eps)
+    want = -lr * (g / (1 + b1)) / (np.abs(g) / math.sqrt(1 + b2) + eps)
+    assert np.allclose(p, want, rtol=1e-13, atol=0)
