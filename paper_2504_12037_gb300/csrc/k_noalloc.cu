@@ -14,11 +14,10 @@
 
 namespace tnvan {
 
-// Kernels of the context-based reduction (k_train.cu), reused unchanged.
+// The two-pass FP64 reduction kernels (k_train.cu).
 __global__ void reduce_part_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
                                    const float* __restrict__ logq, double* __restrict__ part);
-__global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
-                                    const float* __restrict__ logq, const double* __restrict__ part,
+__global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const double* __restrict__ part,
                                     double* __restrict__ stats);
 
 #define NOALLOC_MAX_INST 128
@@ -72,12 +71,19 @@ int tnvan_free_energy_noalloc(int n_inst, int batch, const double* betas, const 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
     return set_err(TNVAN_E_CUDA, "cudaGetDevice failed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* scratch = nullptr;
   {
-    // one-time set-up per device: the host-side symbol is only a stand-in, the
-    // kernels need the device address of this device's copy of the array
+    // The host-side symbol is only a stand-in: the kernels need the device
+    // address of this device's copy of the array.  It is looked up on every
+    // call made outside stream capture (so a device reset, which reloads the
+    // module, cannot leave a stale address behind) and cached per device for
+    // calls made while `stream` is being captured, where the lookup may not
+    // run; the first call on a device must therefore come before any capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return set_err(TNVAN_E_CUDA, "cudaStreamIsCapturing failed");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_ptr[dev]) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess) return set_err(TNVAN_E_CUDA, cudaGetErrorString(e));
@@ -91,10 +97,9 @@ int tnvan_free_energy_noalloc(int n_inst, int batch, const double* betas, const 
   if (n_part < 1) n_part = 1;
   double* stats = scratch;
   double* part = scratch + 8 * NOALLOC_MAX_INST;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // every tuple and statistic read below is written first: nothing to clear
   reduce_part_kernel<<<dim3(n_part, n_inst), 256, 0, s>>>(li, n_part, d_logZR, d_logq, part);
-  reduce_final_kernel<<<n_inst, 32, 0, s>>>(li, n_part, d_logZR, d_logq, part, stats);
+  reduce_final_kernel<<<n_inst, 32, 0, s>>>(li, n_part, part, stats);
   noalloc_out_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(n_inst, stats, d_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(TNVAN_E_CUDA, cudaGetErrorString(e));
