@@ -12,9 +12,11 @@ Metric: samples per second (all instances, all ranks).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank runs the same instances on its own GPU with its own
-random stream (weak scaling, no data-path collective); rank 0 prints one JSON
-line.  `--impl reference` times the FP64 CPU oracle on the same workload.
+Under torchrun every rank draws its own 16384 samples per beta (own Philox
+stream) for one shared set of networks: the ranks exchange their Eq. 9
+statistics (all-gather) and sum their gradients (all-reduce) every step
+(weak scaling; paper_2504_12037_gb300/dp.py); rank 0 prints one JSON line.
+`--impl reference` times the FP64 CPU oracle on the same workload.
 """
 import argparse
 import json
@@ -33,9 +35,25 @@ CONFIG = 2
 METRIC = "samples/sec (sample+contract+reduce) and |F_q-F_exact|/N; mixed vs FP32 on one GB300"
 UNIT = "samples/s"
 FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-MEASURED_BF16_TFLOPS = 1865.6  # MEASURED_PEAKS.json: bf16_tflops (burst)
+# fallbacks when MEASURED_PEAKS.json is absent (one earlier GB300 measurement)
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+
+
+def measured_peaks():
+    """Roofline denominators: the measured copy bandwidth and cuBLAS
+    BF16 throughput of the GB300s, else the fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        out = {k: float(d[k]) for k in FALLBACK_PEAKS if k in d}
+        if "bf16_tflops" in out and "hbm_gbs" in out:
+            out.setdefault("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"])
+            out["source"] = "MEASURED_PEAKS.json, of measured"
+            return out
+    except (OSError, ValueError, KeyError):
+        pass
+    return dict(FALLBACK_PEAKS, source="fallback (MEASURED_PEAKS.json absent), of fallback")
 # dram__bytes_read.sum + dram__bytes_write.sum per whole-batch launch from ncu
 # captures of the same kernels on the same workload (see profiles/); None if not
 # captured
@@ -153,6 +171,27 @@ def strip_flops(w, L):
     return (L - 1) * (w * nx * 3 + nx) + L * 2 * nx
 
 
+def parity_run(model, step, name, bufs, B):
+    """One more step of the timed kind (`step`, the timed path with its tuning),
+    with what the oracle needs to check it copied to the host: the parameters
+    the step sampled with, the samples, log q and log Z_R of sampled rows (every
+    1021st sample and the tile edges), the whole batch's log q and log Z_R and
+    the step's statistics rows."""
+    import numpy as np
+    import torch
+
+    p_before = model.params.cpu().numpy().copy()
+    step(3 * 10 ** 6)
+    torch.cuda.synchronize()
+    st = model.step_stats().cpu().numpy()
+    spins, logq, logZR = bufs
+    rows = np.unique(np.concatenate([np.arange(0, B, 1021), [r for r in (0, 127, 128, 255, 256, B - 1) if r < B]]))
+    lq, lz = logq.cpu().numpy(), logZR.cpu().numpy()
+    return {"precision": name, "params": p_before, "offsets": np.asarray(model.offsets), "rows": rows,
+            "spins": [model.spins_of(spins, k, B).cpu().numpy()[rows] for k in range(model.n)],
+            "logq": lq.reshape(model.n, B), "logZR": lz.reshape(model.n, B), "stats": st}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -185,13 +224,24 @@ def run_ours(a):
             model.ctx.set_tuning(tuned)
         else:
             tuned = None if a.no_autotune else model.ctx.autotune(model.betas, B, mode)
-        bufs = model.buffers(B)
         dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
         dJ = torch.empty(sum(model.n_edges), dtype=torch.float64, device="cuda")
         model.tuned = tuned
+        if world > 1:
+            # one set of networks trained on all ranks' samples: local sampling
+            # and contraction, statistics all-gather, gradient all-reduce, Adam
+            from paper_2504_12037_gb300.dp import DataParallelStep
 
-        def step(i):
-            model.train_step(B, seed, i, mode, 0.01, bufs, dbeta, dJ, stream)
+            dps = DataParallelStep(model, B, mode, 0.01, dbeta=dbeta, dJ=dJ)
+            bufs = dps.out
+
+            def step(i):
+                dps(12037, i, stream)
+        else:
+            bufs = model.buffers(B)
+
+            def step(i):
+                model.train_step(B, seed, i, mode, 0.01, bufs, dbeta, dJ, stream)
 
         for i in range(warmup):
             step(i)
@@ -251,7 +301,9 @@ def run_ours(a):
     samples_step = n_inst * B * world
     graph = None
     captured = None
-    if not a.no_graph:
+    # every rank takes the parity step (a data-parallel step is collective); rank 0 checks it
+    parity_runs = [parity_run(model, step, a.precision, (spins, logq, logZR), B)]
+    if not a.no_graph and world == 1:
         ms_g, captured = graph_time(model, prec, (spins, logq, logZR), dbeta, dJ)
         graph = {"value": samples_step / (ms_g / 1e3), "ms_per_step": ms_g,
                  "note": "whole training step captured once, replayed; Philox step from a device counter"}
@@ -263,8 +315,9 @@ def run_ours(a):
     value = samples_step / (ms_max / 1e3)
     compare = None
     if a.compare and a.compare != a.precision:
-        m_c, b_c, db_c, dj_c, _, ms_c, prof_c, _ = timed(PREC[a.compare], a.steps, a.warmup, False)
-        ms_cg = None if a.no_graph else graph_time(m_c, PREC[a.compare], b_c, db_c, dj_c)[0]
+        m_c, b_c, db_c, dj_c, step_c, ms_c, prof_c, _ = timed(PREC[a.compare], a.steps, a.warmup, False)
+        parity_runs.append(parity_run(m_c, step_c, a.compare, b_c, B))
+        ms_cg = None if (a.no_graph or world > 1) else graph_time(m_c, PREC[a.compare], b_c, db_c, dj_c)[0]
         ms_ch = ms_cg if ms_cg else ms_c
         compare = {"precision": a.compare, "value": samples_step / (ms_ch / 1e3), "ms_per_step": ms_ch,
                    "eager_ms_per_step": ms_c,
@@ -274,10 +327,10 @@ def run_ours(a):
     # Every step: the step's input from pinned host memory (which Philox step
     # and Adam t to run, into the captured step's device counter), the step,
     # and the step's results read back to pinned host memory (samples, log q,
-    # log Z_R) with F_q / F_IS / stderr / log Z_IS per instance read on the
-    # host (model.free_energy).  With a captured step the outputs alternate
-    # between two captures of the step (two buffer sets), so step i's
-    # read-back runs on a copy stream while step i + 1 computes.
+    # log Z_R and the step's Eq. 9 rows: F_q, F_IS, stderr, log Z_IS, ... per
+    # instance, reduced inside the step).  With a captured step the outputs
+    # alternate between two captures of the step (two buffer sets), so step
+    # i's read-back runs on a copy stream while step i + 1 computes.
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -291,6 +344,7 @@ def run_ours(a):
                   torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True),
                   torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)) for _ in range(2)]
         h_ctr = [torch.zeros(1, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        h_st = [torch.zeros(n_inst, 8, dtype=torch.float64, pin_memory=True) for _ in range(2)]
         ran = [torch.cuda.Event() for _ in range(2)]
         read = [torch.cuda.Event() for _ in range(2)]
         torch.cuda.synchronize()
@@ -308,8 +362,8 @@ def run_ours(a):
                 jp = (i - 1) % 2
                 sp_, lq_, lz_ = slots[jp].out
                 cs.wait_event(ran[jp])
-                fe_last = model.free_energy(B, lz_, lq_, cs)  # host read of the step's statistics
                 with torch.cuda.stream(cs):
+                    h_st[jp].copy_(slots[jp].stats, non_blocking=True)  # the step's statistics
                     h_out[jp][0].copy_(sp_, non_blocking=True)
                     h_out[jp][1].copy_(lq_, non_blocking=True)
                     h_out[jp][2].copy_(lz_, non_blocking=True)
@@ -317,15 +371,18 @@ def run_ours(a):
         cs.synchronize()
         stream.synchronize()
         t_e2e = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
+        fe_last = h_st[(a.e2e_steps - 1) % 2].numpy().copy()
     else:
         h_spins = torch.empty(spins.numel(), dtype=torch.int8, pin_memory=True)
         h_logq = torch.empty(logq.numel(), dtype=torch.float32, pin_memory=True)
         h_logZR = torch.empty(logZR.numel(), dtype=torch.float64, pin_memory=True)
+        h_st = torch.zeros(n_inst, 8, dtype=torch.float64, pin_memory=True)
+        d_st = torch.empty(n_inst * 8, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(a.e2e_steps):
             step(10 ** 6 + i)
-            fe_last = model.free_energy(B, logZR, logq, stream)  # D2H of the per-instance results (syncs)
+            h_st.copy_(model.step_stats(d_st, stream), non_blocking=True)  # the step's statistics
             h_spins.copy_(spins, non_blocking=True)
             h_logq.copy_(logq, non_blocking=True)
             h_logZR.copy_(logZR, non_blocking=True)
@@ -338,7 +395,9 @@ def run_ours(a):
            "h2d_bytes_per_step": 8 if captured is not None else 8 * n_inst,
            "path": ("model.capture_train_step replays (two buffer sets; read-back of step i beside step i + 1)"
                     if captured is not None else "model.train_step"),
-           "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 32 * n_inst)}
+           "d2h_bytes_per_step": int(spins.numel() + 4 * logq.numel() + 8 * logZR.numel() + 64 * n_inst),
+           "statistics": "F_q, F_IS, stderr, log Z_IS of every step reduced on the device inside the step "
+                         "and read back with its samples"}
 
     # ----- per-kernel durations: the same step with the overlapped side-stream
     # schedule off, so that every kernel's events bracket it alone -----
@@ -376,15 +435,20 @@ def run_ours(a):
     flop_launch = per_sample.get(dom_name, float("nan")) * n_inst * B
     achieved = flop_launch / (dom_ms / dom_n / 1e3) / 1e12 if dom_n else float("nan")
     note = None
+    peaks = measured_peaks()
+    n_sm = props.multi_processor_count
     if dom_name in ("sample_tc", "bwd_fused"):
         # BF16 operands on tcgen05: the tensor roofline (the sampler is bound by its
         # chain of D dependent steps per sample, Eq. 8, far below it)
-        peak, bound, src = MEASURED_BF16_TFLOPS, "tensor", "MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+        peak, bound = peaks["bf16_tflops"], "tensor"
+        src = f"bf16_tflops (burst) from {peaks['source']}"
         if dom_name == "sample_tc":
             note = f"latency-bound: {D} dependent steps per sample; masked MACs counted once"
     else:
-        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        bound, src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+        peak = n_sm * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        bound = "alu"
+        src = (f"derived: {n_sm} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+               f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['source']})")
     roofline = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom_name), "peak_source": src,
                 "flop_per_launch": flop_launch, "ms_per_launch": dom_ms / dom_n}
@@ -422,7 +486,7 @@ def run_ours(a):
                    "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
                    "timing": ("CUDA-graph replay of the whole step (captured once; fresh Philox step per replay "
                               "from a device counter)" if graph else "eager steps"),
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(round(launches_per_step * a.steps)),
         "roofline": roofline, "kernels": kernels,
         "kernels_note": "per-launch CUDA-event times of 3 steps with the overlapped side-stream schedule off",
@@ -515,6 +579,8 @@ def run_ours(a):
             for name in [k for k in accuracy if isinstance(accuracy[k], dict)]:
                 accuracy[name]["abs_F_q_minus_F_exact_per_spin"] = [
                     abs(fq - fe) for fq, fe in zip(accuracy[name]["F_q_per_spin"], f_exact)]
+        # the oracle on sampled rows of one timed-path step per precision
+        out["parity"] = oracle_parity(w, parity_runs, check_stats=world == 1)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -550,6 +616,47 @@ def oracle_step(w, params, offsets, n_b, seed, step):
         est.adam_step(th.numpy(), grad.numpy(), np.zeros(th.numel()), np.zeros(th.numel()), 1)
         done += n_b
     return done
+
+
+def oracle_parity(w, runs, check_stats=True):
+    """Errors of the GPU step against the FP64 oracle, per precision: on the
+    sampled rows of the GPU's own samples, max |delta log q| / N (the oracle's
+    log q on the parameters the step sampled with), max |delta log Z_R| / N and
+    |delta F_q| / N of those rows' mean; over the whole batch, the step's
+    F_q / F_IS / stderr / log Z_IS rows against the oracle's estimators on the
+    GPU's log q and log Z_R (the reduction's own error)."""
+    import numpy as np
+    import torch
+
+    from oracle import estimators as est
+    from oracle import made, transfer
+
+    out = {}
+    for r in runs:
+        e_q = e_z = e_f = e_red = e_lz = 0.0
+        for k, (g, W, beta) in enumerate(zip(w.graphs, w.widths_sets, w.betas)):
+            D = len(W)
+            th = torch.as_tensor(r["params"][r["offsets"][k]:r["offsets"][k + 1]].astype(np.float64))
+            s = torch.as_tensor(r["spins"][k].astype(np.float64))
+            lq_or = made.log_q(th, D, w.hidden, s).numpy()
+            lz_or = transfer.log_zr_lattice(g.n, g.ei, g.ej, g.J, beta, W, s, g.Lx).numpy()
+            lq = r["logq"][k][r["rows"]].astype(np.float64)
+            lz = r["logZR"][k][r["rows"]]
+            e_q = max(e_q, float(np.abs(lq - lq_or).max()) / g.n)
+            e_z = max(e_z, float(np.abs(lz - lz_or).max()) / g.n)
+            e_f = max(e_f, abs(float((lz - lq).mean() - (lz_or - lq_or).mean())) / beta / g.n)
+            if check_stats:
+                fe = est.free_energies(r["logZR"][k], r["logq"][k].astype(np.float64), beta)
+                st = r["stats"][k]
+                e_red = max(e_red, abs(st[0] - fe["F_q"]) / g.n, abs(st[1] - fe["F_IS"]) / g.n)
+                e_lz = max(e_lz, abs(st[3] - fe["logZ_IS"]) / g.n)
+        out[r["precision"]] = {
+            "rows_per_instance": int(len(r["rows"])), "max_abs_dlogq_per_spin": e_q,
+            "max_abs_dlogZR_per_spin": e_z, "abs_dFq_rows_per_spin": e_f,
+            "reduction_max_abs_dF_per_spin": e_red if check_stats else None,
+            "reduction_max_abs_dlogZ_IS_per_spin": e_lz if check_stats else None}
+    out["tolerance_per_spin"] = {"fp32": 1e-6, "reduced_precision": 1e-3}
+    return out
 
 
 def oracle_exact_f(w):

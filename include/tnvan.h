@@ -247,6 +247,54 @@ int tnvan_contract(tnvan_ctx* ctx, const double* betas, int batch, const int8_t*
 int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR,
                       const float* d_logq, double* h_out, void* stream);
 
+/* Eq. 9 statistics of each instance's batch, asynchronous on `stream` (the
+ * device-side counterpart of tnvan_free_energy, capturable in a CUDA graph):
+ * with l_b = log Z_R(s_b) - log q(s_b), one statistics row per instance,
+ *   row[0] F_q = -(1/beta) mean l,   row[1] F_IS = -(1/beta) logZ_IS,
+ *   row[2] stderr = std(l) / (beta sqrt(n)) (ddof 1),
+ *   row[3] logZ_IS = logsumexp l - ln n,   row[4] mean l,
+ *   row[5] number of non-finite l_b (left out of every other entry),
+ *   row[6] var l (ddof 1),   row[7] n = number of finite l_b.
+ * The rows become the context's step statistics: the baseline (row[4]) and
+ * sample count (row[5] + row[7]) of the next tnvan_backward_stats.
+ *   d_stats_out  device double [8 * n_inst] (row k at 8k), or NULL.
+ * Errors: TNVAN_E_ARG (batch < 1, NULL input), TNVAN_E_STATE, TNVAN_E_CUDA. */
+int tnvan_reduce(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR, const float* d_logq,
+                 double* d_stats_out, void* stream);
+
+/* The step statistics of the context (rows as tnvan_reduce) -- written by the
+ * last tnvan_train_step, tnvan_reduce or tnvan_merge_stats queued on the
+ * context -- copied to d_stats_out (device double [8 * n_inst]),
+ * asynchronously on `stream`.  Eq. 9 for the batch a training step drew.
+ * Errors: TNVAN_E_ARG, TNVAN_E_STATE (no instances), TNVAN_E_CUDA. */
+int tnvan_step_stats(tnvan_ctx* ctx, double* d_stats_out, void* stream);
+
+/* Data-parallel exchange (not in the paper; the samples of one batch split
+ * over ranks, SURVEY's one exchange per step): merges the statistics rows of
+ * n_parts disjoint parts of a batch, d_parts = device double
+ * [n_parts][n_inst][8] (each part's tnvan_reduce rows, e.g. gathered from
+ * every rank), into the rows of their union, in part order: counts add,
+ * means and the second central moments by the pairwise update of Chan,
+ * Golub and LeVeque, log sum e^l by logaddexp.  The result becomes the
+ * context's step statistics (so tnvan_backward_stats then uses the global
+ * baseline and batch size) and goes to d_stats_out (device double
+ * [8 * n_inst]) unless NULL.  One part is copied unchanged.  Asynchronous.
+ * Errors: TNVAN_E_ARG (n_parts < 1, NULL d_parts), TNVAN_E_STATE, TNVAN_E_CUDA. */
+int tnvan_merge_stats(tnvan_ctx* ctx, const double* betas, int n_parts, const double* d_parts, double* d_stats_out,
+                      void* stream);
+
+/* Eq. 10 on this process's samples with the baseline and batch size of the
+ * context's step statistics (tnvan_reduce or tnvan_merge_stats):
+ *   grad = sum_{b local} -(l_b - mean) / (beta B) grad_theta log q(s_b),
+ * mean = row[4], B = row[5] + row[7].  With merged statistics, summing grad
+ * over the ranks (an all-reduce) gives tnvan_backward's gradient of the union
+ * batch; with this process's own statistics it is tnvan_backward's gradient.
+ * Arguments as tnvan_backward without the contraction adjoint.
+ * Asynchronous.  Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_CUDA. */
+int tnvan_backward_stats(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                         const double* d_logZR, const float* d_logq, int precision, float* d_grad_params,
+                         void* stream);
+
 /* Observables from one batch (the paper notes that samples of the trained
  * network give magnetisation, correlations and susceptibility, Sec. 3, and
  * leaves correlation functions to future work, Sec. 4): with the
@@ -301,7 +349,9 @@ int tnvan_adam(tnvan_ctx* ctx, int64_t n, float* d_params, const float* d_grad, 
  * (the d_params pointers given to tnvan_set_made, which this call updates in
  * place).  Equal to those calls in sequence, with tnvan_adam run over the
  * packed gradient layout; here the network is packed once for the whole
- * step and the gradient reduction and Adam are one kernel.
+ * step and the gradient reduction and Adam are one kernel.  The step's Eq. 9
+ * statistics (F_q, F_IS, stderr, logZ_IS of the batch it drew; rows as
+ * tnvan_reduce) are reduced inside the step; tnvan_step_stats copies them out.
  *   d_spins, d_logq, d_logZR, d_dbeta, d_dJ   as tnvan_sample_contract_adjoint.
  *   d_grad_params   device float [total params] out, layout of tnvan_n_params.
  *   d_m, d_v        device float [total params] Adam moments in that layout
@@ -375,7 +425,11 @@ int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, doub
  * nothing: it computes, for n_inst instances of `batch` samples each (layout
  * of tnvan_free_energy), on `stream`, asynchronously,
  *   d_out[5k+0..4] = F_q, F_IS, stderr, logZ_IS, number of non-finite l_b
- * (non-finite l_b are left out of the sums instead of failing the call).
+ * in FP64 (a two-pass reduction; its result equals tnvan_free_energy's to
+ * FP64 rounding).  Non-finite l_b are left out of the sums instead of failing
+ * the call, whichever samples they are: the statistics are those of the
+ * finite l_b alone.  Check d_out[5k+4] < batch: when every l_b of an instance
+ * is non-finite, its four statistics are NaN and d_out[5k+4] = batch.
  *   betas    host double [n_inst], finite and > 0 (read during the call).
  *   d_logZR  device double [n_inst*batch]; d_logq device float [n_inst*batch].
  *   d_out    device double [5*n_inst].
@@ -384,10 +438,12 @@ int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, doub
  * n_inst <= 128 (larger counts fail with TNVAN_E_ARG).  All calls on a device
  * share that array: calls whose work may overlap on the GPU (different
  * streams, or different host threads) race and give wrong results; calls on
- * one stream are ordered and safe.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Errors:
- * TNVAN_E_ARG, TNVAN_E_CUDA; message from tnvan_noalloc_last_error(). */
+ * one stream are ordered and safe.  Each call made outside stream capture
+ * looks up the array's device address (cudaGetSymbolAddress, with the
+ * caller's current device) and remembers it for calls made during a
+ * capture, so the first call on each device must come before any stream
+ * capture.  Errors: TNVAN_E_ARG, TNVAN_E_CUDA; message from
+ * tnvan_noalloc_last_error(). */
 int tnvan_free_energy_noalloc(int n_inst, int batch, const double* betas, const double* d_logZR,
                               const float* d_logq, double* d_out, void* stream);
 const char* tnvan_noalloc_last_error(void);

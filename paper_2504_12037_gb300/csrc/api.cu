@@ -562,7 +562,8 @@ struct FusedBwdPlan {
 };
 int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan& p);
 // Backward and Adam of each instance chunk, queued behind that chunk's
-// adjoint and baseline mean (Eq. 10) in the overlapped schedule.
+// adjoint and Eq. 9 reduction (whose mean is Eq. 10's baseline) in the
+// overlapped schedule.
 struct ChunkBackward {
   const FusedBwdPlan* plan;
   float* d_grad;
@@ -1424,8 +1425,9 @@ static int ensure_side_streams(tnvan_ctx* ctx) {
 // launch.
 // With defer_dj the d/dJ reduction runs on a side stream (beside whatever the
 // caller queues next) and the caller waits on ctx->dj_ev before it is done;
-// with chunk_stats each chunk's baseline mean (tnvan_backward's first kernel)
-// follows its adjoint on the chunk's stream.
+// with chunk_stats each chunk's Eq. 9 reduction (F_q, F_IS, stderr, log Z_IS
+// and the baseline of tnvan_backward) follows its adjoint on the chunk's
+// stream.
 // With cb (implies chunk_stats) each chunk's fused backward and gradient
 // reduction with Adam follow too, so a chunk's whole training step runs as
 // soon as its samples exist.
@@ -1475,8 +1477,9 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
        "strip adjoint kernel");
     CK(cudaEventRecord(ctx->adj_ev[c], ctx->side_lo[c]), "adjoint event");
     if (chunk_stats || cb) {
-      PROF("mean", ctx->side_lo[c]);
-      CK(launch_mean(lr, d_logZR, d_logq, ctx->d_stats, ctx->side_lo[c], k0, k1), "mean kernel");
+      PROF("reduce", ctx->side_lo[c]);
+      CK(launch_reduce(ctx->d_inst, lr, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, ctx->side_lo[c], k0, k1),
+         "reduce kernel");
     }
     if (cb) {
       const FusedBwdPlan& fp = *cb->plan;
@@ -1551,8 +1554,8 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
   for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
   if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision) | PACK_FLAT | (all_fused ? PACK_TILES : 0), s)))
     return rc;
-  // the overlapped schedule runs each chunk's baseline mean behind its
-  // adjoint, and the d/dJ reduction (it reads only the adjoint's partial
+  // the overlapped schedule runs each chunk's Eq. 9 reduction (statistics
+  // and the backward's baseline) behind its adjoint, and the d/dJ reduction (it reads only the adjoint's partial
   // rows) beside the backward; the step ends after both.
   // With the fused BF16 backward the chunks' backward and Adam follow their
   // reductions too.
@@ -1678,6 +1681,75 @@ int tnvan_free_energy(tnvan_ctx* ctx, const double* betas, int batch, const doub
   return TNVAN_OK;
 }
 
+int tnvan_reduce(tnvan_ctx* ctx, const double* betas, int batch, const double* d_logZR, const float* d_logq,
+                 double* d_stats_out, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (!d_logZR || !d_logq) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    PROF("reduce", s);
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernel");
+  }
+  if (d_stats_out)
+    CK(cudaMemcpyAsync(d_stats_out, ctx->d_stats, 8 * (size_t)li.n_inst * sizeof(double), cudaMemcpyDeviceToDevice,
+                       s),
+       "statistics copy");
+  return TNVAN_OK;
+}
+
+int tnvan_step_stats(tnvan_ctx* ctx, double* d_stats_out, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (!d_stats_out) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  if (ctx->inst.empty()) return fail(ctx, TNVAN_E_STATE, "no instances");
+  DeviceGuard g(ctx->device);
+  CK(cudaMemcpyAsync(d_stats_out, ctx->d_stats, 8 * ctx->inst.size() * sizeof(double), cudaMemcpyDeviceToDevice,
+                     static_cast<cudaStream_t>(stream)),
+     "statistics copy");
+  return TNVAN_OK;
+}
+
+int tnvan_merge_stats(tnvan_ctx* ctx, const double* betas, int n_parts, const double* d_parts, double* d_stats_out,
+                      void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (n_parts < 1) return fail(ctx, TNVAN_E_ARG, "n_parts must be >= 1");
+  if (!d_parts) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, 1, 1, li))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    PROF("merge_stats", s);
+    CK(launch_merge_stats(li, n_parts, d_parts, ctx->d_stats, s), "merge kernel");
+  }
+  if (d_stats_out)
+    CK(cudaMemcpyAsync(d_stats_out, ctx->d_stats, 8 * (size_t)li.n_inst * sizeof(double), cudaMemcpyDeviceToDevice,
+                       s),
+       "statistics copy");
+  return TNVAN_OK;
+}
+
+int tnvan_backward_stats(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                         const double* d_logZR, const float* d_logq, int precision, float* d_grad_params,
+                         void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (precision < 0 || precision > 2) return fail(ctx, TNVAN_E_ARG, "unknown precision %d", precision);
+  if (!d_spins || !d_logZR || !d_logq || !d_grad_params) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  return backward_impl(ctx, betas, batch, d_spins, d_logZR, d_logq, precision, d_grad_params, nullptr, nullptr,
+                       static_cast<cudaStream_t>(stream), true, nullptr, true);
+}
+
 int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                       const double* d_logZR, const float* d_logq, double* d_corr, double* h_out, void* stream) {
   if (!ctx) return TNVAN_E_ARG;
@@ -1752,8 +1824,8 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
   for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
   if (pack && (rc = pack_network(ctx, PACK_FLAT | (all_fused ? PACK_TILES : 0), s))) return rc;
   if (!stats_ready) {
-    PROF("mean", s);
-    CK(launch_mean(li, d_logZR, d_logq, ctx->d_stats, s), "mean kernel");
+    PROF("reduce", s);
+    CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernel");
   }
   if (all_fused) {
     FusedBwdPlan fp;

@@ -15,6 +15,11 @@ __device__ __forceinline__ int find_inst(const LaunchInfo& li, int blk) {
   return k;
 }
 
+// Samples B of the batch that Eq. 10's weights -(l_b - mean l) / (beta B)
+// divide by, from an instance's statistics row (written by the reduction or
+// by tnvan_merge_stats): the finite l_b ([7]) plus the non-finite ones ([5]).
+__device__ __forceinline__ double stats_batch(const double* st) { return st[7] + st[5]; }
+
 // Philox step of a launch: the host value plus the optional device counter
 // (lets a captured CUDA graph draw new numbers on every replay).
 __device__ __forceinline__ uint32_t launch_step(const LaunchInfo& li) {

@@ -344,13 +344,16 @@ cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int
 // reduces dbeta and wmul to out[3k..3k+2] = U, U_q, effective sample size.
 cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const float* logq, const double* stats,
                                const double* dbeta, float* wmul, double* out, bool energies, cudaStream_t s);
-// The backward's baseline mean_b l_b of instances [k0, k1) into stats[8k + 4].
-cudaError_t launch_mean(const LaunchInfo& li, const double* logZR, const float* logq, double* stats,
-                        cudaStream_t s, int k0 = 0, int k1 = -1);
-// Instances [k0, k1) (k1 < 0: all) of the launch.
+// Eq. 9 statistics of instances [k0, k1) (k1 < 0: all) of the launch into
+// stats[8k + 0..7] = F_q, F_IS, stderr, logZ_IS, mean l, #non-finite, var l,
+// n (the backward's baseline is [4], its sample count [5] + [7]).
 cudaError_t launch_reduce(const InstDev* d_inst, const LaunchInfo& li, const double* logZR,
                           const float* logq, double* stats, int* counters, cudaStream_t s, int k0 = 0,
                           int k1 = -1);
+// Statistics rows of n_parts disjoint parts of a batch ([n_parts][n_inst][8])
+// merged into stats[8k + 0..7] for their union (fixed order).
+cudaError_t launch_merge_stats(const LaunchInfo& li, int n_parts, const double* parts, double* stats,
+                               cudaStream_t s);
 cudaError_t launch_backward(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                             int precision, const int8_t* spins, const double* logZR,
                             const float* logq, const double* stats, float* partials,

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   const uint32_t id_g2 = tc::idesc(128, H1 + 16, 1u) | (1u << 15) | (1u << 16);
   const uint32_t id_g1 = tc::idesc(128, D + 16, 1u) | (1u << 15) | (1u << 16);
   const double mean = args.stats[8 * k + 4];
-  const double wsc = -1.0 / (li.beta[k] * (double)B);
+  const double wsc = -1.0 / (li.beta[k] * stats_batch(args.stats + 8 * k));
   const int8_t* Sg = args.spins + I.spin_units * (long long)B;
   uint32_t phase = 0;
   bool ok = weights_ok;

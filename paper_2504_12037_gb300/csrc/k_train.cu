@@ -7,41 +7,47 @@
 namespace tnvan {
 
 // ---------------------------------------------------------------------------
-// K7: per-instance reduction of l_b = log Z_R(s_b) - log q(s_b) in FP64.
+// K7, two-pass FP64 form (the allocation-free entry point's reduction): per
+// instance, over l_b = log Z_R(s_b) - log q(s_b).
 // Pass 1 (grid n_part x n_inst): each CTA reduces a contiguous chunk to the
-// mergeable tuple (n, sum(l-K), sum((l-K)^2), max l, sum exp(l - max), #bad),
-// K = l_0 of the instance (a shift that keeps the second moment accurate).
+// mergeable tuple (n, mean, M2, max l, sum exp(l - max), #non-finite):
+// Welford's update per sample, the pairwise update of Chan, Golub and
+// LeVeque to merge (no shift taken from any one sample, so a non-finite
+// first sample cannot spoil the sums).
 // Pass 2 (grid n_inst): merges the n_part tuples in order and writes
-//   stats[8k + 0..6] = F_q, F_IS, stderr, logZ_IS, mean l, #non-finite, var l.
+//   stats[8k + 0..7] = F_q, F_IS, stderr, logZ_IS, mean l, #non-finite, var l, n;
+// with no finite l_b every statistic is NaN and n = 0.
+// Non-finite l_b are counted and left out.  FP64 throughout.
 // ---------------------------------------------------------------------------
 struct Tuple {
-  double n, s1, s2, m, se, bad;
+  double n, mean, M2, m, se, bad;
 };
 
 __device__ __forceinline__ Tuple merge(Tuple a, Tuple b) {
+  if (a.n == 0.0) {
+    b.bad += a.bad;
+    return b;
+  }
+  if (b.n == 0.0) {
+    a.bad += b.bad;
+    return a;
+  }
   Tuple r;
   r.n = a.n + b.n;
-  r.s1 = a.s1 + b.s1;
-  r.s2 = a.s2 + b.s2;
+  const double d = b.mean - a.mean;
+  r.mean = a.mean + d * (b.n / r.n);
+  r.M2 = a.M2 + b.M2 + d * d * (a.n * b.n / r.n);
   r.bad = a.bad + b.bad;
-  if (a.se == 0.0) {
-    r.m = b.m;
-    r.se = b.se;
-  } else if (b.se == 0.0) {
-    r.m = a.m;
-    r.se = a.se;
-  } else {
-    r.m = fmax(a.m, b.m);
-    r.se = a.se * (double)expf((float)(a.m - r.m)) + b.se * (double)expf((float)(b.m - r.m));
-  }
+  r.m = fmax(a.m, b.m);
+  r.se = a.se * exp(a.m - r.m) + b.se * exp(b.m - r.m);
   return r;
 }
 
 __device__ __forceinline__ Tuple shfl_tuple(Tuple t, int o) {
   Tuple r;
   r.n = __shfl_xor_sync(0xffffffffu, t.n, o);
-  r.s1 = __shfl_xor_sync(0xffffffffu, t.s1, o);
-  r.s2 = __shfl_xor_sync(0xffffffffu, t.s2, o);
+  r.mean = __shfl_xor_sync(0xffffffffu, t.mean, o);
+  r.M2 = __shfl_xor_sync(0xffffffffu, t.M2, o);
   r.m = __shfl_xor_sync(0xffffffffu, t.m, o);
   r.se = __shfl_xor_sync(0xffffffffu, t.se, o);
   r.bad = __shfl_xor_sync(0xffffffffu, t.bad, o);
@@ -54,7 +60,6 @@ __global__ void __launch_bounds__(256) reduce_part_kernel(const LaunchInfo li, i
                                                           double* __restrict__ part) {
   const int k = blockIdx.y, p = blockIdx.x, B = li.batch;
   const long long base = (long long)k * B;
-  const double K = logZR[base] - (double)logq[base];
   const int chunk = (B + n_part - 1) / n_part;
   const int lo = p * chunk, hi = min(B, lo + chunk);
   Tuple acc = {0, 0, 0, 0, 0, 0};
@@ -64,18 +69,18 @@ __global__ void __launch_bounds__(256) reduce_part_kernel(const LaunchInfo li, i
       acc.bad += 1.0;
       continue;
     }
-    const double d = l - K;
     acc.n += 1.0;
-    acc.s1 += d;
-    acc.s2 += d * d;
-    if (acc.se == 0.0) {
+    const double d = l - acc.mean;
+    acc.mean += d / acc.n;
+    acc.M2 += d * (l - acc.mean);
+    if (acc.n == 1.0) {
       acc.m = l;
       acc.se = 1.0;
     } else if (l > acc.m) {
-      acc.se = acc.se * (double)expf((float)(acc.m - l)) + 1.0;
+      acc.se = acc.se * exp(acc.m - l) + 1.0;
       acc.m = l;
     } else {
-      acc.se += (double)expf((float)(l - acc.m));
+      acc.se += exp(l - acc.m);
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc = merge(acc, shfl_tuple(acc, o));
@@ -87,17 +92,16 @@ __global__ void __launch_bounds__(256) reduce_part_kernel(const LaunchInfo li, i
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = merge(r, red[w]);
     double* o = part + ((long long)k * n_part + p) * 6;
     o[0] = r.n;
-    o[1] = r.s1;
-    o[2] = r.s2;
+    o[1] = r.mean;
+    o[2] = r.M2;
     o[3] = r.m;
     o[4] = r.se;
     o[5] = r.bad;
   }
 }
 
-__global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
-                                    const float* __restrict__ logq,
-                                    const double* __restrict__ part, double* __restrict__ stats) {
+__global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const double* __restrict__ part,
+                                    double* __restrict__ stats) {
   const int k = blockIdx.x;
   if (threadIdx.x != 0) return;
   Tuple r = {0, 0, 0, 0, 0, 0};
@@ -106,31 +110,33 @@ __global__ void reduce_final_kernel(const LaunchInfo li, int n_part, const doubl
     Tuple t = {o[0], o[1], o[2], o[3], o[4], o[5]};
     r = merge(r, t);
   }
-  const long long base = (long long)k * li.batch;
-  const double K = logZR[base] - (double)logq[base];
+  double* s = stats + 8 * k;
+  s[5] = r.bad;
+  s[7] = r.n;
+  if (r.n == 0.0) {  // no finite l_b: nothing to estimate
+    const double nan = __longlong_as_double(0x7FF8000000000000ll);
+    s[0] = s[1] = s[2] = s[3] = s[4] = s[6] = nan;
+    return;
+  }
   const double beta = li.beta[k];
   const double n = r.n;
-  const double mean_d = r.s1 / n;
-  const double var = n > 1.0 ? fmax(r.s2 - r.s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
-  const double mean = K + mean_d;
+  const double var = n > 1.0 ? r.M2 / (n - 1.0) : 0.0;
   const double lz = r.m + log(r.se) - log(n);
-  double* s = stats + 8 * k;
-  s[0] = -mean / beta;
+  s[0] = -r.mean / beta;
   s[1] = -lz / beta;
   s[2] = sqrt(var) / (beta * sqrt(n));
   s[3] = lz;
-  s[4] = mean;
-  s[5] = r.bad;
+  s[4] = r.mean;
   s[6] = var;
-  s[7] = n;
 }
 
 // ---------------------------------------------------------------------------
-// The same reduction in one launch, in float-float arithmetic: FP64 is a
-// narrow unit on this part, so the per-sample sums and the merges carry each
-// value as an unevaluated sum hi + lo of two floats (error-free transforms:
-// Knuth's TwoSum, Dekker's FastTwoSum, the FMA product error), about 48
-// significant bits; only the final statistics are formed in FP64.
+// The same reduction in one launch (the context's form): the moment sums of
+// l - K in float-float arithmetic -- each value an unevaluated sum hi + lo of
+// two floats (error-free transforms: Knuth's TwoSum, Dekker's FastTwoSum, the
+// FMA product error), about 48 significant bits, because FP64 is a narrow
+// unit on this part -- and the logsumexp of the importance weights (log Z_IS)
+// in FP64, about one FP64 exp per sample; the final statistics in FP64.
 // Every CTA reduces its chunk and counts itself done on counters[k]; the
 // last CTA of an instance merges the instance's n_part (<= 64) tuples with
 // one warp -- a fixed tree over the chunk index, so the result does not
@@ -180,9 +186,13 @@ __device__ __forceinline__ FF ff_from_double(double x) {
 }
 __device__ __forceinline__ double ff_to_double(FF x) { return (double)x.hi + (double)x.lo; }
 
+// s1, s2: float-float sums of l - K and (l - K)^2; m, se: the importance
+// weights' running maximum and sum of exp(l - m), in FP64 (Eq. 9's log Z_IS is
+// a logsumexp of the l_b, kept in FP64 throughout).
 struct TupleFF {
   int n, bad;
-  FF s1, s2, m, se;
+  FF s1, s2;
+  double m, se;
 };
 __device__ __forceinline__ TupleFF merge_ff(const TupleFF& a, const TupleFF& b) {
   if (a.n == 0) return TupleFF{b.n, a.bad + b.bad, b.s1, b.s2, b.m, b.se};
@@ -192,9 +202,8 @@ __device__ __forceinline__ TupleFF merge_ff(const TupleFF& a, const TupleFF& b) 
   r.bad = a.bad + b.bad;
   r.s1 = ff_add(a.s1, b.s1);
   r.s2 = ff_add(a.s2, b.s2);
-  r.m = ff_gt(a.m, b.m) ? a.m : b.m;
-  const float ea = expf(ff_add(a.m, ff_neg(r.m)).hi), eb = expf(ff_add(b.m, ff_neg(r.m)).hi);
-  r.se = ff_add(ff_mul(a.se, FF{ea, 0.f}), ff_mul(b.se, FF{eb, 0.f}));
+  r.m = fmax(a.m, b.m);
+  r.se = a.se * exp(a.m - r.m) + b.se * exp(b.m - r.m);
   return r;
 }
 __device__ __forceinline__ FF shfl_ff(FF x, int o) {
@@ -202,21 +211,23 @@ __device__ __forceinline__ FF shfl_ff(FF x, int o) {
 }
 __device__ __forceinline__ TupleFF shfl_tuple_ff(const TupleFF& t, int o) {
   return TupleFF{__shfl_xor_sync(0xffffffffu, t.n, o), __shfl_xor_sync(0xffffffffu, t.bad, o), shfl_ff(t.s1, o),
-                 shfl_ff(t.s2, o), shfl_ff(t.m, o), shfl_ff(t.se, o)};
+                 shfl_ff(t.s2, o), __shfl_xor_sync(0xffffffffu, t.m, o), __shfl_xor_sync(0xffffffffu, t.se, o)};
 }
-// partial tuples as 10 words in a 12-word (6-double) slot
+// partial tuples in a 6-double slot: n, bad, s1, s2 in words 0..5, m and se
+// in doubles 3 and 4
 __device__ __forceinline__ void st_tuple_ff(double* slot, const TupleFF& t) {
   float* f = reinterpret_cast<float*>(slot);
   reinterpret_cast<int*>(f)[0] = t.n;
   reinterpret_cast<int*>(f)[1] = t.bad;
   f[2] = t.s1.hi, f[3] = t.s1.lo, f[4] = t.s2.hi, f[5] = t.s2.lo;
-  f[6] = t.m.hi, f[7] = t.m.lo, f[8] = t.se.hi, f[9] = t.se.lo;
+  slot[3] = t.m;
+  slot[4] = t.se;
 }
 __device__ __forceinline__ TupleFF ld_tuple_ff(const double* slot) {
   const float* f = reinterpret_cast<const float*>(slot);
   const int* q = reinterpret_cast<const int*>(slot);
   return TupleFF{__ldcg(q), __ldcg(q + 1), FF{__ldcg(f + 2), __ldcg(f + 3)}, FF{__ldcg(f + 4), __ldcg(f + 5)},
-                 FF{__ldcg(f + 6), __ldcg(f + 7)}, FF{__ldcg(f + 8), __ldcg(f + 9)}};
+                 __ldcg(slot + 3), __ldcg(slot + 4)};
 }
 
 __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
@@ -225,11 +236,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
                                                      int k0) {
   const int k = blockIdx.y + k0, p = blockIdx.x, B = li.batch;
   const long long base = (long long)k * B;
-  const FF K = ff_add(ff_from_double(logZR[base]), FF{-logq[base], 0.f});
+  // the shift of the moment sums: l_0 when finite (else 0)
+  FF K = ff_add(ff_from_double(logZR[base]), FF{-logq[base], 0.f});
+  if (!isfinite(K.hi) || !isfinite(K.lo)) K = FF{0.f, 0.f};
   const FF negK = ff_neg(K);
   const int chunk = (B + n_part - 1) / n_part;
   const int lo = p * chunk, hi = min(B, lo + chunk);
-  TupleFF acc = {0, 0, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  TupleFF acc = {0, 0, {0.f, 0.f}, {0.f, 0.f}, 0.0, 0.0};
   for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
     const FF l = ff_add(ff_from_double(logZR[base + b]), FF{-logq[base + b], 0.f});
     if (!isfinite(l.hi) || !isfinite(l.lo)) {
@@ -239,14 +252,15 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
     const FF d = ff_add(l, negK);
     acc.s1 = ff_add(acc.s1, d);
     acc.s2 = ff_add(acc.s2, ff_mul(d, d));
+    const double ld = logZR[base + b] - (double)logq[base + b];
     if (acc.n == 0) {
-      acc.m = l;
-      acc.se = FF{1.f, 0.f};
-    } else if (ff_gt(l, acc.m)) {
-      acc.se = ff_add(ff_mul(acc.se, FF{expf(ff_add(acc.m, ff_neg(l)).hi), 0.f}), FF{1.f, 0.f});
-      acc.m = l;
+      acc.m = ld;
+      acc.se = 1.0;
+    } else if (ld > acc.m) {
+      acc.se = acc.se * exp(acc.m - ld) + 1.0;
+      acc.m = ld;
     } else {
-      acc.se = ff_add(acc.se, FF{expf(ff_add(l, ff_neg(acc.m)).hi), 0.f});
+      acc.se += exp(ld - acc.m);
     }
     acc.n += 1;
   }
@@ -257,7 +271,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
   if (l == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {  // the CTA's warps merged by one warp (tree over warp index)
-    TupleFF r = l < nw ? red[l] : TupleFF{0, 0, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    TupleFF r = l < nw ? red[l] : TupleFF{0, 0, {0.f, 0.f}, {0.f, 0.f}, 0.0, 0.0};
     for (int o = 4; o > 0; o >>= 1) r = merge_ff(r, shfl_tuple_ff(r, o));
     if (l == 0) {
       st_tuple_ff(part + ((long long)k * n_part + p) * 6, r);
@@ -268,7 +282,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
   __syncthreads();
   if (!last || threadIdx.x >= 32) return;
   __threadfence();
-  TupleFF r = {0, 0, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  TupleFF r = {0, 0, {0.f, 0.f}, {0.f, 0.f}, 0.0, 0.0};
   if (l < n_part) r = ld_tuple_ff(part + ((long long)k * n_part + l) * 6);
   if (l + 32 < n_part) r = merge_ff(r, ld_tuple_ff(part + ((long long)k * n_part + l + 32) * 6));
   for (int o = 16; o > 0; o >>= 1) r = merge_ff(r, shfl_tuple_ff(r, o));
@@ -279,7 +293,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
   const double mean_d = s1 / n;
   const double var = r.n > 1 ? fmax(s2 - s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
   double f = 0.0;
-  if (l == 1) f = log(ff_to_double(r.se));
+  if (l == 1) f = log(r.se);
   else if (l == 2) f = log(n);
   else if (l == 3) f = sqrt(var);
   else if (l == 4) f = sqrt(n);
@@ -287,7 +301,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
   const double sd = __shfl_sync(0xffffffffu, f, 3), sn = __shfl_sync(0xffffffffu, f, 4);
   if (l != 0) return;
   const double mean = ff_to_double(K) + mean_d;
-  const double lz = ff_to_double(r.m) + lse - ln_n;
+  const double lz = r.m + lse - ln_n;
   double* st = stats + 8 * k;
   st[0] = -mean / beta;
   st[1] = -lz / beta;
@@ -314,69 +328,57 @@ cudaError_t launch_reduce(const InstDev*, const LaunchInfo& li, const double* lo
   return cudaGetLastError();
 }
 
-// The backward's baseline alone (Eq. 10): stats[8k + 4] = mean_b l_b over the
-// finite l_b and stats[8k + 7] their count, one 1024-thread CTA per instance
-// of [k0, k0 + gridDim.x): float-float sums of l_b - l_0 (eight loads in
-// flight per thread, then the sums in sample order), an xor tree per warp,
-// the warps in order -- a fixed order, so the result does not depend on the
-// launch.  The training path needs only this; tnvan_free_energy keeps the
-// full reduction.
-__global__ void __launch_bounds__(1024) mean_kernel(const LaunchInfo li, const double* __restrict__ logZR,
-                                                    const float* __restrict__ logq, double* __restrict__ stats,
-                                                    int k0) {
-  const int k = blockIdx.x + k0, B = li.batch, tid = threadIdx.x;
-  const double* lz = logZR + (long long)k * B;
-  const float* lq = logq + (long long)k * B;
-  const FF K = ff_add(ff_from_double(lz[0]), FF{-lq[0], 0.f});
-  const FF negK = ff_neg(K);
-  FF s1{0.f, 0.f};
-  int nn = 0;
-  for (int b0 = tid; b0 < B; b0 += 1024 * 8) {
-    double z[8];
-    float q[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int b = b0 + 1024 * j;
-      z[j] = b < B ? lz[b] : 0.0;
-      q[j] = b < B ? lq[b] : 0.f;
+// Merge of Eq. 9 statistics rows computed on disjoint parts of one batch
+// (data-parallel ranks), parts[(p * n_inst + k) * 8 + 0..7] in the layout of
+// the reduction, into stats[8k + 0..7] for the union of the parts.  Each row
+// is taken as the mergeable tuple (n, mean l, M2 = var (n - 1), log sum e^l =
+// logZ_IS + ln n) and the parts are combined in index order by the pairwise
+// update of Chan, Golub and LeVeque (1979) for the mean and M2 and a
+// logaddexp for the log-sum; one thread per instance, so the result does not
+// depend on the launch.  One part is copied unchanged.
+__global__ void merge_stats_kernel(const LaunchInfo li, int n_parts, const double* __restrict__ parts,
+                                   double* __restrict__ stats) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= li.n_inst) return;
+  const double* p0 = parts + 8 * k;
+  double* st = stats + 8 * k;
+  if (n_parts == 1) {
+    for (int j = 0; j < 8; ++j) st[j] = p0[j];
+    return;
+  }
+  double n = 0.0, mean = 0.0, M2 = 0.0, lse = 0.0, bad = 0.0;
+  for (int p = 0; p < n_parts; ++p) {
+    const double* q = parts + ((long long)p * li.n_inst + k) * 8;
+    const double nb = q[7];
+    bad += q[5];
+    if (!(nb > 0.0)) continue;
+    const double mb = q[4], M2b = nb > 1.0 ? q[6] * (nb - 1.0) : 0.0, lb = q[3] + log(nb);
+    if (n == 0.0) {
+      n = nb, mean = mb, M2 = M2b, lse = lb;
+      continue;
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (b0 + 1024 * j >= B) break;
-      const FF l = ff_add(ff_from_double(z[j]), FF{-q[j], 0.f});
-      if (!isfinite(l.hi) || !isfinite(l.lo)) continue;
-      s1 = ff_add(s1, ff_add(l, negK));
-      ++nn;
-    }
+    const double N = n + nb, d = mb - mean;
+    mean += d * (nb / N);
+    M2 += M2b + d * d * (n * nb / N);
+    lse = fmax(lse, lb) + log1p(exp(-fabs(lse - lb)));
+    n = N;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    s1 = ff_add(s1, shfl_ff(s1, o));
-    nn += __shfl_xor_sync(0xffffffffu, nn, o);
-  }
-  __shared__ FF red_s[32];
-  __shared__ int red_n[32];
-  if ((tid & 31) == 0) {
-    red_s[tid >> 5] = s1;
-    red_n[tid >> 5] = nn;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    FF S = red_s[0];
-    int N = red_n[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      S = ff_add(S, red_s[w]);
-      N += red_n[w];
-    }
-    stats[8 * k + 4] = ff_to_double(K) + ff_to_double(S) / (double)N;
-    stats[8 * k + 7] = (double)N;
-  }
+  const double beta = li.beta[k];
+  const double var = n > 1.0 ? M2 / (n - 1.0) : 0.0;
+  const double lz = lse - log(n);
+  st[0] = -mean / beta;
+  st[1] = -lz / beta;
+  st[2] = sqrt(var) / (beta * sqrt(n));
+  st[3] = lz;
+  st[4] = mean;
+  st[5] = bad;
+  st[6] = var;
+  st[7] = n;
 }
 
-cudaError_t launch_mean(const LaunchInfo& li, const double* logZR, const float* logq, double* stats,
-                        cudaStream_t s, int k0, int k1) {
-  if (k1 < 0) k1 = li.n_inst;
-  if (k1 <= k0 || li.batch < 1) return cudaSuccess;
-  mean_kernel<<<k1 - k0, 1024, 0, s>>>(li, logZR, logq, stats, k0);
+cudaError_t launch_merge_stats(const LaunchInfo& li, int n_parts, const double* parts, double* stats,
+                               cudaStream_t s) {
+  merge_stats_kernel<<<(li.n_inst + 127) / 128, 128, 0, s>>>(li, n_parts, parts, stats);
   return cudaGetLastError();
 }
 
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const InstDev* __restrict
   const int* cL = nh == 1 ? md.c1 : md.c2;
   const double mean = stats[8 * k + 4];
   const double beta = li.beta[k];
-  const double wscale = -1.0 / (beta * (double)li.batch);
+  const double wscale = -1.0 / (beta * stats_batch(stats + 8 * k));
   float* Gk = partials + (long long)blockIdx.x * part_stride;
   const int8_t* sp = spins + I.spin_units * li.batch;
   bool first = true;
@@ -742,7 +744,7 @@ __global__ void reinforce_w_kernel(const LaunchInfo li, const double* __restrict
                                    float* __restrict__ w) {
   const int k = blockIdx.y;
   const double mean = stats[8 * k + 4];
-  const double sc = -1.0 / (li.beta[k] * (double)li.batch);
+  const double sc = -1.0 / (li.beta[k] * stats_batch(stats + 8 * k));
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < li.batch; b += gridDim.x * blockDim.x) {
     const long long o = (long long)k * li.batch + b;
     w[o] = (float)(sc * (logZR[o] - (double)logq[o] - mean));

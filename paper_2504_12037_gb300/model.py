@@ -69,6 +69,13 @@ class TNVAN:
         """[n_inst, 4]: F_q, F_IS, stderr, logZ_IS (per instance, not per spin)."""
         return self.ctx.free_energy(self.betas, batch, logZR, logq, stream)
 
+    def step_stats(self, out=None, stream=None) -> torch.Tensor:
+        """Device [n_inst, 8] Eq. 9 rows of the last training step (F_q, F_IS,
+        stderr, logZ_IS, mean l, #non-finite, var l, n), queued on `stream`."""
+        out = torch.empty(8 * self.n, dtype=torch.float64, device=self.device) if out is None else out
+        self.ctx.step_stats(out, stream)
+        return out.view(self.n, 8)
+
     def train_step(self, batch: int, seed: int, step: int, precision: int = tv.FP32, lr: float = 0.01,
                    out=None, dbeta=None, dJ=None, stream=None):
         """One iteration of Algorithm 1: sample, contract, gradient, Adam, in one
@@ -100,8 +107,10 @@ class CapturedStep:
     Each replay() runs the whole step on the device with no host work: the
     Philox step of the sampler and Adam's t advance through a device counter
     (tnvan_set_step_counter), so every replay draws fresh samples into the
-    same buffers (`out`, `dbeta`, `dJ`).  Construction takes one eager step
-    (workspaces and launch plans settle) before capturing."""
+    same buffers (`out`, `dbeta`, `dJ`) and leaves the step's Eq. 9 rows
+    (F_q, F_IS, stderr, logZ_IS, ...) in `stats` [n_inst, 8].  Construction
+    takes one eager step (workspaces and launch plans settle) before
+    capturing."""
 
     def __init__(self, model: "TNVAN", batch: int, seed: int, precision: int = tv.FP32, lr: float = 0.01,
                  out=None, dbeta=None, dJ=None):
@@ -109,6 +118,7 @@ class CapturedStep:
         self.out = out if out is not None else model.buffers(batch)
         self.dbeta, self.dJ = dbeta, dJ
         self.counter = torch.zeros(1, dtype=torch.int64, device=model.device)
+        self.stats = torch.zeros(model.n, 8, dtype=torch.float64, device=model.device)
         self.stream = torch.cuda.Stream(device=model.device)
         self.stream.wait_stream(torch.cuda.current_stream(model.device))
         model.ctx.reserve(batch)
@@ -120,6 +130,7 @@ class CapturedStep:
         t0 = model.t
         with torch.cuda.graph(self.graph, stream=self.stream):
             model.train_step(batch, seed, 1, precision, lr, self.out, dbeta, dJ, self.stream)
+            model.ctx.step_stats(self.stats, self.stream)
             self.counter.add_(1)
         model.t = t0  # the graph's step is t0 + 1 + counter
         model.ctx.set_step_counter(None)

@@ -50,6 +50,10 @@ SIGNATURES = {
     "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp]),
     "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
+    "tnvan_reduce": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _vp]),
+    "tnvan_step_stats": (_c_int, [_vp, _vp, _vp]),
+    "tnvan_merge_stats": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp]),
+    "tnvan_backward_stats": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp]),
     "tnvan_backward": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]),
     "tnvan_adam": (_c_int, [_vp, _c_i64, _vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "tnvan_free_energy_noalloc": (_c_int, [_c_int, _c_int, _dblp, _vp, _vp, _vp, _vp]),
@@ -236,6 +240,28 @@ class Context:
         self._check(lib().tnvan_free_energy(self._h, pb, batch, _ptr(logZR), _ptr(logq),
                                             out.ctypes.data_as(_dblp), _stream(stream)))
         return out.reshape(len(b), 4)
+
+    def reduce(self, betas, batch: int, logZR, logq, stats_out=None, stream=None):
+        """Eq. 9 rows [8 per instance] into the context (and stats_out), async."""
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_reduce(self._h, pb, batch, _ptr(logZR), _ptr(logq), _ptr(stats_out),
+                                       _stream(stream)))
+
+    def step_stats(self, stats_out, stream=None):
+        """The context's step statistics (last training step, reduce or merge) into stats_out."""
+        self._check(lib().tnvan_step_stats(self._h, _ptr(stats_out), _stream(stream)))
+
+    def merge_stats(self, betas, parts, stats_out=None, stream=None):
+        """Statistics rows of disjoint parts [n_parts, n_inst * 8] merged into the context's."""
+        b, pb = _arr(betas, np.float64)
+        n_parts = parts.shape[0] if parts.dim() > 1 else parts.numel() // (8 * len(b))
+        self._check(lib().tnvan_merge_stats(self._h, pb, n_parts, _ptr(parts), _ptr(stats_out), _stream(stream)))
+
+    def backward_stats(self, betas, batch: int, spins, logZR, logq, precision: int, grad, stream=None):
+        """Eq. 10 with the baseline and batch size of the context's step statistics."""
+        b, pb = _arr(betas, np.float64)
+        self._check(lib().tnvan_backward_stats(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq),
+                                               precision, _ptr(grad), _stream(stream)))
 
     def backward(self, betas, batch: int, spins, logZR, logq, precision: int, grad, dlogZR_dbeta=None,
                  dlogZR_dJ=None, stream=None):
