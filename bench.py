@@ -80,6 +80,9 @@ def args_():
     ap.add_argument("--planned", action="store_true",
                     help="also time the training step on random regular graphs (n = 1000, d = 3) whose width "
                          "sets come from the width-set finder")
+    ap.add_argument("--ferro40", type=int, default=0, metavar="STEPS",
+                    help="also train the 40x40 open ferromagnet (W = every 5th column) at T = 1, 2, T_c, 3, 4, 5 "
+                         "for STEPS Adam steps and report |F - F_exact| / |F_exact| against the Kac-Ward value")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the captured step over per-instance batches 2^8 .. 2^18 (the asymptote)")
     return ap.parse_args()
@@ -570,6 +573,26 @@ def run_ours(a):
                             "batch": Bp * world, "ms_per_step": t_ms, "value": Bp * world / (t_ms / 1e3)})
             del cap, mp
         out["planned_rrg_n1000_d3"] = planned
+    ferro = None
+    if a.ferro40 > 0:
+        # the paper's first experiment (Sec. 4, Fig. 2): training steps in FP32,
+        # then F_q and F_IS from one large batch per temperature
+        wf = wl.ferromagnet_columns()
+        mf = TNVAN(wf.graphs, wf.widths_sets, wf.hidden, wf.betas, device=local, seed=1000 * rank + 9)
+        bf = mf.buffers(wf.batch)
+        t0 = time.time()
+        for i in range(a.ferro40):
+            mf.train_step(wf.batch, 40 + rank, i, tv.FP32, 0.01, bf, None, None, stream)
+        torch.cuda.synchronize()
+        t_train = time.time() - t0
+        Bf = 16384
+        spf, lqf, lzf = mf.sample(Bf, 4040 + rank, 10 ** 7, tv.FP32)
+        fe = mf.free_energy(Bf, lzf, lqf)
+        N = wf.graphs[0].n
+        ferro = {"workload": wf.name, "train_steps": a.ferro40, "train_batch": wf.batch, "made": wf.hidden,
+                 "train_s": t_train, "eval_batch": Bf, "T": [1.0 / b for b in wf.betas],
+                 "F_q_per_spin": [float(x) / N for x in fe[:, 0]], "F_IS_per_spin": [float(x) / N for x in fe[:, 1]],
+                 "stderr_per_spin": [float(x) / N for x in fe[:, 2]]}
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
         # the oracle's exact free energy of the lattice (single-site transfer matrix, 2^16 states)
@@ -581,6 +604,10 @@ def run_ours(a):
                     abs(fq - fe) for fq, fe in zip(accuracy[name]["F_q_per_spin"], f_exact)]
         # the oracle on sampled rows of one timed-path step per precision
         out["parity"] = oracle_parity(w, parity_runs, check_stats=world == 1)
+        if ferro is not None:
+            ferro.update(oracle_ferro_exact(wl.ferromagnet_columns(), ferro))
+    if ferro is not None:
+        out["ferromagnet_40x40"] = ferro
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -657,6 +684,18 @@ def oracle_parity(w, runs, check_stats=True):
             "reduction_max_abs_dlogZ_IS_per_spin": e_lz if check_stats else None}
     out["tolerance_per_spin"] = {"fp32": 1e-6, "reduced_precision": 1e-3}
     return out
+
+
+def oracle_ferro_exact(wf, ferro):
+    """Exact F / N of the open ferromagnet at each temperature (the oracle's
+    Kac-Ward determinant) and the relative errors of the trained F_q and F_IS."""
+    from oracle import kacward
+
+    g = wf.graphs[0]
+    f_ex = [-kacward.log_z_kac_ward(g.Lx, g.Ly, g.ei, g.ej, g.J, b) / b / g.n for b in wf.betas]
+    return {"F_exact_per_spin": f_ex, "exact": "Kac-Ward determinant (oracle, FP64)",
+            "rel_err_F_q": [abs(f - e) / abs(e) for f, e in zip(ferro["F_q_per_spin"], f_ex)],
+            "rel_err_F_IS": [abs(f - e) / abs(e) for f, e in zip(ferro["F_IS_per_spin"], f_ex)]}
 
 
 def oracle_exact_f(w):

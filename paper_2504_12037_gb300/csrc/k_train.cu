@@ -186,32 +186,16 @@ __device__ __forceinline__ FF ff_from_double(double x) {
 }
 __device__ __forceinline__ double ff_to_double(FF x) { return (double)x.hi + (double)x.lo; }
 
-// s1, s2: float-float sums of l - K and (l - K)^2; m, se: the importance
-// weights' running maximum and sum of exp(l - m), in FP64 (Eq. 9's log Z_IS is
-// a logsumexp of the l_b, kept in FP64 throughout).
+// s1, s2: float-float sums of l - K and (l - K)^2; m, se: the maximum of the
+// importance weights' logs and the sum of exp(l - m), in FP64 (Eq. 9's log Z_IS
+// is a logsumexp of the l_b, kept in FP64 throughout).
 struct TupleFF {
   int n, bad;
   FF s1, s2;
   double m, se;
 };
-__device__ __forceinline__ TupleFF merge_ff(const TupleFF& a, const TupleFF& b) {
-  if (a.n == 0) return TupleFF{b.n, a.bad + b.bad, b.s1, b.s2, b.m, b.se};
-  if (b.n == 0) return TupleFF{a.n, a.bad + b.bad, a.s1, a.s2, a.m, a.se};
-  TupleFF r;
-  r.n = a.n + b.n;
-  r.bad = a.bad + b.bad;
-  r.s1 = ff_add(a.s1, b.s1);
-  r.s2 = ff_add(a.s2, b.s2);
-  r.m = fmax(a.m, b.m);
-  r.se = a.se * exp(a.m - r.m) + b.se * exp(b.m - r.m);
-  return r;
-}
 __device__ __forceinline__ FF shfl_ff(FF x, int o) {
   return FF{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
-}
-__device__ __forceinline__ TupleFF shfl_tuple_ff(const TupleFF& t, int o) {
-  return TupleFF{__shfl_xor_sync(0xffffffffu, t.n, o), __shfl_xor_sync(0xffffffffu, t.bad, o), shfl_ff(t.s1, o),
-                 shfl_ff(t.s2, o), __shfl_xor_sync(0xffffffffu, t.m, o), __shfl_xor_sync(0xffffffffu, t.se, o)};
 }
 // partial tuples in a 6-double slot: n, bad, s1, s2 in words 0..5, m and se
 // in doubles 3 and 4
@@ -229,7 +213,26 @@ __device__ __forceinline__ TupleFF ld_tuple_ff(const double* slot) {
   return TupleFF{__ldcg(q), __ldcg(q + 1), FF{__ldcg(f + 2), __ldcg(f + 3)}, FF{__ldcg(f + 4), __ldcg(f + 5)},
                  __ldcg(slot + 3), __ldcg(slot + 4)};
 }
+// Block-wide reductions over the 256 threads (8 warps); `red` holds 8 values.
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red[0];
+  for (int w = 1; w < 8; ++w) r = fmax(r, red[w]);
+  __syncthreads();
+  return r;
+}
 
+// Each CTA reduces a chunk in two passes over its samples: the chunk's
+// largest l first (compares only), then per sample one FP64 exp(l - max) and
+// the float-float moment sums; the CTA's warps are summed in a fixed order.
+// The last CTA of an instance rescales the n_part (<= 64) chunk sums to the
+// instance's largest l, one FP64 exp per chunk in parallel lanes, and adds
+// them in a fixed tree, so the result does not depend on which CTA finishes
+// last.  Only two exps lie on any thread's path: FP64 is a narrow unit on
+// this part, and a running maximum with a rescale at every merge would put
+// one exp per merge level on the critical path.
 __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_part, const double* __restrict__ logZR,
                                                      const float* __restrict__ logq, double* __restrict__ part,
                                                      double* __restrict__ stats, int* __restrict__ counters,
@@ -242,58 +245,83 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
   const FF negK = ff_neg(K);
   const int chunk = (B + n_part - 1) / n_part;
   const int lo = p * chunk, hi = min(B, lo + chunk);
-  TupleFF acc = {0, 0, {0.f, 0.f}, {0.f, 0.f}, 0.0, 0.0};
+  __shared__ double redd[8];
+  __shared__ TupleFF red[8];
+  __shared__ int last;
+  // pass 1: the chunk's largest finite l
+  double mx = -INFINITY;
   for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
-    const FF l = ff_add(ff_from_double(logZR[base + b]), FF{-logq[base + b], 0.f});
-    if (!isfinite(l.hi) || !isfinite(l.lo)) {
+    const double ld = logZR[base + b] - (double)logq[base + b];
+    if (isfinite(ld)) mx = fmax(mx, ld);
+  }
+  mx = block_max(mx, redd);
+  // pass 2: exp sums against that maximum, moment sums, counts
+  TupleFF acc = {0, 0, {0.f, 0.f}, {0.f, 0.f}, mx, 0.0};
+  for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+    const double z = logZR[base + b];
+    const float q = logq[base + b];
+    const double ld = z - (double)q;
+    if (!isfinite(ld)) {
       acc.bad += 1;
       continue;
     }
-    const FF d = ff_add(l, negK);
+    const FF d = ff_add(ff_add(ff_from_double(z), FF{-q, 0.f}), negK);
     acc.s1 = ff_add(acc.s1, d);
     acc.s2 = ff_add(acc.s2, ff_mul(d, d));
-    const double ld = logZR[base + b] - (double)logq[base + b];
-    if (acc.n == 0) {
-      acc.m = ld;
-      acc.se = 1.0;
-    } else if (ld > acc.m) {
-      acc.se = acc.se * exp(acc.m - ld) + 1.0;
-      acc.m = ld;
-    } else {
-      acc.se += exp(ld - acc.m);
-    }
+    acc.se += exp(ld - mx);
     acc.n += 1;
   }
-  for (int o = 16; o > 0; o >>= 1) acc = merge_ff(acc, shfl_tuple_ff(acc, o));
-  __shared__ TupleFF red[8];
-  __shared__ int last;
-  const int l = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.n += __shfl_xor_sync(0xffffffffu, acc.n, o);
+    acc.bad += __shfl_xor_sync(0xffffffffu, acc.bad, o);
+    acc.s1 = ff_add(acc.s1, shfl_ff(acc.s1, o));
+    acc.s2 = ff_add(acc.s2, shfl_ff(acc.s2, o));
+    acc.se += __shfl_xor_sync(0xffffffffu, acc.se, o);
+  }
+  const int l = threadIdx.x & 31;
   if (l == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x < 32) {  // the CTA's warps merged by one warp (tree over warp index)
-    TupleFF r = l < nw ? red[l] : TupleFF{0, 0, {0.f, 0.f}, {0.f, 0.f}, 0.0, 0.0};
-    for (int o = 4; o > 0; o >>= 1) r = merge_ff(r, shfl_tuple_ff(r, o));
-    if (l == 0) {
-      st_tuple_ff(part + ((long long)k * n_part + p) * 6, r);
-      __threadfence();
-      last = atomicAdd(counters + k, 1) == n_part - 1;
+  if (threadIdx.x == 0) {  // the CTA's warps in order
+    TupleFF r = red[0];
+    for (int w = 1; w < 8; ++w) {
+      r.n += red[w].n;
+      r.bad += red[w].bad;
+      r.s1 = ff_add(r.s1, red[w].s1);
+      r.s2 = ff_add(r.s2, red[w].s2);
+      r.se += red[w].se;
     }
+    st_tuple_ff(part + ((long long)k * n_part + p) * 6, r);
+    __threadfence();
+    last = atomicAdd(counters + k, 1) == n_part - 1;
   }
   __syncthreads();
   if (!last || threadIdx.x >= 32) return;
   __threadfence();
-  TupleFF r = {0, 0, {0.f, 0.f}, {0.f, 0.f}, 0.0, 0.0};
+  // the instance's chunks: lane l holds chunks l and l + 32
+  TupleFF r = {0, 0, {0.f, 0.f}, {0.f, 0.f}, -INFINITY, 0.0};
+  TupleFF r2 = r;
   if (l < n_part) r = ld_tuple_ff(part + ((long long)k * n_part + l) * 6);
-  if (l + 32 < n_part) r = merge_ff(r, ld_tuple_ff(part + ((long long)k * n_part + l + 32) * 6));
-  for (int o = 16; o > 0; o >>= 1) r = merge_ff(r, shfl_tuple_ff(r, o));
+  if (l + 32 < n_part) r2 = ld_tuple_ff(part + ((long long)k * n_part + l + 32) * 6);
+  double M = fmax(r.n ? r.m : -INFINITY, r2.n ? r2.m : -INFINITY);
+  for (int o = 16; o > 0; o >>= 1) M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
+  double se = (r.n ? r.se * exp(r.m - M) : 0.0) + (r2.n ? r2.se * exp(r2.m - M) : 0.0);
+  int n_ = r.n + r2.n, bad_ = r.bad + r2.bad;
+  FF s1 = ff_add(r.s1, r2.s1), s2 = ff_add(r.s2, r2.s2);
+  for (int o = 16; o > 0; o >>= 1) {
+    n_ += __shfl_xor_sync(0xffffffffu, n_, o);
+    bad_ += __shfl_xor_sync(0xffffffffu, bad_, o);
+    s1 = ff_add(s1, shfl_ff(s1, o));
+    s2 = ff_add(s2, shfl_ff(s2, o));
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+  }
   // FP64 statistics; the transcendental tails in parallel lanes
   const double beta = li.beta[k];
-  const double n = (double)r.n;
-  const double s1 = ff_to_double(r.s1), s2 = ff_to_double(r.s2);
-  const double mean_d = s1 / n;
-  const double var = r.n > 1 ? fmax(s2 - s1 * mean_d, 0.0) / (n - 1.0) : 0.0;
+  const double n = (double)n_;
+  const double s1d = ff_to_double(s1), s2d = ff_to_double(s2);
+  const double mean_d = s1d / n;
+  const double var = n_ > 1 ? fmax(s2d - s1d * mean_d, 0.0) / (n - 1.0) : 0.0;
   double f = 0.0;
-  if (l == 1) f = log(r.se);
+  if (l == 1) f = log(se);
   else if (l == 2) f = log(n);
   else if (l == 3) f = sqrt(var);
   else if (l == 4) f = sqrt(n);
@@ -301,14 +329,14 @@ __global__ void __launch_bounds__(256) reduce_kernel(const LaunchInfo li, int n_
   const double sd = __shfl_sync(0xffffffffu, f, 3), sn = __shfl_sync(0xffffffffu, f, 4);
   if (l != 0) return;
   const double mean = ff_to_double(K) + mean_d;
-  const double lz = r.m + lse - ln_n;
+  const double lz = M + lse - ln_n;
   double* st = stats + 8 * k;
   st[0] = -mean / beta;
   st[1] = -lz / beta;
   st[2] = sd / (beta * sn);
   st[3] = lz;
   st[4] = mean;
-  st[5] = (double)r.bad;
+  st[5] = (double)bad_;
   st[6] = var;
   st[7] = n;
   counters[k] = 0;

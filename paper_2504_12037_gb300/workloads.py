@@ -287,6 +287,20 @@ def workload(config: int, n_instances: Optional[int] = None) -> Workload:
     raise ValueError(f"unknown workload {config}")
 
 
+def ferromagnet_columns(L: int = 40, period: int = 5, hidden: Sequence[int] = (256, 256),
+                        batch: int = 1000) -> Workload:
+    """The paper's first experiment (Sec. 4, Fig. 2): the open L x L
+    ferromagnet (J = 1) at T = 1, 2, T_c, 3, 4, 5 (T_c = 2 / ln(1 + sqrt 2),
+    Onsager's critical temperature), one instance per temperature; W = every
+    `period`-th column (columns c with c % period == period - 1), which leaves
+    strips of period - 1 columns."""
+    g = lattice(L, L, "ferro", 0)
+    W = width_columns(L, L, every_kth_column(L, period))
+    temps = [1.0, 2.0, 2.0 / np.log(1.0 + np.sqrt(2.0)), 3.0, 4.0, 5.0]
+    return Workload(f"ferro_{L}x{L}_open_every{period}th_col", [g] * len(temps), [W] * len(temps), list(hidden),
+                    batch, [float(1.0 / T) for T in temps])
+
+
 # ---------------------------------------------------------------------------
 # Network parameters (seeded initial values; layout of the C-ABI: per layer
 # W [out][in] row-major, then b [out]).
