@@ -393,7 +393,7 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
  * default).  Lets a caller reuse an earlier tuning without re-timing.  Not in
  * the paper.
  * Errors: TNVAN_E_ARG (NULL, or a value outside the candidates the autotuner
- * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {4,6,8}, {1,2}). */
+ * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {8,16,32}, {1,2}). */
 int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* choices);
 
 /* Optional device step counter (not in the paper; for CUDA-graph capture).

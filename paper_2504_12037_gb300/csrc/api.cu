@@ -548,6 +548,9 @@ int sampler_pack_mask(const tnvan_ctx* ctx, int precision);
 int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, uint64_t step, int precision,
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s);
 int pick_tc_plan(const tnvan_ctx* ctx);
+// Every instance has a tensor-core sampler plan and all share one number of
+// hidden layers (one kernel instantiation per launch).
+bool tc_sampler_usable(const tnvan_ctx* ctx);
 int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, const double* d_logZR,
                   const float* d_logq, int precision, float* d_grad_params, double* d_dbeta, double* d_dJ,
                   cudaStream_t s, bool pack, const AdamArgs* adam, bool stats_ready = false);
@@ -1155,75 +1158,123 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     md.blk_src = dsrc;
     md.n_blk = (long long)src.size();
   }
-  // Step groups of the tensor-core sampler, one plan per group-size limit
-  // (kTcGroupMax; the autotuner picks one): at most that many steps and 32
-  // units of each hidden layer completing inside a group.  Per group the
-  // in-group triangles and the group's biases, each row padded to a multiple
-  // of 4 floats, and a record of TNVAN_TCG_INTS ints (bounds, offsets and the
-  // per-step unit counts) that the kernel bulk-copies one group ahead.
-  for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
-    MadeDev::TcPlan& P = md.tc[p];
-    P = MadeDev::TcPlan{};
-    if (!md.wtiles || n_hidden != 2) continue;
-    const int GMAX = kTcGroupMax[p], UGMAX = 32;
-    auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
-    auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
-    std::vector<int> grp, src;
-    int twmax = 0, tcw1 = 16, tcw2 = 16;
-    bool fits = true;
-    auto add_tile = [&](int rlo, int rhi, int clo, int chi, long long wofs, int stride) {
-      const int off = (int)src.size();
-      const int rw = (chi - clo + 3) & ~3;
-      for (int r = rlo; r < rhi; ++r)
-        for (int c = 0; c < rw; ++c) src.push_back(c < chi - clo ? (int)(wofs + (long long)r * stride + clo + c) : -1);
-      return off;
-    };
-    for (int i0 = 0; i0 < D;) {
-      int i1 = i0 + 1;
-      while (i1 < D && i1 - i0 < GMAX && cnt(c1, i0, i1 + 1) <= UGMAX && cnt(c2, i0, i1 + 1) <= UGMAX) ++i1;
-      const int u1lo = before(c1, i0), u1hi = before(c1, i1);
-      const int u2lo = before(c2, i0), u2hi = before(c2, i1);
-      fits = fits && u1hi - u1lo <= UGMAX && u2hi - u2lo <= UGMAX;
-      const int gstart = (int)src.size();
-      add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
-      const int t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
-      const int to = add_tile(i0, i1, u2lo, u2hi, md.layer[2].dst_off, H[1]);
-      // the group's biases (gathered with the triangles)
-      const int b1o = add_tile(0, 1, u1lo, u1hi, md.layer[0].dst_off + (long long)H[0] * D, 0);
-      const int b2o = add_tile(0, 1, u2lo, u2hi, md.layer[1].dst_off + (long long)H[1] * H[0], 0);
-      const int boo = add_tile(0, 1, i0, i1, md.layer[2].dst_off + (long long)D * H[1], 0);
-      const int gsize = (int)src.size() - gstart;
-      twmax = std::max(twmax, gsize);
-      tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
-      tcw2 = std::max(tcw2, ((u2hi + 15) & ~15) - (u2lo & ~15));
-      int rec[TNVAN_TCG_INTS] = {i0, i1, u1lo, u1hi, u2lo, u2hi, gstart, gsize, t2 - gstart, to - gstart,
-                                 b1o - gstart, b2o - gstart, boo - gstart};
-      for (int q = 0; q <= i1 - i0; ++q) {  // units with degree < i0 + q
-        rec[13 + q] = before(c1, i0 + q);
-        rec[22 + q] = before(c2, i0 + q);
+  // Step chunks of the tensor-core sampler, one plan per chunk-size limit
+  // (kTcGroupMax; the autotuner picks one): at most that many steps and 64
+  // layer-1 units completing inside a chunk.  Per chunk a record of
+  // TNVAN_TCG_INTS ints and one BF16 weight blob of three parts, each in the
+  // MMA's K-major canonical layout (core matrices of 8 rows x 16 bytes):
+  //   A  W2's columns [w1c, w1c + n1c) for every layer-2 row: n1c / 16 slabs of
+  //      [H2 rows][16], element (r, kk) at (r >> 3) * 128 + (kk >> 3) * 64 +
+  //      (r & 7) * 8 + (kk & 7) within its slab (two hidden layers only);
+  //   B  Wo's columns over the chunk's last-layer units, [Dp rows][16] slabs;
+  //   C  W1's rows [w1c, w1c + n1c) over the spins 0 .. kSc-1, row groups of
+  //      8: element (r, k) at (r >> 3) * 8 kSc + (k >> 3) * 64 + (r & 7) * 8 + (k & 7).
+  // Rows past the network (outputs >= D, spins >= D) are zero.
+  {
+    const int Dp = (D + 15) & ~15;
+    const bool shape_ok = (n_hidden == 1 || n_hidden == 2) && Dp <= 256 && H[0] % 16 == 0 && H[0] <= 256 &&
+                          (n_hidden == 1 || (H[1] % 16 == 0 && H[1] <= 256));
+    const int Hl = n_hidden == 2 ? H[1] : H[0];
+    const long long wofs = md.layer[n_hidden].dst_off;  // output layer
+    auto before = [](const std::vector<int>& c, int i) { return i >= 1 ? c[i - 1] : 0; };  // degree < i
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+      MadeDev::TcPlan& P = md.tc[p];
+      P = MadeDev::TcPlan{};
+      if (!shape_ok) continue;
+      const int CMAX = kTcGroupMax[p];
+      std::vector<int> rec, src;
+      int tcw1 = 16, dw1 = 16, dw2 = 16, wbmax = 0;
+      bool fits = true;
+      for (int i = 0; i < D; ++i) {  // per-step unit windows (the delta tiles)
+        const int ua = before(c1, i), ub = before(c1, i + 1);
+        if (ub > ua) dw1 = std::max(dw1, ((ub + 15) & ~15) - (ua & ~15));
+        if (n_hidden == 2) {
+          const int va = before(c2, i), vb = before(c2, i + 1);
+          if (vb > va) dw2 = std::max(dw2, ((vb + 15) & ~15) - (va & ~15));
+        }
       }
-      grp.insert(grp.end(), rec, rec + TNVAN_TCG_INTS);
-      i0 = i1;
+      fits = fits && dw1 <= 64 && dw2 <= 64;
+      for (int i0 = 0; i0 < D && fits;) {
+        // units completing at steps [i0, i1): degree in [i0, i1 - 1]
+        auto win = [&](const std::vector<int>& c, int a, int b, int& w, int& n) {
+          const int lo = before(c, a), hi = before(c, b);
+          if (hi <= lo) {
+            w = lo & ~15;
+            n = 0;
+          } else {
+            w = lo & ~15;
+            n = ((hi + 15) & ~15) - w;
+          }
+        };
+        int i1 = i0 + 1;
+        while (i1 < D && i1 - i0 < CMAX) {
+          int w, n;
+          win(c1, i0, i1 + 1, w, n);
+          if (n > 64) break;
+          ++i1;
+        }
+        int w1c, n1c, w2c = 0, n2c = 0;
+        win(c1, i0, i1, w1c, n1c);
+        if (n_hidden == 2) win(c2, i0, i1, w2c, n2c);
+        if (n1c > 64) fits = false;
+        const int kSc = std::min(Dp, std::max(16, (i1 + 15) & ~15));
+        const int wL = n_hidden == 2 ? w2c : w1c, nL = n_hidden == 2 ? n2c : n1c;
+        const int off = (int)src.size();
+        const int nA = n_hidden == 2 ? H[1] * n1c : 0, nB = Dp * nL, nC = n1c * kSc;
+        src.resize(src.size() + nA + nB + nC, -1);
+        int* A = src.data() + off;
+        int* Bp = A + nA;
+        int* C = Bp + nB;
+        for (int sl = 0; sl < n1c / 16 && n_hidden == 2; ++sl)  // W2 [H2][H1], column = layer-1 unit
+          for (int r = 0; r < H[1]; ++r)
+            for (int kk = 0; kk < 16; ++kk)
+              A[sl * H[1] * 16 + (r >> 3) * 128 + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7)] =
+                  (int)(md.layer[1].dst_off + (long long)r * H[0] + w1c + 16 * sl + kk);
+        for (int sl = 0; sl < nL / 16; ++sl)  // Wo [D][Hl]
+          for (int r = 0; r < D; ++r)
+            for (int kk = 0; kk < 16; ++kk)
+              Bp[sl * Dp * 16 + (r >> 3) * 128 + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7)] =
+                  (int)(wofs + (long long)r * Hl + wL + 16 * sl + kk);
+        for (int r = 0; r < n1c; ++r)  // W1 [H1][D]
+          for (int k2 = 0; k2 < std::min(kSc, D); ++k2)
+            C[(r >> 3) * 8 * kSc + (k2 >> 3) * 64 + (r & 7) * 8 + (k2 & 7)] =
+                (int)(md.layer[0].dst_off + (long long)(w1c + r) * D + k2);
+        const int bytes = 2 * (nA + nB + nC);
+        wbmax = std::max(wbmax, bytes);
+        tcw1 = std::max(tcw1, n1c);
+        int r16[TNVAN_TCG_INTS] = {i0, i1, w1c, n1c, w2c, n2c, kSc, off, 2 * nA, 2 * nB, 2 * nC};
+        rec.insert(rec.end(), r16, r16 + TNVAN_TCG_INTS);
+        i0 = i1;
+      }
+      const int need_cols = tcw1 + (n_hidden == 2 ? H[1] : 0) + Dp;
+      int cols = 32;
+      while (cols < need_cols) cols *= 2;
+      fits = fits && cols <= 512;
+      if (!fits) continue;
+      int* drec = nullptr;
+      if ((rc = upload(ctx, in, rec, &drec))) return rc;
+      int* dsrc = nullptr;
+      if ((rc = upload(ctx, in, src, &dsrc))) return rc;
+      void* blob = nullptr;
+      cudaError_t e2 = cudaMalloc(&blob, std::max<size_t>(src.size(), 8) * sizeof(uint16_t));
+      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blobs): %s", cudaGetErrorString(e2));
+      in.dev_allocs.push_back(blob);
+      P.n_chunks = (int)rec.size() / TNVAN_TCG_INTS;
+      P.chunks = drec;
+      P.wblob = static_cast<uint16_t*>(blob);
+      P.wsrc = dsrc;
+      P.n_wblob = (long long)src.size();
+      P.dp = Dp;
+      P.tcw1 = tcw1;
+      P.dw1 = dw1;
+      P.dw2 = n_hidden == 2 ? dw2 : 0;
+      P.wbmax = wbmax;
+      P.tmem_cols = cols;
+      MadeDev probe = md;
+      probe.nh = n_hidden;
+      probe.tc[p] = P;
+      P.ok = sample_tc_smem_bytes(probe, p) <= 227 * 1024;
     }
-    int* dgrp = nullptr;
-    if ((rc = upload(ctx, in, grp, &dgrp))) return rc;
-    int* dsrc = nullptr;
-    if ((rc = upload(ctx, in, src, &dsrc))) return rc;
-    void* blk = nullptr;
-    if (!src.empty()) {
-      cudaError_t e2 = cudaMalloc(&blk, src.size() * sizeof(float));
-      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler triangles): %s", cudaGetErrorString(e2));
-      in.dev_allocs.push_back(blk);
-    }
-    P.n_groups = (int)grp.size() / TNVAN_TCG_INTS;
-    P.groups = dgrp;
-    P.blocks = static_cast<float*>(blk);
-    P.src = dsrc;
-    P.n_blk = (long long)src.size();
-    P.twmax = twmax;
-    P.tcw1 = tcw1;
-    P.tcw2 = tcw2;
-    P.ok = fits && D <= 128 && sample_tc_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
   }
   md.sample_tc_ok = 0;
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tc_ok = md.sample_tc_ok || md.tc[p].ok;
@@ -1445,8 +1496,7 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
   if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
   int smem = 0, max_edges = 0;
   for (const Instance& in : ctx->inst) {
-    const MadeDev::TcPlan& P = in.dev.made.tc[plan];
-    smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax));
+    smem = std::max(smem, sample_tc_smem_bytes(in.dev.made, plan));
     max_edges = std::max(max_edges, in.m);
   }
   const int stride = (max_edges + 3) & ~3;
@@ -1461,7 +1511,7 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
     const int k0 = c * n / nc, k1 = (c + 1) * n / nc;
     {
       PROF("sample_tc", ctx->side[c]);
-      CK(launch_sample_tc(ctx->d_inst, li, plan, smem, d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
+      CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
                           li.tile_begin[k1]),
          "tensor-core sample kernel");
     }
@@ -1595,7 +1645,7 @@ int sample_contract_adjoint_impl(tnvan_ctx* ctx, const double* betas, int batch,
   bool strips_only = ctx->inst.size() >= 2;
   for (const Instance& in : ctx->inst) strips_only = strips_only && in.kind == 0;
   bool tc_all = precision == TNVAN_BF16;
-  for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
+  tc_all = tc_all && tc_sampler_usable(ctx);
   const int plan = tc_all ? pick_tc_plan(ctx) : -1;
   if (strips_only && plan >= 0 && ctx->tune_overlap) {
     const bool defer = dj_deferred && d_dJ;
@@ -1989,7 +2039,7 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
   };
   auto sample = [&]() { return tnvan_sample_and_contract(ctx, betas, batch, 1, 0, precision, sp, lq, lz, stream); };
   bool tc_sampler = precision == TNVAN_BF16;
-  for (const Instance& in : ctx->inst) tc_sampler = tc_sampler && in.dev.made.sample_tc_ok;
+  tc_sampler = tc_sampler && tc_sampler_usable(ctx);
   if (tc_sampler) {
     int best = -1;
     float best_ms = 1e30f;
@@ -2317,10 +2367,18 @@ int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s) {
 // Segments the sampler of this precision reads.
 int sampler_pack_mask(const tnvan_ctx* ctx, int precision) {
   bool tc_all = precision == TNVAN_BF16;
-  for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
+  tc_all = tc_all && tc_sampler_usable(ctx);
   const int plan = tc_all ? pick_tc_plan(ctx) : -1;
-  if (plan >= 0) return PACK_FLAT | PACK_TILES | PACK_TC | ((plan + 1) << 8);  // only the plan in use
+  if (plan >= 0) return PACK_FLAT | PACK_TC | ((plan + 1) << 8);  // only the plan in use
   return PACK_FLAT | PACK_SIMT;
+}
+
+bool tc_sampler_usable(const tnvan_ctx* ctx) {
+  if (ctx->inst.empty()) return false;
+  const int nh = ctx->inst[0].dev.made.nh;
+  for (const Instance& in : ctx->inst)
+    if (!in.dev.made.sample_tc_ok || in.dev.made.nh != nh) return false;
+  return true;
 }
 
 // Tensor-core sampler plan usable by every instance: the autotuned one, else
@@ -2342,7 +2400,7 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
                 int8_t* d_spins, float* d_logq, const int8_t* given, cudaStream_t s) {
   int rc;
   bool tc_all = precision == TNVAN_BF16;
-  for (const Instance& in : ctx->inst) tc_all = tc_all && in.dev.made.sample_tc_ok;
+  tc_all = tc_all && tc_sampler_usable(ctx);
   int plan = -1;
   if (tc_all) plan = pick_tc_plan(ctx);
   if (plan >= 0) {
@@ -2352,11 +2410,11 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
     li.step = step;
     int smem = 0;
     for (const Instance& in : ctx->inst) {
-      const MadeDev::TcPlan& P = in.dev.made.tc[plan];
-      smem = std::max(smem, sample_tc_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax));
+      smem = std::max(smem, sample_tc_smem_bytes(in.dev.made, plan));
     }
     PROF(given ? "log_prob_tc" : "sample_tc", s);
-    CK(launch_sample_tc(ctx->d_inst, li, plan, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
+    CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, given, s),
+       "tensor-core sample kernel");
     return TNVAN_OK;
   }
   const int tile = pick_sample_tile(ctx);

@@ -15,11 +15,12 @@
 #define TNVAN_MAX_STRIP_W 4
 #define TNVAN_MAX_ELIM_W 12
 #define GROUP_INTS 15
-#define TNVAN_TC_PLANS 3  // step-group size limits of the tensor-core sampler: 4, 6, 8
-// Tensor-core sampler group record: i0 i1 u1lo u1hi u2lo u2hi, block start and
-// size (floats), offsets of TW2 TWo b1 b2 bo in the block, then c1 and c2 at
-// the group's steps (9 each: units with degree < i0 + q, q = 0..8), pad.
-#define TNVAN_TCG_INTS 32
+#define TNVAN_TC_PLANS 3  // step-chunk size limits of the tensor-core sampler: 8, 16, 32
+// Tensor-core sampler chunk record: i0 i1 (steps), w1c n1c (16-aligned window
+// of the chunk's layer-1 units), w2c n2c (layer 2), kSc (K width of the W1
+// rows: spins 0 .. kSc-1), blob offset (BF16 elements, a multiple of 8), the
+// blob's three part sizes in bytes (W2 window, Wo window, W1 rows), pad.
+#define TNVAN_TCG_INTS 16
 
 namespace tnvan {
 
@@ -55,18 +56,23 @@ struct MadeDev {
   const int* groups;      // [n_groups][GROUP_INTS], see k_made.cu
   int ug1, ug2, ugo;      // largest group unit counts per layer
   int wmax;               // largest per-group weight block (floats)
-  // Tensor-core sampler: one step-group plan per group-size limit.  Per
-  // group only the in-group triangles, rows padded to 4 floats:
-  //   TW1 [n1g][r4(gi)], TW2 [n2g][r4(n1g)], TWo [gi][r4(n2g)].
+  // Tensor-core sampler: one step-chunk plan per chunk-size limit.  Per
+  // chunk one BF16 weight blob in the MMA's K-major canonical layout (see
+  // k_sample_tc.cu): the K-window of W2 over the chunk's layer-1 units, that
+  // of Wo over its layer-2 (or, with one hidden layer, layer-1) units, and
+  // W1's rows of its layer-1 units.
   struct TcPlan {
-    int ok;               // eligible (unit counts within the kernel's limits)
-    int n_groups;
-    const int* groups;    // [n_groups][TNVAN_TCG_INTS], see TNVAN_TCG_INTS
-    float* blocks;        // gathered from `packed` on every call
-    const int* src;       // [n_blk] index into `packed`, -1 = zero
-    long long n_blk;
-    int twmax;            // largest group (floats)
-    int tcw1, tcw2;       // widest 16-aligned unit window of a group, layers 1 and 2
+    int ok;               // eligible (sizes within the kernel's limits)
+    int n_chunks;
+    const int* chunks;    // [n_chunks][TNVAN_TCG_INTS], see TNVAN_TCG_INTS
+    uint16_t* wblob;      // BF16 blobs, gathered from the network on every call
+    const int* wsrc;      // [n_wblob] index into the packed network, -1 = zero
+    long long n_wblob;
+    int dp;               // D padded to a multiple of 16
+    int tcw1;             // TMEM columns of the chunk's layer-1 pre-activations
+    int dw1, dw2;         // widest per-step unit window (delta tiles), layers 1 and 2
+    int wbmax;            // largest chunk blob (bytes)
+    int tmem_cols;        // TMEM allocation of a CTA
   } tc[TNVAN_TC_PLANS];
   float* blocks;          // blocked weights (gathered from `packed` every call)
   const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
@@ -380,9 +386,10 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
                              const double* stats, float* partials, long long part_stride, int* status,
                              cudaStream_t s, int blk_begin = 0, int blk_end = -1);
 int fused_bwd_smem_bytes(int D, int H1, int H2);
-cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
-                             float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
-int sample_tc_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
+cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int plan, int nh, int smem_bytes,
+                             int8_t* spins, float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0,
+                             int blk_end = -1);
+int sample_tc_smem_bytes(const MadeDev& md, int plan);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 

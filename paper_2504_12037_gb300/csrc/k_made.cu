@@ -57,8 +57,8 @@ __device__ __forceinline__ void store_tile(const MadeDev& md, int l, int r, int 
 //   PACK_TILES BF16 tiles in the tensor cores' canonical K-major layout (no
 //              swizzle): W1 [H1 x D], W2 [H2 x H1], Wo [D x H2]
 //   PACK_SIMT  the blocked SIMT sampler's weight blocks
-//   PACK_TC    the tensor-core sampler plans' triangle tiles (one plan, or
-//              all, per pack_tc_plan)
+//   PACK_TC    the tensor-core sampler plans' BF16 chunk weight blobs (one
+//              plan, or all, per pack_tc_plan)
 __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
   const MadeDev& md = inst[blockIdx.y].made;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,12 +119,14 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
     for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
       if (only >= 0 && p != only) continue;
       const MadeDev::TcPlan& P = md.tc[p];
-      if (e < P.n_blk) {
-        const int j = P.src[e];
-        P.blocks[e] = j >= 0 ? packed_value(md, j) : 0.f;
+      if (e < P.n_wblob) {
+        const int j = P.wsrc[e];
+        uint32_t u = __float_as_uint(j >= 0 ? packed_value(md, j) : 0.f);
+        u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+        P.wblob[e] = (uint16_t)(u >> 16);
         return;
       }
-      e -= P.n_blk;
+      e -= P.n_wblob;
     }
   }
 }
@@ -138,7 +140,7 @@ long long pack_elems(const MadeDev& md, int mask) {
   if (mask & PACK_TC) {
     const int only = pack_tc_plan(mask);
     for (int p = 0; p < TNVAN_TC_PLANS; ++p)
-      if (only < 0 || p == only) n += md.tc[p].n_blk;
+      if (only < 0 || p == only) n += md.tc[p].n_wblob;
   }
   return n;
 }

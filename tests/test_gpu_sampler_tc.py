@@ -1,0 +1,100 @@
+"""The BF16 tensor-core sampler (tcgen05, Eq. 6-8) on every workload: one or
+two hidden layers, hidden widths 16 to 256, width sets of 4 to 256 spins
+(padded to a multiple of 16), mixed instance sizes in one launch.  log q is
+checked against the FP64 oracle (teacher-forced on oracle-drawn samples, and on
+the GPU's own samples), the sampler against its own teacher-forced log q, and
+the distribution of a small network against its exact marginal."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ising, made
+from paper_2504_12037_gb300 import tnvan as tv
+from paper_2504_12037_gb300 import workloads as wl
+
+from gpu_helpers import oracle_samples, to_dev_spins
+
+pytestmark = pytest.mark.gpu
+
+TOL_RED = 1e-3  # |delta log q| / N in the reduced-precision modes
+
+
+def _model(w, n_inst=None, seed=3, scale=1.5):
+    from paper_2504_12037_gb300.model import TNVAN
+
+    n = len(w.graphs) if n_inst is None else n_inst
+    return TNVAN(w.graphs[:n], w.widths_sets[:n], w.hidden, w.betas[:n], seed=seed, init_scale=scale)
+
+
+def _workload(cfg):
+    return wl.workload(cfg, n_instances=10) if cfg == 5 else wl.workload(cfg)
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("chunk", [8, 16, 32])
+def test_tc_log_prob_matches_oracle_every_workload(cfg, chunk):
+    w = _workload(cfg)
+    model = _model(w)
+    model.ctx.set_tuning((0, 0, 0, 0, chunk, 0))
+    batch = 96
+    s_all, refs = [], []
+    for k in range(model.n):
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_or, _, _ = oracle_samples(p32, model.D[k], w.hidden, 3, 0, k, batch)
+        s_all.append(s_or.numpy().reshape(-1))
+        refs.append(made.log_q(torch.as_tensor(p32, dtype=torch.float64), model.D[k], w.hidden, s_or))
+    d_spins = to_dev_spins(np.concatenate(s_all))
+    logq = torch.empty(model.n * batch, dtype=torch.float32, device="cuda")
+    model.ctx.profile(True)
+    model.ctx.log_prob(batch, d_spins, logq, tv.BF16)
+    torch.cuda.synchronize()
+    assert "log_prob_tc" in model.ctx.profile_read()  # the tensor-core path ran
+    model.ctx.profile(False)
+    worst = 0.0
+    for k in range(model.n):
+        err = float((logq[k * batch:(k + 1) * batch].cpu().double() - refs[k]).abs().max()) / w.graphs[k].n
+        worst = max(worst, err)
+        assert err <= TOL_RED, (k, err)
+    print(f"workload {cfg} chunk {chunk}: max |delta log q| / N = {worst:.2e}")
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
+def test_tc_sampler_own_samples_against_oracle(cfg):
+    # sampling on the tensor cores: log q of the GPU's own draws against the
+    # oracle, and against the same kernel teacher-forced on those draws
+    w = _workload(cfg)
+    model = _model(w)
+    B = 300
+    model.ctx.profile(True)
+    spins, logq, _ = model.sample(B, 77, 5, precision=tv.BF16)
+    torch.cuda.synchronize()
+    assert "sample_tc" in model.ctx.profile_read()
+    model.ctx.profile(False)
+    lq2 = torch.empty_like(logq)
+    model.ctx.log_prob(B, spins, lq2, tv.BF16)
+    torch.cuda.synchronize()
+    assert torch.allclose(logq, lq2, atol=1e-5, rtol=0)
+    for k in range(model.n):
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy().astype(np.float64)
+        s = torch.as_tensor(model.spins_of(spins, k, B).cpu().numpy().astype(np.float64))
+        assert torch.all(s.abs() == 1)
+        ref = made.log_q(torch.as_tensor(p32), model.D[k], w.hidden, s)
+        err = float((logq[k * B:(k + 1) * B].cpu().double() - ref).abs().max()) / w.graphs[k].n
+        assert err <= TOL_RED, (k, err)
+
+
+def test_tc_sampler_one_hidden_layer_distribution():
+    # the 4x4 workload's network (4 -> 16 -> 4, one hidden layer): the
+    # frequencies of the 16 width-set states against the network's exact q
+    w = wl.workload(1)
+    model = _model(w, scale=2.0)
+    B = 200000
+    spins, logq, _ = model.sample(B, 4321, 0, precision=tv.BF16)
+    s = model.spins_of(spins, 0, B).cpu().numpy()
+    idx = (((1 - s) // 2) * (2 ** np.arange(4))).sum(1)
+    counts = np.bincount(idx, minlength=16).astype(float)
+    th = torch.as_tensor(model.params.cpu().numpy().astype(np.float64))
+    q = torch.exp(made.log_q(th, 4, w.hidden, ising.all_configs(4))).numpy()
+    chi2 = float(((counts - B * q) ** 2 / (B * q)).sum())
+    print("chi2 (15 dof):", chi2)
+    assert chi2 < 45
