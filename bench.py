@@ -77,6 +77,12 @@ def args_():
                          "(sample tile, strip tile, backward CTAs, adjoint tile, TC group, overlap 2=on 1=off)")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5],
+                    help="2 (default): the 16x16 EA headline; 1, 3, 4, 5: the other synthetic workloads "
+                         "(4x4 +-J, SK N=64, random 3-regular N=256, 64 mixed-size EA instances), each its own line")
+    ap.add_argument("--train-steps", type=int, default=0,
+                    help="with --workload 5: Adam steps of the accuracy run (oracle checks at steps 1, 100 and "
+                         "the last)")
     ap.add_argument("--planned", action="store_true",
                     help="also time the training step on random regular graphs (n = 1000, d = 3) whose width "
                          "sets come from the width-set finder")
@@ -153,14 +159,18 @@ class ClockSampler:
 # algorithmic work per sample (used for the roofline figures)
 # ---------------------------------------------------------------------------
 def made_macs(D, hidden):
-    """Masked multiply-adds of one MADE forward pass (each unit once)."""
+    """Masked multiply-adds of one MADE forward pass (each unit once), one or
+    two hidden layers."""
     import numpy as np
     cyc = max(D - 1, 1)
     d1 = np.sort(np.arange(hidden[0]) % cyc + 1)
-    d2 = np.sort(np.arange(hidden[1]) % cyc + 1)
     c1 = lambda d: int((d1 <= d).sum())
-    c2 = lambda d: int((d2 <= d).sum())
     l1 = int(d1.sum())                       # unit of degree d reads inputs 1..d
+    if len(hidden) == 1:
+        lo = sum(c1(i) for i in range(D))    # output i reads units of degree <= i
+        return l1 + lo, (l1, 0, lo)
+    d2 = np.sort(np.arange(hidden[1]) % cyc + 1)
+    c2 = lambda d: int((d2 <= d).sum())
     l2 = sum(c1(int(d)) for d in d2)         # layer-2 unit reads layer-1 units of degree <= d
     lo = sum(c2(i) for i in range(D))        # output i reads layer-2 units of degree <= i
     return l1 + l2 + lo, (l1, l2, lo)
@@ -616,6 +626,285 @@ def run_ours(a):
 
 
 # ---------------------------------------------------------------------------
+# the other workloads (--workload 1, 3, 4, 5): one JSON line each
+# ---------------------------------------------------------------------------
+def oracle_log_zr(g, W, beta, s):
+    """The oracle's log Z_R (Eq. 4) of given width-set rows, by topology."""
+    from oracle import dense, general, ising, transfer
+
+    if g.topology == 1:
+        return dense.log_zr_dense(g.n, g.ei, g.ej, g.J, beta, W, s)
+    if g.topology == 2:
+        return general.log_zr_general(g.n, g.ei, g.ej, g.J, beta, W, s)
+    if g.n <= 16:
+        return ising.log_zr_enum(g.n, g.ei, g.ej, g.J, beta, W, s)
+    return transfer.log_zr_lattice(g.n, g.ei, g.ej, g.J, beta, W, s, g.Lx)
+
+
+def run_workload(a):
+    """One synthetic workload: the captured training step in BF16 (headline)
+    and FP32, per-kernel times, the dominant kernel's roofline, end to end
+    through host buffers, and (rank 0, oracle leg) parity on sampled rows,
+    the oracle timed on a bounded sample, and for workload 5 an Adam run with
+    oracle checks along it."""
+    import numpy as np
+    import torch
+
+    from paper_2504_12037_gb300 import tnvan as tv
+    from paper_2504_12037_gb300 import workloads as wl
+    from paper_2504_12037_gb300.model import TNVAN
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    w = wl.workload(a.workload)
+    B = w.batch
+    n_inst = len(w.graphs)
+    stream = torch.cuda.current_stream()
+    seed = 12037 + 7919 * rank
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
+    samples_step = n_inst * B * world
+    PREC = {"fp32": tv.FP32, "bf16": tv.BF16}
+
+    def measure(name, sample_clocks):
+        mode = PREC[name]
+        m = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
+        m.ctx.reserve(B)
+        tuned = m.ctx.autotune(m.betas, B, mode)
+        dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
+        dJ = torch.empty(sum(m.n_edges), dtype=torch.float64, device="cuda")
+        cs = m.capture_train_step(B, seed, mode, 0.01, None, dbeta, dJ)
+        for _ in range(a.warmup):
+            cs.replay()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(gpu_id) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for e0, e1 in ev:
+            flush.zero_()  # evict L2 between replays (outside the timed interval)
+            e0.record(stream)
+            cs.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / a.steps
+        clk = clocks.stop() if clocks else None
+        # per-kernel times: eager steps with the overlapped schedule off
+        base = tuple(tuned)
+        m.ctx.set_tuning(base[:5] + (1,))
+        bufs = m.buffers(B)
+        m.train_step(B, seed, 10 ** 6, mode, 0.01, bufs, dbeta, dJ, stream)
+        torch.cuda.synchronize()
+        m.ctx.profile(True)
+        for i in range(3):
+            flush.zero_()
+            m.train_step(B, seed, 10 ** 6 + 1 + i, mode, 0.01, bufs, dbeta, dJ, stream)
+        torch.cuda.synchronize()
+        m.ctx.profile(False)
+        prof = m.ctx.profile_read()
+        m.ctx.set_tuning(base)
+        # launches per step of the captured form (overlapped schedule on)
+        m.ctx.profile(True)
+        m.train_step(B, seed, 10 ** 6 + 9, mode, 0.01, bufs, dbeta, dJ, stream)
+        torch.cuda.synchronize()
+        m.ctx.profile(False)
+        launches = sum(v[1] for v in m.ctx.profile_read().values())
+        run = parity_run(m, lambda i: m.train_step(B, seed, i, mode, 0.01, bufs, dbeta, dJ, stream), name, bufs, B)
+        return {"model": m, "cs": cs, "ms": ms, "clocks": clk, "prof": prof, "tuned": tuned, "run": run,
+                "launches": launches}
+
+    head = measure("bf16", True)
+    cmp_ = measure("fp32", False)
+    m, cs = head["model"], head["cs"]
+    # end to end: counter upload, one replay, samples / log q / log Z_R and the
+    # step's statistics read back to pinned host memory, every step
+    h_ctr = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+    sp_, lq_, lz_ = cs.out
+    h_out = (torch.empty(sp_.numel(), dtype=torch.int8, pin_memory=True),
+             torch.empty(lq_.numel(), dtype=torch.float32, pin_memory=True),
+             torch.empty(lz_.numel(), dtype=torch.float64, pin_memory=True),
+             torch.empty(n_inst, 8, dtype=torch.float64, pin_memory=True))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(a.e2e_steps):
+        h_ctr[0] = 10 ** 7 + i
+        cs.counter.copy_(h_ctr, non_blocking=True)
+        cs.replay()
+        for h, d in zip(h_out, (sp_, lq_, lz_, cs.stats)):
+            h.copy_(d, non_blocking=True)
+        stream.synchronize()
+    t_e2e = (time.perf_counter() - t0) / max(a.e2e_steps, 1)
+    prof = head["prof"]
+    dom_name, (dom_ms, dom_n) = max(prof.items(), key=lambda kv: kv[1][0])
+    peaks = measured_peaks()
+    macs = [made_macs(len(W), w.hidden)[0] for W in w.widths_sets]
+    roofline = {"kernel": dom_name, "ms_per_launch": dom_ms / dom_n}
+    if dom_name in ("sample_tc", "bwd_fused", "sample", "backward"):
+        mult = 3 if dom_name in ("bwd_fused", "backward") else 1
+        flop = 2.0 * mult * sum(macs) * B
+        ach = flop / (dom_ms / dom_n / 1e3) / 1e12
+        tensor = dom_name in ("sample_tc", "bwd_fused")
+        peak = peaks["bf16_tflops"] if tensor else props.multi_processor_count * FP32_LANES_PER_SM * 2 * \
+            peaks["sm_max_mhz"] * 1e6 / 1e12
+        roofline.update({"bound": "tensor" if tensor else "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "flop_per_launch": flop, "traffic": None,
+                         "peak_source": peaks["source"], "note": "masked MACs counted once per unit"})
+    else:
+        roofline.update({"bound": None, "note": "no algorithmic work formula for this kernel"})
+    out = {
+        "metric": METRIC, "value": samples_step / (head["ms"] / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded couplings; random-init MADE)",
+        "config": {"workload": w.name, "instances": n_inst, "batch_per_instance": B, "made": w.hidden,
+                   "betas": sorted(set(float(b) for b in w.betas)),
+                   "width_set_sizes": sorted(set(int(len(W)) for W in w.widths_sets)),
+                   "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
+                   "timing": "CUDA-graph replay of the whole step", "l2": "flushed (256 MB write) between steps",
+                   "parallelism": "single GPU"},
+        "clocks": head["clocks"],
+        "e2e": {"value": samples_step / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 8,
+                "d2h_bytes_per_step": int(sp_.numel() + 4 * lq_.numel() + 8 * lz_.numel() + 64 * n_inst)},
+        "gpu_launches": int(head["launches"] * a.steps), "roofline": roofline,
+        "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()},
+        "autotuned": list(head["tuned"]),
+        "compare": {"precision": "fp32", "value": samples_step / (cmp_["ms"] / 1e3), "ms_per_step": cmp_["ms"],
+                    "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]}
+                                for k, v in cmp_["prof"].items()}},
+    }
+    traj = None
+    if a.workload == 5 and a.train_steps > 0:
+        # Adam from the same start; at steps 1, 100 and the last: the step's
+        # statistics and, for a few instances of each size, the rows the
+        # oracle checks
+        mt = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=77)
+        bt = mt.buffers(B)
+        checks = sorted(set([1, min(100, a.train_steps), a.train_steps]))
+        picks = []
+        for L in sorted(set(g.Lx for g in w.graphs)):
+            picks += [k for k, g in enumerate(w.graphs) if g.Lx == L][:2]
+        traj = {"train_steps": a.train_steps, "checked_steps": checks, "instances_checked": picks, "runs": []}
+        t0 = time.time()
+        for i in range(1, a.train_steps + 1):
+            if i in checks:
+                p_before = mt.params.cpu().numpy().copy()
+            mt.train_step(B, 4242, i, tv.BF16, 0.01, bt, None, None, stream)
+            if i in checks:
+                torch.cuda.synchronize()
+                st = mt.step_stats().cpu().numpy()
+                rows = np.arange(0, B, 97)
+                traj["runs"].append({"step": i, "params": p_before, "offsets": np.asarray(mt.offsets),
+                                     "stats": st, "rows": rows,
+                                     "spins": {k: mt.spins_of(bt[0], k, B).cpu().numpy()[rows] for k in picks},
+                                     "logq": {k: bt[1][k * B:(k + 1) * B].cpu().numpy()[rows] for k in picks},
+                                     "logZR": {k: bt[2][k * B:(k + 1) * B].cpu().numpy()[rows] for k in picks}})
+        torch.cuda.synchronize()
+        traj["train_s"] = time.time() - t0
+    if rank == 0 and not a.no_cpu_baseline:
+        out["parity"] = oracle_parity_any(w, [head["run"], cmp_["run"]])
+        out["cpu_baseline"] = cpu_baseline_any(w, head["model"].params.cpu().numpy(), head["model"].offsets)
+        if traj is not None:
+            out["train_run"] = oracle_train_checks(w, traj)
+    print(json.dumps(out), flush=True)
+
+
+def oracle_parity_any(w, runs, max_inst=8):
+    """oracle_parity for any topology, on at most max_inst instances."""
+    import numpy as np
+    import torch
+
+    from oracle import estimators as est
+    from oracle import made
+
+    out = {}
+    ks = list(range(len(w.graphs)))[:max_inst]
+    for r in runs:
+        e_q = e_z = e_red = 0.0
+        for k in ks:
+            g, W, beta = w.graphs[k], w.widths_sets[k], w.betas[k]
+            th = torch.as_tensor(r["params"][r["offsets"][k]:r["offsets"][k + 1]].astype(np.float64))
+            s = torch.as_tensor(r["spins"][k].astype(np.float64))
+            lq_or = made.log_q(th, len(W), w.hidden, s).numpy()
+            lz_or = oracle_log_zr(g, W, beta, s).detach().numpy()
+            e_q = max(e_q, float(np.abs(r["logq"][k][r["rows"]] - lq_or).max()) / g.n)
+            e_z = max(e_z, float(np.abs(r["logZR"][k][r["rows"]] - lz_or).max()) / g.n)
+            fe = est.free_energies(r["logZR"][k], r["logq"][k].astype(np.float64), beta)
+            e_red = max(e_red, abs(r["stats"][k][0] - fe["F_q"]) / g.n, abs(r["stats"][k][1] - fe["F_IS"]) / g.n)
+        out[r["precision"]] = {"instances_checked": len(ks), "rows_per_instance": int(len(r["rows"])),
+                               "max_abs_dlogq_per_spin": e_q, "max_abs_dlogZR_per_spin": e_z,
+                               "reduction_max_abs_dF_per_spin": e_red}
+    out["tolerance_per_spin"] = {"fp32": 1e-6, "reduced_precision": 1e-3}
+    return out
+
+
+def cpu_baseline_any(w, params, offsets, budget_s=10.0, n_b=64):
+    """The oracle (sampling replay, log q, log Z_R by topology, estimators) on
+    a bounded sample: n_b samples per instance, instances in turn, until about
+    budget_s has elapsed."""
+    import numpy as np
+    import torch
+
+    from oracle import estimators as est
+    from oracle import made, philox
+
+    torch.set_num_threads(os.cpu_count() or 1)
+    done = 0
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        g, W, beta = w.graphs[k % len(w.graphs)], w.widths_sets[k % len(w.graphs)], w.betas[k % len(w.graphs)]
+        kk = k % len(w.graphs)
+        th = torch.as_tensor(params[offsets[kk]:offsets[kk + 1]].astype(np.float64))
+        u = philox.uniforms(1, k, kk, n_b, len(W))
+        s, _ = made.sample(th, len(W), w.hidden, u)
+        lq = made.log_q(th, len(W), w.hidden, s)
+        lz = oracle_log_zr(g, W, beta, s)
+        est.free_energies(lz.detach(), lq.detach(), beta)
+        done += n_b
+        k += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{k} instance batches x {n_b} samples (FP64 sampling replay, log q, log Z_R, estimators) "
+                      f"in {dt:.1f} s"}
+
+
+def oracle_train_checks(w, traj):
+    """At each checked step of the Adam run: |F_q(rows, GPU) - F_q(rows, oracle)|
+    / N on the same parameters and samples, the step's F_q / N and, for each
+    checked instance, the exact F / N (Kac-Ward determinant) and |F_q - F| / N."""
+    import numpy as np
+    import torch
+
+    from oracle import kacward, made
+
+    f_ex = {}
+    for k in traj["instances_checked"]:
+        g = w.graphs[k]
+        f_ex[k] = -kacward.log_z_kac_ward(g.Lx, g.Ly, g.ei, g.ej, g.J, w.betas[k]) / w.betas[k] / g.n
+    out = {"train_steps": traj["train_steps"], "train_s": traj["train_s"], "checks": []}
+    for r in traj["runs"]:
+        rec = {"step": r["step"], "instances": []}
+        for k in traj["instances_checked"]:
+            g, W, beta = w.graphs[k], w.widths_sets[k], w.betas[k]
+            th = torch.as_tensor(r["params"][r["offsets"][k]:r["offsets"][k + 1]].astype(np.float64))
+            s = torch.as_tensor(r["spins"][k].astype(np.float64))
+            lq_or = made.log_q(th, len(W), w.hidden, s).numpy()
+            lz_or = oracle_log_zr(g, W, beta, s).detach().numpy()
+            f_gpu = -float((r["logZR"][k] - r["logq"][k].astype(np.float64)).mean()) / beta
+            f_or = -float((lz_or - lq_or).mean()) / beta
+            fq = float(r["stats"][k][0]) / g.n
+            rec["instances"].append({"instance": k, "L": g.Lx, "abs_dFq_rows_per_spin": abs(f_gpu - f_or) / g.n,
+                                     "F_q_per_spin": fq, "F_exact_per_spin": f_ex[k],
+                                     "abs_F_q_minus_F_exact_per_spin": abs(fq - f_ex[k])})
+        out["checks"].append(rec)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # the FP64 oracle as the CPU baseline / reference arm
 # ---------------------------------------------------------------------------
 def oracle_step(w, params, offsets, n_b, seed, step):
@@ -768,5 +1057,7 @@ if __name__ == "__main__":
     a = args_()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != CONFIG:
+        run_workload(a)
     else:
         run_ours(a)

@@ -186,8 +186,9 @@ int tnvan_reserve(tnvan_ctx* ctx, int max_batch);
  *   batch     samples per instance (>= 0).
  *   precision TNVAN_FP32 | TNVAN_TF32 | TNVAN_BF16.  With TNVAN_BF16 the
  *             network runs on the tensor cores in BF16 (FP32 accumulate) when
- *             every instance has two hidden layers of <= 128 units and D <= 128
- *             (multiples of 16); the contractions stay FP32.
+ *             every instance has one or two hidden layers of <= 256 units
+ *             (multiples of 16) and D <= 256 and all share one number of
+ *             hidden layers; the contractions stay FP32.
  *   d_spins   device int8 out, layout above.   d_logq  device float out.
  *   d_logZR   device double out.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE (an instance lacks network or width set),
@@ -370,7 +371,10 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
  * `batch` samples drawn from the current networks -- the SIMT sampler's
  * samples per CTA, the strip contraction's samples per CTA, the number of
  * CTAs per instance of the fused BF16 backward, the strip adjoint's samples
- * per CTA, the BF16 tensor-core sampler's step-group size limit and whether
+ * per CTA, the BF16 tensor-core sampler's form and plan (the grouped form,
+ * two hidden layers of <= 128 units and D <= 128: step-group size limit 4, 6
+ * or 8; the per-step form, any network the sampler takes: chunk size limit
+ * 12, 16 or 32) and whether
  * tnvan_sample_contract_adjoint overlaps sampling and the strip adjoint on
  * side streams (2 = on, 1 = off) -- with CUDA events on `stream`, and keeps
  * the fastest in the context for later calls.  With the overlapped schedule
@@ -388,12 +392,12 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
  * units as its `out` (host int32[6]: SIMT sampler samples per CTA, strip
  * samples per CTA, fused-backward CTAs per instance, strip-adjoint samples
  * per CTA (1 = one warp per strip over 32 samples), tensor-core sampler
- * step-group size limit, overlapped schedule 2 on / 1 off); 0 restores the
+ * form and plan as above, overlapped schedule 2 on / 1 off); 0 restores the
  * built-in default for that entry (the overlapped schedule is on by
  * default).  Lets a caller reuse an earlier tuning without re-timing.  Not in
  * the paper.
  * Errors: TNVAN_E_ARG (NULL, or a value outside the candidates the autotuner
- * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {8,16,32}, {1,2}). */
+ * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {4,6,8,12,16,32}, {1,2}). */
 int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* choices);
 
 /* Optional device step counter (not in the paper; for CUDA-graph capture).

@@ -551,6 +551,10 @@ int pick_tc_plan(const tnvan_ctx* ctx);
 // Every instance has a tensor-core sampler plan and all share one number of
 // hidden layers (one kernel instantiation per launch).
 bool tc_sampler_usable(const tnvan_ctx* ctx);
+// Every instance fits the grouped form (the fast path).
+bool tc_grouped_usable(const tnvan_ctx* ctx);
+int tc_plan_value(const tnvan_ctx* ctx, int p);
+int tc_sampler_smem(const tnvan_ctx* ctx, int plan, bool grouped);
 int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, const double* d_logZR,
                   const float* d_logq, int precision, float* d_grad_params, double* d_dbeta, double* d_dJ,
                   cudaStream_t s, bool pack, const AdamArgs* adam, bool stats_ready = false);
@@ -1246,6 +1250,22 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
         rec.insert(rec.end(), r16, r16 + TNVAN_TCG_INTS);
         i0 = i1;
       }
+      // in-step weights of every step (the layer-1 -> layer-2 block, then the
+      // last hidden layer -> output i row)
+      std::vector<int> soff(D + 1, 0), ssrc;
+      for (int i = 0; i < D; ++i) {
+        soff[i] = (int)ssrc.size();
+        const int ua = before(c1, i), ub = before(c1, i + 1);
+        if (n_hidden == 2) {
+          const int va = before(c2, i), vb = before(c2, i + 1);
+          for (int v = va; v < vb; ++v)
+            for (int u = ua; u < ub; ++u) ssrc.push_back((int)(md.layer[1].dst_off + (long long)v * H[0] + u));
+          for (int v = va; v < vb; ++v) ssrc.push_back((int)(wofs + (long long)i * Hl + v));
+        } else {
+          for (int u = ua; u < ub; ++u) ssrc.push_back((int)(wofs + (long long)i * Hl + u));
+        }
+      }
+      soff[D] = (int)ssrc.size();
       const int need_cols = tcw1 + (n_hidden == 2 ? H[1] : 0) + Dp;
       int cols = 32;
       while (cols < need_cols) cols *= 2;
@@ -1259,6 +1279,18 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       cudaError_t e2 = cudaMalloc(&blob, std::max<size_t>(src.size(), 8) * sizeof(uint16_t));
       if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blobs): %s", cudaGetErrorString(e2));
       in.dev_allocs.push_back(blob);
+      int* dsoff = nullptr;
+      if ((rc = upload(ctx, in, soff, &dsoff))) return rc;
+      int* dssrc = nullptr;
+      if (!ssrc.empty() && (rc = upload(ctx, in, ssrc, &dssrc))) return rc;
+      void* stab = nullptr;
+      e2 = cudaMalloc(&stab, std::max<size_t>(ssrc.size(), 1) * sizeof(float));
+      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler step tables): %s", cudaGetErrorString(e2));
+      in.dev_allocs.push_back(stab);
+      P.steptab = static_cast<float*>(stab);
+      P.stepsrc = dssrc;
+      P.stepoff = dsoff;
+      P.n_steptab = (int)ssrc.size();
       P.n_chunks = (int)rec.size() / TNVAN_TCG_INTS;
       P.chunks = drec;
       P.wblob = static_cast<uint16_t*>(blob);
@@ -1276,6 +1308,79 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       P.ok = sample_tc_smem_bytes(probe, p) <= 227 * 1024;
     }
   }
+  // Step groups of the grouped tensor-core sampler (the fast path for two
+  // hidden layers of <= 128 units and D <= 128, a multiple of 16), one plan
+  // per group-size limit (kTcGroupMaxG): at most that many steps and 32 units
+  // of each hidden layer completing inside a group.  Per group the in-group
+  // triangles and the group's biases, each row padded to a multiple of 4
+  // floats, and a record of TNVAN_TCGG_INTS ints (bounds, offsets and the
+  // per-step unit counts) that the kernel bulk-copies one group ahead.
+  for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+    MadeDev::TcGroupPlan& P = md.tcg[p];
+    P = MadeDev::TcGroupPlan{};
+    if (!md.wtiles || n_hidden != 2) continue;
+    const int GMAX = kTcGroupMaxG[p], UGMAX = 32;
+    auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
+    auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
+    std::vector<int> grp, src;
+    int twmax = 0, tcw1 = 16, tcw2 = 16;
+    bool fits = true;
+    auto add_tile = [&](int rlo, int rhi, int clo, int chi, long long wofs, int stride) {
+      const int off = (int)src.size();
+      const int rw = (chi - clo + 3) & ~3;
+      for (int r = rlo; r < rhi; ++r)
+        for (int c = 0; c < rw; ++c) src.push_back(c < chi - clo ? (int)(wofs + (long long)r * stride + clo + c) : -1);
+      return off;
+    };
+    for (int i0 = 0; i0 < D;) {
+      int i1 = i0 + 1;
+      while (i1 < D && i1 - i0 < GMAX && cnt(c1, i0, i1 + 1) <= UGMAX && cnt(c2, i0, i1 + 1) <= UGMAX) ++i1;
+      const int u1lo = before(c1, i0), u1hi = before(c1, i1);
+      const int u2lo = before(c2, i0), u2hi = before(c2, i1);
+      fits = fits && u1hi - u1lo <= UGMAX && u2hi - u2lo <= UGMAX;
+      const int gstart = (int)src.size();
+      add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
+      const int t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
+      const int to = add_tile(i0, i1, u2lo, u2hi, md.layer[2].dst_off, H[1]);
+      // the group's biases (gathered with the triangles)
+      const int b1o = add_tile(0, 1, u1lo, u1hi, md.layer[0].dst_off + (long long)H[0] * D, 0);
+      const int b2o = add_tile(0, 1, u2lo, u2hi, md.layer[1].dst_off + (long long)H[1] * H[0], 0);
+      const int boo = add_tile(0, 1, i0, i1, md.layer[2].dst_off + (long long)D * H[1], 0);
+      const int gsize = (int)src.size() - gstart;
+      twmax = std::max(twmax, gsize);
+      tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
+      tcw2 = std::max(tcw2, ((u2hi + 15) & ~15) - (u2lo & ~15));
+      int rec[TNVAN_TCGG_INTS] = {i0, i1, u1lo, u1hi, u2lo, u2hi, gstart, gsize, t2 - gstart, to - gstart,
+                                  b1o - gstart, b2o - gstart, boo - gstart};
+      for (int q = 0; q <= i1 - i0; ++q) {  // units with degree < i0 + q
+        rec[13 + q] = before(c1, i0 + q);
+        rec[22 + q] = before(c2, i0 + q);
+      }
+      grp.insert(grp.end(), rec, rec + TNVAN_TCGG_INTS);
+      i0 = i1;
+    }
+    int* dgrp = nullptr;
+    if ((rc = upload(ctx, in, grp, &dgrp))) return rc;
+    int* dsrc = nullptr;
+    if ((rc = upload(ctx, in, src, &dsrc))) return rc;
+    void* blk = nullptr;
+    if (!src.empty()) {
+      cudaError_t e2 = cudaMalloc(&blk, src.size() * sizeof(float));
+      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler triangles): %s", cudaGetErrorString(e2));
+      in.dev_allocs.push_back(blk);
+    }
+    P.n_groups = (int)grp.size() / TNVAN_TCGG_INTS;
+    P.groups = dgrp;
+    P.blocks = static_cast<float*>(blk);
+    P.src = dsrc;
+    P.n_blk = (long long)src.size();
+    P.twmax = twmax;
+    P.tcw1 = tcw1;
+    P.tcw2 = tcw2;
+    P.ok = fits && D <= 128 && sample_tcg_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
+  }
+  md.sample_tcg_ok = 0;
+  for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tcg_ok = md.sample_tcg_ok || md.tcg[p].ok;
   md.sample_tc_ok = 0;
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tc_ok = md.sample_tc_ok || md.tc[p].ok;
   void* packed = nullptr;
@@ -1494,9 +1599,10 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
   li.seed = seed;
   li.step = step;
   if ((rc = fill_launch(ctx, betas, batch, adj_tile, la))) return rc;
-  int smem = 0, max_edges = 0;
+  const bool grouped = tc_grouped_usable(ctx);
+  const int smem = tc_sampler_smem(ctx, plan, grouped);
+  int max_edges = 0;
   for (const Instance& in : ctx->inst) {
-    smem = std::max(smem, sample_tc_smem_bytes(in.dev.made, plan));
     max_edges = std::max(max_edges, in.m);
   }
   const int stride = (max_edges + 3) & ~3;
@@ -1511,9 +1617,14 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
     const int k0 = c * n / nc, k1 = (c + 1) * n / nc;
     {
       PROF("sample_tc", ctx->side[c]);
-      CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
-                          li.tile_begin[k1]),
-         "tensor-core sample kernel");
+      if (grouped)
+        CK(launch_sample_tcg(ctx->d_inst, li, plan, smem, d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
+                             li.tile_begin[k1]),
+           "tensor-core sample kernel");
+      else
+        CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, nullptr,
+                            ctx->side[c], li.tile_begin[k0], li.tile_begin[k1]),
+           "tensor-core sample kernel");
     }
     CK(cudaEventRecord(ctx->chunk_ev[c], ctx->side[c]), "chunk event");
     // the chunk's strip tables need no samples: built while its sampler runs
@@ -2039,24 +2150,32 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
   };
   auto sample = [&]() { return tnvan_sample_and_contract(ctx, betas, batch, 1, 0, precision, sp, lq, lz, stream); };
   bool tc_sampler = precision == TNVAN_BF16;
+  ctx->tune_tc_form = 0;
   tc_sampler = tc_sampler && tc_sampler_usable(ctx);
-  if (tc_sampler) {
-    int best = -1;
+  if (tc_sampler) {  // every plan of both forms that fits every instance
+    int best = -1, best_form = 0;
     float best_ms = 1e30f;
-    for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
-      ctx->tune_tc_plan = p;
-      if (pick_tc_plan(ctx) != p) continue;
-      float ms = 0.f;
-      if ((rc = time_it(sample, &ms))) {
-        cleanup();
-        return rc;
-      }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = p;
+    for (int form = 1; form <= 2; ++form) {
+      ctx->tune_tc_form = form;
+      if (form == 1 && !tc_grouped_usable(ctx)) continue;
+      if (form == 2 && !tc_sampler_usable(ctx)) continue;
+      for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+        ctx->tune_tc_plan = p;
+        if (pick_tc_plan(ctx) != p) continue;
+        float ms = 0.f;
+        if ((rc = time_it(sample, &ms))) {
+          cleanup();
+          return rc;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = p;
+          best_form = form;
+        }
       }
     }
     ctx->tune_tc_plan = best;
+    ctx->tune_tc_form = best >= 0 ? best_form : 0;
   }
   if (!tc_sampler) {
     int best = 0;
@@ -2272,7 +2391,7 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     out[1] = ctx->tune_strip_tile;
     out[2] = ctx->tune_bwd_ctas;
     out[3] = ctx->tune_adj_tile;
-    out[4] = ctx->tune_tc_plan >= 0 ? kTcGroupMax[ctx->tune_tc_plan] : 0;
+    out[4] = tc_plan_value(ctx, ctx->tune_tc_plan);
     out[5] = ctx->tune_overlap ? 2 : 1;
   }
   cudaError_t e = cudaStreamSynchronize(s);
@@ -2290,9 +2409,12 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
       if (v == o) return true;
     return false;
   };
-  int plan = -1;
-  for (int p = 0; p < TNVAN_TC_PLANS; ++p)
-    if (kTcGroupMax[p] == c[4]) plan = p;
+  // the plan value names the form: grouped 4, 6, 8 steps, per-step chunks 12, 16, 32
+  int plan = -1, form = 0;
+  for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+    if (kTcGroupMaxG[p] == c[4]) plan = p, form = 1;
+    if (kTcGroupMax[p] == c[4]) plan = p, form = 2;
+  }
   if (!in(c[0], {16, 32, 64}) || !in(c[1], {32, 64, 128}) || c[2] < 0 || !in(c[3], {1, 32, 64, 96, 128}) ||
       (c[4] != 0 && plan < 0) || c[5] < 0 || c[5] > 2)
     return fail(ctx, TNVAN_E_ARG, "tuning value outside the autotuner's candidates");
@@ -2301,6 +2423,7 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
   ctx->tune_bwd_ctas = c[2];
   ctx->tune_adj_tile = c[3];
   ctx->tune_tc_plan = plan;
+  ctx->tune_tc_form = form;
   ctx->tune_overlap = c[5] != 1;  // 0 and 2 (default) on, 1 off
   return TNVAN_OK;
 }
@@ -2369,25 +2492,56 @@ int sampler_pack_mask(const tnvan_ctx* ctx, int precision) {
   bool tc_all = precision == TNVAN_BF16;
   tc_all = tc_all && tc_sampler_usable(ctx);
   const int plan = tc_all ? pick_tc_plan(ctx) : -1;
-  if (plan >= 0) return PACK_FLAT | PACK_TC | ((plan + 1) << 8);  // only the plan in use
+  if (plan >= 0)  // only the plan in use
+    return tc_grouped_usable(ctx) ? (PACK_FLAT | PACK_TILES | PACK_TCG | ((plan + 1) << 8))
+                                  : (PACK_FLAT | PACK_TC | ((plan + 1) << 8));
   return PACK_FLAT | PACK_SIMT;
+}
+
+bool tc_grouped_usable(const tnvan_ctx* ctx) {
+  if (ctx->inst.empty() || ctx->tune_tc_form == 2) return false;
+  for (const Instance& in : ctx->inst)
+    if (!in.dev.made.sample_tcg_ok) return false;
+  return true;
 }
 
 bool tc_sampler_usable(const tnvan_ctx* ctx) {
   if (ctx->inst.empty()) return false;
+  if (tc_grouped_usable(ctx)) return true;
   const int nh = ctx->inst[0].dev.made.nh;
   for (const Instance& in : ctx->inst)
     if (!in.dev.made.sample_tc_ok || in.dev.made.nh != nh) return false;
   return true;
 }
 
+// The tuning value of plan p (its step limit) for the sampler form in use.
+int tc_plan_value(const tnvan_ctx* ctx, int p) {
+  if (p < 0 || p >= TNVAN_TC_PLANS) return 0;
+  return tc_grouped_usable(ctx) ? kTcGroupMaxG[p] : kTcGroupMax[p];
+}
+
+// Shared memory of a tensor-core sampler launch over every instance.
+int tc_sampler_smem(const tnvan_ctx* ctx, int plan, bool grouped) {
+  int smem = 0;
+  for (const Instance& in : ctx->inst) {
+    if (grouped) {
+      const MadeDev::TcGroupPlan& P = in.dev.made.tcg[plan];
+      smem = std::max(smem, sample_tcg_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax));
+    } else {
+      smem = std::max(smem, sample_tc_smem_bytes(in.dev.made, plan));
+    }
+  }
+  return smem;
+}
+
 // Tensor-core sampler plan usable by every instance: the autotuned one, else
 // the largest group-size limit that fits, else -1 (SIMT sampler).
 int pick_tc_plan(const tnvan_ctx* ctx) {
+  const bool grouped = tc_grouped_usable(ctx);
   auto usable = [&](int p) {
     if (p < 0 || p >= TNVAN_TC_PLANS) return false;
     for (const Instance& in : ctx->inst)
-      if (!in.dev.made.tc[p].ok) return false;
+      if (!(grouped ? in.dev.made.tcg[p].ok : in.dev.made.tc[p].ok)) return false;
     return true;
   };
   if (usable(ctx->tune_tc_plan)) return ctx->tune_tc_plan;
@@ -2408,13 +2562,14 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
     if ((rc = fill_launch(ctx, betas, batch, 128, li))) return rc;
     li.seed = seed;
     li.step = step;
-    int smem = 0;
-    for (const Instance& in : ctx->inst) {
-      smem = std::max(smem, sample_tc_smem_bytes(in.dev.made, plan));
-    }
+    const bool grouped = tc_grouped_usable(ctx);
+    const int smem = tc_sampler_smem(ctx, plan, grouped);
     PROF(given ? "log_prob_tc" : "sample_tc", s);
-    CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, given, s),
-       "tensor-core sample kernel");
+    if (grouped)
+      CK(launch_sample_tcg(ctx->d_inst, li, plan, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
+    else
+      CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, given, s),
+         "tensor-core sample kernel");
     return TNVAN_OK;
   }
   const int tile = pick_sample_tile(ctx);

@@ -15,12 +15,17 @@
 #define TNVAN_MAX_STRIP_W 4
 #define TNVAN_MAX_ELIM_W 12
 #define GROUP_INTS 15
-#define TNVAN_TC_PLANS 3  // step-chunk size limits of the tensor-core sampler: 8, 16, 32
+#define TNVAN_TC_PLANS 3  // tensor-core sampler plans: grouped 4, 6, 8 steps; per-step chunks 12, 16, 32
 // Tensor-core sampler chunk record: i0 i1 (steps), w1c n1c (16-aligned window
 // of the chunk's layer-1 units), w2c n2c (layer 2), kSc (K width of the W1
 // rows: spins 0 .. kSc-1), blob offset (BF16 elements, a multiple of 8), the
 // blob's three part sizes in bytes (W2 window, Wo window, W1 rows), pad.
 #define TNVAN_TCG_INTS 16
+// Grouped tensor-core sampler group record: i0 i1 u1lo u1hi u2lo u2hi, block
+// start and size (floats), offsets of TW2 TWo b1 b2 bo in the block, then c1
+// and c2 at the group's steps (9 each: units with degree < i0 + q, q = 0..8),
+// pad.
+#define TNVAN_TCGG_INTS 32
 
 namespace tnvan {
 
@@ -73,7 +78,29 @@ struct MadeDev {
     int dw1, dw2;         // widest per-step unit window (delta tiles), layers 1 and 2
     int wbmax;            // largest chunk blob (bytes)
     int tmem_cols;        // TMEM allocation of a CTA
+    // In-step weights of every step i (FP32, gathered on every call): from
+    // its layer-1 units to its layer-2 units [nv][nu], then from its last
+    // hidden layer's units to output i [nv] (one hidden layer: [nu]).
+    float* steptab;
+    const int* stepsrc;   // [n_steptab] index into the packed network
+    const int* stepoff;   // [D + 1] offset of step i's table
+    int n_steptab;
   } tc[TNVAN_TC_PLANS];
+  // Grouped tensor-core sampler (the fast path for two hidden layers of
+  // <= 128 units and D <= 128, a multiple of 16): one step-group plan per
+  // group-size limit.  Per group only the in-group triangles, rows padded to
+  // 4 floats: TW1 [n1g][r4(gi)], TW2 [n2g][r4(n1g)], TWo [gi][r4(n2g)].
+  struct TcGroupPlan {
+    int ok;               // eligible (unit counts within the kernel's limits)
+    int n_groups;
+    const int* groups;    // [n_groups][TNVAN_TCGG_INTS]
+    float* blocks;        // gathered from `packed` on every call
+    const int* src;       // [n_blk] index into `packed`, -1 = zero
+    long long n_blk;
+    int twmax;            // largest group (floats)
+    int tcw1, tcw2;       // widest 16-aligned unit window of a group, layers 1 and 2
+  } tcg[TNVAN_TC_PLANS];
+  int sample_tcg_ok;      // eligible for the grouped sampler
   float* blocks;          // blocked weights (gathered from `packed` every call)
   const int* blk_src;     // [n_blk] index into `packed`, -1 = zero
   long long n_blk;
@@ -271,6 +298,7 @@ struct tnvan_ctx {
   // autotuned launch shapes (0 = built-in heuristic)
   int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0, tune_adj_tile = 0;
   int tune_tc_plan = -1;  // tensor-core sampler step-group plan (-1 = default)
+  int tune_tc_form = 0;   // tensor-core sampler form: 0 automatic, 1 grouped, 2 per-step
   int tune_overlap = 1;   // overlapped sampling + adjoint schedule (1 on, 0 off)
   // last strip-adjoint launch plan (valid while batch, tuning and instances are unchanged)
   struct {
@@ -308,7 +336,7 @@ struct tnvan_ctx {
 namespace tnvan {
 
 // Kernel launchers (defined in the .cu files).  All return a cudaError_t.
-enum { PACK_FLAT = 1, PACK_TILES = 2, PACK_SIMT = 4, PACK_TC = 8 };
+enum { PACK_FLAT = 1, PACK_TILES = 2, PACK_SIMT = 4, PACK_TC = 8, PACK_TCG = 16 };
 long long pack_elems(const MadeDev& md, int mask);
 cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s);
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
@@ -391,6 +419,10 @@ cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int pl
                              int blk_end = -1);
 int sample_tc_smem_bytes(const MadeDev& md, int plan);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
+cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
+                              float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
+int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
+extern const int kTcGroupMaxG[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 
 int sample_smem_bytes(const Instance& in, int tile);

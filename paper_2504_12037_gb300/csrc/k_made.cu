@@ -57,8 +57,10 @@ __device__ __forceinline__ void store_tile(const MadeDev& md, int l, int r, int 
 //   PACK_TILES BF16 tiles in the tensor cores' canonical K-major layout (no
 //              swizzle): W1 [H1 x D], W2 [H2 x H1], Wo [D x H2]
 //   PACK_SIMT  the blocked SIMT sampler's weight blocks
-//   PACK_TC    the tensor-core sampler plans' BF16 chunk weight blobs (one
+//   PACK_TCG   the grouped tensor-core sampler plans' triangle tiles (one
 //              plan, or all, per pack_tc_plan)
+//   PACK_TC    the per-step tensor-core sampler plans' BF16 chunk weight
+//              blobs and FP32 in-step weight tables (likewise)
 __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
   const MadeDev& md = inst[blockIdx.y].made;
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,6 +116,19 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
     }
     e -= md.n_blk;
   }
+  if (mask & PACK_TCG) {
+    const int only = pack_tc_plan(mask);
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
+      if (only >= 0 && p != only) continue;
+      const MadeDev::TcGroupPlan& P = md.tcg[p];
+      if (e < P.n_blk) {
+        const int j = P.src[e];
+        P.blocks[e] = j >= 0 ? packed_value(md, j) : 0.f;
+        return;
+      }
+      e -= P.n_blk;
+    }
+  }
   if (mask & PACK_TC) {
     const int only = pack_tc_plan(mask);
     for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
@@ -127,6 +142,11 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
         return;
       }
       e -= P.n_wblob;
+      if (e < P.n_steptab) {
+        P.steptab[e] = packed_value(md, P.stepsrc[e]);
+        return;
+      }
+      e -= P.n_steptab;
     }
   }
 }
@@ -137,10 +157,15 @@ long long pack_elems(const MadeDev& md, int mask) {
   if (mask & PACK_FLAT) n += md.n_params;
   if (tiles && !(mask & PACK_FLAT)) n += tile_elems(md);
   if (mask & PACK_SIMT) n += md.n_blk;
+  if (mask & PACK_TCG) {
+    const int only = pack_tc_plan(mask);
+    for (int p = 0; p < TNVAN_TC_PLANS; ++p)
+      if (only < 0 || p == only) n += md.tcg[p].n_blk;
+  }
   if (mask & PACK_TC) {
     const int only = pack_tc_plan(mask);
     for (int p = 0; p < TNVAN_TC_PLANS; ++p)
-      if (only < 0 || p == only) n += md.tc[p].n_wblob;
+      if (only < 0 || p == only) n += md.tc[p].n_wblob + md.tc[p].n_steptab;
   }
   return n;
 }

@@ -1,0 +1,476 @@
+// BF16 ancestral sampler on tcgen05 (Eq. 6-8), grouped form, for networks
+// with two hidden layers of at most 128 units and at most 128 inputs (a
+// multiple of 16): the fast path where it applies; k_sample_tc.cu holds the
+// general per-step form.
+//
+// One CTA (128 threads, thread = sample = TMEM lane) draws 128 samples; its
+// TMEM footprint is at most 256 columns and its shared memory about 100 KB
+// for the 64-128-128-64 network, so two CTAs share an SM.  TMEM holds
+//   P1g [128 x w1]  layer-1 pre-activations of the current step group's units
+//                   from every spin before the group, recomputed per group as
+//                   S W1_g^T (S = the spin tile so far, zero beyond);
+//   P2  [128 x H2]  layer-2 pre-activations, accumulated over the groups;
+//   PO  [128 x D]   output pre-activations, accumulated over the groups.
+// Steps are processed in the host's step groups.  Inside a group, each step
+// reads the pre-activations of the units completing at that step straight
+// from TMEM (tcgen05.ld), adds the in-group contributions on the CUDA cores
+// (FP32 triangle tiles of the group, bulk-copied into shared memory; in-group
+// spins from a register bitmask, in-group hidden values from the BF16 fold
+// tiles), and draws s_i = +1 iff u < sigmoid(x_i).  After the group one
+// tcgen05.mma chain folds its hidden values into the accumulators and
+// recomputes P1g for the next group:
+//   P2 += H1_g W2_g^T,  PO += H2_g Wo_g^T,  P1g' = S W1_g'^T.
+// Every hidden value enters every later product as BF16 with FP32
+// accumulation; in-group arithmetic is FP32 on the same BF16 values.
+//
+// The spin tile S and the fold tiles H1_g, H2_g are MN-major MMA operands in
+// which consecutive 8-sample core-matrix groups are 16 bytes apart modulo
+// 128, so the per-sample stores and loads (one 2-byte element per thread)
+// are free of bank conflicts.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace tnvan {
+
+namespace {
+
+// MN-major operand tile of 128 rows (samples) and kw columns (K, a multiple
+// of 16): element (m, k) at (m >> 3) * sbo + (k >> 3) * 128 + (k & 7) * 16 +
+// (m & 7) * 2 = (m >> 3) * sbo + (m & 7) * 2 + 16 k.
+__host__ __device__ __forceinline__ uint32_t mn_sbo(int kw) { return (uint32_t)kw * 16u + 16u; }
+__device__ __forceinline__ void st_bf16(unsigned char* base, uint32_t o, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + o) = __float2bfloat16(v);
+}
+__device__ __forceinline__ float ld_bf16(const unsigned char* base, uint32_t o) {
+  return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + o));
+}
+
+// One TMEM column of the warp's 32 lanes into a register, without waiting;
+// tmem_wait9 / tmem_wait1 order every later use of the destinations after
+// the wait.
+__device__ __forceinline__ void tmem_ld1_nowait(uint32_t taddr, uint32_t& r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait9(uint32_t (&a)[4], uint32_t (&b)[4], uint32_t& c) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]),
+                 "+r"(c)::"memory");
+}
+__device__ __forceinline__ void tmem_wait1(uint32_t& c) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(c)::"memory");
+}
+__device__ __forceinline__ float pick4(const uint32_t (&r)[4], int j) {
+  const uint32_t v = j == 0 ? r[0] : (j == 1 ? r[1] : (j == 2 ? r[2] : r[3]));
+  return __uint_as_float(v);
+}
+
+}  // namespace
+
+#define STC_GI 8   // most steps in a group
+
+const int kTcGroupMaxG[TNVAN_TC_PLANS] = {4, 6, 8};
+
+struct SampleTcgLayout {
+  int wbytes, oS, oH1, oH2, oBuf, buf, oBar, total;
+};
+
+__host__ __device__ inline SampleTcgLayout sample_tcg_layout(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
+  SampleTcgLayout L;
+  L.wbytes = 2 * (H1 * D + H2 * H1 + D * H2);
+  int p = (L.wbytes + 127) & ~127;
+  L.oS = p;
+  p += 16 * (int)mn_sbo(D);
+  L.oH1 = p;
+  p += 16 * (int)mn_sbo(tcw1) + 64;  // + zeroed tail read by the 4-wide in-group loops
+  L.oH2 = p;
+  p += 16 * (int)mn_sbo(tcw2) + 64;
+  // two group buffers (this group's, the next group's): the record then the
+  // triangles and biases
+  L.oBuf = p;
+  L.buf = 4 * TNVAN_TCGG_INTS + 4 * ((twmax + 3) & ~3);
+  p += 2 * L.buf;
+  p = (p + 15) & ~15;
+  L.oBar = p;
+  p += 32;
+  L.total = p;
+  return L;
+}
+
+__host__ __device__ inline int sample_tcg_tmem_cols(int D, int H2, int tcw1) {
+  return tcw1 + H2 + D <= 256 ? 256 : 512;
+}
+
+__global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __restrict__ inst,
+                                                           const LaunchInfo li, int plan,
+                                                           int8_t* __restrict__ spins, float* __restrict__ logq,
+                                                           const int8_t* __restrict__ given) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int gblk = blockIdx.x + li.blk0;
+  const int k = find_inst(li, gblk);
+  const InstDev& I = inst[k];
+  const MadeDev& md = I.made;
+  const MadeDev::TcGroupPlan& P = md.tcg[plan];
+  const int D = md.D, H1 = md.H1, H2 = md.H2;
+  const int t = threadIdx.x, w = t >> 5;
+  const int b = (gblk - li.tile_begin[k]) * 128 + t;
+  const bool valid = b < li.batch;
+  const SampleTcgLayout LY = sample_tcg_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax);
+  unsigned char* sW1 = smem;
+  unsigned char* sW2 = sW1 + 2 * H1 * D;
+  unsigned char* sWo = sW2 + 2 * H2 * H1;
+  unsigned char* sS = smem + LY.oS;
+  unsigned char* sH1 = smem + LY.oH1;
+  unsigned char* sH2 = smem + LY.oH2;
+  unsigned char* gbuf0 = smem + LY.oBuf;
+  unsigned char* gbuf1 = gbuf0 + LY.buf;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + LY.oBar);  // MMA completion
+  uint64_t* cbar = bar + 1;                                     // bulk copies
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const uint32_t sboS = mn_sbo(D), sbo1 = mn_sbo(P.tcw1), sbo2 = mn_sbo(P.tcw2);
+  // this thread's row in the MN-major tiles: element k at row base + 16 k
+  const uint32_t rowb = (uint32_t)(t & 7) * 2u;
+  const uint32_t rbS = (uint32_t)(t >> 3) * sboS + rowb, rb1 = (uint32_t)(t >> 3) * sbo1 + rowb,
+                 rb2 = (uint32_t)(t >> 3) * sbo2 + rowb;
+  const uint32_t kbW1 = 2u * D / 16u * 128u, kbW2 = 2u * H1 / 16u * 128u, kbWo = 2u * H2 / 16u * 128u;
+  const int ncols = sample_tcg_tmem_cols(D, H2, P.tcw1);
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_init(cbar, 1);
+  }
+  if (w == 0) {
+    tc::tmem_alloc(slot, (uint32_t)ncols);
+    tc::tmem_relinquish();
+  }
+  // the spin tile starts at zero (spins not drawn yet contribute nothing);
+  // the fold tiles too (later groups zero only the columns they do not write)
+  for (int o = t * 16; o < 16 * (int)sboS; o += 128 * 16)
+    *reinterpret_cast<uint4*>(sS + o) = make_uint4(0, 0, 0, 0);
+  for (int o = t * 16; o < 16 * (int)sbo1 + 64; o += 128 * 16)
+    *reinterpret_cast<uint4*>(sH1 + o) = make_uint4(0, 0, 0, 0);
+  for (int o = t * 16; o < 16 * (int)sbo2 + 64; o += 128 * 16)
+    *reinterpret_cast<uint4*>(sH2 + o) = make_uint4(0, 0, 0, 0);
+  fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  uint32_t cphase = 0;
+  bool copy_pending = false, mma_pending = false;
+  // group gg's record and block into a group buffer (one thread; the caller
+  // has armed cbar for `extra` more bytes)
+  auto copy_group = [&](int gg, unsigned char* dst, uint32_t extra) {
+    const int* Gg = P.groups + TNVAN_TCGG_INTS * gg;
+    const uint32_t nb = (uint32_t)__ldg(Gg + 7) * 4u;
+    mbar_expect_tx(cbar, extra + 4u * TNVAN_TCGG_INTS + nb);
+    bulk_g2s(dst, Gg, 4u * TNVAN_TCGG_INTS, cbar);
+    if (nb) bulk_g2s(dst + 4 * TNVAN_TCGG_INTS, P.blocks + __ldg(Gg + 6), nb, cbar);
+  };
+  if (t == 0) {
+    copy_group(0, gbuf0, (uint32_t)LY.wbytes);
+    bulk_g2s(sW1, md.wtiles, (uint32_t)LY.wbytes, cbar);
+  }
+  copy_pending = true;
+  const uint32_t tmem = *slot;
+  const uint32_t lane_off = (uint32_t)(w * 32) << 16;
+  const uint32_t tP1 = tmem + lane_off, tP2 = tP1 + (uint32_t)P.tcw1, tPO = tP2 + (uint32_t)H2;
+  const uint32_t idA = 1u << 15;  // A operand MN-major
+  const uint32_t id2 = tc::idesc(128, H2, 1u) | idA, ido = tc::idesc(128, D, 1u) | idA;
+  const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
+  const uint32_t step32 = launch_step(li);
+  const int8_t* gv = given ? given + I.spin_units * li.batch + (long long)b * D : nullptr;
+  uint32_t phase = 0;
+  bool ok = true;
+  bool p1ok = false, init2 = false, inito = false;  // accumulator holds data
+  float lq = 0.f;
+  uint4 rnd = make_uint4(0, 0, 0, 0);
+  unsigned long long sb0 = 0ull, sb1 = 0ull;  // spin i is +1 iff bit i is set
+  for (int g = 0; g < P.n_groups; ++g) {
+    unsigned char* gb = (g & 1) ? gbuf1 : gbuf0;      // this group's buffer
+    unsigned char* gbn = (g & 1) ? gbuf0 : gbuf1;     // the next group's
+    if (copy_pending) {  // group 0 (with the weights); later groups arrived during the previous group
+      if (mbar_wait(cbar, cphase)) {
+        cphase ^= 1u;
+        copy_pending = false;
+      } else {
+        ok = false;
+      }
+    }
+    const int* G = reinterpret_cast<const int*>(gb);
+    const float* TWb = reinterpret_cast<const float*>(gb + 4 * TNVAN_TCGG_INTS);
+    const int i0 = G[0], i1 = G[1], u1lo = G[2], u1hi = G[3], u2lo = G[4], u2hi = G[5];
+    const int gi = i1 - i0, n1g = u1hi - u1lo, n2g = u2hi - u2lo;
+    const int w1 = u1lo & ~15, w2 = u2lo & ~15;
+    const int n1 = ((u1hi + 15) & ~15) - w1, n2 = ((u2hi + 15) & ~15) - w2;
+    // the previous MMA chain is done: fold tiles free, accumulators and P1g final
+    if (mma_pending) {
+      if (mbar_wait(bar, phase)) {
+        phase ^= 1u;
+        mma_pending = false;
+      } else {
+        ok = false;
+      }
+      tc::fence_after_sync();
+    }
+    // the fold's K windows must be zero outside the units this group writes:
+    // columns [0, u_lo - w) and [u_hi - w, n) of every 8-sample row group
+    {
+      const int lo1 = u1lo - w1, hi1 = u1hi - w1, p1 = lo1 + (n1 - hi1);
+      const int lo2 = u2lo - w2, hi2 = u2hi - w2, p2 = lo2 + (n2 - hi2);
+      // f / pn by a multiply and a shift: f < 16 pn <= 512 and r = ceil(2^16 / pn)
+      // give floor(f r / 2^16) = floor(f / pn) exactly
+      const uint32_t r1 = p1 ? (65535u + (uint32_t)p1) / (uint32_t)p1 : 0u;
+      const uint32_t r2 = p2 ? (65535u + (uint32_t)p2) / (uint32_t)p2 : 0u;
+      for (int e = t; e < 16 * (p1 + p2); e += 128) {
+        const bool l1 = e < 16 * p1;
+        const int f = l1 ? e : e - 16 * p1, pn = l1 ? p1 : p2, lo = l1 ? lo1 : lo2, hi = l1 ? hi1 : hi2;
+        const int rg = (int)(((uint32_t)f * (l1 ? r1 : r2)) >> 16), j = f - rg * pn;
+        const int col = j < lo ? j : hi + (j - lo);
+        *reinterpret_cast<uint4*>((l1 ? sH1 : sH2) + rg * (l1 ? sbo1 : sbo2) + 16 * col) = make_uint4(0, 0, 0, 0);
+      }
+    }
+    ok = __syncthreads_and(ok) != 0;  // zeroed fold tiles visible; one agreed flag
+    if (!ok) break;
+    if (t == 0 && g + 1 < P.n_groups) {  // the next group's data, while this group runs
+      copy_group(g + 1, gbn, 0u);
+    }
+    if (g + 1 < P.n_groups) copy_pending = true;
+    const float* TW1 = TWb;
+    const float* TW2 = TWb + G[8];
+    const float* TWo = TWb + G[9];
+    const float* gb1 = TWb + G[10];  // biases of the group's units
+    const float* gb2 = TWb + G[11];
+    const float* gbo = TWb + G[12];
+    const int* gc1 = G + 13;  // c1[i], c2[i] for i = i0-1 .. i1-1
+    const int* gc2 = G + 22;
+    const int s1 = (gi + 3) & ~3, s2 = (n1g + 3) & ~3, so = (n2g + 3) & ~3;  // triangle row strides
+    float sg[STC_GI];  // in-group spins (0 until drawn)
+#pragma unroll
+    for (int j = 0; j < STC_GI; ++j) sg[j] = 0.f;
+    for (int i = i0; i < i1; ++i) {
+      if ((i & 3) == 0)
+        rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
+      const int q = i - i0;  // gc*[q] = c*[i-1], gc*[q+1] = c*[i]
+      const int ua = gc1[q], ub = gc1[q + 1], va = gc2[q], vb = gc2[q + 1];
+      // pre-activations of the units completing at step i (up to four per layer at once)
+      uint32_t ra[4] = {0u, 0u, 0u, 0u}, rb[4] = {0u, 0u, 0u, 0u}, rc = 0u;
+      if (p1ok) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (ua + j < ub) tmem_ld1_nowait(tP1 + (uint32_t)(ua + j - w1), ra[j]);
+      }
+      if (init2) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (va + j < vb) tmem_ld1_nowait(tP2 + (uint32_t)(va + j), rb[j]);
+      }
+      if (inito) tmem_ld1_nowait(tPO + (uint32_t)i, rc);
+      tmem_wait9(ra, rb, rc);
+      // layer 1: + in-group spins (q <= 7 of them; sg is 0 for the rest)
+      for (int u = ua; u < ub; ++u) {
+        float a0;
+        if (u - ua < 4) {
+          a0 = pick4(ra, u - ua);
+        } else {  // more than four units at one step
+          uint32_t rx = 0u;
+          if (p1ok) tmem_ld1_nowait(tP1 + (uint32_t)(u - w1), rx);
+          tmem_wait1(rx);
+          a0 = __uint_as_float(rx);
+        }
+        a0 += gb1[u - u1lo];
+        const float4* wr = reinterpret_cast<const float4*>(TW1 + (u - u1lo) * s1);
+        const float4 wa = wr[0];
+        const float4 wb = s1 > 4 ? wr[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float a1 = wa.y * sg[1];
+        a0 = fmaf(wa.x, sg[0], a0);
+        a0 = fmaf(wa.z, sg[2], a0);
+        a1 = fmaf(wa.w, sg[3], a1);
+        a0 = fmaf(wb.x, sg[4], a0);
+        a1 = fmaf(wb.y, sg[5], a1);
+        a0 = fmaf(wb.z, sg[6], a0);
+        a1 = fmaf(wb.w, sg[7], a1);
+        st_bf16(sH1, rb1 + 16u * (uint32_t)(u - w1), fmaxf(a0 + a1, 0.f));
+      }
+      // layer 2: + in-group layer-1 units completed so far (BF16 values, 4 at a time;
+      // units not computed yet read as 0 and carry masked weights)
+      const uint32_t o1 = rb1 + 16u * (uint32_t)(u1lo - w1);
+      auto pre2 = [&](int v) -> float {  // accumulated pre-activation + bias of layer-2 unit v
+        float a;
+        if (v - va < 4) {
+          a = pick4(rb, v - va);
+        } else {
+          uint32_t rx = 0u;
+          if (init2) tmem_ld1_nowait(tP2 + (uint32_t)v, rx);
+          tmem_wait1(rx);
+          a = __uint_as_float(rx);
+        }
+        return a + gb2[v - u2lo];
+      };
+      int v = va;
+      for (; v + 2 <= vb; v += 2) {  // two units of one step share the in-group H1 values
+        float a0 = pre2(v), b0 = pre2(v + 1);
+        const float* wr = TW2 + (v - u2lo) * s2;
+        const float* wq = wr + s2;
+        float a1 = 0.f, b1 = 0.f;
+        for (int c = 0; c < ub - u1lo; c += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+          const float4 q4 = *reinterpret_cast<const float4*>(wq + c);
+          const uint32_t o = o1 + 16u * (uint32_t)c;
+          const float h0 = ld_bf16(sH1, o), h1 = ld_bf16(sH1, o + 16u), h2 = ld_bf16(sH1, o + 32u),
+                      h3 = ld_bf16(sH1, o + 48u);
+          a0 = fmaf(w4.x, h0, a0);
+          b0 = fmaf(q4.x, h0, b0);
+          a1 = fmaf(w4.y, h1, a1);
+          b1 = fmaf(q4.y, h1, b1);
+          a0 = fmaf(w4.z, h2, a0);
+          b0 = fmaf(q4.z, h2, b0);
+          a1 = fmaf(w4.w, h3, a1);
+          b1 = fmaf(q4.w, h3, b1);
+        }
+        st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf(a0 + a1, 0.f));
+        st_bf16(sH2, rb2 + 16u * (uint32_t)(v + 1 - w2), fmaxf(b0 + b1, 0.f));
+      }
+      if (v < vb) {
+        float a0 = pre2(v);
+        const float* wr = TW2 + (v - u2lo) * s2;
+        float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int c = 0; c < ub - u1lo; c += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+          const uint32_t o = o1 + 16u * (uint32_t)c;
+          a0 = fmaf(w4.x, ld_bf16(sH1, o), a0);
+          a1 = fmaf(w4.y, ld_bf16(sH1, o + 16u), a1);
+          a2 = fmaf(w4.z, ld_bf16(sH1, o + 32u), a2);
+          a3 = fmaf(w4.w, ld_bf16(sH1, o + 48u), a3);
+        }
+        st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf((a0 + a1) + (a2 + a3), 0.f));
+      }
+      float x;
+      {
+        const float* wr = TWo + q * so;
+        const uint32_t o2 = rb2 + 16u * (uint32_t)(u2lo - w2);
+        float a0 = __uint_as_float(rc) + gbo[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int c = 0; c < vb - u2lo; c += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+          const uint32_t o = o2 + 16u * (uint32_t)c;
+          a0 = fmaf(w4.x, ld_bf16(sH2, o), a0);
+          a1 = fmaf(w4.y, ld_bf16(sH2, o + 16u), a1);
+          a2 = fmaf(w4.z, ld_bf16(sH2, o + 32u), a2);
+          a3 = fmaf(w4.w, ld_bf16(sH2, o + 48u), a3);
+        }
+        x = (a0 + a1) + (a2 + a3);
+      }
+      // one exponential for both sigmoid(x) and softplus(-s x) (fast-math forms:
+      // this kernel is the reduced-precision mode)
+      const float ex = __expf(-fabsf(x));  // in (0, 1]
+      const float rcp = __frcp_rn(1.f + ex);
+      const float pr = x >= 0.f ? rcp : ex * rcp;
+      const uint32_t word = (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
+      const float u = (float)(word >> 8) * 5.9604644775390625e-08f;
+      bool up = u < pr;
+      if (gv) up = valid ? gv[i] > 0 : true;
+      const float s = up ? 1.f : -1.f;
+#pragma unroll
+      for (int j = 0; j < STC_GI; ++j) sg[j] = j == q ? s : sg[j];
+      if (up) {
+        if (i < 64) sb0 |= 1ull << i;
+        else sb1 |= 1ull << (i - 64);
+      }
+      st_bf16(sS, rbS + 16u * (uint32_t)i, s);
+      lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
+    }
+    // fold the group; recompute P1g for the next group
+    fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (g + 1 < P.n_groups) {
+      if (mbar_wait(cbar, cphase)) {  // the next group's record (issued at this group's start)
+        cphase ^= 1u;
+        copy_pending = false;
+      } else {
+        ok = false;
+      }
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      const int* Gn = reinterpret_cast<const int*>(gbn);
+      const int w1n = Gn[2] & ~15, n1n = ((Gn[3] + 15) & ~15) - w1n;
+      const int kS = (i1 + 15) & ~15;  // spins 0 .. i1-1 (zero beyond)
+      if (t == 0) {
+        const uint32_t aS = smem_u32(sS), aH1 = smem_u32(sH1), aH2 = smem_u32(sH2);
+        for (int kk = 0; kk < n1 / 16; ++kk)
+          tc::mma_bf16(tmem + (uint32_t)P.tcw1, tc::smem_desc(aH1 + kk * 256u, 128u, sbo1),
+                       tc::smem_desc(smem_u32(sW2) + (uint32_t)((w1 >> 4) + kk) * 256u, 128u, kbW2), id2,
+                       (init2 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < n2 / 16; ++kk)
+          tc::mma_bf16(tmem + (uint32_t)(P.tcw1 + H2), tc::smem_desc(aH2 + kk * 256u, 128u, sbo2),
+                       tc::smem_desc(smem_u32(sWo) + (uint32_t)((w2 >> 4) + kk) * 256u, 128u, kbWo), ido,
+                       (inito || kk > 0) ? 1u : 0u);
+        if (n1n > 0) {
+          const uint32_t id1 = tc::idesc(128, n1n, 1u) | idA;
+          for (int kk = 0; kk < kS / 16; ++kk)
+            tc::mma_bf16(tmem,
+                         tc::smem_desc(aS + kk * 256u, 128u, sboS),
+                         tc::smem_desc(smem_u32(sW1) + (uint32_t)(w1n >> 3) * kbW1 + (uint32_t)kk * 256u, 128u, kbW1),
+                         id1, kk > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(bar);
+      }
+      mma_pending = true;
+      init2 = init2 || n1 > 0;
+      inito = inito || n2 > 0;
+      p1ok = n1n > 0;
+    }
+  }
+  if (!ok) {
+    // give the work still in flight a bounded time to finish before TMEM is freed
+    if (mma_pending) mbar_wait(bar, phase);
+    if (copy_pending) mbar_wait(cbar, cphase);
+    if (t == 0) atomicExch(li.status, 4);
+  }
+  if (ok && valid) {
+    if (spins) {
+      uint32_t* out = reinterpret_cast<uint32_t*>(spins + I.spin_units * li.batch + (long long)b * D);
+      for (int i = 0; i < D; i += 4) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int ii = i + j;
+          const bool up = ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0;
+          v |= (up ? 0x01u : 0xFFu) << (8 * j);
+        }
+        out[i >> 2] = v;
+      }
+    }
+    logq[(long long)k * li.batch + b] = lq;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, (uint32_t)ncols);
+}
+
+int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
+  const int need = sample_tcg_layout(D, H1, H2, tcw1, tcw2, twmax).total;
+  // never more resident CTAs per SM than the TMEM columns allow (228 KB of
+  // shared memory per SM, 1 KB of it reserved per CTA)
+  const int per_sm = sample_tcg_tmem_cols(D, H2, tcw1) <= 256 ? 2 : 1;
+  const int floor_bytes = 228 * 1024 / (per_sm + 1) - 1024 + 16;
+  return need > floor_bytes ? need : floor_bytes;
+}
+
+// Blocks [blk_begin, blk_end) of the launch (blk_end < 0: all).
+cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
+                             float* logq, const int8_t* given, cudaStream_t s, int blk_begin, int blk_end) {
+  if (blk_end < 0) blk_end = li.tile_begin[li.n_inst];
+  const int nblk = blk_end - blk_begin;
+  if (nblk <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(sample_tcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  LaunchInfo lc = li;
+  lc.blk0 = blk_begin;
+  sample_tcg_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, lc, plan, spins, logq, given);
+  return cudaGetLastError();
+}
+
+}  // namespace tnvan

@@ -275,7 +275,8 @@ class Context:
     def autotune(self, betas, batch: int, precision: int, stream=None):
         """Time candidate launch shapes on a synthetic batch and keep the fastest;
         returns the chosen (sampler tile, strip tile, backward CTAs, strip adjoint tile,
-        tensor-core sampler step-group size, overlapped schedule 2 on / 1 off)."""
+        tensor-core sampler plan (grouped form: 4, 6, 8 steps per group; per-step
+        form: 12, 16, 32 steps per chunk), overlapped schedule 2 on / 1 off)."""
         b, pb = _arr(betas, np.float64)
         out = (ctypes.c_int32 * 6)()
         self._check(lib().tnvan_autotune(self._h, pb, batch, precision, _stream(stream), out))

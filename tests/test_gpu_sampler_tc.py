@@ -30,8 +30,10 @@ def _workload(cfg):
     return wl.workload(cfg, n_instances=10) if cfg == 5 else wl.workload(cfg)
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
-@pytest.mark.parametrize("chunk", [8, 16, 32])
+# plan values: the grouped form (4, 6, 8 steps per group; workload 2's
+# shapes only) and the per-step form (12, 16, 32 steps per chunk; every shape)
+@pytest.mark.parametrize("cfg,chunk", [(c, v) for c in (1, 2, 3, 4, 5) for v in (12, 16, 32)] +
+                         [(2, 4), (2, 6), (2, 8)])
 def test_tc_log_prob_matches_oracle_every_workload(cfg, chunk):
     w = _workload(cfg)
     model = _model(w)
@@ -58,12 +60,13 @@ def test_tc_log_prob_matches_oracle_every_workload(cfg, chunk):
     print(f"workload {cfg} chunk {chunk}: max |delta log q| / N = {worst:.2e}")
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3, 4, 5])
-def test_tc_sampler_own_samples_against_oracle(cfg):
+@pytest.mark.parametrize("cfg,plan", [(1, 0), (2, 0), (2, 16), (3, 0), (4, 0), (5, 0)])
+def test_tc_sampler_own_samples_against_oracle(cfg, plan):
     # sampling on the tensor cores: log q of the GPU's own draws against the
     # oracle, and against the same kernel teacher-forced on those draws
     w = _workload(cfg)
     model = _model(w)
+    model.ctx.set_tuning((0, 0, 0, 0, plan, 0))
     B = 300
     model.ctx.profile(True)
     spins, logq, _ = model.sample(B, 77, 5, precision=tv.BF16)
