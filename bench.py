@@ -80,6 +80,9 @@ def args_():
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="2 (default): the 16x16 EA headline; 1, 3, 4, 5: the other synthetic workloads "
                          "(4x4 +-J, SK N=64, random 3-regular N=256, 64 mixed-size EA instances), each its own line")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="with --workload 1, 3, 4, 5: include the contraction adjoint (d/dbeta, d/dJ) in the step "
+                         "(the 16x16 headline always does)")
     ap.add_argument("--train-steps", type=int, default=0,
                     help="with --workload 5: Adam steps of the accuracy run (oracle checks at steps 1, 100 and "
                          "the last)")
@@ -672,8 +675,8 @@ def run_workload(a):
         m = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1000 * rank + 1)
         m.ctx.reserve(B)
         tuned = m.ctx.autotune(m.betas, B, mode)
-        dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda")
-        dJ = torch.empty(sum(m.n_edges), dtype=torch.float64, device="cuda")
+        dbeta = torch.empty(n_inst * B, dtype=torch.float64, device="cuda") if a.adjoint else None
+        dJ = torch.empty(sum(m.n_edges), dtype=torch.float64, device="cuda") if a.adjoint else None
         cs = m.capture_train_step(B, seed, mode, 0.01, None, dbeta, dJ)
         for _ in range(a.warmup):
             cs.replay()
@@ -741,7 +744,15 @@ def run_workload(a):
     peaks = measured_peaks()
     macs = [made_macs(len(W), w.hidden)[0] for W in w.widths_sets]
     roofline = {"kernel": dom_name, "ms_per_launch": dom_ms / dom_n}
-    if dom_name in ("sample_tc", "bwd_fused", "sample", "backward"):
+    if dom_name == "dense" and any(g.topology == 1 for g in w.graphs):
+        # the leftover block as a [B x 256] x [256 x 256] product (BF16 tensor cores)
+        flop = 2.0 * 256 * 256 * B * sum(1 for g in w.graphs if g.topology == 1)
+        ach = flop / (dom_ms / dom_n / 1e3) / 1e12
+        roofline.update({"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": ach / peaks["bf16_tflops"], "flop_per_launch": flop, "traffic": None,
+                         "peak_source": peaks["source"],
+                         "note": "dense_table_kernel (the 256 x 256 table per beta) and dense_tc_kernel together"})
+    elif dom_name in ("sample_tc", "bwd_fused", "sample", "backward"):
         mult = 3 if dom_name in ("bwd_fused", "backward") else 1
         flop = 2.0 * mult * sum(macs) * B
         ach = flop / (dom_ms / dom_n / 1e3) / 1e12
@@ -761,7 +772,8 @@ def run_workload(a):
         "config": {"workload": w.name, "instances": n_inst, "batch_per_instance": B, "made": w.hidden,
                    "betas": sorted(set(float(b) for b in w.betas)),
                    "width_set_sizes": sorted(set(int(len(W)) for W in w.widths_sets)),
-                   "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
+                   "step": ("sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam" if a.adjoint
+                            else "sample+contract+reduce+REINFORCE backward+Adam"),
                    "timing": "CUDA-graph replay of the whole step", "l2": "flushed (256 MB write) between steps",
                    "parallelism": "single GPU"},
         "clocks": head["clocks"],

@@ -331,8 +331,9 @@ __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restr
   if (I.kind != 1) return;
   const int t = threadIdx.x, w = t >> 5, D = I.D;
   const int tiles = (li.batch + 127) / 128;
-  const int tile0 = (blockIdx.x - li.tile_begin[k]) * DTC_TILES_PER_CTA;
-  const int tile1 = min(tiles, tile0 + DTC_TILES_PER_CTA);
+  const int per_cta = li.tile;  // tiles of this instance per CTA
+  const int tile0 = (blockIdx.x - li.tile_begin[k]) * per_cta;
+  const int tile1 = min(tiles, tile0 + per_cta);
   unsigned char* sC = smem;                   // 128 KB
   unsigned char* sG = smem + 131072;          // [128 x 256] BF16, 64 KB
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 131072 + 65536);
@@ -454,8 +455,18 @@ cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li_in, int pre
   if (precision == TNVAN_BF16 && !dJ && !dbeta && logZR) {
     LaunchInfo lt = li_in;
     const int tiles = (li.batch + 127) / 128;
-    const int per = (tiles + DTC_TILES_PER_CTA - 1) / DTC_TILES_PER_CTA;
+    // tiles per CTA: enough CTAs to cover the SMs, at most DTC_TILES_PER_CTA
+    // (each CTA copies the 128 KB table once)
+    int n_sm = 148;
+    {
+      int dev = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int want = (tiles * lt.n_inst + n_sm - 1) / n_sm;
+    const int per_cta = want < 1 ? 1 : (want > DTC_TILES_PER_CTA ? DTC_TILES_PER_CTA : want);
+    const int per = (tiles + per_cta - 1) / per_cta;
     for (int k = 0; k <= lt.n_inst; ++k) lt.tile_begin[k] = k * per;
+    lt.tile = per_cta;
     const int smem = 131072 + 65536 + 64;
     e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
