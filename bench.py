@@ -73,7 +73,7 @@ def args_():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay timing")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="",
-                    help="six comma-separated ints for Context.set_tuning instead of autotuning "
+                    help="six or seven comma-separated ints for Context.set_tuning instead of autotuning "
                          "(sample tile, strip tile, backward CTAs, adjoint tile, TC group, overlap 2=on 1=off)")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -185,6 +185,38 @@ def strip_flops(w, L):
     (2^w mults); renormalisation adds 2^w mults + 2^w max per row."""
     nx = 1 << w
     return (L - 1) * (w * nx * 3 + nx) + L * 2 * nx
+
+
+def sampler_latency_bound(model, w, prec, ms_full, n_sm, stream):
+    """The sampler's latency bound: every sample is a chain of D dependent
+    steps (Eq. 8) and an SM holds at most 2 x 128 samples in flight (TMEM: 128
+    lanes, two CTAs of <= 256 columns), so the batch takes at least
+    t_step x D x (samples / (2 x 128 x SMs)), with t_step the per-step
+    latency of one full wave, measured here: the same kernel timed alone on a
+    batch that fills exactly one wave of resident CTAs."""
+    import torch
+
+    n_inst = len(w.graphs)
+    per_inst = (2 * n_sm * 128) // n_inst // 128 * 128  # one wave of CTAs over the instances
+    bufs = model.buffers(per_inst)
+    for i in range(3):
+        model.sample(per_inst, 5, i, prec, bufs, stream)
+    torch.cuda.synchronize()
+    model.ctx.profile(True)
+    for i in range(5):
+        model.sample(per_inst, 5, 10 + i, prec, bufs, stream)
+    torch.cuda.synchronize()
+    model.ctx.profile(False)
+    prof = model.ctx.profile_read()
+    ms_wave, n = prof.get("sample_tc", (float("nan"), 1))
+    ms_wave /= n
+    D = max(len(W) for W in w.widths_sets)
+    in_flight = 2 * n_sm * 128
+    total = n_inst * w.batch
+    bound = ms_wave * total / (per_inst * n_inst)  # = t_step x D x total / in_flight
+    return {"model": "t_step x D x samples / samples_in_flight", "samples_in_flight": in_flight,
+            "wave_samples": per_inst * n_inst, "wave_ms": ms_wave, "t_step_us": ms_wave / D * 1e3,
+            "bound_ms": bound, "measured_ms": ms_full, "frac": bound / ms_full}
 
 
 def parity_run(model, step, name, bufs, B):
@@ -418,7 +450,7 @@ def run_ours(a):
     # ----- per-kernel durations: the same step with the overlapped side-stream
     # schedule off, so that every kernel's events bracket it alone -----
     base = tuple(model.tuned) if model.tuned else (0, 0, 0, 0, 0, 0)
-    model.ctx.set_tuning(base[:5] + (1,))
+    model.ctx.set_tuning(base[:5] + (1,) + base[6:])
     for i in range(2):
         step(2 * 10 ** 6 + i)
     torch.cuda.synchronize()
@@ -470,6 +502,8 @@ def run_ours(a):
                 "flop_per_launch": flop_launch, "ms_per_launch": dom_ms / dom_n}
     if note:
         roofline["note"] = note
+    if dom_name == "sample_tc":
+        roofline["latency_bound"] = sampler_latency_bound(model, w, prec, dom_ms / dom_n, n_sm, stream)
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items()}
     launches_per_step = sum(v[1] for v in prof_overlapped.values()) / a.steps
 
@@ -512,7 +546,8 @@ def run_ours(a):
                                       "bwd_ctas_per_instance": None if not model.tuned else model.tuned[2],
                                       "strip_adjoint_tile": None if not model.tuned else model.tuned[3],
                                       "tc_sampler_group_steps": None if not model.tuned else model.tuned[4],
-                                      "overlapped_schedule": None if not model.tuned else model.tuned[5] == 2},
+                                      "overlapped_schedule": None if not model.tuned else model.tuned[5] == 2,
+                                      "backward_form": None if not model.tuned else model.tuned[6]},
     }
     if a.sweep:
         # samples/s of the whole captured step against the batch: per-instance
@@ -591,7 +626,8 @@ def run_ours(a):
         # the paper's first experiment (Sec. 4, Fig. 2): training steps in FP32,
         # then F_q and F_IS from one large batch per temperature
         wf = wl.ferromagnet_columns()
-        mf = TNVAN(wf.graphs, wf.widths_sets, wf.hidden, wf.betas, device=local, seed=1000 * rank + 9)
+        mf = TNVAN(wf.graphs, wf.widths_sets, wf.hidden, wf.betas, device=local, seed=1000 * rank + 9,
+                   elim_orders=wf.elim_orders)
         bf = mf.buffers(wf.batch)
         t0 = time.time()
         for i in range(a.ferro40):
@@ -696,7 +732,7 @@ def run_workload(a):
         clk = clocks.stop() if clocks else None
         # per-kernel times: eager steps with the overlapped schedule off
         base = tuple(tuned)
-        m.ctx.set_tuning(base[:5] + (1,))
+        m.ctx.set_tuning(base[:5] + (1,) + base[6:])
         bufs = m.buffers(B)
         m.train_step(B, seed, 10 ** 6, mode, 0.01, bufs, dbeta, dJ, stream)
         torch.cuda.synchronize()
@@ -993,7 +1029,8 @@ def oracle_ferro_exact(wf, ferro):
     from oracle import kacward
 
     g = wf.graphs[0]
-    f_ex = [-kacward.log_z_kac_ward(g.Lx, g.Ly, g.ei, g.ej, g.J, b) / b / g.n for b in wf.betas]
+    L = int(round(g.n ** 0.5))
+    f_ex = [-kacward.log_z_kac_ward(L, L, g.ei, g.ej, g.J, b) / b / g.n for b in wf.betas]
     return {"F_exact_per_spin": f_ex, "exact": "Kac-Ward determinant (oracle, FP64)",
             "rel_err_F_q": [abs(f - e) / abs(e) for f, e in zip(ferro["F_q_per_spin"], f_ex)],
             "rel_err_F_IS": [abs(f - e) / abs(e) for f, e in zip(ferro["F_IS_per_spin"], f_ex)]}

@@ -374,30 +374,36 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
  * per CTA, the BF16 tensor-core sampler's form and plan (the grouped form,
  * two hidden layers of <= 128 units and D <= 128: step-group size limit 4, 6
  * or 8; the per-step form, any network the sampler takes: chunk size limit
- * 12, 16 or 32) and whether
- * tnvan_sample_contract_adjoint overlaps sampling and the strip adjoint on
- * side streams (2 = on, 1 = off) -- with CUDA events on `stream`, and keeps
+ * 12, 16 or 32), whether tnvan_sample_contract_adjoint overlaps sampling
+ * and the strip adjoint on side streams (2 = on, 1 = off), and, for networks
+ * the fused BF16 backward does not take, whether the TF32 / BF16 backward
+ * runs as the tensor-core GEMM chain (1) or as the FP32 SIMT backward (2,
+ * exact to FP32 and faster for small networks) -- with CUDA events on
+ * `stream`, and keeps
  * the fastest in the context for later calls.  With the overlapped schedule
  * and the fused backward, the backward's CTA count and the adjoint's shape
  * are finally re-timed together on whole tnvan_train_step calls, captured
  * in a CUDA graph on a private stream and replayed, with learning rate 0 and
- * scratch moments, so the networks are left as they were.  out (host int32[6], may be
- * NULL) receives the choices in that order (0 = heuristic, not tuned).
+ * scratch moments, so the networks are left as they were.  out (host
+ * int32[7], may be NULL) receives the choices in that order (0 = heuristic,
+ * not tuned).
  * Synchronous; allocates and frees temporary device buffers.
  * Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM, TNVAN_E_CUDA. */
 int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision, void* stream,
                    int32_t* out);
 
 /* Sets the launch shapes that tnvan_autotune chooses, in the same order and
- * units as its `out` (host int32[6]: SIMT sampler samples per CTA, strip
+ * units as its `out` (host int32[7]: SIMT sampler samples per CTA, strip
  * samples per CTA, fused-backward CTAs per instance, strip-adjoint samples
  * per CTA (1 = one warp per strip over 32 samples), tensor-core sampler
- * form and plan as above, overlapped schedule 2 on / 1 off); 0 restores the
+ * form and plan as above, overlapped schedule 2 on / 1 off, backward form 1
+ * tensor-core chain / 2 FP32 SIMT); 0 restores the
  * built-in default for that entry (the overlapped schedule is on by
  * default).  Lets a caller reuse an earlier tuning without re-timing.  Not in
  * the paper.
  * Errors: TNVAN_E_ARG (NULL, or a value outside the candidates the autotuner
- * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {4,6,8,12,16,32}, {1,2}). */
+ * tries: {16,32,64}, {32,64,128}, >= 1, {1,32,64,96,128}, {4,6,8,12,16,32}, {1,2},
+ * {1,2}). */
 int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* choices);
 
 /* Optional device step counter (not in the paper; for CUDA-graph capture).

@@ -2002,7 +2002,11 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
       CK(launch_grad_reduce(ctx->d_inst, fp.lf, ctx->d_grad_packed, (int)fp.max_elems, d_grad_params, s, adam),
          "gradient reduce kernel");
     }
-  } else if (precision != TNVAN_FP32) {
+  }
+  // without the fused kernel, the reduced-precision modes take the tensor-core
+  // GEMM chain or (tuned, where faster) the FP32 SIMT backward
+  const bool simt = precision == TNVAN_FP32 || (!all_fused && ctx->tune_bwd_form == 2);
+  if (!all_fused && !simt) {
     const int splits = std::max(1, std::min(TC_SPLITS, (batch + 127) / 128));
     if ((rc = ensure_grad_ws(ctx, (size_t)splits * ctx->inst.size() * (size_t)max_elems))) return rc;
     if ((rc = backward_tc(ctx, betas, batch, d_spins, d_logZR, d_logq, precision == TNVAN_BF16,
@@ -2020,11 +2024,11 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
   const int chunk = backward_chunk(ctx, batch);
   LaunchInfo lb;
   if ((rc = fill_launch(ctx, betas, batch, chunk, lb))) return rc;
-  if (precision == TNVAN_FP32 && (rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, batch)))) return rc;
+  if (simt && (rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, batch)))) return rc;
   int smem = 0;
   for (const Instance& in : ctx->inst)
     smem = std::max(smem, (int)((2 * in.W.size() + 2 * in.H[0] + 2 * in.H[1]) * 33 * sizeof(float)));
-  if (precision == TNVAN_FP32) {
+  if (simt) {
     {
       PROF("backward", s);
       CK(launch_backward(ctx->d_inst, lb, smem, precision, d_spins, d_logZR, d_logq, ctx->d_stats,
@@ -2243,6 +2247,26 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     }
     ctx->tune_bwd_ctas = best;
   }
+  if (!fused && precision != TNVAN_FP32) {  // the tensor-core GEMM chain or the FP32 SIMT backward
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int f : {1, 2}) {
+      ctx->tune_bwd_form = f;
+      float ms = 0.f;
+      auto bwd = [&]() {
+        return tnvan_backward(ctx, betas, batch, sp, lz, lq, precision, gr, nullptr, nullptr, stream);
+      };
+      if ((rc = time_it(bwd, &ms))) {
+        cleanup();
+        return rc;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = f;
+      }
+    }
+    ctx->tune_bwd_form = best;
+  }
   if (any_strip) {
     // the strip adjoint's launch shape, and (tensor-core sampler) whether
     // sampling and the adjoint overlap on side streams: timed together on the
@@ -2393,6 +2417,7 @@ int tnvan_autotune(tnvan_ctx* ctx, const double* betas, int batch, int precision
     out[3] = ctx->tune_adj_tile;
     out[4] = tc_plan_value(ctx, ctx->tune_tc_plan);
     out[5] = ctx->tune_overlap ? 2 : 1;
+    out[6] = ctx->tune_bwd_form;
   }
   cudaError_t e = cudaStreamSynchronize(s);
   cleanup();
@@ -2416,7 +2441,7 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
     if (kTcGroupMax[p] == c[4]) plan = p, form = 2;
   }
   if (!in(c[0], {16, 32, 64}) || !in(c[1], {32, 64, 128}) || c[2] < 0 || !in(c[3], {1, 32, 64, 96, 128}) ||
-      (c[4] != 0 && plan < 0) || c[5] < 0 || c[5] > 2)
+      (c[4] != 0 && plan < 0) || c[5] < 0 || c[5] > 2 || c[6] < 0 || c[6] > 2)
     return fail(ctx, TNVAN_E_ARG, "tuning value outside the autotuner's candidates");
   ctx->tune_sample_tile = c[0];
   ctx->tune_strip_tile = c[1];
@@ -2425,6 +2450,7 @@ int tnvan_set_tuning(tnvan_ctx* ctx, const int32_t* c) {
   ctx->tune_tc_plan = plan;
   ctx->tune_tc_form = form;
   ctx->tune_overlap = c[5] != 1;  // 0 and 2 (default) on, 1 off
+  ctx->tune_bwd_form = c[6];
   return TNVAN_OK;
 }
 

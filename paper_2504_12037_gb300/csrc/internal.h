@@ -299,6 +299,7 @@ struct tnvan_ctx {
   int tune_sample_tile = 0, tune_strip_tile = 0, tune_bwd_ctas = 0, tune_adj_tile = 0;
   int tune_tc_plan = -1;  // tensor-core sampler step-group plan (-1 = default)
   int tune_tc_form = 0;   // tensor-core sampler form: 0 automatic, 1 grouped, 2 per-step
+  int tune_bwd_form = 0;  // backward without the fused kernel, BF16/TF32: 0/1 tensor-core GEMM chain, 2 FP32 SIMT
   int tune_overlap = 1;   // overlapped sampling + adjoint schedule (1 on, 0 off)
   // last strip-adjoint launch plan (valid while batch, tuning and instances are unchanged)
   struct {

@@ -276,17 +276,22 @@ class Context:
         """Time candidate launch shapes on a synthetic batch and keep the fastest;
         returns the chosen (sampler tile, strip tile, backward CTAs, strip adjoint tile,
         tensor-core sampler plan (grouped form: 4, 6, 8 steps per group; per-step
-        form: 12, 16, 32 steps per chunk), overlapped schedule 2 on / 1 off)."""
+        form: 12, 16, 32 steps per chunk), overlapped schedule 2 on / 1 off, backward
+        form of networks without the fused kernel 1 tensor-core chain / 2 FP32 SIMT)."""
         b, pb = _arr(betas, np.float64)
-        out = (ctypes.c_int32 * 6)()
+        out = (ctypes.c_int32 * 7)()
         self._check(lib().tnvan_autotune(self._h, pb, batch, precision, _stream(stream), out))
-        return tuple(out[:6])
+        return tuple(out[:7])
 
     def set_tuning(self, choices):
-        """Reuse launch shapes (the 6-tuple autotune returns; 0 = default)."""
-        c, pc = _arr(list(choices), np.int32)
-        if c.shape[0] != 6:
-            raise ValueError("expected 6 tuning values")
+        """Reuse launch shapes (the 7-tuple autotune returns; 0 = default; a
+        6-tuple leaves the backward form at its default)."""
+        c = list(choices)
+        if len(c) == 6:
+            c.append(0)
+        c, pc = _arr(c, np.int32)
+        if c.shape[0] != 7:
+            raise ValueError("expected 6 or 7 tuning values")
         self._check(lib().tnvan_set_tuning(self._h, pc))
 
     def profile(self, enable: bool):

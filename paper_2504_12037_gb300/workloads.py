@@ -250,6 +250,7 @@ class Workload:
     hidden: List[int]
     batch: int
     betas: List[float]
+    elim_orders: Optional[List[np.ndarray]] = None  # R's elimination order per instance (GENERAL graphs)
 
 
 def workload(config: int, n_instances: Optional[int] = None) -> Workload:
@@ -287,18 +288,27 @@ def workload(config: int, n_instances: Optional[int] = None) -> Workload:
     raise ValueError(f"unknown workload {config}")
 
 
-def ferromagnet_columns(L: int = 40, period: int = 5, hidden: Sequence[int] = (256, 256),
+def ferromagnet_columns(L: int = 40, period: int = 13, hidden: Sequence[int] = (256, 256),
                         batch: int = 1000) -> Workload:
     """The paper's first experiment (Sec. 4, Fig. 2): the open L x L
     ferromagnet (J = 1) at T = 1, 2, T_c, 3, 4, 5 (T_c = 2 / ln(1 + sqrt 2),
     Onsager's critical temperature), one instance per temperature; W = every
     `period`-th column (columns c with c % period == period - 1), which leaves
-    strips of period - 1 columns."""
+    strips of period - 1 columns.  With period > 5 the strips are wider than
+    the strip contraction takes, so the graph is given as a general one and
+    each strip is eliminated row by row (elimination width = strip width)."""
     g = lattice(L, L, "ferro", 0)
-    W = width_columns(L, L, every_kth_column(L, period))
+    cols = every_kth_column(L, period)
+    W = width_columns(L, L, cols)
+    order = None
+    if period > 5:
+        g = Graph(g.n, g.ei, g.ej, g.J, GENERAL)
+        wset = set(int(v) for v in W)
+        order = np.asarray([y * L + x for y in range(L) for x in range(L) if y * L + x not in wset], np.int32)
     temps = [1.0, 2.0, 2.0 / np.log(1.0 + np.sqrt(2.0)), 3.0, 4.0, 5.0]
-    return Workload(f"ferro_{L}x{L}_open_every{period}th_col", [g] * len(temps), [W] * len(temps), list(hidden),
-                    batch, [float(1.0 / T) for T in temps])
+    n = len(temps)
+    return Workload(f"ferro_{L}x{L}_open_every{period}th_col", [g] * n, [W] * n, list(hidden), batch,
+                    [float(1.0 / T) for T in temps], None if order is None else [order] * n)
 
 
 # ---------------------------------------------------------------------------
