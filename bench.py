@@ -83,6 +83,9 @@ def args_():
     ap.add_argument("--adjoint", action="store_true",
                     help="with --workload 1, 3, 4, 5: include the contraction adjoint (d/dbeta, d/dJ) in the step "
                          "(the 16x16 headline always does)")
+    ap.add_argument("--sampler-only", type=int, default=-1, metavar="PLAN",
+                    help="with --workload: build the workload, pin the tensor-core sampler plan PLAN (0 = default) "
+                         "and draw two BF16 batches, nothing else (a short command for ncu captures)")
     ap.add_argument("--train-steps", type=int, default=0,
                     help="with --workload 5: Adam steps of the accuracy run (oracle checks at steps 1, 100 and "
                          "the last)")
@@ -705,6 +708,15 @@ def run_workload(a):
     gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
     samples_step = n_inst * B * world
     PREC = {"fp32": tv.FP32, "bf16": tv.BF16}
+    if a.sampler_only >= 0:
+        m = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, device=local, seed=1)
+        m.ctx.set_tuning((0, 0, 0, 0, a.sampler_only, 0))
+        t0 = time.perf_counter()
+        for i in range(2):
+            m.sample(B, 1, i, tv.BF16)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": w.name, "sampler_only": a.sampler_only, "s": time.perf_counter() - t0}))
+        return
 
     def measure(name, sample_clocks):
         mode = PREC[name]

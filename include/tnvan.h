@@ -321,7 +321,13 @@ int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8
 /* Eq. 10: REINFORCE gradient of F_q for every instance,
  *   grad = sum_b w_b grad_theta log q(s_b),  w_b = -(l_b - mean_b l) / (beta batch),
  * (the batch mean is the baseline; it leaves the expectation unchanged), by a
- * teacher-forced forward and hand-written backward of the network.
+ * teacher-forced forward and hand-written backward of the network.  With
+ * TNVAN_BF16, instances whose network has two hidden layers of <= 128 units
+ * (multiples of 16) and a width set that fits the fused kernel's TMEM (D
+ * padded to 16; 128 + (D + 16) + (H1 + 16) + (H2 + 16) <= 512 columns) run
+ * the fused tcgen05 backward; the other instances of the same call run the
+ * tensor-core GEMM chain (TF32 / BF16 operands, FP32 accumulate) or, where the
+ * autotuner found it faster, the FP32 SIMT backward.
  *   d_grad_params   device float [total params] out, packed layout of
  *                   tnvan_n_params (overwritten; masked entries are 0).
  * Contraction adjoint (optional, NULL to skip):

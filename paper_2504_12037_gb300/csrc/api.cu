@@ -610,9 +610,11 @@ size_t tc_ws_floats(const tnvan_ctx* ctx, int batch) {
 // gradients (bias gradients ride along as an extra column of ones).
 int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
                 const double* d_logZR, const float* d_logq, bool bf16, int part_stride,
-                cudaStream_t s) {
+                cudaStream_t s, bool skip_fused) {
   int rc;
   const int n = (int)ctx->inst.size();
+  // instances the fused backward handles in the same call are left out
+  auto skip = [&](int k) { return skip_fused && ctx->inst[k].dev.made.fused_ok; };
   if ((rc = ensure_ws(ctx, tc_ws_floats(ctx, batch) * sizeof(float)))) return rc;
   float* ws = static_cast<float*>(ctx->d_ws);
   struct Bufs { float *A1, *A2, *dX, *dA2, *dA1, *w; };
@@ -675,6 +677,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   const int B = batch;
   // stage 1: A1 = relu(S W1^T + b1)
   for (int k = 0; k < n; ++k) {
+    if (skip(k)) continue;
     const Instance& in = ctx->inst[k];
     const MadeDev& md = in.dev.made;
     if (md.nh < 1) continue;
@@ -689,6 +692,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if ((rc = flush("gemm_fwd1"))) return rc;
   // stage 2: A2 = relu(A1 W2^T + b2)
   for (int k = 0; k < n; ++k) {
+    if (skip(k)) continue;
     const MadeDev& md = ctx->inst[k].dev.made;
     if (md.nh < 2) continue;
     const float* W2 = md.packed + md.layer[1].dst_off;
@@ -701,6 +705,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if ((rc = flush("gemm_fwd2"))) return rc;
   // stage 3: dX = w_b s sigmoid(-s x), x = src Wo^T + bo
   for (int k = 0; k < n; ++k) {
+    if (skip(k)) continue;
     const Instance& in = ctx->inst[k];
     const MadeDev& md = in.dev.made;
     const int D = md.D, Hl = md.Hl;
@@ -718,6 +723,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if ((rc = flush("gemm_out_dx"))) return rc;
   // stage 4: delta of the last hidden layer = (dX Wo) * 1[h > 0]
   for (int k = 0; k < n; ++k) {
+    if (skip(k)) continue;
     const MadeDev& md = ctx->inst[k].dev.made;
     if (md.nh < 1) continue;
     const int D = md.D, Hl = md.Hl;
@@ -733,6 +739,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   if ((rc = flush("gemm_bwd_last"))) return rc;
   // stage 5: dA1 = (dA2 W2) * 1[h1 > 0]
   for (int k = 0; k < n; ++k) {
+    if (skip(k)) continue;
     const MadeDev& md = ctx->inst[k].dev.made;
     if (md.nh < 2) continue;
     const float* W2 = md.packed + md.layer[1].dst_off;
@@ -748,6 +755,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
   splits = std::max(1, std::min(TC_SPLITS, (batch + 127) / 128));
   float* part = ctx->d_grad_packed;
   for (int k = 0; k < n; ++k) {
+    if (skip(k)) continue;
     const Instance& in = ctx->inst[k];
     const MadeDev& md = in.dev.made;
     const int D = md.D;
@@ -1061,16 +1069,18 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   }
   md.n_params = off;
   if (off >= (1LL << 30)) return fail(ctx, TNVAN_E_UNSUPPORTED, "network too large (%lld parameters)", off);
-  md.fused_ok = n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
-                H[0] <= 128 && H[1] <= 128 && 128 + (D + 16) + (H[0] + 16) + (H[1] + 16) <= 512 &&
+  const int Dp16 = (D + 15) & ~15;  // the fused backward pads D to a multiple of 16
+  md.fused_ok = n_hidden == 2 && H[0] % 16 == 0 && H[1] % 16 == 0 && Dp16 <= 128 && H[0] <= 128 &&
+                H[1] <= 128 && 128 + (Dp16 + 16) + (H[0] + 16) + (H[1] + 16) <= 512 &&
                 fused_bwd_smem_bytes(D, H[0], H[1]) <= 227 * 1024;
   md.sample_tc_ok = 0;  // decided once the step groups are known
   md.wtiles = nullptr;
   if (md.fused_ok || (n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
                       H[0] <= 128 && H[1] <= 128)) {
     void* wt = nullptr;
-    const size_t n = (size_t)H[0] * D + (size_t)H[1] * H[0] + (size_t)D * H[1];
+    const size_t n = (size_t)H[0] * Dp16 + (size_t)H[1] * H[0] + (size_t)Dp16 * H[1];
     cudaError_t e2 = cudaMalloc(&wt, n * sizeof(uint16_t));
+    if (e2 == cudaSuccess) e2 = cudaMemset(wt, 0, n * sizeof(uint16_t));  // the padding stays zero
     if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(weight tiles): %s", cudaGetErrorString(e2));
     in.dev_allocs.push_back(wt);
     md.wtiles = static_cast<uint16_t*>(wt);
@@ -1711,9 +1721,13 @@ int tnvan_train_step(tnvan_ctx* ctx, const double* betas, int batch, uint64_t se
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // one pack serves the sampler and the backward (the parameters change only
   // in the last kernel of the step)
-  bool all_fused = precision == TNVAN_BF16;
-  for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
-  if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision) | PACK_FLAT | (all_fused ? PACK_TILES : 0), s)))
+  bool all_fused = precision == TNVAN_BF16, any_fused = false;
+  for (const Instance& in : ctx->inst) {
+    all_fused = all_fused && in.dev.made.fused_ok;
+    any_fused = any_fused || in.dev.made.fused_ok;
+  }
+  any_fused = any_fused && precision == TNVAN_BF16;  // the fused backward reads the BF16 tiles
+  if ((rc = pack_network(ctx, sampler_pack_mask(ctx, precision) | PACK_FLAT | (any_fused ? PACK_TILES : 0), s)))
     return rc;
   // the overlapped schedule runs each chunk's Eq. 9 reduction (statistics
   // and the backward's baseline) behind its adjoint, and the d/dJ reduction (it reads only the adjoint's partial
@@ -1981,14 +1995,22 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
   for (const Instance& in : ctx->inst) max_elems = std::max(max_elems, in.n_params);
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
-  bool all_fused = precision == TNVAN_BF16;
-  for (const Instance& in : ctx->inst) all_fused = all_fused && in.dev.made.fused_ok;
-  if (pack && (rc = pack_network(ctx, PACK_FLAT | (all_fused ? PACK_TILES : 0), s))) return rc;
+  bool all_fused = precision == TNVAN_BF16, any_fused = false;
+  for (const Instance& in : ctx->inst) {
+    all_fused = all_fused && in.dev.made.fused_ok;
+    any_fused = any_fused || in.dev.made.fused_ok;
+  }
+  any_fused = any_fused && precision == TNVAN_BF16;
+  if (pack && (rc = pack_network(ctx, PACK_FLAT | (any_fused ? PACK_TILES : 0), s))) return rc;
   if (!stats_ready) {
     PROF("reduce", s);
     CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, ctx->d_status + 4, s), "reduce kernel");
   }
-  if (all_fused) {
+  // instances the fused kernel takes (BF16): fused; the rest by the forms below
+  unsigned int fused_bits[TNVAN_MAX_INST / 32] = {0u};
+  for (int k = 0; k < (int)ctx->inst.size() && any_fused; ++k)
+    if (ctx->inst[k].dev.made.fused_ok) fused_bits[k >> 5] |= 1u << (k & 31);
+  if (any_fused) {
     FusedBwdPlan fp;
     if ((rc = plan_fused_bwd(ctx, betas, batch, fp))) return rc;
     {
@@ -2010,11 +2032,12 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
     const int splits = std::max(1, std::min(TC_SPLITS, (batch + 127) / 128));
     if ((rc = ensure_grad_ws(ctx, (size_t)splits * ctx->inst.size() * (size_t)max_elems))) return rc;
     if ((rc = backward_tc(ctx, betas, batch, d_spins, d_logZR, d_logq, precision == TNVAN_BF16,
-                          (int)max_elems, s)))
+                          (int)max_elems, s, any_fused)))
       return rc;
     LaunchInfo lr;
     if ((rc = fill_launch(ctx, betas, batch, 1, lr))) return rc;
     for (int k = 0; k <= lr.n_inst; ++k) lr.tile_begin[k] = k * splits;
+    for (int j = 0; j < TNVAN_MAX_INST / 32; ++j) lr.skip[j] = fused_bits[j];
     {
       PROF("grad_reduce", s);
       CK(launch_grad_reduce(ctx->d_inst, lr, ctx->d_grad_packed, (int)max_elems, d_grad_params, s, adam),
@@ -2024,6 +2047,15 @@ int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* 
   const int chunk = backward_chunk(ctx, batch);
   LaunchInfo lb;
   if ((rc = fill_launch(ctx, betas, batch, chunk, lb))) return rc;
+  if (any_fused) {  // the SIMT backward leaves the fused instances out (no CTAs, not reduced)
+    int acc = 0;
+    for (int k = 0; k < lb.n_inst; ++k) {
+      lb.tile_begin[k] = acc;
+      if (!((fused_bits[k >> 5] >> (k & 31)) & 1u)) acc += (batch + chunk - 1) / chunk;
+    }
+    lb.tile_begin[lb.n_inst] = acc;
+    for (int j = 0; j < TNVAN_MAX_INST / 32; ++j) lb.skip[j] = fused_bits[j];
+  }
   if (simt && (rc = ensure_grad_ws(ctx, grad_ws_floats(ctx, batch)))) return rc;
   int smem = 0;
   for (const Instance& in : ctx->inst)
@@ -2051,7 +2083,8 @@ int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan&
   p.smem = 0;
   for (const Instance& in : ctx->inst) {
     p.max_elems = std::max(p.max_elems, in.n_params);
-    p.smem = std::max(p.smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
+    if (in.dev.made.fused_ok)
+      p.smem = std::max(p.smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
   }
   const int n_inst = (int)ctx->inst.size();
   const int tiles = (batch + 127) / 128;
@@ -2066,7 +2099,8 @@ int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan&
   for (int k = 0; k < p.lf.n_inst; ++k) {
     p.lf.tile_begin[k] = acc;
     const int pk = (k == n_inst - 1 && n_inst > 1) ? per_last : per;
-    acc += (tiles + pk - 1) / pk;
+    if (ctx->inst[k].dev.made.fused_ok) acc += (tiles + pk - 1) / pk;
+    else p.lf.skip[k >> 5] |= 1u << (k & 31);  // no CTAs; another backward form reduces it
   }
   p.lf.tile_begin[p.lf.n_inst] = acc;
   p.lf.tile = per;
@@ -2630,7 +2664,10 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
   }
   if (k1) {
     PROF(d_dbeta ? "dense_dbeta" : "dense", s);
-    CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s), "dense kernel");
+    int max_D = 0;
+    for (const Instance& in : ctx->inst)
+      if (in.kind == 1) max_D = std::max(max_D, (int)in.W.size());
+    CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s, max_D), "dense kernel");
   }
   if (k2) {
     int arena = 0, Dm = 0, nsteps = 0;

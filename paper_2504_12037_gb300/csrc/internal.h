@@ -232,6 +232,7 @@ struct LaunchInfo {
   int gen_tab;        // elimination instances: > 0 = build and use the component tables (the largest n_tab)
   double beta[TNVAN_MAX_INST];
   int tile_begin[TNVAN_MAX_INST + 1];
+  unsigned int skip[TNVAN_MAX_INST / 32];  // per-instance bits: 1 = a kernel that reads them leaves the instance out
 };
 
 // ---------------------------------------------------------------------------
@@ -351,7 +352,7 @@ cudaError_t launch_strips_dJ_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                     double* dJ, cudaStream_t s, bool assign);
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
-                         cudaStream_t s);
+                         cudaStream_t s, int max_D = 1024);
 // Elimination kernels keep their tables in shared memory, or (garena
 // non-NULL: arenas too large for 32 samples per CTA) in a global scratch
 // buffer of general_scratch_floats / general_dJ_scratch_floats floats.

@@ -1,5 +1,7 @@
 // Fused BF16 backward of the MADE network on tcgen05 (Eq. 10), for networks
-// with two hidden layers of at most 128 units and at most 128 inputs.
+// with two hidden layers of at most 128 units (multiples of 16) and at most
+// 128 inputs (padded to Dp, a multiple of 16: the padded inputs and outputs
+// are zero and carry no gradient).
 //
 // One CTA (256 threads: two warpgroups, each thread one sample = TMEM lane
 // and every other 16-column chunk of each epilogue) walks the 128-sample
@@ -85,7 +87,8 @@ struct FusedBwdArgs {
 };
 
 // Shared memory bytes for (D, H1, H2).
-__host__ __device__ inline int fused_bwd_smem(int D, int H1, int H2) {
+__host__ __device__ inline int fused_bwd_smem(int D0, int H1, int H2) {
+  const int D = (D0 + 15) & ~15;
   const int w = H1 * D + H2 * H1 + D * H2;                        // weights
   const int a = 128 * ((D + 16) + (H1 + 16) + (H2 + 16) + D + H2);  // S, A1, A2/dA1, dX, dA2
   return 2 * (w + a) + 4 * (H1 + H2 + D) + 64;  // + biases, barriers and the TMEM slot
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   const InstDev& I = inst[k];
   const MadeDev& md = I.made;
   if (!md.fused_ok) return;
-  const int D = md.D, H1 = md.H1, H2 = md.H2;
+  const int D = md.D, Dp = (D + 15) & ~15, H1 = md.H1, H2 = md.H2;
   // two warpgroups: thread (g, r) owns TMEM lane / sample row r and the
   // 16-column chunks c with (c / 16) % 2 == g of every epilogue
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 127, g = tid >> 7;
@@ -112,29 +115,29 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   const int tile0 = c_idx * per, tile1 = min(tiles_total, tile0 + per);
   // ---- shared memory carve ----
   unsigned char* p = smem;
-  unsigned char* sW1 = p; p += H1 * D * 2;
+  unsigned char* sW1 = p; p += H1 * Dp * 2;
   unsigned char* sW2 = p; p += H2 * H1 * 2;
-  unsigned char* sWo = p; p += D * H2 * 2;
-  unsigned char* sS = p; p += 128 * (D + 16) * 2;
+  unsigned char* sWo = p; p += Dp * H2 * 2;
+  unsigned char* sS = p; p += 128 * (Dp + 16) * 2;
   unsigned char* sA1 = p; p += 128 * (H1 + 16) * 2;
   unsigned char* sA2 = p; p += 128 * (H2 + 16) * 2;  // later dA1 (128 x H1)
-  unsigned char* sdX = p; p += 128 * D * 2;           // must precede sdA2 (MN view overruns into it)
+  unsigned char* sdX = p; p += 128 * Dp * 2;          // must precede sdA2 (MN view overruns into it)
   unsigned char* sdA2 = p; p += 128 * H2 * 2;
   float* sb1 = reinterpret_cast<float*>(p); p += 4 * H1;  // biases
   float* sb2 = reinterpret_cast<float*>(p); p += 4 * H2;
   float* sbo = reinterpret_cast<float*>(p); p += 4 * D;
   uint64_t* bar = reinterpret_cast<uint64_t*>(p);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);  // cbar is bar + 2
-  const Tile tW1{smem_u32(sW1), D}, tW2{smem_u32(sW2), H1}, tWo{smem_u32(sWo), H2};
-  const Tile tS{smem_u32(sS), D + 16}, tA1{smem_u32(sA1), H1 + 16}, tA2{smem_u32(sA2), H2 + 16};
-  const Tile tdX{smem_u32(sdX), D}, tdA2{smem_u32(sdA2), H2}, tdA1{smem_u32(sA2), H1};
+  const Tile tW1{smem_u32(sW1), Dp}, tW2{smem_u32(sW2), H1}, tWo{smem_u32(sWo), H2};
+  const Tile tS{smem_u32(sS), Dp + 16}, tA1{smem_u32(sA1), H1 + 16}, tA2{smem_u32(sA2), H2 + 16};
+  const Tile tdX{smem_u32(sdX), Dp}, tdA2{smem_u32(sdA2), H2}, tdA1{smem_u32(sA2), H1};
   // ---- weights: packed FP32 (masked, degree-sorted) -> BF16 K-major tiles ----
   const float* W1 = md.packed + md.layer[0].dst_off;
   const float* b1 = W1 + (long long)H1 * D;
   const float* W2 = md.packed + md.layer[1].dst_off;
   const float* b2 = W2 + (long long)H2 * H1;
   const float* Wo = md.packed + md.layer[2].dst_off;
-  const float* bo = Wo + (long long)D * H2;
+  const float* bo = Wo + (long long)D * H2;  // the packed layer is [D][H2] then b [D]
   // BF16 weight tiles (laid out once per call in the canonical K-major form)
   // arrive with one bulk copy; W1, W2, Wo are contiguous in both places
   uint64_t* cbar = bar + 2;
@@ -153,20 +156,20 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   __syncthreads();
   tc::fence_after_sync();
   if (tid == 0) {
-    const uint32_t wbytes = 2u * (uint32_t)(H1 * D + H2 * H1 + D * H2);
+    const uint32_t wbytes = 2u * (uint32_t)(H1 * Dp + H2 * H1 + Dp * H2);
     mbar_expect_tx(cbar, wbytes);
     bulk_g2s(sW1, md.wtiles, wbytes, cbar);
   }
   const bool weights_ok = mbar_wait(cbar, 0);
   const uint32_t tmem = *slot;
-  const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)(D + 16), tGo = tG2 + (uint32_t)(H1 + 16);
+  const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)(Dp + 16), tGo = tG2 + (uint32_t)(H1 + 16);
   const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
-  const uint32_t id_fwd1 = tc::idesc(128, H1, 1u), id_fwd2 = tc::idesc(128, H2, 1u), id_fwd3 = tc::idesc(128, D, 1u);
+  const uint32_t id_fwd1 = tc::idesc(128, H1, 1u), id_fwd2 = tc::idesc(128, H2, 1u), id_fwd3 = tc::idesc(128, Dp, 1u);
   const uint32_t id_d2 = tc::idesc(128, H2, 1u) | (1u << 16);         // B MN-major
   const uint32_t id_d1 = tc::idesc(128, H1, 1u) | (1u << 16);
   const uint32_t id_go = tc::idesc(128, H2 + 16, 1u) | (1u << 15) | (1u << 16);  // A, B MN-major
   const uint32_t id_g2 = tc::idesc(128, H1 + 16, 1u) | (1u << 15) | (1u << 16);
-  const uint32_t id_g1 = tc::idesc(128, D + 16, 1u) | (1u << 15) | (1u << 16);
+  const uint32_t id_g1 = tc::idesc(128, Dp + 16, 1u) | (1u << 15) | (1u << 16);
   const double mean = args.stats[8 * k + 4];
   const double wsc = -1.0 / (li.beta[k] * stats_batch(args.stats + 8 * k));
   const int8_t* Sg = args.spins + I.spin_units * (long long)B;
@@ -192,34 +195,44 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     const float vf = valid ? 1.f : 0.f;
     // spins -> S tile (+ ones column), 16 per vector load; mS bit f = (s_f > 0)
     Mask128 mS, m1, m2;
-    for (int c = 16 * g; c < D; c += 32) {
-      uint4 raw = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-      if (valid) raw = *reinterpret_cast<const uint4*>(Sg + (long long)b * D + c);
-      const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+    for (int c = 16 * g; c < Dp; c += 32) {
       float sp[16];
       uint32_t m16 = 0;
+      if ((D & 15) == 0) {  // 16 spins per vector load
+        uint4 raw = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+        if (valid) raw = *reinterpret_cast<const uint4*>(Sg + (long long)b * D + c);
+        const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int8_t sv = (int8_t)((wv[i >> 2] >> (8 * (i & 3))) & 0xFFu);
-        sp[i] = valid ? (float)sv : 0.f;
-        m16 |= (sv > 0 ? 1u : 0u) << i;
+        for (int i = 0; i < 16; ++i) {
+          const int8_t sv = (int8_t)((wv[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+          sp[i] = valid ? (float)sv : 0.f;
+          m16 |= (sv > 0 ? 1u : 0u) << i;
+        }
+      } else {  // rows not 16-byte aligned: byte loads; padded spins are 0
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int f = c + i;
+          const int8_t sv = (valid && f < D) ? Sg[(long long)b * D + f] : (int8_t)0;
+          sp[i] = (float)sv;
+          m16 |= (sv > 0 ? 1u : 0u) << i;
+        }
       }
       mS.put16(c, m16);
       store8(sS, tS.rowbytes(), t, c, sp);
       store8(sS, tS.rowbytes(), t, c + 8, sp + 8);
     }
-    if (((D >> 4) & 1) == g) {
+    if (((Dp >> 4) & 1) == g) {
       float sp[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) sp[i] = i == 0 ? vf : 0.f;
-      store8(sS, tS.rowbytes(), t, D, sp);
-      store8(sS, tS.rowbytes(), t, D + 8, sp + 8);
+      store8(sS, tS.rowbytes(), t, Dp, sp);
+      store8(sS, tS.rowbytes(), t, Dp + 8, sp + 8);
     }
     const float wb = valid ? (float)(wsc * (args.logZR[(long long)k * B + b] - (double)args.logq[(long long)k * B + b] - mean)) : 0.f;
     sync_for_mma();
     // fwd1: scratch = S W1^T
     if (tid == 0)
-      for (int kk = 0; kk < D / 16; ++kk) tc::mma_bf16(tScr, tS.kdesc(kk), tW1.kdesc(kk), id_fwd1, kk > 0);
+      for (int kk = 0; kk < Dp / 16; ++kk) tc::mma_bf16(tScr, tS.kdesc(kk), tW1.kdesc(kk), id_fwd1, kk > 0);
     if (!(ok = mma_wait())) break;
     for (int c = 16 * g; c < H1 + 16; c += 32) {
       float v[16];
@@ -259,16 +272,16 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     if (tid == 0)
       for (int kk = 0; kk < H2 / 16; ++kk) tc::mma_bf16(tScr, tA2.kdesc(kk), tWo.kdesc(kk), id_fwd3, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 16 * g; c < D; c += 32) {
+    for (int c = 16 * g; c < Dp; c += 32) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
       const uint32_t ms = mS.get16(c);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int f = c + i;
-        const float x = v[i] + sbo[f];
+        const float x = v[i] + (f < D ? sbo[f] : 0.f);
         const float s = ((ms >> i) & 1u) ? 1.f : -1.f;
-        v[i] = wb * s * __frcp_rn(1.f + __expf(s * x));
+        v[i] = f < D ? wb * s * __frcp_rn(1.f + __expf(s * x)) : 0.f;  // padded outputs carry no gradient
       }
       store8(sdX, tdX.rowbytes(), t, c, v);
       store8(sdX, tdX.rowbytes(), t, c + 8, v + 8);
@@ -276,7 +289,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     sync_for_mma();
     // scratch = dX Wo (B = Wo read MN-major);  GWo += dX^T [A2 | 1]
     if (tid == 0) {
-      for (int kk = 0; kk < D / 16; ++kk) tc::mma_bf16(tScr, tdX.kdesc(kk), tWo.mndesc(kk), id_d2, kk > 0);
+      for (int kk = 0; kk < Dp / 16; ++kk) tc::mma_bf16(tScr, tdX.kdesc(kk), tWo.mndesc(kk), id_d2, kk > 0);
       for (int kk = 0; kk < 8; ++kk)
         tc::mma_bf16(tGo, tdX.mndesc(kk), tA2.mndesc(kk), id_go, (!first || kk > 0) ? 1u : 0u);
     }
@@ -326,24 +339,33 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   // row-major layer blocks need no transpose), the bias column as one float.
   float* G = args.partials + (long long)gblk * args.part_stride;
   if (ok && !first) {
-    auto flush = [&](uint32_t tacc, int nin, int nout, long long off) {
-      for (int c = 16 * g; c < nin + 16; c += 32) {
+    // ncol: the accumulator's input columns (a multiple of 16; the bias
+    // column follows), nin <= ncol of them real
+    auto flush = [&](uint32_t tacc, int nin, int ncol, int nout, long long off) {
+      for (int c = 16 * g; c < ncol + 16; c += 32) {
         float v[16];
         tc::tmem_ld16(tacc + lane_off + (uint32_t)c, v);
         if (t < nout) {
-          if (c < nin) {
-            float4* row = reinterpret_cast<float4*>(G + off + (long long)t * nin + c);
+          if (c < ncol) {
+            float* row = G + off + (long long)t * nin + c;
+            if ((nin & 3) == 0 && c + 16 <= nin) {
+              float4* row4 = reinterpret_cast<float4*>(row);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) row[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              for (int q = 0; q < 4; ++q) row4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (c + q < nin) row[q] = v[q];
+            }
           } else {
-            G[off + (long long)nout * nin + t] = v[0];  // c == nin: the bias column
+            G[off + (long long)nout * nin + t] = v[0];  // c == ncol: the bias column
           }
         }
       }
     };
-    flush(tG1, D, H1, md.layer[0].dst_off);
-    flush(tG2, H1, H2, md.layer[1].dst_off);
-    flush(tGo, H2, D, md.layer[2].dst_off);
+    flush(tG1, D, Dp, H1, md.layer[0].dst_off);
+    flush(tG2, H1, H1, H2, md.layer[1].dst_off);
+    flush(tGo, H2, H2, D, md.layer[2].dst_off);
   } else {
     for (long long e = tid; e < md.n_params; e += 256) G[e] = 0.f;
   }

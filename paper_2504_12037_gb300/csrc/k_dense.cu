@@ -322,6 +322,13 @@ __device__ __forceinline__ void half_products(const float* h, float beta, float*
   }
 }
 
+// The W-side terms of a tile (Eq. 4: the fields h = J_RW s on R and the W-W
+// energy E_1(s)) are computed from the sample's spins held as 64 bits, with
+// the couplings in shared memory (J_RW transposed [DMAX][16], J_WW as a dense
+// upper triangle [DMAX][DMAX]) and every loop unrolled to DMAX >= D, so that
+// no global load sits on the per-sample chain.  DMAX = 0: D > 64, the same
+// sums straight from global memory.
+template <int DMAX>
 __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
                                                           const int8_t* __restrict__ spins,
                                                           double* __restrict__ logZR) {
@@ -339,6 +346,20 @@ __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restr
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 131072 + 65536);
   uint64_t* cbar = bar + 1;
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  float* sJ1 = reinterpret_cast<float*>(smem + 131072 + 65536 + 64);  // [DMAX][16] J_RW^T
+  float* sJ2 = sJ1 + DMAX * 16;                                        // [DMAX][DMAX] J_WW, i < j
+  if (DMAX > 0) {
+    for (int e = t; e < DMAX * 16; e += 128) {
+      const int wp = e >> 4, r = e & 15;
+      sJ1[e] = wp < D ? I.dense.JRW[r * D + wp] : 0.f;
+    }
+    for (int e = t; e < DMAX * DMAX; e += 128) sJ2[e] = 0.f;
+    __syncthreads();
+    for (int e = t; e < I.n_ww; e += 128) {
+      const EdgeWW q = I.ww[e];
+      sJ2[min(q.a, q.b) * DMAX + max(q.a, q.b)] = q.J;
+    }
+  }
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_init(cbar, 1);
@@ -370,15 +391,55 @@ __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restr
     float h[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) h[r] = 0.f;
-    for (int wpos = 0; wpos < D; ++wpos) {
-      const float sw = (float)st[wpos];
-#pragma unroll
-      for (int r = 0; r < 16; ++r) h[r] = fmaf(__ldg(I.dense.JRW + r * D + wpos), sw, h[r]);
-    }
     float e1 = 0.f;
-    for (int e = 0; e < I.n_ww; ++e) {
-      const EdgeWW q = I.ww[e];
-      e1 = fmaf(q.J, (float)(st[q.a] * st[q.b]), e1);
+    if (DMAX > 0) {
+      unsigned long long m = 0ull;  // bit w: spin w is +1
+      if ((D & 15) == 0) {
+        for (int c = 0; c < D; c += 16) {
+          const uint4 raw = *reinterpret_cast<const uint4*>(st + c);
+          const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            m |= (unsigned long long)((int8_t)((wv[i >> 2] >> (8 * (i & 3))) & 0xFFu) > 0) << (c + i);
+        }
+      } else {
+        for (int w = 0; w < D; ++w) m |= (unsigned long long)(st[w] > 0) << w;
+      }
+      float sv[DMAX > 0 ? DMAX : 1];
+#pragma unroll
+      for (int w = 0; w < DMAX; ++w) sv[w] = w < D ? (((m >> w) & 1ull) ? 1.f : -1.f) : 0.f;
+#pragma unroll
+      for (int w = 0; w < DMAX; ++w) {
+        const float4* j4 = reinterpret_cast<const float4*>(sJ1 + w * 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 jq = j4[q];
+          h[4 * q + 0] = fmaf(jq.x, sv[w], h[4 * q + 0]);
+          h[4 * q + 1] = fmaf(jq.y, sv[w], h[4 * q + 1]);
+          h[4 * q + 2] = fmaf(jq.z, sv[w], h[4 * q + 2]);
+          h[4 * q + 3] = fmaf(jq.w, sv[w], h[4 * q + 3]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i + 1 < DMAX; ++i) {  // sum_{i<j} J_ij s_i s_j, rows of the upper triangle
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int j = i + 1; j < DMAX; j += 2) {
+          a0 = fmaf(sJ2[i * DMAX + j], sv[j], a0);
+          if (j + 1 < DMAX) a1 = fmaf(sJ2[i * DMAX + j + 1], sv[j + 1], a1);
+        }
+        e1 = fmaf(sv[i], a0 + a1, e1);
+      }
+    } else {
+      for (int wpos = 0; wpos < D; ++wpos) {
+        const float sw = (float)st[wpos];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) h[r] = fmaf(__ldg(I.dense.JRW + r * D + wpos), sw, h[r]);
+      }
+      for (int e = 0; e < I.n_ww; ++e) {
+        const EdgeWW q = I.ww[e];
+        e1 = fmaf(q.J, (float)(st[q.a] * st[q.b]), e1);
+      }
     }
     float lo[16], hi[16];
     half_products(h + 8, beta, lo, hi);  // g_B over the B half
@@ -435,7 +496,7 @@ __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restr
 
 cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li_in, int precision,
                          const int8_t* spins, double* logZR, double* dbeta, double* dJ,
-                         cudaStream_t s) {
+                         cudaStream_t s, int max_D) {
   (void)precision;
   if (li_in.n_inst == 0 || li_in.batch == 0) return cudaSuccess;
   int max_d = 0;
@@ -467,11 +528,19 @@ cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li_in, int pre
     const int per = (tiles + per_cta - 1) / per_cta;
     for (int k = 0; k <= lt.n_inst; ++k) lt.tile_begin[k] = k * per;
     lt.tile = per_cta;
-    const int smem = 131072 + 65536 + 64;
-    e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    dense_tc_kernel<<<lt.tile_begin[lt.n_inst], 128, smem, s>>>(d_inst, lt, spins, logZR);
-    return cudaGetLastError();
+    const int dmax = max_D;  // the largest width set of the dense instances
+    auto go = [&](auto kern, int DM) -> cudaError_t {
+      const int smem = 131072 + 65536 + 64 + 4 * (DM * 16 + DM * DM);
+      cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e2 != cudaSuccess) return e2;
+      kern<<<lt.tile_begin[lt.n_inst], 128, smem, s>>>(d_inst, lt, spins, logZR);
+      return cudaGetLastError();
+    };
+    if (dmax <= 16) return go(dense_tc_kernel<16>, 16);
+    if (dmax <= 32) return go(dense_tc_kernel<32>, 32);
+    if (dmax <= 48) return go(dense_tc_kernel<48>, 48);
+    if (dmax <= 64) return go(dense_tc_kernel<64>, 64);
+    return go(dense_tc_kernel<0>, 0);
   }
   max_d = TNVAN_MAX_D;
   if (dJ) {

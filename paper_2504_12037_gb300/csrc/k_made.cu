@@ -27,6 +27,7 @@ __device__ __forceinline__ float packed_value(const MadeDev& md, long long jj) {
   return 0.f;
 }
 
+// Weights the tiles hold (the padding excluded).
 __host__ __device__ inline long long tile_elems(const MadeDev& md) {
   return md.wtiles ? (long long)md.H1 * md.D + (long long)md.H2 * md.H1 + (long long)md.D * md.H2 : 0;
 }
@@ -36,11 +37,12 @@ __host__ __device__ inline long long tile_elems(const MadeDev& md) {
 __host__ __device__ inline int pack_tc_plan(int mask) { return (mask >> 8) - 1; }
 
 // BF16 copy of packed weight (r, c) of layer l (l < 3) into the tensor cores'
-// canonical K-major tiles: W1 [H1 x D], W2 [H2 x H1], Wo [D x H2], no swizzle.
+// canonical K-major tiles: W1 [H1 x Dp], W2 [H2 x H1], Wo [Dp x H2], no
+// swizzle, Dp = D rounded up to 16 (the padding stays zero).
 __device__ __forceinline__ void store_tile(const MadeDev& md, int l, int r, int c, float v) {
-  const int D = md.D, H1 = md.H1, H2 = md.H2;
-  const long long n1 = (long long)H1 * D, n2 = (long long)H2 * H1;
-  const int cols = l == 0 ? D : (l == 1 ? H1 : H2);
+  const int Dp = (md.D + 15) & ~15, H1 = md.H1, H2 = md.H2;
+  const long long n1 = (long long)H1 * Dp, n2 = (long long)H2 * H1;
+  const int cols = l == 0 ? Dp : (l == 1 ? H1 : H2);
   const long long base = l == 0 ? 0 : (l == 1 ? n1 : n1 + n2);
   const long long o = base + (long long)(r >> 3) * (cols / 8) * 64 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
   uint32_t u = __float_as_uint(v);

@@ -653,6 +653,7 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
                                    const float* __restrict__ partials, long long part_stride,
                                    float* __restrict__ grad, const AdamArgs adam, int k0) {
   const int k = blockIdx.y + k0;
+  if ((li.skip[k >> 5] >> (k & 31)) & 1u) return;  // reduced by another backward form
   const MadeDev& md = inst[k].made;
   float bc1 = 1.f, bc2 = 1.f;
   if (ADAM) adam_corrections(adam, bc1, bc2);

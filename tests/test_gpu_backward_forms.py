@@ -1,7 +1,8 @@
-"""The two backward forms of networks the fused BF16 kernel does not take
-(Eq. 10): the tensor-core GEMM chain (BF16 operands) and the FP32 SIMT
-backward the autotuner may pick in its place in the reduced-precision modes,
-against the oracle's REINFORCE gradient on the same samples."""
+"""The backward forms of Eq. 10 in the reduced-precision modes, against the
+oracle's REINFORCE gradient on the same samples: for networks the fused BF16
+kernel does not take, the tensor-core GEMM chain or the FP32 SIMT backward the
+autotuner may pick instead; and a multi-instance call mixing instances the
+fused kernel takes (width sets padded to a multiple of 16) with others."""
 import numpy as np
 import pytest
 import torch
@@ -16,16 +17,13 @@ from gpu_helpers import oracle_samples, to_dev_spins
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cfg,form", [(4, 1), (4, 2), (1, 2), (3, 2)])
-def test_backward_forms_match_oracle(cfg, form):
+def _case(w, n_inst, form, batch=200, seed=3):
     from paper_2504_12037_gb300.model import TNVAN
 
-    w = wl.workload(cfg)
-    model = TNVAN(w.graphs, w.widths_sets, w.hidden, w.betas, seed=3, init_scale=1.5)
+    model = TNVAN(w.graphs[:n_inst], w.widths_sets[:n_inst], w.hidden, w.betas[:n_inst], seed=seed, init_scale=1.5)
     model.ctx.set_tuning((0, 0, 0, 0, 0, 0, form))
-    batch = 200
     s_all, lq_all, lz_all, ref = [], [], [], []
-    rng = np.random.default_rng(cfg)
+    rng = np.random.default_rng(n_inst)
     for k in range(model.n):
         D = model.D[k]
         p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
@@ -46,12 +44,41 @@ def test_backward_forms_match_oracle(cfg, form):
     torch.cuda.synchronize()
     ran = model.ctx.profile_read()
     model.ctx.profile(False)
-    assert ("backward" in ran) == (form == 2) and ("gemm_wgrad" in ran) == (form == 1)
+    return model, grad, ref, ran
+
+
+def _check(gk, ref, exact):
+    assert torch.isfinite(gk).all()
+    if exact:  # FP32 arithmetic
+        assert float((gk - ref).abs().max()) <= 2e-5 * float(ref.abs().max())
+    else:  # BF16 operands: relative Frobenius error and direction
+        fro = float((gk - ref).norm() / ref.norm())
+        cos = float(torch.nn.functional.cosine_similarity(gk, ref, dim=0))
+        assert fro <= 1e-1 and cos >= 0.99, (fro, cos)
+
+
+@pytest.mark.parametrize("cfg,form", [(1, 1), (1, 2), (3, 1), (3, 2), (4, 1), (4, 2)])
+def test_backward_forms_match_oracle(cfg, form):
+    w = wl.workload(cfg)
+    model, grad, ref, ran = _case(w, len(w.graphs), form)
+    fused = False  # one hidden layer, 256-unit layers, or D = 83 (TMEM needs D <= 80 with 2 x 128 units)
+    assert ("bwd_fused" in ran) == fused
+    assert ("backward" in ran) == (form == 2 and not fused)
+    assert ("gemm_wgrad" in ran) == (form == 1 and not fused)
     for k in range(model.n):
-        gk = grad[model.offsets[k]:model.offsets[k + 1]].cpu().double()
-        if form == 2:  # FP32 arithmetic
-            assert float((gk - ref[k]).abs().max()) <= 2e-5 * float(ref[k].abs().max())
-        else:
-            fro = float((gk - ref[k]).norm() / ref[k].norm())
-            cos = float(torch.nn.functional.cosine_similarity(gk, ref[k], dim=0))
-            assert fro <= 1e-1 and cos >= 0.99
+        _check(grad[model.offsets[k]:model.offsets[k + 1]].cpu().double(), ref[k], form == 2 and not fused)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_mixed_fused_and_unfused_instances(form):
+    # ten of the multi-instance workload's lattices (width sets of 16, 36, 64,
+    # 144 and 256 spins): instances whose padded width set fits the fused
+    # kernel's TMEM (D <= 80 with two hidden layers of 128) take it, the others
+    # the chosen form, in one call; every instance's gradient against the oracle
+    w = wl.workload(5, n_instances=10)
+    model, grad, ref, ran = _case(w, 10, form, batch=160)
+    fused = [d <= 80 for d in model.D]
+    assert any(fused) and not all(fused)
+    assert "bwd_fused" in ran and (("backward" in ran) == (form == 2)) and (("gemm_wgrad" in ran) == (form == 1))
+    for k in range(model.n):
+        _check(grad[model.offsets[k]:model.offsets[k + 1]].cpu().double(), ref[k], form == 2 and not fused[k])

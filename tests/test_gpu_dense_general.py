@@ -255,11 +255,19 @@ def test_sampler_replay_sk_and_rrg():
             assert float((logZR[k * B:(k + 1) * B].cpu()[m] - lz[m]).abs().max()) / g.n <= TOL_FP32
 
 
-@pytest.mark.parametrize("case", ["sk_workload", "small_remainders"])
+@pytest.mark.parametrize("case", ["sk_workload", "small_remainders", "wide_width_sets"])
 def test_dense_block_bf16_tensor_cores(case):
+    # width sets of 48 (the SK workload), 8 to 10 and 70 to 84 spins: the W-side
+    # terms take the unrolled shared-memory form up to 64 spins, global loads beyond
     if case == "sk_workload":
         w = wl.workload(3)
         graphs, Ws, betas = w.graphs, w.widths_sets, w.betas
+    elif case == "wide_width_sets":
+        graphs, Ws = [], []
+        for n, seed in [(86, 4), (100, 5)]:
+            graphs.append(wl.sk(n, seed))
+            Ws.append(np.random.default_rng(seed).permutation(n)[:n - 16].astype(np.int32))
+        betas = [0.9, 1.4]
     else:
         graphs, Ws = [], []
         for n, nw, seed in [(20, 10, 1), (11, 8, 2), (9, 9, 3)]:
