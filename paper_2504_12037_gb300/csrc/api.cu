@@ -2623,13 +2623,32 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
     li.seed = seed;
     li.step = step;
     const bool grouped = tc_grouped_usable(ctx);
-    const int smem = tc_sampler_smem(ctx, plan, grouped);
     PROF(given ? "log_prob_tc" : "sample_tc", s);
-    if (grouped)
+    if (grouped) {
+      const int smem = tc_sampler_smem(ctx, plan, grouped);
       CK(launch_sample_tcg(ctx->d_inst, li, plan, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
-    else
-      CK(launch_sample_tc(ctx->d_inst, li, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, given, s),
+      return TNVAN_OK;
+    }
+    // per-step form: instances whose CTAs fit two per SM (<= 256 TMEM columns)
+    // launch apart from those that need a whole SM, each launch with its own
+    // shared memory (a launch's CTAs all take its largest instance's); the
+    // other class's instances get no blocks (empty tile ranges)
+    for (int cls = 0; cls < 2; ++cls) {
+      LaunchInfo lc = li;
+      int acc = 0, smem = 0;
+      for (int k = 0; k < li.n_inst; ++k) {
+        lc.tile_begin[k] = acc;
+        const MadeDev& md = ctx->inst[k].dev.made;
+        if ((md.tc[plan].tmem_cols > 256) == (cls == 1)) {
+          acc += li.tile_begin[k + 1] - li.tile_begin[k];
+          smem = std::max(smem, sample_tc_smem_bytes(md, plan));
+        }
+      }
+      lc.tile_begin[li.n_inst] = acc;
+      if (acc == 0) continue;
+      CK(launch_sample_tc(ctx->d_inst, lc, plan, ctx->inst[0].dev.made.nh, smem, d_spins, d_logq, given, s),
          "tensor-core sample kernel");
+    }
     return TNVAN_OK;
   }
   const int tile = pick_sample_tile(ctx);
