@@ -846,6 +846,18 @@ def run_workload(a):
         for L in sorted(set(g.Lx for g in w.graphs)):
             picks += [k for k, g in enumerate(w.graphs) if g.Lx == L][:2]
         traj = {"train_steps": a.train_steps, "checked_steps": checks, "instances_checked": picks, "runs": []}
+        # the gradient at step 1 (before the first update), through the C-ABI
+        # backward on the GPU's own samples: FP32 sampler + FP32 backward, and
+        # the step's BF16 samples + BF16 backward
+        gchk = {"params": mt.params.cpu().numpy().copy(), "offsets": np.asarray(mt.offsets), "runs": {}}
+        for name, prec in (("fp32", tv.FP32), ("bf16", tv.BF16)):
+            sp_g, lq_g, lz_g = mt.sample(B, 4242, 1, prec)
+            gg = torch.full_like(mt.params, float("nan"))
+            mt.ctx.backward(mt.betas, B, sp_g, lz_g, lq_g, prec, gg)
+            torch.cuda.synchronize()
+            gchk["runs"][name] = {"spins": {k: mt.spins_of(sp_g, k, B).cpu().numpy() for k in picks},
+                                  "grad": gg.cpu().numpy()}
+        traj["grad_check"] = gchk
         t0 = time.time()
         for i in range(1, a.train_steps + 1):
             if i in checks:
@@ -961,7 +973,56 @@ def oracle_train_checks(w, traj):
                                      "F_q_per_spin": fq, "F_exact_per_spin": f_ex[k],
                                      "abs_F_q_minus_F_exact_per_spin": abs(fq - f_ex[k])})
         out["checks"].append(rec)
+    if "grad_check" in traj:
+        out["grad_check_step1"] = oracle_grad_checks(w, traj["instances_checked"], traj["grad_check"])
     return out
+
+
+def oracle_grad_checks(w, picks, gchk, n_dir=3, h=1e-4):
+    """The Eq. 10 gradient at the first step against the oracle, per checked
+    instance, on the GPU's own samples: the oracle's surrogate gradient (its
+    own FP64 log q, log Z_R and weights) against the GPU backward (FP32: max
+    |delta| / max |g|; BF16: relative Frobenius error and cosine), and central
+    finite differences (step h) of the oracle's surrogate sum_b w_b log q_theta(s_b)
+    along n_dir random unit directions v against g_FP32 . v."""
+    import numpy as np
+    import torch
+
+    from oracle import estimators as est
+    from oracle import made
+
+    rng = np.random.default_rng(5)
+    res = {"fp32_max_rel": 0.0, "bf16_max_rel_fro": 0.0, "bf16_min_cos": 1.0, "fd_max_rel": 0.0,
+           "fd_step": h, "fd_directions": n_dir, "instances": len(picks)}
+    for k in picks:
+        g, W, beta = w.graphs[k], w.widths_sets[k], w.betas[k]
+        D = len(W)
+        o0, o1 = int(gchk["offsets"][k]), int(gchk["offsets"][k + 1])
+        th = gchk["params"][o0:o1].astype(np.float64)
+        for name, r in gchk["runs"].items():
+            s = torch.as_tensor(r["spins"][k].astype(np.float64))
+            lq = made.log_q(torch.as_tensor(th), D, w.hidden, s)
+            lz = oracle_log_zr(g, W, beta, s).detach()
+            wts = est.reinforce_weights(lz, lq, beta)
+            ref = est.surrogate_grad(th, D, w.hidden, s, wts).numpy()
+            gk = r["grad"][o0:o1].astype(np.float64)
+            if name == "fp32":
+                res["fp32_max_rel"] = max(res["fp32_max_rel"], float(np.abs(gk - ref).max() / np.abs(ref).max()))
+                for _ in range(n_dir):
+                    v = rng.normal(size=th.shape)
+                    v /= np.linalg.norm(v)
+                    fp = float((wts * made.log_q(torch.as_tensor(th + h * v), D, w.hidden, s)).sum())
+                    fm = float((wts * made.log_q(torch.as_tensor(th - h * v), D, w.hidden, s)).sum())
+                    fd = (fp - fm) / (2 * h)
+                    res["fd_max_rel"] = max(res["fd_max_rel"], abs(float(gk @ v) - fd) / np.linalg.norm(ref))
+            else:
+                res["bf16_max_rel_fro"] = max(res["bf16_max_rel_fro"],
+                                              float(np.linalg.norm(gk - ref) / np.linalg.norm(ref)))
+                res["bf16_min_cos"] = min(res["bf16_min_cos"],
+                                          float(gk @ ref / (np.linalg.norm(gk) * np.linalg.norm(ref))))
+    res["note"] = ("fd_max_rel = |g_FP32 . v - FD| / |g_oracle| over the directions; the oracle's weights use "
+                   "its own FP64 log q and log Z_R")
+    return res
 
 
 # ---------------------------------------------------------------------------
