@@ -318,6 +318,31 @@ int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8
                       const double* d_logZR, const float* d_logq, double* d_corr, double* h_out,
                       void* stream);
 
+/* Magnetisation and susceptibility from samples (Sec. 3: with the trained
+ * network, samples give magnetisation and susceptibility).  For each sample
+ * the exact conditional moments of the total magnetisation M = sum_i s_i
+ * given its width-set spins,
+ *   mu_b = E[M | s_b] = M_W(s_b) + <M_R>_{r|s_b},   v_b = Var(M | s_b) = Var(M_R | s_b),
+ * by each contraction kind carried in moment form (every partial sum keeps its
+ * weight, the conditional mean and the conditional variance of the
+ * magnetisation summed into it; two branches merge by the law of total
+ * variance), FP32 arithmetic with FP64 sums over strips and components.  With
+ * the self-normalised importance weights w_b of tnvan_observables:
+ *   h_out[6k+0] <M>    = sum_b w_b mu_b
+ *   h_out[6k+1] <M^2>  = sum_b w_b (mu_b^2 + v_b)
+ *   h_out[6k+2] chi    = beta (<M^2> - <M>^2) / N   (per spin)
+ *   h_out[6k+3] <M>_q  = mean_b mu_b,  h_out[6k+4] <M^2>_q = mean_b (mu_b^2 + v_b)
+ *   h_out[6k+5] ESS    = 1 / sum_b w_b^2
+ *   d_mag_mean, d_mag_var  device double [n_inst*batch] out (mu_b, v_b), or
+ *                  NULL (the context's workspace holds them).
+ * h_out: host double [6 * n_instances].  Every contraction kind.  Shares the
+ * workspace of tnvan_observables (do not overlap the two).  Synchronises
+ * `stream`.  Errors: TNVAN_E_ARG, TNVAN_E_STATE, TNVAN_E_NOMEM,
+ * TNVAN_E_UNSUPPORTED (tables beyond shared memory), TNVAN_E_CUDA. */
+int tnvan_magnetisation(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                        const double* d_logZR, const float* d_logq, double* d_mag_mean, double* d_mag_var,
+                        double* h_out, void* stream);
+
 /* Eq. 10: REINFORCE gradient of F_q for every instance,
  *   grad = sum_b w_b grad_theta log q(s_b),  w_b = -(l_b - mean_b l) / (beta batch),
  * (the batch mean is the baseline; it leaves the expectation unchanged), by a

@@ -21,6 +21,11 @@ Modules and the passages they restate:
   made       Eq. 6-8 (MADE conditionals, log q, ancestral sampling).
   estimators Eq. 5, 9, 10 (F_q, importance-sampled log Z, REINFORCE weights
              and gradient, exact enumeration of F_q) and the Adam update.
+  kacward    the Kac-Ward determinant: exact ln Z of an open planar lattice
+             (the ferromagnet of Sec. 4, Fig. 2).
+  magnetisation  Sec. 3 observables: conditional magnetisation moments from
+             a uniform-field derivative of any contraction above, and their
+             importance-weighted averages (magnetisation, susceptibility).
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
 closed form, brute force, or an invariant, except where its docstring says

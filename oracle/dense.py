@@ -19,8 +19,9 @@ def coupling_matrix(n, ei, ej, J) -> torch.Tensor:
     return M + M.T
 
 
-def log_zr_dense(n, ei, ej, J, beta, W, sW: torch.Tensor, chunk: int = 64) -> torch.Tensor:
-    """Plain 2^|R| sum for each row of sW [B, |W|] (|R| <= 20)."""
+def log_zr_dense(n, ei, ej, J, beta, W, sW: torch.Tensor, chunk: int = 64, field=None) -> torch.Tensor:
+    """Plain 2^|R| sum for each row of sW [B, |W|] (|R| <= 20).  `field`
+    ([B] or a scalar): a uniform field on R, added to every R spin's field."""
     W = np.asarray(W, np.int64)
     R = np.setdiff1d(np.arange(n), W)
     M = coupling_matrix(n, ei, ej, J)
@@ -33,6 +34,8 @@ def log_zr_dense(n, ei, ej, J, beta, W, sW: torch.Tensor, chunk: int = 64) -> to
     out = []
     for start in range(0, sW.shape[0], chunk):
         h = sW[start:start + chunk] @ J_RW.T  # [b, |R|] fields from W
+        if field is not None:
+            h = h + (field[start:start + chunk][:, None] if torch.is_tensor(field) and field.dim() > 0 else field)
         expo = beta * (e_rr[None, :] + h @ rc.T)  # [b, S]
         out.append(torch.logsumexp(expo, dim=1))
     return w_energy_term(ei, ej, J, beta, W, sW) + torch.cat(out)

@@ -99,14 +99,17 @@ def _comp_elim(J, beta, comp, inner, h, order=None, order_rule="min_degree"):
 
 
 def log_zr_general(n, ei, ej, J, beta, W, sW: torch.Tensor, enum_max: int = 16,
-                   order_rule: str = "min_degree") -> torch.Tensor:
-    """-beta E_1(s) + sum_c ln Z_c(s) for each row of sW [B, |W|]."""
+                   order_rule: str = "min_degree", field=None) -> torch.Tensor:
+    """-beta E_1(s) + sum_c ln Z_c(s) for each row of sW [B, |W|].  `field`
+    ([B] or a scalar): a uniform field on R, added to every R spin's field."""
     J = torch.as_tensor(J, dtype=DT) if not torch.is_tensor(J) else J
     sW = sW.to(DT)
     total = w_energy_term(ei, ej, J, beta, W, sW)
     for comp in components(n, ei, ej, W):
         inner = _inner_edges(ei, ej, comp)
         h = _fields(ei, ej, J, W, sW, comp)
+        if field is not None:
+            h = h + (field[:, None] if torch.is_tensor(field) and field.dim() > 0 else field)
         if len(comp) <= enum_max:
             total = total + _comp_enum(J, beta, comp, inner, h)
         else:

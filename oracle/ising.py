@@ -44,9 +44,12 @@ def log_z_brute(n: int, ei, ej, J, beta) -> torch.Tensor:
     return total
 
 
-def log_zr_enum(n: int, ei, ej, J, beta, W, sW: torch.Tensor) -> torch.Tensor:
+def log_zr_enum(n: int, ei, ej, J, beta, W, sW: torch.Tensor, field=None) -> torch.Tensor:
     """log Z_R(s) = ln sum_{r in {+-1}^|R|} exp(-beta E(s, r)) for each row s
-    of sW [B, |W|] (Eq. 3-4 with E_1 included), by enumerating R (|R| <= 20)."""
+    of sW [B, |W|] (Eq. 3-4 with E_1 included), by enumerating R (|R| <= 20).
+    With `field` ([B] or a scalar), a uniform field on the R spins adds
+    beta * field * sum_{i in R} r_i to every exponent (its derivatives at 0
+    give the magnetisation moments of R)."""
     W = np.asarray(W, np.int64)
     R = np.setdiff1d(np.arange(n), W)
     rc = all_configs(len(R))  # [2^|R|, |R|]
@@ -55,7 +58,11 @@ def log_zr_enum(n: int, ei, ej, J, beta, W, sW: torch.Tensor) -> torch.Tensor:
         full = torch.zeros(rc.shape[0], n, dtype=DT)
         full[:, torch.as_tensor(R)] = rc
         full[:, torch.as_tensor(W)] = sW[b].to(DT)[None, :]
-        out.append(torch.logsumexp(-beta * energy(ei, ej, J, full), dim=0))
+        expo = -beta * energy(ei, ej, J, full)
+        if field is not None:
+            hb = field[b] if torch.is_tensor(field) and field.dim() > 0 else field
+            expo = expo + beta * hb * rc.sum(1)
+        out.append(torch.logsumexp(expo, dim=0))
     return torch.stack(out)
 
 

@@ -41,10 +41,11 @@ def _chain(diags, verts):
     return acc + torch.log(v.sum(dim=1))
 
 
-def log_zr_lattice(n, ei, ej, J, beta, W, sW: torch.Tensor, Lx: int) -> torch.Tensor:
+def log_zr_lattice(n, ei, ej, J, beta, W, sW: torch.Tensor, Lx: int, field=None) -> torch.Tensor:
     """log Z_R(s) = -beta E_1(s) + sum_c ln Z_c(s) (Eq. 4) for sW [B, |W|] on a
     lattice with spin index y*Lx + x.  Each leftover component must occupy the
-    same columns in a run of consecutive rows."""
+    same columns in a run of consecutive rows.  `field` ([B] or a scalar): a
+    uniform field on R, beta * field * (sum of the row's spins) in every row."""
     J = torch.as_tensor(J, dtype=DT) if not torch.is_tensor(J) else J
     sW = sW.to(DT)
     B = sW.shape[0]
@@ -64,6 +65,9 @@ def log_zr_lattice(n, ei, ej, J, beta, W, sW: torch.Tensor, Lx: int) -> torch.Te
         cpos = {c: k for k, c in enumerate(cols)}
         X = all_configs(w)  # [2^w, w]
         diags = [torch.zeros(B, 2 ** w, dtype=DT) for _ in rows]
+        if field is not None:
+            fb = field[:, None] if torch.is_tensor(field) and field.dim() > 0 else field
+            diags = [d + beta * fb * X.sum(1)[None, :] for d in diags]
         verts = [torch.zeros(2 ** w, 2 ** w, dtype=DT) for _ in rows[:-1]]
         cset = set(comp)
         for e, (a, b) in enumerate(edges):

@@ -182,6 +182,9 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
       for (int c = 0; c < TNVAN_MAX_STRIP_W; ++c) R.ev[c] = -1;
       R.eL = R.eR = -1;
       R.posL = R.posR = -1;
+      R.tau_mask = 0;
+      for (int c = 0; c < w; ++c)
+        if (tau[c] < 0.f) R.tau_mask |= 1 << c;
       for (int c = 0; c + 1 < w; ++c) {
         int e = eid(y * Lx + x0 + c, y * Lx + x0 + c + 1);
         if (e >= 0) {
@@ -1962,6 +1965,92 @@ int tnvan_observables(tnvan_ctx* ctx, const double* betas, int batch, const int8
   CK(cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "sums copy");
   CK(cudaStreamSynchronize(s), "stream sync");
   for (int k = 0; k < 3 * n; ++k) h_out[k] = sums[k];
+  return TNVAN_OK;
+}
+
+int tnvan_magnetisation(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins,
+                        const double* d_logZR, const float* d_logq, double* d_mag_mean, double* d_mag_var,
+                        double* h_out, void* stream) {
+  if (!ctx) return TNVAN_E_ARG;
+  if (batch < 1) return fail(ctx, TNVAN_E_ARG, "batch must be >= 1");
+  if (!d_spins || !d_logZR || !d_logq || !h_out) return fail(ctx, TNVAN_E_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  const int n = (int)ctx->inst.size();
+  const size_t nb = (size_t)n * batch;
+  const size_t bytes = 2 * nb * sizeof(double) + 5 * (size_t)n * sizeof(double) + nb * sizeof(float) + 64;
+  if (bytes > ctx->obs_bytes) {
+    if (ctx->d_obs) cudaFree(ctx->d_obs);
+    ctx->d_obs = nullptr;
+    ctx->obs_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_obs, bytes);
+    if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(observables): %s", cudaGetErrorString(e));
+    ctx->obs_bytes = bytes;
+  }
+  double* mean = d_mag_mean ? d_mag_mean : static_cast<double*>(ctx->d_obs);
+  double* var = d_mag_var ? d_mag_var : static_cast<double*>(ctx->d_obs) + nb;
+  double* d_sums = static_cast<double*>(ctx->d_obs) + 2 * nb;
+  float* d_w = reinterpret_cast<float*>(d_sums + 5 * n);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LaunchInfo li;
+  if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  // importance weights (logZ_IS from the F_q reduction, in tnvan_free_energy's workspace)
+  CK(launch_reduce(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats_fe, ctx->d_status + 4 + TNVAN_MAX_INST, s),
+     "reduce kernels");
+  CK(launch_observables(li, d_logZR, d_logq, ctx->d_stats_fe, nullptr, d_w, nullptr, false, s), "weights kernel");
+  // per-sample moments, by contraction kind
+  bool k0 = false, k1 = false, k2 = false;
+  int max_D = 0, arena = 0, nsteps = 0;
+  int strip_sm = 0;
+  for (const Instance& in : ctx->inst) {
+    max_D = std::max(max_D, (int)in.W.size());
+    if (in.kind == 0) {
+      k0 = true;
+      strip_sm = std::max(strip_sm, strip_smem_bytes(in, 128));
+    } else if (in.kind == 1) {
+      k1 = true;
+    } else {
+      k2 = true;
+      arena = std::max(arena, in.g_max_live);
+      nsteps = std::max(nsteps, (int)in.gfstep.size());
+    }
+  }
+  if (k0) {
+    if (strip_sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "strip tables need %d B of shared memory", strip_sm);
+    LaunchInfo ls;
+    if ((rc = fill_launch(ctx, betas, batch, 128, ls))) return rc;
+    CK(launch_strips_mom(ctx->d_inst, ls, strip_sm, d_spins, mean, var, s), "strip moments kernel");
+  }
+  if (k1) CK(launch_dense_mom(ctx->d_inst, li, max_D, d_spins, mean, var, s), "dense moments kernel");
+  if (k2) {
+    const int GL = gen_lanes(ctx, batch, 16), T = 128 / GL;
+    const bool glob = gen_tables_global(T, [&](int t, bool gg) { return general_mom_smem_bytes(arena, max_D, t, GL, gg); });
+    const int sm = general_mom_smem_bytes(arena, max_D, T, GL, glob);
+    if (sm > 227 * 1024) return fail(ctx, TNVAN_E_UNSUPPORTED, "elimination tables need %d B of shared memory", sm);
+    LaunchInfo lg;
+    if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
+    CK(launch_general_pp(ctx->d_inst, lg, nsteps, s), "elimination bond products");
+    float* gs = nullptr;
+    if (glob) {
+      if ((rc = ensure_gen_scratch(ctx, 0, general_mom_scratch_floats(lg, arena, GL)))) return rc;
+      gs = ctx->d_gen_scratch[0];
+    }
+    CK(launch_general_mom(ctx->d_inst, lg, sm, arena, GL, d_spins, mean, var, gs, s), "elimination moments kernel");
+  }
+  CK(launch_obs_mag(li, mean, var, d_w, d_sums, s), "magnetisation reduction");
+  std::vector<double> sums(5 * n);
+  CK(cudaMemcpyAsync(sums.data(), d_sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "sums copy");
+  CK(cudaStreamSynchronize(s), "stream sync");
+  for (int k = 0; k < n; ++k) {
+    const double* a = sums.data() + 5 * k;
+    h_out[6 * k + 0] = a[0];
+    h_out[6 * k + 1] = a[1];
+    h_out[6 * k + 2] = li.beta[k] * (a[1] - a[0] * a[0]) / (double)ctx->inst[k].n;
+    h_out[6 * k + 3] = a[2];
+    h_out[6 * k + 4] = a[3];
+    h_out[6 * k + 5] = a[4];
+  }
   return TNVAN_OK;
 }
 

@@ -100,4 +100,26 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Merge of two weighted branches in the moment form used for the
+// magnetisation moments: each branch carries its (unnormalised) weight v, the
+// conditional mean m and the conditional variance q of a sum over the
+// branch's states.  The merged branch has weight v0 + v1, mean
+// m1 + p0 (m0 - m1) and, by the law of total variance,
+// q = p0 q0 + p1 q1 + p0 p1 (m0 - m1)^2 with p_i = v_i / (v0 + v1) -- the
+// variance is never formed as a difference of raw second moments.  Zero
+// total weight keeps branch 0 (any finite value: it is weighted by 0).
+__device__ __forceinline__ void moment_mix(float v0, float m0, float q0, float v1, float m1, float q1, float& v,
+                                           float& m, float& q) {
+  const float vs = v0 + v1;
+  if (vs > 0.f) {
+    const float p0 = v0 / vs, p1 = v1 / vs, d = m0 - m1;
+    m = fmaf(p0, d, m1);
+    q = fmaf(p0, q0, p1 * q1) + p0 * p1 * d * d;
+  } else {
+    m = m0;
+    q = q0;
+  }
+  v = vs;
+}
+
 }  // namespace tnvan

@@ -127,6 +127,7 @@ struct alignas(16) StripRow {
   int eh[TNVAN_MAX_STRIP_W - 1];  // edge ids (-1 none), for d/dJ
   int eL, eR;
   int ev[TNVAN_MAX_STRIP_W];
+  int tau_mask;  // bit c set iff the gauge flips column c in this row (model spin = -strip spin)
 };
 
 struct StripDev {
@@ -380,6 +381,24 @@ cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int
 // reduces dbeta and wmul to out[3k..3k+2] = U, U_q, effective sample size.
 cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const float* logq, const double* stats,
                                const double* dbeta, float* wmul, double* out, bool energies, cudaStream_t s);
+// Magnetisation moments (tnvan_magnetisation): per sample E[M | s] and
+// Var(M | s) of the whole system's magnetisation given the width set, by
+// contraction kind (strips: li.tile samples per CTA, smem as strip_smem_bytes;
+// dense: builds the block's table at li.beta; elimination: as launch_general,
+// tables x 3, garena of general_mom_scratch_floats when too large).
+cudaError_t launch_strips_mom(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, const int8_t* spins,
+                              double* mag_mean, double* mag_var, cudaStream_t s);
+cudaError_t launch_dense_mom(const InstDev* d_inst, const LaunchInfo& li, int max_D, const int8_t* spins,
+                             double* mag_mean, double* mag_var, cudaStream_t s);
+int general_mom_smem_bytes(int arena, int D, int T, int GL, bool glob);
+size_t general_mom_scratch_floats(const LaunchInfo& li, int arena, int GL);
+cudaError_t launch_general_mom(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int GL,
+                               const int8_t* spins, double* mag_mean, double* mag_var, float* garena,
+                               cudaStream_t s);
+// out[5k + 0..4] = <M>, <M^2> (importance-weighted), the same under q, and
+// the effective sample size, from the moments and the multipliers B w_b.
+cudaError_t launch_obs_mag(const LaunchInfo& li, const double* mean, const double* var, const float* wmul,
+                           double* out, cudaStream_t s);
 // Eq. 9 statistics of instances [k0, k1) (k1 < 0: all) of the launch into
 // stats[8k + 0..7] = F_q, F_IS, stderr, logZ_IS, mean l, #non-finite, var l,
 // n (the backward's baseline is [4], its sample count [5] + [7]).

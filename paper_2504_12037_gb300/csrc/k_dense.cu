@@ -563,4 +563,162 @@ cudaError_t launch_dense(const InstDev* d_inst, const LaunchInfo& li_in, int pre
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Magnetisation moments of the dense block (observables from samples, Sec. 3):
+// the conditional mean and variance of M_R = sum of the real R spins given
+// the width set, from the same factored sum.  With P(a, b) = g_A(a) C(a,b)
+// g_B(b) / z and M_R = M_A(a) + M_B(b) (phantom spins excluded):
+//   pass 1:  m = sum_a g_A(a) [M_A(a) (C g_B)(a) + (C (g_B M_B))(a)] / z;
+//   pass 2:  var = sum_a g_A(a) [al^2 (C g_B) + 2 al (C (g_B be)) + C (g_B be^2)](a) / z
+// with al = M_A - m/2 and be = M_B - m/2, so the variance is a sum of
+// non-negative centred terms.  FP32, DN_T samples per CTA, thread t = row a
+// of C.  Output E[M | s] = M_W(s) + m and Var(M | s) = var.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float half_mag(int x, int n) {
+  return (float)(n - 2 * __popc(x & ((1 << n) - 1)));
+}
+
+__global__ void __launch_bounds__(256) dense_mom_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                        const int8_t* __restrict__ spins,
+                                                        double* __restrict__ mag_mean, double* __restrict__ mag_var) {
+  extern __shared__ float sm[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  if (I.kind != 1) return;
+  const int t = threadIdx.x, D = I.D;
+  const int b0 = (blockIdx.x - li.tile_begin[k]) * DN_T;
+  const int nv = min(DN_T, li.batch - b0);
+  const float beta = (float)li.beta[k];
+  const int nA = I.dense.nA, nB = I.dense.nB;
+  float* gA = sm;                    // [T][256]
+  float* gB = gA + DN_T * 256;       // [T][256]
+  float* h = gB + DN_T * 256;        // [T][16]
+  float* e1 = h + DN_T * 16;         // [8 warps][T] (fields helper scratch)
+  float* red = e1 + 8 * DN_T;        // [8 warps][T][2]
+  float* cen = red + 8 * DN_T * 2;   // [T] m / 2
+  float* zs = cen + DN_T;            // [T] z
+  int8_t* sp = reinterpret_cast<int8_t*>(zs + DN_T);  // [T][D]
+  const int8_t* g = spins + I.spin_units * li.batch + (long long)b0 * D;
+  for (int e = t; e < nv * D; e += blockDim.x) sp[e] = g[e];
+  __syncthreads();
+  dense_fields(I, sp, D, nv, h, e1, t);
+  __syncthreads();
+  for (int tt = 0; tt < DN_T; ++tt) {
+    float sa = 0.f, aa = 0.f, sb = 0.f, ab = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float ha = h[tt * 16 + i], hb = h[tt * 16 + 8 + i];
+      sa = fmaf(ha, sgn_bit(t, i), sa);
+      aa += fabsf(ha);
+      sb = fmaf(hb, sgn_bit(t, i), sb);
+      ab += fabsf(hb);
+    }
+    gA[tt * 256 + t] = expf(beta * (sa - aa));
+    gB[tt * 256 + t] = expf(beta * (sb - ab));
+  }
+  __syncthreads();
+  const float4* crow = reinterpret_cast<const float4*>(I.dense.C32 + t * 256);
+  const float ma = half_mag(t, nA);
+  float y0[DN_T], y1[DN_T];
+#pragma unroll
+  for (int tt = 0; tt < DN_T; ++tt) y0[tt] = y1[tt] = 0.f;
+  // pass 1: C g_B and C (g_B M_B)
+  for (int b4 = 0; b4 < 64; ++b4) {
+    const float4 c = __ldg(crow + b4);
+    const float m0 = half_mag(4 * b4, nB), m1 = half_mag(4 * b4 + 1, nB), m2 = half_mag(4 * b4 + 2, nB),
+                m3 = half_mag(4 * b4 + 3, nB);
+#pragma unroll
+    for (int tt = 0; tt < DN_T; ++tt) {
+      const float4 v = reinterpret_cast<const float4*>(gB + tt * 256)[b4];
+      const float p0 = c.x * v.x, p1 = c.y * v.y, p2 = c.z * v.z, p3 = c.w * v.w;
+      y0[tt] += (p0 + p1) + (p2 + p3);
+      y1[tt] = fmaf(p0, m0, fmaf(p1, m1, fmaf(p2, m2, fmaf(p3, m3, y1[tt]))));
+    }
+  }
+#pragma unroll
+  for (int tt = 0; tt < DN_T; ++tt) {
+    const float ga = gA[tt * 256 + t];
+    const float z = warp_sum(ga * y0[tt]);
+    const float s1 = warp_sum(ga * fmaf(ma, y0[tt], y1[tt]));
+    if ((t & 31) == 0) {
+      red[((t >> 5) * DN_T + tt) * 2] = z;
+      red[((t >> 5) * DN_T + tt) * 2 + 1] = s1;
+    }
+  }
+  __syncthreads();
+  if (t < DN_T) {
+    float z = 0.f, s1 = 0.f;
+    for (int w = 0; w < 8; ++w) {
+      z += red[(w * DN_T + t) * 2];
+      s1 += red[(w * DN_T + t) * 2 + 1];
+    }
+    cen[t] = t < nv ? 0.5f * s1 / z : 0.f;
+    zs[t] = z;
+  }
+  __syncthreads();
+  // pass 2: centred second moment
+#pragma unroll
+  for (int tt = 0; tt < DN_T; ++tt) y1[tt] = 0.f;
+  float y2[DN_T];
+#pragma unroll
+  for (int tt = 0; tt < DN_T; ++tt) y2[tt] = 0.f;
+  for (int b4 = 0; b4 < 64; ++b4) {
+    const float4 c = __ldg(crow + b4);
+    const float m0 = half_mag(4 * b4, nB), m1 = half_mag(4 * b4 + 1, nB), m2 = half_mag(4 * b4 + 2, nB),
+                m3 = half_mag(4 * b4 + 3, nB);
+#pragma unroll
+    for (int tt = 0; tt < DN_T; ++tt) {
+      const float4 v = reinterpret_cast<const float4*>(gB + tt * 256)[b4];
+      const float ct = cen[tt];
+      const float d0 = m0 - ct, d1 = m1 - ct, d2 = m2 - ct, d3 = m3 - ct;
+      const float p0 = c.x * v.x * d0, p1 = c.y * v.y * d1, p2 = c.z * v.z * d2, p3 = c.w * v.w * d3;
+      y1[tt] += (p0 + p1) + (p2 + p3);
+      y2[tt] = fmaf(p0, d0, fmaf(p1, d1, fmaf(p2, d2, fmaf(p3, d3, y2[tt]))));
+    }
+  }
+  __syncthreads();  // red is reused
+#pragma unroll
+  for (int tt = 0; tt < DN_T; ++tt) {
+    const float ga = gA[tt * 256 + t];
+    const float al = ma - cen[tt];
+    const float q = warp_sum(ga * fmaf(al * al, y0[tt], fmaf(2.f * al, y1[tt], y2[tt])));
+    if ((t & 31) == 0) red[((t >> 5) * DN_T + tt) * 2] = q;
+  }
+  __syncthreads();
+  if (t < nv) {
+    float q = 0.f;
+    for (int w = 0; w < 8; ++w) q += red[(w * DN_T + t) * 2];
+    int mw = 0;
+    for (int j = 0; j < D; ++j) mw += sp[t * D + j];
+    const long long o = (long long)k * li.batch + b0 + t;
+    mag_mean[o] = (double)mw + 2.0 * (double)cen[t];
+    mag_var[o] = (double)(q / zs[t]);
+  }
+}
+
+int dense_mom_smem_bytes(int D) {
+  return (2 * DN_T * 256 + DN_T * 16 + 8 * DN_T + 8 * DN_T * 2 + 2 * DN_T) * 4 + DN_T * D;
+}
+
+cudaError_t launch_dense_mom(const InstDev* d_inst, const LaunchInfo& li_in, int max_D, const int8_t* spins,
+                             double* mag_mean, double* mag_var, cudaStream_t s) {
+  if (li_in.n_inst == 0 || li_in.batch == 0) return cudaSuccess;
+  LaunchInfo li = li_in;
+  int acc = 0;
+  for (int k = 0; k < li.n_inst; ++k) {
+    li.tile_begin[k] = acc;
+    acc += (li.batch + DN_T - 1) / DN_T;
+  }
+  li.tile_begin[li.n_inst] = acc;
+  li.tile = DN_T;
+  dense_table_kernel<<<dim3(256, li.n_inst), 256, 0, s>>>(d_inst, li);  // C at this call's betas
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int smem = dense_mom_smem_bytes(max_D);
+  e = cudaFuncSetAttribute(dense_mom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  dense_mom_kernel<<<acc, 256, smem, s>>>(d_inst, li, spins, mag_mean, mag_var);
+  return cudaGetLastError();
+}
+
 }  // namespace tnvan

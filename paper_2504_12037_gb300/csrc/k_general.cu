@@ -579,4 +579,122 @@ cudaError_t launch_general(const InstDev* d_inst, const LaunchInfo& li, int smem
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Magnetisation moments of the elimination components (observables from
+// samples, Sec. 3).  The forward program run in the moment form: every table
+// entry carries, besides its weight, the conditional mean and variance of the
+// magnetisation of the spins already summed into it given its scope.  A
+// step's product term at (x, sigma) has mean sigma + sum of its inputs' means
+// and variance the sum of their variances (the inputs cover disjoint
+// eliminated spins, independent given the scope), and summing sigma out
+// merges the two terms (moment_mix).  A component's final entry gives the
+// conditional mean and variance of its magnetisation; components are
+// independent given the width set.  Tabulated components run their programs
+// here too.  Tables: weights, means, variances, each [entry][sample].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void run_component_mom(const GenDev& G, int c, const int8_t* s, float* A, float* Mu,
+                                                  float* Q, int RS, int lane, int GL, float beta, double& mean,
+                                                  double& var) {
+  const int* H = G.fprog + G.fhdr[c];
+  const int nsteps = H[0], fin = H[1];
+  const int g0 = G.comp_step0[c];
+  for (int st = 0; st < nsteps; ++st) {
+    const StepRec r = step_at(G, g0 + st);
+    const float h = field_of(G, r.fb, r.fc, s);
+    const float ah = fabsf(h);
+    const float fv[2] = {expf(beta * (h - ah)), expf(beta * (-h - ah))};
+    const int M = 1 << r.m, E = 2 * M;
+    const float* pp = G.pp + r.ppo;
+    const unsigned short* mp = G.map + r.mo;
+    const int out = r.out_live;
+    float mx = 0.f;
+    for (int x = lane; x < M; x += GL) {
+      float tv[2], tm[2], tq[2];
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        const int ext = x | (sg << r.m);
+        float p = fv[sg] * pp[ext], m = sg ? -1.f : 1.f, q = 0.f;
+        for (int i = 0; i < r.nin; ++i) {
+          const int a = (r.io[3 * i] + mp[i * E + ext]) * RS;
+          p *= A[a];
+          m += Mu[a];
+          q += Q[a];
+        }
+        tv[sg] = p;
+        tm[sg] = m;
+        tq[sg] = q;
+      }
+      float v, m, q;
+      moment_mix(tv[0], tm[0], tq[0], tv[1], tm[1], tq[1], v, m, q);
+      A[(out + x) * RS] = v;
+      Mu[(out + x) * RS] = m;
+      Q[(out + x) * RS] = q;
+      mx = fmaxf(mx, v);
+    }
+    mx = group_max(mx, GL);
+    const float sc = pow2i(-exponent_of(mx));
+    for (int x = lane; x < M; x += GL) A[(out + x) * RS] *= sc;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    mean += (double)Mu[fin * RS];
+    var += (double)Q[fin * RS];
+  }
+}
+
+__global__ void __launch_bounds__(128) general_mom_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                          int arena_floats, int GL, const int8_t* __restrict__ spins,
+                                                          double* __restrict__ mag_mean, double* __restrict__ mag_var,
+                                                          float* __restrict__ garena) {
+  extern __shared__ float sm[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  if (I.kind != 2) return;
+  const int S = li.tile, slot = threadIdx.x / GL, lane = threadIdx.x % GL;
+  const int b0 = (blockIdx.x - li.tile_begin[k]) * S, b = b0 + slot;
+  const float beta = (float)li.beta[k];
+  const int D = I.D, Dp = padded_bytes(D);
+  const int RS = gen_row_stride(S, GL);
+  const size_t cta_floats = (size_t)arena_floats * RS * 3;
+  float* base = garena ? garena + (size_t)blockIdx.x * cta_floats : sm;
+  float* A = base + slot;
+  float* Mu = A + (size_t)arena_floats * RS;
+  float* Q = Mu + (size_t)arena_floats * RS;
+  int8_t* ssp = reinterpret_cast<int8_t*>(garena ? sm : sm + cta_floats);
+  const GenDev& G = I.gen;
+  const int n_valid = min(S, li.batch - b0);
+  stage_spins(ssp, spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, S, D, Dp);
+  __syncthreads();
+  const int8_t* s = ssp + slot * Dp;
+  double mean = 0.0, var = 0.0;
+  for (int c = 0; c < G.n_comp; ++c) run_component_mom(G, c, s, A, Mu, Q, RS, lane, GL, beta, mean, var);
+  if (lane != 0 || b >= li.batch) return;
+  int mw = 0;
+  for (int j = 0; j < D; ++j) mw += s[j];
+  const long long o = (long long)k * li.batch + b;
+  mag_mean[o] = (double)mw + mean;
+  mag_var[o] = var;
+}
+
+int general_mom_smem_bytes(int arena, int D, int T, int GL, bool glob) {
+  int w4 = (D + 3) / 4;
+  if ((w4 & 1) == 0) ++w4;
+  return (glob ? 0 : arena * gen_row_stride(T, GL) * 4 * 3) + T * 4 * w4;
+}
+
+size_t general_mom_scratch_floats(const LaunchInfo& li, int arena, int GL) {
+  return (size_t)arena * gen_row_stride(li.tile, GL) * 3 * (size_t)li.tile_begin[li.n_inst];
+}
+
+cudaError_t launch_general_mom(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, int arena, int GL,
+                               const int8_t* spins, double* mag_mean, double* mag_var, float* garena,
+                               cudaStream_t s) {
+  const int nblk = li.tile_begin[li.n_inst];
+  if (nblk == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(general_mom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  general_mom_kernel<<<nblk, li.tile * GL, smem_bytes, s>>>(d_inst, li, arena, GL, spins, mag_mean, mag_var, garena);
+  return cudaGetLastError();
+}
+
 }  // namespace tnvan

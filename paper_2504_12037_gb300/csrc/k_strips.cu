@@ -893,4 +893,124 @@ cudaError_t launch_ww(const InstDev* d_inst, const LaunchInfo& li, const int8_t*
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Magnetisation moments of the strips (observables from samples, Sec. 3).
+// For one sample, the conditional mean and variance of M_strip = sum of the
+// strip's model spins given the width set, by the row chain in the moment
+// form: each state x of the current row carries the chain's weight v(x) and
+// the mean mu(x) and variance q(x) of the rows' magnetisation so far given
+// that the current row is in x.  A vertical factor I + t X on bit c mixes x
+// with x ^ (1 << c) at weight t (moment_mix), the diagonal D_y scales v and adds the
+// row's magnetisation to mu (q unchanged: it is fixed given x), and the end
+// sums the states the same way.  Model spin = tau * strip spin (the planner's
+// gauge): the row's magnetisation of state x is w - 2 popc((x ^ tau_mask) & (2^w - 1)).
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ void strip_moments(const StripTab& tb, const StripRow* __restrict__ rows, int L, const int8_t* srow,
+                              float& mean, float& var) {
+  constexpr int NX = 1 << W;
+  float v[NX], mu[NX], q[NX];
+  for (int y = 0; y < L; ++y) {
+    const int idx = row_index(tb.pos, y, srow);
+    const float* dy = tb.diag + (y * 4 + idx) * NX;
+    const int tm = rows[y].tau_mask;
+    if (y > 0) {
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const float t = tb.vert[(y - 1) * W + c].y;
+#pragma unroll
+        for (int x = 0; x < NX; ++x) {
+          if ((x >> c) & 1) continue;
+          const int x1 = x | (1 << c);
+          const float v0 = v[x], m0 = mu[x], q0 = q[x], v1 = v[x1], m1 = mu[x1], q1 = q[x1];
+          moment_mix(v0, m0, q0, t * v1, m1, q1, v[x], mu[x], q[x]);
+          moment_mix(v1, m1, q1, t * v0, m0, q0, v[x1], mu[x1], q[x1]);
+        }
+      }
+    }
+    float mx = 0.f;
+#pragma unroll
+    for (int x = 0; x < NX; ++x) {
+      const float a = (float)(W - 2 * __popc((x ^ tm) & (NX - 1)));
+      if (y == 0) {
+        v[x] = dy[x];
+        mu[x] = a;
+        q[x] = 0.f;
+      } else {
+        v[x] *= dy[x];
+        mu[x] += a;
+      }
+      mx = fmaxf(mx, v[x]);
+    }
+    const float sc = pow2i(-exponent_of(mx));
+#pragma unroll
+    for (int x = 0; x < NX; ++x) v[x] *= sc;
+  }
+  float Z = 0.f, m = 0.f;
+#pragma unroll
+  for (int x = 0; x < NX; ++x) Z += v[x];
+#pragma unroll
+  for (int x = 0; x < NX; ++x) m = fmaf(v[x] / Z, mu[x], m);
+  float qq = 0.f;
+#pragma unroll
+  for (int x = 0; x < NX; ++x) {
+    const float d = mu[x] - m;
+    qq = fmaf(v[x] / Z, fmaf(d, d, q[x]), qq);
+  }
+  mean = m;
+  var = qq;
+}
+
+// One thread per sample: E[M | s] = M_W(s) + sum over strips of the strip
+// means, Var(M | s) = sum of the strip variances (the strips are independent
+// given the width set), both FP64 sums of the FP32 per-strip values.
+__global__ void __launch_bounds__(128) strips_mom_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                                         const int8_t* __restrict__ spins,
+                                                         double* __restrict__ mag_mean, double* __restrict__ mag_var) {
+  extern __shared__ float sm[];
+  const int k = find_inst(li, blockIdx.x);
+  const InstDev& I = inst[k];
+  if (I.kind != 0) return;
+  const int T = li.tile, t = threadIdx.x;
+  const int b0 = (blockIdx.x - li.tile_begin[k]) * T, b = b0 + t;
+  const int D = I.D, Dp = padded_row_bytes(D);
+  build_strip_tables(I, (float)li.beta[k], sm, t, T, false);  // tables without ddiag (adjoint layout)
+  int8_t* ssp = reinterpret_cast<int8_t*>(sm + I.strip_tab_floats);
+  const int n_valid = min(T, li.batch - b0);
+  stage_spins(spins + I.spin_units * li.batch + (long long)b0 * D, n_valid, D, Dp, ssp, t, T);
+  __syncthreads();
+  if (b >= li.batch) return;
+  const int8_t* srow = ssp + t * Dp;
+  int mw = 0;
+  for (int j = 0; j < D; ++j) mw += srow[j];
+  double mean = (double)mw, var = 0.0;
+  for (int st = 0; st < I.n_strips; ++st) {
+    const StripDev& sd = I.strips[st];
+    const StripTab tb = strip_tab_at(sm + strip_tab_offset(I, st, false), sd.w, sd.L, false);
+    const StripRow* rows = I.rows + sd.row0;
+    float m = 0.f, q = 0.f;
+    switch (sd.w) {
+      case 1: strip_moments<1>(tb, rows, sd.L, srow, m, q); break;
+      case 2: strip_moments<2>(tb, rows, sd.L, srow, m, q); break;
+      case 3: strip_moments<3>(tb, rows, sd.L, srow, m, q); break;
+      default: strip_moments<4>(tb, rows, sd.L, srow, m, q); break;
+    }
+    mean += (double)m;
+    var += (double)q;
+  }
+  const long long o = (long long)k * li.batch + b;
+  mag_mean[o] = mean;
+  mag_var[o] = var;
+}
+
+cudaError_t launch_strips_mom(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes, const int8_t* spins,
+                              double* mag_mean, double* mag_var, cudaStream_t s) {
+  const int nblk = li.tile_begin[li.n_inst];
+  if (nblk == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(strips_mom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  strips_mom_kernel<<<nblk, li.tile, smem_bytes, s>>>(d_inst, li, spins, mag_mean, mag_var);
+  return cudaGetLastError();
+}
+
 }  // namespace tnvan

@@ -766,6 +766,47 @@ cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const 
   return cudaGetLastError();
 }
 
+// Per instance (one CTA each), in a fixed order (FP64), with m_b the
+// multipliers B w_b above, mu_b = E[M | s_b] and v_b = Var(M | s_b):
+//   out[5k+0] = sum_b m_b mu_b / B                 (<M>, importance-weighted)
+//   out[5k+1] = sum_b m_b (mu_b^2 + v_b) / B       (<M^2>)
+//   out[5k+2] = mean_b mu_b,  out[5k+3] = mean_b (mu_b^2 + v_b)   (the same under q)
+//   out[5k+4] = B^2 / sum_b m_b^2                  (effective sample size)
+__global__ void obs_mag_kernel(const LaunchInfo li, const double* __restrict__ mean, const double* __restrict__ var,
+                               const float* __restrict__ wmul, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < li.batch; b += blockDim.x) {
+    const long long o = (long long)k * li.batch + b;
+    const double mu = mean[o], m2 = mu * mu + var[o], w = (double)wmul[o];
+    a[0] += w * mu;
+    a[1] += w * m2;
+    a[2] += mu;
+    a[3] += m2;
+    a[4] += w * w;
+  }
+  __shared__ double red[5][256];
+  for (int j = 0; j < 5; ++j) red[j][threadIdx.x] = a[j];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int j = 0; j < 5; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double B = (double)li.batch;
+    for (int j = 0; j < 4; ++j) out[5 * k + j] = red[j][0] / B;
+    out[5 * k + 4] = B * B / red[4][0];
+  }
+}
+
+cudaError_t launch_obs_mag(const LaunchInfo& li, const double* mean, const double* var, const float* wmul,
+                           double* out, cudaStream_t s) {
+  if (li.n_inst == 0 || li.batch == 0) return cudaSuccess;
+  obs_mag_kernel<<<li.n_inst, 256, 0, s>>>(li, mean, var, wmul, out);
+  return cudaGetLastError();
+}
+
 // REINFORCE weights w_b = -(l_b - mean_b l) / (beta B) per instance (Eq. 10
 // with the batch-mean baseline), FP32 copy for the tensor-core backward.
 __global__ void reinforce_w_kernel(const LaunchInfo li, const double* __restrict__ logZR,

@@ -47,6 +47,7 @@ SIGNATURES = {
     "tnvan_train_step": (_c_int, [_vp, _dblp, _c_int, _c_u64, _c_u64, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_i64, _vp]),
     "tnvan_observables": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _vp, _dblp, _vp]),
+    "tnvan_magnetisation": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _vp, _vp, _vp, _dblp, _vp]),
     "tnvan_log_prob": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp]),
     "tnvan_contract": (_c_int, [_vp, _dblp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
     "tnvan_free_energy": (_c_int, [_vp, _dblp, _c_int, _vp, _vp, _dblp, _vp]),
@@ -232,6 +233,19 @@ class Context:
         self._check(lib().tnvan_observables(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq), _ptr(corr),
                                             out.ctypes.data_as(_dblp), _stream(stream)))
         return out.reshape(len(b), 3)
+
+    def magnetisation(self, betas, batch: int, spins, logZR, logq, mag_mean=None, mag_var=None,
+                      stream=None) -> np.ndarray:
+        """[n_inst, 6]: importance-weighted <M>, <M^2>, the susceptibility per
+        spin beta (<M^2> - <M>^2) / N, <M> and <M^2> under q, and the weights'
+        effective sample size; with `mag_mean` / `mag_var` (device double
+        [n_inst * batch]) also each sample's E[M | s] and Var(M | s)."""
+        b, pb = _arr(betas, np.float64)
+        out = np.zeros(6 * len(b))
+        self._check(lib().tnvan_magnetisation(self._h, pb, batch, _ptr(spins), _ptr(logZR), _ptr(logq),
+                                              _ptr(mag_mean), _ptr(mag_var), out.ctypes.data_as(_dblp),
+                                              _stream(stream)))
+        return out.reshape(len(b), 6)
 
     def free_energy(self, betas, batch: int, logZR, logq, stream=None) -> np.ndarray:
         b, pb = _arr(betas, np.float64)
