@@ -168,7 +168,10 @@ int tnvan_n_params(const tnvan_ctx* ctx, int instance, int64_t* n_params, int64_
  * components, [5] largest component (spins), [6] largest elimination width,
  * [7] number of W-W edges, [8] per-sample table arena of elimination plans
  * (floats, every table kept: reverse sweeps), [9] the same with consumed
- * tables' space reused (forward passes).  info: host array [10]. */
+ * tables' space reused (forward passes), [10] the grouped BF16 sampler's
+ * in-group form (-1 not eligible or no network, 0 per unit, 2-4 slots per
+ * layer and step: the register form), [11] 1 if the fused BF16 backward takes
+ * the instance.  info: host array [12]. */
 int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info);
 
 /* Pre-allocate the context's internal workspaces for batches up to

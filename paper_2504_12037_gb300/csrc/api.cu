@@ -1338,6 +1338,12 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     std::vector<int> grp, src;
     int twmax = 0, tcw1 = 16, tcw2 = 16;
     bool fits = true;
+    // most units of one layer completing at one step: up to 4, the slot layout
+    // (the kernel keeps the group's hidden values in registers)
+    int umax = 1;
+    for (int i = 0; i < D; ++i) umax = std::max({umax, cnt(c1, i, i + 1), cnt(c2, i, i + 1)});
+    const int U = umax <= 4 ? std::max(umax, 2) : 0;
+    P.slot_u = U;
     auto add_tile = [&](int rlo, int rhi, int clo, int chi, long long wofs, int stride) {
       const int off = (int)src.size();
       const int rw = (chi - clo + 3) & ~3;
@@ -1352,13 +1358,59 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       const int u2lo = before(c2, i0), u2hi = before(c2, i1);
       fits = fits && u1hi - u1lo <= UGMAX && u2hi - u2lo <= UGMAX;
       const int gstart = (int)src.size();
-      add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
-      const int t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
-      const int to = add_tile(i0, i1, u2lo, u2hi, md.layer[2].dst_off, H[1]);
-      // the group's biases (gathered with the triangles)
-      const int b1o = add_tile(0, 1, u1lo, u1hi, md.layer[0].dst_off + (long long)H[0] * D, 0);
-      const int b2o = add_tile(0, 1, u2lo, u2hi, md.layer[1].dst_off + (long long)H[1] * H[0], 0);
-      const int boo = add_tile(0, 1, i0, i1, md.layer[2].dst_off + (long long)D * H[1], 0);
+      int t2, to, b1o, b2o, boo;
+      if (U == 0) {
+        add_tile(u1lo, u1hi, i0, i1, md.layer[0].dst_off, D);
+        t2 = add_tile(u2lo, u2hi, u1lo, u1hi, md.layer[1].dst_off, H[0]);
+        to = add_tile(i0, i1, u2lo, u2hi, md.layer[2].dst_off, H[1]);
+        // the group's biases (gathered with the triangles)
+        b1o = add_tile(0, 1, u1lo, u1hi, md.layer[0].dst_off + (long long)H[0] * D, 0);
+        b2o = add_tile(0, 1, u2lo, u2hi, md.layer[1].dst_off + (long long)H[1] * H[0], 0);
+        boo = add_tile(0, 1, i0, i1, md.layer[2].dst_off + (long long)D * H[1], 0);
+      } else {
+        // slot layout (strides for 8 steps whatever the group's length): slot
+        // (q, a) is unit a of those completing at step i0 + q (empty: zeros)
+        //   TW1 [8U][8]   layer-1 slot x in-group spin j < q
+        //   TW2 [8U][8U]  layer-2 slot (q, b) x layer-1 slot (q', a'), q' <= q
+        //   TWo [8][8U]   output i0 + q x layer-2 slot (q', b'), q' <= q
+        //   b1 [8U], b2 [8U], bo [8]
+        const int gi = i1 - i0, S = 8 * U;
+        auto u_at = [&](const std::vector<int>& c, int q, int a) {  // unit of slot (q, a), -1 empty
+          if (q >= gi) return -1;
+          const int lo = before(c, i0 + q), hi = before(c, i0 + q + 1);
+          return a < hi - lo ? lo + a : -1;
+        };
+        const long long o0 = md.layer[0].dst_off, o1 = md.layer[1].dst_off, o2 = md.layer[2].dst_off;
+        for (int r = 0; r < S; ++r)
+          for (int j = 0; j < 8; ++j) {
+            const int u = u_at(c1, r / U, r % U);
+            src.push_back(u >= 0 && j < r / U ? (int)(o0 + (long long)u * D + i0 + j) : -1);
+          }
+        t2 = (int)src.size();
+        for (int r = 0; r < S; ++r)
+          for (int c = 0; c < S; ++c) {
+            const int v = u_at(c2, r / U, r % U), u = u_at(c1, c / U, c % U);
+            src.push_back(v >= 0 && u >= 0 && c / U <= r / U ? (int)(o1 + (long long)v * H[0] + u) : -1);
+          }
+        to = (int)src.size();
+        for (int q = 0; q < 8; ++q)
+          for (int c = 0; c < S; ++c) {
+            const int v = u_at(c2, c / U, c % U);
+            src.push_back(q < gi && v >= 0 && c / U <= q ? (int)(o2 + (long long)(i0 + q) * H[1] + v) : -1);
+          }
+        b1o = (int)src.size();
+        for (int r = 0; r < S; ++r) {
+          const int u = u_at(c1, r / U, r % U);
+          src.push_back(u >= 0 ? (int)(o0 + (long long)H[0] * D + u) : -1);
+        }
+        b2o = (int)src.size();
+        for (int r = 0; r < S; ++r) {
+          const int v = u_at(c2, r / U, r % U);
+          src.push_back(v >= 0 ? (int)(o1 + (long long)H[1] * H[0] + v) : -1);
+        }
+        boo = (int)src.size();
+        for (int q = 0; q < 8; ++q) src.push_back(q < gi ? (int)(o2 + (long long)D * H[1] + i0 + q) : -1);
+      }
       const int gsize = (int)src.size() - gstart;
       twmax = std::max(twmax, gsize);
       tcw1 = std::max(tcw1, ((u1hi + 15) & ~15) - (u1lo & ~15));
@@ -1435,6 +1487,9 @@ int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info) {
   info[7] = (int)in.ww.size();
   info[8] = in.kind == 2 ? in.g_max_entries : 0;
   info[9] = in.kind == 2 ? in.g_max_live : 0;
+  const MadeDev& md = in.dev.made;
+  info[10] = md.sample_tcg_ok ? md.tcg[TNVAN_TC_PLANS - 1].slot_u : -1;
+  info[11] = md.fused_ok ? 1 : 0;
   return TNVAN_OK;
 }
 

@@ -88,8 +88,10 @@ struct MadeDev {
   } tc[TNVAN_TC_PLANS];
   // Grouped tensor-core sampler (the fast path for two hidden layers of
   // <= 128 units and D <= 128, a multiple of 16): one step-group plan per
-  // group-size limit.  Per group only the in-group triangles, rows padded to
-  // 4 floats: TW1 [n1g][r4(gi)], TW2 [n2g][r4(n1g)], TWo [gi][r4(n2g)].
+  // group-size limit.  Per group only the in-group triangles: per unit, rows
+  // padded to 4 floats, TW1 [n1g][r4(gi)], TW2 [n2g][r4(n1g)], TWo [gi][r4(n2g)];
+  // or, when at most 4 units of a layer complete at any step, per slot (U
+  // slots per layer and step, strides for 8 steps; see the host builder).
   struct TcGroupPlan {
     int ok;               // eligible (unit counts within the kernel's limits)
     int n_groups;
@@ -99,6 +101,7 @@ struct MadeDev {
     long long n_blk;
     int twmax;            // largest group (floats)
     int tcw1, tcw2;       // widest 16-aligned unit window of a group, layers 1 and 2
+    int slot_u;           // 0: per-unit triangles; 1..4: slot layout, U slots per layer and step
   } tcg[TNVAN_TC_PLANS];
   int sample_tcg_ok;      // eligible for the grouped sampler
   float* blocks;          // blocked weights (gathered from `packed` every call)

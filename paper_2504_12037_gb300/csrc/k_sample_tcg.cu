@@ -23,6 +23,14 @@
 // Every hidden value enters every later product as BF16 with FP32
 // accumulation; in-group arithmetic is FP32 on the same BF16 values.
 //
+// When at most 4 units of a layer complete at any step (the host's slot
+// layout, U slots per layer and step), the in-group steps run in the slot
+// form: the group's accumulated pre-activations come from TMEM in one batch
+// of loads at the group's start, and its hidden values stay in registers at
+// compile-time indices (the group's 8 steps unrolled), so a step's dependency
+// chain is register arithmetic only; the per-unit form reads them back from
+// the fold tiles.
+//
 // The spin tile S and the fold tiles H1_g, H2_g are MN-major MMA operands in
 // which consecutive 8-sample core-matrix groups are 16 bytes apart modulo
 // 128, so the per-sample stores and loads (one 2-byte element per thread)
@@ -96,6 +104,142 @@ __host__ __device__ inline SampleTcgLayout sample_tcg_layout(int D, int H1, int 
   p += 32;
   L.total = p;
   return L;
+}
+
+__device__ __forceinline__ void tmem_wait_all() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Orders later uses of r after the preceding tcgen05.wait::ld.
+__device__ __forceinline__ void tie(uint32_t& r) { asm volatile("" : "+r"(r)); }
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16(v)); }
+
+// Dot product of a weight row (shared memory, 16-byte aligned) with the first
+// N register values, four accumulators; N is a compile-time constant.
+template <int N, int S>
+__device__ __forceinline__ float slot_dot(const float* __restrict__ w, const float (&h)[S], float a0) {
+  float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+  for (int c4 = 0; c4 < (N + 3) / 4; ++c4) {
+    const float4 x = reinterpret_cast<const float4*>(w)[c4];
+    if (4 * c4 + 0 < N) a0 = fmaf(x.x, h[4 * c4 + 0], a0);
+    if (4 * c4 + 1 < N) a1 = fmaf(x.y, h[4 * c4 + 1], a1);
+    if (4 * c4 + 2 < N) a2 = fmaf(x.z, h[4 * c4 + 2], a2);
+    if (4 * c4 + 3 < N) a3 = fmaf(x.w, h[4 * c4 + 3], a3);
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Per-sample state the in-group steps update.
+struct SlotState {
+  uint4 rnd;
+  unsigned long long sb0, sb1;
+  float lq;
+};
+
+// The steps of one group in the slot form (U slots per layer and step, the
+// host's slot layout): the accumulated pre-activations of every slot come
+// from TMEM at once, the group's hidden values stay in registers at
+// compile-time indices (q U + a), and only the fold tiles and the spin tile
+// are written to shared memory.  Same arithmetic as the per-unit form: BF16
+// hidden values, FP32 sums.
+template <int U, int Q>
+__device__ __forceinline__ void slot_step(const int* G, const float* TWb, int i0, int w1, int w2,
+                                          const uint32_t (&r1)[8 * U], const uint32_t (&r2)[8 * U],
+                                          const uint32_t (&ro)[8], float (&h1)[8 * U], float (&h2)[8 * U],
+                                          float (&sg)[8], unsigned char* sH1, unsigned char* sH2, unsigned char* sS,
+                                          uint32_t rb1, uint32_t rb2, uint32_t rbS, int b, uint32_t step32, int k,
+                                          uint2 key, const int8_t* gv, bool valid, SlotState& st) {
+  constexpr int S = 8 * U;
+  const int i = i0 + Q;
+  if ((i & 3) == 0) st.rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
+  const float* TW1 = TWb;
+  const float* TW2 = TWb + G[8];
+  const float* TWo = TWb + G[9];
+  const float* B1 = TWb + G[10];
+  const float* B2 = TWb + G[11];
+  const float* BO = TWb + G[12];
+  const int ua = G[13 + Q], nu = G[14 + Q] - ua, va = G[22 + Q], nv = G[23 + Q] - va;
+  // layer 1: + in-group spins j < Q
+#pragma unroll
+  for (int a = 0; a < U; ++a) {
+    const int r = Q * U + a;
+    const float x = slot_dot<Q, 8>(TW1 + r * 8, sg, __uint_as_float(r1[r]) + B1[r]);
+    h1[r] = bf16_round(fmaxf(x, 0.f));
+    if (a < nu) st_bf16(sH1, rb1 + 16u * (uint32_t)(ua + a - w1), h1[r]);
+  }
+  // layer 2: + in-group layer-1 slots of steps <= Q
+#pragma unroll
+  for (int a = 0; a < U; ++a) {
+    const int r = Q * U + a;
+    const float x = slot_dot<(Q + 1) * U, S>(TW2 + r * S, h1, __uint_as_float(r2[r]) + B2[r]);
+    h2[r] = bf16_round(fmaxf(x, 0.f));
+    if (a < nv) st_bf16(sH2, rb2 + 16u * (uint32_t)(va + a - w2), h2[r]);
+  }
+  // output i: + in-group layer-2 slots of steps <= Q
+  const float x = slot_dot<(Q + 1) * U, S>(TWo + Q * S, h2, __uint_as_float(ro[Q]) + BO[Q]);
+  // one exponential for both sigmoid(x) and softplus(-s x) (fast-math forms)
+  const float ex = __expf(-fabsf(x));
+  const float rcp = __frcp_rn(1.f + ex);
+  const float pr = x >= 0.f ? rcp : ex * rcp;
+  const uint32_t word = (i & 3) == 0 ? st.rnd.x : (i & 3) == 1 ? st.rnd.y : (i & 3) == 2 ? st.rnd.z : st.rnd.w;
+  const float u = (float)(word >> 8) * 5.9604644775390625e-08f;
+  bool up = u < pr;
+  if (gv) up = valid ? gv[i] > 0 : true;
+  const float s = up ? 1.f : -1.f;
+  sg[Q] = s;
+  if (up) {
+    if (i < 64) st.sb0 |= 1ull << i;
+    else st.sb1 |= 1ull << (i - 64);
+  }
+  st_bf16(sS, rbS + 16u * (uint32_t)i, s);
+  st.lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
+}
+
+template <int U>
+__device__ __forceinline__ void slot_group(const int* G, const float* TWb, int gi, int i0, int w1, int w2, uint32_t tP1,
+                                           uint32_t tP2, uint32_t tPO, bool p1ok, bool init2, bool inito,
+                                           unsigned char* sH1, unsigned char* sH2, unsigned char* sS, uint32_t rb1,
+                                           uint32_t rb2, uint32_t rbS, int b, uint32_t step32, int k, uint2 key,
+                                           const int8_t* gv, bool valid, SlotState& st) {
+  constexpr int S = 8 * U;
+  uint32_t r1[S], r2[S], ro[8];
+#pragma unroll
+  for (int j = 0; j < S; ++j) r1[j] = r2[j] = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ro[q] = 0u;
+  // every slot's accumulated pre-activations (warp-uniform conditions)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q < gi) {
+      const int ua = G[13 + q], nu = G[14 + q] - ua, va = G[22 + q], nv = G[23 + q] - va;
+#pragma unroll
+      for (int a = 0; a < U; ++a) {
+        if (p1ok && a < nu) tmem_ld1_nowait(tP1 + (uint32_t)(ua + a - w1), r1[q * U + a]);
+        if (init2 && a < nv) tmem_ld1_nowait(tP2 + (uint32_t)(va + a), r2[q * U + a]);
+      }
+      if (inito) tmem_ld1_nowait(tPO + (uint32_t)(i0 + q), ro[q]);
+    }
+  }
+  tmem_wait_all();
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    tie(r1[j]);
+    tie(r2[j]);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) tie(ro[q]);
+  float h1[S], h2[S], sg[8];
+#define TNVAN_SLOT_STEP(QQ)                                                                                     \
+  if (QQ < gi)                                                                                                  \
+    slot_step<U, QQ>(G, TWb, i0, w1, w2, r1, r2, ro, h1, h2, sg, sH1, sH2, sS, rb1, rb2, rbS, b, step32, k, key, \
+                     gv, valid, st);
+  TNVAN_SLOT_STEP(0)
+  TNVAN_SLOT_STEP(1)
+  TNVAN_SLOT_STEP(2)
+  TNVAN_SLOT_STEP(3)
+  TNVAN_SLOT_STEP(4)
+  TNVAN_SLOT_STEP(5)
+  TNVAN_SLOT_STEP(6)
+  TNVAN_SLOT_STEP(7)
+#undef TNVAN_SLOT_STEP
 }
 
 __host__ __device__ inline int sample_tcg_tmem_cols(int D, int H2, int tcw1) {
@@ -235,148 +379,165 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
       copy_group(g + 1, gbn, 0u);
     }
     if (g + 1 < P.n_groups) copy_pending = true;
-    const float* TW1 = TWb;
-    const float* TW2 = TWb + G[8];
-    const float* TWo = TWb + G[9];
-    const float* gb1 = TWb + G[10];  // biases of the group's units
-    const float* gb2 = TWb + G[11];
-    const float* gbo = TWb + G[12];
-    const int* gc1 = G + 13;  // c1[i], c2[i] for i = i0-1 .. i1-1
-    const int* gc2 = G + 22;
-    const int s1 = (gi + 3) & ~3, s2 = (n1g + 3) & ~3, so = (n2g + 3) & ~3;  // triangle row strides
-    float sg[STC_GI];  // in-group spins (0 until drawn)
-#pragma unroll
-    for (int j = 0; j < STC_GI; ++j) sg[j] = 0.f;
-    for (int i = i0; i < i1; ++i) {
-      if ((i & 3) == 0)
-        rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
-      const int q = i - i0;  // gc*[q] = c*[i-1], gc*[q+1] = c*[i]
-      const int ua = gc1[q], ub = gc1[q + 1], va = gc2[q], vb = gc2[q + 1];
-      // pre-activations of the units completing at step i (up to four per layer at once)
-      uint32_t ra[4] = {0u, 0u, 0u, 0u}, rb[4] = {0u, 0u, 0u, 0u}, rc = 0u;
-      if (p1ok) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (ua + j < ub) tmem_ld1_nowait(tP1 + (uint32_t)(ua + j - w1), ra[j]);
-      }
-      if (init2) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (va + j < vb) tmem_ld1_nowait(tP2 + (uint32_t)(va + j), rb[j]);
-      }
-      if (inito) tmem_ld1_nowait(tPO + (uint32_t)i, rc);
-      tmem_wait9(ra, rb, rc);
-      // layer 1: + in-group spins (q <= 7 of them; sg is 0 for the rest)
-      for (int u = ua; u < ub; ++u) {
-        float a0;
-        if (u - ua < 4) {
-          a0 = pick4(ra, u - ua);
-        } else {  // more than four units at one step
-          uint32_t rx = 0u;
-          if (p1ok) tmem_ld1_nowait(tP1 + (uint32_t)(u - w1), rx);
-          tmem_wait1(rx);
-          a0 = __uint_as_float(rx);
+    if (P.slot_u == 0) {
+      const float* TW1 = TWb;
+      const float* TW2 = TWb + G[8];
+      const float* TWo = TWb + G[9];
+      const float* gb1 = TWb + G[10];  // biases of the group's units
+      const float* gb2 = TWb + G[11];
+      const float* gbo = TWb + G[12];
+      const int* gc1 = G + 13;  // c1[i], c2[i] for i = i0-1 .. i1-1
+      const int* gc2 = G + 22;
+      const int s1 = (gi + 3) & ~3, s2 = (n1g + 3) & ~3, so = (n2g + 3) & ~3;  // triangle row strides
+      float sg[STC_GI];  // in-group spins (0 until drawn)
+  #pragma unroll
+      for (int j = 0; j < STC_GI; ++j) sg[j] = 0.f;
+      for (int i = i0; i < i1; ++i) {
+        if ((i & 3) == 0)
+          rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
+        const int q = i - i0;  // gc*[q] = c*[i-1], gc*[q+1] = c*[i]
+        const int ua = gc1[q], ub = gc1[q + 1], va = gc2[q], vb = gc2[q + 1];
+        // pre-activations of the units completing at step i (up to four per layer at once)
+        uint32_t ra[4] = {0u, 0u, 0u, 0u}, rb[4] = {0u, 0u, 0u, 0u}, rc = 0u;
+        if (p1ok) {
+  #pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (ua + j < ub) tmem_ld1_nowait(tP1 + (uint32_t)(ua + j - w1), ra[j]);
         }
-        a0 += gb1[u - u1lo];
-        const float4* wr = reinterpret_cast<const float4*>(TW1 + (u - u1lo) * s1);
-        const float4 wa = wr[0];
-        const float4 wb = s1 > 4 ? wr[1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float a1 = wa.y * sg[1];
-        a0 = fmaf(wa.x, sg[0], a0);
-        a0 = fmaf(wa.z, sg[2], a0);
-        a1 = fmaf(wa.w, sg[3], a1);
-        a0 = fmaf(wb.x, sg[4], a0);
-        a1 = fmaf(wb.y, sg[5], a1);
-        a0 = fmaf(wb.z, sg[6], a0);
-        a1 = fmaf(wb.w, sg[7], a1);
-        st_bf16(sH1, rb1 + 16u * (uint32_t)(u - w1), fmaxf(a0 + a1, 0.f));
-      }
-      // layer 2: + in-group layer-1 units completed so far (BF16 values, 4 at a time;
-      // units not computed yet read as 0 and carry masked weights)
-      const uint32_t o1 = rb1 + 16u * (uint32_t)(u1lo - w1);
-      auto pre2 = [&](int v) -> float {  // accumulated pre-activation + bias of layer-2 unit v
-        float a;
-        if (v - va < 4) {
-          a = pick4(rb, v - va);
-        } else {
-          uint32_t rx = 0u;
-          if (init2) tmem_ld1_nowait(tP2 + (uint32_t)v, rx);
-          tmem_wait1(rx);
-          a = __uint_as_float(rx);
+        if (init2) {
+  #pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (va + j < vb) tmem_ld1_nowait(tP2 + (uint32_t)(va + j), rb[j]);
         }
-        return a + gb2[v - u2lo];
-      };
-      int v = va;
-      for (; v + 2 <= vb; v += 2) {  // two units of one step share the in-group H1 values
-        float a0 = pre2(v), b0 = pre2(v + 1);
-        const float* wr = TW2 + (v - u2lo) * s2;
-        const float* wq = wr + s2;
-        float a1 = 0.f, b1 = 0.f;
-        for (int c = 0; c < ub - u1lo; c += 4) {
-          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
-          const float4 q4 = *reinterpret_cast<const float4*>(wq + c);
-          const uint32_t o = o1 + 16u * (uint32_t)c;
-          const float h0 = ld_bf16(sH1, o), h1 = ld_bf16(sH1, o + 16u), h2 = ld_bf16(sH1, o + 32u),
-                      h3 = ld_bf16(sH1, o + 48u);
-          a0 = fmaf(w4.x, h0, a0);
-          b0 = fmaf(q4.x, h0, b0);
-          a1 = fmaf(w4.y, h1, a1);
-          b1 = fmaf(q4.y, h1, b1);
-          a0 = fmaf(w4.z, h2, a0);
-          b0 = fmaf(q4.z, h2, b0);
-          a1 = fmaf(w4.w, h3, a1);
-          b1 = fmaf(q4.w, h3, b1);
+        if (inito) tmem_ld1_nowait(tPO + (uint32_t)i, rc);
+        tmem_wait9(ra, rb, rc);
+        // layer 1: + in-group spins (q <= 7 of them; sg is 0 for the rest)
+        for (int u = ua; u < ub; ++u) {
+          float a0;
+          if (u - ua < 4) {
+            a0 = pick4(ra, u - ua);
+          } else {  // more than four units at one step
+            uint32_t rx = 0u;
+            if (p1ok) tmem_ld1_nowait(tP1 + (uint32_t)(u - w1), rx);
+            tmem_wait1(rx);
+            a0 = __uint_as_float(rx);
+          }
+          a0 += gb1[u - u1lo];
+          const float4* wr = reinterpret_cast<const float4*>(TW1 + (u - u1lo) * s1);
+          const float4 wa = wr[0];
+          const float4 wb = s1 > 4 ? wr[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+          float a1 = wa.y * sg[1];
+          a0 = fmaf(wa.x, sg[0], a0);
+          a0 = fmaf(wa.z, sg[2], a0);
+          a1 = fmaf(wa.w, sg[3], a1);
+          a0 = fmaf(wb.x, sg[4], a0);
+          a1 = fmaf(wb.y, sg[5], a1);
+          a0 = fmaf(wb.z, sg[6], a0);
+          a1 = fmaf(wb.w, sg[7], a1);
+          st_bf16(sH1, rb1 + 16u * (uint32_t)(u - w1), fmaxf(a0 + a1, 0.f));
         }
-        st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf(a0 + a1, 0.f));
-        st_bf16(sH2, rb2 + 16u * (uint32_t)(v + 1 - w2), fmaxf(b0 + b1, 0.f));
-      }
-      if (v < vb) {
-        float a0 = pre2(v);
-        const float* wr = TW2 + (v - u2lo) * s2;
-        float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        for (int c = 0; c < ub - u1lo; c += 4) {
-          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
-          const uint32_t o = o1 + 16u * (uint32_t)c;
-          a0 = fmaf(w4.x, ld_bf16(sH1, o), a0);
-          a1 = fmaf(w4.y, ld_bf16(sH1, o + 16u), a1);
-          a2 = fmaf(w4.z, ld_bf16(sH1, o + 32u), a2);
-          a3 = fmaf(w4.w, ld_bf16(sH1, o + 48u), a3);
+        // layer 2: + in-group layer-1 units completed so far (BF16 values, 4 at a time;
+        // units not computed yet read as 0 and carry masked weights)
+        const uint32_t o1 = rb1 + 16u * (uint32_t)(u1lo - w1);
+        auto pre2 = [&](int v) -> float {  // accumulated pre-activation + bias of layer-2 unit v
+          float a;
+          if (v - va < 4) {
+            a = pick4(rb, v - va);
+          } else {
+            uint32_t rx = 0u;
+            if (init2) tmem_ld1_nowait(tP2 + (uint32_t)v, rx);
+            tmem_wait1(rx);
+            a = __uint_as_float(rx);
+          }
+          return a + gb2[v - u2lo];
+        };
+        int v = va;
+        for (; v + 2 <= vb; v += 2) {  // two units of one step share the in-group H1 values
+          float a0 = pre2(v), b0 = pre2(v + 1);
+          const float* wr = TW2 + (v - u2lo) * s2;
+          const float* wq = wr + s2;
+          float a1 = 0.f, b1 = 0.f;
+          for (int c = 0; c < ub - u1lo; c += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+            const float4 q4 = *reinterpret_cast<const float4*>(wq + c);
+            const uint32_t o = o1 + 16u * (uint32_t)c;
+            const float h0 = ld_bf16(sH1, o), h1 = ld_bf16(sH1, o + 16u), h2 = ld_bf16(sH1, o + 32u),
+                        h3 = ld_bf16(sH1, o + 48u);
+            a0 = fmaf(w4.x, h0, a0);
+            b0 = fmaf(q4.x, h0, b0);
+            a1 = fmaf(w4.y, h1, a1);
+            b1 = fmaf(q4.y, h1, b1);
+            a0 = fmaf(w4.z, h2, a0);
+            b0 = fmaf(q4.z, h2, b0);
+            a1 = fmaf(w4.w, h3, a1);
+            b1 = fmaf(q4.w, h3, b1);
+          }
+          st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf(a0 + a1, 0.f));
+          st_bf16(sH2, rb2 + 16u * (uint32_t)(v + 1 - w2), fmaxf(b0 + b1, 0.f));
         }
-        st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf((a0 + a1) + (a2 + a3), 0.f));
-      }
-      float x;
-      {
-        const float* wr = TWo + q * so;
-        const uint32_t o2 = rb2 + 16u * (uint32_t)(u2lo - w2);
-        float a0 = __uint_as_float(rc) + gbo[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        for (int c = 0; c < vb - u2lo; c += 4) {
-          const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
-          const uint32_t o = o2 + 16u * (uint32_t)c;
-          a0 = fmaf(w4.x, ld_bf16(sH2, o), a0);
-          a1 = fmaf(w4.y, ld_bf16(sH2, o + 16u), a1);
-          a2 = fmaf(w4.z, ld_bf16(sH2, o + 32u), a2);
-          a3 = fmaf(w4.w, ld_bf16(sH2, o + 48u), a3);
+        if (v < vb) {
+          float a0 = pre2(v);
+          const float* wr = TW2 + (v - u2lo) * s2;
+          float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+          for (int c = 0; c < ub - u1lo; c += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+            const uint32_t o = o1 + 16u * (uint32_t)c;
+            a0 = fmaf(w4.x, ld_bf16(sH1, o), a0);
+            a1 = fmaf(w4.y, ld_bf16(sH1, o + 16u), a1);
+            a2 = fmaf(w4.z, ld_bf16(sH1, o + 32u), a2);
+            a3 = fmaf(w4.w, ld_bf16(sH1, o + 48u), a3);
+          }
+          st_bf16(sH2, rb2 + 16u * (uint32_t)(v - w2), fmaxf((a0 + a1) + (a2 + a3), 0.f));
         }
-        x = (a0 + a1) + (a2 + a3);
+        float x;
+        {
+          const float* wr = TWo + q * so;
+          const uint32_t o2 = rb2 + 16u * (uint32_t)(u2lo - w2);
+          float a0 = __uint_as_float(rc) + gbo[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+          for (int c = 0; c < vb - u2lo; c += 4) {
+            const float4 w4 = *reinterpret_cast<const float4*>(wr + c);
+            const uint32_t o = o2 + 16u * (uint32_t)c;
+            a0 = fmaf(w4.x, ld_bf16(sH2, o), a0);
+            a1 = fmaf(w4.y, ld_bf16(sH2, o + 16u), a1);
+            a2 = fmaf(w4.z, ld_bf16(sH2, o + 32u), a2);
+            a3 = fmaf(w4.w, ld_bf16(sH2, o + 48u), a3);
+          }
+          x = (a0 + a1) + (a2 + a3);
+        }
+        // one exponential for both sigmoid(x) and softplus(-s x) (fast-math forms:
+        // this kernel is the reduced-precision mode)
+        const float ex = __expf(-fabsf(x));  // in (0, 1]
+        const float rcp = __frcp_rn(1.f + ex);
+        const float pr = x >= 0.f ? rcp : ex * rcp;
+        const uint32_t word = (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
+        const float u = (float)(word >> 8) * 5.9604644775390625e-08f;
+        bool up = u < pr;
+        if (gv) up = valid ? gv[i] > 0 : true;
+        const float s = up ? 1.f : -1.f;
+  #pragma unroll
+        for (int j = 0; j < STC_GI; ++j) sg[j] = j == q ? s : sg[j];
+        if (up) {
+          if (i < 64) sb0 |= 1ull << i;
+          else sb1 |= 1ull << (i - 64);
+        }
+        st_bf16(sS, rbS + 16u * (uint32_t)i, s);
+        lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
       }
-      // one exponential for both sigmoid(x) and softplus(-s x) (fast-math forms:
-      // this kernel is the reduced-precision mode)
-      const float ex = __expf(-fabsf(x));  // in (0, 1]
-      const float rcp = __frcp_rn(1.f + ex);
-      const float pr = x >= 0.f ? rcp : ex * rcp;
-      const uint32_t word = (i & 3) == 0 ? rnd.x : (i & 3) == 1 ? rnd.y : (i & 3) == 2 ? rnd.z : rnd.w;
-      const float u = (float)(word >> 8) * 5.9604644775390625e-08f;
-      bool up = u < pr;
-      if (gv) up = valid ? gv[i] > 0 : true;
-      const float s = up ? 1.f : -1.f;
-#pragma unroll
-      for (int j = 0; j < STC_GI; ++j) sg[j] = j == q ? s : sg[j];
-      if (up) {
-        if (i < 64) sb0 |= 1ull << i;
-        else sb1 |= 1ull << (i - 64);
-      }
-      st_bf16(sS, rbS + 16u * (uint32_t)i, s);
-      lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
+    } else {
+      SlotState st{rnd, sb0, sb1, lq};
+      if (P.slot_u == 2)
+        slot_group<2>(G, TWb, gi, i0, w1, w2, tP1, tP2, tPO, p1ok, init2, inito, sH1, sH2, sS, rb1, rb2, rbS, b,
+                      step32, k, key, gv, valid, st);
+      else if (P.slot_u == 3)
+        slot_group<3>(G, TWb, gi, i0, w1, w2, tP1, tP2, tPO, p1ok, init2, inito, sH1, sH2, sS, rb1, rb2, rbS, b,
+                      step32, k, key, gv, valid, st);
+      else
+        slot_group<4>(G, TWb, gi, i0, w1, w2, tP1, tP2, tPO, p1ok, init2, inito, sH1, sH2, sS, rb1, rb2, rbS, b,
+                      step32, k, key, gv, valid, st);
+      rnd = st.rnd;
+      sb0 = st.sb0;
+      sb1 = st.sb1;
+      lq = st.lq;
     }
     // fold the group; recompute P1g for the next group
     fence_proxy_async_smem();

@@ -101,3 +101,58 @@ def test_tc_sampler_one_hidden_layer_distribution():
     chi2 = float(((counts - B * q) ** 2 / (B * q)).sum())
     print("chi2 (15 dof):", chi2)
     assert chi2 < 45
+
+
+# grouped-form networks by in-group form (MADE hidden degrees k mod (D-1) + 1):
+# 2 slots (D = 64, H = 64), 3 (workload 2's 64-128-128), 4 (D = 32, H = 96),
+# and the per-unit form (D = 16, H = 128: up to 9 units per degree)
+GROUPED_SHAPES = [(16, 16, [64, 64], 2), (16, 16, [128, 128], 3), (16, 8, [96, 96], 4), (8, 8, [128, 128], 0)]
+
+
+@pytest.mark.parametrize("plan", [4, 6, 8])
+@pytest.mark.parametrize("shape", range(len(GROUPED_SHAPES)))
+def test_tc_grouped_forms_against_oracle(shape, plan):
+    from paper_2504_12037_gb300.model import TNVAN
+
+    Lx, Ly, hidden, slots = GROUPED_SHAPES[shape]
+    g = wl.lattice(Lx, Ly, "gauss", seed=31 + shape)
+    W = wl.width_columns(Lx, Ly, wl.every_kth_column(Lx))
+    model = TNVAN([g, g], [W, W], hidden, [0.6, 1.1], seed=4 + shape, init_scale=1.5)
+    assert model.ctx.instance_info(0)["tcg_slots"] == slots
+    model.ctx.set_tuning((0, 0, 0, 0, plan, 0))
+    D, B = len(W), 300  # three CTAs, the last one ragged
+    # teacher-forced on oracle draws
+    s_all, refs = [], []
+    for k in range(2):
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_or, _, _ = oracle_samples(p32, D, hidden, 3, 0, k, B)
+        s_all.append(s_or.numpy().reshape(-1))
+        refs.append(made.log_q(torch.as_tensor(p32, dtype=torch.float64), D, hidden, s_or))
+    logq = torch.empty(2 * B, dtype=torch.float32, device="cuda")
+    model.ctx.profile(True)
+    model.ctx.log_prob(B, to_dev_spins(np.concatenate(s_all)), logq, tv.BF16)
+    torch.cuda.synchronize()
+    assert "log_prob_tc" in model.ctx.profile_read()
+    for k in range(2):
+        err = float((logq[k * B:(k + 1) * B].cpu().double() - refs[k]).abs().max()) / g.n
+        assert err <= TOL_RED, (k, err)
+    # own draws: log q against the oracle and the teacher-forced kernel; the
+    # draws themselves against the oracle's replay of the same uniforms (rows
+    # differ only where a BF16 probability falls on the other side of u)
+    spins, lq_s, _ = model.sample(B, 77, 5, precision=tv.BF16)
+    torch.cuda.synchronize()
+    assert "sample_tc" in model.ctx.profile_read()
+    model.ctx.profile(False)
+    lq2 = torch.empty_like(lq_s)
+    model.ctx.log_prob(B, spins, lq2, tv.BF16)
+    torch.cuda.synchronize()
+    assert torch.allclose(lq_s, lq2, atol=1e-5, rtol=0)
+    for k in range(2):
+        p32 = model.params[model.offsets[k]:model.offsets[k + 1]].cpu().numpy()
+        s_gpu = model.spins_of(spins, k, B).cpu().numpy().astype(np.float64)
+        ref = made.log_q(torch.as_tensor(p32, dtype=torch.float64), D, hidden, torch.as_tensor(s_gpu))
+        err = float((lq_s[k * B:(k + 1) * B].cpu().double() - ref).abs().max()) / g.n
+        assert err <= TOL_RED, (k, err)
+        s_or, _, _ = oracle_samples(p32, D, hidden, 77, 5, k, B)
+        same = np.all(s_gpu == s_or.numpy(), axis=1).mean()
+        assert same >= 0.8, (k, same)
