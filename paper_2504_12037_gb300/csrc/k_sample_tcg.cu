@@ -130,7 +130,7 @@ __device__ __forceinline__ float slot_dot(const float* __restrict__ w, const flo
 // Per-sample state the in-group steps update.
 struct SlotState {
   uint4 rnd;
-  unsigned long long sb0, sb1;
+  uint32_t gbits;  // bit q set iff the group's step q drew +1
   float lq;
 };
 
@@ -141,12 +141,13 @@ struct SlotState {
 // are written to shared memory.  Same arithmetic as the per-unit form: BF16
 // hidden values, FP32 sums.
 template <int U, int Q>
-__device__ __forceinline__ void slot_step(const int* G, const float* TWb, int i0, int w1, int w2,
+__device__ __forceinline__ void slot_step(const int* G, const float* TWb, int i0, const uint32_t (&a1)[8],
+                                          const uint32_t (&a2)[8], uint32_t m1, uint32_t m2,
                                           const uint32_t (&r1)[8 * U], const uint32_t (&r2)[8 * U],
                                           const uint32_t (&ro)[8], float (&h1)[8 * U], float (&h2)[8 * U],
                                           float (&sg)[8], unsigned char* sH1, unsigned char* sH2, unsigned char* sS,
-                                          uint32_t rb1, uint32_t rb2, uint32_t rbS, int b, uint32_t step32, int k,
-                                          uint2 key, const int8_t* gv, bool valid, SlotState& st) {
+                                          uint32_t rbS, int b, uint32_t step32, int k, uint2 key, const int8_t* gv,
+                                          bool valid, SlotState& st) {
   constexpr int S = 8 * U;
   const int i = i0 + Q;
   if ((i & 3) == 0) st.rnd = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(i >> 2), step32, (uint32_t)k), key);
@@ -156,22 +157,23 @@ __device__ __forceinline__ void slot_step(const int* G, const float* TWb, int i0
   const float* B1 = TWb + G[10];
   const float* B2 = TWb + G[11];
   const float* BO = TWb + G[12];
-  const int ua = G[13 + Q], nu = G[14 + Q] - ua, va = G[22 + Q], nv = G[23 + Q] - va;
-  // layer 1: + in-group spins j < Q
+  // layer 1: + in-group spins j < Q (slot (Q, a) stores at a1[Q] + 16 a when it holds a unit)
 #pragma unroll
   for (int a = 0; a < U; ++a) {
     const int r = Q * U + a;
     const float x = slot_dot<Q, 8>(TW1 + r * 8, sg, __uint_as_float(r1[r]) + B1[r]);
-    h1[r] = bf16_round(fmaxf(x, 0.f));
-    if (a < nu) st_bf16(sH1, rb1 + 16u * (uint32_t)(ua + a - w1), h1[r]);
+    const __nv_bfloat16 hb = __float2bfloat16(fmaxf(x, 0.f));
+    h1[r] = __bfloat162float(hb);
+    if ((m1 >> r) & 1u) *reinterpret_cast<__nv_bfloat16*>(sH1 + a1[Q] + 16u * a) = hb;
   }
   // layer 2: + in-group layer-1 slots of steps <= Q
 #pragma unroll
   for (int a = 0; a < U; ++a) {
     const int r = Q * U + a;
     const float x = slot_dot<(Q + 1) * U, S>(TW2 + r * S, h1, __uint_as_float(r2[r]) + B2[r]);
-    h2[r] = bf16_round(fmaxf(x, 0.f));
-    if (a < nv) st_bf16(sH2, rb2 + 16u * (uint32_t)(va + a - w2), h2[r]);
+    const __nv_bfloat16 hb = __float2bfloat16(fmaxf(x, 0.f));
+    h2[r] = __bfloat162float(hb);
+    if ((m2 >> r) & 1u) *reinterpret_cast<__nv_bfloat16*>(sH2 + a2[Q] + 16u * a) = hb;
   }
   // output i: + in-group layer-2 slots of steps <= Q
   const float x = slot_dot<(Q + 1) * U, S>(TWo + Q * S, h2, __uint_as_float(ro[Q]) + BO[Q]);
@@ -185,10 +187,7 @@ __device__ __forceinline__ void slot_step(const int* G, const float* TWb, int i0
   if (gv) up = valid ? gv[i] > 0 : true;
   const float s = up ? 1.f : -1.f;
   sg[Q] = s;
-  if (up) {
-    if (i < 64) st.sb0 |= 1ull << i;
-    else st.sb1 |= 1ull << (i - 64);
-  }
+  st.gbits |= (up ? 1u : 0u) << Q;
   st_bf16(sS, rbS + 16u * (uint32_t)i, s);
   st.lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
 }
@@ -201,6 +200,8 @@ __device__ __forceinline__ void slot_group(const int* G, const float* TWb, int g
                                            const int8_t* gv, bool valid, SlotState& st) {
   constexpr int S = 8 * U;
   uint32_t r1[S], r2[S], ro[8];
+  // fold-tile addresses of each step's first unit, and which slots hold units
+  uint32_t a1[8], a2[8], m1 = 0u, m2 = 0u;
 #pragma unroll
   for (int j = 0; j < S; ++j) r1[j] = r2[j] = 0u;
 #pragma unroll
@@ -208,10 +209,15 @@ __device__ __forceinline__ void slot_group(const int* G, const float* TWb, int g
   // every slot's accumulated pre-activations (warp-uniform conditions)
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
+    a1[q] = a2[q] = 0u;
     if (q < gi) {
       const int ua = G[13 + q], nu = G[14 + q] - ua, va = G[22 + q], nv = G[23 + q] - va;
+      a1[q] = rb1 + 16u * (uint32_t)(ua - w1);
+      a2[q] = rb2 + 16u * (uint32_t)(va - w2);
 #pragma unroll
       for (int a = 0; a < U; ++a) {
+        if (a < nu) m1 |= 1u << (q * U + a);
+        if (a < nv) m2 |= 1u << (q * U + a);
         if (p1ok && a < nu) tmem_ld1_nowait(tP1 + (uint32_t)(ua + a - w1), r1[q * U + a]);
         if (init2 && a < nv) tmem_ld1_nowait(tP2 + (uint32_t)(va + a), r2[q * U + a]);
       }
@@ -229,8 +235,8 @@ __device__ __forceinline__ void slot_group(const int* G, const float* TWb, int g
   float h1[S], h2[S], sg[8];
 #define TNVAN_SLOT_STEP(QQ)                                                                                     \
   if (QQ < gi)                                                                                                  \
-    slot_step<U, QQ>(G, TWb, i0, w1, w2, r1, r2, ro, h1, h2, sg, sH1, sH2, sS, rb1, rb2, rbS, b, step32, k, key, \
-                     gv, valid, st);
+    slot_step<U, QQ>(G, TWb, i0, a1, a2, m1, m2, r1, r2, ro, h1, h2, sg, sH1, sH2, sS, rbS, b, step32, k, key, gv, \
+                     valid, st);
   TNVAN_SLOT_STEP(0)
   TNVAN_SLOT_STEP(1)
   TNVAN_SLOT_STEP(2)
@@ -524,7 +530,7 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
         lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
       }
     } else {
-      SlotState st{rnd, sb0, sb1, lq};
+      SlotState st{rnd, 0u, lq};
       if (P.slot_u == 2)
         slot_group<2>(G, TWb, gi, i0, w1, w2, tP1, tP2, tPO, p1ok, init2, inito, sH1, sH2, sS, rb1, rb2, rbS, b,
                       step32, k, key, gv, valid, st);
@@ -535,9 +541,15 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
         slot_group<4>(G, TWb, gi, i0, w1, w2, tP1, tP2, tPO, p1ok, init2, inito, sH1, sH2, sS, rb1, rb2, rbS, b,
                       step32, k, key, gv, valid, st);
       rnd = st.rnd;
-      sb0 = st.sb0;
-      sb1 = st.sb1;
       lq = st.lq;
+      // the group's spin bits (at most 8, from bit i0) into the 128-bit mask
+      const unsigned long long gb64 = st.gbits;
+      if (i0 < 64) {
+        sb0 |= gb64 << i0;
+        if (i0 > 56) sb1 |= gb64 >> (64 - i0);
+      } else {
+        sb1 |= gb64 << (i0 - 64);
+      }
     }
     // fold the group; recompute P1g for the next group
     fence_proxy_async_smem();
