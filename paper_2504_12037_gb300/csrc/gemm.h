@@ -43,6 +43,7 @@ struct GemmProblem {
 
 struct GemmLaunch {
   int* status;
+  int ncb;  // column blocks per M tile (set by launch_gemm)
   GemmProblem prob[GEMM_MAX_PROB];
 };
 

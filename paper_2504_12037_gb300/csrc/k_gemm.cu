@@ -12,6 +12,8 @@
 // accumulator row per thread (tcgen05.ld) and applies the fused operation.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "gemm.h"
 #include "tc.cuh"
@@ -19,6 +21,7 @@
 namespace tnvan {
 
 #define GM 128
+#define GN 128  // columns per CTA
 #define GK 32
 
 template <int TYPE>
@@ -135,6 +138,71 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
     }
     return;
   }
+  const bool i8 = op.type == GT_I8;
+  const bool aligned4 = ((reinterpret_cast<uintptr_t>(op.ptr) & 3) == 0);
+  if (i8 && aligned4 && full_k && op.sk == 1 && (op.sr & 3) == 0) {
+    // int8 rows along k (spins): units of (row, 4 k), four bytes per load
+    const int8_t* p = static_cast<const int8_t*>(op.ptr);
+    const int units = nrows * (GK / 4);
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      char4 c[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        const int gr = r0 + (u >> 3), kq = (u & 7) * 4;
+        c[j] = make_char4(0, 0, 0, 0);
+        if (u < units && gr != ones_row && gr < rlim)
+          c[j] = __ldg(reinterpret_cast<const char4*>(p + (long long)gr * op.sr + k0 + kq));
+        if (u < units && gr == ones_row) c[j] = make_char4(1, 1, 1, 1);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        if (u < units)
+          st4k<BF16>(s, u >> 3, (u & 7) * 4, make_float4((float)c[j].x, (float)c[j].y, (float)c[j].z, (float)c[j].w));
+      }
+    }
+    return;
+  }
+  if (i8 && aligned4 && op.sr == 1 && (op.sk & 3) == 0 && (r0 & 3) == 0 && (nrows & 3) == 0) {
+    // int8 contiguous along rows (transposed spins): units of (4 rows, k)
+    const int8_t* p = static_cast<const int8_t*>(op.ptr);
+    const int rq = nrows / 4;
+    const int units = rq * GK;
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      char4 c[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        const int gr = r0 + (u % rq) * 4, gk = k0 + u / rq;
+        c[j] = make_char4(0, 0, 0, 0);
+        if (u < units && gk < klim) {
+          if (gr + 3 < rlim && (ones_row < gr || ones_row > gr + 3)) {
+            c[j] = __ldg(reinterpret_cast<const char4*>(p + (long long)gk * op.sk + gr));
+          } else {
+            signed char e[4] = {0, 0, 0, 0};
+            for (int i = 0; i < 4; ++i) {
+              if (gr + i == ones_row) e[i] = 1;
+              else if (gr + i < rlim) e[i] = p[(long long)gk * op.sk + gr + i];
+            }
+            c[j] = make_char4(e[0], e[1], e[2], e[3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
+        if (u < units) {
+          const int r = (u % rq) * 4, k = u / rq;
+          st1<BF16>(s, r, k, (float)c[j].x);
+          st1<BF16>(s, r + 1, k, (float)c[j].y);
+          st1<BF16>(s, r + 2, k, (float)c[j].z);
+          st1<BF16>(s, r + 3, k, (float)c[j].w);
+        }
+      }
+    }
+    return;
+  }
   // generic: element by element, loads batched 16 at a time
   const bool kfast = op.sk == 1;
   const int total = nrows * GK;
@@ -184,11 +252,17 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   constexpr int EL = BF16 ? 2 : 4;
   constexpr int KB = GK * EL;
   const GemmProblem& P = L.prob[blockIdx.y];
-  const int m0 = blockIdx.x * GM;
+  // blockIdx.x = M tile * L.ncb + column block: this CTA computes columns
+  // [n_lo, n_lo + Nc) of the padded N
+  const int cb = blockIdx.x % L.ncb;
+  const int m0 = (blockIdx.x / L.ncb) * GM;
   if (m0 >= P.M) return;
   const int t = threadIdx.x;
-  const int Np = (P.N + (P.ones_col >= 0 ? 1 : 0) + 15) & ~15;  // padded N (multiple of 16)
-  const int stageA = GM * KB, stageB = 256 * KB;
+  const int Npad = (P.N + (P.ones_col >= 0 ? 1 : 0) + 15) & ~15;  // padded N (multiple of 16)
+  const int n_lo = cb * GN;
+  if (n_lo >= Npad) return;
+  const int Np = min(GN, Npad - n_lo);
+  const int stageA = GM * KB, stageB = GN * KB;
   unsigned char* sA[2] = {smem, smem + stageA + stageB};
   unsigned char* sB[2] = {smem + stageA, smem + 2 * stageA + stageB};
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (stageA + stageB));
@@ -201,7 +275,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
     mbar_init(&bar[1], 1);
   }
   if (t < 32) {
-    tc::tmem_alloc(slot, 256);
+    tc::tmem_alloc(slot, GN);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -219,7 +293,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
     }
     const int k0 = kbeg + ks * GK;
     fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t);
-    fill_stage<BF16>(sB[st], Np, P.B, 0, P.N, k0, kend, P.ones_col, t);
+    fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t);
     fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -238,71 +312,103 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   if (ok && nk > 0) ok = mbar_wait(&bar[(nk - 1) & 1], (uint32_t)(((nk - 1) >> 1) & 1));
   if (!ok && t == 0) atomicExch(L.status, 2);
   tc::fence_after_sync();
-  // epilogue: thread t owns row m0 + t (TMEM lane t)
-  const int w = t >> 5;
-  const int m = m0 + t;
+  // epilogue: TMEM lane t holds row m0 + t.  Each warp stages its 32 rows x
+  // 16 columns in shared memory (the operand stages are free: the last MMA
+  // has completed) and applies the epilogue with half a warp per row, so
+  // that every global access of a warp covers two 64-byte row segments; the
+  // chunk's epilogue inputs are loaded before any of them is used
+  const int w = t >> 5, lane = t & 31;
+  float* stg = reinterpret_cast<float*>(smem) + w * 32 * 17;
   if (ok) {
+    const int cc = lane & 15;
     for (int c = 0; c < Np; c += 16) {
       float v[16];
       if (nk > 0) tc::tmem_ld16(tmem + ((uint32_t)(w * 32) << 16) + (uint32_t)c, v);
       else
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
-      if (m >= P.M) continue;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int n = c + i;
-        float a = v[i];
+      for (int i = 0; i < 16; ++i) stg[lane * 17 + i] = v[i];
+      __syncwarp();
+      const int n = n_lo + c + cc;
+      const bool ncol = n < P.N;
+      float a[16], in[16];
+      bool ok_r[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int r = 2 * j + (lane >> 4);
+        const int m = m0 + w * 32 + r;
+        ok_r[j] = m < P.M;
+        a[j] = stg[r * 17 + cc];
+        in[j] = 0.f;
+        if (ok_r[j] && ncol) {
+          if (P.epi == EPI_MASK) in[j] = P.mask[(long long)m * P.ld_mask + n];
+          else if (P.epi == EPI_DX) in[j] = (float)P.spins[(long long)m * P.ld_spins + n];
+        }
+      }
+      const float bn = (ncol && (P.epi == EPI_BIAS_RELU || P.epi == EPI_DX)) ? P.bias[n] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int m = m0 + w * 32 + 2 * j + (lane >> 4);
+        if (!ok_r[j]) continue;
         if (n == P.ones_col) {
-          if (P.bias_out) P.bias_out[(long long)blockIdx.z * P.split_stride + m] = a;
+          if (P.bias_out) P.bias_out[(long long)blockIdx.z * P.split_stride + m] = a[j];
           continue;
         }
-        if (n >= P.N) continue;
+        if (!ncol) continue;
         const long long o = (long long)m * P.ldc + n;
         switch (P.epi) {
           case EPI_STORE:
-            P.C[(long long)blockIdx.z * P.split_stride + o] = a;
+            P.C[(long long)blockIdx.z * P.split_stride + o] = a[j];
             break;
           case EPI_BIAS_RELU:
-            P.C[o] = fmaxf(a + P.bias[n], 0.f);
+            P.C[o] = fmaxf(a[j] + bn, 0.f);
             break;
           case EPI_DX: {
-            const float x = a + P.bias[n];
-            const float s = (float)P.spins[(long long)m * P.ld_spins + n];
-            P.C[o] = P.row_w[m] * s / (1.f + expf(s * x));
+            const float x = a[j] + bn, sp = in[j];
+            P.C[o] = P.row_w[m] * sp / (1.f + expf(sp * x));
             break;
           }
           case EPI_MASK:
-            P.C[o] = P.mask[(long long)m * P.ld_mask + n] > 0.f ? a : 0.f;
+            P.C[o] = in[j] > 0.f ? a[j] : 0.f;
             break;
         }
       }
+      __syncwarp();
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (t < 32) tc::tmem_dealloc(tmem, 256);
+  if (t < 32) tc::tmem_dealloc(tmem, GN);
 }
 
 int gemm_smem_bytes(bool bf16) {
   const int EL = bf16 ? 2 : 4;
-  return 2 * (GM * GK * EL + 256 * GK * EL) + 64;
+  return 2 * (GM * GK * EL + GN * GK * EL) + 64;
 }
 
 cudaError_t launch_gemm(const GemmLaunch& L, int n_prob, int max_m, int splits, bool bf16,
                         cudaStream_t s) {
   if (n_prob == 0 || max_m == 0) return cudaSuccess;
   const int smem = gemm_smem_bytes(bf16);
-  dim3 grid((max_m + GM - 1) / GM, n_prob, splits);
+  // column blocks of GN: the widest padded N of the launch's problems
+  int max_np = 16;
+  for (int i = 0; i < n_prob; ++i) {
+    const GemmProblem& P = L.prob[i];
+    max_np = std::max(max_np, (P.N + (P.ones_col >= 0 ? 1 : 0) + 15) & ~15);
+  }
+  GemmLaunch Lm = L;
+  Lm.ncb = (max_np + GN - 1) / GN;
+  dim3 grid(((max_m + GM - 1) / GM) * Lm.ncb, n_prob, splits);
   cudaError_t e;
   if (bf16) {
     e = cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<true><<<grid, 128, smem, s>>>(L);
+    gemm_tc_kernel<true><<<grid, 128, smem, s>>>(Lm);
   } else {
     e = cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<false><<<grid, 128, smem, s>>>(L);
+    gemm_tc_kernel<false><<<grid, 128, smem, s>>>(Lm);
   }
   return cudaGetLastError();
 }
