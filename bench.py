@@ -93,7 +93,7 @@ def args_():
                     help="also time the training step on random regular graphs (n = 1000, d = 3) whose width "
                          "sets come from the width-set finder")
     ap.add_argument("--ferro40", type=int, default=0, metavar="STEPS",
-                    help="also train the 40x40 open ferromagnet (W = every 5th column) at T = 1, 2, T_c, 3, 4, 5 "
+                    help="also train the 40x40 open ferromagnet (W = every 13th column) at T = 1, 2, T_c, 3, 4, 5 "
                          "for STEPS Adam steps and report |F - F_exact| / |F_exact| against the Kac-Ward value")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the captured step over per-instance batches 2^8 .. 2^18 (the asymptote)")

@@ -264,6 +264,95 @@ int plan_strips(tnvan_ctx* ctx, Instance& in, const std::map<std::pair<int, int>
   return TNVAN_OK;
 }
 
+// Wide strips: a lattice whose width set is whole columns, leaving strips of
+// at most TNVAN_WIDE_MAX_W columns, gets (besides its elimination plan) the
+// rows of every strip for the wide-strip forward contraction, in the same
+// gauge as plan_strips.  Leaves in.wide empty when the instance does not
+// qualify (then the elimination plan does everything).
+void plan_wide_strips(Instance& in, const std::map<std::pair<int, int>, int>& edge_of, const std::vector<int>& pos) {
+  in.wide = HostWidePlan{};
+  if (in.topology != TNVAN_LATTICE2D) return;
+  const int Lx = in.Lx, Ly = in.Ly;
+  std::vector<int> colW(Lx, 0);
+  for (int w : in.W) colW[w % Lx]++;
+  for (int x = 0; x < Lx; ++x)
+    if (colW[x] != 0 && colW[x] != Ly) return;
+  auto eid = [&](int a, int b) {
+    auto it = edge_of.find({std::min(a, b), std::max(a, b)});
+    return it == edge_of.end() ? -1 : it->second;
+  };
+  std::vector<char> used(in.m, 0);
+  HostWidePlan plan;
+  for (int x = 0; x < Lx;) {
+    if (colW[x]) {
+      ++x;
+      continue;
+    }
+    const int x0 = x;
+    while (x < Lx && !colW[x]) ++x;
+    const int w = x - x0;
+    if (w > TNVAN_WIDE_MAX_W) return;
+    WideStripDev sd{};
+    sd.w = w;
+    sd.L = Ly;
+    sd.row0 = (int)plan.rows.size();
+    double chat = 0;
+    // gauge: tau_c(y + 1) = tau_c(y) sign(Jv(y, c)) makes every vertical bond ferromagnetic
+    float tau[TNVAN_WIDE_MAX_W];
+    for (int c = 0; c < TNVAN_WIDE_MAX_W; ++c) tau[c] = 1.f;
+    for (int y = 0; y < Ly; ++y) {
+      WideRow R{};
+      R.posL = R.posR = -1;
+      for (int c = 0; c + 1 < w; ++c) {
+        const int e = eid(y * Lx + x0 + c, y * Lx + x0 + c + 1);
+        if (e >= 0) {
+          R.Jh[c] = (float)in.J[e] * tau[c] * tau[c + 1];
+          used[e] = 1;
+          chat += fabs((double)R.Jh[c]);
+        }
+      }
+      if (x0 > 0) {
+        const int e = eid(y * Lx + x0 - 1, y * Lx + x0);
+        if (e >= 0) {
+          R.JL = (float)in.J[e] * tau[0];
+          R.posL = pos[y * Lx + x0 - 1];
+          used[e] = 1;
+          chat += fabs((double)R.JL);
+        }
+      }
+      if (x0 + w < Lx) {
+        const int e = eid(y * Lx + x0 + w - 1, y * Lx + x0 + w);
+        if (e >= 0) {
+          R.JR = (float)in.J[e] * tau[w - 1];
+          R.posR = pos[y * Lx + x0 + w];
+          used[e] = 1;
+          chat += fabs((double)R.JR);
+        }
+      }
+      if (y + 1 < Ly) {
+        for (int c = 0; c < w; ++c) {
+          const int e = eid(y * Lx + x0 + c, (y + 1) * Lx + x0 + c);
+          if (e >= 0) {
+            R.Jv[c] = (float)fabs(in.J[e]);
+            if (in.J[e] < 0) tau[c] = -tau[c];
+            used[e] = 1;
+            chat += fabs((double)R.Jv[c]);
+          }
+        }
+      }
+      plan.rows.push_back(R);
+    }
+    sd.c_hat = chat;
+    plan.strips.push_back(sd);
+  }
+  for (int e = 0; e < in.m; ++e) {
+    const bool wa = pos[in.ei[e]] >= 0, wb = pos[in.ej[e]] >= 0;
+    if (wa && wb) used[e] = 1;
+    if (!used[e]) return;  // a bond the strips do not carry
+  }
+  in.wide = std::move(plan);
+}
+
 // Connected components of the graph induced on R.
 std::vector<std::vector<int>> r_components(const Instance& in, const std::vector<int>& pos) {
   std::vector<std::vector<int>> adj(in.n);
@@ -298,6 +387,16 @@ int upload_plan(tnvan_ctx* ctx, Instance& in) {
   if ((rc = upload(ctx, in, in.ww, &dww))) return rc;
   in.dev.ww = dww;
   in.dev.n_ww = (int)in.ww.size();
+  in.dev.n_wide = 0;
+  if (!in.wide.strips.empty()) {
+    WideStripDev* dws = nullptr;
+    WideRow* dwr = nullptr;
+    if ((rc = upload(ctx, in, in.wide.strips, &dws))) return rc;
+    if ((rc = upload(ctx, in, in.wide.rows, &dwr))) return rc;
+    in.dev.wide = dws;
+    in.dev.wrows = dwr;
+    in.dev.n_wide = (int)in.wide.strips.size();
+  }
   if (in.kind == 0) {
     StripDev* ds = nullptr;
     StripRow* dr = nullptr;
@@ -859,6 +958,7 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   if (ctx->d_ws) cudaFree(ctx->d_ws);
   if (ctx->d_obs) cudaFree(ctx->d_obs);
   if (ctx->d_dj_part) cudaFree(ctx->d_dj_part);
+  if (ctx->d_wide_part) cudaFree(ctx->d_wide_part);
   for (float* p : ctx->d_gen_scratch)
     if (p) cudaFree(p);
   delete ctx;
@@ -941,6 +1041,7 @@ int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int
   reset_plan(in);
   in.W.assign(w, w + n_w);
   in.ww.clear();
+  in.wide = HostWidePlan{};
   std::map<std::pair<int, int>, int> edge_of;
   for (int e = 0; e < in.m; ++e) {
     edge_of[{std::min(in.ei[e], in.ej[e]), std::max(in.ei[e], in.ej[e])}] = e;
@@ -969,8 +1070,23 @@ int tnvan_set_width_set_ordered(tnvan_ctx* ctx, int instance, int n_w, const int
   if (rc == TNVAN_OK && r_order) return fail(ctx, TNVAN_E_ARG, "r_order is only used by elimination plans");
   if (rc == TNVAN_E_UNSUPPORTED) {
     ctx->err.clear();
-    rc = plan_general(ctx, in, pos, rank);
+    if (in.topology == TNVAN_LATTICE2D && rank.empty()) {
+      // a lattice whose strips are too wide for the strip kernels: eliminate
+      // row by row (width = the widest strip), else by min-fill
+      std::vector<int> rm(in.n, -1);
+      int r = 0;
+      for (int v = 0; v < in.n; ++v)
+        if (pos[v] < 0) rm[v] = r++;
+      rc = plan_general(ctx, in, pos, rm);
+      if (rc == TNVAN_E_UNSUPPORTED) {
+        ctx->err.clear();
+        rc = plan_general(ctx, in, pos, rank);
+      }
+    } else {
+      rc = plan_general(ctx, in, pos, rank);
+    }
     if (rc) return rc;
+    plan_wide_strips(in, edge_of, pos);
   }
   if ((rc = upload_plan(ctx, in))) return rc;
   in.has_ws = true;
@@ -1543,6 +1659,25 @@ static int ensure_gen_scratch(tnvan_ctx* ctx, int which, size_t floats) {
   return TNVAN_OK;
 }
 
+// Per-strip results of the wide-strip kernels [n_inst][batch][strips]; grows only.
+static int ensure_wide_part(tnvan_ctx* ctx, size_t n) {
+  if (n <= ctx->wide_part_n) return TNVAN_OK;
+  if (ctx->d_wide_part) cudaFree(ctx->d_wide_part);
+  ctx->d_wide_part = nullptr;
+  ctx->wide_part_n = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_wide_part, n * sizeof(double));
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(wide strips, %zu): %s", n, cudaGetErrorString(e));
+  ctx->wide_part_n = n;
+  return TNVAN_OK;
+}
+
+static int wide_max_strips(const tnvan_ctx* ctx) {
+  int ms = 0;
+  for (const Instance& in : ctx->inst)
+    if (in.kind == 2) ms = std::max(ms, in.dev.n_wide);
+  return ms;
+}
+
 static int ensure_grad_ws(tnvan_ctx* ctx, size_t floats) {
   if (floats <= ctx->grad_packed_floats) return TNVAN_OK;
   if (ctx->d_grad_packed) cudaFree(ctx->d_grad_packed);
@@ -1594,6 +1729,8 @@ int tnvan_reserve(tnvan_ctx* ctx, int max_batch) {
     }
     rc = ensure_dj_part(ctx, (size_t)ctas * ((max_edges + 3) & ~3));
     if (rc) return rc;
+    const int ms = wide_max_strips(ctx);
+    if (ms > 0 && (rc = ensure_wide_part(ctx, ctx->inst.size() * (size_t)std::max(max_batch, 1) * ms))) return rc;
   }
   ctx->reserved_batch = std::max(ctx->reserved_batch, max_batch);
   CK(cudaDeviceSynchronize(), "reserve");
@@ -2832,6 +2969,39 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
       if (in.kind == 1) max_D = std::max(max_D, (int)in.W.size());
     CK(launch_dense(ctx->d_inst, li, precision, d_spins, d_logZR, d_dbeta, nullptr, s, max_D), "dense kernel");
   }
+  // lattice instances with a wide-strip plan: log Z_R by the wide-strip
+  // kernel (forward mode d/dbeta stays with their elimination plans)
+  bool any_wide = false;
+  for (const Instance& in : ctx->inst) any_wide = any_wide || (in.kind == 2 && in.dev.n_wide > 0 && !d_dbeta);
+  if (any_wide) {
+    LaunchInfo lw;
+    if ((rc = fill_launch(ctx, betas, batch, 1, lw))) return rc;
+    int acc = 0, ms = 0, Dm = 0;
+    bool rest = false;
+    for (int k = 0; k < lw.n_inst; ++k) {
+      const Instance& in = ctx->inst[k];
+      lw.tile_begin[k] = acc;
+      if (in.kind == 2 && in.dev.n_wide > 0) {
+        acc += batch;
+        ms = std::max(ms, in.dev.n_wide);
+        Dm = std::max(Dm, (int)in.W.size());
+      } else if (in.kind == 2) {
+        rest = true;
+      }
+    }
+    lw.tile_begin[lw.n_inst] = acc;
+    int per_class[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (const Instance& in : ctx->inst) {
+      if (in.kind != 2 || in.dev.n_wide == 0) continue;
+      int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (const WideStripDev& sd : in.wide.strips) ++cnt[sd.w <= 5 ? 0 : sd.w - 5];
+      for (int c = 0; c < 8; ++c) per_class[c] = std::max(per_class[c], cnt[c]);
+    }
+    if ((rc = ensure_wide_part(ctx, (size_t)lw.n_inst * batch * ms))) return rc;
+    PROF("wide_strips", s);
+    CK(launch_wide(ctx->d_inst, lw, per_class, ms, Dm, d_spins, ctx->d_wide_part, d_logZR, s), "wide-strip kernels");
+    k2 = rest;
+  }
   if (k2) {
     int arena = 0, Dm = 0, nsteps = 0;
     for (const Instance& in : ctx->inst)
@@ -2849,6 +3019,15 @@ int contract_all(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d
     LaunchInfo lg;
     if ((rc = fill_launch(ctx, betas, batch, T, lg))) return rc;
     lg.seed = (unsigned long long)arena;
+    if (any_wide) {  // instances the wide-strip kernel has contracted get no tiles
+      int acc = 0;
+      for (int k = 0; k < lg.n_inst; ++k) {
+        const int nt = lg.tile_begin[k + 1] - lg.tile_begin[k];
+        lg.tile_begin[k] = acc;
+        if (!(ctx->inst[k].kind == 2 && ctx->inst[k].dev.n_wide > 0)) acc += nt;
+      }
+      lg.tile_begin[lg.n_inst] = acc;
+    }
     {
       PROF("general_pp", s);
       CK(launch_general_pp(ctx->d_inst, lg, nsteps, s), "elimination bond products");

@@ -133,6 +133,25 @@ struct alignas(16) StripRow {
   int tau_mask;  // bit c set iff the gauge flips column c in this row (model spin = -strip spin)
 };
 
+// Wide lattice strip (5 to TNVAN_WIDE_MAX_W whole columns; forward
+// contraction of elimination instances, see k_wide.cu): per row the
+// gauge-signed horizontal couplings Jh[c] (c, c+1), the W-neighbour couplings
+// JL, JR (0 = none) with their AR positions, and the vertical couplings
+// Jv[c] >= 0 to the next row (the planner's gauge, as for StripRow).
+#define TNVAN_WIDE_MAX_W 12
+struct WideRow {
+  float Jh[TNVAN_WIDE_MAX_W - 1];
+  float JL, JR;
+  float Jv[TNVAN_WIDE_MAX_W];
+  int posL, posR;
+};
+struct WideStripDev {
+  int w, L;
+  int row0;      // first row in the instance's wide-row array
+  int pad;
+  double c_hat;  // sum of |J| over the strip's bonds (horizontal, vertical, W neighbours)
+};
+
 struct StripDev {
   int w, L;
   int row0;       // index of the first row in the instance's row array
@@ -221,6 +240,11 @@ struct InstDev {
   DenseDev dense;
   // general
   GenDev gen;
+  // wide lattice strips of an elimination instance (forward log Z_R only;
+  // n_wide = 0: none)
+  int n_wide;
+  const WideStripDev* wide;
+  const WideRow* wrows;
 };
 
 // Per-launch parameters passed by value.
@@ -234,6 +258,7 @@ struct LaunchInfo {
   const unsigned long long* step_dev;  // optional device step counter added to `step`
   const float* wmul;  // optional per-sample multipliers [n_inst * batch] of the adjoint's bond sums
   int gen_tab;        // elimination instances: > 0 = build and use the component tables (the largest n_tab)
+  int tile_aux;       // wide-strip launches: the most strips of an instance (shared-memory rows)
   double beta[TNVAN_MAX_INST];
   int tile_begin[TNVAN_MAX_INST + 1];
   unsigned int skip[TNVAN_MAX_INST / 32];  // per-instance bits: 1 = a kernel that reads them leaves the instance out
@@ -251,6 +276,11 @@ struct HostStripPlan {
   std::vector<float> edge_sign;
 };
 
+struct HostWidePlan {
+  std::vector<WideStripDev> strips;
+  std::vector<WideRow> rows;
+};
+
 struct Instance {
   bool has_graph = false, has_ws = false, has_made = false;
   int n = 0, m = 0, topology = 0, Lx = 0, Ly = 0;
@@ -262,6 +292,7 @@ struct Instance {
   int n_comp = 0, max_comp = 0, max_width = 0;
   std::vector<EdgeWW> ww;
   HostStripPlan strip;
+  HostWidePlan wide;  // lattice instances planned for elimination whose R is strips of <= 12 columns
   // dense
   int dense_nR = 0;
   std::vector<float> JRW, JRR;
@@ -335,6 +366,8 @@ struct tnvan_ctx {
   size_t dj_part_floats = 0;
   float* d_gen_scratch[2] = {nullptr, nullptr};  // global elimination tables: forward, reverse sweep
   size_t gen_scratch_floats[2] = {0, 0};
+  double* d_wide_part = nullptr;  // per-strip log Z of the wide-strip kernels
+  size_t wide_part_n = 0;
   void* d_obs = nullptr;             // tnvan_observables: weights, d/dbeta, sums
   size_t obs_bytes = 0;
 };
@@ -384,6 +417,14 @@ cudaError_t launch_strip_tables(const InstDev* d_inst, const LaunchInfo& li, int
 // reduces dbeta and wmul to out[3k..3k+2] = U, U_q, effective sample size.
 cudaError_t launch_observables(const LaunchInfo& li, const double* logZR, const float* logq, const double* stats,
                                const double* dbeta, float* wmul, double* out, bool energies, cudaStream_t s);
+// Wide strips (k_wide.cu): log Z_R of the elimination instances that carry a
+// wide-strip plan (li: one tile per sample of the instances to run, zero
+// tiles for the others), one CTA per sample, one launch per class of states
+// per lane (strips_per_class[c]: the most strips of 2^c states per lane in
+// one instance, c = 0 for strips of <= 5 columns), per-strip results in
+// part [n_inst][batch][max_strips], then their sum in strip order.
+cudaError_t launch_wide(const InstDev* d_inst, const LaunchInfo& li, const int* strips_per_class, int max_strips,
+                        int max_D, const int8_t* spins, double* part, double* logZR, cudaStream_t s);
 // Magnetisation moments (tnvan_magnetisation): per sample E[M | s] and
 // Var(M | s) of the whole system's magnetisation given the width set, by
 // contraction kind (strips: li.tile samples per CTA, smem as strip_smem_bytes;

@@ -295,14 +295,14 @@ def ferromagnet_columns(L: int = 40, period: int = 13, hidden: Sequence[int] = (
     Onsager's critical temperature), one instance per temperature; W = every
     `period`-th column (columns c with c % period == period - 1), which leaves
     strips of period - 1 columns.  With period > 5 the strips are wider than
-    the strip contraction takes, so the graph is given as a general one and
-    each strip is eliminated row by row (elimination width = strip width)."""
+    the per-thread strip contraction takes: the plan is an elimination plan
+    (each strip eliminated row by row, elimination width = strip width, the
+    order given here) and the forward contraction runs the wide-strip kernel."""
     g = lattice(L, L, "ferro", 0)
     cols = every_kth_column(L, period)
     W = width_columns(L, L, cols)
     order = None
     if period > 5:
-        g = Graph(g.n, g.ei, g.ej, g.J, GENERAL)
         wset = set(int(v) for v in W)
         order = np.asarray([y * L + x for y in range(L) for x in range(L) if y * L + x not in wset], np.int32)
     temps = [1.0, 2.0, 2.0 / np.log(1.0 + np.sqrt(2.0)), 3.0, 4.0, 5.0]
