@@ -95,6 +95,11 @@ def args_():
     ap.add_argument("--ferro40", type=int, default=0, metavar="STEPS",
                     help="also train the 40x40 open ferromagnet (W = every 13th column) at T = 1, 2, T_c, 3, 4, 5 "
                          "for STEPS Adam steps and report |F - F_exact| / |F_exact| against the Kac-Ward value")
+    ap.add_argument("--ferro-batch", type=int, default=1000, help="--ferro40: samples per temperature and step")
+    ap.add_argument("--ferro-lr", type=float, default=0.01,
+                    help="--ferro40: Adam learning rate (divided by 10 for the last third of the steps)")
+    ap.add_argument("--ferro-period", type=int, default=13,
+                    help="--ferro40: W = columns c with c %% P == P - 1 (strips of P - 1 columns)")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the captured step over per-instance batches 2^8 .. 2^18 (the asymptote)")
     return ap.parse_args()
@@ -629,13 +634,14 @@ def run_ours(a):
     if a.ferro40 > 0:
         # the paper's first experiment (Sec. 4, Fig. 2): training steps in FP32,
         # then F_q and F_IS from one large batch per temperature
-        wf = wl.ferromagnet_columns()
+        wf = wl.ferromagnet_columns(period=a.ferro_period, batch=a.ferro_batch)
         mf = TNVAN(wf.graphs, wf.widths_sets, wf.hidden, wf.betas, device=local, seed=1000 * rank + 9,
                    elim_orders=wf.elim_orders)
         bf = mf.buffers(wf.batch)
         t0 = time.time()
         for i in range(a.ferro40):
-            mf.train_step(wf.batch, 40 + rank, i, tv.FP32, 0.01, bf, None, None, stream)
+            lr = a.ferro_lr if 3 * i < 2 * a.ferro40 else a.ferro_lr / 10
+            mf.train_step(wf.batch, 40 + rank, i, tv.FP32, lr, bf, None, None, stream)
         torch.cuda.synchronize()
         t_train = time.time() - t0
         Bf = 16384
@@ -643,9 +649,21 @@ def run_ours(a):
         fe = mf.free_energy(Bf, lzf, lqf)
         N = wf.graphs[0].n
         ferro = {"workload": wf.name, "train_steps": a.ferro40, "train_batch": wf.batch, "made": wf.hidden,
+                 "lr": [a.ferro_lr, a.ferro_lr / 10], "W_size": int(len(wf.widths_sets[0])),
                  "train_s": t_train, "eval_batch": Bf, "T": [1.0 / b for b in wf.betas],
                  "F_q_per_spin": [float(x) / N for x in fe[:, 0]], "F_IS_per_spin": [float(x) / N for x in fe[:, 1]],
                  "stderr_per_spin": [float(x) / N for x in fe[:, 2]]}
+        # magnetisation and susceptibility (Sec. 3) from a smaller batch: the
+        # exact conditional moments of M per sample, importance-weighted
+        Bm = 2048
+        spm, lqm, lzm = mf.sample(Bm, 4141 + rank, 10 ** 7 + 1, tv.FP32)
+        t0 = time.time()
+        mag = mf.ctx.magnetisation(mf.betas, Bm, spm, lzm, lqm)
+        torch.cuda.synchronize()
+        ferro["magnetisation"] = {"batch": Bm, "s": time.time() - t0,
+                                  "rms_M_per_spin": [float(np.sqrt(max(r[1], 0.0))) / N for r in mag],
+                                  "M_per_spin": [float(r[0]) / N for r in mag],
+                                  "chi_per_spin": [float(r[2]) for r in mag], "ess": [float(r[5]) for r in mag]}
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, model.params.cpu().numpy(), model.offsets, budget_s=15.0)
         # the oracle's exact free energy of the lattice (single-site transfer matrix, 2^16 states)
@@ -658,7 +676,7 @@ def run_ours(a):
         # the oracle on sampled rows of one timed-path step per precision
         out["parity"] = oracle_parity(w, parity_runs, check_stats=world == 1)
         if ferro is not None:
-            ferro.update(oracle_ferro_exact(wl.ferromagnet_columns(), ferro))
+            ferro.update(oracle_ferro_exact(wl.ferromagnet_columns(period=a.ferro_period), ferro))
     if ferro is not None:
         out["ferromagnet_40x40"] = ferro
     if world > 1:

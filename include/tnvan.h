@@ -461,6 +461,17 @@ int tnvan_profile(tnvan_ctx* ctx, int enable);
 int tnvan_profile_read(tnvan_ctx* ctx, int index, char* name, int name_len, double* total_ms,
                        int64_t* launches);
 
+/* Timeline of the launches recorded since profiling was enabled, a tracing
+ * aid: for launch n (kernels in first-launch order, each kernel's launches in
+ * recording order) kernel[n] = its kernel index (as for tnvan_profile_read)
+ * and start_ms[n], end_ms[n] its bracketing events relative to an event
+ * recorded before the first profiled launch, whatever streams the launches
+ * ran on.  Writes at most max_entries (host arrays, any may be NULL); *n_out =
+ * the number of recorded launches.  Call before tnvan_profile_read, which
+ * consumes the records.  Synchronous.  Errors: TNVAN_E_ARG, TNVAN_E_CUDA. */
+int tnvan_profile_trace(tnvan_ctx* ctx, int64_t max_entries, int32_t* kernel, float* start_ms, float* end_ms,
+                        int64_t* n_out);
+
 /* Allocation-free free-energy reduction.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory at all
  * (an external memory manager that owns every byte, a plugin that must not

@@ -79,6 +79,11 @@ struct Prof {
     }
     a = take(ctx);
     b = take(ctx);
+    if (!ctx->prof_ref_set) {
+      if (!ctx->prof_ref) cudaEventCreate(&ctx->prof_ref);
+      if (ctx->prof_ref) cudaEventRecord(ctx->prof_ref, s);
+      ctx->prof_ref_set = ctx->prof_ref != nullptr;
+    }
     if (a) cudaEventRecord(a, s);
   }
   ~Prof() {
@@ -959,6 +964,7 @@ int tnvan_destroy(tnvan_ctx* ctx) {
   if (ctx->d_obs) cudaFree(ctx->d_obs);
   if (ctx->d_dj_part) cudaFree(ctx->d_dj_part);
   if (ctx->d_wide_part) cudaFree(ctx->d_wide_part);
+  if (ctx->prof_ref) cudaEventDestroy(ctx->prof_ref);
   for (float* p : ctx->d_gen_scratch)
     if (p) cudaFree(p);
   delete ctx;
@@ -2786,8 +2792,31 @@ int tnvan_profile(tnvan_ctx* ctx, int enable) {
         ctx->event_pool.push_back(pr.second);
       }
     ctx->prof.clear();
+    ctx->prof_ref_set = false;
   }
   ctx->prof_on = enable != 0;
+  return TNVAN_OK;
+}
+
+int tnvan_profile_trace(tnvan_ctx* ctx, int64_t max_entries, int32_t* kernel, float* start_ms, float* end_ms,
+                        int64_t* n_out) {
+  if (!ctx || !n_out || max_entries < 0) return TNVAN_E_ARG;
+  DeviceGuard g(ctx->device);
+  int64_t n = 0;
+  for (size_t i = 0; i < ctx->prof.size(); ++i)
+    for (auto& pr : ctx->prof[i].pending) {
+      if (n < max_entries && ctx->prof_ref_set) {
+        CK(cudaEventSynchronize(pr.second), "trace event sync");
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, ctx->prof_ref, pr.first), "trace elapsed time");
+        CK(cudaEventElapsedTime(&b, ctx->prof_ref, pr.second), "trace elapsed time");
+        if (kernel) kernel[n] = (int32_t)i;
+        if (start_ms) start_ms[n] = a;
+        if (end_ms) end_ms[n] = b;
+      }
+      ++n;
+    }
+  *n_out = n;
   return TNVAN_OK;
 }
 

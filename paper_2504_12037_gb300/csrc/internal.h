@@ -348,6 +348,8 @@ struct tnvan_ctx {
   bool prof_on = false;
   std::vector<tnvan_prof_rec> prof;
   std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t prof_ref = nullptr;  // recorded before the first launch of a profiled region (trace origin)
+  bool prof_ref_set = false;
   std::string err;
   std::vector<tnvan::Instance> inst;
   tnvan::InstDev* d_inst = nullptr;  // device copy of the descriptors

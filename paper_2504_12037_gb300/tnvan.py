@@ -64,6 +64,7 @@ SIGNATURES = {
     "tnvan_set_tuning": (_c_int, [_vp, _i32p]),
     "tnvan_profile": (_c_int, [_vp, _c_int]),
     "tnvan_profile_read": (_c_int, [_vp, _c_int, ctypes.c_char_p, _c_int, _dblp, _i64p]),
+    "tnvan_profile_trace": (_c_int, [_vp, ctypes.c_int64, _vp, _vp, _vp, _i64p]),
 }
 
 _LIB = None
@@ -310,6 +311,19 @@ class Context:
 
     def profile(self, enable: bool):
         self._check(lib().tnvan_profile(self._h, int(enable)))
+
+    def profile_trace(self):
+        """[(kernel index, start ms, end ms)] of every recorded launch, relative to
+        the start of the profiled region (call before profile_read)."""
+        n = ctypes.c_int64()
+        self._check(lib().tnvan_profile_trace(self._h, 0, None, None, None, ctypes.byref(n)))
+        m = n.value
+        kk = np.zeros(m, np.int32)
+        a = np.zeros(m, np.float32)
+        b = np.zeros(m, np.float32)
+        self._check(lib().tnvan_profile_trace(self._h, m, kk.ctypes.data, a.ctypes.data, b.ctypes.data,
+                                              ctypes.byref(n)))
+        return list(zip(kk.tolist(), a.tolist(), b.tolist()))
 
     def profile_read(self):
         """{kernel name: (total ms, launches)} of the recorded launches."""
