@@ -1842,11 +1842,13 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
     CK(cudaStreamWaitEvent(ctx->side_lo[c], ctx->fork_ev, 0), "fork wait");
     CK(launch_strip_tables(ctx->d_inst, la, k0, k1, ctx->side_lo[c]), "strip tables");
     CK(cudaStreamWaitEvent(ctx->side_lo[c], ctx->chunk_ev[c], 0), "chunk wait");
-    PROF("strips_adj", ctx->side_lo[c]);
-    CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
-                         d_dJ ? ctx->d_dj_part : nullptr, stride, nullptr, ctx->side_lo[c], la.tile_begin[k0],
-                         la.tile_begin[k1], adj_ws),
-       "strip adjoint kernel");
+    {
+      PROF("strips_adj", ctx->side_lo[c]);
+      CK(launch_strips_adj(ctx->d_inst, la, adj_smem, adj_lv, d_spins, d_logZR, d_dbeta,
+                           d_dJ ? ctx->d_dj_part : nullptr, stride, nullptr, ctx->side_lo[c], la.tile_begin[k0],
+                           la.tile_begin[k1], adj_ws),
+         "strip adjoint kernel");
+    }
     CK(cudaEventRecord(ctx->adj_ev[c], ctx->side_lo[c]), "adjoint event");
     if (chunk_stats || cb) {
       PROF("reduce", ctx->side_lo[c]);

@@ -60,6 +60,34 @@ __device__ __forceinline__ void st1(unsigned char* s, int r, int k, float v) {
   else *reinterpret_cast<float*>(s + o) = v;
 }
 
+// BF16 operands contiguous along their rows (transposed: the weight-gradient
+// operands, the transposed weights) are staged MN-major instead: element
+// (r, k) at (r >> 3) * MN_SBO + (k >> 3) * 128 + (k & 7) * 16 + (r & 7) * 2, so
+// four consecutive rows at one k are one 8-byte store; the MMA reads them
+// with the operand's major bit set.  MN_SBO pads each 8-row group by 16 bytes.
+#define MN_SBO (GK * 2 / 16 * 128 + 16)
+#define GSTAGE_BF16 (16 * MN_SBO)  // bytes of one BF16 operand stage (either layout, 128 rows)
+__device__ __forceinline__ uint32_t mn_off(int r, int k) {
+  return (uint32_t)((r >> 3) * MN_SBO + (k >> 3) * 128 + (k & 7) * 16 + (r & 7) * 2);
+}
+__device__ __forceinline__ void st4r_bf16(unsigned char* s, int r, int k, float a, float b, float c, float d) {
+  __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+  uint2 u;
+  u.x = *reinterpret_cast<uint32_t*>(&x);
+  u.y = *reinterpret_cast<uint32_t*>(&y);
+  *reinterpret_cast<uint2*>(s + mn_off(r, k)) = u;
+}
+
+// Whether fill_stage stages this operand MN-major (BF16 only; the transposed
+// FP32 or int8 paths, whatever the stage).
+__device__ __forceinline__ bool operand_mn(const GemmOperand& op, int r0, int nrows) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(op.ptr);
+  if (op.sr != 1 || op.sk == 1 || (op.sk & 3) != 0 || (r0 & 3) != 0 || (nrows & 3) != 0) return false;
+  if (op.type == GT_F32) return (a & 15) == 0;
+  if (op.type == GT_I8) return (a & 3) == 0;
+  return false;
+}
+
 // Fill one K stage: rows [r0, r0 + nrows) of an operand, k in [k0, k0 + GK).
 // Rows >= rlim or k >= klim are zero; row == ones_row reads 1 (bias column).
 // Loads are issued in batches (registers first, stores after) so that each
@@ -67,11 +95,11 @@ __device__ __forceinline__ void st1(unsigned char* s, int r, int k, float v) {
 // index is k (or the row) are read as float4.
 template <bool BF16>
 __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
-                                           int r0, int rlim, int k0, int klim, int ones_row, int t) {
+                                           int r0, int rlim, int k0, int klim, int ones_row, int t, bool mn) {
   const bool full_k = k0 + GK <= klim;
   const bool f32 = op.type == GT_F32;
   const bool aligned = ((reinterpret_cast<uintptr_t>(op.ptr) & 15) == 0);
-  if (f32 && aligned && full_k && op.sk == 1 && (op.sr & 3) == 0) {
+  if (!mn && f32 && aligned && full_k && op.sk == 1 && (op.sr & 3) == 0) {
     // row-major along k: units of (row, 4 k)
     const float* p = static_cast<const float*>(op.ptr);
     const int units = nrows * (GK / 4);
@@ -129,10 +157,14 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
         const int u = u0 + t + 128 * j;
         if (u < units) {
           const int r = (u % rq) * 4, k = u / rq;
-          st1<BF16>(s, r, k, v[j].x);
-          st1<BF16>(s, r + 1, k, v[j].y);
-          st1<BF16>(s, r + 2, k, v[j].z);
-          st1<BF16>(s, r + 3, k, v[j].w);
+          if (BF16 && mn) {
+            st4r_bf16(s, r, k, v[j].x, v[j].y, v[j].z, v[j].w);
+          } else {
+            st1<BF16>(s, r, k, v[j].x);
+            st1<BF16>(s, r + 1, k, v[j].y);
+            st1<BF16>(s, r + 2, k, v[j].z);
+            st1<BF16>(s, r + 3, k, v[j].w);
+          }
         }
       }
     }
@@ -140,7 +172,7 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
   }
   const bool i8 = op.type == GT_I8;
   const bool aligned4 = ((reinterpret_cast<uintptr_t>(op.ptr) & 3) == 0);
-  if (i8 && aligned4 && full_k && op.sk == 1 && (op.sr & 3) == 0) {
+  if (!mn && i8 && aligned4 && full_k && op.sk == 1 && (op.sr & 3) == 0) {
     // int8 rows along k (spins): units of (row, 4 k), four bytes per load
     const int8_t* p = static_cast<const int8_t*>(op.ptr);
     const int units = nrows * (GK / 4);
@@ -194,10 +226,14 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
         const int u = u0 + t + 128 * j;
         if (u < units) {
           const int r = (u % rq) * 4, k = u / rq;
-          st1<BF16>(s, r, k, (float)c[j].x);
-          st1<BF16>(s, r + 1, k, (float)c[j].y);
-          st1<BF16>(s, r + 2, k, (float)c[j].z);
-          st1<BF16>(s, r + 3, k, (float)c[j].w);
+          if (BF16 && mn) {
+            st4r_bf16(s, r, k, (float)c[j].x, (float)c[j].y, (float)c[j].z, (float)c[j].w);
+          } else {
+            st1<BF16>(s, r, k, (float)c[j].x);
+            st1<BF16>(s, r + 1, k, (float)c[j].y);
+            st1<BF16>(s, r + 2, k, (float)c[j].z);
+            st1<BF16>(s, r + 3, k, (float)c[j].w);
+          }
         }
       }
     }
@@ -262,7 +298,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   const int n_lo = cb * GN;
   if (n_lo >= Npad) return;
   const int Np = min(GN, Npad - n_lo);
-  const int stageA = GM * KB, stageB = GN * KB;
+  const int stageA = BF16 ? GSTAGE_BF16 : GM * KB, stageB = BF16 ? GSTAGE_BF16 : GN * KB;
+  const bool amn = BF16 && operand_mn(P.A, m0, GM), bmn = BF16 && operand_mn(P.B, n_lo, Np);
   unsigned char* sA[2] = {smem, smem + stageA + stageB};
   unsigned char* sB[2] = {smem + stageA, smem + 2 * stageA + stageB};
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (stageA + stageB));
@@ -282,7 +319,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *slot;
-  const uint32_t id = tc::idesc(GM, Np, BF16 ? 1u : 2u);
+  const uint32_t id = tc::idesc(GM, Np, BF16 ? 1u : 2u) | (amn ? 1u << 15 : 0u) | (bmn ? 1u << 16 : 0u);
   const int nk = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
   bool ok = true;
   for (int ks = 0; ks < nk; ++ks) {
@@ -292,8 +329,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
       break;
     }
     const int k0 = kbeg + ks * GK;
-    fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t);
-    fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t);
+    fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+    fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
     fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -301,8 +338,8 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
     if (t == 0) {
 #pragma unroll
       for (int kk = 0; kk < KB / 32; ++kk) {
-        const uint64_t a = tc::smem_desc(smem_u32(sA[st]) + kk * 256, 128, KB / 16 * 128);
-        const uint64_t b = tc::smem_desc(smem_u32(sB[st]) + kk * 256, 128, KB / 16 * 128);
+        const uint64_t a = tc::smem_desc(smem_u32(sA[st]) + kk * 256, 128, amn ? MN_SBO : KB / 16 * 128);
+        const uint64_t b = tc::smem_desc(smem_u32(sB[st]) + kk * 256, 128, bmn ? MN_SBO : KB / 16 * 128);
         if (BF16) tc::mma_bf16(tmem, a, b, id, (ks > 0 || kk > 0) ? 1u : 0u);
         else tc::mma_tf32(tmem, a, b, id, (ks > 0 || kk > 0) ? 1u : 0u);
       }
@@ -384,7 +421,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
 
 int gemm_smem_bytes(bool bf16) {
   const int EL = bf16 ? 2 : 4;
-  return 2 * (GM * GK * EL + GN * GK * EL) + 64;
+  return bf16 ? 2 * (2 * GSTAGE_BF16) + 64 : 2 * (GM * GK * EL + GN * GK * EL) + 64;
 }
 
 cudaError_t launch_gemm(const GemmLaunch& L, int n_prob, int max_m, int splits, bool bf16,
