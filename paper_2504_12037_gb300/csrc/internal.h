@@ -378,7 +378,7 @@ namespace tnvan {
 
 // Kernel launchers (defined in the .cu files).  All return a cudaError_t.
 enum { PACK_FLAT = 1, PACK_TILES = 2, PACK_SIMT = 4, PACK_TC = 8, PACK_TCG = 16 };
-long long pack_elems(const MadeDev& md, int mask);
+__host__ __device__ long long pack_elems(const MadeDev& md, int mask);
 cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s);
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);

@@ -1,4 +1,6 @@
 // MADE network kernels: parameter packing and ancestral sampling (Eq. 6-8).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tnvan {
@@ -63,9 +65,7 @@ __device__ __forceinline__ void store_tile(const MadeDev& md, int l, int r, int 
 //              plan, or all, per pack_tc_plan)
 //   PACK_TC    the per-step tensor-core sampler plans' BF16 chunk weight
 //              blobs and FP32 in-step weight tables (likewise)
-__global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
-  const MadeDev& md = inst[blockIdx.y].made;
-  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void pack_one(const MadeDev& md, int mask, long long e) {
   const bool tiles = (mask & PACK_TILES) && md.wtiles && md.n_layers == 3;
   if (mask & PACK_FLAT) {
     if (e < md.n_params) {
@@ -153,7 +153,15 @@ __global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
   }
 }
 
-long long pack_elems(const MadeDev& md, int mask) {
+// One instance per grid row; the row's threads stride over its elements.
+__global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
+  const MadeDev& md = inst[blockIdx.y].made;
+  const long long n = pack_elems(md, mask);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    pack_one(md, mask, e);
+}
+
+__host__ __device__ long long pack_elems(const MadeDev& md, int mask) {
   long long n = 0;
   const bool tiles = (mask & PACK_TILES) && md.wtiles && md.n_layers == 3;
   if (mask & PACK_FLAT) n += md.n_params;
@@ -174,7 +182,9 @@ long long pack_elems(const MadeDev& md, int mask) {
 
 cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s) {
   if (n_inst == 0 || max_total == 0) return cudaSuccess;
-  pack_all_kernel<<<dim3((unsigned)((max_total + 255) / 256), n_inst), 256, 0, s>>>(d_inst, mask);
+  // about eight CTAs per SM in all (152 SMs), at least one per instance
+  const long long need = (max_total + 255) / 256, cap = std::max(1, 1216 / n_inst);
+  pack_all_kernel<<<dim3((unsigned)std::min(need, cap), n_inst), 256, 0, s>>>(d_inst, mask);
   return cudaGetLastError();
 }
 
