@@ -1200,8 +1200,8 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
                 fused_bwd_smem_bytes(D, H[0], H[1]) <= 227 * 1024;
   md.sample_tc_ok = 0;  // decided once the step groups are known
   md.wtiles = nullptr;
-  if (md.fused_ok || (n_hidden == 2 && D % 16 == 0 && H[0] % 16 == 0 && H[1] % 16 == 0 && D <= 128 &&
-                      H[0] <= 128 && H[1] <= 128)) {
+  if (md.fused_ok || (n_hidden == 2 && H[0] % 16 == 0 && H[1] % 16 == 0 && Dp16 <= 128 && H[0] <= 128 &&
+                      H[1] <= 128)) {
     void* wt = nullptr;
     const size_t n = (size_t)H[0] * Dp16 + (size_t)H[1] * H[0] + (size_t)Dp16 * H[1];
     cudaError_t e2 = cudaMalloc(&wt, n * sizeof(uint16_t));

@@ -84,7 +84,10 @@ struct SampleTcgLayout {
   int wbytes, oS, oH1, oH2, oBuf, buf, oBar, total;
 };
 
+// D is padded to a multiple of 16 (the weight tiles' padding: zero rows and
+// columns, spins beyond D never drawn).
 __host__ __device__ inline SampleTcgLayout sample_tcg_layout(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
+  D = (D + 15) & ~15;
   SampleTcgLayout L;
   L.wbytes = 2 * (H1 * D + H2 * H1 + D * H2);
   int p = (L.wbytes + 127) & ~127;
@@ -249,6 +252,7 @@ __device__ __forceinline__ void slot_group(const int* G, const float* TWb, int g
 }
 
 __host__ __device__ inline int sample_tcg_tmem_cols(int D, int H2, int tcw1) {
+  D = (D + 15) & ~15;
   return tcw1 + H2 + D <= 256 ? 256 : 512;
 }
 
@@ -268,7 +272,8 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   const bool valid = b < li.batch;
   const SampleTcgLayout LY = sample_tcg_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax);
   unsigned char* sW1 = smem;
-  unsigned char* sW2 = sW1 + 2 * H1 * D;
+  const int Dp = (D + 15) & ~15;  // the tiles' padded width set
+  unsigned char* sW2 = sW1 + 2 * H1 * Dp;
   unsigned char* sWo = sW2 + 2 * H2 * H1;
   unsigned char* sS = smem + LY.oS;
   unsigned char* sH1 = smem + LY.oH1;
@@ -278,12 +283,12 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + LY.oBar);  // MMA completion
   uint64_t* cbar = bar + 1;                                     // bulk copies
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
-  const uint32_t sboS = mn_sbo(D), sbo1 = mn_sbo(P.tcw1), sbo2 = mn_sbo(P.tcw2);
+  const uint32_t sboS = mn_sbo(Dp), sbo1 = mn_sbo(P.tcw1), sbo2 = mn_sbo(P.tcw2);
   // this thread's row in the MN-major tiles: element k at row base + 16 k
   const uint32_t rowb = (uint32_t)(t & 7) * 2u;
   const uint32_t rbS = (uint32_t)(t >> 3) * sboS + rowb, rb1 = (uint32_t)(t >> 3) * sbo1 + rowb,
                  rb2 = (uint32_t)(t >> 3) * sbo2 + rowb;
-  const uint32_t kbW1 = 2u * D / 16u * 128u, kbW2 = 2u * H1 / 16u * 128u, kbWo = 2u * H2 / 16u * 128u;
+  const uint32_t kbW1 = 2u * Dp / 16u * 128u, kbW2 = 2u * H1 / 16u * 128u, kbWo = 2u * H2 / 16u * 128u;
   const int ncols = sample_tcg_tmem_cols(D, H2, P.tcw1);
   if (t == 0) {
     mbar_init(bar, 1);
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   const uint32_t lane_off = (uint32_t)(w * 32) << 16;
   const uint32_t tP1 = tmem + lane_off, tP2 = tP1 + (uint32_t)P.tcw1, tPO = tP2 + (uint32_t)H2;
   const uint32_t idA = 1u << 15;  // A operand MN-major
-  const uint32_t id2 = tc::idesc(128, H2, 1u) | idA, ido = tc::idesc(128, D, 1u) | idA;
+  const uint32_t id2 = tc::idesc(128, H2, 1u) | idA, ido = tc::idesc(128, Dp, 1u) | idA;
   const uint2 key = make_uint2((uint32_t)li.seed, (uint32_t)(li.seed >> 32));
   const uint32_t step32 = launch_step(li);
   const int8_t* gv = given ? given + I.spin_units * li.batch + (long long)b * D : nullptr;

@@ -30,10 +30,11 @@ def _workload(cfg):
     return wl.workload(cfg, n_instances=10) if cfg == 5 else wl.workload(cfg)
 
 
-# plan values: the grouped form (4, 6, 8 steps per group; workload 2's
-# shapes only) and the per-step form (12, 16, 32 steps per chunk; every shape)
+# plan values: the grouped form (4, 6, 8 steps per group; two hidden layers
+# of <= 128 units, D <= 128 padded to 16: workloads 2 and 4) and the per-step
+# form (12, 16, 32 steps per chunk; every shape)
 @pytest.mark.parametrize("cfg,chunk", [(c, v) for c in (1, 2, 3, 4, 5) for v in (12, 16, 32)] +
-                         [(2, 4), (2, 6), (2, 8)])
+                         [(2, 4), (2, 6), (2, 8), (4, 4), (4, 6), (4, 8)])
 def test_tc_log_prob_matches_oracle_every_workload(cfg, chunk):
     w = _workload(cfg)
     model = _model(w)
@@ -104,9 +105,10 @@ def test_tc_sampler_one_hidden_layer_distribution():
 
 
 # grouped-form networks by in-group form (MADE hidden degrees k mod (D-1) + 1):
-# 2 slots (D = 64, H = 64), 3 (workload 2's 64-128-128), 4 (D = 32, H = 96),
-# and the per-unit form (D = 16, H = 128: up to 9 units per degree)
-GROUPED_SHAPES = [(16, 16, [64, 64], 2), (16, 16, [128, 128], 3), (16, 8, [96, 96], 4), (8, 8, [128, 128], 0)]
+# 2 slots (D = 64, H = 64), 3 (workload 2's 64-128-128), 4 (D = 32, H = 96;
+# D = 21, H = 64), and the per-unit form (D = 16, H = 128: up to 9 units per degree)
+GROUPED_SHAPES = [(16, 16, [64, 64], 2), (16, 16, [128, 128], 3), (16, 8, [96, 96], 4), (8, 8, [128, 128], 0),
+                  (14, 7, [64, 64], 4)]  # the last: D = 21, padded to 32
 
 
 @pytest.mark.parametrize("plan", [4, 6, 8])
