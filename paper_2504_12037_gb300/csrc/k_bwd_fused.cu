@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     for (int c = 16 * g; c < Dp; c += 32) {
       float sp[16];
       uint32_t m16 = 0;
-      if ((D & 15) == 0) {  // 16 spins per vector load
+      if ((D & 15) == 0 && (reinterpret_cast<uintptr_t>(Sg) & 15) == 0) {  // 16 spins per vector load
         uint4 raw = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
         if (valid) raw = *reinterpret_cast<const uint4*>(Sg + (long long)b * D + c);
         const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};

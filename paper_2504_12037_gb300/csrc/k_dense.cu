@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const InstDev* __restr
     float e1 = 0.f;
     if (DMAX > 0) {
       unsigned long long m = 0ull;  // bit w: spin w is +1
-      if ((D & 15) == 0) {
+      if ((D & 15) == 0 && (reinterpret_cast<uintptr_t>(spins + I.spin_units * li.batch) & 15) == 0) {
         for (int c = 0; c < D; c += 16) {
           const uint4 raw = *reinterpret_cast<const uint4*>(st + c);
           const uint32_t wv[4] = {raw.x, raw.y, raw.z, raw.w};

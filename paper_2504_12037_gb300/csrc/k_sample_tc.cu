@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(128, 2) sample_tc_kernel(const InstDev* __rest
   if (ok && valid) {
     if (spins) {  // the drawn spins, from the spin tile
       int8_t* out = spins + I.spin_units * li.batch + (long long)b * D;
-      if ((D & 3) == 0) {
+      if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 3) == 0) {
         for (int i = 0; i < D; i += 4) {
           uint32_t v = 0;
 #pragma unroll

@@ -609,16 +609,18 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   }
   if (ok && valid) {
     if (spins) {
-      uint32_t* out = reinterpret_cast<uint32_t*>(spins + I.spin_units * li.batch + (long long)b * D);
-      for (int i = 0; i < D; i += 4) {
-        uint32_t v = 0;
+      int8_t* row = spins + I.spin_units * li.batch + (long long)b * D;
+      auto up_at = [&](int ii) { return ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0; };
+      if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 3) == 0) {  // four spins per store
+        uint32_t* out = reinterpret_cast<uint32_t*>(row);
+        for (int i = 0; i < D; i += 4) {
+          uint32_t v = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int ii = i + j;
-          const bool up = ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0;
-          v |= (up ? 0x01u : 0xFFu) << (8 * j);
+          for (int j = 0; j < 4; ++j) v |= (up_at(i + j) ? 0x01u : 0xFFu) << (8 * j);
+          out[i >> 2] = v;
         }
-        out[i >> 2] = v;
+      } else {  // rows of other lengths or offsets: one byte per spin, none past the row
+        for (int i = 0; i < D; ++i) row[i] = up_at(i) ? 1 : -1;
       }
     }
     logq[(long long)k * li.batch + b] = lq;
