@@ -1195,8 +1195,12 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   md.n_params = off;
   if (off >= (1LL << 30)) return fail(ctx, TNVAN_E_UNSUPPORTED, "network too large (%lld parameters)", off);
   const int Dp16 = (D + 15) & ~15;  // the fused backward pads D to a multiple of 16
+  // TMEM of the fused kernel: 128 scratch columns, then the weight-gradient
+  // accumulators [S | 1], [A1 | 1], [A2 | 1] (the ones column of S sits in
+  // its padding when D is not a multiple of 16)
+  const int g1n = (D % 16) ? Dp16 : Dp16 + 16;
   md.fused_ok = n_hidden == 2 && H[0] % 16 == 0 && H[1] % 16 == 0 && Dp16 <= 128 && H[0] <= 128 &&
-                H[1] <= 128 && 128 + (Dp16 + 16) + (H[0] + 16) + (H[1] + 16) <= 512 &&
+                H[1] <= 128 && 128 + g1n + (H[0] + 16) + (H[1] + 16) <= 512 &&
                 fused_bwd_smem_bytes(D, H[0], H[1]) <= 227 * 1024;
   md.sample_tc_ok = 0;  // decided once the step groups are known
   md.wtiles = nullptr;

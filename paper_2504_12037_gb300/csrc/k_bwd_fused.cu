@@ -162,14 +162,18 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   }
   const bool weights_ok = mbar_wait(cbar, 0);
   const uint32_t tmem = *slot;
-  const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)(Dp + 16), tGo = tG2 + (uint32_t)(H1 + 16);
+  // the ones column of [S | 1] (layer-1 bias gradient): inside the padding at
+  // column D when D is not a multiple of 16 (W1's padded columns are zero, so
+  // the forward product ignores it), else a 16-column block of its own at Dp
+  const int oc1 = (D & 15) ? D : Dp, g1n = (D & 15) ? Dp : Dp + 16;
+  const uint32_t tScr = tmem, tG1 = tmem + 128, tG2 = tG1 + (uint32_t)g1n, tGo = tG2 + (uint32_t)(H1 + 16);
   const uint32_t lane_off = (uint32_t)((w & 3) * 32) << 16;
   const uint32_t id_fwd1 = tc::idesc(128, H1, 1u), id_fwd2 = tc::idesc(128, H2, 1u), id_fwd3 = tc::idesc(128, Dp, 1u);
   const uint32_t id_d2 = tc::idesc(128, H2, 1u) | (1u << 16);         // B MN-major
   const uint32_t id_d1 = tc::idesc(128, H1, 1u) | (1u << 16);
   const uint32_t id_go = tc::idesc(128, H2 + 16, 1u) | (1u << 15) | (1u << 16);  // A, B MN-major
   const uint32_t id_g2 = tc::idesc(128, H1 + 16, 1u) | (1u << 15) | (1u << 16);
-  const uint32_t id_g1 = tc::idesc(128, Dp + 16, 1u) | (1u << 15) | (1u << 16);
+  const uint32_t id_g1 = tc::idesc(128, g1n, 1u) | (1u << 15) | (1u << 16);
   const double mean = args.stats[8 * k + 4];
   const double wsc = -1.0 / (li.beta[k] * stats_batch(args.stats + 8 * k));
   const int8_t* Sg = args.spins + I.spin_units * (long long)B;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
         for (int i = 0; i < 16; ++i) {
           const int f = c + i;
           const int8_t sv = (valid && f < D) ? Sg[(long long)b * D + f] : (int8_t)0;
-          sp[i] = (float)sv;
+          sp[i] = f == oc1 ? vf : (float)sv;  // oc1 < Dp only when D is not a multiple of 16
           m16 |= (sv > 0 ? 1u : 0u) << i;
         }
       }
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
       store8(sS, tS.rowbytes(), t, c, sp);
       store8(sS, tS.rowbytes(), t, c + 8, sp + 8);
     }
-    if (((Dp >> 4) & 1) == g) {
+    if (oc1 == Dp && ((Dp >> 4) & 1) == g) {
       float sp[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) sp[i] = i == 0 ? vf : 0.f;
@@ -341,12 +345,14 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   if (ok && !first) {
     // ncol: the accumulator's input columns (a multiple of 16; the bias
     // column follows), nin <= ncol of them real
-    auto flush = [&](uint32_t tacc, int nin, int ncol, int nout, long long off) {
-      for (int c = 16 * g; c < ncol + 16; c += 32) {
+    // accumulator columns [0, ncols): the nin weight-gradient columns, and
+    // the bias gradient at column bcol
+    auto flush = [&](uint32_t tacc, int nin, int ncols, int bcol, int nout, long long off) {
+      for (int c = 16 * g; c < ncols; c += 32) {
         float v[16];
         tc::tmem_ld16(tacc + lane_off + (uint32_t)c, v);
         if (t < nout) {
-          if (c < ncol) {
+          if (c < nin) {
             float* row = G + off + (long long)t * nin + c;
             if ((nin & 3) == 0 && c + 16 <= nin) {
               float4* row4 = reinterpret_cast<float4*>(row);
@@ -357,15 +363,19 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
               for (int q = 0; q < 16; ++q)
                 if (c + q < nin) row[q] = v[q];
             }
-          } else {
-            G[off + (long long)nout * nin + t] = v[0];  // c == ncol: the bias column
+          }
+          if (bcol >= c && bcol < c + 16) {
+            float bv = v[0];
+#pragma unroll
+            for (int q = 1; q < 16; ++q) bv = q == bcol - c ? v[q] : bv;
+            G[off + (long long)nout * nin + t] = bv;
           }
         }
       }
     };
-    flush(tG1, D, Dp, H1, md.layer[0].dst_off);
-    flush(tG2, H1, H1, H2, md.layer[1].dst_off);
-    flush(tGo, H2, H2, D, md.layer[2].dst_off);
+    flush(tG1, D, g1n, oc1, H1, md.layer[0].dst_off);
+    flush(tG2, H1, H1 + 16, H1, H2, md.layer[1].dst_off);
+    flush(tGo, H2, H2 + 16, H2, D, md.layer[2].dst_off);
   } else {
     for (long long e = tid; e < md.n_params; e += 256) G[e] = 0.f;
   }
