@@ -93,8 +93,9 @@ __device__ __forceinline__ bool operand_mn(const GemmOperand& op, int r0, int nr
 // Loads are issued in batches (registers first, stores after) so that each
 // thread keeps many global loads in flight; FP32 operands whose contiguous
 // index is k (or the row) are read as float4.
+// Out of line: both operands share one copy of the paths (instruction cache).
 template <bool BF16>
-__device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
+__device__ __noinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
                                            int r0, int rlim, int k0, int klim, int ones_row, int t, bool mn) {
   const bool full_k = k0 + GK <= klim;
   const bool f32 = op.type == GT_F32;
@@ -282,7 +283,8 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
   }
 }
 
-template <bool BF16>
+// EPI: the epilogue of every problem of the launch (one compiled per case).
+template <bool BF16, int EPI>
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int EL = BF16 ? 2 : 4;
@@ -379,11 +381,11 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
         a[j] = stg[r * 17 + cc];
         in[j] = 0.f;
         if (ok_r[j] && ncol) {
-          if (P.epi == EPI_MASK) in[j] = P.mask[(long long)m * P.ld_mask + n];
-          else if (P.epi == EPI_DX) in[j] = (float)P.spins[(long long)m * P.ld_spins + n];
+          if (EPI == EPI_MASK) in[j] = P.mask[(long long)m * P.ld_mask + n];
+          else if (EPI == EPI_DX) in[j] = (float)P.spins[(long long)m * P.ld_spins + n];
         }
       }
-      const float bn = (ncol && (P.epi == EPI_BIAS_RELU || P.epi == EPI_DX)) ? P.bias[n] : 0.f;
+      const float bn = (ncol && (EPI == EPI_BIAS_RELU || EPI == EPI_DX)) ? P.bias[n] : 0.f;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int m = m0 + w * 32 + 2 * j + (lane >> 4);
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
         }
         if (!ncol) continue;
         const long long o = (long long)m * P.ldc + n;
-        switch (P.epi) {
+        switch (EPI) {
           case EPI_STORE:
             P.C[(long long)blockIdx.z * P.split_stride + o] = a[j];
             break;
@@ -437,16 +439,25 @@ cudaError_t launch_gemm(const GemmLaunch& L, int n_prob, int max_m, int splits, 
   GemmLaunch Lm = L;
   Lm.ncb = (max_np + GN - 1) / GN;
   dim3 grid(((max_m + GM - 1) / GM) * Lm.ncb, n_prob, splits);
-  cudaError_t e;
-  if (bf16) {
-    e = cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    gemm_tc_kernel<true><<<grid, 128, smem, s>>>(Lm);
-  } else {
-    e = cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    gemm_tc_kernel<false><<<grid, 128, smem, s>>>(Lm);
-  }
+  const int epi = L.prob[0].epi;
+  for (int i = 1; i < n_prob; ++i)
+    if (L.prob[i].epi != epi) return cudaErrorInvalidValue;  // one epilogue per launch
+  void (*kern)(const GemmLaunch) = nullptr;
+#define TNVAN_GEMM_KERN(B, E) \
+  if (bf16 == B && epi == E) kern = gemm_tc_kernel<B, E>;
+  TNVAN_GEMM_KERN(true, EPI_STORE)
+  TNVAN_GEMM_KERN(true, EPI_BIAS_RELU)
+  TNVAN_GEMM_KERN(true, EPI_DX)
+  TNVAN_GEMM_KERN(true, EPI_MASK)
+  TNVAN_GEMM_KERN(false, EPI_STORE)
+  TNVAN_GEMM_KERN(false, EPI_BIAS_RELU)
+  TNVAN_GEMM_KERN(false, EPI_DX)
+  TNVAN_GEMM_KERN(false, EPI_MASK)
+#undef TNVAN_GEMM_KERN
+  if (!kern) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 128, smem, s>>>(Lm);
   return cudaGetLastError();
 }
 
