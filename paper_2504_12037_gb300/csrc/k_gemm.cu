@@ -93,9 +93,8 @@ __device__ __forceinline__ bool operand_mn(const GemmOperand& op, int r0, int nr
 // Loads are issued in batches (registers first, stores after) so that each
 // thread keeps many global loads in flight; FP32 operands whose contiguous
 // index is k (or the row) are read as float4.
-// Out of line: both operands share one copy of the paths (instruction cache).
 template <bool BF16>
-__device__ __noinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
+__device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
                                            int r0, int rlim, int k0, int klim, int ones_row, int t, bool mn) {
   const bool full_k = k0 + GK <= klim;
   const bool f32 = op.type == GT_F32;
@@ -283,6 +282,14 @@ __device__ __noinline__ void fill_stage(unsigned char* s, int nrows, const GemmO
   }
 }
 
+// Out of line: both operands share one copy of the paths, which keeps the
+// kernels with the larger epilogues within the instruction cache.
+template <bool BF16>
+__device__ __noinline__ void fill_stage_call(unsigned char* s, int nrows, const GemmOperand& op, int r0, int rlim,
+                                             int k0, int klim, int ones_row, int t, bool mn) {
+  fill_stage<BF16>(s, nrows, op, r0, rlim, k0, klim, ones_row, t, mn);
+}
+
 // EPI: the epilogue of every problem of the launch (one compiled per case).
 template <bool BF16, int EPI>
 __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
@@ -331,8 +338,13 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
       break;
     }
     const int k0 = kbeg + ks * GK;
-    fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
-    fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
+    if (EPI == EPI_STORE) {  // the weight gradients: many K stages, a short epilogue
+      fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
+    } else {
+      fill_stage_call<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      fill_stage_call<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
+    }
     fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
