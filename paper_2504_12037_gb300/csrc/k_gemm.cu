@@ -93,10 +93,9 @@ __device__ __forceinline__ bool operand_mn(const GemmOperand& op, int r0, int nr
 // Loads are issued in batches (registers first, stores after) so that each
 // thread keeps many global loads in flight; FP32 operands whose contiguous
 // index is k (or the row) are read as float4.
-template <bool BF16, int NTH>
+template <bool BF16>
 __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const GemmOperand& op,
                                            int r0, int rlim, int k0, int klim, int ones_row, int t, bool mn) {
-  constexpr int NB = 8 * 128 / NTH;  // units per thread and batch (one batch covers 128 rows x GK)
   const bool full_k = k0 + GK <= klim;
   const bool f32 = op.type == GT_F32;
   const bool aligned = ((reinterpret_cast<uintptr_t>(op.ptr) & 15) == 0);
@@ -104,11 +103,11 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
     // row-major along k: units of (row, 4 k)
     const float* p = static_cast<const float*>(op.ptr);
     const int units = nrows * (GK / 4);
-    for (int u0 = 0; u0 < units; u0 += NTH * NB) {
-      float4 v[NB];
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      float4 v[8];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         const int r = u >> 3, kq = (u & 7) * 4;
         const int gr = r0 + r;
         v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -119,8 +118,8 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
         }
       }
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         if (u < units) st4k<BF16>(s, u >> 3, (u & 7) * 4, v[j]);
       }
     }
@@ -131,11 +130,11 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
     const float* p = static_cast<const float*>(op.ptr);
     const int rq = nrows / 4;
     const int units = rq * GK;
-    for (int u0 = 0; u0 < units; u0 += NTH * NB) {
-      float4 v[NB];
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      float4 v[8];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         const int r = (u % rq) * 4, k = u / rq;
         const int gr = r0 + r, gk = k0 + k;
         v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -154,8 +153,8 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
         }
       }
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         if (u < units) {
           const int r = (u % rq) * 4, k = u / rq;
           if (BF16 && mn) {
@@ -177,11 +176,11 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
     // int8 rows along k (spins): units of (row, 4 k), four bytes per load
     const int8_t* p = static_cast<const int8_t*>(op.ptr);
     const int units = nrows * (GK / 4);
-    for (int u0 = 0; u0 < units; u0 += NTH * NB) {
-      char4 c[NB];
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      char4 c[8];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         const int gr = r0 + (u >> 3), kq = (u & 7) * 4;
         c[j] = make_char4(0, 0, 0, 0);
         if (u < units && gr != ones_row && gr < rlim)
@@ -189,8 +188,8 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
         if (u < units && gr == ones_row) c[j] = make_char4(1, 1, 1, 1);
       }
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         if (u < units)
           st4k<BF16>(s, u >> 3, (u & 7) * 4, make_float4((float)c[j].x, (float)c[j].y, (float)c[j].z, (float)c[j].w));
       }
@@ -202,11 +201,11 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
     const int8_t* p = static_cast<const int8_t*>(op.ptr);
     const int rq = nrows / 4;
     const int units = rq * GK;
-    for (int u0 = 0; u0 < units; u0 += NTH * NB) {
-      char4 c[NB];
+    for (int u0 = 0; u0 < units; u0 += 128 * 8) {
+      char4 c[8];
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         const int gr = r0 + (u % rq) * 4, gk = k0 + u / rq;
         c[j] = make_char4(0, 0, 0, 0);
         if (u < units && gk < klim) {
@@ -223,8 +222,8 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
         }
       }
 #pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        const int u = u0 + t + NTH * j;
+      for (int j = 0; j < 8; ++j) {
+        const int u = u0 + t + 128 * j;
         if (u < units) {
           const int r = (u % rq) * 4, k = u / rq;
           if (BF16 && mn) {
@@ -243,11 +242,11 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
   // generic: element by element, loads batched 16 at a time
   const bool kfast = op.sk == 1;
   const int total = nrows * GK;
-  for (int e0 = 0; e0 < total; e0 += NTH * 16) {
+  for (int e0 = 0; e0 < total; e0 += 128 * 16) {
     float v[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const int e = e0 + t + NTH * j;
+      const int e = e0 + t + 128 * j;
       int r, k;
       if (kfast) {
         r = e / GK;
@@ -267,7 +266,7 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const int e = e0 + t + NTH * j;
+      const int e = e0 + t + 128 * j;
       if (e < total) {
         int r, k;
         if (kfast) {
@@ -288,7 +287,7 @@ __device__ __forceinline__ void fill_stage(unsigned char* s, int nrows, const Ge
 template <bool BF16>
 __device__ __noinline__ void fill_stage_call(unsigned char* s, int nrows, const GemmOperand& op, int r0, int rlim,
                                              int k0, int klim, int ones_row, int t, bool mn) {
-  fill_stage<BF16, 64>(s, nrows, op, r0, rlim, k0, klim, ones_row, t, mn);
+  fill_stage<BF16>(s, nrows, op, r0, rlim, k0, klim, ones_row, t, mn);
 }
 
 // EPI: the epilogue of every problem of the launch (one compiled per case).
@@ -339,14 +338,12 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
       break;
     }
     const int k0 = kbeg + ks * GK;
-    // warps 0-1 stage A, warps 2-3 stage B: both operands' loads in flight at once
-    const bool fa = t < 64;
     if (EPI == EPI_STORE) {  // the weight gradients: many K stages, a short epilogue
-      if (fa) fill_stage<BF16, 64>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
-      else fill_stage<BF16, 64>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t - 64, bmn);
+      fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
     } else {
-      if (fa) fill_stage_call<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
-      else fill_stage_call<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t - 64, bmn);
+      fill_stage_call<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      fill_stage_call<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
     }
     fence_proxy_async_smem();
     tc::fence_before_sync();
