@@ -171,7 +171,10 @@ int tnvan_n_params(const tnvan_ctx* ctx, int instance, int64_t* n_params, int64_
  * tables' space reused (forward passes), [10] the grouped BF16 sampler's
  * in-group form (-1 not eligible or no network, 0 per unit, 2-4 slots per
  * layer and step: the register form), [11] 1 if the fused BF16 backward takes
- * the instance.  info: host array [12]. */
+ * the instance, [12] 1 if the grouped sampler streams the instance's weights
+ * per step group (width sets of 129 to 256 spins, or tiles too large to stay
+ * in shared memory), 0 if they stay resident, -1 not eligible.  info: host
+ * array [13]. */
 int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info);
 
 /* Pre-allocate the context's internal workspaces for batches up to

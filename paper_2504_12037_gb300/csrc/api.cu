@@ -1457,7 +1457,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
     MadeDev::TcGroupPlan& P = md.tcg[p];
     P = MadeDev::TcGroupPlan{};
-    if (!md.wtiles || n_hidden != 2) continue;
+    if (n_hidden != 2 || H[0] % 16 || H[1] % 16 || H[0] > 128 || H[1] > 128 || ((D + 15) & ~15) > 256) continue;
     const int GMAX = kTcGroupMaxG[p], UGMAX = 32;
     auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
     auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };
@@ -1550,6 +1550,46 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       grp.insert(grp.end(), rec, rec + TNVAN_TCGG_INTS);
       i0 = i1;
     }
+    // the weight tiles resident in shared memory (D <= 128 and room for
+    // them), else one streamed blob per group: the W2 window [H2 x n1] (the
+    // fold of the group's layer-1 units), the Wo window [Dp x n2] (its
+    // layer-2 units) and W1's rows of its layer-1 units [n1 x r16(i0)] (their
+    // pre-activations, recomputed at the end of the group before), each in the
+    // MMA's K-major canonical layout; record word 31 = the blob's offset
+    const bool resident = md.wtiles != nullptr && D <= 128 &&
+                          sample_tcg_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
+    std::vector<int> wsrc;
+    int wbmax = 0;
+    if (!resident) {
+      const int Dpg = (D + 15) & ~15;
+      const long long o0 = md.layer[0].dst_off, o1 = md.layer[1].dst_off, o2 = md.layer[2].dst_off;
+      auto kmaj = [](int r, int c, int kw) {
+        return (size_t)(r >> 3) * (size_t)(kw / 8) * 64 + (size_t)(c >> 3) * 64 + (size_t)(r & 7) * 8 + (size_t)(c & 7);
+      };
+      const int ng = (int)grp.size() / TNVAN_TCGG_INTS;
+      for (int g = 0; g < ng; ++g) {
+        int* Gr = grp.data() + (size_t)g * TNVAN_TCGG_INTS;
+        const int gi0 = Gr[0], u1lo = Gr[2], u1hi = Gr[3], u2lo = Gr[4], u2hi = Gr[5];
+        // the fold windows as the kernel forms them
+        const int w1 = u1lo & ~15, n1 = ((u1hi + 15) & ~15) - w1;
+        const int w2 = u2lo & ~15, n2 = ((u2hi + 15) & ~15) - w2;
+        const int kS = (gi0 + 15) & ~15;
+        const size_t base = wsrc.size();
+        Gr[31] = (int)base;
+        const size_t nA = (size_t)H[1] * n1, nB = (size_t)Dpg * n2, nC = (size_t)n1 * kS;
+        wsrc.resize(base + nA + nB + nC, -1);
+        for (int v = 0; v < H[1]; ++v)
+          for (int c = 0; c < n1; ++c)
+            if (w1 + c < H[0]) wsrc[base + kmaj(v, c, n1)] = (int)(o1 + (long long)v * H[0] + w1 + c);
+        for (int i = 0; i < D; ++i)
+          for (int c = 0; c < n2; ++c)
+            if (w2 + c < H[1]) wsrc[base + nA + kmaj(i, c, n2)] = (int)(o2 + (long long)i * H[1] + w2 + c);
+        for (int r = 0; r < n1; ++r)
+          for (int kk = 0; kk < kS && kk < D; ++kk)
+            if (w1 + r < H[0]) wsrc[base + nA + nB + kmaj(r, kk, kS)] = (int)(o0 + (long long)(w1 + r) * D + kk);
+        wbmax = std::max(wbmax, (int)(2 * (nA + nB + nC)));
+      }
+    }
     int* dgrp = nullptr;
     if ((rc = upload(ctx, in, grp, &dgrp))) return rc;
     int* dsrc = nullptr;
@@ -1560,6 +1600,19 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler triangles): %s", cudaGetErrorString(e2));
       in.dev_allocs.push_back(blk);
     }
+    P.streamed = resident ? 0 : 1;
+    P.wbmax = wbmax;
+    if (!resident && !wsrc.empty()) {
+      int* dws = nullptr;
+      if ((rc = upload(ctx, in, wsrc, &dws))) return rc;
+      void* wb = nullptr;
+      cudaError_t e2 = cudaMalloc(&wb, wsrc.size() * sizeof(uint16_t));
+      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blobs): %s", cudaGetErrorString(e2));
+      in.dev_allocs.push_back(wb);
+      P.wsrc = dws;
+      P.wblob = static_cast<uint16_t*>(wb);
+      P.n_wblob = (long long)wsrc.size();
+    }
     P.n_groups = (int)grp.size() / TNVAN_TCGG_INTS;
     P.groups = dgrp;
     P.blocks = static_cast<float*>(blk);
@@ -1568,7 +1621,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     P.twmax = twmax;
     P.tcw1 = tcw1;
     P.tcw2 = tcw2;
-    P.ok = fits && D <= 128 && sample_tcg_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax) <= 227 * 1024;
+    P.ok = fits && (resident || sample_tcg_smem_bytes(D, H[0], H[1], tcw1, tcw2, twmax, wbmax) <= 227 * 1024);
   }
   md.sample_tcg_ok = 0;
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tcg_ok = md.sample_tcg_ok || md.tcg[p].ok;
@@ -1616,6 +1669,7 @@ int tnvan_instance_info(const tnvan_ctx* ctx, int instance, int32_t* info) {
   const MadeDev& md = in.dev.made;
   info[10] = md.sample_tcg_ok ? md.tcg[TNVAN_TC_PLANS - 1].slot_u : -1;
   info[11] = md.fused_ok ? 1 : 0;
+  info[12] = md.sample_tcg_ok ? md.tcg[TNVAN_TC_PLANS - 1].streamed : -1;
   return TNVAN_OK;
 }
 
@@ -2902,7 +2956,8 @@ int tc_sampler_smem(const tnvan_ctx* ctx, int plan, bool grouped) {
   for (const Instance& in : ctx->inst) {
     if (grouped) {
       const MadeDev::TcGroupPlan& P = in.dev.made.tcg[plan];
-      smem = std::max(smem, sample_tcg_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax));
+      smem = std::max(smem, sample_tcg_smem_bytes((int)in.W.size(), in.H[0], in.H[1], P.tcw1, P.tcw2, P.twmax,
+                                                  P.streamed ? P.wbmax : 0));
     } else {
       smem = std::max(smem, sample_tc_smem_bytes(in.dev.made, plan));
     }

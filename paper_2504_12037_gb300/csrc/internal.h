@@ -102,6 +102,16 @@ struct MadeDev {
     int twmax;            // largest group (floats)
     int tcw1, tcw2;       // widest 16-aligned unit window of a group, layers 1 and 2
     int slot_u;           // 0: per-unit triangles; 1..4: slot layout, U slots per layer and step
+    // streamed weights (width sets the resident tiles do not fit: D up to 256):
+    // per group one BF16 blob in the MMA's K-major layout, bulk-copied one
+    // group ahead -- the W2 window [H2 x n1], the Wo window [Dp x n2] and W1's
+    // rows of the group's layer-1 units [n1 x r16(i0)]; record word 31 = its
+    // element offset
+    int streamed;
+    uint16_t* wblob;      // gathered from `packed` on every call
+    const int* wsrc;      // [n_wblob] index into `packed`, -1 = zero
+    long long n_wblob;
+    int wbmax;            // largest blob (bytes)
   } tcg[TNVAN_TC_PLANS];
   int sample_tcg_ok;      // eligible for the grouped sampler
   float* blocks;          // blocked weights (gathered from `packed` every call)
@@ -488,7 +498,7 @@ int sample_tc_smem_bytes(const MadeDev& md, int plan);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
 cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
                               float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
-int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax);
+int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax, int wbmax = 0);
 extern const int kTcGroupMaxG[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);
 

@@ -129,6 +129,14 @@ __device__ __forceinline__ void pack_one(const MadeDev& md, int mask, long long 
         return;
       }
       e -= P.n_blk;
+      if (e < P.n_wblob) {  // streamed group blobs (BF16, round to nearest even)
+        const int j = P.wsrc[e];
+        uint32_t u = __float_as_uint(j >= 0 ? packed_value(md, j) : 0.f);
+        u += 0x7fffu + ((u >> 16) & 1u);
+        P.wblob[e] = (uint16_t)(u >> 16);
+        return;
+      }
+      e -= P.n_wblob;
     }
   }
   if (mask & PACK_TC) {
@@ -170,7 +178,7 @@ __host__ __device__ long long pack_elems(const MadeDev& md, int mask) {
   if (mask & PACK_TCG) {
     const int only = pack_tc_plan(mask);
     for (int p = 0; p < TNVAN_TC_PLANS; ++p)
-      if (only < 0 || p == only) n += md.tcg[p].n_blk;
+      if (only < 0 || p == only) n += md.tcg[p].n_blk + md.tcg[p].n_wblob;
   }
   if (mask & PACK_TC) {
     const int only = pack_tc_plan(mask);

@@ -1,11 +1,15 @@
 // BF16 ancestral sampler on tcgen05 (Eq. 6-8), grouped form, for networks
-// with two hidden layers of at most 128 units and at most 128 inputs (a
-// multiple of 16): the fast path where it applies; k_sample_tc.cu holds the
-// general per-step form.
+// with two hidden layers of at most 128 units (multiples of 16) and at most
+// 256 inputs (padded to a multiple of 16): the fast path where it applies;
+// k_sample_tc.cu holds the general per-step form.
 //
 // One CTA (128 threads, thread = sample = TMEM lane) draws 128 samples; its
 // TMEM footprint is at most 256 columns and its shared memory about 100 KB
-// for the 64-128-128-64 network, so two CTAs share an SM.  TMEM holds
+// for the 64-128-128-64 network, so two CTAs share an SM.  Width sets of more
+// than 128 spins (or weight tiles too large for shared memory) stream the
+// weights instead: each step group carries one BF16 blob (its W2 and Wo
+// windows, and W1's rows of its layer-1 units) that is bulk-copied one group
+// ahead into one of two buffers; 512 TMEM columns, one CTA per SM.  TMEM holds
 //   P1g [128 x w1]  layer-1 pre-activations of the current step group's units
 //                   from every spin before the group, recomputed per group as
 //                   S W1_g^T (S = the spin tile so far, zero beyond);
@@ -86,10 +90,13 @@ struct SampleTcgLayout {
 
 // D is padded to a multiple of 16 (the weight tiles' padding: zero rows and
 // columns, spins beyond D never drawn).
-__host__ __device__ inline SampleTcgLayout sample_tcg_layout(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
+// wbmax > 0: streamed weights, two group blobs of wbmax bytes in place of the
+// resident tiles.
+__host__ __device__ inline SampleTcgLayout sample_tcg_layout(int D, int H1, int H2, int tcw1, int tcw2, int twmax,
+                                                             int wbmax = 0) {
   D = (D + 15) & ~15;
   SampleTcgLayout L;
-  L.wbytes = 2 * (H1 * D + H2 * H1 + D * H2);
+  L.wbytes = wbmax > 0 ? 2 * ((wbmax + 127) & ~127) : 2 * (H1 * D + H2 * H1 + D * H2);
   int p = (L.wbytes + 127) & ~127;
   L.oS = p;
   p += 16 * (int)mn_sbo(D);
@@ -270,7 +277,9 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   const int t = threadIdx.x, w = t >> 5;
   const int b = (gblk - li.tile_begin[k]) * 128 + t;
   const bool valid = b < li.batch;
-  const SampleTcgLayout LY = sample_tcg_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax);
+  const bool streamed = P.streamed != 0;
+  const SampleTcgLayout LY = sample_tcg_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax, streamed ? P.wbmax : 0);
+  const uint32_t wbuf = (uint32_t)((P.wbmax + 127) & ~127);  // one streamed blob buffer
   unsigned char* sW1 = smem;
   const int Dp = (D + 15) & ~15;  // the tiles' padded width set
   unsigned char* sW2 = sW1 + 2 * H1 * Dp;
@@ -314,16 +323,32 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   bool copy_pending = false, mma_pending = false;
   // group gg's record and block into a group buffer (one thread; the caller
   // has armed cbar for `extra` more bytes)
+  // streamed blob of group gg (its record r): bytes of the W2 window, the Wo
+  // window and the W1 rows
+  auto blob_parts = [&](const int* r, uint32_t& a, uint32_t& bb, uint32_t& c) {
+    const int u1lo = r[2], u1hi = r[3], u2lo = r[4], u2hi = r[5];
+    const int n1 = ((u1hi + 15) & ~15) - (u1lo & ~15), n2 = ((u2hi + 15) & ~15) - (u2lo & ~15);
+    a = 2u * (uint32_t)(H2 * n1);
+    bb = 2u * (uint32_t)(Dp * n2);
+    c = 2u * (uint32_t)(n1 * ((r[0] + 15) & ~15));
+  };
   auto copy_group = [&](int gg, unsigned char* dst, uint32_t extra) {
     const int* Gg = P.groups + TNVAN_TCGG_INTS * gg;
     const uint32_t nb = (uint32_t)__ldg(Gg + 7) * 4u;
-    mbar_expect_tx(cbar, extra + 4u * TNVAN_TCGG_INTS + nb);
+    uint32_t wa = 0, wb = 0, wc = 0;
+    if (streamed) {
+      const int r[6] = {__ldg(Gg), 0, __ldg(Gg + 2), __ldg(Gg + 3), __ldg(Gg + 4), __ldg(Gg + 5)};
+      blob_parts(r, wa, wb, wc);
+    }
+    const uint32_t wt = wa + wb + wc;
+    mbar_expect_tx(cbar, extra + 4u * TNVAN_TCGG_INTS + nb + wt);
     bulk_g2s(dst, Gg, 4u * TNVAN_TCGG_INTS, cbar);
     if (nb) bulk_g2s(dst + 4 * TNVAN_TCGG_INTS, P.blocks + __ldg(Gg + 6), nb, cbar);
+    if (wt) bulk_g2s(smem + (gg & 1) * wbuf, P.wblob + __ldg(Gg + 31), wt, cbar);
   };
   if (t == 0) {
-    copy_group(0, gbuf0, (uint32_t)LY.wbytes);
-    bulk_g2s(sW1, md.wtiles, (uint32_t)LY.wbytes, cbar);
+    copy_group(0, gbuf0, streamed ? 0u : (uint32_t)LY.wbytes);
+    if (!streamed) bulk_g2s(sW1, md.wtiles, (uint32_t)LY.wbytes, cbar);
   }
   copy_pending = true;
   const uint32_t tmem = *slot;
@@ -529,7 +554,7 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
         for (int j = 0; j < STC_GI; ++j) sg[j] = j == q ? s : sg[j];
         if (up) {
           if (i < 64) sb0 |= 1ull << i;
-          else sb1 |= 1ull << (i - 64);
+          else if (i < 128) sb1 |= 1ull << (i - 64);  // wider rows are written from the spin tile
         }
         st_bf16(sS, rbS + 16u * (uint32_t)i, s);
         lq -= fmaxf(-s * x, 0.f) + __logf(1.f + ex);
@@ -552,7 +577,7 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
       if (i0 < 64) {
         sb0 |= gb64 << i0;
         if (i0 > 56) sb1 |= gb64 >> (64 - i0);
-      } else {
+      } else if (i0 < 128) {  // wider rows are written from the spin tile
         sb1 |= gb64 << (i0 - 64);
       }
     }
@@ -577,20 +602,32 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
       const int kS = (i1 + 15) & ~15;  // spins 0 .. i1-1 (zero beyond)
       if (t == 0) {
         const uint32_t aS = smem_u32(sS), aH1 = smem_u32(sH1), aH2 = smem_u32(sH2);
+        // the B operands: windows of the resident tiles, or this group's blob
+        // (W2 window, Wo window) and the next group's (W1 rows)
+        const uint32_t aB = smem_u32(smem + (g & 1) * wbuf), aBn = smem_u32(smem + ((g + 1) & 1) * wbuf);
+        uint32_t pa = 0, pb = 0, pc = 0, na = 0, nbn = 0, nc = 0;
+        if (streamed) {
+          blob_parts(G, pa, pb, pc);
+          blob_parts(Gn, na, nbn, nc);
+        }
         for (int kk = 0; kk < n1 / 16; ++kk)
           tc::mma_bf16(tmem + (uint32_t)P.tcw1, tc::smem_desc(aH1 + kk * 256u, 128u, sbo1),
-                       tc::smem_desc(smem_u32(sW2) + (uint32_t)((w1 >> 4) + kk) * 256u, 128u, kbW2), id2,
-                       (init2 || kk > 0) ? 1u : 0u);
+                       streamed ? tc::smem_desc(aB + (uint32_t)kk * 256u, 128u, (uint32_t)n1 * 16u)
+                                : tc::smem_desc(smem_u32(sW2) + (uint32_t)((w1 >> 4) + kk) * 256u, 128u, kbW2),
+                       id2, (init2 || kk > 0) ? 1u : 0u);
         for (int kk = 0; kk < n2 / 16; ++kk)
           tc::mma_bf16(tmem + (uint32_t)(P.tcw1 + H2), tc::smem_desc(aH2 + kk * 256u, 128u, sbo2),
-                       tc::smem_desc(smem_u32(sWo) + (uint32_t)((w2 >> 4) + kk) * 256u, 128u, kbWo), ido,
-                       (inito || kk > 0) ? 1u : 0u);
+                       streamed ? tc::smem_desc(aB + pa + (uint32_t)kk * 256u, 128u, (uint32_t)n2 * 16u)
+                                : tc::smem_desc(smem_u32(sWo) + (uint32_t)((w2 >> 4) + kk) * 256u, 128u, kbWo),
+                       ido, (inito || kk > 0) ? 1u : 0u);
         if (n1n > 0) {
           const uint32_t id1 = tc::idesc(128, n1n, 1u) | idA;
           for (int kk = 0; kk < kS / 16; ++kk)
             tc::mma_bf16(tmem,
                          tc::smem_desc(aS + kk * 256u, 128u, sboS),
-                         tc::smem_desc(smem_u32(sW1) + (uint32_t)(w1n >> 3) * kbW1 + (uint32_t)kk * 256u, 128u, kbW1),
+                         streamed ? tc::smem_desc(aBn + na + nbn + (uint32_t)kk * 256u, 128u, (uint32_t)kS * 16u)
+                                  : tc::smem_desc(smem_u32(sW1) + (uint32_t)(w1n >> 3) * kbW1 + (uint32_t)kk * 256u,
+                                                  128u, kbW1),
                          id1, kk > 0 ? 1u : 0u);
         }
         tc::mma_commit(bar);
@@ -610,7 +647,11 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   if (ok && valid) {
     if (spins) {
       int8_t* row = spins + I.spin_units * li.batch + (long long)b * D;
-      auto up_at = [&](int ii) { return ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0; };
+      // rows of more than 128 spins: from the spin tile
+      auto up_at = [&](int ii) {
+        if (D > 128) return ld_bf16(sS, rbS + 16u * (uint32_t)ii) > 0.f;
+        return ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0;
+      };
       if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 3) == 0) {  // four spins per store
         uint32_t* out = reinterpret_cast<uint32_t*>(row);
         for (int i = 0; i < D; i += 4) {
@@ -630,8 +671,8 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
   if (w == 0) tc::tmem_dealloc(tmem, (uint32_t)ncols);
 }
 
-int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax) {
-  const int need = sample_tcg_layout(D, H1, H2, tcw1, tcw2, twmax).total;
+int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax, int wbmax) {
+  const int need = sample_tcg_layout(D, H1, H2, tcw1, tcw2, twmax, wbmax).total;
   // never more resident CTAs per SM than the TMEM columns allow (228 KB of
   // shared memory per SM, 1 KB of it reserved per CTA)
   const int per_sm = sample_tcg_tmem_cols(D, H2, tcw1) <= 256 ? 2 : 1;

@@ -185,10 +185,10 @@ class Context:
         return n.value, off.value
 
     def instance_info(self, instance: int):
-        info = (ctypes.c_int32 * 12)()
+        info = (ctypes.c_int32 * 13)()
         self._check(lib().tnvan_instance_info(self._h, instance, info))
         keys = ["n_spins", "n_edges", "D", "kind", "n_components", "max_component", "max_width", "n_ww",
-                "arena", "arena_live", "tcg_slots", "fused_bwd"]
+                "arena", "arena_live", "tcg_slots", "fused_bwd", "tcg_streamed"]
         return dict(zip(keys, list(info)))
 
     def reserve(self, max_batch: int):

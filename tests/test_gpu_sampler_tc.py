@@ -31,10 +31,11 @@ def _workload(cfg):
 
 
 # plan values: the grouped form (4, 6, 8 steps per group; two hidden layers
-# of <= 128 units, D <= 128 padded to 16: workloads 2 and 4) and the per-step
-# form (12, 16, 32 steps per chunk; every shape)
+# of <= 128 units, D <= 256 padded to 16: workloads 2, 4 and 5, the last with
+# weights streamed per group for D = 144 and 256) and the per-step form (12,
+# 16, 32 steps per chunk; every shape)
 @pytest.mark.parametrize("cfg,chunk", [(c, v) for c in (1, 2, 3, 4, 5) for v in (12, 16, 32)] +
-                         [(2, 4), (2, 6), (2, 8), (4, 4), (4, 6), (4, 8)])
+                         [(c, v) for c in (2, 4, 5) for v in (4, 6, 8)])
 def test_tc_log_prob_matches_oracle_every_workload(cfg, chunk):
     w = _workload(cfg)
     model = _model(w)
@@ -106,9 +107,11 @@ def test_tc_sampler_one_hidden_layer_distribution():
 
 # grouped-form networks by in-group form (MADE hidden degrees k mod (D-1) + 1):
 # 2 slots (D = 64, H = 64), 3 (workload 2's 64-128-128), 4 (D = 32, H = 96;
-# D = 21, H = 64), and the per-unit form (D = 16, H = 128: up to 9 units per degree)
-GROUPED_SHAPES = [(16, 16, [64, 64], 2), (16, 16, [128, 128], 3), (16, 8, [96, 96], 4), (8, 8, [128, 128], 0),
-                  (14, 7, [64, 64], 4)]  # the last: D = 21, padded to 32
+# D = 21, H = 64), the per-unit form (D = 16, H = 128: up to 9 units per
+# degree), and weights streamed per step group (D = 144 and D = 256, H = 128)
+GROUPED_SHAPES = [(16, 16, [64, 64], 2, 0), (16, 16, [128, 128], 3, 0), (16, 8, [96, 96], 4, 0),
+                  (8, 8, [128, 128], 0, 0), (14, 7, [64, 64], 4, 0),  # D = 21, padded to 32
+                  (24, 24, [128, 128], 2, 1), (32, 32, [128, 128], 2, 1)]
 
 
 @pytest.mark.parametrize("plan", [4, 6, 8])
@@ -116,11 +119,12 @@ GROUPED_SHAPES = [(16, 16, [64, 64], 2), (16, 16, [128, 128], 3), (16, 8, [96, 9
 def test_tc_grouped_forms_against_oracle(shape, plan):
     from paper_2504_12037_gb300.model import TNVAN
 
-    Lx, Ly, hidden, slots = GROUPED_SHAPES[shape]
+    Lx, Ly, hidden, slots, streamed = GROUPED_SHAPES[shape]
     g = wl.lattice(Lx, Ly, "gauss", seed=31 + shape)
     W = wl.width_columns(Lx, Ly, wl.every_kth_column(Lx))
     model = TNVAN([g, g], [W, W], hidden, [0.6, 1.1], seed=4 + shape, init_scale=1.5)
-    assert model.ctx.instance_info(0)["tcg_slots"] == slots
+    info = model.ctx.instance_info(0)
+    assert info["tcg_slots"] == slots and info["tcg_streamed"] == streamed, info
     model.ctx.set_tuning((0, 0, 0, 0, plan, 0))
     D, B = len(W), 300  # three CTAs, the last one ragged
     # teacher-forced on oracle draws
