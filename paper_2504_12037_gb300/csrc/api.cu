@@ -114,6 +114,33 @@ void free_instance(Instance& in) {
   in.dev_allocs.clear();
 }
 
+// A BF16 weight blob of full.size() elements whose element e is packed
+// weight full[e] (-1: zero).  The blob is zeroed once here; the pack kernel
+// rewrites only the live elements, from the lists *src / *dst (*n_live long).
+int upload_blob(tnvan_ctx* ctx, Instance& in, const std::vector<int>& full, uint16_t** blob, const int** src,
+                const int** dst, long long* n_live) {
+  std::vector<int> s, d;
+  for (size_t e = 0; e < full.size(); ++e)
+    if (full[e] >= 0) {
+      s.push_back(full[e]);
+      d.push_back((int)e);
+    }
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(full.size(), 8) * sizeof(uint16_t);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blobs): %s", cudaGetErrorString(e));
+  in.dev_allocs.push_back(p);
+  if ((e = cudaMemset(p, 0, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset (sampler blobs)");
+  int rc;
+  int *ds = nullptr, *dd = nullptr;
+  if ((rc = upload(ctx, in, s, &ds)) || (rc = upload(ctx, in, d, &dd))) return rc;
+  *blob = static_cast<uint16_t*>(p);
+  *src = ds;
+  *dst = dd;
+  *n_live = (long long)s.size();
+  return TNVAN_OK;
+}
+
 // Drop the device plan + network of an instance (keeps the graph).
 void reset_plan(Instance& in) {
   free_instance(in);
@@ -662,6 +689,9 @@ bool tc_sampler_usable(const tnvan_ctx* ctx);
 bool tc_grouped_usable(const tnvan_ctx* ctx);
 int tc_plan_value(const tnvan_ctx* ctx, int p);
 int tc_sampler_smem(const tnvan_ctx* ctx, int plan, bool grouped);
+// Some instance streams its weights in the grouped sampler's plan `plan`.
+bool tc_any_streamed(const tnvan_ctx* ctx, int plan);
+TcgOrder tcg_order(const tnvan_ctx* ctx, const LaunchInfo& li, int k0, int k1);
 int backward_impl(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_spins, const double* d_logZR,
                   const float* d_logq, int precision, float* d_grad_params, double* d_dbeta, double* d_dJ,
                   cudaStream_t s, bool pack, const AdamArgs* adam, bool stats_ready = false);
@@ -1412,18 +1442,13 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       if (!fits) continue;
       int* drec = nullptr;
       if ((rc = upload(ctx, in, rec, &drec))) return rc;
-      int* dsrc = nullptr;
-      if ((rc = upload(ctx, in, src, &dsrc))) return rc;
-      void* blob = nullptr;
-      cudaError_t e2 = cudaMalloc(&blob, std::max<size_t>(src.size(), 8) * sizeof(uint16_t));
-      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blobs): %s", cudaGetErrorString(e2));
-      in.dev_allocs.push_back(blob);
+      if ((rc = upload_blob(ctx, in, src, &P.wblob, &P.wsrc, &P.wdst, &P.n_wblob))) return rc;
       int* dsoff = nullptr;
       if ((rc = upload(ctx, in, soff, &dsoff))) return rc;
       int* dssrc = nullptr;
       if (!ssrc.empty() && (rc = upload(ctx, in, ssrc, &dssrc))) return rc;
       void* stab = nullptr;
-      e2 = cudaMalloc(&stab, std::max<size_t>(ssrc.size(), 1) * sizeof(float));
+      cudaError_t e2 = cudaMalloc(&stab, std::max<size_t>(ssrc.size(), 1) * sizeof(float));
       if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler step tables): %s", cudaGetErrorString(e2));
       in.dev_allocs.push_back(stab);
       P.steptab = static_cast<float*>(stab);
@@ -1432,9 +1457,6 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
       P.n_steptab = (int)ssrc.size();
       P.n_chunks = (int)rec.size() / TNVAN_TCG_INTS;
       P.chunks = drec;
-      P.wblob = static_cast<uint16_t*>(blob);
-      P.wsrc = dsrc;
-      P.n_wblob = (long long)src.size();
       P.dp = Dp;
       P.tcw1 = tcw1;
       P.dw1 = dw1;
@@ -1602,17 +1624,9 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
     }
     P.streamed = resident ? 0 : 1;
     P.wbmax = wbmax;
-    if (!resident && !wsrc.empty()) {
-      int* dws = nullptr;
-      if ((rc = upload(ctx, in, wsrc, &dws))) return rc;
-      void* wb = nullptr;
-      cudaError_t e2 = cudaMalloc(&wb, wsrc.size() * sizeof(uint16_t));
-      if (e2 != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(sampler blobs): %s", cudaGetErrorString(e2));
-      in.dev_allocs.push_back(wb);
-      P.wsrc = dws;
-      P.wblob = static_cast<uint16_t*>(wb);
-      P.n_wblob = (long long)wsrc.size();
-    }
+    if (!resident && !wsrc.empty() &&
+        (rc = upload_blob(ctx, in, wsrc, &P.wblob, &P.wsrc, &P.wdst, &P.n_wblob)))
+      return rc;
     P.n_groups = (int)grp.size() / TNVAN_TCGG_INTS;
     P.groups = dgrp;
     P.blocks = static_cast<float*>(blk);
@@ -1887,7 +1901,8 @@ static int sample_adjoint_overlapped(tnvan_ctx* ctx, const double* betas, int ba
     {
       PROF("sample_tc", ctx->side[c]);
       if (grouped)
-        CK(launch_sample_tcg(ctx->d_inst, li, plan, smem, d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
+        CK(launch_sample_tcg(ctx->d_inst, li, tcg_order(ctx, li, k0, k1), plan, smem, tc_any_streamed(ctx, plan),
+                             d_spins, d_logq, nullptr, ctx->side[c], li.tile_begin[k0],
                              li.tile_begin[k1]),
            "tensor-core sample kernel");
       else
@@ -2910,10 +2925,10 @@ namespace {
 
 // Rebuild what the kernels read from the networks (segments in `mask`).
 int pack_network(tnvan_ctx* ctx, int mask, cudaStream_t s) {
-  long long mx = 0;
-  for (const Instance& in : ctx->inst) mx = std::max(mx, pack_elems(in.dev.made, mask));
+  std::vector<long long> counts;
+  for (const Instance& in : ctx->inst) counts.push_back(pack_elems(in.dev.made, mask));
   PROF("pack", s);
-  CK(launch_pack_all(ctx->d_inst, (int)ctx->inst.size(), mx, mask, s), "pack kernel");
+  CK(launch_pack_all(ctx->d_inst, (int)ctx->inst.size(), counts.data(), mask, s), "pack kernel");
   return TNVAN_OK;
 }
 
@@ -2948,6 +2963,31 @@ bool tc_sampler_usable(const tnvan_ctx* ctx) {
 int tc_plan_value(const tnvan_ctx* ctx, int p) {
   if (p < 0 || p >= TNVAN_TC_PLANS) return 0;
   return tc_grouped_usable(ctx) ? kTcGroupMaxG[p] : kTcGroupMax[p];
+}
+
+// The grouped sampler's block order over instances [k0, k1) of a launch:
+// widest width set first, ties in instance order.
+TcgOrder tcg_order(const tnvan_ctx* ctx, const LaunchInfo& li, int k0, int k1) {
+  TcgOrder o;
+  o.n = k1 - k0;
+  std::vector<int> ks;
+  for (int k = k0; k < k1; ++k) ks.push_back(k);
+  std::stable_sort(ks.begin(), ks.end(),
+                   [&](int a, int b) { return ctx->inst[a].W.size() > ctx->inst[b].W.size(); });
+  int acc = li.tile_begin[k0];
+  for (int j = 0; j < o.n; ++j) {
+    o.inst[j] = ks[j];
+    o.begin[j] = acc;
+    acc += li.tile_begin[ks[j] + 1] - li.tile_begin[ks[j]];
+  }
+  o.begin[o.n] = acc;
+  return o;
+}
+
+bool tc_any_streamed(const tnvan_ctx* ctx, int plan) {
+  for (const Instance& in : ctx->inst)
+    if (in.dev.made.tcg[plan].streamed) return true;
+  return false;
 }
 
 // Shared memory of a tensor-core sampler launch over every instance.
@@ -2997,7 +3037,9 @@ int run_sampler(tnvan_ctx* ctx, const double* betas, int batch, uint64_t seed, u
     PROF(given ? "log_prob_tc" : "sample_tc", s);
     if (grouped) {
       const int smem = tc_sampler_smem(ctx, plan, grouped);
-      CK(launch_sample_tcg(ctx->d_inst, li, plan, smem, d_spins, d_logq, given, s), "tensor-core sample kernel");
+      CK(launch_sample_tcg(ctx->d_inst, li, tcg_order(ctx, li, 0, li.n_inst), plan, smem,
+                           tc_any_streamed(ctx, plan), d_spins, d_logq, given, s),
+         "tensor-core sample kernel");
       return TNVAN_OK;
     }
     // per-step form: instances whose CTAs fit two per SM (<= 256 TMEM columns)

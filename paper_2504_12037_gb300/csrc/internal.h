@@ -70,8 +70,9 @@ struct MadeDev {
     int ok;               // eligible (sizes within the kernel's limits)
     int n_chunks;
     const int* chunks;    // [n_chunks][TNVAN_TCG_INTS], see TNVAN_TCG_INTS
-    uint16_t* wblob;      // BF16 blobs, gathered from the network on every call
-    const int* wsrc;      // [n_wblob] index into the packed network, -1 = zero
+    uint16_t* wblob;      // BF16 blobs (zero where no weight), gathered from the network on every call
+    const int* wsrc;      // [n_wblob] the live elements: index into the packed network
+    const int* wdst;      // [n_wblob] and element of wblob
     long long n_wblob;
     int dp;               // D padded to a multiple of 16
     int tcw1;             // TMEM columns of the chunk's layer-1 pre-activations
@@ -108,8 +109,9 @@ struct MadeDev {
     // rows of the group's layer-1 units [n1 x r16(i0)]; record word 31 = its
     // element offset
     int streamed;
-    uint16_t* wblob;      // gathered from `packed` on every call
-    const int* wsrc;      // [n_wblob] index into `packed`, -1 = zero
+    uint16_t* wblob;      // gathered from the network on every call (zero where no weight)
+    const int* wsrc;      // [n_wblob] the live elements: index into the packed network
+    const int* wdst;      // [n_wblob] and element of wblob
     long long n_wblob;
     int wbmax;            // largest blob (bytes)
   } tcg[TNVAN_TC_PLANS];
@@ -274,6 +276,16 @@ struct LaunchInfo {
   unsigned int skip[TNVAN_MAX_INST / 32];  // per-instance bits: 1 = a kernel that reads them leaves the instance out
 };
 
+// Block order of a grouped-sampler launch: the instances of the launch's
+// range, longest width set first (a CTA's time grows with D), so that the
+// longest CTAs start first.  Blocks [begin[j], begin[j + 1]) draw the tiles
+// of instance inst[j]; n = 0 keeps the LaunchInfo order.
+struct TcgOrder {
+  int n;
+  int inst[TNVAN_MAX_INST];
+  int begin[TNVAN_MAX_INST + 1];
+};
+
 // ---------------------------------------------------------------------------
 // Host-side instance state.
 // ---------------------------------------------------------------------------
@@ -389,7 +401,7 @@ namespace tnvan {
 // Kernel launchers (defined in the .cu files).  All return a cudaError_t.
 enum { PACK_FLAT = 1, PACK_TILES = 2, PACK_SIMT = 4, PACK_TC = 8, PACK_TCG = 16 };
 __host__ __device__ long long pack_elems(const MadeDev& md, int mask);
-cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s);
+cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, const long long* counts, int mask, cudaStream_t s);
 cudaError_t launch_sample(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                           int8_t* spins, float* logq, const int8_t* given, cudaStream_t s);
 cudaError_t launch_strips(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
@@ -496,8 +508,10 @@ cudaError_t launch_sample_tc(const InstDev* d_inst, const LaunchInfo& li, int pl
                              int blk_end = -1);
 int sample_tc_smem_bytes(const MadeDev& md, int plan);
 extern const int kTcGroupMax[TNVAN_TC_PLANS];
-cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
-                              float* logq, const int8_t* given, cudaStream_t s, int blk_begin = 0, int blk_end = -1);
+// streamed: some instance of the launch streams its weights (plan `plan`).
+cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, const TcgOrder& ord, int plan,
+                              int smem_bytes, bool streamed, int8_t* spins, float* logq, const int8_t* given,
+                              cudaStream_t s, int blk_begin = 0, int blk_end = -1);
 int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax, int wbmax = 0);
 extern const int kTcGroupMaxG[TNVAN_TC_PLANS];
 cudaError_t launch_adam(long long n, float* p, const float* g, const AdamArgs& a, cudaStream_t s);

@@ -129,11 +129,10 @@ __device__ __forceinline__ void pack_one(const MadeDev& md, int mask, long long 
         return;
       }
       e -= P.n_blk;
-      if (e < P.n_wblob) {  // streamed group blobs (BF16, round to nearest even)
-        const int j = P.wsrc[e];
-        uint32_t u = __float_as_uint(j >= 0 ? packed_value(md, j) : 0.f);
+      if (e < P.n_wblob) {  // streamed group blobs' live elements (BF16, round to nearest even)
+        uint32_t u = __float_as_uint(packed_value(md, P.wsrc[e]));
         u += 0x7fffu + ((u >> 16) & 1u);
-        P.wblob[e] = (uint16_t)(u >> 16);
+        P.wblob[P.wdst[e]] = (uint16_t)(u >> 16);
         return;
       }
       e -= P.n_wblob;
@@ -144,11 +143,10 @@ __device__ __forceinline__ void pack_one(const MadeDev& md, int mask, long long 
     for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
       if (only >= 0 && p != only) continue;
       const MadeDev::TcPlan& P = md.tc[p];
-      if (e < P.n_wblob) {
-        const int j = P.wsrc[e];
-        uint32_t u = __float_as_uint(j >= 0 ? packed_value(md, j) : 0.f);
+      if (e < P.n_wblob) {  // the chunk blobs' live elements
+        uint32_t u = __float_as_uint(packed_value(md, P.wsrc[e]));
         u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
-        P.wblob[e] = (uint16_t)(u >> 16);
+        P.wblob[P.wdst[e]] = (uint16_t)(u >> 16);
         return;
       }
       e -= P.n_wblob;
@@ -161,11 +159,21 @@ __device__ __forceinline__ void pack_one(const MadeDev& md, int mask, long long 
   }
 }
 
-// One instance per grid row; the row's threads stride over its elements.
-__global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask) {
-  const MadeDev& md = inst[blockIdx.y].made;
+// CTAs [cta_begin[j], cta_begin[j + 1]) pack instance k0 + j, striding over
+// its elements; the host shares the CTAs out in proportion to the instances'
+// element counts, so a launch of mixed sizes ends with its largest instance.
+struct PackGrid {
+  int n, k0;
+  int cta_begin[TNVAN_MAX_INST + 1];
+};
+
+__global__ void pack_all_kernel(const InstDev* __restrict__ inst, int mask, const PackGrid pg) {
+  int j = 0;
+  while (j + 1 < pg.n && pg.cta_begin[j + 1] <= (int)blockIdx.x) ++j;
+  const MadeDev& md = inst[pg.k0 + j].made;
   const long long n = pack_elems(md, mask);
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+  const int c0 = pg.cta_begin[j], nc = pg.cta_begin[j + 1] - c0;
+  for (long long e = (long long)(blockIdx.x - c0) * blockDim.x + threadIdx.x; e < n; e += (long long)nc * blockDim.x)
     pack_one(md, mask, e);
 }
 
@@ -188,12 +196,31 @@ __host__ __device__ long long pack_elems(const MadeDev& md, int mask) {
   return n;
 }
 
-cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, long long max_total, int mask, cudaStream_t s) {
-  if (n_inst == 0 || max_total == 0) return cudaSuccess;
-  // about eight CTAs per SM in all (152 SMs), at least one per instance
-  const long long need = (max_total + 255) / 256, cap = std::max(1, 1216 / n_inst);
-  pack_all_kernel<<<dim3((unsigned)std::min(need, cap), n_inst), 256, 0, s>>>(d_inst, mask);
-  return cudaGetLastError();
+cudaError_t launch_pack_all(const InstDev* d_inst, int n_inst, const long long* counts, int mask, cudaStream_t s) {
+  for (int k0 = 0; k0 < n_inst; k0 += TNVAN_MAX_INST) {
+    const int n = std::min(TNVAN_MAX_INST, n_inst - k0);
+    long long tot = 0;
+    for (int j = 0; j < n; ++j) tot += counts[k0 + j];
+    if (tot == 0) continue;
+    // about sixteen CTAs per SM in all (152 SMs), at least one per instance,
+    // none without 256 elements of its own
+    const long long budget = 2432;
+    PackGrid pg;
+    pg.n = n;
+    pg.k0 = k0;
+    int acc = 0;
+    for (int j = 0; j < n; ++j) {
+      pg.cta_begin[j] = acc;
+      const long long c = counts[k0 + j];
+      const long long share = std::max(1LL, std::min((c + 255) / 256, (budget * c + tot - 1) / tot));
+      acc += (int)share;
+    }
+    pg.cta_begin[n] = acc;
+    pack_all_kernel<<<(unsigned)acc, 256, 0, s>>>(d_inst, mask, pg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Dot product of a warp-uniform weight row with this thread's activation

@@ -263,21 +263,33 @@ __host__ __device__ inline int sample_tcg_tmem_cols(int D, int H2, int tcw1) {
   return tcw1 + H2 + D <= 256 ? 256 : 512;
 }
 
+// ANY_STREAMED: some instance of the launch streams its weights (the
+// resident-only instantiation carries none of that code).
+template <bool ANY_STREAMED>
 __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __restrict__ inst,
-                                                           const LaunchInfo li, int plan,
+                                                           const LaunchInfo li, const TcgOrder ord, int plan,
                                                            int8_t* __restrict__ spins, float* __restrict__ logq,
                                                            const int8_t* __restrict__ given) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int gblk = blockIdx.x + li.blk0;
-  const int k = find_inst(li, gblk);
+  int k, tile;
+  if (ord.n > 0) {
+    int j = 0;
+    while (j + 1 < ord.n && ord.begin[j + 1] <= gblk) ++j;
+    k = ord.inst[j];
+    tile = gblk - ord.begin[j];
+  } else {
+    k = find_inst(li, gblk);
+    tile = gblk - li.tile_begin[k];
+  }
   const InstDev& I = inst[k];
   const MadeDev& md = I.made;
   const MadeDev::TcGroupPlan& P = md.tcg[plan];
   const int D = md.D, H1 = md.H1, H2 = md.H2;
   const int t = threadIdx.x, w = t >> 5;
-  const int b = (gblk - li.tile_begin[k]) * 128 + t;
+  const int b = tile * 128 + t;
   const bool valid = b < li.batch;
-  const bool streamed = P.streamed != 0;
+  const bool streamed = ANY_STREAMED && P.streamed != 0;
   const SampleTcgLayout LY = sample_tcg_layout(D, H1, H2, P.tcw1, P.tcw2, P.twmax, streamed ? P.wbmax : 0);
   const uint32_t wbuf = (uint32_t)((P.wbmax + 127) & ~127);  // one streamed blob buffer
   unsigned char* sW1 = smem;
@@ -649,7 +661,7 @@ __global__ void __launch_bounds__(128, 2) sample_tcg_kernel(const InstDev* __res
       int8_t* row = spins + I.spin_units * li.batch + (long long)b * D;
       // rows of more than 128 spins: from the spin tile
       auto up_at = [&](int ii) {
-        if (D > 128) return ld_bf16(sS, rbS + 16u * (uint32_t)ii) > 0.f;
+        if (ANY_STREAMED && D > 128) return ld_bf16(sS, rbS + 16u * (uint32_t)ii) > 0.f;
         return ii < 64 ? ((sb0 >> ii) & 1ull) != 0 : ((sb1 >> (ii - 64)) & 1ull) != 0;
       };
       if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(row) & 3) == 0) {  // four spins per store
@@ -681,16 +693,18 @@ int sample_tcg_smem_bytes(int D, int H1, int H2, int tcw1, int tcw2, int twmax, 
 }
 
 // Blocks [blk_begin, blk_end) of the launch (blk_end < 0: all).
-cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, int plan, int smem_bytes, int8_t* spins,
-                             float* logq, const int8_t* given, cudaStream_t s, int blk_begin, int blk_end) {
+cudaError_t launch_sample_tcg(const InstDev* d_inst, const LaunchInfo& li, const TcgOrder& ord, int plan,
+                              int smem_bytes, bool streamed, int8_t* spins, float* logq, const int8_t* given,
+                              cudaStream_t s, int blk_begin, int blk_end) {
   if (blk_end < 0) blk_end = li.tile_begin[li.n_inst];
   const int nblk = blk_end - blk_begin;
   if (nblk <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(sample_tcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  auto kern = streamed ? sample_tcg_kernel<true> : sample_tcg_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   LaunchInfo lc = li;
   lc.blk0 = blk_begin;
-  sample_tcg_kernel<<<nblk, 128, smem_bytes, s>>>(d_inst, lc, plan, spins, logq, given);
+  kern<<<nblk, 128, smem_bytes, s>>>(d_inst, lc, ord, plan, spins, logq, given);
   return cudaGetLastError();
 }
 
