@@ -2444,7 +2444,8 @@ int plan_fused_bwd(tnvan_ctx* ctx, const double* betas, int batch, FusedBwdPlan&
   p.max_elems = 0;
   p.smem = 0;
   for (const Instance& in : ctx->inst) {
-    p.max_elems = std::max(p.max_elems, in.n_params);
+    // rows of a multiple of 4 floats: the flush writes 16-byte vectors
+    p.max_elems = std::max(p.max_elems, (in.n_params + 3) & ~3LL);
     if (in.dev.made.fused_ok)
       p.smem = std::max(p.smem, fused_bwd_smem_bytes((int)in.W.size(), in.H[0], in.H[1]));
   }

@@ -86,12 +86,21 @@ struct FusedBwdArgs {
   int* status;
 };
 
+// Bytes of the buffer dX and then dA2 share (D padded): dA2 is written once
+// the products reading dX are done.  The MN-major view of dX (M = 128 of its
+// D columns) reads up to 2 KB past the dX tile when D < 128; the buffer
+// covers that.
+__host__ __device__ inline int fused_bwd_xbuf(int D, int H2) {
+  const int a = 256 * D + 2048, b = 256 * H2;
+  return a > b ? a : b;
+}
+
 // Shared memory bytes for (D, H1, H2).
 __host__ __device__ inline int fused_bwd_smem(int D0, int H1, int H2) {
   const int D = (D0 + 15) & ~15;
-  const int w = H1 * D + H2 * H1 + D * H2;                        // weights
-  const int a = 128 * ((D + 16) + (H1 + 16) + (H2 + 16) + D + H2);  // S, A1, A2/dA1, dX, dA2
-  return 2 * (w + a) + 4 * (H1 + H2 + D) + 64;  // + biases, barriers and the TMEM slot
+  const int w = H1 * D + H2 * H1 + D * H2;              // weights
+  const int a = 128 * ((D + 16) + (H1 + 16) + (H2 + 16));  // S, A1, A2/dA1
+  return 2 * (w + a) + fused_bwd_xbuf(D, H2) + 4 * (H1 + H2 + D) + 64;  // + dX/dA2, biases, barriers, TMEM slot
 }
 
 __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
@@ -121,11 +130,11 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   unsigned char* sS = p; p += 128 * (Dp + 16) * 2;
   unsigned char* sA1 = p; p += 128 * (H1 + 16) * 2;
   unsigned char* sA2 = p; p += 128 * (H2 + 16) * 2;  // later dA1 (128 x H1)
-  unsigned char* sdX = p; p += 128 * Dp * 2;          // must precede sdA2 (MN view overruns into it)
-  unsigned char* sdA2 = p; p += 128 * H2 * 2;
+  unsigned char* sdX = p;                             // dX, then dA2 in the same buffer
+  unsigned char* sdA2 = p; p += fused_bwd_xbuf(Dp, H2);
   float* sb1 = reinterpret_cast<float*>(p); p += 4 * H1;  // biases
   float* sb2 = reinterpret_cast<float*>(p); p += 4 * H2;
-  float* sbo = reinterpret_cast<float*>(p); p += 4 * D;
+  float* sbo = reinterpret_cast<float*>(p); p += 4 * Dp;  // padded: the barriers below stay 8-byte aligned
   uint64_t* bar = reinterpret_cast<uint64_t*>(p);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);  // cbar is bar + 2
   const Tile tW1{smem_u32(sW1), Dp}, tW2{smem_u32(sW2), H1}, tWo{smem_u32(sWo), H2};

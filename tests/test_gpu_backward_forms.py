@@ -1,8 +1,9 @@
 """The backward forms of Eq. 10 in the reduced-precision modes, against the
 oracle's REINFORCE gradient on the same samples: for networks the fused BF16
 kernel does not take, the tensor-core GEMM chain or the FP32 SIMT backward the
-autotuner may pick instead; and a multi-instance call mixing instances the
-fused kernel takes (width sets padded to a multiple of 16) with others."""
+autotuner may pick instead, and the fused kernel on a width set of 83 spins
+(padded to 96); and a multi-instance call mixing instances the fused kernel
+takes (width sets padded to a multiple of 16) with others."""
 import numpy as np
 import pytest
 import torch
@@ -61,11 +62,11 @@ def _check(gk, ref, exact):
 def test_backward_forms_match_oracle(cfg, form):
     w = wl.workload(cfg)
     model, grad, ref, ran = _case(w, len(w.graphs), form)
-    # none of these networks is fused: one hidden layer (1), 256-unit layers
-    # (3), and D = 83 with 2 x 128 units (4: its TMEM accumulators would fit,
-    # 128 + 96 + 144 + 144 columns with the ones column in the padding, but the
-    # tiles need about 236 KB of shared memory)
-    fused = False
+    # the fused kernel takes workload 4 only (D = 83 with 2 x 128 units: 128 +
+    # 96 + 144 + 144 TMEM columns with the layer-1 ones column in the padding,
+    # 213 KB of shared memory with dX and dA2 in one buffer); workloads 1 (one
+    # hidden layer) and 3 (256-unit layers) take the chosen form
+    fused = cfg == 4
     assert model.ctx.instance_info(0)["fused_bwd"] == int(fused)
     assert ("bwd_fused" in ran) == fused
     assert ("backward" in ran) == (form == 2 and not fused)
