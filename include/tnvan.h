@@ -356,7 +356,8 @@ int tnvan_magnetisation(tnvan_ctx* ctx, const double* betas, int batch, const in
  * TNVAN_BF16, instances whose network has two hidden layers of <= 128 units
  * (multiples of 16) and a width set that fits the fused kernel's TMEM (D
  * padded to 16 as Dp; 128 + G + (H1 + 16) + (H2 + 16) <= 512 columns with
- * G = Dp when D is not a multiple of 16, else Dp + 16) run
+ * G = Dp when D is not a multiple of 16, else Dp + 16) and whose tiles fit
+ * 227 KB of shared memory (every such width set does with H1 = H2 = 128) run
  * the fused tcgen05 backward; the other instances of the same call run the
  * tensor-core GEMM chain (TF32 / BF16 operands, FP32 accumulate) or, where the
  * autotuner found it faster, the FP32 SIMT backward.
