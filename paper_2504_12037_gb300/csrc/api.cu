@@ -772,6 +772,13 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     bf[k].dA1 = take(B * in.H[0]);
     bf[k].w = take(B);
   }
+  // BF16 mode: the intermediates (A1 ... dA1) are stored in BF16 (the next
+  // product's operands) and the weights read from the packed BF16 copy; the
+  // biases and the REINFORCE weights stay FP32
+  const int IT = bf16 ? GT_BF16 : GT_F32;
+  auto wts = [&](const MadeDev& md, long long o) -> const void* {
+    return bf16 ? static_cast<const void*>(md.packed16 + o) : static_cast<const void*>(md.packed + o);
+  };
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
   // per-instance REINFORCE weights laid out [k][batch] in one contiguous buffer
@@ -820,9 +827,9 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     if (md.nh < 1) continue;
     const int D = md.D;
     const int8_t* S = d_spins + in.dev.spin_units * batch;
-    const float* W1 = md.packed + md.layer[0].dst_off;
-    GemmProblem P = base(B, md.H1, D, op(S, D, 1, GT_I8), op(W1, D, 1, GT_F32), EPI_BIAS_RELU, bf[k].A1, md.H1);
-    P.bias = W1 + (long long)md.H1 * D;
+    const long long o1 = md.layer[0].dst_off;
+    GemmProblem P = base(B, md.H1, D, op(S, D, 1, GT_I8), op(wts(md, o1), D, 1, IT), EPI_BIAS_RELU, bf[k].A1, md.H1);
+    P.bias = md.packed + o1 + (long long)md.H1 * D;
     probs.push_back(P);
     max_m = std::max(max_m, B);
   }
@@ -832,10 +839,10 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     if (skip(k)) continue;
     const MadeDev& md = ctx->inst[k].dev.made;
     if (md.nh < 2) continue;
-    const float* W2 = md.packed + md.layer[1].dst_off;
-    GemmProblem P = base(B, md.H2, md.H1, op(bf[k].A1, md.H1, 1, GT_F32), op(W2, md.H1, 1, GT_F32),
+    const long long o2 = md.layer[1].dst_off;
+    GemmProblem P = base(B, md.H2, md.H1, op(bf[k].A1, md.H1, 1, IT), op(wts(md, o2), md.H1, 1, IT),
                          EPI_BIAS_RELU, bf[k].A2, md.H2);
-    P.bias = W2 + (long long)md.H2 * md.H1;
+    P.bias = md.packed + o2 + (long long)md.H2 * md.H1;
     probs.push_back(P);
     max_m = std::max(max_m, B);
   }
@@ -847,10 +854,10 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     const MadeDev& md = in.dev.made;
     const int D = md.D, Hl = md.Hl;
     const int8_t* S = d_spins + in.dev.spin_units * batch;
-    const float* Wo = md.packed + md.layer[md.nh].dst_off;
-    GemmOperand A = md.nh == 0 ? op(S, D, 1, GT_I8) : op(md.nh == 1 ? bf[k].A1 : bf[k].A2, Hl, 1, GT_F32);
-    GemmProblem P = base(B, D, Hl, A, op(Wo, Hl, 1, GT_F32), EPI_DX, bf[k].dX, D);
-    P.bias = Wo + (long long)D * Hl;
+    const long long oo = md.layer[md.nh].dst_off;
+    GemmOperand A = md.nh == 0 ? op(S, D, 1, GT_I8) : op(md.nh == 1 ? bf[k].A1 : bf[k].A2, Hl, 1, IT);
+    GemmProblem P = base(B, D, Hl, A, op(wts(md, oo), Hl, 1, IT), EPI_DX, bf[k].dX, D);
+    P.bias = md.packed + oo + (long long)D * Hl;
     P.spins = S;
     P.ld_spins = D;
     P.row_w = wall + (size_t)k * batch;
@@ -864,10 +871,10 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     const MadeDev& md = ctx->inst[k].dev.made;
     if (md.nh < 1) continue;
     const int D = md.D, Hl = md.Hl;
-    const float* Wo = md.packed + md.layer[md.nh].dst_off;
     float* out = md.nh == 2 ? bf[k].dA2 : bf[k].dA1;
     const float* mask = md.nh == 2 ? bf[k].A2 : bf[k].A1;
-    GemmProblem P = base(B, Hl, D, op(bf[k].dX, D, 1, GT_F32), op(Wo, 1, Hl, GT_F32), EPI_MASK, out, Hl);
+    GemmProblem P = base(B, Hl, D, op(bf[k].dX, D, 1, IT), op(wts(md, md.layer[md.nh].dst_off), 1, Hl, IT), EPI_MASK,
+                         out, Hl);
     P.mask = mask;
     P.ld_mask = Hl;
     probs.push_back(P);
@@ -879,8 +886,7 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     if (skip(k)) continue;
     const MadeDev& md = ctx->inst[k].dev.made;
     if (md.nh < 2) continue;
-    const float* W2 = md.packed + md.layer[1].dst_off;
-    GemmProblem P = base(B, md.H1, md.H2, op(bf[k].dA2, md.H2, 1, GT_F32), op(W2, 1, md.H1, GT_F32),
+    GemmProblem P = base(B, md.H1, md.H2, op(bf[k].dA2, md.H2, 1, IT), op(wts(md, md.layer[1].dst_off), 1, md.H1, IT),
                          EPI_MASK, bf[k].dA1, md.H1);
     P.mask = bf[k].A1;
     P.ld_mask = md.H1;
@@ -903,13 +909,13 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
       const float* delta = l == md.nh ? bf[k].dX : (l == 1 ? bf[k].dA2 : bf[k].dA1);
       GemmOperand act;
       if (l == 0) act = op(S, 1, D, GT_I8);
-      else act = op(l == 1 ? bf[k].A1 : bf[k].A2, 1, L.nin, GT_F32);
+      else act = op(l == 1 ? bf[k].A1 : bf[k].A2, 1, L.nin, IT);
       for (int n0 = 0; n0 < L.nin; n0 += 128) {
         const bool last = n0 + 128 >= L.nin;
         const int nn = (L.nin + 1 <= 256) ? L.nin : std::min(128, L.nin - n0);
         GemmOperand actn = act;
-        actn.ptr = static_cast<const char*>(act.ptr) + (size_t)n0 * (act.type == GT_F32 ? 4 : 1);
-        GemmProblem P = base(L.nout, nn, B, op(delta, 1, L.nout, GT_F32), actn, EPI_STORE,
+        actn.ptr = static_cast<const char*>(act.ptr) + (size_t)n0 * (act.type == GT_F32 ? 4 : act.type == GT_BF16 ? 2 : 1);
+        GemmProblem P = base(L.nout, nn, B, op(delta, 1, L.nout, IT), actn, EPI_STORE,
                              pk + L.dst_off + n0, L.nin);
         P.split_stride = part_stride;
         if (last || L.nin + 1 <= 256) {
@@ -1641,11 +1647,14 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tcg_ok = md.sample_tcg_ok || md.tcg[p].ok;
   md.sample_tc_ok = 0;
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) md.sample_tc_ok = md.sample_tc_ok || md.tc[p].ok;
+  // the FP32 copy, then (16-byte aligned) its BF16 twin
+  const size_t f32_bytes = ((size_t)off * sizeof(float) + 15) & ~size_t(15);
   void* packed = nullptr;
-  cudaError_t e = cudaMalloc(&packed, off * sizeof(float));
+  cudaError_t e = cudaMalloc(&packed, f32_bytes + (size_t)off * sizeof(uint16_t));
   if (e != cudaSuccess) return fail(ctx, TNVAN_E_NOMEM, "cudaMalloc(packed params): %s", cudaGetErrorString(e));
   in.dev_allocs.push_back(packed);
   md.packed = static_cast<float*>(packed);
+  md.packed16 = reinterpret_cast<uint16_t*>(static_cast<char*>(packed) + f32_bytes);
   in.dev.made = md;
   in.nh = n_hidden;
   in.H[0] = H[0];

@@ -5,7 +5,7 @@
 
 namespace tnvan {
 
-enum { GT_F32 = 0, GT_I8 = 1 };
+enum { GT_F32 = 0, GT_I8 = 1, GT_BF16 = 2 };
 enum { EPI_STORE = 0, EPI_BIAS_RELU = 1, EPI_DX = 2, EPI_MASK = 3 };
 
 // Operand element (row r, k) is ptr[r * sr + k * sk] of type `type`.
@@ -23,19 +23,21 @@ struct GemmOperand {
 //   EPI_MASK       C[m * ldc + n] = mask[m * ld_mask + n] > 0 ? acc : 0
 // ones_col >= 0 appends a B row of ones at that column index; its result
 // (the row sums of A) goes to bias_out[z * split_stride + m].
+// In BF16 launches C and mask of EPI_BIAS_RELU, EPI_DX and EPI_MASK are BF16
+// arrays (the next product's operands), C of EPI_STORE stays FP32.
 struct GemmProblem {
   int M, N, K;
   GemmOperand A, B;
   int ones_col;
   int epi;
-  float* C;
+  void* C;  // float, or BF16 (see above)
   long long ldc, split_stride;
   float* bias_out;
   const float* bias;
   const int8_t* spins;
   long long ld_spins;
   const float* row_w;
-  const float* mask;
+  const void* mask;  // float, or BF16 (see above)
   long long ld_mask;
 };
 

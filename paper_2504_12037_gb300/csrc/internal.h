@@ -52,6 +52,7 @@ struct MadeDev {
   LayerDev layer[3];
   float* raw;             // borrowed natural-layout parameters (written only by the fused Adam step)
   float* packed;          // packed, masked, degree-sorted copy (W then b per layer)
+  uint16_t* packed16;     // the same in BF16 (round to nearest even): the GEMM chain's weight operands
   const int* c1;          // [D+1] number of layer-1 units with degree <= d
   const int* c2;          // [D+1] number of layer-2 units with degree <= d
   // Blocked sampler: steps are grouped; for each group and layer the weights

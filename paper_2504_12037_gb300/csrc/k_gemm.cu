@@ -4,12 +4,16 @@
 // One CTA (128 threads) computes a 128-row tile of C[M x N] = A[M x K] B[N x K]^T
 // (N <= 256) for one problem of the launch.  A and B are read from global
 // memory through arbitrary (row, k) strides -- so transposed operands cost
-// nothing extra -- converted to BF16 or TF32 and written by the threads into
-// the canonical no-swizzle K-major shared-memory layout.  Two K stages of 32
-// elements are double-buffered: the threads fill one stage while the tensor
-// core works on the other; one elected thread issues tcgen05.mma into a TMEM
-// accumulator and commits each stage to an mbarrier.  The epilogue reads the
-// accumulator row per thread (tcgen05.ld) and applies the fused operation.
+// nothing extra -- into the canonical no-swizzle shared-memory layouts (K- or
+// MN-major).  BF16 operands in aligned rows (the chain's intermediates and
+// the BF16 copy of the weights) arrive by 16-byte asynchronous copies through
+// a ring of four K stages of 32 elements, three in flight while the tensor
+// core works on the fourth; FP32 and int8 operands are converted by the
+// threads when their stage is filled (TF32: two stages).  One elected thread
+// issues tcgen05.mma into a TMEM accumulator and commits each stage to an
+// mbarrier, which frees the stage's slot for the stage NS - 1 ahead.  The
+// epilogue reads the accumulator row per thread (tcgen05.ld), applies the
+// fused operation and writes the next product's operand in BF16 (TF32: FP32).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -23,6 +27,7 @@ namespace tnvan {
 #define GM 128
 #define GN 128  // columns per CTA
 #define GK 32
+#define GNS_BF16 4  // BF16: K stages in flight (asynchronous copies)
 
 template <int TYPE>
 __device__ __forceinline__ float load_elem(const void* p, long long idx) {
@@ -32,6 +37,7 @@ __device__ __forceinline__ float load_elem(const void* p, long long idx) {
 }
 
 __device__ __forceinline__ float load_any(int type, const void* p, long long idx) {
+  if (type == GT_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
   return type == GT_F32 ? static_cast<const float*>(p)[idx]
                         : (float)static_cast<const int8_t*>(p)[idx];
 }
@@ -79,13 +85,79 @@ __device__ __forceinline__ void st4r_bf16(unsigned char* s, int r, int k, float 
 }
 
 // Whether fill_stage stages this operand MN-major (BF16 only; the transposed
-// FP32 or int8 paths, whatever the stage).
+// FP32 or int8 paths, and BF16 operands read in 16-byte granules along rows).
 __device__ __forceinline__ bool operand_mn(const GemmOperand& op, int r0, int nrows) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(op.ptr);
   if (op.sr != 1 || op.sk == 1 || (op.sk & 3) != 0 || (r0 & 3) != 0 || (nrows & 3) != 0) return false;
   if (op.type == GT_F32) return (a & 15) == 0;
   if (op.type == GT_I8) return (a & 3) == 0;
+  if (op.type == GT_BF16) return (a & 15) == 0 && (op.sk & 7) == 0 && (r0 & 7) == 0 && (nrows & 7) == 0;
   return false;
+}
+
+// Whether a BF16 operand's stages are fetched with 16-byte asynchronous copies
+// (granules of 8 elements along the operand's contiguous index, aligned).
+__device__ __forceinline__ bool operand_async(const GemmOperand& op, bool mn) {
+  if (op.type != GT_BF16 || (reinterpret_cast<uintptr_t>(op.ptr) & 15) != 0) return false;
+  return mn || (op.sk == 1 && (op.sr & 7) == 0);
+}
+
+// One 16-byte asynchronous copy global -> shared; src_bytes < 16 zero-fills
+// the rest (0: nothing is read).
+__device__ __forceinline__ void cp16(unsigned char* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Asynchronous fill of one BF16 stage: rows [r0, r0 + nrows), k in [k0, k0 +
+// GK); rows >= rlim or k >= klim zero.  The granule that holds the ones row
+// (the bias column) is written by the thread instead (a plain store).
+__device__ void fill_stage_async(unsigned char* s, int nrows, const GemmOperand& op, int r0, int rlim, int k0,
+                                 int klim, int ones_row, int t, bool mn) {
+  const uint16_t* p = static_cast<const uint16_t*>(op.ptr);
+  const uint16_t one = 0x3F80u;  // 1.0 in BF16
+  if (!mn) {  // K-major: granule = row r, k .. k + 7
+    const int units = nrows * (GK / 8);
+    for (int u = t; u < units; u += 128) {
+      const int r = u >> 2, kq = (u & 3) * 8;
+      const int gr = r0 + r, gk = k0 + kq;
+      unsigned char* dst = s + tc::kmajor_off(r, kq, GK * 2, 2);
+      if (gr == ones_row) {
+        uint16_t h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = gk + j < klim ? one : (uint16_t)0;
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+      } else {
+        const int nv = gr < rlim ? max(0, min(8, klim - gk)) : 0;
+        cp16(dst, nv ? static_cast<const void*>(p + (long long)gr * op.sr + gk) : op.ptr, 2u * (uint32_t)nv);
+      }
+    }
+  } else {  // MN-major: granule = rows r .. r + 7 at one k
+    const int rg = nrows >> 3;
+    const int units = rg * GK;
+    for (int u = t; u < units; u += 128) {
+      const int r = (u % rg) * 8, k = u / rg;
+      const int gr = r0 + r, gk = k0 + k;
+      unsigned char* dst = s + mn_off(r, k);
+      if (ones_row >= gr && ones_row < gr + 8) {
+        uint16_t h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          h[i] = 0;
+          if (gk < klim) h[i] = gr + i == ones_row ? one : (gr + i < rlim ? p[(long long)gk * op.sk + gr + i] : (uint16_t)0);
+        }
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+      } else {
+        const int nv = gk < klim ? max(0, min(8, rlim - gr)) : 0;
+        cp16(dst, nv ? static_cast<const void*>(p + (long long)gk * op.sk + gr) : op.ptr, 2u * (uint32_t)nv);
+      }
+    }
+  }
 }
 
 // Fill one K stage: rows [r0, r0 + nrows) of an operand, k in [k0, k0 + GK).
@@ -308,18 +380,20 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   if (n_lo >= Npad) return;
   const int Np = min(GN, Npad - n_lo);
   const int stageA = BF16 ? GSTAGE_BF16 : GM * KB, stageB = BF16 ? GSTAGE_BF16 : GN * KB;
+  constexpr int NS = BF16 ? GNS_BF16 : 2;  // K stages in the ring
   const bool amn = BF16 && operand_mn(P.A, m0, GM), bmn = BF16 && operand_mn(P.B, n_lo, Np);
-  unsigned char* sA[2] = {smem, smem + stageA + stageB};
-  unsigned char* sB[2] = {smem + stageA, smem + 2 * stageA + stageB};
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (stageA + stageB));
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 2);
+  // BF16 operands in aligned 16-byte granules arrive by asynchronous copies,
+  // the others are converted by the threads when their stage is filled
+  const bool aas = BF16 && operand_async(P.A, amn), bas = BF16 && operand_async(P.B, bmn);
+  auto sA = [&](int st) { return smem + st * (stageA + stageB); };
+  auto sB = [&](int st) { return smem + st * (stageA + stageB) + stageA; };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * (stageA + stageB));
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + NS);
   // split K
   const int kchunk = (((P.K + gridDim.z - 1) / gridDim.z) + GK - 1) / GK * GK;
   const int kbeg = blockIdx.z * kchunk, kend = min(P.K, kbeg + kchunk);
-  if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-  }
+  if (t == 0)
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
   if (t < 32) {
     tc::tmem_alloc(slot, GN);
     tc::tmem_relinquish();
@@ -330,21 +404,25 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   const uint32_t tmem = *slot;
   const uint32_t id = tc::idesc(GM, Np, BF16 ? 1u : 2u) | (amn ? 1u << 15 : 0u) | (bmn ? 1u << 16 : 0u);
   const int nk = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
+  // stage ks into ring slot ks % NS (every thread commits one copy group per
+  // stage, empty past the last)
+  auto fill = [&](int ks) {
+    if (ks < nk) {
+      const int st = ks % NS, k0 = kbeg + ks * GK;
+      if (aas) fill_stage_async(sA(st), GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      else if (EPI == EPI_STORE) fill_stage<BF16>(sA(st), GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      else fill_stage_call<BF16>(sA(st), GM, P.A, m0, P.M, k0, kend, -1, t, amn);
+      if (bas) fill_stage_async(sB(st), Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
+      else if (EPI == EPI_STORE) fill_stage<BF16>(sB(st), Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
+      else fill_stage_call<BF16>(sB(st), Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
+    }
+    if (BF16) cp_commit();
+  };
+  for (int ks = 0; ks < NS - 1; ++ks) fill(ks);
   bool ok = true;
   for (int ks = 0; ks < nk; ++ks) {
-    const int st = ks & 1;
-    if (ks >= 2 && !mbar_wait(&bar[st], (uint32_t)(((ks >> 1) - 1) & 1))) {
-      ok = false;
-      break;
-    }
-    const int k0 = kbeg + ks * GK;
-    if (EPI == EPI_STORE) {  // the weight gradients: many K stages, a short epilogue
-      fill_stage<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
-      fill_stage<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
-    } else {
-      fill_stage_call<BF16>(sA[st], GM, P.A, m0, P.M, k0, kend, -1, t, amn);
-      fill_stage_call<BF16>(sB[st], Np, P.B, n_lo, P.N, k0, kend, P.ones_col, t, bmn);
-    }
+    const int st = ks % NS;
+    if (BF16) cp_wait<NS - 2>();  // this thread's copies of stage ks have landed
     fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -352,15 +430,22 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
     if (t == 0) {
 #pragma unroll
       for (int kk = 0; kk < KB / 32; ++kk) {
-        const uint64_t a = tc::smem_desc(smem_u32(sA[st]) + kk * 256, 128, amn ? MN_SBO : KB / 16 * 128);
-        const uint64_t b = tc::smem_desc(smem_u32(sB[st]) + kk * 256, 128, bmn ? MN_SBO : KB / 16 * 128);
+        const uint64_t a = tc::smem_desc(smem_u32(sA(st)) + kk * 256, 128, amn ? MN_SBO : KB / 16 * 128);
+        const uint64_t b = tc::smem_desc(smem_u32(sB(st)) + kk * 256, 128, bmn ? MN_SBO : KB / 16 * 128);
         if (BF16) tc::mma_bf16(tmem, a, b, id, (ks > 0 || kk > 0) ? 1u : 0u);
         else tc::mma_tf32(tmem, a, b, id, (ks > 0 || kk > 0) ? 1u : 0u);
       }
       tc::mma_commit(&bar[st]);
     }
+    // stage ks + NS - 1 reuses the slot of stage ks - 1: its MMAs first
+    if (ks >= 1 && !mbar_wait(&bar[(ks - 1) % NS], (uint32_t)(((ks - 1) / NS) & 1))) {
+      ok = false;
+      break;
+    }
+    fill(ks + NS - 1);
   }
-  if (ok && nk > 0) ok = mbar_wait(&bar[(nk - 1) & 1], (uint32_t)(((nk - 1) >> 1) & 1));
+  if (ok && nk > 0) ok = mbar_wait(&bar[(nk - 1) % NS], (uint32_t)(((nk - 1) / NS) & 1));
+  if (BF16) cp_wait<0>();  // no copy still in flight when the epilogue reuses the stages
   if (!ok && t == 0) atomicExch(L.status, 2);
   tc::fence_after_sync();
   // epilogue: TMEM lane t holds row m0 + t.  Each warp stages its 32 rows x
@@ -393,7 +478,9 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
         a[j] = stg[r * 17 + cc];
         in[j] = 0.f;
         if (ok_r[j] && ncol) {
-          if (EPI == EPI_MASK) in[j] = P.mask[(long long)m * P.ld_mask + n];
+          if (EPI == EPI_MASK)
+            in[j] = BF16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(P.mask)[(long long)m * P.ld_mask + n])
+                         : static_cast<const float*>(P.mask)[(long long)m * P.ld_mask + n];
           else if (EPI == EPI_DX) in[j] = (float)P.spins[(long long)m * P.ld_spins + n];
         }
       }
@@ -408,21 +495,26 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
         }
         if (!ncol) continue;
         const long long o = (long long)m * P.ldc + n;
+        float r = 0.f;
         switch (EPI) {
           case EPI_STORE:
-            P.C[(long long)blockIdx.z * P.split_stride + o] = a[j];
+            static_cast<float*>(P.C)[(long long)blockIdx.z * P.split_stride + o] = a[j];
             break;
           case EPI_BIAS_RELU:
-            P.C[o] = fmaxf(a[j] + bn, 0.f);
+            r = fmaxf(a[j] + bn, 0.f);
             break;
           case EPI_DX: {
             const float x = a[j] + bn, sp = in[j];
-            P.C[o] = P.row_w[m] * sp / (1.f + expf(sp * x));
+            r = P.row_w[m] * sp / (1.f + expf(sp * x));
             break;
           }
           case EPI_MASK:
-            P.C[o] = in[j] > 0.f ? a[j] : 0.f;
+            r = in[j] > 0.f ? a[j] : 0.f;
             break;
+        }
+        if (EPI != EPI_STORE) {  // the next product's operand
+          if (BF16) static_cast<__nv_bfloat16*>(P.C)[o] = __float2bfloat16(r);
+          else static_cast<float*>(P.C)[o] = r;
         }
       }
       __syncwarp();
@@ -434,8 +526,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
 }
 
 int gemm_smem_bytes(bool bf16) {
-  const int EL = bf16 ? 2 : 4;
-  return bf16 ? 2 * (2 * GSTAGE_BF16) + 64 : 2 * (GM * GK * EL + GN * GK * EL) + 64;
+  return bf16 ? GNS_BF16 * (2 * GSTAGE_BF16) + 8 * GNS_BF16 + 16 : 2 * (GM * GK * 4 + GN * GK * 4) + 32;
 }
 
 cudaError_t launch_gemm(const GemmLaunch& L, int n_prob, int max_m, int splits, bool bf16,

@@ -71,6 +71,11 @@ __device__ __forceinline__ void pack_one(const MadeDev& md, int mask, long long 
     if (e < md.n_params) {
       const float v = packed_value(md, e);
       md.packed[e] = v;
+      if (md.packed16) {
+        uint32_t u = __float_as_uint(v);
+        u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+        md.packed16[e] = (uint16_t)(u >> 16);
+      }
       if (tiles) {  // weights of layer l at [dst_off, dst_off + nout * nin), row-major
         int j = (int)e;
         for (int l = 0; l < 3; ++l) {
