@@ -734,10 +734,13 @@ int ensure_ws(tnvan_ctx* ctx, size_t bytes) {
 
 // Floats of the tensor-core backward workspace for `batch` samples.
 size_t tc_ws_floats(const tnvan_ctx* ctx, int batch) {
+  // per instance: A1, A2, dX, dA2, dA1, w and the BF16 spins, each rounded up
+  // to 16 floats by the carve; then the REINFORCE weights of all instances
   size_t tot = 0;
   for (const Instance& in : ctx->inst)
-    tot += (size_t)batch * (2 * in.H[0] + 2 * in.H[1] + in.W.size() + 1) + 64;
-  return tot;
+    tot += (size_t)batch * (2 * in.H[0] + 2 * in.H[1] + in.W.size() + 1) + 6 * 16 +
+           ((size_t)batch * ((in.W.size() + 7) & ~size_t(7)) + 1) / 2 + 16;
+  return tot + (size_t)ctx->inst.size() * batch + 16;
 }
 
 #define TC_SPLITS 16
@@ -773,21 +776,41 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     bf[k].w = take(B);
   }
   // BF16 mode: the intermediates (A1 ... dA1) are stored in BF16 (the next
-  // product's operands) and the weights read from the packed BF16 copy; the
+  // product's operands), the weights read from the packed BF16 copy and the
+  // spins from a BF16 copy (rows of r8(D)) that the weights kernel writes; the
   // biases and the REINFORCE weights stay FP32
   const int IT = bf16 ? GT_BF16 : GT_F32;
+  uint16_t* s16 = nullptr;
+  std::vector<size_t> s16off(n, 0);
+  if (bf16) {
+    size_t tot16 = 0;
+    for (int k = 0; k < n; ++k) {
+      s16off[k] = tot16;
+      tot16 += (size_t)batch * ((ctx->inst[k].W.size() + 7) & ~size_t(7));
+    }
+    s16 = reinterpret_cast<uint16_t*>(take((tot16 + 1) / 2));
+  }
   auto wts = [&](const MadeDev& md, long long o) -> const void* {
     return bf16 ? static_cast<const void*>(md.packed16 + o) : static_cast<const void*>(md.packed + o);
   };
   LaunchInfo li;
   if ((rc = fill_launch(ctx, betas, batch, 1, li))) return rc;
+  for (int k = 0; k < n; ++k)
+    if (skip(k)) li.skip[k >> 5] |= 1u << (k & 31);  // no BF16 spins for the fused instances
   // per-instance REINFORCE weights laid out [k][batch] in one contiguous buffer
   float* wall = take((size_t)n * batch);
   {
     PROF("reinforce_w", s);
-    CK(launch_reinforce_w(li, d_logZR, d_logq, ctx->d_stats, wall, s), "weights kernel");
+    CK(launch_reinforce_w(ctx->d_inst, li, d_logZR, d_logq, ctx->d_stats, wall, d_spins, s16, s), "weights kernel");
   }
   auto op = [](const void* p, long long sr, long long sk, int type) { return GemmOperand{p, sr, sk, type}; };
+  auto spin_op = [&](int k, bool transposed) {
+    const Instance& in = ctx->inst[k];
+    const long long D = (long long)in.W.size(), D8 = (D + 7) & ~7LL;
+    if (bf16) return transposed ? op(s16 + s16off[k], 1, D8, GT_BF16) : op(s16 + s16off[k], D8, 1, GT_BF16);
+    const int8_t* S = d_spins + in.dev.spin_units * batch;
+    return transposed ? op(S, 1, D, GT_I8) : op(S, D, 1, GT_I8);
+  };
   std::vector<GemmProblem> probs;
   int max_m = 0, splits = 1;
   auto flush = [&](const char* name) -> int {
@@ -826,9 +849,8 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     const MadeDev& md = in.dev.made;
     if (md.nh < 1) continue;
     const int D = md.D;
-    const int8_t* S = d_spins + in.dev.spin_units * batch;
     const long long o1 = md.layer[0].dst_off;
-    GemmProblem P = base(B, md.H1, D, op(S, D, 1, GT_I8), op(wts(md, o1), D, 1, IT), EPI_BIAS_RELU, bf[k].A1, md.H1);
+    GemmProblem P = base(B, md.H1, D, spin_op(k, false), op(wts(md, o1), D, 1, IT), EPI_BIAS_RELU, bf[k].A1, md.H1);
     P.bias = md.packed + o1 + (long long)md.H1 * D;
     probs.push_back(P);
     max_m = std::max(max_m, B);
@@ -901,14 +923,12 @@ int backward_tc(tnvan_ctx* ctx, const double* betas, int batch, const int8_t* d_
     if (skip(k)) continue;
     const Instance& in = ctx->inst[k];
     const MadeDev& md = in.dev.made;
-    const int D = md.D;
-    const int8_t* S = d_spins + in.dev.spin_units * batch;
     float* pk = part + (long long)k * splits * part_stride;
     for (int l = 0; l <= md.nh; ++l) {
       const LayerDev& L = md.layer[l];
       const float* delta = l == md.nh ? bf[k].dX : (l == 1 ? bf[k].dA2 : bf[k].dA1);
       GemmOperand act;
-      if (l == 0) act = op(S, 1, D, GT_I8);
+      if (l == 0) act = spin_op(k, true);
       else act = op(l == 1 ? bf[k].A1 : bf[k].A2, 1, L.nin, IT);
       for (int n0 = 0; n0 < L.nin; n0 += 128) {
         const bool last = n0 + 128 >= L.nin;

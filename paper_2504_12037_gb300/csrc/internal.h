@@ -497,8 +497,9 @@ struct AdamArgs {
 cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li,
                                const float* partials, int part_stride, float* grad,
                                cudaStream_t s, const AdamArgs* adam = nullptr, int k0 = 0, int k1 = -1);
-cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
-                               const double* stats, float* w, cudaStream_t s);
+// s16 != nullptr: also the spins as BF16 rows of r8(D) (the GEMM chain's operand)
+cudaError_t launch_reinforce_w(const InstDev* d_inst, const LaunchInfo& li, const double* logZR, const float* logq,
+                               const double* stats, float* w, const int8_t* spins, uint16_t* s16, cudaStream_t s);
 cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int smem_bytes,
                              const int8_t* spins, const double* logZR, const float* logq,
                              const double* stats, float* partials, long long part_stride, int* status,

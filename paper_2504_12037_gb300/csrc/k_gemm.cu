@@ -25,7 +25,7 @@
 namespace tnvan {
 
 #define GM 128
-#define GN 128  // columns per CTA
+#define GN 64  // columns per CTA
 #define GK 32
 #define GNS_BF16 4  // BF16: K stages in flight (asynchronous copies)
 
@@ -72,7 +72,8 @@ __device__ __forceinline__ void st1(unsigned char* s, int r, int k, float v) {
 // four consecutive rows at one k are one 8-byte store; the MMA reads them
 // with the operand's major bit set.  MN_SBO pads each 8-row group by 16 bytes.
 #define MN_SBO (GK * 2 / 16 * 128 + 16)
-#define GSTAGE_BF16 (16 * MN_SBO)  // bytes of one BF16 operand stage (either layout, 128 rows)
+#define GSTAGE_BF16 (16 * MN_SBO)  // bytes of one BF16 A stage (either layout, 128 rows)
+#define GSTAGE_B_BF16 (GN / 8 * MN_SBO)  // the same for B (GN rows)
 __device__ __forceinline__ uint32_t mn_off(int r, int k) {
   return (uint32_t)((r >> 3) * MN_SBO + (k >> 3) * 128 + (k & 7) * 16 + (r & 7) * 2);
 }
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
   const int n_lo = cb * GN;
   if (n_lo >= Npad) return;
   const int Np = min(GN, Npad - n_lo);
-  const int stageA = BF16 ? GSTAGE_BF16 : GM * KB, stageB = BF16 ? GSTAGE_BF16 : GN * KB;
+  const int stageA = BF16 ? GSTAGE_BF16 : GM * KB, stageB = BF16 ? GSTAGE_B_BF16 : GN * KB;
   constexpr int NS = BF16 ? GNS_BF16 : 2;  // K stages in the ring
   const bool amn = BF16 && operand_mn(P.A, m0, GM), bmn = BF16 && operand_mn(P.B, n_lo, Np);
   // BF16 operands in aligned 16-byte granules arrive by asynchronous copies,
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(const GemmLaunch L) {
 }
 
 int gemm_smem_bytes(bool bf16) {
-  return bf16 ? GNS_BF16 * (2 * GSTAGE_BF16) + 8 * GNS_BF16 + 16 : 2 * (GM * GK * 4 + GN * GK * 4) + 32;
+  return bf16 ? GNS_BF16 * (GSTAGE_BF16 + GSTAGE_B_BF16) + 8 * GNS_BF16 + 16 : 2 * (GM * GK * 4 + GN * GK * 4) + 32;
 }
 
 cudaError_t launch_gemm(const GemmLaunch& L, int n_prob, int max_m, int splits, bool bf16,

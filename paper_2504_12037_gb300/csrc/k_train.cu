@@ -809,9 +809,14 @@ cudaError_t launch_obs_mag(const LaunchInfo& li, const double* mean, const doubl
 
 // REINFORCE weights w_b = -(l_b - mean_b l) / (beta B) per instance (Eq. 10
 // with the batch-mean baseline), FP32 copy for the tensor-core backward.
-__global__ void reinforce_w_kernel(const LaunchInfo li, const double* __restrict__ logZR,
-                                   const float* __restrict__ logq, const double* __restrict__ stats,
-                                   float* __restrict__ w) {
+// Eq. 10's per-sample weights w[k][b]; with s16, also the spins of every
+// instance not marked in li.skip as BF16 rows of D rounded up to 8 (zeros
+// beyond D), instance k at sum_{j<k} batch * r8(D_j): the GEMM chain's spin
+// operands.
+__global__ void reinforce_w_kernel(const InstDev* __restrict__ inst, const LaunchInfo li,
+                                   const double* __restrict__ logZR, const float* __restrict__ logq,
+                                   const double* __restrict__ stats, float* __restrict__ w,
+                                   const int8_t* __restrict__ spins, uint16_t* __restrict__ s16) {
   const int k = blockIdx.y;
   const double mean = stats[8 * k + 4];
   const double sc = -1.0 / (li.beta[k] * stats_batch(stats + 8 * k));
@@ -819,12 +824,36 @@ __global__ void reinforce_w_kernel(const LaunchInfo li, const double* __restrict
     const long long o = (long long)k * li.batch + b;
     w[o] = (float)(sc * (logZR[o] - (double)logq[o] - mean));
   }
+  if (!s16 || ((li.skip[k >> 5] >> (k & 31)) & 1u)) return;  // skipped: another backward form reads the spins
+  long long off = 0;
+  for (int j = 0; j < k; ++j) off += (long long)li.batch * ((inst[j].D + 7) & ~7);
+  const int D = inst[k].D, G8 = (D + 7) >> 3;  // 8-spin groups per row
+  const int8_t* src = spins + inst[k].spin_units * li.batch;
+  const long long n = (long long)li.batch * G8;
+  uint4* dst = reinterpret_cast<uint4*>(s16 + off);  // 16-byte aligned: off is a multiple of 8
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / G8;
+    const int i0 = (int)(e - b * G8) * 8;
+    uint32_t h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int i = i0 + 2 * q + j;
+        const uint32_t x = i < D ? (src[b * D + i] > 0 ? 0x3F80u : 0xBF80u) : 0u;
+        v |= x << (16 * j);
+      }
+      h[q] = v;
+    }
+    dst[e] = make_uint4(h[0], h[1], h[2], h[3]);
+  }
 }
 
-cudaError_t launch_reinforce_w(const LaunchInfo& li, const double* logZR, const float* logq,
-                               const double* stats, float* w, cudaStream_t s) {
+cudaError_t launch_reinforce_w(const InstDev* d_inst, const LaunchInfo& li, const double* logZR, const float* logq,
+                               const double* stats, float* w, const int8_t* spins, uint16_t* s16, cudaStream_t s) {
   if (li.n_inst == 0 || li.batch == 0) return cudaSuccess;
-  reinforce_w_kernel<<<dim3(32, li.n_inst), 256, 0, s>>>(li, logZR, logq, stats, w);
+  reinforce_w_kernel<<<dim3(32, li.n_inst), 256, 0, s>>>(d_inst, li, logZR, logq, stats, w, spins, s16);
   return cudaGetLastError();
 }
 
