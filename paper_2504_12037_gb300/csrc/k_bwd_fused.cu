@@ -3,8 +3,8 @@
 // 128 inputs (padded to Dp, a multiple of 16: the padded inputs and outputs
 // are zero and carry no gradient).
 //
-// One CTA (256 threads: two warpgroups, each thread one sample = TMEM lane
-// and every other 16-column chunk of each epilogue) walks the 128-sample
+// One CTA (BWD_WG warpgroups, each thread one sample = TMEM lane and every
+// BWD_WG-th 16-column chunk of each epilogue) walks the 128-sample
 // tiles of its chunk.  Per tile, everything stays on chip:
 //   A1 = relu(S W1^T + b1), A2 = relu(A1 W2^T + b2), X = A2 Wo^T + bo,
 //   dX = w_b s sigmoid(-s x), dA2 = (dX Wo) 1[A2 > 0], dA1 = (dA2 W2) 1[A1 > 0],
@@ -76,6 +76,10 @@ struct Mask128 {
 
 }  // namespace
 
+// Warpgroups per CTA: thread (g, r) owns TMEM lane / sample row r and the
+// 16-column chunks c with (c / 16) % BWD_WG == g of every epilogue.
+#define BWD_WG 4
+
 struct FusedBwdArgs {
   const int8_t* spins;
   const double* logZR;
@@ -103,7 +107,7 @@ __host__ __device__ inline int fused_bwd_smem(int D0, int H1, int H2) {
   return 2 * (w + a) + fused_bwd_xbuf(D, H2) + 4 * (H1 + H2 + D) + 64;  // + dX/dA2, biases, barriers, TMEM slot
 }
 
-__global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
+__global__ void __launch_bounds__(128 * BWD_WG, 1) bwd_fused_kernel(const InstDev* __restrict__ inst,
                                                            const LaunchInfo li, FusedBwdArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int gblk = blockIdx.x + li.blk0;  // a launch may cover a sub-range of the blocks
@@ -112,8 +116,6 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
   const MadeDev& md = I.made;
   if (!md.fused_ok) return;
   const int D = md.D, Dp = (D + 15) & ~15, H1 = md.H1, H2 = md.H2;
-  // two warpgroups: thread (g, r) owns TMEM lane / sample row r and the
-  // 16-column chunks c with (c / 16) % 2 == g of every epilogue
   const int tid = threadIdx.x, w = tid >> 5, t = tid & 127, g = tid >> 7;
   const int B = li.batch;
   const int tiles_total = (B + 127) / 128;
@@ -158,9 +160,9 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     tc::tmem_alloc(slot, 512);
     tc::tmem_relinquish();
   }
-  for (int u = tid; u < H1; u += 256) sb1[u] = __ldg(b1 + u);
-  for (int u = tid; u < H2; u += 256) sb2[u] = __ldg(b2 + u);
-  for (int u = tid; u < D; u += 256) sbo[u] = __ldg(bo + u);
+  for (int u = tid; u < H1; u += blockDim.x) sb1[u] = __ldg(b1 + u);
+  for (int u = tid; u < H2; u += blockDim.x) sb2[u] = __ldg(b2 + u);
+  for (int u = tid; u < D; u += blockDim.x) sbo[u] = __ldg(bo + u);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     const float vf = valid ? 1.f : 0.f;
     // spins -> S tile (+ ones column), 16 per vector load; mS bit f = (s_f > 0)
     Mask128 mS, m1, m2;
-    for (int c = 16 * g; c < Dp; c += 32) {
+    for (int c = 16 * g; c < Dp; c += 16 * BWD_WG) {
       float sp[16];
       uint32_t m16 = 0;
       if ((D & 15) == 0 && (reinterpret_cast<uintptr_t>(Sg) & 15) == 0) {  // 16 spins per vector load
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
       store8(sS, tS.rowbytes(), t, c, sp);
       store8(sS, tS.rowbytes(), t, c + 8, sp + 8);
     }
-    if (oc1 == Dp && ((Dp >> 4) & 1) == g) {
+    if (oc1 == Dp && ((Dp >> 4) % BWD_WG) == g) {
       float sp[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) sp[i] = i == 0 ? vf : 0.f;
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     if (tid == 0)
       for (int kk = 0; kk < Dp / 16; ++kk) tc::mma_bf16(tScr, tS.kdesc(kk), tW1.kdesc(kk), id_fwd1, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 16 * g; c < H1 + 16; c += 32) {
+    for (int c = 16 * g; c < H1 + 16; c += 16 * BWD_WG) {
       float v[16];
       if (c < H1) tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
       uint32_t m16 = 0;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     if (tid == 0)
       for (int kk = 0; kk < H1 / 16; ++kk) tc::mma_bf16(tScr, tA1.kdesc(kk), tW2.kdesc(kk), id_fwd2, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 16 * g; c < H2 + 16; c += 32) {
+    for (int c = 16 * g; c < H2 + 16; c += 16 * BWD_WG) {
       float v[16];
       if (c < H2) tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
       uint32_t m16 = 0;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     if (tid == 0)
       for (int kk = 0; kk < H2 / 16; ++kk) tc::mma_bf16(tScr, tA2.kdesc(kk), tWo.kdesc(kk), id_fwd3, kk > 0);
     if (!(ok = mma_wait())) break;
-    for (int c = 16 * g; c < Dp; c += 32) {
+    for (int c = 16 * g; c < Dp; c += 16 * BWD_WG) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
       const uint32_t ms = mS.get16(c);
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
         tc::mma_bf16(tGo, tdX.mndesc(kk), tA2.mndesc(kk), id_go, (!first || kk > 0) ? 1u : 0u);
     }
     if (!(ok = mma_wait())) break;
-    for (int c = 16 * g; c < H2; c += 32) {
+    for (int c = 16 * g; c < H2; c += 16 * BWD_WG) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
       const uint32_t mk = m2.get16(c);
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
         tc::mma_bf16(tG2, tdA2.mndesc(kk), tA1.mndesc(kk), id_g2, (!first || kk > 0) ? 1u : 0u);
     }
     if (!(ok = mma_wait())) break;
-    for (int c = 16 * g; c < H1; c += 32) {
+    for (int c = 16 * g; c < H1; c += 16 * BWD_WG) {
       float v[16];
       tc::tmem_ld16(tScr + lane_off + (uint32_t)c, v);
       const uint32_t mk = m1.get16(c);
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     // accumulator columns [0, ncols): the nin weight-gradient columns, and
     // the bias gradient at column bcol
     auto flush = [&](uint32_t tacc, int nin, int ncols, int bcol, int nout, long long off) {
-      for (int c = 16 * g; c < ncols; c += 32) {
+      for (int c = 16 * g; c < ncols; c += 16 * BWD_WG) {
         float v[16];
         tc::tmem_ld16(tacc + lane_off + (uint32_t)c, v);
         if (t < nout) {
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(256, 1) bwd_fused_kernel(const InstDev* __rest
     flush(tG2, H1, H1 + 16, H1, H2, md.layer[1].dst_off);
     flush(tGo, H2, H2 + 16, H2, D, md.layer[2].dst_off);
   } else {
-    for (long long e = tid; e < md.n_params; e += 256) G[e] = 0.f;
+    for (long long e = tid; e < md.n_params; e += blockDim.x) G[e] = 0.f;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -405,7 +407,7 @@ cudaError_t launch_bwd_fused(const InstDev* d_inst, const LaunchInfo& li, int sm
   LaunchInfo lc = li;
   lc.blk0 = blk_begin;
   FusedBwdArgs a{spins, logZR, logq, stats, partials, part_stride, status};
-  bwd_fused_kernel<<<nblk, 256, smem_bytes, s>>>(d_inst, lc, a);
+  bwd_fused_kernel<<<nblk, 128 * BWD_WG, smem_bytes, s>>>(d_inst, lc, a);
   return cudaGetLastError();
 }
 
