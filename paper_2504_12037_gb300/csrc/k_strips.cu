@@ -547,6 +547,8 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
   for (int e = n_valid * Dp + t; e < T * Dp; e += T) ssp[e] = 1;  // padding rows
   __syncthreads();
   const bool valid = b < li.batch;
+  // the backward sweep only when d/dbeta or the bond sums are wanted
+  const bool back = dbeta != nullptr || part != nullptr;
   // this sample's weight in the bond sums: 1, or the caller's multiplier
   // (importance weights of tnvan_observables); 0 for padding samples
   const float wv = !valid ? 0.f : (li.wmul ? li.wmul[(long long)k * li.batch + b] : 1.f);
@@ -560,23 +562,32 @@ __global__ void __launch_bounds__(128, 3) strips_adj_kernel(const InstDev* __res
     const StripRow* rows = I.rows + sd.row0;
     double l = 0.0;
     float d = 0.f;
-    switch (sd.w) {
-      case 1:
-        strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
-        break;
-      case 2:
-        strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
-        break;
-      case 3:
-        strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
-        break;
-      default:
-        strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
-        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
-        break;
+    if (!back) {  // log Z_R only: the forward chain, no left vectors kept
+      switch (sd.w) {
+        case 1: strip_chain<1, false>(tab, sd.L, srow, l, d); break;
+        case 2: strip_chain<2, false>(tab, sd.L, srow, l, d); break;
+        case 3: strip_chain<3, false>(tab, sd.L, srow, l, d); break;
+        default: strip_chain<4, false>(tab, sd.L, srow, l, d); break;
+      }
+    } else {
+      switch (sd.w) {
+        case 1:
+          strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+          d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
+          break;
+        case 2:
+          strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+          d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
+          break;
+        case 3:
+          strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+          d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
+          break;
+        default:
+          strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, t, T);
+          d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, t, T, wv, accw, lane);
+          break;
+      }
     }
     dl += d;
     lz += l;
@@ -648,6 +659,8 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
   for (int e = n_valid * Dp + tid; e < 32 * Dp; e += NT) ssp[e] = 1;  // padding rows
   __syncthreads();
   const bool valid = b < li.batch;
+  // the backward sweep only when d/dbeta or the bond sums are wanted
+  const bool back = dbeta != nullptr || part != nullptr;
   // this sample's weight in the bond sums: 1, or the caller's multiplier
   // (importance weights of tnvan_observables); 0 for padding samples
   const float wv = !valid ? 0.f : (li.wmul ? li.wmul[(long long)k * li.batch + b] : 1.f);
@@ -659,23 +672,32 @@ __global__ void __launch_bounds__(256) strips_adj_ws_kernel(const InstDev* __res
     const StripRow* rows = I.rows + sd.row0;
     double l = 0.0;
     float d = 0.f;
-    switch (sd.w) {
-      case 1:
-        strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
-        break;
-      case 2:
-        strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
-        break;
-      case 3:
-        strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
-        break;
-      default:
-        strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
-        d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
-        break;
+    if (!back) {  // log Z_R only: the forward chain, no left vectors kept
+      switch (sd.w) {
+        case 1: strip_chain<1, false>(tab, sd.L, srow, l, d); break;
+        case 2: strip_chain<2, false>(tab, sd.L, srow, l, d); break;
+        case 3: strip_chain<3, false>(tab, sd.L, srow, l, d); break;
+        default: strip_chain<4, false>(tab, sd.L, srow, l, d); break;
+      }
+    } else {
+      switch (sd.w) {
+        case 1:
+          strip_chain<1, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+          d = strip_backsweep<1>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
+          break;
+        case 2:
+          strip_chain<2, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+          d = strip_backsweep<2>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
+          break;
+        case 3:
+          strip_chain<3, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+          d = strip_backsweep<3>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
+          break;
+        default:
+          strip_chain<4, false, true>(tab, sd.L, srow, l, d, lvs, tid, NT);
+          d = strip_backsweep<4>(tab, rows, sd.L, srow, lvs, tid, NT, wv, accw, lane);
+          break;
+      }
     }
     pl[st * 32 + lane] = l;
     pd[st * 32 + lane] = d;
