@@ -536,13 +536,10 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}[a.precision],
         "data": "synthetic (seeded EA couplings; random-init MADE)",
-        "config": {"workload": w.name, "lattice": "16x16 open", "couplings": "N(0,1)",
-                   "betas": w.betas, "batch_per_beta": B, "instances": n_inst,
-                   "width_set": "every 4th column (64 spins)", "made": [64] + w.hidden + [64],
+        "config": {**headline_config(w, B),
                    "precision": f"{a.precision}: network (sampler, backward) in {a.precision} on the "
                                 "tensor cores with FP32 accumulation; contractions FP32; reductions FP64"
                                 if a.precision != "fp32" else "fp32 everywhere, FP64 reductions",
-                   "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam",
                    "timing": ("CUDA-graph replay of the whole step (captured once; fresh Philox step per replay "
                               "from a device counter)" if graph else "eager steps"),
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
@@ -1159,6 +1156,14 @@ def cpu_baseline(w, params, offsets, budget_s=15.0, n_b=2048):
                       f"and adjoint, Adam) in {dt:.1f} s"}
 
 
+def headline_config(w, batch_per_beta):
+    """The 16x16 workload's configuration keys both arms report."""
+    return {"workload": w.name, "lattice": "16x16 open", "couplings": "N(0,1)", "betas": w.betas,
+            "batch_per_beta": batch_per_beta, "instances": len(w.graphs),
+            "width_set": "every 4th column (64 spins)", "made": [64] + w.hidden + [64],
+            "step": "sample+contract+reduce+REINFORCE backward+d/dbeta+d/dJ+Adam"}
+
+
 def run_reference(a):
     import numpy as np
 
@@ -1187,9 +1192,11 @@ def run_reference(a):
            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": w.name, "batch_per_beta": n_b, "instances": len(w.graphs)},
+           "config": {**headline_config(w, w.batch), "precision": "fp64 (the oracle, as it stands)",
+                      "timing": "host cores, wall clock; each step a bounded sample of the workload's batch",
+                      "parallelism": "host threads"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-                            "sample": f"{n_b} samples per beta x {len(w.graphs)} betas per step"},
+                            "sample": f"{n_b} of the {w.batch} samples per beta x {len(w.graphs)} betas per step"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
