@@ -670,13 +670,14 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
     for (int j = 0; j < 8; ++j)
       if (p + j < p1) a[j] += partials[(long long)(p + j) * part_stride + e];
     const float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    long long r = e, nat = -1;
+    int r = (int)e;  // a network's parameter count fits in 32 bits (checked at set-up)
+    long long nat = -1;
     float gv = s;
     for (int l = 0; l < md.n_layers; ++l) {
       const LayerDev& L = md.layer[l];
-      const long long nw = (long long)L.nout * L.nin;
+      const int nw = L.nout * L.nin;
       if (r < nw) {
-        const int o = (int)(r / L.nin), i = (int)(r % L.nin);
+        const int o = r / L.nin, i = r - o * L.nin;
         const int no = L.perm_out ? L.perm_out[o] : o;
         const int ni = L.perm_in ? L.perm_in[i] : i;
         const bool conn = L.strict ? (L.deg_out[o] > L.deg_in[i]) : (L.deg_out[o] >= L.deg_in[i]);
@@ -686,7 +687,7 @@ __global__ void grad_reduce_kernel(const InstDev* __restrict__ inst, const Launc
       }
       r -= nw;
       if (r < L.nout) {
-        nat = L.src_off + nw + (L.perm_out ? L.perm_out[r] : (int)r);
+        nat = L.src_off + nw + (L.perm_out ? L.perm_out[r] : r);
         break;
       }
       r -= L.nout;
@@ -702,7 +703,9 @@ cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, cons
                                int part_stride, float* grad, cudaStream_t s, const AdamArgs* adam, int k0, int k1) {
   if (k1 < 0) k1 = li.n_inst;
   if (k1 <= k0) return cudaSuccess;
-  const dim3 grid(64, k1 - k0);
+  // one parameter per thread (the row stride bounds every instance's count),
+  // at most 256 CTAs per instance
+  const dim3 grid((unsigned)std::max(1, std::min(256, (part_stride + 255) / 256)), k1 - k0);
   if (adam)
     grad_reduce_kernel<true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam, k0);
   else
