@@ -277,7 +277,7 @@ int tnvan_reduce(tnvan_ctx* ctx, const double* betas, int batch, const double* d
 int tnvan_step_stats(tnvan_ctx* ctx, double* d_stats_out, void* stream);
 
 /* Data-parallel exchange (not in the paper; the samples of one batch split
- * over ranks, SURVEY's one exchange per step): merges the statistics rows of
+ * over ranks, one exchange of statistics per step): merges the statistics rows of
  * n_parts disjoint parts of a batch, d_parts = device double
  * [n_parts][n_inst][8] (each part's tnvan_reduce rows, e.g. gathered from
  * every rank), into the rows of their union, in part order: counts add,
