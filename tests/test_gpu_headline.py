@@ -233,3 +233,33 @@ def test_device_merge_equals_host_merge():
     assert np.all(dev[:, dp.BAD] == 9.0) and np.all(dev[:, dp.N] == 1400)
     st = model.step_stats().cpu().numpy()  # the merge became the context's statistics
     assert np.array_equal(st, dev)
+
+
+@pytest.mark.parametrize("prec", [tv.BF16, tv.FP32])
+def test_train_step_without_adjoint_outputs(prec):
+    # a training step that asks for neither d/dbeta nor d/dJ runs only the
+    # forward strip chain in its contraction pass: its samples, log q and
+    # log Z_R equal those of the same step with d/dbeta requested (same
+    # parameters, seed and step), log Z_R equals tnvan_contract's on those
+    # samples, and sampled rows match the oracle
+    w = wl.workload(2)
+    B = 700  # several CTAs per instance and chunk, ragged last CTA
+    a, b = _model(w, n_inst=3, seed=8), _model(w, n_inst=3, seed=8)
+    out_a, out_b = a.buffers(B), b.buffers(B)
+    dbeta = torch.empty(b.n * B, dtype=torch.float64, device="cuda")
+    a.train_step(B, 17, 4, prec, 0.01, out_a, None, None)
+    b.train_step(B, 17, 4, prec, 0.01, out_b, dbeta, None)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a[0], out_b[0]) and torch.equal(out_a[1], out_b[1])
+    assert torch.allclose(out_a[2], out_b[2], rtol=1e-12, atol=0)
+    lz = torch.empty_like(out_a[2])
+    a.ctx.contract(a.betas, B, out_a[0], prec, lz)
+    torch.cuda.synchronize()
+    assert torch.allclose(lz, out_a[2], rtol=1e-12, atol=0)
+    rows = np.arange(0, B, 97)
+    for k in range(a.n):
+        g, W = w.graphs[k], w.widths_sets[k]
+        s = torch.as_tensor(a.spins_of(out_a[0], k, B).cpu().numpy().astype(np.float64)[rows])
+        ref = transfer.log_zr_lattice(g.n, g.ei, g.ej, g.J, w.betas[k], W, s, g.Lx).numpy()
+        err = np.abs(out_a[2][k * B:(k + 1) * B].cpu().numpy()[rows] - ref).max() / g.n
+        assert err <= TOL_FP32, (k, err)
