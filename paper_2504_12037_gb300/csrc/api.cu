@@ -1505,7 +1505,7 @@ int tnvan_set_made(tnvan_ctx* ctx, int instance, int n_hidden, const int32_t* wi
   for (int p = 0; p < TNVAN_TC_PLANS; ++p) {
     MadeDev::TcGroupPlan& P = md.tcg[p];
     P = MadeDev::TcGroupPlan{};
-    if (n_hidden != 2 || H[0] % 16 || H[1] % 16 || H[0] > 128 || H[1] > 128 || ((D + 15) & ~15) > 256) continue;
+    if (n_hidden != 2 || H[0] % 16 || H[1] % 16 || H[0] > 256 || H[1] > 256 || ((D + 15) & ~15) > 256) continue;
     const int GMAX = kTcGroupMaxG[p], UGMAX = 32;
     auto before = [](const std::vector<int>& c, int d) { return d >= 1 ? c[d - 1] : 0; };  // deg < d
     auto cnt = [&](const std::vector<int>& c, int a, int b) { return before(c, b) - before(c, a); };

@@ -1,12 +1,13 @@
 // BF16 ancestral sampler on tcgen05 (Eq. 6-8), grouped form, for networks
-// with two hidden layers of at most 128 units (multiples of 16) and at most
+// with two hidden layers of at most 256 units (multiples of 16) and at most
 // 256 inputs (padded to a multiple of 16): the fast path where it applies;
 // k_sample_tc.cu holds the general per-step form.
 //
 // One CTA (128 threads, thread = sample = TMEM lane) draws 128 samples; its
 // TMEM footprint is at most 256 columns and its shared memory about 100 KB
 // for the 64-128-128-64 network, so two CTAs share an SM.  Width sets of more
-// than 128 spins (or weight tiles too large for shared memory) stream the
+// than 128 spins, layers of more than 128 units (or weight tiles too large
+// for shared memory) stream the
 // weights instead: each step group carries one BF16 blob (its W2 and Wo
 // windows, and W1's rows of its layer-1 units) that is bulk-copied one group
 // ahead into one of two buffers; 512 TMEM columns, one CTA per SM.  TMEM holds

@@ -31,11 +31,12 @@ def _workload(cfg):
 
 
 # plan values: the grouped form (4, 6, 8 steps per group; two hidden layers
-# of <= 128 units, D <= 256 padded to 16: workloads 2, 4 and 5, the last with
-# weights streamed per group for D = 144 and 256) and the per-step form (12,
-# 16, 32 steps per chunk; every shape)
+# of <= 256 units, D <= 256 padded to 16: workloads 2, 3, 4 and 5, with
+# weights streamed per group for workload 3's 256-unit layers and workload 5's
+# D = 144 and 256) and the per-step form (12, 16, 32 steps per chunk; every
+# shape)
 @pytest.mark.parametrize("cfg,chunk", [(c, v) for c in (1, 2, 3, 4, 5) for v in (12, 16, 32)] +
-                         [(c, v) for c in (2, 4, 5) for v in (4, 6, 8)])
+                         [(c, v) for c in (2, 3, 4, 5) for v in (4, 6, 8)])
 def test_tc_log_prob_matches_oracle_every_workload(cfg, chunk):
     w = _workload(cfg)
     model = _model(w)
