@@ -704,8 +704,13 @@ cudaError_t launch_grad_reduce(const InstDev* d_inst, const LaunchInfo& li, cons
   if (k1 < 0) k1 = li.n_inst;
   if (k1 <= k0) return cudaSuccess;
   // one parameter per thread (the row stride bounds every instance's count),
-  // at most 256 CTAs per instance
-  const dim3 grid((unsigned)std::max(1, std::min(256, (part_stride + 255) / 256)), k1 - k0);
+  // at most 256 CTAs per instance and about 4096 per launch (a launch over
+  // many instances strides instead)
+  const int cap = 4096 / (k1 - k0) > 16 ? 4096 / (k1 - k0) : 16;
+  int gx = (int)((part_stride + 255) / 256);
+  gx = gx < cap ? gx : cap;
+  gx = gx < 256 ? gx : 256;
+  const dim3 grid((unsigned)(gx > 1 ? gx : 1), k1 - k0);
   if (adam)
     grad_reduce_kernel<true><<<grid, 256, 0, s>>>(d_inst, li, partials, part_stride, grad, *adam, k0);
   else
