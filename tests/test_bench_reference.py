@@ -16,8 +16,25 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _workload_config():
+    # the configuration keys the main arm reports for the 16x16 workload
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_main", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    from paper_2504_12037_gb300 import workloads as wl
+
+    w = wl.workload(b.CONFIG)
+    return b.headline_config(w, w.batch)
+
+
 def _check_line(d, n_gpus):
     assert d["impl"] == "reference" and d["n_gpus"] == n_gpus
+    # the same workload configuration as the main arm (its bounded sample in cpu_baseline)
+    cfg = _workload_config()
+    assert {k: d["config"][k] for k in cfg} == cfg
+    assert d["config"]["batch_per_beta"] == 16384 and d["config"]["instances"] == 5
     assert d["value"] > 0 and d["higher_is_better"] is True and d["dtype"] == "f64"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"]
