@@ -96,3 +96,17 @@ def test_mixed_fused_and_unfused_instances(form):
             H1, D = w.hidden[0], model.D[k]
             o = model.offsets[k] + H1 * D
             _check(grad[o:o + H1].cpu().double(), ref[k][H1 * D:H1 * D + H1], False)
+
+
+@pytest.mark.parametrize("hidden", [[64, 128], [128, 64]])
+def test_fused_backward_unequal_hidden_widths(hidden):
+    # the fused kernel's three weight-gradient accumulators with H1 != H2
+    # (TMEM 128 + 80 + (H1 + 16) + (H2 + 16) columns), against the oracle
+    g = wl.lattice(16, 16, "gauss", seed=91)
+    W = wl.width_columns(16, 16, wl.every_kth_column(16))
+    w = wl.Workload("unequal", [g, g], [W, W], hidden, 200, [0.6, 1.0])
+    model, grad, ref, ran = _case(w, 2, 0, batch=200)
+    assert model.ctx.instance_info(0)["fused_bwd"] == 1
+    assert "bwd_fused" in ran
+    for k in range(model.n):
+        _check(grad[model.offsets[k]:model.offsets[k + 1]].cpu().double(), ref[k], False)
